@@ -1,0 +1,231 @@
+"""ctypes front end of the FP64 CPU oracle (``atlas_oracle.c``).
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` import this module. It imports nothing from the
+product package and the product never imports it.
+
+The oracle computes, in plain FP64 C, the octahedral reduced Gaussian grid,
+its zipper triangulation with pole edges, the median-dual geometry and the
+nabla operators (gradient, divergence, Laplacian and the adjoints of gradient
+and divergence) that Atlas supplies (paper Sec. 2.3).  The formulas and the
+readings they follow are stated beside each function in ``atlas_oracle.c``.
+Every function here is pinned by ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "atlas_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+R_EARTH = 6371220.0
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, no GPU)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        lib.orc_build.restype = P
+        lib.orc_build.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_free.argtypes = [P]
+        lib.orc_counts.argtypes = [P, P]
+        lib.orc_gauss_colatitudes.argtypes = [ctypes.c_int, P]
+        lib.orc_get_grid.argtypes = [P, P, P, P, P]
+        lib.orc_get_mesh.argtypes = [P] * 9
+        lib.orc_get_dual.argtypes = [P] * 5
+        lib.orc_gradient.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+        lib.orc_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+        lib.orc_gradient_triplets.restype = i64
+        lib.orc_gradient_triplets.argtypes = [P, P, P, P]
+        lib.orc_divergence_triplets.restype = i64
+        lib.orc_divergence_triplets.argtypes = [P, P, P, P]
+        lib.orc_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
+        lib.orc_closure.argtypes = [P, P, P]
+        for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
+                     "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def gauss_colatitudes(n: int) -> np.ndarray:
+    """Colatitudes (radians, ascending from the north pole) of the n roots of P_n."""
+    out = np.empty(n, dtype=np.float64)
+    if _load().orc_gauss_colatitudes(int(n), _ptr(out)) != 0:
+        raise ValueError("invalid n")
+    return out
+
+
+def _field(x):
+    """Accept a 2-D float32/float64 array [node][level] (any leading dim)."""
+    x = np.asarray(x)
+    if x.ndim == 1:
+        x = x[:, None]
+    if x.dtype not in (np.float32, np.float64):
+        raise TypeError("oracle fields are float32 or float64")
+    if x.strides[1] != x.itemsize:
+        x = np.ascontiguousarray(x)
+    ld = x.strides[0] // x.itemsize
+    return x, int(x.dtype == np.float32), ld
+
+
+class Mesh:
+    """Oracle grid + mesh + median dual for the octahedral grid O<N>."""
+
+    def __init__(self, N: int, R: float = R_EARTH):
+        lib = _load()
+        h = lib.orc_build(int(N), float(R))
+        if not h:
+            raise ValueError("oracle mesh build failed for N=%r" % (N,))
+        self._h = ctypes.c_void_p(h)
+        self._lib = lib
+        self.R = float(R)
+        c = np.zeros(6, dtype=np.int64)
+        lib.orc_counts(self._h, _ptr(c))
+        self.N, self.nlat, self.nnodes, self.ntri, self.nedges, self.nnz = (int(v) for v in c)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.orc_free(h)
+            self._h = None
+
+    # ---------------------------------------------------------------- data
+    def grid(self):
+        pl = np.empty(self.nlat, np.int32)
+        lat = np.empty(self.nlat)
+        colat = np.empty(self.nlat)
+        lonlat = np.empty((self.nnodes, 2))
+        self._lib.orc_get_grid(self._h, _ptr(pl), _ptr(lat), _ptr(colat), _ptr(lonlat))
+        return dict(pl=pl, lat=lat, colat=colat, lon=lonlat[:, 0].copy(), lat_node=lonlat[:, 1].copy())
+
+    def mesh(self):
+        T, E, V = self.ntri, self.nedges, self.nnodes
+        d = dict(tri=np.empty((T, 3), np.int32), tri_r=np.empty((T, 3), np.int32),
+                 tri_j=np.empty((T, 3), np.int32), e2n=np.empty((E, 2), np.int32),
+                 is_pole=np.empty(E, np.uint8), n2e_ptr=np.empty(V + 1, np.int32),
+                 n2e=np.empty(2 * E, np.int32), n2e_sign=np.empty(2 * E, np.int8))
+        self._lib.orc_get_mesh(self._h, *(_ptr(d[k]) for k in
+                                          ("tri", "tri_r", "tri_j", "e2n", "is_pole", "n2e_ptr", "n2e", "n2e_sign")))
+        return d
+
+    def dual(self):
+        d = dict(S=np.empty((self.nedges, 2)), V=np.empty(self.nnodes), coslat=np.empty(self.nnodes),
+                 pole_nphi=np.empty(self.nnodes))
+        self._lib.orc_get_dual(self._h, _ptr(d["S"]), _ptr(d["V"]), _ptr(d["coslat"]), _ptr(d["pole_nphi"]))
+        return d
+
+    def closure(self):
+        res = np.empty((self.nnodes, 2))
+        ab = np.empty(self.nnodes)
+        self._lib.orc_closure(self._h, _ptr(res), _ptr(ab))
+        return res, ab
+
+    # ----------------------------------------------------------- operators
+    def _nodes(self, nodes):
+        if nodes is None:
+            return None, self.nnodes
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        return nodes, int(nodes.shape[0])
+
+    def gradient(self, f, nlev=None, nodes=None):
+        f, f32, ld = _field(f)
+        nlev = f.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        gx = np.empty((n, nlev)); gy = np.empty((n, nlev))
+        rc = self._lib.orc_gradient(self._h, _ptr(f), f32, ld, nlev, _ptr(nodes), n, _ptr(gx), _ptr(gy))
+        if rc:
+            raise ValueError("orc_gradient rc=%d" % rc)
+        return gx, gy
+
+    def divergence(self, u, v, nlev=None, nodes=None):
+        u, f32, ld = _field(u)
+        v, f32v, ldv = _field(v)
+        if (f32, ld) != (f32v, ldv):
+            raise ValueError("u and v need the same dtype and leading dimension")
+        nlev = u.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        rc = self._lib.orc_divergence(self._h, _ptr(u), _ptr(v), f32, ld, nlev, _ptr(nodes), n, _ptr(out))
+        if rc:
+            raise ValueError("orc_divergence rc=%d" % rc)
+        return out
+
+    def laplacian(self, f, nlev=None, nodes=None):
+        f, f32, ld = _field(f)
+        nlev = f.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        rc = self._lib.orc_laplacian(self._h, _ptr(f), f32, ld, nlev, _ptr(nodes), n, _ptr(out))
+        if rc:
+            raise ValueError("orc_laplacian rc=%d" % rc)
+        return out
+
+    def gradient_adjoint(self, y0, y1, nlev=None, nodes=None):
+        y0, f32, ld = _field(y0)
+        y1, f32b, ldb = _field(y1)
+        if (f32, ld) != (f32b, ldb):
+            raise ValueError("y0 and y1 need the same dtype and leading dimension")
+        nlev = y0.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        rc = self._lib.orc_gradient_adjoint(self._h, _ptr(y0), _ptr(y1), f32, ld, nlev, _ptr(nodes), n, _ptr(out))
+        if rc:
+            raise ValueError("orc_gradient_adjoint rc=%d" % rc)
+        return out
+
+    def divergence_adjoint(self, d, nlev=None, nodes=None):
+        d, f32, ld = _field(d)
+        nlev = d.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        xu = np.empty((n, nlev)); xv = np.empty((n, nlev))
+        rc = self._lib.orc_divergence_adjoint(self._h, _ptr(d), f32, ld, nlev, _ptr(nodes), n, _ptr(xu), _ptr(xv))
+        if rc:
+            raise ValueError("orc_divergence_adjoint rc=%d" % rc)
+        return xu, xv
+
+    def gradient_averaged(self, f):
+        f, f32, ld = _field(f)
+        nlev = f.shape[1]
+        gx = np.empty((self.nnodes, nlev)); gy = np.empty((self.nnodes, nlev))
+        self._lib.orc_gradient_averaged(self._h, _ptr(f), f32, ld, nlev, _ptr(gx), _ptr(gy))
+        return gx, gy
+
+    def triplets(self, op: str):
+        fn = {"gradient": self._lib.orc_gradient_triplets, "divergence": self._lib.orc_divergence_triplets}[op]
+        n = int(fn(self._h, None, None, None))
+        rows = np.empty(n, np.int64); cols = np.empty(n, np.int64); vals = np.empty(n)
+        fn(self._h, _ptr(rows), _ptr(cols), _ptr(vals))
+        return rows, cols, vals
