@@ -1,0 +1,438 @@
+"""Benchmark of the nabla operators on O1280 x 137 levels (one GB300).
+
+One step = one pass of the whole operator set on one batch of synthetic
+fields resident in HBM: gradient of f, divergence of (u, v), Laplacian of f,
+gradient adjoint of (u, v) and divergence adjoint of f, each a single fused
+node-stencil kernel, FP32 fields with FP64-built geometry.  The metric is
+node-levels per second over the step (5 * nnodes * nlev per step), plus the
+achieved fraction of the HBM roofline of the dominant kernel; the FP64 and
+BF16-storage forms are timed in the same run and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun every rank runs an independent replica on its own GPU (the
+operators need no exchange on one grid); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Nabla grad node-levels/s & % HBM roofline, FP32 vs FP64, O1280 x 137 levels"
+N_GRID, NLEV = 1280, 137
+OPS = ("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint")
+# (inputs, outputs) per operator
+IO = {"gradient": (1, 2), "divergence": (2, 1), "laplacian": (1, 1), "gradient_adjoint": (2, 1),
+      "divergence_adjoint": (1, 2)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _fields_torch(torch, lon, lat, nlev, ld, dtype, device, seed):
+    """Synthetic fields of the standard recipe (base field scaled by
+    1 + 0.01 k plus N(0, 1e-3^2) noise) generated on the device with a seeded
+    torch generator, stored [node][ld] with zero padding."""
+    import synthetic
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    lon_t = torch.from_numpy(lon).to(device)
+    lat_t = torch.from_numpy(lat).to(device)
+    scale = 1.0 + 0.01 * torch.arange(nlev, device=device, dtype=torch.float64)
+    bs = torch.from_numpy(synthetic.base_scalar(lon, lat)).to(device)
+    bu, bv = (torch.from_numpy(x).to(device) for x in synthetic.base_vector(lon, lat))
+    del lon_t, lat_t
+    out = []
+    for base in (bs, bu, bv):
+        t = torch.zeros((base.shape[0], ld), dtype=dtype, device=device)
+        V = base.shape[0]
+        step = 1 << 20
+        for i0 in range(0, V, step):
+            i1 = min(V, i0 + step)
+            blk = base[i0:i1, None] * scale[None, :]
+            blk = blk + synthetic.NOISE_SIGMA * torch.randn((i1 - i0, nlev), generator=g, device=device,
+                                                            dtype=torch.float64)
+            t[i0:i1, :nlev] = blk.to(dtype)
+        out.append(t)
+    return out
+
+
+def _run_step(fvm, f, u, v, outs, nlev):
+    gx, gy, d, lap, ga, du, dv = outs
+    fvm.gradient(f, nlev, out=(gx, gy))
+    fvm.divergence(u, v, nlev, out=d)
+    fvm.laplacian(f, nlev, out=lap)
+    fvm.gradient_adjoint(u, v, nlev, out=ga)
+    fvm.divergence_adjoint(f, nlev, out=(du, dv))
+
+
+def _time_ops(torch, fvm, f, u, v, outs, nlev, steps, warmup, barrier):
+    """Warm up, then time `steps` steps with CUDA events on the launching
+    stream: whole-step time and per-operator kernel time."""
+    gx, gy, d, lap, ga, du, dv = outs
+    calls = [lambda: fvm.gradient(f, nlev, out=(gx, gy)), lambda: fvm.divergence(u, v, nlev, out=d),
+             lambda: fvm.laplacian(f, nlev, out=lap), lambda: fvm.gradient_adjoint(u, v, nlev, out=ga),
+             lambda: fvm.divergence_adjoint(f, nlev, out=(du, dv))]
+    for _ in range(warmup):
+        for c in calls:
+            c()
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(steps):
+        ev[s][0].record(stream)
+        for k, c in enumerate(calls):
+            c()
+            ev[s][k + 1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = t0.elapsed_time(t1)
+    per_op = [0.0] * len(calls)
+    for s in range(steps):
+        for k in range(len(calls)):
+            per_op[k] += ev[s][k].elapsed_time(ev[s][k + 1])
+    return total_ms, [p / steps for p in per_op]
+
+
+def _alg_bytes(op, V, nlev, esize, table_bytes):
+    nin, nout = IO[op]
+    return (nin + nout) * V * nlev * esize + table_bytes
+
+
+_NNZ = {}
+
+
+def _table_bytes(fvm, op, wbytes):
+    if op not in _NNZ:
+        _NNZ[op] = fvm.stencil_table(op)["nbr"].shape[0]
+    nnz = _NNZ[op]
+    V = fvm.nnodes
+    has_b = op in ("divergence", "gradient_adjoint", "divergence_adjoint")
+    nw = 1 if op == "laplacian" else 2
+    return 4 * (V + 1) + nnz * (4 + nw * wbytes) + (2 * wbytes * V if has_b else 0)
+
+
+def _cpu_baseline(fvm_nodes, f_host, u_host, v_host, nlev, budget_s=12.0):
+    """The oracle as it stands, single-threaded, on a contiguous node sample
+    of the same workload (all five operators)."""
+    from oracle.oracle import Mesh
+    om = Mesh(N_GRID)
+    n = 64
+    while True:
+        nodes = np.arange(0, n, dtype=np.int64) + fvm_nodes // 3
+        t = time.perf_counter()
+        om.gradient(f_host, nlev, nodes=nodes)
+        om.divergence(u_host, v_host, nlev, nodes=nodes)
+        om.laplacian(f_host, nlev, nodes=nodes)
+        om.gradient_adjoint(u_host, v_host, nlev, nodes=nodes)
+        om.divergence_adjoint(f_host, nlev, nodes=nodes)
+        dt = time.perf_counter() - t
+        if dt > budget_s / 4 or n >= fvm_nodes:
+            break
+        n = min(fvm_nodes, int(n * max(2.0, budget_s / max(dt, 1e-3) / 2)))
+    value = 5 * n * nlev / dt
+    return {"value": value, "unit": "node-levels/s", "cores": 1, "kind": "oracle",
+            "sample": "nodes %d..%d of O1280 (%d nodes) x %d levels, all five operators, %.1f s" %
+                      (int(nodes[0]), int(nodes[-1]), n, nlev, dt)}
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1908_07038_gb300 import atlas
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    nlev = NLEV
+    fvm = atlas.build_fvm(N_GRID)
+    V = fvm.nnodes
+    g = fvm.grid.arrays()
+    fvm.prepare(OPS, dtypes=(atlas.ATLAS_F32, atlas.ATLAS_F64, atlas.ATLAS_BF16))
+    hbm, peak_kind = _peaks()
+
+    # ------------------------------------------------------------ FP32 main
+    ld = 140
+    f, u, v = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ld, torch.float32, "cuda", 1234 + rank)
+    outs = [torch.empty_like(f) for _ in range(7)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, per_op = _time_ops(torch, fvm, f, u, v, outs, nlev, args.steps, args.warmup, barrier)
+    clocks = sampler.stop()
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    node_levels_step = 5 * V * nlev
+    value = ws * node_levels_step / (ms_step * 1e-3)
+
+    # per-op roofline (algorithmic bytes / average kernel time)
+    tables = {op: _table_bytes(fvm, op, 4) for op in OPS}
+    per = {}
+    for op, ms in zip(OPS, per_op):
+        b = _alg_bytes(op, V, nlev, 4, tables[op])
+        per[op] = {"ms": round(ms, 4), "node_levels_per_s": V * nlev / (ms * 1e-3),
+                   "alg_bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / hbm}
+    dom = max(OPS, key=lambda o: per[o]["ms"])
+    roofline = {"bound": "hbm", "kernel": "stencil_kernel<%s>" % dom, "achieved": round(per[dom]["gbs"], 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(per[dom]["frac"], 4), "traffic": None,
+                "peak_kind": peak_kind}
+
+    # ---------------------------------------------------------------- e2e
+    e2e = None
+    if not args.no_e2e:
+        hin = [t.cpu().pin_memory() for t in (f, u, v)]
+        hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+        nbytes = f.numel() * f.element_size()
+        stream = torch.cuda.current_stream()
+
+        def e2e_step():
+            for h, dv in zip(hin, (f, u, v)):
+                atlas.field_sync(dv.data_ptr(), h.data_ptr(), nbytes, 0)
+            _run_step(fvm, f, u, v, outs, nlev)
+            for h, dv in zip(hout, outs):
+                atlas.field_sync(h.data_ptr(), dv.data_ptr(), nbytes, 1)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ksteps = max(2, min(args.steps, 5))
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = a.elapsed_time(b) / ksteps
+        e2e = {"value": ws * node_levels_step / (e_ms * 1e-3), "unit": "node-levels/s",
+               "h2d_bytes_per_step": 3 * nbytes, "d2h_bytes_per_step": 7 * nbytes, "ms_per_step": round(e_ms, 3),
+               "steps": ksteps}
+        del hin, hout
+
+    # ------------------------------------------------ FP64 and BF16 beside
+    side = {}
+    if not args.no_side:
+        f_host = f[:, :nlev].cpu().numpy() if rank == 0 and not args.no_cpu_baseline else None
+        u_host = u[:, :nlev].cpu().numpy() if f_host is not None else None
+        v_host = v[:, :nlev].cpu().numpy() if f_host is not None else None
+        del f, u, v, outs
+        torch.cuda.empty_cache()
+        for name, dt, ldx, es, wb in (("fp64", torch.float64, 138, 8, 8), ("bf16", torch.bfloat16, 144, 2, 4)):
+            fx, ux, vx = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ldx, dt, "cuda", 99 + rank)
+            ox = [torch.empty_like(fx) for _ in range(7)]
+            k = max(3, args.steps // 4)
+            tms, pops = _time_ops(torch, fvm, fx, ux, vx, ox, nlev, k, 3, barrier)
+            entry = {"ms_per_step": round(tms / k, 4), "node_levels_per_s": node_levels_step / (tms / k * 1e-3),
+                     "per_op": {}}
+            for op, ms in zip(OPS, pops):
+                bytes_ = _alg_bytes(op, V, nlev, es, _table_bytes(fvm, op, wb) if name == "fp64" else tables[op])
+                entry["per_op"][op] = {"ms": round(ms, 4), "node_levels_per_s": V * nlev / (ms * 1e-3),
+                                       "frac_hbm": round(bytes_ / (ms * 1e-3) / 1e9 / hbm, 4)}
+            side[name] = entry
+            del fx, ux, vx, ox
+            torch.cuda.empty_cache()
+    else:
+        f_host = None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and f_host is not None:
+        cpu = _cpu_baseline(V, f_host, u_host, v_host, nlev)
+
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "node-levels/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "O1280 octahedral grid (%d nodes, %d edges) x %d levels, field[node][ld=%d] FP32, "
+                               "FP64-built geometry; step = gradient + divergence + Laplacian + gradient adjoint "
+                               "+ divergence adjoint" % (V, fvm.mesh.nedges, nlev, ld),
+                   "l2": "inputs larger than L2 (3.7 GB per field), no flush", "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roofline, "per_op": {k: {"ms": v_["ms"], "node_levels_per_s": v_["node_levels_per_s"],
+                                             "frac_hbm": round(v_["frac"], 4)} for k, v_ in per.items()},
+        "side_by_side": side, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        "gpu_launches": 5 * args.steps,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on a bounded node sample of the same
+    workload; rank 0 only."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import synthetic
+    from oracle.oracle import Mesh
+    om = Mesh(N_GRID)
+    g = om.grid()
+    nlev = NLEV
+    # fields on a band of rows around the sample (the operators need the 2-ring)
+    off = np.concatenate([[0], np.cumsum(g["pl"])])
+    r0 = N_GRID // 2
+    lo, hi = off[r0 - 3], off[r0 + 4]
+    f = np.zeros((om.nnodes, nlev), np.float32)
+    u = np.zeros_like(f)
+    v = np.zeros_like(f)
+    sl = slice(lo, hi)
+    f[sl] = synthetic.level_scalar(g["lon"][sl], g["lat_node"][sl], nlev, np.float32)
+    u[sl], v[sl] = synthetic.level_vector(g["lon"][sl], g["lat_node"][sl], nlev, np.float32)
+    budget = float(os.environ.get("ORACLE_STEP_SECONDS", "2"))
+    n = 16
+    base = off[r0]
+    while True:
+        nodes = np.arange(base, base + n, dtype=np.int64)
+        t = time.perf_counter()
+        for _ in range(1):
+            om.gradient(f, nlev, nodes=nodes)
+            om.divergence(u, v, nlev, nodes=nodes)
+            om.laplacian(f, nlev, nodes=nodes)
+            om.gradient_adjoint(u, v, nlev, nodes=nodes)
+            om.divergence_adjoint(f, nlev, nodes=nodes)
+        dt = time.perf_counter() - t
+        if dt > budget / 4 or n >= g["pl"][r0]:
+            break
+        n = min(int(g["pl"][r0]), int(n * max(2.0, budget / max(dt, 1e-3) / 2)))
+    for _ in range(args.warmup):
+        om.gradient(f, nlev, nodes=nodes)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        om.gradient(f, nlev, nodes=nodes)
+        om.divergence(u, v, nlev, nodes=nodes)
+        om.laplacian(f, nlev, nodes=nodes)
+        om.gradient_adjoint(u, v, nlev, nodes=nodes)
+        om.divergence_adjoint(f, nlev, nodes=nodes)
+    el = time.perf_counter() - t0
+    value = 5 * n * nlev * args.steps / el
+    sample = "%d nodes of row %d of O1280 x %d levels per step, all five operators" % (n, r0, nlev)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-levels/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "O1280 octahedral grid x 137 levels (node sample), FP32 fields upcast to FP64"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": "node-levels/s"},
+            "e2e": {"value": value, "unit": "node-levels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-side", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * atlas_gb.h -- C ABI of libatlasgb.so: median-dual finite-volume nabla
+ * operators (gradient, divergence, Laplacian and the adjoints of gradient and
+ * divergence) on multi-level fields over the octahedral reduced Gaussian grid,
+ * computed by CUDA kernels on one GB300 (sm_103a).
+ *
+ * The paper (ESCAPE D2.3, the Atlas release) describes the workflow
+ * Grid -> Mesh -> FunctionSpace -> Field (Sec. 2.3, Fig. 1 and Fig. 2), says
+ * that Atlas supplies gradient, divergence, curl and Laplacian operators
+ * on it (Sec. 2.3), exposes its C++ objects through C interfaces holding raw
+ * pointers (Sec. 4.1, Fig. 3), keeps Fields in host and device memory that
+ * are synchronised explicitly (Sec. 4.2, Listings 3 and 4), and brackets use
+ * of the library with initialise/finalise (Sec. 3.5, Listings 1 and 2).  The
+ * calls below follow that shape.
+ *
+ * Conventions (all calls):
+ *   - Return 0 on success or a negative ATLAS_E* code; atlas_last_error()
+ *     then returns a message (thread-local, valid until the next call on the
+ *     same thread).  No C++ exception crosses this interface.
+ *   - Handles (atlas_grid_t, atlas_mesh_t, atlas_fvm_t, atlas_batch_t) are
+ *     owned by the library and released by the matching *_destroy call.  A
+ *     mesh keeps a reference to its grid and an fvm to its mesh: destroy in
+ *     reverse order of creation.
+ *   - Field pointers are DEVICE pointers owned by the caller (for example
+ *     torch tensors); the library never frees them.  A field is stored
+ *     field[node][level]: node i, level k at element offset i*ld + k, with
+ *     nlev >= 0 levels and leading dimension ld >= nlev (elements).  Levels
+ *     nlev..ld-1 of an output are never written.  Nodes are numbered row by
+ *     row from north to south, and within a row by increasing longitude
+ *     starting at 0.
+ *   - dtype selects the storage type of every field argument of the call:
+ *     ATLAS_F32 (float, FP32 arithmetic), ATLAS_F64 (double, FP64
+ *     arithmetic) or ATLAS_BF16 (bfloat16 storage, FP32 arithmetic).
+ *     Geometry is FP64 on the host and converted once per dtype.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Operator
+ *     calls only enqueue work and return; a kernel that fails to launch is
+ *     reported as ATLAS_ECUDA, faults during execution surface at the
+ *     caller's next synchronisation.  The first operator call of a kind on an
+ *     fvm builds and uploads that operator's tables synchronously (or call
+ *     atlas_fvm_prepare first); keep first calls out of CUDA-graph capture.
+ *   - Pointers must be aligned to the element size; the vectorised paths
+ *     additionally need 16-byte aligned rows (ld a multiple of 16/sizeof),
+ *     and fall back to element-wise loads otherwise.
+ *   - Input and output fields of one call must not overlap.
+ *   - No call ever computes on the CPU: without a CUDA device every operator
+ *     call fails with ATLAS_ECUDA.
+ */
+#ifndef ATLAS_GB_H
+#define ATLAS_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct atlas_grid_s* atlas_grid_t;
+typedef struct atlas_mesh_s* atlas_mesh_t;
+typedef struct atlas_fvm_s* atlas_fvm_t;
+typedef struct atlas_batch_s* atlas_batch_t;
+
+typedef enum { ATLAS_F32 = 0, ATLAS_F64 = 1, ATLAS_BF16 = 2 } atlas_dtype;
+
+enum {
+  ATLAS_OK = 0,
+  ATLAS_EINVAL = -1,  /* invalid argument (null pointer, size, ld < nlev, ...) */
+  ATLAS_ENOMEM = -2,  /* host or device allocation failed */
+  ATLAS_ECUDA = -3,   /* CUDA runtime error, or no CUDA device */
+  ATLAS_EALIGN = -4,  /* pointer not aligned to its element size */
+  ATLAS_EDTYPE = -5,  /* unsupported dtype */
+  ATLAS_ESTATE = -6   /* handle in the wrong state (destroyed, wrong device) */
+};
+
+/* Operator identifiers (atlas_fvm_prepare masks use 1 << op). */
+enum {
+  ATLAS_OP_GRADIENT = 0,
+  ATLAS_OP_DIVERGENCE = 1,
+  ATLAS_OP_GRADIENT_ADJOINT = 2,
+  ATLAS_OP_DIVERGENCE_ADJOINT = 3,
+  ATLAS_OP_LAPLACIAN = 4
+};
+
+/* ---------------------------------------------------------------------- */
+/* Library lifecycle (paper Sec. 3.5, Listings 1-2: initialise/finalise). */
+/* Both are idempotent and optional; finalize releases nothing the caller  */
+/* still holds.                                                            */
+/* ---------------------------------------------------------------------- */
+int atlas_init(void);
+int atlas_finalize(void);
+/* Version string and a one-line feature report (GPU name, sm, build).   */
+const char* atlas_version(void);
+const char* atlas_info(void);
+const char* atlas_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Grid (paper Sec. 2.3: "a predefined list of two-dimensional points";   */
+/* the O<N> octahedral grid is named in Sec. 4.3, Fig. 4).                 */
+/* ---------------------------------------------------------------------- */
+/* Octahedral reduced Gaussian grid O<N>, 1 <= N <= 8000: 2N Gaussian      */
+/* latitudes (roots of the Legendre polynomial P_2N, north to south); row  */
+/* r holds 4i+16 equally spaced longitudes starting at 0, i = r+1 for      */
+/* r < N and 2N-r otherwise; 4N^2+36N points.                              */
+int atlas_grid_octahedral(int N, atlas_grid_t* out);
+/* Views into library-owned arrays, valid until atlas_grid_destroy:        */
+/* nnodes, nlat = 2N, pl[nlat] points per row, lonlat[nnodes][2]           */
+/* (longitude, latitude in radians), lat[nlat] row latitudes (radians).    */
+/* Any output pointer may be NULL.                                         */
+int atlas_grid_info(atlas_grid_t g, int64_t* nnodes, int* nlat, const int32_t** pl,
+                    const double** lonlat, const double** lat);
+void atlas_grid_destroy(atlas_grid_t g);
+
+/* ---------------------------------------------------------------------- */
+/* Mesh (paper Sec. 2.3: connectivity of elements, edges and nodes).       */
+/* ---------------------------------------------------------------------- */
+/* Zipper triangulation of every pair of adjacent rows (advance on the row */
+/* whose next longitude is smaller; on a tie the row with fewer points,    */
+/* between equal rows the northern one), plus pole edges joining node j to */
+/* j + n/2 on the first and last row.  Edges are (a, b) with a < b, sorted */
+/* by (a, b); 4N^2+36N nodes give 2V-40 triangles and 3V-20 edges.          */
+int atlas_mesh_build(atlas_grid_t g, atlas_mesh_t* out);
+/* Views valid until atlas_mesh_destroy: e2n[E][2], is_pole[E],            */
+/* n2e_ptr[V+1], n2e[2E] (ascending edge ids per node), n2e_sign[2E]       */
+/* (+1 where the node is the edge's a, -1 where it is b), tri[T][3].       */
+int atlas_mesh_info(atlas_mesh_t m, int64_t* nedges, int64_t* ntri, const int32_t** e2n,
+                    const uint8_t** is_pole, const int32_t** n2e_ptr, const int32_t** n2e,
+                    const int8_t** n2e_sign, const int32_t** tri);
+void atlas_mesh_destroy(atlas_mesh_t m);
+
+/* ---------------------------------------------------------------------- */
+/* Finite-volume geometry (the FunctionSpace of nodes, paper Sec. 2.3).    */
+/* ---------------------------------------------------------------------- */
+/* Median dual in the (lon, lat) plane with radius R (metres): every node  */
+/* owns the polygon of its side midpoints and triangle centroids, extended */
+/* to the pole on the first and last rows.  V_i = R^2 * integral of        */
+/* cos(lat) over the cell; S_e = R (dlat, -dlon) integrated along the dual */
+/* face of edge e from cell a into cell b; pole edges carry the pole       */
+/* segment normal (0, +-2 pi R / n).  Everything is FP64 on the host; the  */
+/* call also records the current CUDA device, on which every operator of  */
+/* this fvm must then run.                                                 */
+int atlas_fvm_build_dual(atlas_mesh_t m, double radius, atlas_fvm_t* out);
+/* Host FP64 views valid until atlas_fvm_destroy: V[nnodes], S[E][2],      */
+/* coslat[nnodes], pole_nphi[nnodes] (phi-normal of the pole segment).     */
+int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const double** coslat,
+                   const double** pole_nphi);
+/* Build and upload the tables of the operators in op_mask (bits 1<<op)    */
+/* for the dtypes in dtype_mask (bits 1<<dtype).  Synchronous.             */
+int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
+/* Launch shape of the node-stencil kernels for one operator: levels per   */
+/* thread (vec: 1, 2, 4 or 8; 0 = default for the dtype), threads per     */
+/* block (64..1024, multiple of 32) and blocks per SM (1..32).  Any zero   */
+/* field keeps the current value.                                          */
+int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int threads, int blocks_per_sm);
+/* Inspection: copy out the FP64 host table of one operator's node stencil */
+/*   out_c(i) = sum_{q in [ptr[i], ptr[i+1])} sum_m W_cm(q) (x_m(nbr[q]) - x_m(i))  */
+/*              + sum_m B_cm(i) x_m(i)                                     */
+/* (w[q][2] = (W_00, W_10) for one input, (W_00, W_01) for two; the        */
+/* Laplacian uses w[q][0] only; b[i][2] is zero when the operator has no  */
+/* B term).  Call once with NULL arrays to get nnz, nin and nout, then     */
+/* with ptr[V+1], nbr[nnz], w[nnz][2], b[V][2].  Host only: works without */
+/* a GPU; the device tables are rounded copies of these.                   */
+int atlas_fvm_stencil_table(atlas_fvm_t f, int op, int64_t* nnz, int* nin, int* nout, int32_t* ptr,
+                            int32_t* nbr, double* w, double* b);
+void atlas_fvm_destroy(atlas_fvm_t f);
+
+/* ---------------------------------------------------------------------- */
+/* Nabla operators (paper Sec. 2.3: gradient, divergence, Laplacian).      */
+/* Every operator is deterministic: no atomics, fixed summation order.    */
+/* ---------------------------------------------------------------------- */
+/* Gradient: gx = (1/V_i) sum_e n_ie,lon (f_j - f_i)/2,                    */
+/*           gy = (cos(lat_i)/V_i) sum_e n_ie,lat (f_j - f_i)/2,           */
+/* summed over the edges e = (i, j) of node i including its pole edge;     */
+/* n_ie = +-S_e (sign of i in e) on regular edges and S_e on pole edges.   */
+/* Because every dual cell is closed this equals the Green's-theorem form  */
+/* with face values (f_a + f_b)/2.  Units: 1/m.  in: f; out: gx, gy.       */
+int atlas_nabla_gradient(atlas_fvm_t fvm, const void* f, void* gx, void* gy, int nlev, int64_t ld,
+                         atlas_dtype dtype, void* stream);
+/* Divergence of the vector (u, v) in physical components:                 */
+/* V_i div_i = sum_{regular e} n_ie . (F_j - F_i)/2 - F_i . n_pole,i,      */
+/* F = (u, v cos(lat)): the flux form with zero flux through the pole.     */
+int atlas_nabla_divergence(atlas_fvm_t fvm, const void* u, const void* v, void* div, int nlev,
+                           int64_t ld, atlas_dtype dtype, void* stream);
+/* Laplacian = divergence of the gradient, applied as one fused two-ring   */
+/* stencil L = D G (no intermediate field).                                */
+int atlas_nabla_laplacian(atlas_fvm_t fvm, const void* f, void* lap, int nlev, int64_t ld,
+                          atlas_dtype dtype, void* stream);
+/* Adjoints: the exact transposes of the gradient (f = G^T (gx, gy)) and   */
+/* divergence ((u, v) = D^T d) maps, written as gathers.                   */
+int atlas_nabla_gradient_adjoint(atlas_fvm_t fvm, const void* gx, const void* gy, void* f, int nlev,
+                                 int64_t ld, atlas_dtype dtype, void* stream);
+int atlas_nabla_divergence_adjoint(atlas_fvm_t fvm, const void* div, void* u, void* v, int nlev,
+                                   int64_t ld, atlas_dtype dtype, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Edge-based two-kernel forms: an edge-flux kernel writes one flux per    */
+/* edge and level into a caller-owned device workspace, then a node-gather */
+/* kernel sums each node's CSR row of fluxes.  Same results as the fused   */
+/* calls up to rounding.  ws must hold atlas_nabla_workspace_bytes(...)    */
+/* bytes, 256-byte aligned; its contents on entry are ignored.             */
+/* ---------------------------------------------------------------------- */
+size_t atlas_nabla_workspace_bytes(atlas_fvm_t fvm, int op, int nlev, int64_t ld, atlas_dtype dtype);
+int atlas_nabla_gradient_edges(atlas_fvm_t fvm, const void* f, void* gx, void* gy, void* ws,
+                               size_t ws_bytes, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
+int atlas_nabla_divergence_edges(atlas_fvm_t fvm, const void* u, const void* v, void* div, void* ws,
+                                 size_t ws_bytes, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
+/* grad into ws, then div of it: the two-pass Laplacian.                   */
+int atlas_nabla_laplacian_edges(atlas_fvm_t fvm, const void* f, void* lap, void* ws, size_t ws_bytes,
+                                int nlev, int64_t ld, atlas_dtype dtype, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched launch: many fields of different grids and level counts in one */
+/* persistent kernel (one launch, capturable in a CUDA graph).            */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  int op;              /* ATLAS_OP_GRADIENT or ATLAS_OP_DIVERGENCE           */
+  atlas_fvm_t fvm;     /* geometry of this field's grid                      */
+  const void* in0;     /* f (gradient) or u (divergence)                     */
+  const void* in1;     /* NULL (gradient) or v (divergence)                  */
+  void* out0;          /* gx (gradient) or div (divergence)                  */
+  void* out1;          /* gy (gradient) or NULL                              */
+  int nlev;
+  int64_t ld;
+} atlas_batch_desc;
+/* Work split: each descriptor is cut into tiles of tile_items (node,      */
+/* level-vector) items; vec levels per thread (1, 2 or 4; ld must be a     */
+/* multiple of vec for vec > 1), threads per block, blocks per SM of the   */
+/* persistent grid.  Zero fields take the defaults.                        */
+typedef struct {
+  int vec;
+  int tile_items;
+  int threads;
+  int blocks_per_sm;
+} atlas_batch_tune;
+/* Validates the descriptors, uploads them and the tile table to device    */
+/* memory (owned by the batch) and prepares every fvm's tables.  dtype is  */
+/* ATLAS_F32 or ATLAS_F64 for all fields of the batch.  The field pointers  */
+/* are fixed at creation; re-create the batch for other fields.            */
+int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, const atlas_batch_tune* tune,
+                       atlas_batch_t* out);
+/* One persistent launch over every tile of every descriptor.              */
+int atlas_batch_launch(atlas_batch_t b, void* stream);
+/* Total tiles and total (node, level) pairs of the batch.                  */
+int atlas_batch_info(atlas_batch_t b, int64_t* tiles, int64_t* node_levels);
+void atlas_batch_destroy(atlas_batch_t b);
+
+/* ---------------------------------------------------------------------- */
+/* Field synchronisation (paper Sec. 4.2: update_host after device work).  */
+/* One cudaMemcpyAsync of bytes from src to dst on stream; direction 0 =   */
+/* host to device, 1 = device to host, 2 = device to device.  Host memory  */
+/* should be pinned for the copy to be asynchronous.                       */
+/* ---------------------------------------------------------------------- */
+int atlas_field_sync(void* dst, const void* src, size_t bytes, int direction, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATLAS_GB_H */

@@ -1,0 +1,329 @@
+"""Object wrappers over the C ABI (handles) and torch conveniences.
+
+``Grid`` -> ``Mesh`` -> ``Fvm`` mirrors the paper's Grid -> Mesh ->
+FunctionSpace workflow (Sec. 2.3, Fig. 2).  The operator methods of ``Fvm``
+take torch CUDA tensors shaped [nnodes, ld] (field[node][level], levels
+innermost) and call the C ABI on torch's current stream; torch only provides
+the device memory and the stream.  ``GradientFn`` / ``DivergenceFn`` wrap the
+forward kernels and their hand-written adjoint kernels as autograd functions.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+from .capi import ATLAS_BF16, ATLAS_F32, ATLAS_F64
+
+R_EARTH = 6371220.0
+
+OPS = {"gradient": capi.ATLAS_OP_GRADIENT, "divergence": capi.ATLAS_OP_DIVERGENCE,
+       "gradient_adjoint": capi.ATLAS_OP_GRADIENT_ADJOINT,
+       "divergence_adjoint": capi.ATLAS_OP_DIVERGENCE_ADJOINT, "laplacian": capi.ATLAS_OP_LAPLACIAN}
+
+
+def _view(ptr, ctype, n, shape=None, dtype=None):
+    if n == 0:
+        return np.zeros(shape or (0,), dtype=dtype)
+    arr = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), shape=(n,))
+    arr = arr.copy()
+    return arr.reshape(shape) if shape else arr
+
+
+class Grid:
+    """Octahedral reduced Gaussian grid O<N> (library-owned handle)."""
+
+    def __init__(self, N: int):
+        h = ctypes.c_void_p()
+        capi.atlas_grid_octahedral(int(N), ctypes.byref(h))
+        self.handle = h
+        self.N = int(N)
+        nn = ctypes.c_int64()
+        nl = ctypes.c_int()
+        capi.atlas_grid_info(h, ctypes.byref(nn), ctypes.byref(nl), None, None, None)
+        self.nnodes, self.nlat = nn.value, nl.value
+
+    def arrays(self):
+        pl, ll, lat = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        capi.atlas_grid_info(self.handle, None, None, ctypes.byref(pl), ctypes.byref(ll), ctypes.byref(lat))
+        lonlat = _view(ll, ctypes.c_double, 2 * self.nnodes, (self.nnodes, 2))
+        return dict(pl=_view(pl, ctypes.c_int32, self.nlat), lat=_view(lat, ctypes.c_double, self.nlat),
+                    lon=lonlat[:, 0].copy(), lat_node=lonlat[:, 1].copy())
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            capi.atlas_grid_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    """Zipper triangulation + pole edges + CSR of a Grid."""
+
+    def __init__(self, grid: Grid):
+        h = ctypes.c_void_p()
+        capi.atlas_mesh_build(grid.handle, ctypes.byref(h))
+        self.handle = h
+        self.grid = grid
+        ne, nt = ctypes.c_int64(), ctypes.c_int64()
+        capi.atlas_mesh_info(h, ctypes.byref(ne), ctypes.byref(nt), None, None, None, None, None, None)
+        self.nedges, self.ntri = ne.value, nt.value
+
+    def arrays(self):
+        ptrs = [ctypes.c_void_p() for _ in range(6)]
+        capi.atlas_mesh_info(self.handle, None, None, *(ctypes.byref(p) for p in ptrs))
+        V, E, T = self.grid.nnodes, self.nedges, self.ntri
+        e2n, pole, ptr, n2e, sgn, tri = ptrs
+        return dict(e2n=_view(e2n, ctypes.c_int32, 2 * E, (E, 2)), is_pole=_view(pole, ctypes.c_uint8, E),
+                    n2e_ptr=_view(ptr, ctypes.c_int32, V + 1), n2e=_view(n2e, ctypes.c_int32, 2 * E),
+                    n2e_sign=_view(sgn, ctypes.c_int8, 2 * E), tri=_view(tri, ctypes.c_int32, 3 * T, (T, 3)))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            capi.atlas_mesh_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _torch():
+    import torch
+    return torch
+
+
+_DTYPES = None
+
+
+def _dtype_code(t):
+    global _DTYPES
+    torch = _torch()
+    if _DTYPES is None:
+        _DTYPES = {torch.float32: ATLAS_F32, torch.float64: ATLAS_F64, torch.bfloat16: ATLAS_BF16}
+    try:
+        return _DTYPES[t.dtype]
+    except KeyError:
+        raise TypeError("fields must be float32, float64 or bfloat16 (got %s)" % t.dtype) from None
+
+
+def _stream():
+    return _torch().cuda.current_stream().cuda_stream
+
+
+class Fvm:
+    """Median-dual geometry of a Mesh with radius R, plus the operator calls."""
+
+    def __init__(self, mesh: Mesh, radius: float = R_EARTH):
+        h = ctypes.c_void_p()
+        capi.atlas_fvm_build_dual(mesh.handle, float(radius), ctypes.byref(h))
+        self.handle = h
+        self.mesh = mesh
+        self.grid = mesh.grid
+        self.R = float(radius)
+        self.nnodes = mesh.grid.nnodes
+
+    # ----------------------------------------------------------- geometry
+    def arrays(self):
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        capi.atlas_fvm_info(self.handle, *(ctypes.byref(p) for p in ptrs))
+        V, E = self.nnodes, self.mesh.nedges
+        return dict(V=_view(ptrs[0], ctypes.c_double, V), S=_view(ptrs[1], ctypes.c_double, 2 * E, (E, 2)),
+                    coslat=_view(ptrs[2], ctypes.c_double, V), pole_nphi=_view(ptrs[3], ctypes.c_double, V))
+
+    def prepare(self, ops=("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint"),
+                dtypes=(ATLAS_F32,)):
+        om = 0
+        for o in ops:
+            om |= 1 << OPS[o]
+        dm = 0
+        for d in dtypes:
+            dm |= 1 << d
+        capi.atlas_fvm_prepare(self.handle, om, dm)
+
+    def stencil_table(self, op):
+        """FP64 host table of one operator's node stencil (inspection)."""
+        code = OPS.get(op, op)
+        nnz, nin, nout = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        capi.atlas_fvm_stencil_table(self.handle, code, ctypes.byref(nnz), ctypes.byref(nin), ctypes.byref(nout),
+                                     None, None, None, None)
+        V, n = self.nnodes, nnz.value
+        ptr = np.empty(V + 1, np.int32)
+        nbr = np.empty(max(n, 1), np.int32)
+        w = np.empty((max(n, 1), 2))
+        b = np.empty((V, 2))
+        capi.atlas_fvm_stencil_table(self.handle, code, None, None, None, ptr.ctypes.data, nbr.ctypes.data,
+                                     w.ctypes.data, b.ctypes.data)
+        return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
+
+    def set_launch(self, op, vec=0, threads=0, blocks_per_sm=0):
+        capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(vec), int(threads), int(blocks_per_sm))
+
+    # ---------------------------------------------------------- operators
+    def _check(self, *ts):
+        t0 = ts[0]
+        for t in ts:
+            if not t.is_cuda or t.dim() != 2 or t.shape[0] != self.nnodes or t.stride(1) != 1:
+                raise ValueError("fields must be CUDA tensors [nnodes=%d, ld] with unit level stride" % self.nnodes)
+            if t.dtype != t0.dtype or t.stride(0) != t0.stride(0):
+                raise ValueError("all fields of one call need the same dtype and leading dimension")
+        return _dtype_code(t0), t0.stride(0)
+
+    def _out(self, like, out):
+        return _torch().empty_like(like) if out is None else out
+
+    def gradient(self, f, nlev=None, out=None):
+        gx, gy = out if out is not None else (self._out(f, None), self._out(f, None))
+        dt, ld = self._check(f, gx, gy)
+        capi.atlas_nabla_gradient(self.handle, f.data_ptr(), gx.data_ptr(), gy.data_ptr(),
+                                  f.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return gx, gy
+
+    def divergence(self, u, v, nlev=None, out=None):
+        d = self._out(u, out)
+        dt, ld = self._check(u, v, d)
+        capi.atlas_nabla_divergence(self.handle, u.data_ptr(), v.data_ptr(), d.data_ptr(),
+                                    u.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return d
+
+    def laplacian(self, f, nlev=None, out=None):
+        lap = self._out(f, out)
+        dt, ld = self._check(f, lap)
+        capi.atlas_nabla_laplacian(self.handle, f.data_ptr(), lap.data_ptr(),
+                                   f.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return lap
+
+    def gradient_adjoint(self, gx, gy, nlev=None, out=None):
+        f = self._out(gx, out)
+        dt, ld = self._check(gx, gy, f)
+        capi.atlas_nabla_gradient_adjoint(self.handle, gx.data_ptr(), gy.data_ptr(), f.data_ptr(),
+                                          gx.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return f
+
+    def divergence_adjoint(self, d, nlev=None, out=None):
+        u, v = out if out is not None else (self._out(d, None), self._out(d, None))
+        dt, ld = self._check(d, u, v)
+        capi.atlas_nabla_divergence_adjoint(self.handle, d.data_ptr(), u.data_ptr(), v.data_ptr(),
+                                            d.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return u, v
+
+    # edge-based two-kernel forms
+    def workspace(self, op, ld, dtype_code):
+        torch = _torch()
+        n = capi.atlas_nabla_workspace_bytes(self.handle, OPS.get(op, op), 0, int(ld), int(dtype_code))
+        return torch.empty(max(int(n), 256), dtype=torch.uint8, device="cuda")
+
+    def gradient_edges(self, f, nlev=None, ws=None, out=None):
+        gx, gy = out if out is not None else (self._out(f, None), self._out(f, None))
+        dt, ld = self._check(f, gx, gy)
+        ws = self.workspace("gradient", ld, dt) if ws is None else ws
+        capi.atlas_nabla_gradient_edges(self.handle, f.data_ptr(), gx.data_ptr(), gy.data_ptr(), ws.data_ptr(),
+                                        ws.numel() * ws.element_size(), f.shape[1] if nlev is None else nlev,
+                                        ld, dt, _stream())
+        return gx, gy
+
+    def divergence_edges(self, u, v, nlev=None, ws=None, out=None):
+        d = self._out(u, out)
+        dt, ld = self._check(u, v, d)
+        ws = self.workspace("divergence", ld, dt) if ws is None else ws
+        capi.atlas_nabla_divergence_edges(self.handle, u.data_ptr(), v.data_ptr(), d.data_ptr(), ws.data_ptr(),
+                                          ws.numel() * ws.element_size(), u.shape[1] if nlev is None else nlev,
+                                          ld, dt, _stream())
+        return d
+
+    def laplacian_edges(self, f, nlev=None, ws=None, out=None):
+        lap = self._out(f, out)
+        dt, ld = self._check(f, lap)
+        ws = self.workspace("laplacian", ld, dt) if ws is None else ws
+        capi.atlas_nabla_laplacian_edges(self.handle, f.data_ptr(), lap.data_ptr(), ws.data_ptr(),
+                                         ws.numel() * ws.element_size(), f.shape[1] if nlev is None else nlev,
+                                         ld, dt, _stream())
+        return lap
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            capi.atlas_fvm_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_fvm(N: int, radius: float = R_EARTH) -> Fvm:
+    """Grid O<N> -> Mesh -> median-dual Fvm in one call."""
+    g = Grid(N)
+    m = Mesh(g)
+    return Fvm(m, radius)
+
+
+def field_sync(dst, src, nbytes, direction, stream=None):
+    """One cudaMemcpyAsync (0 = H2D, 1 = D2H, 2 = D2D) on torch's current stream."""
+    capi.atlas_field_sync(dst, src, int(nbytes), int(direction), _stream() if stream is None else stream)
+
+
+# ---------------------------------------------------------------- autograd
+def _make_autograd():
+    torch = _torch()
+
+    class GradientFn(torch.autograd.Function):
+        """(gx, gy) = G f; backward f_bar = G^T (gx_bar, gy_bar) by the adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, f, fvm):
+            ctx.fvm = fvm
+            f = f.contiguous()
+            out = (torch.zeros_like(f), torch.zeros_like(f))  # padding levels stay 0
+            return fvm.gradient(f, out=out)
+
+        @staticmethod
+        def backward(ctx, gx_bar, gy_bar):
+            fvm = ctx.fvm
+            gx_bar = torch.zeros_like(gy_bar) if gx_bar is None else gx_bar.contiguous()
+            gy_bar = torch.zeros_like(gx_bar) if gy_bar is None else gy_bar.contiguous()
+            return fvm.gradient_adjoint(gx_bar, gy_bar, out=torch.zeros_like(gx_bar)), None
+
+    class DivergenceFn(torch.autograd.Function):
+        """d = D (u, v); backward (u_bar, v_bar) = D^T d_bar by the adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, u, v, fvm):
+            ctx.fvm = fvm
+            u = u.contiguous()
+            return fvm.divergence(u, v.contiguous(), out=torch.zeros_like(u))
+
+        @staticmethod
+        def backward(ctx, d_bar):
+            d_bar = d_bar.contiguous()
+            out = (torch.zeros_like(d_bar), torch.zeros_like(d_bar))
+            u_bar, v_bar = ctx.fvm.divergence_adjoint(d_bar, out=out)
+            return u_bar, v_bar, None
+
+    return GradientFn, DivergenceFn
+
+
+_AUTOGRAD = None
+
+
+def gradient_fn(f, fvm: Fvm):
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD[0].apply(f, fvm)
+
+
+def divergence_fn(u, v, fvm: Fvm):
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD[1].apply(u, v, fvm)

@@ -1,0 +1,85 @@
+"""Build libatlasgb.so in-tree (nvcc for sm_103a + g++ for the host geometry).
+
+The three translation units compile in parallel into ``_build/`` and link
+into ``paper_1908_07038_gb300/libatlasgb.so``.  Host geometry is compiled
+with ``-ffp-contract=off`` so that its FP64 arithmetic is evaluated exactly
+as written on every host (x86-64 and aarch64 alike).
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+BUILD = os.path.join(PKG, "_build")
+LIB = os.path.join(PKG, "libatlasgb.so")
+INCLUDE = os.path.join(ROOT, "include")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _cuda_home() -> str:
+    for cand in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if cand and os.path.exists(os.path.join(cand, "bin", "nvcc")):
+            return cand
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        return os.path.dirname(os.path.dirname(nvcc))
+    raise RuntimeError("nvcc not found: set CUDA_HOME")
+
+
+def _sources():
+    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "capi.cpp", "kernels.cu")]
+
+
+def _headers():
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    return hs + [os.path.join(INCLUDE, "atlas_gb.h")]
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in _sources() + _headers() + [__file__])
+
+
+def _compile(src: str, cuda: str) -> str:
+    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    if src.endswith(".cu"):
+        cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", *ARCH, "-lineinfo",
+               "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    else:
+        cmd = ["g++", "-c", src, "-o", obj, "-O2", "-std=c++17", "-fPIC", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas",
+               "-I", INCLUDE, "-I", CSRC, "-I", os.path.join(cuda, "include")]
+    subprocess.check_call(cmd)
+    return obj
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if sources changed) and return the path of libatlasgb.so."""
+    if not force and not _stale():
+        return LIB
+    cuda = _cuda_home()
+    os.makedirs(BUILD, exist_ok=True)
+    with ThreadPoolExecutor(max_workers=3) as ex:
+        objs = list(ex.map(lambda s: _compile(s, cuda), _sources()))
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    cmd = [os.path.join(cuda, "bin", "nvcc"), "-shared", "-o", tmp, *objs, *ARCH,
+           "-Xcompiler", "-fopenmp", "-lgomp"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,910 @@
+// C ABI of libatlasgb.so (declared in include/atlas_gb.h): handles,
+// argument validation, table upload and kernel dispatch.  Every compute call
+// runs on the GPU; without a CUDA device the operator calls fail.
+#include "atlas_gb.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "geometry.h"
+#include "kernels.h"
+
+using atlasgb::StorageType;
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  if (std::getenv("ATLAS_DEBUG")) std::fprintf(stderr, "[atlas error] %s\n", buf);
+  return code;
+}
+int ok() {
+  g_err.clear();
+  return ATLAS_OK;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(ATLAS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+std::mutex g_registry_mu;
+std::set<const void*> g_live;  // live handles of every kind
+
+void reg(const void* h) {
+  std::lock_guard<std::mutex> lk(g_registry_mu);
+  g_live.insert(h);
+}
+bool live(const void* h) {
+  std::lock_guard<std::mutex> lk(g_registry_mu);
+  return h != nullptr && g_live.count(h) != 0;
+}
+void unreg(const void* h) {
+  std::lock_guard<std::mutex> lk(g_registry_mu);
+  g_live.erase(h);
+}
+}  // namespace
+
+// ----------------------------------------------------------------- handles
+struct atlas_grid_s {
+  atlasgb::Grid g;
+  int users = 0;
+};
+struct atlas_mesh_s {
+  atlas_grid_s* grid = nullptr;
+  atlasgb::Mesh m;
+  int users = 0;
+};
+
+namespace {
+struct DevAlloc {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* upload(const std::vector<T>& h, cudaError_t& err) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
+    err = cudaMalloc(&p, bytes);
+    if (err != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    if (!h.empty()) err = cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <typename A>
+std::vector<A> convert(const std::vector<double>& v) {
+  std::vector<A> out(v.size());
+  for (size_t k = 0; k < v.size(); ++k) out[k] = static_cast<A>(v[k]);
+  return out;
+}
+
+struct OpTables {
+  bool ready = false;
+  atlasgb::DevStencil dev;
+  DevAlloc mem;
+};
+struct EdgeTables {
+  bool ready = false;
+  atlasgb::DevEdges dev;
+  DevAlloc mem;
+};
+struct LaunchCfg {
+  int vec = 0;  // 0 = widest the dtype and alignment allow
+  int threads = 256;
+  int blocks_per_sm = 0;  // 0 = occupancy limit
+};
+}  // namespace
+
+struct atlas_fvm_s {
+  atlas_mesh_s* mesh = nullptr;
+  atlasgb::Dual d;
+  int device = -1;
+  int num_sms = 0;
+  std::mutex mu;
+  OpTables st[atlasgb::OP_COUNT][2];  // [op][weights: 0 float, 1 double]
+  EdgeTables eg[2][2];                // [gradient, divergence][precision]
+  LaunchCfg cfg[atlasgb::OP_COUNT];
+  int users = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+int elem_size(atlas_dtype t) { return t == ATLAS_F64 ? 8 : (t == ATLAS_BF16 ? 2 : 4); }
+int prec_of(atlas_dtype t) { return t == ATLAS_F64 ? 1 : 0; }
+StorageType storage_of(atlas_dtype t) {
+  return t == ATLAS_F64 ? atlasgb::ST_F64 : (t == ATLAS_BF16 ? atlasgb::ST_BF16 : atlasgb::ST_F32);
+}
+bool valid_dtype(int t) { return t == ATLAS_F32 || t == ATLAS_F64 || t == ATLAS_BF16; }
+
+int check_device(atlas_fvm_s* f) {
+  if (f->device < 0) return fail(ATLAS_ECUDA, "no CUDA device was available when this fvm was built");
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != f->device) return fail(ATLAS_ESTATE, "fvm lives on device %d, current device is %d", f->device, cur);
+  return ATLAS_OK;
+}
+
+// Build and upload the stencil tables of op in the given weight precision.
+int ensure_stencil(atlas_fvm_s* f, int op, int prec) {
+  OpTables& t = f->st[op][prec];
+  if (t.ready) return ATLAS_OK;
+  atlasgb::Stencil s;
+  try {
+    if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+  }
+  cudaError_t err = cudaSuccess;
+  const int64_t V = f->mesh->grid->g.nnodes;
+  t.dev.ptr = t.mem.upload(s.ptr, err);
+  if (err == cudaSuccess) t.dev.nbr = t.mem.upload(s.nbr, err);
+  std::vector<double> w = s.w;
+  if (s.scalar_w) {
+    std::vector<double> ws(s.nbr.size());
+    for (size_t q = 0; q < ws.size(); ++q) ws[q] = s.w[2 * q];
+    w.swap(ws);
+  }
+  if (err == cudaSuccess) t.dev.w = prec ? static_cast<const void*>(t.mem.upload(w, err))
+                                         : static_cast<const void*>(t.mem.upload(convert<float>(w), err));
+  if (err == cudaSuccess && s.has_b)
+    t.dev.b = prec ? static_cast<const void*>(t.mem.upload(s.b, err))
+                   : static_cast<const void*>(t.mem.upload(convert<float>(s.b), err));
+  if (err != cudaSuccess) {
+    t.mem.release();
+    return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for operator tables")
+                                            : cuda_fail(err, "upload of operator tables");
+  }
+  t.dev.nnodes = static_cast<int32_t>(V);
+  t.dev.nnz = static_cast<int64_t>(s.nbr.size());
+  t.dev.nin = s.nin;
+  t.dev.nout = s.nout;
+  t.dev.has_b = s.has_b;
+  t.dev.scalar_w = s.scalar_w;
+  t.ready = true;
+  return ATLAS_OK;
+}
+
+int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div*/, int prec) {
+  EdgeTables& t = f->eg[which][prec];
+  if (t.ready) return ATLAS_OK;
+  const atlasgb::Mesh& m = f->mesh->m;
+  atlasgb::EdgeGather g;
+  try {
+    if (!atlasgb::build_edge_gather(m, f->d, which == 0 ? atlasgb::OP_GRAD : atlasgb::OP_DIV, g))
+      return fail(ATLAS_EINVAL, "edge table build failed");
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building edge tables");
+  }
+  const int64_t E = m.nedges, V = f->mesh->grid->g.nnodes;
+  std::vector<double> coef(static_cast<size_t>(3 * E), 0.0), node(static_cast<size_t>(3 * V), 0.0);
+  for (int64_t e = 0; e < E; ++e) {
+    const double s0 = f->d.S[2 * e], s1 = f->d.S[2 * e + 1];
+    if (which == 0) {
+      coef[3 * e] = 0.5 * s0;
+      coef[3 * e + 1] = 0.5 * s1;
+    } else if (!m.is_pole[e]) {
+      coef[3 * e] = 0.5 * s0;
+      coef[3 * e + 1] = 0.5 * s1 * f->d.coslat[m.e2n[2 * e + 1]];
+      coef[3 * e + 2] = 0.5 * s1 * g.dcos[e];
+    }
+  }
+  for (int64_t i = 0; i < V; ++i) {
+    node[3 * i] = g.inv_v[i];
+    node[3 * i + 1] = which == 0 ? g.cos_v[i] : 0.0;
+    node[3 * i + 2] = which == 0 ? 0.0 : g.pole_coef[i];
+  }
+  cudaError_t err = cudaSuccess;
+  t.dev.e2n = t.mem.upload(m.e2n, err);
+  if (err == cudaSuccess) t.dev.ptr = t.mem.upload(g.ptr, err);
+  if (err == cudaSuccess) t.dev.ent = t.mem.upload(g.ent, err);
+  if (err == cudaSuccess)
+    t.dev.coef = prec ? static_cast<const void*>(t.mem.upload(coef, err))
+                      : static_cast<const void*>(t.mem.upload(convert<float>(coef), err));
+  if (err == cudaSuccess)
+    t.dev.node = prec ? static_cast<const void*>(t.mem.upload(node, err))
+                      : static_cast<const void*>(t.mem.upload(convert<float>(node), err));
+  if (err != cudaSuccess) {
+    t.mem.release();
+    return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for edge tables")
+                                            : cuda_fail(err, "upload of edge tables");
+  }
+  t.dev.nnodes = static_cast<int32_t>(V);
+  t.dev.nedges = E;
+  t.ready = true;
+  return ATLAS_OK;
+}
+
+// Widest levels-per-thread vector that the dtype, ld and every pointer allow
+// (capped by the requested width, 0 = no cap).
+int pick_vec(atlas_dtype dt, int64_t ld, const void* const* ptrs, int nptr, int want) {
+  const int es = elem_size(dt);
+  int v = 16 / es;
+  if (want > 0) v = std::min(v, want);
+  while (v > 1) {
+    bool okv = (ld % v) == 0;
+    for (int k = 0; k < nptr && okv; ++k)
+      if (ptrs[k] && (reinterpret_cast<uintptr_t>(ptrs[k]) % static_cast<uintptr_t>(v * es)) != 0) okv = false;
+    if (okv) break;
+    v >>= 1;
+  }
+  return v;
+}
+
+int check_field_args(atlas_dtype dtype, int nlev, int64_t ld, const void* const* ptrs, int nptr) {
+  if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unsupported dtype %d", static_cast<int>(dtype));
+  if (nlev < 0) return fail(ATLAS_EINVAL, "nlev must be >= 0 (got %d)", nlev);
+  if (ld < nlev || ld < 1) return fail(ATLAS_EINVAL, "leading dimension ld=%lld must be >= max(nlev, 1) (nlev=%d)",
+                                       static_cast<long long>(ld), nlev);
+  for (int k = 0; k < nptr; ++k) {
+    if (!ptrs[k]) return fail(ATLAS_EINVAL, "field pointer %d is NULL", k);
+    if (reinterpret_cast<uintptr_t>(ptrs[k]) % static_cast<uintptr_t>(elem_size(dtype)) != 0)
+      return fail(ATLAS_EALIGN, "field pointer %d is not aligned to its element size", k);
+  }
+  return ATLAS_OK;
+}
+
+int check_no_overlap(const void* const* ins, int nin, void* const* outs, int nout, int64_t bytes) {
+  auto overlaps = [bytes](const void* a, const void* b) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + static_cast<uintptr_t>(bytes) && y < x + static_cast<uintptr_t>(bytes);
+  };
+  for (int o = 0; o < nout; ++o) {
+    for (int i = 0; i < nin; ++i)
+      if (overlaps(outs[o], ins[i])) return fail(ATLAS_EINVAL, "output field %d overlaps input field %d", o, i);
+    for (int p = o + 1; p < nout; ++p)
+      if (overlaps(outs[o], outs[p])) return fail(ATLAS_EINVAL, "output fields %d and %d overlap", o, p);
+  }
+  return ATLAS_OK;
+}
+
+int grid_blocks(atlas_fvm_s* f, StorageType st, const atlasgb::DevStencil& s, int vec, int threads, int bps_req,
+                int64_t items) {
+  int bps = atlasgb::stencil_occupancy(st, s, vec, threads);
+  if (bps_req > 0) bps = std::min(bps, bps_req);
+  int64_t blocks = static_cast<int64_t>(f->num_sms) * bps;
+  const int64_t need = (items + threads - 1) / threads;
+  if (need < blocks) blocks = need;
+  return static_cast<int>(std::max<int64_t>(blocks, 1));
+}
+
+atlas_fvm_s* get_fvm(atlas_fvm_t h) { return live(h) ? reinterpret_cast<atlas_fvm_s*>(h) : nullptr; }
+
+// Fused node-stencil operator call.
+int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
+                   int64_t ld, atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  const void* ins[2] = {in0, in1};
+  void* outs[2] = {out0, out1};
+  const int nin = (op == atlasgb::OP_DIV || op == atlasgb::OP_GRAD_ADJ) ? 2 : 1;
+  const int nout = (op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ) ? 2 : 1;
+  const void* all[4] = {in0, in1, out0, out1};
+  const void* used[4];
+  int nu = 0;
+  for (int k = 0; k < nin; ++k) used[nu++] = ins[k];
+  for (int k = 0; k < nout; ++k) used[nu++] = outs[k];
+  (void)all;
+  int rc = check_field_args(dtype, nlev, ld, used, nu);
+  if (rc) return rc;
+  const int64_t V = f->mesh->grid->g.nnodes;
+  rc = check_no_overlap(ins, nin, outs, nout, V * ld * elem_size(dtype));
+  if (rc) return rc;
+  rc = check_device(f);
+  if (rc) return rc;
+  if (nlev == 0 || V == 0) return ok();
+  const int prec = prec_of(dtype);
+  {
+    std::lock_guard<std::mutex> lk(f->mu);
+    rc = ensure_stencil(f, op, prec);
+    if (rc) return rc;
+  }
+  const LaunchCfg& c = f->cfg[op];
+  atlasgb::StencilLaunch l;
+  l.in0 = in0;
+  l.in1 = nin == 2 ? in1 : nullptr;
+  l.out0 = out0;
+  l.out1 = nout == 2 ? out1 : nullptr;
+  l.nlev = nlev;
+  l.ld = ld;
+  l.vec = pick_vec(dtype, ld, used, nu, c.vec);
+  const int64_t nvec = (nlev + l.vec - 1) / l.vec;
+  const int64_t items = V * nvec;
+  if (items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
+  l.threads = c.threads;
+  const StorageType st = storage_of(dtype);
+  l.blocks = grid_blocks(f, st, f->st[op][prec].dev, l.vec, l.threads, c.blocks_per_sm, items);
+  cudaError_t e = atlasgb::launch_stencil(st, f->st[op][prec].dev, l, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
+  return ok();
+}
+
+size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+struct WsLayout {
+  size_t flux0 = 0, flux1 = 0, g0 = 0, g1 = 0, total = 0;
+};
+WsLayout ws_layout(atlas_fvm_s* f, int op, int64_t ld, atlas_dtype dt) {
+  WsLayout w;
+  const int64_t E = f->mesh->m.nedges, V = f->mesh->grid->g.nnodes;
+  const size_t ab = dt == ATLAS_F64 ? 8 : 4;
+  const size_t fbytes = align256(static_cast<size_t>(E) * ld * ab);
+  const size_t gbytes = align256(static_cast<size_t>(V) * ld * elem_size(dt));
+  size_t o = 0;
+  w.flux0 = o;
+  o += fbytes;
+  if (op == ATLAS_OP_GRADIENT || op == ATLAS_OP_LAPLACIAN) {
+    w.flux1 = o;
+    o += fbytes;
+  }
+  if (op == ATLAS_OP_LAPLACIAN) {
+    w.g0 = o;
+    o += gbytes;
+    w.g1 = o;
+    o += gbytes;
+  }
+  w.total = o;
+  return w;
+}
+
+int edge_blocks(atlas_fvm_s* f, int64_t items, int threads) {
+  int64_t blocks = static_cast<int64_t>(f->num_sms) * 8;
+  const int64_t need = (items + threads - 1) / threads;
+  return static_cast<int>(std::max<int64_t>(1, std::min(blocks, need)));
+}
+
+// Edge-based two-kernel gradient (which = 0) or divergence (which = 1).
+int run_edges_op(atlas_fvm_s* f, int which, const void* in0, const void* in1, void* out0, void* out1, char* ws,
+                 const WsLayout& w, int nlev, int64_t ld, atlas_dtype dtype, cudaStream_t stream) {
+  const int prec = prec_of(dtype);
+  {
+    std::lock_guard<std::mutex> lk(f->mu);
+    int rc = ensure_edges(f, which, prec);
+    if (rc) return rc;
+  }
+  const atlasgb::DevEdges& E = f->eg[which][prec].dev;
+  const void* ptrs[5] = {in0, in1, out0, out1, ws};
+  const int vec = pick_vec(dtype, ld, ptrs, 5, f->cfg[which].vec);
+  const int64_t nvec = (nlev + vec - 1) / vec;
+  if (E.nedges * nvec >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nedges * level-vectors must stay below 2^31");
+  const int threads = 256;
+  const StorageType st = storage_of(dtype);
+  cudaError_t e = atlasgb::launch_edge_flux(st, which, E, in0, in1, ws + w.flux0, which == 0 ? ws + w.flux1 : nullptr,
+                                            nlev, ld, vec, threads, edge_blocks(f, E.nedges * nvec, threads), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "edge-flux kernel launch");
+  e = atlasgb::launch_node_gather(st, which, E, ws + w.flux0, which == 0 ? ws + w.flux1 : nullptr,
+                                  which == 1 ? in1 : nullptr, out0, which == 0 ? out1 : nullptr, nlev, ld, vec, threads,
+                                  edge_blocks(f, static_cast<int64_t>(E.nnodes) * nvec, threads), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "node-gather kernel launch");
+  return ATLAS_OK;
+}
+
+int check_ws(atlas_fvm_s* f, int op, void* ws, size_t ws_bytes, int64_t ld, atlas_dtype dt, WsLayout& w) {
+  w = ws_layout(f, op, ld, dt);
+  if (!ws) return fail(ATLAS_EINVAL, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(ATLAS_EALIGN, "workspace must be 256-byte aligned");
+  if (ws_bytes < w.total)
+    return fail(ATLAS_EINVAL, "workspace too small: %zu bytes given, %zu needed", ws_bytes, w.total);
+  return ATLAS_OK;
+}
+
+const char* kVersion = "atlasgb 0.1.0 (sm_103a)";
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int atlas_init(void) { return ok(); }
+int atlas_finalize(void) { return ok(); }
+const char* atlas_version(void) { return kVersion; }
+
+const char* atlas_info(void) {
+  static thread_local std::string s;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  char buf[512];
+  if (e != cudaSuccess || n == 0) {
+    std::snprintf(buf, sizeof buf, "%s; no CUDA device (%s)", kVersion, cudaGetErrorString(e));
+  } else {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, dev);
+    std::snprintf(buf, sizeof buf, "%s; device %d: %s, sm_%d%d, %d SMs, %.1f GiB", kVersion, dev, p.name, p.major,
+                  p.minor, p.multiProcessorCount, static_cast<double>(p.totalGlobalMem) / (1 << 30));
+  }
+  s = buf;
+  return s.c_str();
+}
+
+const char* atlas_last_error(void) { return g_err.c_str(); }
+
+int atlas_grid_octahedral(int N, atlas_grid_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (N < 1 || N > 8000) return fail(ATLAS_EINVAL, "octahedral number N=%d out of range [1, 8000]", N);
+  atlas_grid_s* g = new (std::nothrow) atlas_grid_s();
+  if (!g) return fail(ATLAS_ENOMEM, "out of host memory");
+  try {
+    if (!atlasgb::build_grid(N, g->g)) {
+      delete g;
+      return fail(ATLAS_EINVAL, "grid build failed");
+    }
+  } catch (const std::bad_alloc&) {
+    delete g;
+    return fail(ATLAS_ENOMEM, "out of host memory building O%d", N);
+  }
+  reg(g);
+  *out = reinterpret_cast<atlas_grid_t>(g);
+  return ok();
+}
+
+int atlas_grid_info(atlas_grid_t h, int64_t* nnodes, int* nlat, const int32_t** pl, const double** lonlat,
+                    const double** lat) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
+  const atlasgb::Grid& g = reinterpret_cast<atlas_grid_s*>(h)->g;
+  if (nnodes) *nnodes = g.nnodes;
+  if (nlat) *nlat = g.nlat;
+  if (pl) *pl = g.pl.data();
+  if (lonlat) *lonlat = g.lonlat.data();
+  if (lat) *lat = g.lat.data();
+  return ok();
+}
+
+void atlas_grid_destroy(atlas_grid_t h) {
+  if (!live(h)) return;
+  atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(h);
+  if (g->users > 0) {
+    fail(ATLAS_ESTATE, "grid still used by %d mesh(es); not destroyed", g->users);
+    return;
+  }
+  unreg(g);
+  delete g;
+}
+
+int atlas_mesh_build(atlas_grid_t gh, atlas_mesh_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!live(gh)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
+  atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(gh);
+  atlas_mesh_s* m = new (std::nothrow) atlas_mesh_s();
+  if (!m) return fail(ATLAS_ENOMEM, "out of host memory");
+  try {
+    if (!atlasgb::build_mesh(g->g, m->m)) {
+      delete m;
+      return fail(ATLAS_EINVAL, "mesh build failed (inconsistent zipper)");
+    }
+  } catch (const std::bad_alloc&) {
+    delete m;
+    return fail(ATLAS_ENOMEM, "out of host memory building the mesh");
+  }
+  m->grid = g;
+  g->users++;
+  reg(m);
+  *out = reinterpret_cast<atlas_mesh_t>(m);
+  return ok();
+}
+
+int atlas_mesh_info(atlas_mesh_t h, int64_t* nedges, int64_t* ntri, const int32_t** e2n, const uint8_t** is_pole,
+                    const int32_t** n2e_ptr, const int32_t** n2e, const int8_t** n2e_sign, const int32_t** tri) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed mesh handle");
+  const atlasgb::Mesh& m = reinterpret_cast<atlas_mesh_s*>(h)->m;
+  if (nedges) *nedges = m.nedges;
+  if (ntri) *ntri = m.ntri;
+  if (e2n) *e2n = m.e2n.data();
+  if (is_pole) *is_pole = m.is_pole.data();
+  if (n2e_ptr) *n2e_ptr = m.n2e_ptr.data();
+  if (n2e) *n2e = m.n2e.data();
+  if (n2e_sign) *n2e_sign = m.n2e_sign.data();
+  if (tri) *tri = m.tri.data();
+  return ok();
+}
+
+void atlas_mesh_destroy(atlas_mesh_t h) {
+  if (!live(h)) return;
+  atlas_mesh_s* m = reinterpret_cast<atlas_mesh_s*>(h);
+  if (m->users > 0) {
+    fail(ATLAS_ESTATE, "mesh still used by %d fvm(s); not destroyed", m->users);
+    return;
+  }
+  unreg(m);
+  m->grid->users--;
+  delete m;
+}
+
+int atlas_fvm_build_dual(atlas_mesh_t mh, double radius, atlas_fvm_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!live(mh)) return fail(ATLAS_ESTATE, "invalid or destroyed mesh handle");
+  if (!(radius > 0) || radius > 1e12) return fail(ATLAS_EINVAL, "radius must be positive and finite");
+  atlas_mesh_s* m = reinterpret_cast<atlas_mesh_s*>(mh);
+  atlas_fvm_s* f = new (std::nothrow) atlas_fvm_s();
+  if (!f) return fail(ATLAS_ENOMEM, "out of host memory");
+  try {
+    if (!atlasgb::build_dual(m->m, radius, f->d)) {
+      delete f;
+      return fail(ATLAS_EINVAL, "dual build failed");
+    }
+  } catch (const std::bad_alloc&) {
+    delete f;
+    return fail(ATLAS_ENOMEM, "out of host memory building the dual");
+  }
+  f->mesh = m;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) == cudaSuccess && n > 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    f->device = dev;
+    cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  } else {
+    cudaGetLastError();  // clear the sticky "no device" status of the runtime
+    f->device = -1;
+  }
+  m->users++;
+  reg(f);
+  *out = reinterpret_cast<atlas_fvm_t>(f);
+  return ok();
+}
+
+int atlas_fvm_info(atlas_fvm_t h, const double** V, const double** S, const double** coslat, const double** pole_nphi) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (V) *V = f->d.V.data();
+  if (S) *S = f->d.S.data();
+  if (coslat) *coslat = f->d.coslat.data();
+  if (pole_nphi) *pole_nphi = f->d.pole_nphi.data();
+  return ok();
+}
+
+int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  int rc = check_device(f);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(f->mu);
+  for (int op = 0; op < atlasgb::OP_COUNT; ++op) {
+    if (!(op_mask & (1u << op))) continue;
+    for (int dt = 0; dt < 3; ++dt) {
+      if (!(dtype_mask & (1u << dt))) continue;
+      rc = ensure_stencil(f, op, prec_of(static_cast<atlas_dtype>(dt)));
+      if (rc) return rc;
+      if (op <= atlasgb::OP_DIV && dt != ATLAS_BF16) {
+        rc = ensure_edges(f, op, prec_of(static_cast<atlas_dtype>(dt)));
+        if (rc) return rc;
+      }
+    }
+  }
+  return ok();
+}
+
+int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int threads, int blocks_per_sm) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (vec != 0 && vec != 1 && vec != 2 && vec != 4 && vec != 8) return fail(ATLAS_EINVAL, "vec must be 1, 2, 4 or 8");
+  if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32 != 0))
+    return fail(ATLAS_EINVAL, "threads must be a multiple of 32 in [64, 1024]");
+  if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(ATLAS_EINVAL, "blocks_per_sm must be in [0, 32]");
+  std::lock_guard<std::mutex> lk(f->mu);
+  if (vec) f->cfg[op].vec = vec;
+  if (threads) f->cfg[op].threads = threads;
+  if (blocks_per_sm) f->cfg[op].blocks_per_sm = blocks_per_sm;
+  return ok();
+}
+
+int atlas_fvm_stencil_table(atlas_fvm_t h, int op, int64_t* nnz, int* nin, int* nout, int32_t* ptr, int32_t* nbr,
+                            double* w, double* b) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  atlasgb::Stencil s;
+  try {
+    if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+  }
+  const size_t V = s.ptr.size() - 1, n = s.nbr.size();
+  if (nnz) *nnz = static_cast<int64_t>(n);
+  if (nin) *nin = s.nin;
+  if (nout) *nout = s.nout;
+  if (ptr) std::memcpy(ptr, s.ptr.data(), sizeof(int32_t) * (V + 1));
+  if (nbr && n) std::memcpy(nbr, s.nbr.data(), sizeof(int32_t) * n);
+  if (w && n) std::memcpy(w, s.w.data(), sizeof(double) * 2 * n);
+  if (b) {
+    if (s.has_b) std::memcpy(b, s.b.data(), sizeof(double) * 2 * V);
+    else std::memset(b, 0, sizeof(double) * 2 * V);
+  }
+  return ok();
+}
+
+void atlas_fvm_destroy(atlas_fvm_t h) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return;
+  if (f->users > 0) {
+    fail(ATLAS_ESTATE, "fvm still used by %d batch(es); not destroyed", f->users);
+    return;
+  }
+  unreg(f);
+  for (auto& row : f->st)
+    for (auto& t : row) t.mem.release();
+  for (auto& row : f->eg)
+    for (auto& t : row) t.mem.release();
+  f->mesh->users--;
+  delete f;
+}
+
+int atlas_nabla_gradient(atlas_fvm_t fvm, const void* f, void* gx, void* gy, int nlev, int64_t ld, atlas_dtype dtype,
+                         void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_GRAD, f, nullptr, gx, gy, nlev, ld, dtype, stream);
+}
+int atlas_nabla_divergence(atlas_fvm_t fvm, const void* u, const void* v, void* div, int nlev, int64_t ld,
+                           atlas_dtype dtype, void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_DIV, u, v, div, nullptr, nlev, ld, dtype, stream);
+}
+int atlas_nabla_laplacian(atlas_fvm_t fvm, const void* f, void* lap, int nlev, int64_t ld, atlas_dtype dtype,
+                          void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_LAP, f, nullptr, lap, nullptr, nlev, ld, dtype, stream);
+}
+int atlas_nabla_gradient_adjoint(atlas_fvm_t fvm, const void* gx, const void* gy, void* f, int nlev, int64_t ld,
+                                 atlas_dtype dtype, void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_GRAD_ADJ, gx, gy, f, nullptr, nlev, ld, dtype, stream);
+}
+int atlas_nabla_divergence_adjoint(atlas_fvm_t fvm, const void* div, void* u, void* v, int nlev, int64_t ld,
+                                   atlas_dtype dtype, void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_DIV_ADJ, div, nullptr, u, v, nlev, ld, dtype, stream);
+}
+
+size_t atlas_nabla_workspace_bytes(atlas_fvm_t h, int op, int nlev, int64_t ld, atlas_dtype dtype) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f || nlev < 0 || ld < nlev || ld < 1 || !valid_dtype(dtype)) return 0;
+  if (op != ATLAS_OP_GRADIENT && op != ATLAS_OP_DIVERGENCE && op != ATLAS_OP_LAPLACIAN) return 0;
+  return ws_layout(f, op, ld, dtype).total;
+}
+
+int atlas_nabla_gradient_edges(atlas_fvm_t h, const void* fin, void* gx, void* gy, void* ws, size_t ws_bytes, int nlev,
+                               int64_t ld, atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
+  const void* used[3] = {fin, gx, gy};
+  int rc = check_field_args(dtype, nlev, ld, used, 3);
+  if (rc) return rc;
+  const void* ins[1] = {fin};
+  void* outs[2] = {gx, gy};
+  rc = check_no_overlap(ins, 1, outs, 2, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
+  if (rc) return rc;
+  WsLayout w;
+  rc = check_ws(f, ATLAS_OP_GRADIENT, ws, ws_bytes, ld, dtype, w);
+  if (rc) return rc;
+  rc = check_device(f);
+  if (rc) return rc;
+  if (nlev == 0) return ok();
+  rc = run_edges_op(f, 0, fin, nullptr, gx, gy, static_cast<char*>(ws), w, nlev, ld, dtype,
+                    static_cast<cudaStream_t>(stream));
+  return rc ? rc : ok();
+}
+
+int atlas_nabla_divergence_edges(atlas_fvm_t h, const void* u, const void* v, void* div, void* ws, size_t ws_bytes,
+                                 int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
+  const void* used[3] = {u, v, div};
+  int rc = check_field_args(dtype, nlev, ld, used, 3);
+  if (rc) return rc;
+  const void* ins[2] = {u, v};
+  void* outs[1] = {div};
+  rc = check_no_overlap(ins, 2, outs, 1, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
+  if (rc) return rc;
+  WsLayout w;
+  rc = check_ws(f, ATLAS_OP_DIVERGENCE, ws, ws_bytes, ld, dtype, w);
+  if (rc) return rc;
+  rc = check_device(f);
+  if (rc) return rc;
+  if (nlev == 0) return ok();
+  rc = run_edges_op(f, 1, u, v, div, nullptr, static_cast<char*>(ws), w, nlev, ld, dtype,
+                    static_cast<cudaStream_t>(stream));
+  return rc ? rc : ok();
+}
+
+int atlas_nabla_laplacian_edges(atlas_fvm_t h, const void* fin, void* lap, void* ws, size_t ws_bytes, int nlev,
+                                int64_t ld, atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
+  const void* used[2] = {fin, lap};
+  int rc = check_field_args(dtype, nlev, ld, used, 2);
+  if (rc) return rc;
+  const void* ins[1] = {fin};
+  void* outs[1] = {lap};
+  rc = check_no_overlap(ins, 1, outs, 1, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
+  if (rc) return rc;
+  WsLayout w;
+  rc = check_ws(f, ATLAS_OP_LAPLACIAN, ws, ws_bytes, ld, dtype, w);
+  if (rc) return rc;
+  rc = check_device(f);
+  if (rc) return rc;
+  if (nlev == 0) return ok();
+  char* base = static_cast<char*>(ws);
+  void* g0 = base + w.g0;
+  void* g1 = base + w.g1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = run_edges_op(f, 0, fin, nullptr, g0, g1, base, w, nlev, ld, dtype, s);
+  if (rc) return rc;
+  rc = run_edges_op(f, 1, g0, g1, lap, nullptr, base, w, nlev, ld, dtype, s);
+  return rc ? rc : ok();
+}
+
+int atlas_field_sync(void* dst, const void* src, size_t bytes, int direction, void* stream) {
+  if (bytes == 0) return ok();
+  if (!dst || !src) return fail(ATLAS_EINVAL, "NULL pointer");
+  cudaMemcpyKind kind;
+  switch (direction) {
+    case 0: kind = cudaMemcpyHostToDevice; break;
+    case 1: kind = cudaMemcpyDeviceToHost; break;
+    case 2: kind = cudaMemcpyDeviceToDevice; break;
+    default: return fail(ATLAS_EINVAL, "direction must be 0 (H2D), 1 (D2H) or 2 (D2D)");
+  }
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  return ok();
+}
+
+}  // extern "C"
+
+// ================================================================= batches
+struct atlas_batch_s {
+  std::vector<atlas_fvm_s*> fvms;
+  atlasgb::BatchDescDev* d_desc = nullptr;
+  int ndesc = 0;
+  int64_t ntiles = 0, node_levels = 0;
+  int tile_items = 0, threads = 0, blocks = 0, device = -1;
+  StorageType st = atlasgb::ST_F32;
+};
+
+extern "C" {
+
+int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, const atlas_batch_tune* tune,
+                       atlas_batch_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!descs || n < 1 || n > 4096) return fail(ATLAS_EINVAL, "need 1..4096 descriptors");
+  if (dtype != ATLAS_F32 && dtype != ATLAS_F64) return fail(ATLAS_EDTYPE, "batches take F32 or F64 fields");
+  atlas_batch_tune t{0, 0, 0, 0};
+  if (tune) t = *tune;
+  const int want_vec = t.vec > 0 ? t.vec : 16 / elem_size(dtype);
+  if (want_vec != 1 && want_vec != 2 && want_vec != 4) return fail(ATLAS_EINVAL, "batch vec must be 1, 2 or 4");
+  const int tile_items = t.tile_items > 0 ? t.tile_items : 4096;
+  const int threads = t.threads > 0 ? t.threads : 256;
+  if (threads < 64 || threads > 1024 || threads % 32) return fail(ATLAS_EINVAL, "bad thread count %d", threads);
+  const int prec = prec_of(dtype);
+  std::vector<atlasgb::BatchDescDev> hd(static_cast<size_t>(n));
+  int64_t tiles = 0, nl = 0;
+  int device = -1;
+  std::vector<atlas_fvm_s*> fv;
+  for (int k = 0; k < n; ++k) {
+    const atlas_batch_desc& d = descs[k];
+    atlas_fvm_s* f = get_fvm(d.fvm);
+    if (!f) return fail(ATLAS_ESTATE, "descriptor %d: invalid fvm handle", k);
+    int rc = check_device(f);
+    if (rc) return rc;
+    if (device < 0) device = f->device;
+    if (f->device != device) return fail(ATLAS_EINVAL, "descriptor %d: all fields must live on one device", k);
+    const bool grad = d.op == ATLAS_OP_GRADIENT;
+    if (!grad && d.op != ATLAS_OP_DIVERGENCE) return fail(ATLAS_EINVAL, "descriptor %d: op must be gradient or divergence", k);
+    const void* used[3] = {d.in0, grad ? d.out0 : d.in1, grad ? d.out1 : d.out0};
+    rc = check_field_args(dtype, d.nlev, d.ld, used, 3);
+    if (rc) return fail(rc, "descriptor %d: %s", k, g_err.c_str());
+    {
+      std::lock_guard<std::mutex> lk(f->mu);
+      rc = ensure_stencil(f, grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV, prec);
+      if (rc) return rc;
+    }
+    const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][prec].dev;
+    const int vec = pick_vec(dtype, d.ld, used, 3, want_vec);
+    atlasgb::BatchDescDev& o = hd[k];
+    o.ptr = s.ptr;
+    o.nbr = s.nbr;
+    o.w = s.w;
+    o.b = s.b;
+    o.in0 = d.in0;
+    o.in1 = grad ? nullptr : d.in1;
+    o.out0 = d.out0;
+    o.out1 = grad ? d.out1 : nullptr;
+    o.ld = d.ld;
+    o.nnodes = s.nnodes;
+    o.nlev = d.nlev;
+    o.vec = vec;
+    o.nvec = (d.nlev + vec - 1) / vec;
+    o.items = static_cast<int64_t>(s.nnodes) * o.nvec;
+    if (o.items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "descriptor %d too large", k);
+    o.op = grad ? 0 : 1;
+    o.pad = 0;
+    o.tile0 = tiles;
+    tiles += (o.items + tile_items - 1) / tile_items;
+    nl += static_cast<int64_t>(s.nnodes) * d.nlev;
+    fv.push_back(f);
+  }
+  atlas_batch_s* b = new (std::nothrow) atlas_batch_s();
+  if (!b) return fail(ATLAS_ENOMEM, "out of host memory");
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_desc), sizeof(atlasgb::BatchDescDev) * n);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "cudaMalloc (batch descriptors)");
+  }
+  e = cudaMemcpy(b->d_desc, hd.data(), sizeof(atlasgb::BatchDescDev) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(b->d_desc);
+    delete b;
+    return cuda_fail(e, "cudaMemcpy (batch descriptors)");
+  }
+  b->fvms = fv;
+  for (atlas_fvm_s* f : fv) f->users++;
+  b->ndesc = n;
+  b->ntiles = tiles;
+  b->node_levels = nl;
+  b->tile_items = tile_items;
+  b->threads = threads;
+  b->st = storage_of(dtype);
+  b->device = device;
+  int bps = atlasgb::batch_occupancy(b->st, threads);
+  if (t.blocks_per_sm > 0) bps = std::min(bps, t.blocks_per_sm);
+  const int64_t blocks = std::min<int64_t>(static_cast<int64_t>(fv[0]->num_sms) * bps, std::max<int64_t>(tiles, 1));
+  b->blocks = static_cast<int>(blocks);
+  reg(b);
+  *out = reinterpret_cast<atlas_batch_t>(b);
+  return ok();
+}
+
+int atlas_batch_launch(atlas_batch_t h, void* stream) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed batch handle");
+  atlas_batch_s* b = reinterpret_cast<atlas_batch_s*>(h);
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device)
+    return fail(ATLAS_ESTATE, "batch lives on device %d, current device is %d", b->device, cur);
+  if (b->ntiles == 0) return ok();
+  cudaError_t e = atlasgb::launch_batch(b->st, b->d_desc, b->ndesc, b->ntiles, b->tile_items, b->threads, b->blocks,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+  return ok();
+}
+
+int atlas_batch_info(atlas_batch_t h, int64_t* tiles, int64_t* node_levels) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed batch handle");
+  atlas_batch_s* b = reinterpret_cast<atlas_batch_s*>(h);
+  if (tiles) *tiles = b->ntiles;
+  if (node_levels) *node_levels = b->node_levels;
+  return ok();
+}
+
+void atlas_batch_destroy(atlas_batch_t h) {
+  if (!live(h)) return;
+  atlas_batch_s* b = reinterpret_cast<atlas_batch_s*>(h);
+  unreg(b);
+  for (atlas_fvm_s* f : b->fvms) f->users--;
+  cudaFree(b->d_desc);
+  delete b;
+}
+
+}  // extern "C"

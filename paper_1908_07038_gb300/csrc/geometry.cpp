@@ -1,0 +1,665 @@
+// Host geometry of the octahedral reduced Gaussian grid (see geometry.h).
+//
+// Construction route: the mesh is generated edge by edge.  The zipper walk of
+// every band yields the band's cross edges in longitude order; triangle k of
+// the band lies between cross edges k and k+1, so the two dual-face end
+// points of every edge (the centroids of its two triangles, or the pole) are
+// known from the walk position without any geometric test.  Volumes are then
+// gathered per node over its CSR row.
+//
+// Per-quantity definitions (FP64, evaluated exactly as written, no FMA
+// contraction; the build passes -ffp-contract=off):
+//   latitude        : Newton in colatitude on the cosine series of P_2N
+//   centroid lat    : ((lat_p + lat_p) + lat_q) / 3, p = row with two vertices
+//   midpoint lat    : lat_r on a ring edge, 0.5 * (lat_r + lat_s) across rows
+//   end-point offset: longitude of the end point minus the edge midpoint, in
+//                     turns, rounded once from the exact rational
+//   S_e             : (R * (lat_L - lat_R), -(2 pi R * (off_L - off_R)))
+//   segment p -> q  : -((2 pi dturns) * sin(0.5 (lat_p + lat_q))) * sinc(0.5 (lat_q - lat_p))
+//   V_i             : R^2 * compensated sum of the signed segment integrals
+#include "geometry.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace atlasgb {
+namespace {
+
+const double kPi = 3.14159265358979323846;
+const double kTwoPi = 2.0 * kPi;
+const double kHalfPi = 0.5 * kPi;
+
+// error-free transformations (Ogita, Rump, Oishi 2005)
+inline void tsum(double a, double b, double& s, double& e) {
+  s = a + b;
+  double z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+inline void tprod(double a, double b, double& p, double& e) {
+  p = a * b;
+  e = std::fma(a, b, -p);
+}
+struct Comp {
+  double s = 0, c = 0;
+  void add(double x) {
+    double t, e;
+    tsum(s, x, t, e);
+    s = t;
+    c += e;
+  }
+  void add_prod(double x, double y) {
+    double p, e;
+    tprod(x, y, p, e);
+    add(p);
+    c += e;
+  }
+  double value() const { return s + c; }
+};
+
+inline int64_t gcd_i64(int64_t a, int64_t b) {
+  a = a < 0 ? -a : a;
+  b = b < 0 ? -b : b;
+  while (b != 0) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+// correctly rounded double of p/q (exact integers below 2^53 after reduction)
+inline double ratio(int64_t p, int64_t q) {
+  int64_t g = gcd_i64(p, q);
+  if (g > 1) {
+    p /= g;
+    q /= g;
+  }
+  return static_cast<double>(p) / static_cast<double>(q);
+}
+inline double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
+
+int row_points(int N, int r) { return 4 * ((r < N) ? r + 1 : 2 * N - r) + 16; }
+
+// P_n(cos t) and dP/dt from the cosine series; the argument m*t is split
+// into its rounded product and exact remainder.
+void legendre_cos_series(int n, const std::vector<double>& coef, double t, double& P, double& dP) {
+  Comp pv, dv;
+  for (int k = 0; 2 * k < n; ++k) {
+    const double m = static_cast<double>(n - 2 * k);
+    double a, e;
+    tprod(m, t, a, e);
+    const double ca = std::cos(a), sa = std::sin(a);
+    const double cm = ca - e * sa;
+    const double sm = sa + e * ca;
+    pv.add_prod(2.0 * coef[k], cm);
+    dv.add_prod(-2.0 * coef[k] * m, sm);
+  }
+  if (n % 2 == 0) pv.add(coef[n / 2]);
+  P = pv.value();
+  dP = dv.value();
+}
+
+}  // namespace
+
+// Roots of P_n as colatitudes (ascending from the north pole).  The cosine
+// series of the Legendre polynomial, P_n(cos t) = sum_k g_k g_{n-k}
+// cos((n-2k) t) with g_k = binom(2k, k) / 4^k, is evaluated directly in the
+// colatitude so that the polar roots keep their relative accuracy.
+void gauss_colatitudes(int n, double* theta) {
+  std::vector<double> g(static_cast<size_t>(n) + 1), coef(static_cast<size_t>(n) / 2 + 1);
+  g[0] = 1.0;
+  for (int k = 1; k <= n; ++k) g[k] = g[k - 1] * static_cast<double>(2 * k - 1) / static_cast<double>(2 * k);
+  for (int k = 0; 2 * k <= n; ++k) coef[k] = g[k] * g[n - k];
+  const int half = (n + 1) / 2;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int k = 0; k < half; ++k) {
+    double t = kPi * (static_cast<double>(k) + 0.75) / (static_cast<double>(n) + 0.5);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_cos_series(n, coef, t, P, dP);
+      const double step = P / dP;
+      t -= step;
+      if (std::fabs(step) <= 1e-15 * (t > 1.0 ? t : 1.0)) {
+        legendre_cos_series(n, coef, t, P, dP);  // one polishing step
+        t -= P / dP;
+        break;
+      }
+    }
+    theta[k] = t;
+  }
+  for (int k = 0; k < n / 2; ++k) theta[n - 1 - k] = kPi - theta[k];
+  if (n % 2 == 1) theta[n / 2] = kHalfPi;
+}
+
+bool build_grid(int N, Grid& g) {
+  if (N < 1 || N > 8000) return false;
+  g.N = N;
+  g.nlat = 2 * N;
+  g.pl.resize(g.nlat);
+  g.off.resize(g.nlat + 1);
+  g.colat.resize(g.nlat);
+  g.lat.resize(g.nlat);
+  gauss_colatitudes(g.nlat, g.colat.data());
+  for (int r = 0; r < g.nlat; ++r) g.lat[r] = kHalfPi - g.colat[r];
+  for (int r = 0; r < N; ++r) g.lat[g.nlat - 1 - r] = -g.lat[r];
+  g.off[0] = 0;
+  for (int r = 0; r < g.nlat; ++r) {
+    g.pl[r] = row_points(N, r);
+    g.off[r + 1] = g.off[r] + g.pl[r];
+  }
+  g.nnodes = g.off[g.nlat];
+  g.lonlat.resize(static_cast<size_t>(2 * g.nnodes));
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int r = 0; r < g.nlat; ++r)
+    for (int j = 0; j < g.pl[r]; ++j) {
+      const int64_t i = g.off[r] + j;
+      g.lonlat[2 * i] = kTwoPi * ratio(j, g.pl[r]);
+      g.lonlat[2 * i + 1] = g.lat[r];
+    }
+  return true;
+}
+
+namespace {
+
+// One step of the zipper walk of band (r, r+1): true if the northern row
+// advances.  Compare the next longitudes (ia+1)/n1 and (ib+1)/n2; on a tie
+// the row with fewer points advances, and between equal rows the northern.
+inline bool north_advances(int64_t ia, int64_t ib, int64_t n1, int64_t n2) {
+  if (ia == n1) return false;
+  if (ib == n2) return true;
+  const int64_t ln = (ia + 1) * n2, ls = (ib + 1) * n1;
+  if (ln != ls) return ln < ls;
+  return n1 <= n2;
+}
+
+struct ForwardEdges {
+  std::vector<int32_t> first;  // [V+1] first edge id with this node as 'a'
+  std::vector<int32_t> b;      // [E] second endpoint, sorted within each node
+  int64_t find(int32_t a, int32_t bb) const {
+    for (int32_t e = first[a]; e < first[a + 1]; ++e)
+      if (b[e] == bb) return e;
+    return -1;
+  }
+};
+
+}  // namespace
+
+bool build_mesh(const Grid& g, Mesh& m) {
+  m.grid = &g;
+  const int nlat = g.nlat;
+  const int64_t V = g.nnodes;
+  // ---- forward-edge counts: ring (next, wrap), pole, cross edges ----
+  std::vector<int32_t> cnt(static_cast<size_t>(V) + 1, 0);
+  for (int r = 0; r < nlat; ++r) {
+    const int n = g.pl[r];
+    const int64_t o = g.off[r];
+    for (int j = 0; j < n; ++j) {
+      int c = 0;
+      if (j < n - 1) ++c;                                    // (j, j+1)
+      if (j == 0) ++c;                                       // wrap (0, n-1)
+      if ((r == 0 || r == nlat - 1) && j < n / 2) ++c;       // pole edge (j, j+n/2)
+      cnt[o + j] += c;
+    }
+  }
+  for (int r = 0; r + 1 < nlat; ++r) {  // cross edges of band r, one per walk position
+    const int64_t n1 = g.pl[r], n2 = g.pl[r + 1];
+    int64_t ia = 0, ib = 0;
+    for (int64_t k = 0; k < n1 + n2; ++k) {
+      cnt[g.off[r] + (ia % n1)] += 1;  // cross edge k = (N(ia), S(ib)), before the step
+      if (north_advances(ia, ib, n1, n2)) ++ia; else ++ib;
+    }
+  }
+  ForwardEdges fe;
+  fe.first.assign(static_cast<size_t>(V) + 1, 0);
+  for (int64_t i = 0; i < V; ++i) fe.first[i + 1] = fe.first[i] + cnt[i];
+  const int64_t E = fe.first[V];
+  if (E != 3 * V - 20) return false;
+  m.nedges = E;
+  fe.b.assign(static_cast<size_t>(E), -1);
+  std::vector<int32_t> fill(fe.first.begin(), fe.first.end() - 1);
+  for (int r = 0; r < nlat; ++r) {
+    const int n = g.pl[r];
+    const int32_t o = static_cast<int32_t>(g.off[r]);
+    for (int j = 0; j < n; ++j) {
+      const int32_t a = o + j;
+      if (j < n - 1) fe.b[fill[a]++] = a + 1;
+      if (j == 0) fe.b[fill[a]++] = o + n - 1;
+      if ((r == 0 || r == nlat - 1) && j < n / 2) fe.b[fill[a]++] = a + n / 2;
+    }
+  }
+  for (int r = 0; r + 1 < nlat; ++r) {
+    const int64_t n1 = g.pl[r], n2 = g.pl[r + 1];
+    int64_t ia = 0, ib = 0;
+    for (int64_t k = 0; k < n1 + n2; ++k) {
+      const int32_t a = static_cast<int32_t>(g.off[r] + (ia % n1));
+      fe.b[fill[a]++] = static_cast<int32_t>(g.off[r + 1] + (ib % n2));
+      if (north_advances(ia, ib, n1, n2)) ++ia; else ++ib;
+    }
+  }
+  for (int64_t i = 0; i < V; ++i) {
+    std::sort(fe.b.begin() + fe.first[i], fe.b.begin() + fe.first[i + 1]);
+    for (int32_t e = fe.first[i] + 1; e < fe.first[i + 1]; ++e)
+      if (fe.b[e] == fe.b[e - 1]) return false;  // a pole edge may not repeat a side
+  }
+  m.e2n.resize(static_cast<size_t>(2 * E));
+  m.is_pole.assign(static_cast<size_t>(E), 0);
+  for (int64_t a = 0; a < V; ++a)
+    for (int32_t e = fe.first[a]; e < fe.first[a + 1]; ++e) {
+      m.e2n[2 * e] = static_cast<int32_t>(a);
+      m.e2n[2 * e + 1] = fe.b[e];
+    }
+  for (int r = 0; r < nlat; r += nlat - 1) {
+    const int n = g.pl[r];
+    for (int j = 0; j < n / 2; ++j) {
+      const int64_t e = fe.find(static_cast<int32_t>(g.off[r] + j), static_cast<int32_t>(g.off[r] + j + n / 2));
+      if (e < 0) return false;
+      m.is_pole[e] = 1;
+    }
+  }
+  // ---- CSR node -> edges (ascending edge id) ----
+  m.n2e_ptr.assign(static_cast<size_t>(V) + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    m.n2e_ptr[m.e2n[2 * e] + 1]++;
+    m.n2e_ptr[m.e2n[2 * e + 1] + 1]++;
+  }
+  for (int64_t i = 0; i < V; ++i) m.n2e_ptr[i + 1] += m.n2e_ptr[i];
+  m.n2e.resize(static_cast<size_t>(2 * E));
+  m.n2e_sign.resize(static_cast<size_t>(2 * E));
+  {
+    std::vector<int32_t> pos(m.n2e_ptr.begin(), m.n2e_ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+      const int32_t a = m.e2n[2 * e], b = m.e2n[2 * e + 1];
+      m.n2e[pos[a]] = static_cast<int32_t>(e);
+      m.n2e_sign[pos[a]++] = 1;
+      m.n2e[pos[b]] = static_cast<int32_t>(e);
+      m.n2e_sign[pos[b]++] = -1;
+    }
+  }
+  // ---- triangles and dual-face end points from the zipper walk ----
+  int64_t T = 0;
+  for (int r = 0; r + 1 < nlat; ++r) T += g.pl[r] + g.pl[r + 1];
+  m.ntri = T;
+  m.tri.resize(static_cast<size_t>(3 * T));
+  m.side_off.assign(static_cast<size_t>(2 * E), 0.0);
+  m.side_lat.assign(static_cast<size_t>(2 * E), 0.0);
+  m.mid_lat.assign(static_cast<size_t>(E), 0.0);
+  std::vector<int64_t> tri_base(static_cast<size_t>(nlat), 0);
+  for (int r = 0; r + 1 < nlat; ++r) tri_base[r + 1] = tri_base[r] + g.pl[r] + g.pl[r + 1];
+  bool ok = true;
+#pragma omp parallel for schedule(dynamic, 1) reduction(&& : ok)
+  for (int r = 0; r < nlat - 1; ++r) {
+    const int s = r + 1;
+    const int64_t n1 = g.pl[r], n2 = g.pl[s];
+    const int64_t o1 = g.off[r], o2 = g.off[s];
+    const int64_t D = 6 * n1 * n2;  // every longitude of the band is an integer / D turns
+    const double lat_r = g.lat[r], lat_s = g.lat[s];
+    const double cent_n = ((lat_r + lat_r) + lat_s) / 3.0;  // two vertices in the northern row
+    const double cent_s = ((lat_s + lat_s) + lat_r) / 3.0;  // two vertices in the southern row
+    auto node = [&](int64_t o, int64_t n, int64_t j) { return static_cast<int32_t>(o + (j % n)); };
+    auto set_side = [&](int64_t e, int side, double off, double lat) {
+      m.side_off[2 * e + side] = off;
+      m.side_lat[2 * e + side] = lat;
+    };
+    // cross edge k is bounded by triangle k on its left (east) and k-1 on its right (west)
+    int64_t ia = 0, ib = 0;
+    const int64_t K = n1 + n2;
+    int64_t e_first = -1;
+    for (int64_t k = 0; k < K; ++k) {
+      const bool north = north_advances(ia, ib, n1, n2);
+      const int64_t xa = ia * 6 * n2, xb = ib * 6 * n1;  // west cross edge, both ends
+      const int64_t xc = north ? (ia + 1) * 6 * n2 : (ib + 1) * 6 * n1;
+      const int64_t cD = (xa + xb + xc) / 3;
+      const double clat = north ? cent_n : cent_s;
+      int32_t* t = &m.tri[3 * (tri_base[r] + k)];
+      t[0] = node(o1, n1, ia);
+      if (north) { t[1] = node(o1, n1, ia + 1); t[2] = node(o2, n2, ib); }
+      else { t[1] = node(o2, n2, ib); t[2] = node(o2, n2, ib + 1); }
+      // west cross edge (N(ia), S(ib)): this triangle is on its left
+      const int64_t ew = fe.find(node(o1, n1, ia), node(o2, n2, ib));
+      if (ew < 0) { ok = false; break; }
+      if (k == 0) e_first = ew;
+      set_side(ew, 0, ratio(2 * cD - (xa + xb), 2 * D), clat);
+      // east cross edge: this triangle is on its right
+      const int64_t na = north ? ia + 1 : ia, nb = north ? ib : ib + 1;
+      const int64_t ee = (k + 1 < K) ? fe.find(node(o1, n1, na), node(o2, n2, nb)) : e_first;
+      if (ee < 0) { ok = false; break; }
+      set_side(ee, 1, ratio(2 * cD - (na * 6 * n2 + nb * 6 * n1), 2 * D), clat);
+      // ring edge of the advancing row
+      if (north) {
+        // row r edge (ia, ia+1); the triangle lies south of it
+        const int32_t u = node(o1, n1, ia), v = node(o1, n1, ia + 1);
+        const bool wrap = (ia + 1 == n1);
+        const int64_t er = wrap ? fe.find(v, u) : fe.find(u, v);
+        if (er < 0) { ok = false; break; }
+        const int side = wrap ? 0 : 1;  // eastward edge: south is right; the wrap edge runs west
+        set_side(er, side, ratio(2 * cD - (xa + (ia + 1) * 6 * n2), 2 * D), clat);
+        if (r == 0) set_side(er, 1 - side, 0.0, kHalfPi);  // the face continues to the pole
+        ++ia;
+      } else {
+        // row s edge (ib, ib+1); the triangle lies north of it
+        const int32_t u = node(o2, n2, ib), v = node(o2, n2, ib + 1);
+        const bool wrap = (ib + 1 == n2);
+        const int64_t er = wrap ? fe.find(v, u) : fe.find(u, v);
+        if (er < 0) { ok = false; break; }
+        const int side = wrap ? 1 : 0;  // eastward edge: north is left
+        set_side(er, side, ratio(2 * cD - (xb + (ib + 1) * 6 * n1), 2 * D), clat);
+        if (s == nlat - 1) set_side(er, 1 - side, 0.0, -kHalfPi);
+        ++ib;
+      }
+    }
+  }
+  if (!ok) return false;
+  // midpoint latitude of every edge: its row, or the mean of the two rows
+  std::vector<int32_t> row_of(static_cast<size_t>(V));
+  for (int r = 0; r < nlat; ++r)
+    for (int64_t i = g.off[r]; i < g.off[r + 1]; ++i) row_of[i] = r;
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < E; ++e) {
+    const int ra = row_of[m.e2n[2 * e]], rb = row_of[m.e2n[2 * e + 1]];
+    m.mid_lat[e] = (ra == rb) ? g.lat[ra] : 0.5 * (g.lat[ra] + g.lat[rb]);
+  }
+  return true;
+}
+
+bool build_dual(const Mesh& m, double R, Dual& d) {
+  const Grid& g = *m.grid;
+  const int64_t V = g.nnodes, E = m.nedges;
+  if (!(R > 0)) return false;
+  d.R = R;
+  d.S.assign(static_cast<size_t>(2 * E), 0.0);
+  d.V.assign(static_cast<size_t>(V), 0.0);
+  d.coslat.resize(static_cast<size_t>(V));
+  d.pole_nphi.assign(static_cast<size_t>(V), 0.0);
+  const double C = kTwoPi * R;
+  std::vector<double> seg(static_cast<size_t>(2 * E), 0.0);  // integrals of c_R -> m and m -> c_L
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < E; ++e) {
+    if (m.is_pole[e]) {
+      const int32_t a = m.e2n[2 * e];
+      const bool north = a < g.pl[0];
+      const double sp = C * ratio(1, north ? g.pl[0] : g.pl[g.nlat - 1]);
+      d.S[2 * e] = 0.0;
+      d.S[2 * e + 1] = north ? sp : -sp;
+      continue;
+    }
+    const double offL = m.side_off[2 * e], offR = m.side_off[2 * e + 1];
+    const double latL = m.side_lat[2 * e], latR = m.side_lat[2 * e + 1], latm = m.mid_lat[e];
+    d.S[2 * e] = R * (latL - latR);
+    d.S[2 * e + 1] = -(C * (offL - offR));
+    const double d1 = -offR, d2 = offL;
+    seg[2 * e] = -((kTwoPi * d1) * std::sin(0.5 * (latR + latm))) * sinc(0.5 * (latm - latR));
+    seg[2 * e + 1] = -((kTwoPi * d2) * std::sin(0.5 * (latm + latL))) * sinc(0.5 * (latL - latm));
+  }
+  const double R2 = R * R;
+  const int nlat = g.nlat;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < V; ++i) {
+    Comp acc;
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+      const int32_t e = m.n2e[q];
+      if (m.is_pole[e]) continue;
+      if (m.n2e_sign[q] > 0) {
+        acc.add(seg[2 * e]);
+        acc.add(seg[2 * e + 1]);
+      } else {
+        acc.add(-seg[2 * e]);
+        acc.add(-seg[2 * e + 1]);
+      }
+    }
+    const int r = static_cast<int>(std::upper_bound(g.off.begin(), g.off.end(), i) - g.off.begin()) - 1;
+    if (r == 0 || r == nlat - 1) {
+      acc.add(kTwoPi * ratio(1, g.pl[r]));  // pole segment of the polar cell
+      const double sp = C * ratio(1, g.pl[r]);
+      d.pole_nphi[i] = (r == 0) ? sp : -sp;
+    }
+    d.V[i] = R2 * acc.value();
+    d.coslat[i] = std::cos(g.lat[r]);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Stencil tables.  n_ie denotes the outward normal of cell i on the face of
+// edge e: s_ie S_e for a regular edge, S_e at both ends of a pole edge.
+// ---------------------------------------------------------------------------
+namespace {
+
+inline int32_t other_end(const Mesh& m, int32_t e, int64_t i) {
+  const int32_t a = m.e2n[2 * e], b = m.e2n[2 * e + 1];
+  return a == i ? b : a;
+}
+inline void normal_of(const Mesh& m, const Dual& d, int32_t q, double& nl, double& np) {
+  const int32_t e = m.n2e[q];
+  const double s = m.is_pole[e] ? 1.0 : static_cast<double>(m.n2e_sign[q]);
+  nl = s * d.S[2 * e];
+  np = s * d.S[2 * e + 1];
+}
+// normal of cell j on the face it shares with cell i through edge e
+inline void normal_seen_from(const Mesh& m, const Dual& d, int32_t e, int64_t j, double& nl, double& np) {
+  const double s = m.is_pole[e] ? 1.0 : (m.e2n[2 * e] == j ? 1.0 : -1.0);
+  nl = s * d.S[2 * e];
+  np = s * d.S[2 * e + 1];
+}
+
+// gradient weights of row i on its edge through CSR slot q
+inline void grad_w(const Mesh& m, const Dual& d, int64_t i, int32_t q, double& w0, double& w1) {
+  double nl, np;
+  normal_of(m, d, q, nl, np);
+  w0 = nl / (2.0 * d.V[i]);
+  w1 = d.coslat[i] * np / (2.0 * d.V[i]);
+}
+// divergence weights of row i towards neighbour j (regular edge)
+inline void div_w(const Dual& d, int64_t i, int64_t j, double nl, double np, double& w0, double& w1) {
+  w0 = nl / (2.0 * d.V[i]);
+  w1 = np * d.coslat[j] / (2.0 * d.V[i]);
+}
+// phi-coefficient of v_i in the divergence of row i:
+//   [ sum_regular n_phi (cos_j - cos_i)/2 - cos_i n_pole,phi ] / V_i
+double div_vdiag(const Mesh& m, const Dual& d, int64_t i) {
+  Comp acc;
+  const double ci = d.coslat[i];
+  for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+    const int32_t e = m.n2e[q];
+    if (m.is_pole[e]) continue;
+    double nl, np;
+    normal_of(m, d, q, nl, np);
+    const int32_t j = other_end(m, e, i);
+    acc.add_prod(np, 0.5 * (d.coslat[j] - ci));
+  }
+  acc.add_prod(-ci, d.pole_nphi[i]);
+  return acc.value() / d.V[i];
+}
+
+}  // namespace
+
+bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
+  const int64_t V = m.grid->nnodes;
+  s.ptr.assign(static_cast<size_t>(V) + 1, 0);
+  const bool regular_only = (op == OP_DIV || op == OP_DIV_ADJ);
+  if (op == OP_LAP) {
+    s.nin = 1; s.nout = 1; s.has_b = false; s.scalar_w = true;
+    // L = D G as sparse matrices; the row sums of L vanish (G applied to a
+    // constant is zero), so only the off-diagonal entries are stored.
+    std::vector<double> vdiag(static_cast<size_t>(V));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < V; ++i) vdiag[i] = div_vdiag(m, d, i);
+    struct Acc { int32_t col; Comp v; };
+    auto row = [&](int64_t i, std::vector<Acc>& out) {
+      out.clear();
+      auto add = [&](int32_t col, double a, double b) {
+        for (auto& x : out)
+          if (x.col == col) { x.v.add_prod(a, b); return; }
+        out.push_back(Acc{col, Comp{}});
+        out.back().v.add_prod(a, b);
+      };
+      // D row i: (k, du, dv); diagonal pieces kept separate
+      auto g_row = [&](int64_t k, double du, double dv) {
+        for (int32_t q = m.n2e_ptr[k]; q < m.n2e_ptr[k + 1]; ++q) {
+          double gl, gp;
+          grad_w(m, d, k, q, gl, gp);
+          const int32_t j = other_end(m, m.n2e[q], k);
+          add(j, du, gl); add(j, dv, gp);
+          add(static_cast<int32_t>(k), du, -gl); add(static_cast<int32_t>(k), dv, -gp);
+        }
+      };
+      for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+        const int32_t e = m.n2e[q];
+        if (m.is_pole[e]) continue;
+        double nl, np, du, dv;
+        normal_of(m, d, q, nl, np);
+        const int32_t k = other_end(m, e, i);
+        div_w(d, i, k, nl, np, du, dv);
+        g_row(k, du, dv);
+        g_row(i, -du, -dv);
+      }
+      g_row(i, 0.0, vdiag[i]);
+      std::sort(out.begin(), out.end(), [](const Acc& x, const Acc& y) { return x.col < y.col; });
+    };
+    std::vector<int32_t> len(static_cast<size_t>(V));
+#pragma omp parallel
+    {
+      std::vector<Acc> buf;
+#pragma omp for schedule(dynamic, 256)
+      for (int64_t i = 0; i < V; ++i) {
+        row(i, buf);
+        len[i] = static_cast<int32_t>(buf.size()) - 1;  // minus the diagonal
+      }
+    }
+    for (int64_t i = 0; i < V; ++i) {
+      if (static_cast<int64_t>(s.ptr[i]) + len[i] > INT32_MAX) return false;
+      s.ptr[i + 1] = s.ptr[i] + len[i];
+    }
+    s.nbr.resize(static_cast<size_t>(s.ptr[V]));
+    s.w.assign(static_cast<size_t>(2 * s.ptr[V]), 0.0);
+#pragma omp parallel
+    {
+      std::vector<Acc> buf;
+#pragma omp for schedule(dynamic, 256)
+      for (int64_t i = 0; i < V; ++i) {
+        row(i, buf);
+        int32_t q = s.ptr[i];
+        for (auto& x : buf) {
+          if (x.col == i) continue;
+          s.nbr[q] = x.col;
+          s.w[2 * static_cast<int64_t>(q)] = x.v.value();
+          ++q;
+        }
+      }
+    }
+    return true;
+  }
+  // 1-ring stencils
+  for (int64_t i = 0; i < V; ++i) {
+    int32_t c = 0;
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q)
+      if (!(regular_only && m.is_pole[m.n2e[q]])) ++c;
+    s.ptr[i + 1] = s.ptr[i] + c;
+  }
+  const int64_t nnz = s.ptr[V];
+  s.nbr.resize(static_cast<size_t>(nnz));
+  s.w.resize(static_cast<size_t>(2 * nnz));
+  s.has_b = (op != OP_GRAD);
+  s.scalar_w = false;
+  s.nin = (op == OP_GRAD || op == OP_DIV_ADJ) ? 1 : 2;
+  s.nout = 3 - s.nin;
+  if (s.has_b) s.b.assign(static_cast<size_t>(2 * V), 0.0);
+  std::vector<double> vdiag;
+  if (op == OP_DIV || op == OP_DIV_ADJ) {
+    vdiag.resize(static_cast<size_t>(V));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < V; ++i) vdiag[i] = div_vdiag(m, d, i);
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < V; ++i) {
+    int32_t o = s.ptr[i];
+    Comp b0, b1;
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+      const int32_t e = m.n2e[q];
+      if (regular_only && m.is_pole[e]) continue;
+      const int32_t j = other_end(m, e, i);
+      double w0 = 0, w1 = 0;
+      if (op == OP_GRAD) {
+        grad_w(m, d, i, q, w0, w1);
+      } else if (op == OP_DIV) {
+        double nl, np;
+        normal_of(m, d, q, nl, np);
+        div_w(d, i, j, nl, np, w0, w1);
+      } else if (op == OP_GRAD_ADJ) {
+        // column i of row j of the gradient: weights of row j towards node i
+        double nl, np;
+        normal_seen_from(m, d, e, j, nl, np);
+        w0 = nl / (2.0 * d.V[j]);
+        w1 = d.coslat[j] * np / (2.0 * d.V[j]);
+        double r0, r1;
+        grad_w(m, d, i, q, r0, r1);
+        b0.add(w0); b0.add(-r0);
+        b1.add(w1); b1.add(-r1);
+      } else {  // OP_DIV_ADJ: column i of row j of the divergence
+        double nl, np;
+        normal_seen_from(m, d, e, j, nl, np);
+        div_w(d, j, i, nl, np, w0, w1);
+        double own_l, own_p, r0, r1;
+        normal_of(m, d, q, own_l, own_p);
+        div_w(d, i, j, own_l, own_p, r0, r1);
+        b0.add(w0); b0.add(-r0);
+        b1.add(w1); b1.add(-r1);
+      }
+      s.nbr[o] = j;
+      s.w[2 * static_cast<int64_t>(o)] = w0;
+      s.w[2 * static_cast<int64_t>(o) + 1] = w1;
+      ++o;
+    }
+    if (op == OP_DIV) {
+      s.b[2 * i] = 0.0;
+      s.b[2 * i + 1] = vdiag[i];
+    } else if (op == OP_GRAD_ADJ) {
+      s.b[2 * i] = b0.value();
+      s.b[2 * i + 1] = b1.value();
+    } else if (op == OP_DIV_ADJ) {
+      s.b[2 * i] = b0.value();
+      b1.add(vdiag[i]);
+      s.b[2 * i + 1] = b1.value();
+    }
+  }
+  return true;
+}
+
+bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg) {
+  const int64_t V = m.grid->nnodes, E = m.nedges;
+  const bool div = (op == OP_DIV);
+  eg.ptr.assign(static_cast<size_t>(V) + 1, 0);
+  for (int64_t i = 0; i < V; ++i) {
+    int32_t c = 0;
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q)
+      if (!(div && m.is_pole[m.n2e[q]])) ++c;
+    eg.ptr[i + 1] = eg.ptr[i] + c;
+  }
+  eg.ent.resize(static_cast<size_t>(eg.ptr[V]));
+  eg.inv_v.resize(static_cast<size_t>(V));
+  eg.cos_v.resize(static_cast<size_t>(V));
+  eg.pole_coef.assign(static_cast<size_t>(V), 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < V; ++i) {
+    int32_t o = eg.ptr[i];
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+      const int32_t e = m.n2e[q];
+      if (div && m.is_pole[e]) continue;
+      // difference-form edge flux S_e (x_b - x_a)/2 enters both ends with +1;
+      // a pole edge enters its second end with -1 (its normal is the same at both ends)
+      const bool neg = m.is_pole[e] && m.n2e_sign[q] < 0;
+      eg.ent[o++] = (e << 1) | (neg ? 1 : 0);
+    }
+    eg.inv_v[i] = 1.0 / d.V[i];
+    eg.cos_v[i] = d.coslat[i] / d.V[i];
+    eg.pole_coef[i] = -(d.coslat[i] * d.pole_nphi[i]) / d.V[i];
+  }
+  eg.dcos.resize(static_cast<size_t>(E));
+  for (int64_t e = 0; e < E; ++e) eg.dcos[e] = d.coslat[m.e2n[2 * e + 1]] - d.coslat[m.e2n[2 * e]];
+  return true;
+}
+
+}  // namespace atlasgb

@@ -1,0 +1,85 @@
+// Host-side grid, mesh and median-dual geometry of the octahedral reduced
+// Gaussian grid, plus the per-operator stencil tables the GPU kernels read.
+//
+// The paper's workflow is Grid -> Mesh -> FunctionSpace -> Field, with
+// gradient, divergence and Laplacian supplied on top (Sec. 2.3, Fig. 2).  This
+// file builds the Grid (Gaussian latitudes, octahedral rows), the Mesh (zipper
+// triangulation, pole edges, node->edge CSR) and the FunctionSpace geometry
+// (median-dual volumes and normals, FP64), all on the host.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace atlasgb {
+
+struct Grid {
+  int N = 0;
+  int nlat = 0;
+  int64_t nnodes = 0;
+  std::vector<int32_t> pl;     // points per row, north -> south
+  std::vector<int64_t> off;    // first node of each row, size nlat+1
+  std::vector<double> colat;   // colatitude of each row (radians)
+  std::vector<double> lat;     // latitude of each row (radians)
+  std::vector<double> lonlat;  // [nnodes][2] longitude, latitude (radians)
+};
+
+struct Mesh {
+  const Grid* grid = nullptr;
+  int64_t nedges = 0, ntri = 0;
+  std::vector<int32_t> e2n;       // [E][2], a < b, sorted by (a, b)
+  std::vector<uint8_t> is_pole;   // [E]
+  std::vector<int32_t> n2e_ptr;   // [V+1]
+  std::vector<int32_t> n2e;       // [2E], ascending edge id per node
+  std::vector<int8_t> n2e_sign;   // [2E], +1 at a, -1 at b
+  std::vector<int32_t> tri;       // [T][3] node ids, band by band
+  // dual-face end points of every regular edge: side 0 = left of a->b, 1 = right
+  std::vector<double> side_off;   // [E][2] offset of the end point from the edge midpoint (turns)
+  std::vector<double> side_lat;   // [E][2] latitude of the end point
+  std::vector<double> mid_lat;    // [E]
+};
+
+struct Dual {
+  double R = 0;
+  std::vector<double> S;          // [E][2] (S_lambda, S_phi) oriented a -> b
+  std::vector<double> V;          // [V]
+  std::vector<double> coslat;     // [V]
+  std::vector<double> pole_nphi;  // [V] phi-normal of the pole segment (0 off the polar rows)
+};
+
+// A node-centred stencil: out_c(i) = sum_{q in row i} sum_m W_{c,m}(q) (x_m(nbr[q]) - x_m(i))
+//                                    + sum_m B_{c,m}(i) x_m(i)
+// with one (NIN = 1) or two (NIN = 2) inputs and one or two outputs.  The
+// weight pair w[2q], w[2q+1] is (W_{0,0}, W_{1,0}) when NIN = 1 and
+// (W_{0,0}, W_{0,1}) when NIN = 2; b[2i], b[2i+1] likewise.
+struct Stencil {
+  int nin = 1, nout = 1;
+  bool has_b = false;
+  bool scalar_w = false;          // only w[2q] is used (Laplacian)
+  std::vector<int32_t> ptr;       // [V+1]
+  std::vector<int32_t> nbr;       // [nnz]
+  std::vector<double> w;          // [nnz][2]
+  std::vector<double> b;          // [V][2] (empty when !has_b)
+};
+
+// Edge-based two-pass data (edge-flux kernel + node-gather kernel).
+struct EdgeGather {
+  std::vector<int32_t> ptr;       // [V+1]
+  std::vector<int32_t> ent;       // [nnz] edge id << 1 | (negative sign)
+  std::vector<double> inv_v;      // [V] 1/V
+  std::vector<double> cos_v;      // [V] cos/V
+  std::vector<double> pole_coef;  // [V] -cos * n_pole / V (divergence), 0 off the polar rows
+  std::vector<double> dcos;       // [E] cos(b) - cos(a)
+};
+
+void gauss_colatitudes(int n, double* theta);
+bool build_grid(int N, Grid& g);
+bool build_mesh(const Grid& g, Mesh& m);
+bool build_dual(const Mesh& m, double R, Dual& d);
+
+enum StencilOp { OP_GRAD = 0, OP_DIV = 1, OP_GRAD_ADJ = 2, OP_DIV_ADJ = 3, OP_LAP = 4, OP_COUNT = 5 };
+bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
+bool build_edge_gather(const Mesh& m, const Dual& d, int op /*OP_GRAD or OP_DIV*/, EdgeGather& eg);
+
+}  // namespace atlasgb

@@ -1,0 +1,489 @@
+// CUDA kernels (sm_103a) of the nabla operators on field[node][level].
+//
+// The operators are sparse stencils: every output value needs the node's own
+// value and those of its 6-7 edge neighbours (19 for the fused Laplacian), a
+// few flops each.  The work is therefore bound by HBM traffic, not by
+// arithmetic, and tensor cores have no role.  Design:
+//   * one thread handles one (node, level-vector) item: VEC consecutive levels
+//     of one node, loaded as one 16-byte (or narrower) vector; consecutive
+//     threads take consecutive level vectors of the same node row, so a warp
+//     reads whole 128-byte segments of a row (levels innermost);
+//   * neighbour rows are re-read through the read-only path (ld.global.nc);
+//     the rows of three adjacent latitudes are a few MB and stay in L2, so
+//     each input value leaves HBM about once;
+//   * the CSR row (neighbour id and weight pair) is the same for all level
+//     vectors of a node and is served from L1 as a broadcast;
+//   * fixed CSR summation order, no atomics: results are bitwise
+//     deterministic and independent of the launch shape.
+// The edge-flux / node-gather pair and the persistent batched kernel reuse
+// the same per-item device functions.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace atlasgb {
+namespace {
+
+// ---------------------------------------------------------------- storage
+template <int BYTES> struct Raw;
+template <> struct Raw<16> { using T = uint4; };
+template <> struct Raw<8> { using T = uint2; };
+template <> struct Raw<4> { using T = unsigned int; };
+template <> struct Raw<2> { using T = unsigned short; };
+
+// bfloat16 is carried as its 16-bit pattern (uint16_t) inside the kernels
+template <typename S, typename A> struct Conv {
+  static __device__ __forceinline__ A to(S x) { return static_cast<A>(x); }
+  static __device__ __forceinline__ S from(A x) { return static_cast<S>(x); }
+};
+template <> struct Conv<uint16_t, float> {
+  static __device__ __forceinline__ float to(uint16_t x) { return __uint_as_float(static_cast<uint32_t>(x) << 16); }
+  static __device__ __forceinline__ uint16_t from(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+};
+
+template <typename S, typename A, int VEC>
+__device__ __forceinline__ void vload(const S* __restrict__ p, A (&out)[VEC]) {
+  constexpr int BYTES = VEC * static_cast<int>(sizeof(S));
+  using R = typename Raw<BYTES>::T;
+  const R raw = __ldg(reinterpret_cast<const R*>(p));
+  S e[VEC];
+  memcpy(e, &raw, BYTES);
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) out[k] = Conv<S, A>::to(e[k]);
+}
+
+template <typename S, typename A, int VEC>
+__device__ __forceinline__ void vstore(S* __restrict__ p, const A (&v)[VEC], int nvalid) {
+  constexpr int BYTES = VEC * static_cast<int>(sizeof(S));
+  using R = typename Raw<BYTES>::T;
+  S e[VEC];
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) e[k] = Conv<S, A>::from(v[k]);
+  if (nvalid >= VEC) {
+    R raw;
+    memcpy(&raw, e, BYTES);
+    *reinterpret_cast<R*>(p) = raw;
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k)
+      if (k < nvalid) p[k] = e[k];
+  }
+}
+
+template <typename A> struct Pair;
+template <> struct Pair<float> {
+  static __device__ __forceinline__ void load(const float* p, int64_t k, float& x, float& y) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p) + k);
+    x = t.x;
+    y = t.y;
+  }
+};
+template <> struct Pair<double> {
+  static __device__ __forceinline__ void load(const double* p, int64_t k, double& x, double& y) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p) + k);
+    x = t.x;
+    y = t.y;
+  }
+};
+
+// ------------------------------------------------------- node stencil item
+// out_c(i) = sum_q sum_m W_cm(q) (x_m(nbr q) - x_m(i)) + sum_m B_cm(i) x_m(i)
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+__device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
+                                             const A* __restrict__ w, const A* __restrict__ b,
+                                             const S* __restrict__ in0, const S* __restrict__ in1,
+                                             S* __restrict__ out0, S* __restrict__ out1, int64_t ld, int32_t nlev,
+                                             int32_t i, int32_t lev0) {
+  const int64_t oi = static_cast<int64_t>(i) * ld + lev0;
+  A xi0[VEC], xi1[VEC], acc0[VEC], acc1[VEC];
+  vload<S, A, VEC>(in0 + oi, xi0);
+  if constexpr (NIN == 2) vload<S, A, VEC>(in1 + oi, xi1);
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) {
+    acc0[k] = A(0);
+    acc1[k] = A(0);
+  }
+  const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
+  for (int32_t q = q0; q < q1; ++q) {
+    const int32_t j = __ldg(nbr + q);
+    A w0, w1 = A(0);
+    if constexpr (SCALAR_W) {
+      w0 = __ldg(w + q);
+    } else {
+      Pair<A>::load(w, q, w0, w1);
+    }
+    const int64_t oj = static_cast<int64_t>(j) * ld + lev0;
+    A xj0[VEC];
+    vload<S, A, VEC>(in0 + oj, xj0);
+    if constexpr (NIN == 1) {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        const A d = xj0[k] - xi0[k];
+        acc0[k] = fma(w0, d, acc0[k]);
+        if constexpr (NOUT == 2) acc1[k] = fma(w1, d, acc1[k]);
+      }
+    } else {
+      A xj1[VEC];
+      vload<S, A, VEC>(in1 + oj, xj1);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        acc0[k] = fma(w0, xj0[k] - xi0[k], acc0[k]);
+        acc0[k] = fma(w1, xj1[k] - xi1[k], acc0[k]);
+      }
+    }
+  }
+  if constexpr (HAS_B) {
+    A b0, b1;
+    Pair<A>::load(b, i, b0, b1);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      if constexpr (NIN == 2) {
+        acc0[k] = fma(b0, xi0[k], acc0[k]);
+        acc0[k] = fma(b1, xi1[k], acc0[k]);
+      } else {
+        acc0[k] = fma(b0, xi0[k], acc0[k]);
+        acc1[k] = fma(b1, xi0[k], acc1[k]);
+      }
+    }
+  }
+  const int nvalid = nlev - lev0;
+  vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
+  if constexpr (NOUT == 2) vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
+}
+
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+__global__ void __launch_bounds__(1024) stencil_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
+                                                       const A* __restrict__ w, const A* __restrict__ b,
+                                                       const S* __restrict__ in0, const S* __restrict__ in1,
+                                                       S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
+                                                       int32_t nlev, int64_t ld, uint32_t nvec) {
+  const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;  // host guarantees < 2^31
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+    const uint32_t i = item / nvec;
+    const uint32_t v = item - i * nvec;
+    stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+                                                        static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
+  }
+}
+
+// ------------------------------------------------------------- edge pass
+// OP 0 (gradient): flux0 = k1 (x_b - x_a), flux1 = k2 (x_b - x_a)
+// OP 1 (divergence): flux0 = k1 (u_b - u_a) + k2 (v_b - v_a) + k3 v_a
+template <typename S, typename A, int OP, int VEC>
+__global__ void __launch_bounds__(1024) edge_flux_kernel(const int32_t* __restrict__ e2n, const A* __restrict__ coef,
+                                                         const S* __restrict__ in0, const S* __restrict__ in1,
+                                                         A* __restrict__ flux0, A* __restrict__ flux1,
+                                                         uint32_t nedges, int32_t nlev, int64_t ld, uint32_t nvec) {
+  const uint32_t total = nedges * nvec;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+    const uint32_t e = item / nvec;
+    const int32_t lev0 = static_cast<int32_t>((item - e * nvec) * VEC);
+    const int2 ab = __ldg(reinterpret_cast<const int2*>(e2n) + e);
+    const A k1 = __ldg(coef + 3 * static_cast<int64_t>(e));
+    const A k2 = __ldg(coef + 3 * static_cast<int64_t>(e) + 1);
+    const int64_t oa = static_cast<int64_t>(ab.x) * ld + lev0, ob = static_cast<int64_t>(ab.y) * ld + lev0;
+    const int64_t oe = static_cast<int64_t>(e) * ld + lev0;
+    A xa[VEC], xb[VEC], f0[VEC];
+    vload<S, A, VEC>(in0 + oa, xa);
+    vload<S, A, VEC>(in0 + ob, xb);
+    const int nvalid = nlev - lev0;
+    if constexpr (OP == 0) {
+      A f1[VEC];
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        const A d = xb[k] - xa[k];
+        f0[k] = k1 * d;
+        f1[k] = k2 * d;
+      }
+      vstore<A, A, VEC>(flux0 + oe, f0, nvalid);
+      vstore<A, A, VEC>(flux1 + oe, f1, nvalid);
+    } else {
+      const A k3 = __ldg(coef + 3 * static_cast<int64_t>(e) + 2);
+      A ya[VEC], yb[VEC];
+      vload<S, A, VEC>(in1 + oa, ya);
+      vload<S, A, VEC>(in1 + ob, yb);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        A t = k1 * (xb[k] - xa[k]);
+        t = fma(k2, yb[k] - ya[k], t);
+        f0[k] = fma(k3, ya[k], t);
+      }
+      vstore<A, A, VEC>(flux0 + oe, f0, nvalid);
+    }
+  }
+}
+
+// OP 0: out0 = (1/V) sum +-flux0, out1 = (cos/V) sum +-flux1
+// OP 1: out0 = (1/V) sum flux0 + pole_coef * v_i
+template <typename S, typename A, int OP, int VEC>
+__global__ void __launch_bounds__(1024) node_gather_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+                                                           const A* __restrict__ node, const A* __restrict__ flux0,
+                                                           const A* __restrict__ flux1, const S* __restrict__ vin,
+                                                           S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
+                                                           int32_t nlev, int64_t ld, uint32_t nvec) {
+  const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+    const uint32_t i = item / nvec;
+    const int32_t lev0 = static_cast<int32_t>((item - i * nvec) * VEC);
+    A acc0[VEC], acc1[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      acc0[k] = A(0);
+      acc1[k] = A(0);
+    }
+    const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
+    for (int32_t q = q0; q < q1; ++q) {
+      const int32_t t = __ldg(ent + q);
+      const int64_t oe = static_cast<int64_t>(t >> 1) * ld + lev0;
+      A f[VEC];
+      vload<A, A, VEC>(flux0 + oe, f);
+      if (t & 1) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc0[k] -= f[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc0[k] += f[k];
+      }
+      if constexpr (OP == 0) {
+        vload<A, A, VEC>(flux1 + oe, f);
+        if (t & 1) {
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) acc1[k] -= f[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) acc1[k] += f[k];
+        }
+      }
+    }
+    const A inv_v = __ldg(node + 3 * static_cast<int64_t>(i));
+    const int64_t oi = static_cast<int64_t>(i) * ld + lev0;
+    const int nvalid = nlev - lev0;
+    if constexpr (OP == 0) {
+      const A cos_v = __ldg(node + 3 * static_cast<int64_t>(i) + 1);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        acc0[k] *= inv_v;
+        acc1[k] *= cos_v;
+      }
+      vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
+      vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
+    } else {
+      const A pc = __ldg(node + 3 * static_cast<int64_t>(i) + 2);
+      A vi[VEC];
+      vload<S, A, VEC>(vin + oi, vi);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) acc0[k] = fma(pc, vi[k], acc0[k] * inv_v);
+      vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
+    }
+  }
+}
+
+// ------------------------------------------------------- persistent batch
+template <typename S, typename A, int VEC>
+__device__ __forceinline__ void batch_items(const BatchDescDev& D, int64_t it0, int64_t it1) {
+  const A* w = static_cast<const A*>(D.w);
+  const A* b = static_cast<const A*>(D.b);
+  const S* in0 = static_cast<const S*>(D.in0);
+  const S* in1 = static_cast<const S*>(D.in1);
+  S* out0 = static_cast<S*>(D.out0);
+  S* out1 = static_cast<S*>(D.out1);
+  const uint32_t nvec = static_cast<uint32_t>(D.nvec);
+  for (int64_t it = it0 + threadIdx.x; it < it1; it += blockDim.x) {
+    const uint32_t u = static_cast<uint32_t>(it);
+    const uint32_t i = u / nvec;
+    const int32_t lev0 = static_cast<int32_t>((u - i * nvec) * VEC);
+    if (D.op == 0)
+      stencil_item<S, A, 1, 2, VEC, false, false>(D.ptr, D.nbr, w, b, in0, in1, out0, out1, D.ld, D.nlev,
+                                                  static_cast<int32_t>(i), lev0);
+    else
+      stencil_item<S, A, 2, 1, VEC, true, false>(D.ptr, D.nbr, w, b, in0, in1, out0, out1, D.ld, D.nlev,
+                                                 static_cast<int32_t>(i), lev0);
+  }
+}
+
+template <typename S, typename A>
+__global__ void __launch_bounds__(1024) batch_kernel(const BatchDescDev* __restrict__ descs, int ndesc, int64_t ntiles,
+                                                     int tile_items) {
+  extern __shared__ int64_t s_tile0[];
+  for (int d = threadIdx.x; d < ndesc; d += blockDim.x) s_tile0[d] = descs[d].tile0;
+  __syncthreads();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int lo = 0, hi = ndesc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_tile0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchDescDev D = descs[lo];
+    const int64_t it0 = (t - D.tile0) * tile_items;
+    const int64_t it1 = (it0 + tile_items < D.items) ? it0 + tile_items : D.items;
+    if (D.vec == 4) {
+      if constexpr (sizeof(S) * 4 <= 16) batch_items<S, A, 4>(D, it0, it1);
+    } else if (D.vec == 2) {
+      batch_items<S, A, 2>(D, it0, it1);
+    } else {
+      batch_items<S, A, 1>(D, it0, it1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- dispatch
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
+  const uint32_t nvec = static_cast<uint32_t>((l.nlev + VEC - 1) / VEC);
+  stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W><<<l.blocks, l.threads, 0, stream>>>(
+      s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
+      static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec);
+  return cudaGetLastError();
+}
+
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+const void* stencil_fn() {
+  return reinterpret_cast<const void*>(&stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>);
+}
+
+// Visit the kernel instantiation of (storage, shape, vec); F is called with a
+// tag carrying the template arguments.
+template <typename S, typename A, int VEC, typename F>
+auto with_shape(const DevStencil& s, F&& f) {
+  if (s.scalar_w) return f.template operator()<S, A, 1, 1, VEC, false, true>();
+  if (s.nin == 1 && s.nout == 2 && !s.has_b) return f.template operator()<S, A, 1, 2, VEC, false, false>();
+  if (s.nin == 1 && s.nout == 2) return f.template operator()<S, A, 1, 2, VEC, true, false>();
+  return f.template operator()<S, A, 2, 1, VEC, true, false>();
+}
+
+template <typename S, typename A, typename F>
+auto with_vec(const DevStencil& s, int vec, F&& f) {
+  constexpr int maxvec = 16 / static_cast<int>(sizeof(S));
+  if (vec >= 8 && maxvec >= 8) return with_shape<S, A, (maxvec >= 8 ? 8 : 1)>(s, f);
+  if (vec >= 4 && maxvec >= 4) return with_shape<S, A, (maxvec >= 4 ? 4 : 1)>(s, f);
+  if (vec >= 2) return with_shape<S, A, 2>(s, f);
+  return with_shape<S, A, 1>(s, f);
+}
+
+template <typename F>
+auto with_storage(StorageType st, const DevStencil& s, int vec, F&& f) {
+  if (st == ST_F64) return with_vec<double, double>(s, vec, f);
+  if (st == ST_BF16) return with_vec<uint16_t, float>(s, vec, f);
+  return with_vec<float, float>(s, vec, f);
+}
+
+struct RunStencil {
+  const DevStencil& s;
+  const StencilLaunch& l;
+  cudaStream_t stream;
+  template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+  cudaError_t operator()() const {
+    return run_stencil<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>(s, l, stream);
+  }
+};
+
+struct StencilFn {
+  template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+  const void* operator()() const {
+    return stencil_fn<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>();
+  }
+};
+
+}  // namespace
+
+cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
+  return with_storage(st, s, l.vec, RunStencil{s, l, stream});
+}
+
+int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int threads) {
+  const void* fn = with_storage(st, s, vec, StencilFn{});
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess) return 1;
+  return blocks > 0 ? blocks : 1;
+}
+
+namespace {
+template <typename S, typename A, int VEC>
+cudaError_t run_edges(int op, const DevEdges& e, const void* in0, const void* in1, void* flux0, void* flux1,
+                      int32_t nlev, int64_t ld, int threads, int blocks, cudaStream_t stream) {
+  const uint32_t nvec = static_cast<uint32_t>((nlev + VEC - 1) / VEC);
+  const A* coef = static_cast<const A*>(e.coef);
+  if (op == 0)
+    edge_flux_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
+        e.e2n, coef, static_cast<const S*>(in0), nullptr, static_cast<A*>(flux0), static_cast<A*>(flux1),
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec);
+  else
+    edge_flux_kernel<S, A, 1, VEC><<<blocks, threads, 0, stream>>>(
+        e.e2n, coef, static_cast<const S*>(in0), static_cast<const S*>(in1), static_cast<A*>(flux0), nullptr,
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec);
+  return cudaGetLastError();
+}
+template <typename S, typename A, int VEC>
+cudaError_t run_gather(int op, const DevEdges& e, const void* flux0, const void* flux1, const void* vin, void* out0,
+                       void* out1, int32_t nlev, int64_t ld, int threads, int blocks, cudaStream_t stream) {
+  const uint32_t nvec = static_cast<uint32_t>((nlev + VEC - 1) / VEC);
+  const A* node = static_cast<const A*>(e.node);
+  if (op == 0)
+    node_gather_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
+        e.ptr, e.ent, node, static_cast<const A*>(flux0), static_cast<const A*>(flux1), nullptr, static_cast<S*>(out0),
+        static_cast<S*>(out1), e.nnodes, nlev, ld, nvec);
+  else
+    node_gather_kernel<S, A, 1, VEC><<<blocks, threads, 0, stream>>>(
+        e.ptr, e.ent, node, static_cast<const A*>(flux0), nullptr, static_cast<const S*>(vin), static_cast<S*>(out0),
+        nullptr, e.nnodes, nlev, ld, nvec);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_edge_flux(StorageType st, int op, const DevEdges& e, const void* in0, const void* in1, void* flux0,
+                             void* flux1, int32_t nlev, int64_t ld, int vec, int threads, int blocks,
+                             cudaStream_t stream) {
+  if (st == ST_F64) {
+    if (vec >= 2) return run_edges<double, double, 2>(op, e, in0, in1, flux0, flux1, nlev, ld, threads, blocks, stream);
+    return run_edges<double, double, 1>(op, e, in0, in1, flux0, flux1, nlev, ld, threads, blocks, stream);
+  }
+  if (st == ST_F32) {
+    if (vec >= 4) return run_edges<float, float, 4>(op, e, in0, in1, flux0, flux1, nlev, ld, threads, blocks, stream);
+    if (vec >= 2) return run_edges<float, float, 2>(op, e, in0, in1, flux0, flux1, nlev, ld, threads, blocks, stream);
+    return run_edges<float, float, 1>(op, e, in0, in1, flux0, flux1, nlev, ld, threads, blocks, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const void* flux0, const void* flux1,
+                               const void* vin, void* out0, void* out1, int32_t nlev, int64_t ld, int vec, int threads,
+                               int blocks, cudaStream_t stream) {
+  if (st == ST_F64) {
+    if (vec >= 2) return run_gather<double, double, 2>(op, e, flux0, flux1, vin, out0, out1, nlev, ld, threads, blocks, stream);
+    return run_gather<double, double, 1>(op, e, flux0, flux1, vin, out0, out1, nlev, ld, threads, blocks, stream);
+  }
+  if (st == ST_F32) {
+    if (vec >= 4) return run_gather<float, float, 4>(op, e, flux0, flux1, vin, out0, out1, nlev, ld, threads, blocks, stream);
+    if (vec >= 2) return run_gather<float, float, 2>(op, e, flux0, flux1, vin, out0, out1, nlev, ld, threads, blocks, stream);
+    return run_gather<float, float, 1>(op, e, flux0, flux1, vin, out0, out1, nlev, ld, threads, blocks, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch(StorageType st, const BatchDescDev* descs, int ndesc, int64_t ntiles, int tile_items,
+                         int threads, int blocks, cudaStream_t stream) {
+  const size_t smem = sizeof(int64_t) * static_cast<size_t>(ndesc);
+  if (st == ST_F64)
+    batch_kernel<double, double><<<blocks, threads, smem, stream>>>(descs, ndesc, ntiles, tile_items);
+  else if (st == ST_F32)
+    batch_kernel<float, float><<<blocks, threads, smem, stream>>>(descs, ndesc, ntiles, tile_items);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+int batch_occupancy(StorageType st, int threads) {
+  int blocks = 0;
+  const void* fn = (st == ST_F64) ? reinterpret_cast<const void*>(&batch_kernel<double, double>)
+                                  : reinterpret_cast<const void*>(&batch_kernel<float, float>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess) return 1;
+  return blocks > 0 ? blocks : 1;
+}
+
+}  // namespace atlasgb

@@ -1,0 +1,88 @@
+// Launch interface between the C ABI (capi.cpp) and the CUDA kernels
+// (kernels.cu).  Plain structs of device pointers; no CUDA types leak into
+// the C ABI header.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace atlasgb {
+
+enum StorageType { ST_F32 = 0, ST_F64 = 1, ST_BF16 = 2 };
+
+// Device tables of one node stencil (see Stencil in geometry.h).  w holds
+// [nnz] scalars when scalar_w, else [nnz][2] pairs; b holds [V][2] or is null.
+// Weight precision: double for ST_F64 fields, float otherwise.
+struct DevStencil {
+  const int32_t* ptr = nullptr;
+  const int32_t* nbr = nullptr;
+  const void* w = nullptr;
+  const void* b = nullptr;
+  int32_t nnodes = 0;
+  int64_t nnz = 0;
+  int nin = 1, nout = 1;
+  bool has_b = false, scalar_w = false;
+};
+
+struct StencilLaunch {
+  const void* in0 = nullptr;
+  const void* in1 = nullptr;
+  void* out0 = nullptr;
+  void* out1 = nullptr;
+  int32_t nlev = 0;
+  int64_t ld = 0;
+  int vec = 1;
+  int threads = 256;
+  int blocks = 0;  // grid size (grid-stride loop over all items)
+};
+
+// Edge-based two-pass data on the device.
+struct DevEdges {
+  const int32_t* e2n = nullptr;   // [E][2]
+  const void* coef = nullptr;     // [E][3] (k1, k2, k3) in the weight precision
+  const int32_t* ptr = nullptr;   // [V+1]
+  const int32_t* ent = nullptr;   // [nnz] edge << 1 | negative
+  const void* node = nullptr;     // [V][3] (1/V, cos/V, pole coefficient)
+  int32_t nnodes = 0;
+  int64_t nedges = 0;
+};
+
+// Persistent batched launch: one descriptor per field.
+struct BatchDescDev {
+  const int32_t* ptr;
+  const int32_t* nbr;
+  const void* w;
+  const void* b;
+  const void* in0;
+  const void* in1;
+  void* out0;
+  void* out1;
+  int64_t ld;
+  int64_t items;      // nnodes * nvec
+  int64_t tile0;      // first tile of this descriptor
+  int32_t nnodes;
+  int32_t nlev;
+  int32_t nvec;
+  int32_t op;         // 0 gradient (1 in, 2 out), 1 divergence (2 in, 1 out, with b)
+  int32_t vec;
+  int32_t pad;
+};
+
+cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream);
+// Maximum resident blocks per SM of the stencil kernel for this configuration.
+int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int threads);
+
+cudaError_t launch_edge_flux(StorageType st, int op, const DevEdges& e, const void* in0, const void* in1,
+                             void* flux0, void* flux1, int32_t nlev, int64_t ld, int vec, int threads,
+                             int blocks, cudaStream_t stream);
+cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const void* flux0, const void* flux1,
+                               const void* vin, void* out0, void* out1, int32_t nlev, int64_t ld, int vec,
+                               int threads, int blocks, cudaStream_t stream);
+
+cudaError_t launch_batch(StorageType st, const BatchDescDev* descs, int ndesc, int64_t ntiles, int tile_items,
+                         int threads, int blocks, cudaStream_t stream);
+int batch_occupancy(StorageType st, int threads);
+
+}  // namespace atlasgb

@@ -41,3 +41,28 @@ def omesh():
         return _MESHES[N]
 
     return get
+
+
+@pytest.fixture(scope="session")
+def product():
+    """The product package with its library built in-tree (nvcc, no GPU needed)."""
+    from paper_1908_07038_gb300 import build as pbuild
+    pbuild.build()
+    from paper_1908_07038_gb300 import atlas, capi
+    return atlas, capi
+
+
+_FVMS = {}
+
+
+@pytest.fixture(scope="session")
+def pfvm(product):
+    """Factory of cached product Fvm objects keyed by N."""
+    atlas, _ = product
+
+    def get(N):
+        if N not in _FVMS:
+            _FVMS[N] = atlas.build_fvm(N, R_EARTH)
+        return _FVMS[N]
+
+    return get

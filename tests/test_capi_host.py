@@ -1,0 +1,99 @@
+"""The C ABI without a GPU: every symbol declared in include/atlas_gb.h is
+exported, handles and arguments are validated on the host with the
+documented error codes, and operator calls refuse to run without CUDA
+(there is no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "atlas_gb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(atlas_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(product):
+    _, capi = product
+    names = _declared()
+    assert len(names) >= 30
+    for n in names:
+        assert hasattr(capi.lib, n), n
+        assert n in capi.EXPORTED, n
+
+
+def test_error_codes_on_bad_arguments(product):
+    atlas, capi = product
+    E = capi.AtlasError
+    out = ctypes.c_void_p()
+    with pytest.raises(E) as ei:
+        capi.atlas_grid_octahedral(0, ctypes.byref(out))
+    assert ei.value.code == -1
+    with pytest.raises(E) as ei:
+        capi.atlas_grid_octahedral(8001, ctypes.byref(out))
+    assert ei.value.code == -1
+    with pytest.raises(E) as ei:
+        capi.atlas_grid_octahedral(4, None)
+    assert ei.value.code == -1
+    fvm = atlas.build_fvm(4)
+    h = fvm.handle
+    fake = 1 << 20  # never dereferenced: validation fails first
+    # bad dtype, ld < nlev, NULL field, misaligned field, overlapping fields
+    for args, code in [((h, fake, fake + 4096, fake + 8192, 3, 4, 7, None), -5),
+                       ((h, fake, fake + 4096, fake + 8192, 5, 4, 0, None), -1),
+                       ((h, None, fake + 4096, fake + 8192, 3, 4, 0, None), -1),
+                       ((h, fake + 2, fake + 4096, fake + 8192, 3, 4, 0, None), -4),
+                       ((h, fake, fake, fake + 8192, 3, 4, 0, None), -1)]:
+        with pytest.raises(E) as ei:
+            capi.atlas_nabla_gradient(*args)
+        assert ei.value.code == code, args
+    assert capi.atlas_nabla_workspace_bytes(h, 0, 3, 4, 0) > 0
+    assert capi.atlas_nabla_workspace_bytes(h, 3, 3, 4, 0) == 0
+    with pytest.raises(E) as ei:
+        capi.atlas_nabla_gradient_edges(h, fake, fake + 4096, fake + 8192, fake + 1 << 24, 16, 3, 4, 0, None)
+    assert ei.value.code in (-1, -4)
+    with pytest.raises(E) as ei:
+        capi.atlas_fvm_set_launch(h, 0, 3, 0, 0)
+    assert ei.value.code == -1
+    # a destroyed handle is rejected, not dereferenced
+    fvm.close()
+    with pytest.raises(E) as ei:
+        capi.atlas_nabla_gradient(h, fake, fake + 4096, fake + 8192, 3, 4, 0, None)
+    assert ei.value.code == -6
+    # a grid in use by a mesh is not destroyed
+    g = atlas.Grid(2)
+    m = atlas.Mesh(g)
+    capi.atlas_grid_destroy(g.handle)
+    capi.atlas_grid_info(g.handle, None, None, None, None, None)  # still alive
+    m.close()
+    g.close()
+
+
+def test_no_cpu_fallback_without_cuda(product):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    atlas, capi = product
+    fvm = atlas.build_fvm(4)
+    with pytest.raises(capi.AtlasError) as ei:
+        capi.atlas_nabla_gradient(fvm.handle, 1 << 20, 1 << 21, 1 << 22, 3, 4, 0, None)
+    assert ei.value.code == -3
+    with pytest.raises(capi.AtlasError) as ei:
+        capi.atlas_fvm_prepare(fvm.handle, 1, 1)
+    assert ei.value.code == -3
+    # the host-only inspection still works
+    t = fvm.stencil_table("gradient")
+    assert t["nbr"].shape[0] == 2 * fvm.mesh.nedges
+
+
+def test_info_strings(product):
+    _, capi = product
+    assert capi.atlas_version().startswith(b"atlasgb")
+    assert b"atlasgb" in capi.atlas_info()
+    capi.atlas_init()
+    capi.atlas_finalize()
