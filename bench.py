@@ -198,11 +198,11 @@ def _table_bytes(fvm, op, wbytes):
     return 4 * (V + 1) + nnz * (4 + nw * wbytes) + (2 * wbytes * V if has_b else 0)
 
 
-def _cpu_baseline(fvm_nodes, f_host, u_host, v_host, nlev, budget_s=12.0):
+def _cpu_baseline(grid, fvm_nodes, f_host, u_host, v_host, nlev, budget_s=12.0):
     """The oracle as it stands, single-threaded, on a contiguous node sample
     of the same workload (all five operators)."""
     from oracle.oracle import Mesh
-    om = Mesh(N_GRID)
+    om = Mesh(grid)
     n = 64
     while True:
         nodes = np.arange(0, n, dtype=np.int64) + fvm_nodes // 3
@@ -238,16 +238,21 @@ def run_native(args):
             dist.barrier()
 
     nlev = NLEV
-    fvm = atlas.build_fvm(N_GRID)
+    fvm = atlas.build_fvm(args.grid)
     V = fvm.nnodes
     g = fvm.grid.arrays()
     fvm.prepare(OPS, dtypes=(atlas.ATLAS_F32, atlas.ATLAS_F64, atlas.ATLAS_BF16))
     hbm, peak_kind = _peaks()
 
     # ------------------------------------------------------------ FP32 main
+    from paper_1908_07038_gb300 import tune
     ld = 140
     f, u, v = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ld, torch.float32, "cuda", 1234 + rank)
     outs = [torch.empty_like(f) for _ in range(7)]
+    tuned = tune.tune_fvm(fvm, atlas.ATLAS_F32, nlev, ld, OPS, fields=(f, u, v), reps=3)
+    for op, t in tuned.items():
+        print("tuned %s: vec=%d batch=%d threads=%d (%.3f ms)" % (op, t["vec"], t["batch"], t["threads"], t["ms"]),
+              file=sys.stderr)
     sampler = ClockSampler(local)
     sampler.start()
     total_ms, per_op = _time_ops(torch, fvm, f, u, v, outs, nlev, args.steps, args.warmup, barrier)
@@ -315,6 +320,8 @@ def run_native(args):
         for name, dt, ldx, es, wb in (("fp64", torch.float64, 138, 8, 8), ("bf16", torch.bfloat16, 144, 2, 4)):
             fx, ux, vx = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ldx, dt, "cuda", 99 + rank)
             ox = [torch.empty_like(fx) for _ in range(7)]
+            code = atlas.ATLAS_F64 if name == "fp64" else atlas.ATLAS_BF16
+            tune.tune_fvm(fvm, code, nlev, ldx, OPS, fields=(fx, ux, vx), reps=2)
             k = max(3, args.steps // 4)
             tms, pops = _time_ops(torch, fvm, fx, ux, vx, ox, nlev, k, 3, barrier)
             entry = {"ms_per_step": round(tms / k, 4), "node_levels_per_s": node_levels_step / (tms / k * 1e-3),
@@ -329,9 +336,32 @@ def run_native(args):
     else:
         f_host = None
 
+    # ------------------------------------- 24 mixed fields, one launch each vs batched
+    batched = None
+    if not args.no_batch:
+        from paper_1908_07038_gb300 import batch as B
+        fvms = {N: atlas.build_fvm(N) for N in B.GRIDS}
+        jobs = B.make_jobs(fvms, 24, seed=3)
+        for N, fv in fvms.items():
+            fv.prepare(("gradient", "divergence"), dtypes=(atlas.ATLAS_F32,))
+            tune.tune_fvm(fv, atlas.ATLAS_F32, 137, 140, ("gradient", "divergence"), reps=2)
+        bt, bt_cfg, _ = tune.tune_batch(lambda c: B.Batch(jobs, tune=c), reps=5)
+        bt.capture()
+        nl = bt.node_levels
+        ms_graph = tune.time_call(bt.replay, reps=20, warmup=3)
+        ms_plain = tune.time_call(lambda: B.plain(jobs), reps=20, warmup=3)
+        batched = {"fields": len(jobs), "node_levels": nl, "graph_replay_ms": round(ms_graph, 4),
+                   "plain_launches_ms": round(ms_plain, 4),
+                   "graph_node_levels_per_s": nl / (ms_graph * 1e-3),
+                   "plain_node_levels_per_s": nl / (ms_plain * 1e-3), "tune": bt_cfg,
+                   "grids": sorted({j["N"] for j in jobs}), "levels": sorted({j["nlev"] for j in jobs})}
+        bt.close()
+        del jobs, fvms
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and f_host is not None:
-        cpu = _cpu_baseline(V, f_host, u_host, v_host, nlev)
+        cpu = _cpu_baseline(args.grid, V, f_host, u_host, v_host, nlev)
 
     if ws > 1:
         dist.barrier()
@@ -343,13 +373,15 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": "node-levels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "O1280 octahedral grid (%d nodes, %d edges) x %d levels, field[node][ld=%d] FP32, "
+        "config": {"workload": "O%d octahedral grid (%d nodes, %d edges) x %d levels, field[node][ld=%d] FP32, "
                                "FP64-built geometry; step = gradient + divergence + Laplacian + gradient adjoint "
-                               "+ divergence adjoint" % (V, fvm.mesh.nedges, nlev, ld),
+                               "+ divergence adjoint" % (args.grid, V, fvm.mesh.nedges, nlev, ld),
                    "l2": "inputs larger than L2 (3.7 GB per field), no flush", "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline, "per_op": {k: {"ms": v_["ms"], "node_levels_per_s": v_["node_levels_per_s"],
                                              "frac_hbm": round(v_["frac"], 4)} for k, v_ in per.items()},
-        "side_by_side": side, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        "side_by_side": side, "batched": batched, "tuned": {k: {kk: t[kk] for kk in ("vec", "batch", "threads")}
+                                                            for k, t in tuned.items()},
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": 5 * args.steps,
     }
     print(json.dumps(line))
@@ -425,6 +457,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--grid", type=int, default=N_GRID,
+                    help="octahedral number of a smaller case (profiling only; the metric is O1280)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -147,10 +147,11 @@ int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const doub
 /* for the dtypes in dtype_mask (bits 1<<dtype).  Synchronous.             */
 int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 /* Launch shape of the node-stencil kernels for one operator: levels per   */
-/* thread (vec: 1, 2, 4 or 8; 0 = default for the dtype), threads per     */
-/* block (64..1024, multiple of 32) and blocks per SM (1..32).  Any zero   */
-/* field keeps the current value.                                          */
-int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int threads, int blocks_per_sm);
+/* thread (vec: 1, 2, 4 or 8; 0 = default for the dtype), CSR entries per */
+/* load batch (batch: 3 or 6), threads per block (64..512, multiple of    */
+/* 32) and blocks per SM (1..32).  Any zero field keeps the current value; */
+/* results are bitwise identical for every shape.                          */
+int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int batch, int threads, int blocks_per_sm);
 /* Inspection: copy out the FP64 host table of one operator's node stencil */
 /*   out_c(i) = sum_{q in [ptr[i], ptr[i+1])} sum_m W_cm(q) (x_m(nbr[q]) - x_m(i))  */
 /*              + sum_m B_cm(i) x_m(i)                                     */
@@ -222,8 +223,9 @@ typedef struct {
   int64_t ld;
 } atlas_batch_desc;
 /* Work split: each descriptor is cut into tiles of tile_items (node,      */
-/* level-vector) items; vec levels per thread (1, 2 or 4; ld must be a     */
-/* multiple of vec for vec > 1), threads per block, blocks per SM of the   */
+/* level-vector) items; vec levels per thread (1, 2 or 4; the batch uses  */
+/* the widest vec that every field's ld and pointers allow, capped by     */
+/* this value), threads per block (64..512), blocks per SM of the          */
 /* persistent grid.  Zero fields take the defaults.                        */
 typedef struct {
   int vec;

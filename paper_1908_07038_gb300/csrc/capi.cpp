@@ -109,6 +109,7 @@ struct EdgeTables {
 };
 struct LaunchCfg {
   int vec = 0;  // 0 = widest the dtype and alignment allow
+  int batch = 6;
   int threads = 256;
   int blocks_per_sm = 0;  // 0 = occupancy limit
 };
@@ -278,9 +279,9 @@ int check_no_overlap(const void* const* ins, int nin, void* const* outs, int nou
   return ATLAS_OK;
 }
 
-int grid_blocks(atlas_fvm_s* f, StorageType st, const atlasgb::DevStencil& s, int vec, int threads, int bps_req,
-                int64_t items) {
-  int bps = atlasgb::stencil_occupancy(st, s, vec, threads);
+int grid_blocks(atlas_fvm_s* f, StorageType st, const atlasgb::DevStencil& s, int vec, int batch, int threads,
+                int bps_req, int64_t items) {
+  int bps = atlasgb::stencil_occupancy(st, s, vec, batch, threads);
   if (bps_req > 0) bps = std::min(bps, bps_req);
   int64_t blocks = static_cast<int64_t>(f->num_sms) * bps;
   const int64_t need = (items + threads - 1) / threads;
@@ -332,8 +333,9 @@ int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void
   const int64_t items = V * nvec;
   if (items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
   l.threads = c.threads;
+  l.batch = c.batch;
   const StorageType st = storage_of(dtype);
-  l.blocks = grid_blocks(f, st, f->st[op][prec].dev, l.vec, l.threads, c.blocks_per_sm, items);
+  l.blocks = grid_blocks(f, st, f->st[op][prec].dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
   cudaError_t e = atlasgb::launch_stencil(st, f->st[op][prec].dev, l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
   return ok();
@@ -598,16 +600,18 @@ int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
   return ok();
 }
 
-int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int threads, int blocks_per_sm) {
+int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int batch, int threads, int blocks_per_sm) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
   if (vec != 0 && vec != 1 && vec != 2 && vec != 4 && vec != 8) return fail(ATLAS_EINVAL, "vec must be 1, 2, 4 or 8");
-  if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32 != 0))
-    return fail(ATLAS_EINVAL, "threads must be a multiple of 32 in [64, 1024]");
+  if (batch != 0 && batch != 3 && batch != 6) return fail(ATLAS_EINVAL, "batch must be 3 or 6");
+  if (threads != 0 && (threads < 64 || threads > 512 || threads % 32 != 0))
+    return fail(ATLAS_EINVAL, "threads must be a multiple of 32 in [64, 512]");
   if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(ATLAS_EINVAL, "blocks_per_sm must be in [0, 32]");
   std::lock_guard<std::mutex> lk(f->mu);
   if (vec) f->cfg[op].vec = vec;
+  if (batch) f->cfg[op].batch = batch;
   if (threads) f->cfg[op].threads = threads;
   if (blocks_per_sm) f->cfg[op].blocks_per_sm = blocks_per_sm;
   return ok();
@@ -779,7 +783,7 @@ struct atlas_batch_s {
   atlasgb::BatchDescDev* d_desc = nullptr;
   int ndesc = 0;
   int64_t ntiles = 0, node_levels = 0;
-  int tile_items = 0, threads = 0, blocks = 0, device = -1;
+  int tile_items = 0, threads = 0, blocks = 0, device = -1, vec = 1;
   StorageType st = atlasgb::ST_F32;
 };
 
@@ -803,6 +807,15 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   int64_t tiles = 0, nl = 0;
   int device = -1;
   std::vector<atlas_fvm_s*> fv;
+  // one levels-per-thread width for the whole batch: the widest every field allows
+  int vec = want_vec;
+  for (int k = 0; k < n; ++k) {
+    const atlas_batch_desc& d = descs[k];
+    const bool grad = d.op == ATLAS_OP_GRADIENT;
+    const void* used[3] = {d.in0, grad ? d.out0 : d.in1, grad ? d.out1 : d.out0};
+    vec = std::min(vec, pick_vec(dtype, d.ld, used, 3, want_vec));
+  }
+  if (threads > 512) return fail(ATLAS_EINVAL, "batch threads must be <= 512");
   for (int k = 0; k < n; ++k) {
     const atlas_batch_desc& d = descs[k];
     atlas_fvm_s* f = get_fvm(d.fvm);
@@ -822,7 +835,6 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
       if (rc) return rc;
     }
     const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][prec].dev;
-    const int vec = pick_vec(dtype, d.ld, used, 3, want_vec);
     atlasgb::BatchDescDev& o = hd[k];
     o.ptr = s.ptr;
     o.nbr = s.nbr;
@@ -868,7 +880,8 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   b->threads = threads;
   b->st = storage_of(dtype);
   b->device = device;
-  int bps = atlasgb::batch_occupancy(b->st, threads);
+  b->vec = vec;
+  int bps = atlasgb::batch_occupancy(b->st, vec, threads, n);
   if (t.blocks_per_sm > 0) bps = std::min(bps, t.blocks_per_sm);
   const int64_t blocks = std::min<int64_t>(static_cast<int64_t>(fv[0]->num_sms) * bps, std::max<int64_t>(tiles, 1));
   b->blocks = static_cast<int>(blocks);
@@ -884,8 +897,8 @@ int atlas_batch_launch(atlas_batch_t h, void* stream) {
   if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device)
     return fail(ATLAS_ESTATE, "batch lives on device %d, current device is %d", b->device, cur);
   if (b->ntiles == 0) return ok();
-  cudaError_t e = atlasgb::launch_batch(b->st, b->d_desc, b->ndesc, b->ntiles, b->tile_items, b->threads, b->blocks,
-                                        static_cast<cudaStream_t>(stream));
+  cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->d_desc, b->ndesc, b->ntiles, b->tile_items, b->threads,
+                                        b->blocks, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return ok();
 }

@@ -91,13 +91,20 @@ template <> struct Pair<double> {
 
 // ------------------------------------------------------- node stencil item
 // out_c(i) = sum_q sum_m W_cm(q) (x_m(nbr q) - x_m(i)) + sum_m B_cm(i) x_m(i)
-template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+//
+// The CSR row is consumed BATCH entries at a time: first the BATCH neighbour
+// ids and weights, then all BATCH neighbour level-vectors are requested
+// before any is used, so one item keeps BATCH independent loads in flight
+// instead of a chain of index -> value round trips.  Accumulation stays in
+// CSR order, so the result does not depend on BATCH or VEC.
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                                              const A* __restrict__ w, const A* __restrict__ b,
                                              const S* __restrict__ in0, const S* __restrict__ in1,
                                              S* __restrict__ out0, S* __restrict__ out1, int64_t ld, int32_t nlev,
                                              int32_t i, int32_t lev0) {
   const int64_t oi = static_cast<int64_t>(i) * ld + lev0;
+  const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
   A xi0[VEC], xi1[VEC], acc0[VEC], acc1[VEC];
   vload<S, A, VEC>(in0 + oi, xi0);
   if constexpr (NIN == 2) vload<S, A, VEC>(in1 + oi, xi1);
@@ -106,32 +113,47 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
     acc0[k] = A(0);
     acc1[k] = A(0);
   }
-  const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
-  for (int32_t q = q0; q < q1; ++q) {
-    const int32_t j = __ldg(nbr + q);
-    A w0, w1 = A(0);
-    if constexpr (SCALAR_W) {
-      w0 = __ldg(w + q);
-    } else {
-      Pair<A>::load(w, q, w0, w1);
-    }
-    const int64_t oj = static_cast<int64_t>(j) * ld + lev0;
-    A xj0[VEC];
-    vload<S, A, VEC>(in0 + oj, xj0);
-    if constexpr (NIN == 1) {
+  for (int32_t qb = q0; qb < q1; qb += BATCH) {
+    const int cnt = (q1 - qb < BATCH) ? (q1 - qb) : BATCH;
+    int32_t jj[BATCH];
+    A wa[BATCH], wb[BATCH];
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        const A d = xj0[k] - xi0[k];
-        acc0[k] = fma(w0, d, acc0[k]);
-        if constexpr (NOUT == 2) acc1[k] = fma(w1, d, acc1[k]);
+    for (int t = 0; t < BATCH; ++t) {
+      jj[t] = i;
+      wa[t] = A(0);
+      wb[t] = A(0);
+      if (t < cnt) {
+        jj[t] = __ldg(nbr + qb + t);
+        if constexpr (SCALAR_W) {
+          wa[t] = __ldg(w + qb + t);
+        } else {
+          Pair<A>::load(w, qb + t, wa[t], wb[t]);
+        }
       }
-    } else {
-      A xj1[VEC];
-      vload<S, A, VEC>(in1 + oj, xj1);
+    }
+    A xa[BATCH][VEC], xb[NIN == 2 ? BATCH : 1][VEC];
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        acc0[k] = fma(w0, xj0[k] - xi0[k], acc0[k]);
-        acc0[k] = fma(w1, xj1[k] - xi1[k], acc0[k]);
+    for (int t = 0; t < BATCH; ++t) {
+      if (t < cnt) {
+        const int64_t oj = static_cast<int64_t>(jj[t]) * ld + lev0;
+        vload<S, A, VEC>(in0 + oj, xa[t]);
+        if constexpr (NIN == 2) vload<S, A, VEC>(in1 + oj, xb[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < BATCH; ++t) {
+      if (t < cnt) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+          if constexpr (NIN == 1) {
+            const A d = xa[t][k] - xi0[k];
+            acc0[k] = fma(wa[t], d, acc0[k]);
+            if constexpr (NOUT == 2) acc1[k] = fma(wb[t], d, acc1[k]);
+          } else {
+            acc0[k] = fma(wa[t], xa[t][k] - xi0[k], acc0[k]);
+            acc0[k] = fma(wb[t], xb[t][k] - xi1[k], acc0[k]);
+          }
+        }
       }
     }
   }
@@ -154,8 +176,8 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
   if constexpr (NOUT == 2) vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
 }
 
-template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
-__global__ void __launch_bounds__(1024) stencil_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
+__global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                                                        const A* __restrict__ w, const A* __restrict__ b,
                                                        const S* __restrict__ in0, const S* __restrict__ in1,
                                                        S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
@@ -165,8 +187,8 @@ __global__ void __launch_bounds__(1024) stencil_kernel(const int32_t* __restrict
   for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
     const uint32_t i = item / nvec;
     const uint32_t v = item - i * nvec;
-    stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
-                                                        static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
+    stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+                                                               static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
   }
 }
 
@@ -174,7 +196,7 @@ __global__ void __launch_bounds__(1024) stencil_kernel(const int32_t* __restrict
 // OP 0 (gradient): flux0 = k1 (x_b - x_a), flux1 = k2 (x_b - x_a)
 // OP 1 (divergence): flux0 = k1 (u_b - u_a) + k2 (v_b - v_a) + k3 v_a
 template <typename S, typename A, int OP, int VEC>
-__global__ void __launch_bounds__(1024) edge_flux_kernel(const int32_t* __restrict__ e2n, const A* __restrict__ coef,
+__global__ void __launch_bounds__(512) edge_flux_kernel(const int32_t* __restrict__ e2n, const A* __restrict__ coef,
                                                          const S* __restrict__ in0, const S* __restrict__ in1,
                                                          A* __restrict__ flux0, A* __restrict__ flux1,
                                                          uint32_t nedges, int32_t nlev, int64_t ld, uint32_t nvec) {
@@ -221,7 +243,7 @@ __global__ void __launch_bounds__(1024) edge_flux_kernel(const int32_t* __restri
 // OP 0: out0 = (1/V) sum +-flux0, out1 = (cos/V) sum +-flux1
 // OP 1: out0 = (1/V) sum flux0 + pole_coef * v_i
 template <typename S, typename A, int OP, int VEC>
-__global__ void __launch_bounds__(1024) node_gather_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+__global__ void __launch_bounds__(512) node_gather_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
                                                            const A* __restrict__ node, const A* __restrict__ flux0,
                                                            const A* __restrict__ flux1, const S* __restrict__ vin,
                                                            S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
@@ -285,31 +307,14 @@ __global__ void __launch_bounds__(1024) node_gather_kernel(const int32_t* __rest
 }
 
 // ------------------------------------------------------- persistent batch
+// One launch walks a static list of tiles; tile t belongs to the descriptor d
+// with tile0[d] <= t < tile0[d+1] (binary search in shared memory) and covers
+// tile_items consecutive (node, level-vector) items of that field.  All fields
+// of a batch share one VEC; operators are gradient (1 in, 2 out) and
+// divergence (2 in, 1 out, B term).
 template <typename S, typename A, int VEC>
-__device__ __forceinline__ void batch_items(const BatchDescDev& D, int64_t it0, int64_t it1) {
-  const A* w = static_cast<const A*>(D.w);
-  const A* b = static_cast<const A*>(D.b);
-  const S* in0 = static_cast<const S*>(D.in0);
-  const S* in1 = static_cast<const S*>(D.in1);
-  S* out0 = static_cast<S*>(D.out0);
-  S* out1 = static_cast<S*>(D.out1);
-  const uint32_t nvec = static_cast<uint32_t>(D.nvec);
-  for (int64_t it = it0 + threadIdx.x; it < it1; it += blockDim.x) {
-    const uint32_t u = static_cast<uint32_t>(it);
-    const uint32_t i = u / nvec;
-    const int32_t lev0 = static_cast<int32_t>((u - i * nvec) * VEC);
-    if (D.op == 0)
-      stencil_item<S, A, 1, 2, VEC, false, false>(D.ptr, D.nbr, w, b, in0, in1, out0, out1, D.ld, D.nlev,
-                                                  static_cast<int32_t>(i), lev0);
-    else
-      stencil_item<S, A, 2, 1, VEC, true, false>(D.ptr, D.nbr, w, b, in0, in1, out0, out1, D.ld, D.nlev,
-                                                 static_cast<int32_t>(i), lev0);
-  }
-}
-
-template <typename S, typename A>
-__global__ void __launch_bounds__(1024) batch_kernel(const BatchDescDev* __restrict__ descs, int ndesc, int64_t ntiles,
-                                                     int tile_items) {
+__global__ void __launch_bounds__(512) batch_kernel(const BatchDescDev* __restrict__ descs, int ndesc, int64_t ntiles,
+                                                    int tile_items) {
   extern __shared__ int64_t s_tile0[];
   for (int d = threadIdx.x; d < ndesc; d += blockDim.x) s_tile0[d] = descs[d].tile0;
   __syncthreads();
@@ -319,85 +324,107 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchDescDev* __restr
       const int mid = (lo + hi + 1) >> 1;
       if (s_tile0[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const BatchDescDev D = descs[lo];
-    const int64_t it0 = (t - D.tile0) * tile_items;
-    const int64_t it1 = (it0 + tile_items < D.items) ? it0 + tile_items : D.items;
-    if (D.vec == 4) {
-      if constexpr (sizeof(S) * 4 <= 16) batch_items<S, A, 4>(D, it0, it1);
-    } else if (D.vec == 2) {
-      batch_items<S, A, 2>(D, it0, it1);
-    } else {
-      batch_items<S, A, 1>(D, it0, it1);
+    const BatchDescDev* D = descs + lo;
+    const int32_t* ptr = D->ptr;
+    const int32_t* nbr = D->nbr;
+    const A* w = static_cast<const A*>(D->w);
+    const A* b = static_cast<const A*>(D->b);
+    const S* in0 = static_cast<const S*>(D->in0);
+    const S* in1 = static_cast<const S*>(D->in1);
+    S* out0 = static_cast<S*>(D->out0);
+    S* out1 = static_cast<S*>(D->out1);
+    const int64_t ld = D->ld;
+    const int32_t nlev = D->nlev;
+    const uint32_t nvec = static_cast<uint32_t>(D->nvec);
+    const int op = D->op;
+    const int64_t it0 = (t - D->tile0) * tile_items;
+    const int64_t it1 = (it0 + tile_items < D->items) ? it0 + tile_items : D->items;
+    for (int64_t it = it0 + threadIdx.x; it < it1; it += blockDim.x) {
+      const uint32_t u = static_cast<uint32_t>(it);
+      const uint32_t i = u / nvec;
+      const int32_t lev0 = static_cast<int32_t>((u - i * nvec) * VEC);
+      if (op == 0)
+        stencil_item<S, A, 1, 2, VEC, false, false, 3>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+                                                       static_cast<int32_t>(i), lev0);
+      else
+        stencil_item<S, A, 2, 1, VEC, true, false, 3>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+                                                      static_cast<int32_t>(i), lev0);
     }
   }
 }
 
 // ---------------------------------------------------------------- dispatch
-template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
   const uint32_t nvec = static_cast<uint32_t>((l.nlev + VEC - 1) / VEC);
-  stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W><<<l.blocks, l.threads, 0, stream>>>(
+  stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH><<<l.blocks, l.threads, 0, stream>>>(
       s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
       static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec);
   return cudaGetLastError();
 }
 
-template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 const void* stencil_fn() {
-  return reinterpret_cast<const void*>(&stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>);
+  return reinterpret_cast<const void*>(&stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH>);
 }
 
 // Visit the kernel instantiation of (storage, shape, vec); F is called with a
 // tag carrying the template arguments.
-template <typename S, typename A, int VEC, typename F>
+template <typename S, typename A, int VEC, int BATCH, typename F>
 auto with_shape(const DevStencil& s, F&& f) {
-  if (s.scalar_w) return f.template operator()<S, A, 1, 1, VEC, false, true>();
-  if (s.nin == 1 && s.nout == 2 && !s.has_b) return f.template operator()<S, A, 1, 2, VEC, false, false>();
-  if (s.nin == 1 && s.nout == 2) return f.template operator()<S, A, 1, 2, VEC, true, false>();
-  return f.template operator()<S, A, 2, 1, VEC, true, false>();
+  if (s.scalar_w) return f.template operator()<S, A, 1, 1, VEC, false, true, BATCH>();
+  if (s.nin == 1 && s.nout == 2 && !s.has_b) return f.template operator()<S, A, 1, 2, VEC, false, false, BATCH>();
+  if (s.nin == 1 && s.nout == 2) return f.template operator()<S, A, 1, 2, VEC, true, false, BATCH>();
+  return f.template operator()<S, A, 2, 1, VEC, true, false, BATCH>();
+}
+
+template <typename S, typename A, int VEC, typename F>
+auto with_batch(const DevStencil& s, int batch, F&& f) {
+  if (batch == 3) return with_shape<S, A, VEC, 3>(s, f);
+  return with_shape<S, A, VEC, 6>(s, f);
 }
 
 template <typename S, typename A, typename F>
-auto with_vec(const DevStencil& s, int vec, F&& f) {
+auto with_vec(const DevStencil& s, int vec, int batch, F&& f) {
   constexpr int maxvec = 16 / static_cast<int>(sizeof(S));
-  if (vec >= 8 && maxvec >= 8) return with_shape<S, A, (maxvec >= 8 ? 8 : 1)>(s, f);
-  if (vec >= 4 && maxvec >= 4) return with_shape<S, A, (maxvec >= 4 ? 4 : 1)>(s, f);
-  if (vec >= 2) return with_shape<S, A, 2>(s, f);
-  return with_shape<S, A, 1>(s, f);
+  if (vec >= 8 && maxvec >= 8) return with_batch<S, A, (maxvec >= 8 ? 8 : 1)>(s, batch, f);
+  if (vec >= 4 && maxvec >= 4) return with_batch<S, A, (maxvec >= 4 ? 4 : 1)>(s, batch, f);
+  if (vec >= 2) return with_batch<S, A, 2>(s, batch, f);
+  return with_batch<S, A, 1>(s, batch, f);
 }
 
 template <typename F>
-auto with_storage(StorageType st, const DevStencil& s, int vec, F&& f) {
-  if (st == ST_F64) return with_vec<double, double>(s, vec, f);
-  if (st == ST_BF16) return with_vec<uint16_t, float>(s, vec, f);
-  return with_vec<float, float>(s, vec, f);
+auto with_storage(StorageType st, const DevStencil& s, int vec, int batch, F&& f) {
+  if (st == ST_F64) return with_vec<double, double>(s, vec, batch, f);
+  if (st == ST_BF16) return with_vec<uint16_t, float>(s, vec, batch, f);
+  return with_vec<float, float>(s, vec, batch, f);
 }
 
 struct RunStencil {
   const DevStencil& s;
   const StencilLaunch& l;
   cudaStream_t stream;
-  template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+  template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
   cudaError_t operator()() const {
-    return run_stencil<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>(s, l, stream);
+    return run_stencil<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH>(s, l, stream);
   }
 };
 
 struct StencilFn {
-  template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W>
+  template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
   const void* operator()() const {
-    return stencil_fn<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W>();
+    return stencil_fn<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH>();
   }
 };
 
 }  // namespace
 
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
-  return with_storage(st, s, l.vec, RunStencil{s, l, stream});
+  return with_storage(st, s, l.vec, l.batch, RunStencil{s, l, stream});
 }
 
-int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int threads) {
-  const void* fn = with_storage(st, s, vec, StencilFn{});
+int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int batch, int threads) {
+  const void* fn = with_storage(st, s, vec, batch, StencilFn{});
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess) return 1;
   return blocks > 0 ? blocks : 1;
@@ -466,23 +493,30 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch(StorageType st, const BatchDescDev* descs, int ndesc, int64_t ntiles, int tile_items,
-                         int threads, int blocks, cudaStream_t stream) {
-  const size_t smem = sizeof(int64_t) * static_cast<size_t>(ndesc);
+namespace {
+const void* batch_fn(StorageType st, int vec) {
   if (st == ST_F64)
-    batch_kernel<double, double><<<blocks, threads, smem, stream>>>(descs, ndesc, ntiles, tile_items);
-  else if (st == ST_F32)
-    batch_kernel<float, float><<<blocks, threads, smem, stream>>>(descs, ndesc, ntiles, tile_items);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+    return vec >= 2 ? reinterpret_cast<const void*>(&batch_kernel<double, double, 2>)
+                    : reinterpret_cast<const void*>(&batch_kernel<double, double, 1>);
+  if (vec >= 4) return reinterpret_cast<const void*>(&batch_kernel<float, float, 4>);
+  if (vec >= 2) return reinterpret_cast<const void*>(&batch_kernel<float, float, 2>);
+  return reinterpret_cast<const void*>(&batch_kernel<float, float, 1>);
+}
+}  // namespace
+
+cudaError_t launch_batch(StorageType st, int vec, const BatchDescDev* descs, int ndesc, int64_t ntiles,
+                         int tile_items, int threads, int blocks, cudaStream_t stream) {
+  if (st != ST_F64 && st != ST_F32) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(int64_t) * static_cast<size_t>(ndesc);
+  void* args[] = {const_cast<BatchDescDev**>(&descs), &ndesc, &ntiles, &tile_items};
+  return cudaLaunchKernel(batch_fn(st, vec), dim3(blocks), dim3(threads), args, smem, stream);
 }
 
-int batch_occupancy(StorageType st, int threads) {
+int batch_occupancy(StorageType st, int vec, int threads, int ndesc) {
   int blocks = 0;
-  const void* fn = (st == ST_F64) ? reinterpret_cast<const void*>(&batch_kernel<double, double>)
-                                  : reinterpret_cast<const void*>(&batch_kernel<float, float>);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_fn(st, vec), threads,
+                                                    sizeof(int64_t) * static_cast<size_t>(ndesc)) != cudaSuccess)
+    return 1;
   return blocks > 0 ? blocks : 1;
 }
 

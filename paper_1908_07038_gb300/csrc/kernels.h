@@ -34,6 +34,7 @@ struct StencilLaunch {
   int32_t nlev = 0;
   int64_t ld = 0;
   int vec = 1;
+  int batch = 6;   // CSR entries whose neighbour values are requested together (3 or 6)
   int threads = 256;
   int blocks = 0;  // grid size (grid-stride loop over all items)
 };
@@ -72,7 +73,7 @@ struct BatchDescDev {
 
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream);
 // Maximum resident blocks per SM of the stencil kernel for this configuration.
-int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int threads);
+int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int batch, int threads);
 
 cudaError_t launch_edge_flux(StorageType st, int op, const DevEdges& e, const void* in0, const void* in1,
                              void* flux0, void* flux1, int32_t nlev, int64_t ld, int vec, int threads,
@@ -81,8 +82,8 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
                                const void* vin, void* out0, void* out1, int32_t nlev, int64_t ld, int vec,
                                int threads, int blocks, cudaStream_t stream);
 
-cudaError_t launch_batch(StorageType st, const BatchDescDev* descs, int ndesc, int64_t ntiles, int tile_items,
-                         int threads, int blocks, cudaStream_t stream);
-int batch_occupancy(StorageType st, int threads);
+cudaError_t launch_batch(StorageType st, int vec, const BatchDescDev* descs, int ndesc, int64_t ntiles,
+                         int tile_items, int threads, int blocks, cudaStream_t stream);
+int batch_occupancy(StorageType st, int vec, int threads, int ndesc);
 
 }  // namespace atlasgb

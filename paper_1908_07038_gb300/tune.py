@@ -1,0 +1,147 @@
+"""Autotuner of the launch shapes of the nabla kernels.
+
+For every operator the node-stencil kernel has four free parameters that do
+not change its result (bitwise): levels per thread (``vec``), CSR entries per
+load batch (``batch``), threads per block and blocks per SM.  ``tune_fvm``
+times each candidate with CUDA events on the real field sizes and installs
+the fastest with ``atlas_fvm_set_launch``; ``tune_batch`` does the same for
+the tile size and block shape of a persistent batched launch.  Results are
+cached in the JSON file named by ``ATLASGB_TUNE_CACHE`` (if set), keyed by
+device name, grid, dtype, level count and leading dimension.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+from . import atlas
+from .capi import ATLAS_BF16, ATLAS_F32, ATLAS_F64
+
+CANDIDATES = {
+    ATLAS_F32: dict(vec=(4, 2), batch=(6, 3), threads=(128, 256, 512), bps=(0,)),
+    ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,)),
+    ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,)),
+}
+_TORCH_DT = None
+
+
+def _torch_dtype(code):
+    import torch
+    return {ATLAS_F32: torch.float32, ATLAS_F64: torch.float64, ATLAS_BF16: torch.bfloat16}[code]
+
+
+def _cache_path():
+    return os.environ.get("ATLASGB_TUNE_CACHE")
+
+
+def _load_cache():
+    p = _cache_path()
+    if p and os.path.exists(p):
+        try:
+            with open(p) as fh:
+                return json.load(fh)
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _store_cache(c):
+    p = _cache_path()
+    if not p:
+        return
+    tmp = p + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as fh:
+        json.dump(c, fh, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def _call(fvm, op, ins, outs, nlev):
+    if op == "gradient":
+        fvm.gradient(ins[0], nlev, out=(outs[0], outs[1]))
+    elif op == "divergence":
+        fvm.divergence(ins[0], ins[1], nlev, out=outs[0])
+    elif op == "laplacian":
+        fvm.laplacian(ins[0], nlev, out=outs[0])
+    elif op == "gradient_adjoint":
+        fvm.gradient_adjoint(ins[0], ins[1], nlev, out=outs[0])
+    else:
+        fvm.divergence_adjoint(ins[0], nlev, out=(outs[0], outs[1]))
+
+
+def time_call(fn, reps=5, warmup=2):
+    """Average milliseconds of fn() over reps launches (CUDA events, current stream)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn()
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fields=None, reps=5, verbose=False):
+    """Pick and install the fastest launch shape of every operator in ops.
+    fields: optional (f, u, v) tensors [nnodes, ld] to time on (else zeros)."""
+    import torch
+    dev_name = torch.cuda.get_device_name()
+    es = {ATLAS_F32: 4, ATLAS_F64: 8, ATLAS_BF16: 2}[dtype]
+    if ld is None:
+        q = 16 // es
+        ld = (nlev + q - 1) // q * q
+    key_base = "%s|O%d|dt%d|L%d|ld%d" % (dev_name, fvm.grid.N, dtype, nlev, ld)
+    cache = _load_cache()
+    if fields is None:
+        t = _torch_dtype(dtype)
+        fields = [torch.randn((fvm.nnodes, ld), device="cuda").to(t) for _ in range(3)]
+    outs = [torch.empty_like(fields[0]) for _ in range(2)]
+    best = {}
+    for op in ops:
+        key = key_base + "|" + op
+        if key in cache:
+            c = cache[key]
+            fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"])
+            best[op] = c
+            continue
+        ins = (fields[1], fields[2]) if op in ("divergence", "gradient_adjoint") else (fields[0],)
+        cand = CANDIDATES[dtype]
+        results = []
+        for vec, batch, threads, bps in itertools.product(cand["vec"], cand["batch"], cand["threads"], cand["bps"]):
+            fvm.set_launch(op, vec, batch, threads, bps)
+            ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
+            results.append((ms, vec, batch, threads, bps))
+            if verbose:
+                print("tune %-18s vec=%d batch=%d threads=%d bps=%d: %.4f ms" % (op, vec, batch, threads, bps, ms))
+        ms, vec, batch, threads, bps = min(results)
+        fvm.set_launch(op, vec, batch, threads, bps)
+        best[op] = dict(vec=vec, batch=batch, threads=threads, bps=bps, ms=ms,
+                        sweep=[dict(ms=r[0], vec=r[1], batch=r[2], threads=r[3], bps=r[4]) for r in results])
+        cache[key] = {k: best[op][k] for k in ("vec", "batch", "threads", "bps", "ms")}
+    _store_cache(cache)
+    return best
+
+
+def tune_batch(make, candidates=None, reps=5, verbose=False):
+    """make(tune_dict) -> Batch; returns (best Batch, best tune, sweep)."""
+    if candidates is None:
+        candidates = [dict(vec=0, tile_items=t, threads=th, blocks_per_sm=0)
+                      for t in (1024, 2048, 4096, 8192, 16384) for th in (256, 512)]
+    sweep = []
+    best = None
+    for c in candidates:
+        b = make(c)
+        ms = time_call(b.launch, reps=reps)
+        sweep.append(dict(ms=ms, **c))
+        if verbose:
+            print("tune batch %r: %.4f ms" % (c, ms))
+        if best is None or ms < best[0]:
+            if best is not None:
+                best[1].close()
+            best = (ms, b, c)
+        else:
+            b.close()
+    return best[1], best[2], sweep

@@ -191,9 +191,9 @@ def test_deterministic_and_launch_shape_independent(torch, product):
     f = _dev(torch, rng.standard_normal((fvm.nnodes, 40)).astype(np.float32))
     ref = [t.clone() for t in fvm.gradient(f)]
     lref = fvm.laplacian(f).clone()
-    for vec, threads, bps in ((1, 128, 2), (2, 512, 1), (4, 256, 0), (4, 64, 3)):
-        fvm.set_launch("gradient", vec, threads, bps)
-        fvm.set_launch("laplacian", vec, threads, bps)
+    for vec, batch, threads, bps in ((1, 3, 128, 2), (2, 6, 512, 1), (4, 3, 256, 0), (4, 6, 64, 3)):
+        fvm.set_launch("gradient", vec, batch, threads, bps)
+        fvm.set_launch("laplacian", vec, batch, threads, bps)
         gx, gy = fvm.gradient(f)
         lap = fvm.laplacian(f)
         torch.cuda.synchronize()
