@@ -249,7 +249,7 @@ def run_native(args):
     ld = 140
     f, u, v = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ld, torch.float32, "cuda", 1234 + rank)
     outs = [torch.empty_like(f) for _ in range(7)]
-    tuned = tune.tune_fvm(fvm, atlas.ATLAS_F32, nlev, ld, OPS, fields=(f, u, v), reps=3)
+    tuned = {} if args.no_tune else tune.tune_fvm(fvm, atlas.ATLAS_F32, nlev, ld, OPS, fields=(f, u, v), reps=3)
     for op, t in tuned.items():
         print("tuned %s: vec=%d batch=%d threads=%d (%.3f ms)" % (op, t["vec"], t["batch"], t["threads"], t["ms"]),
               file=sys.stderr)
@@ -321,7 +321,8 @@ def run_native(args):
             fx, ux, vx = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ldx, dt, "cuda", 99 + rank)
             ox = [torch.empty_like(fx) for _ in range(7)]
             code = atlas.ATLAS_F64 if name == "fp64" else atlas.ATLAS_BF16
-            tune.tune_fvm(fvm, code, nlev, ldx, OPS, fields=(fx, ux, vx), reps=2)
+            if not args.no_tune:
+                tune.tune_fvm(fvm, code, nlev, ldx, OPS, fields=(fx, ux, vx), reps=2)
             k = max(3, args.steps // 4)
             tms, pops = _time_ops(torch, fvm, fx, ux, vx, ox, nlev, k, 3, barrier)
             entry = {"ms_per_step": round(tms / k, 4), "node_levels_per_s": node_levels_step / (tms / k * 1e-3),
@@ -458,6 +459,7 @@ def main():
     ap.add_argument("--no-side", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (profiling runs)")
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="octahedral number of a smaller case (profiling only; the metric is O1280)")
     args = ap.parse_args()

@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, cuda), _sources()))
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [os.path.join(cuda, "bin", "nvcc"), "-shared", "-o", tmp, *objs, *ARCH,
-           "-Xcompiler", "-fopenmp", "-lgomp"]
+           "-Xcompiler", "-fopenmp", "-lgomp", "-Xlinker", "--no-undefined"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)

@@ -110,7 +110,7 @@ struct EdgeTables {
 struct LaunchCfg {
   int vec = 0;  // 0 = widest the dtype and alignment allow
   int batch = 6;
-  int threads = 256;
+  int threads = 128;
   int blocks_per_sm = 0;  // 0 = occupancy limit
 };
 }  // namespace
@@ -784,6 +784,7 @@ struct atlas_batch_s {
   int ndesc = 0;
   int64_t ntiles = 0, node_levels = 0;
   int tile_items = 0, threads = 0, blocks = 0, device = -1, vec = 1;
+  bool idx32 = true;
   StorageType st = atlasgb::ST_F32;
 };
 
@@ -809,6 +810,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   std::vector<atlas_fvm_s*> fv;
   // one levels-per-thread width for the whole batch: the widest every field allows
   int vec = want_vec;
+  bool idx32 = true;
   for (int k = 0; k < n; ++k) {
     const atlas_batch_desc& d = descs[k];
     const bool grad = d.op == ATLAS_OP_GRADIENT;
@@ -852,7 +854,11 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     o.items = static_cast<int64_t>(s.nnodes) * o.nvec;
     if (o.items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "descriptor %d too large", k);
     o.op = grad ? 0 : 1;
-    o.pad = 0;
+    const atlasgb::Div32 dv = atlasgb::make_div32(static_cast<uint32_t>(o.nvec));
+    o.div_m = dv.m;
+    o.div_s1 = dv.s1;
+    o.div_s2 = dv.s2;
+    if (static_cast<int64_t>(s.nnodes) * d.ld >= (int64_t(1) << 31)) idx32 = false;
     o.tile0 = tiles;
     tiles += (o.items + tile_items - 1) / tile_items;
     nl += static_cast<int64_t>(s.nnodes) * d.nlev;
@@ -881,7 +887,8 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   b->st = storage_of(dtype);
   b->device = device;
   b->vec = vec;
-  int bps = atlasgb::batch_occupancy(b->st, vec, threads, n);
+  b->idx32 = idx32;
+  int bps = atlasgb::batch_occupancy(b->st, vec, idx32, threads, n);
   if (t.blocks_per_sm > 0) bps = std::min(bps, t.blocks_per_sm);
   const int64_t blocks = std::min<int64_t>(static_cast<int64_t>(fv[0]->num_sms) * bps, std::max<int64_t>(tiles, 1));
   b->blocks = static_cast<int>(blocks);
@@ -897,7 +904,7 @@ int atlas_batch_launch(atlas_batch_t h, void* stream) {
   if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device)
     return fail(ATLAS_ESTATE, "batch lives on device %d, current device is %d", b->device, cur);
   if (b->ntiles == 0) return ok();
-  cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->d_desc, b->ndesc, b->ntiles, b->tile_items, b->threads,
+  cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->idx32, b->d_desc, b->ndesc, b->ntiles, b->tile_items, b->threads,
                                         b->blocks, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return ok();

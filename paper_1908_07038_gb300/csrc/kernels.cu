@@ -94,16 +94,23 @@ template <> struct Pair<double> {
 //
 // The CSR row is consumed BATCH entries at a time: first the BATCH neighbour
 // ids and weights, then all BATCH neighbour level-vectors are requested
-// before any is used, so one item keeps BATCH independent loads in flight
-// instead of a chain of index -> value round trips.  Accumulation stays in
-// CSR order, so the result does not depend on BATCH or VEC.
-template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
+// before any is used.  A short last batch is padded with the node itself and
+// a zero weight (d = 0, so the padding adds exactly 0), which keeps every
+// load and FMA unconditional.  Accumulation follows the CSR order, so the
+// result does not depend on BATCH or VEC.  IDX32 selects 32-bit element
+// offsets (nnodes * ld < 2^31), which saves the 64-bit index arithmetic.
+template <bool IDX32> struct IdxT { using T = int64_t; };
+template <> struct IdxT<true> { using T = uint32_t; };
+
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH, bool IDX32>
 __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                                              const A* __restrict__ w, const A* __restrict__ b,
                                              const S* __restrict__ in0, const S* __restrict__ in1,
                                              S* __restrict__ out0, S* __restrict__ out1, int64_t ld, int32_t nlev,
                                              int32_t i, int32_t lev0) {
-  const int64_t oi = static_cast<int64_t>(i) * ld + lev0;
+  using Idx = typename IdxT<IDX32>::T;
+  const Idx ldx = static_cast<Idx>(ld);
+  const Idx oi = static_cast<Idx>(i) * ldx + static_cast<Idx>(lev0);
   const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
   A xi0[VEC], xi1[VEC], acc0[VEC], acc1[VEC];
   vload<S, A, VEC>(in0 + oi, xi0);
@@ -114,45 +121,41 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
     acc1[k] = A(0);
   }
   for (int32_t qb = q0; qb < q1; qb += BATCH) {
-    const int cnt = (q1 - qb < BATCH) ? (q1 - qb) : BATCH;
     int32_t jj[BATCH];
     A wa[BATCH], wb[BATCH];
 #pragma unroll
     for (int t = 0; t < BATCH; ++t) {
-      jj[t] = i;
-      wa[t] = A(0);
-      wb[t] = A(0);
-      if (t < cnt) {
-        jj[t] = __ldg(nbr + qb + t);
-        if constexpr (SCALAR_W) {
-          wa[t] = __ldg(w + qb + t);
-        } else {
-          Pair<A>::load(w, qb + t, wa[t], wb[t]);
-        }
+      const bool real = qb + t < q1;
+      const int32_t q = real ? qb + t : qb;
+      const int32_t j = __ldg(nbr + q);
+      A x0, x1 = A(0);
+      if constexpr (SCALAR_W) {
+        x0 = __ldg(w + q);
+      } else {
+        Pair<A>::load(w, q, x0, x1);
       }
+      jj[t] = real ? j : i;
+      wa[t] = real ? x0 : A(0);
+      wb[t] = real ? x1 : A(0);
     }
     A xa[BATCH][VEC], xb[NIN == 2 ? BATCH : 1][VEC];
 #pragma unroll
     for (int t = 0; t < BATCH; ++t) {
-      if (t < cnt) {
-        const int64_t oj = static_cast<int64_t>(jj[t]) * ld + lev0;
-        vload<S, A, VEC>(in0 + oj, xa[t]);
-        if constexpr (NIN == 2) vload<S, A, VEC>(in1 + oj, xb[t]);
-      }
+      const Idx oj = static_cast<Idx>(jj[t]) * ldx + static_cast<Idx>(lev0);
+      vload<S, A, VEC>(in0 + oj, xa[t]);
+      if constexpr (NIN == 2) vload<S, A, VEC>(in1 + oj, xb[t]);
     }
 #pragma unroll
     for (int t = 0; t < BATCH; ++t) {
-      if (t < cnt) {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-          if constexpr (NIN == 1) {
-            const A d = xa[t][k] - xi0[k];
-            acc0[k] = fma(wa[t], d, acc0[k]);
-            if constexpr (NOUT == 2) acc1[k] = fma(wb[t], d, acc1[k]);
-          } else {
-            acc0[k] = fma(wa[t], xa[t][k] - xi0[k], acc0[k]);
-            acc0[k] = fma(wb[t], xb[t][k] - xi1[k], acc0[k]);
-          }
+      for (int k = 0; k < VEC; ++k) {
+        if constexpr (NIN == 1) {
+          const A d = xa[t][k] - xi0[k];
+          acc0[k] = fma(wa[t], d, acc0[k]);
+          if constexpr (NOUT == 2) acc1[k] = fma(wb[t], d, acc1[k]);
+        } else {
+          acc0[k] = fma(wa[t], xa[t][k] - xi0[k], acc0[k]);
+          acc0[k] = fma(wb[t], xb[t][k] - xi1[k], acc0[k]);
         }
       }
     }
@@ -176,19 +179,26 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
   if constexpr (NOUT == 2) vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
 }
 
-template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
+// n / d for a divisor fixed per launch: t = umulhi(m, n), q = (t + ((n - t) >> s1)) >> s2
+// (branch-free unsigned division by an invariant integer; exact for all 32-bit n).
+__device__ __forceinline__ uint32_t div_by(uint32_t n, Div32 d) {
+  const uint32_t t = __umulhi(d.m, n);
+  return (t + ((n - t) >> d.s1)) >> d.s2;
+}
+
+template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH, bool IDX32>
 __global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
-                                                       const A* __restrict__ w, const A* __restrict__ b,
-                                                       const S* __restrict__ in0, const S* __restrict__ in1,
-                                                       S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
-                                                       int32_t nlev, int64_t ld, uint32_t nvec) {
+                                                      const A* __restrict__ w, const A* __restrict__ b,
+                                                      const S* __restrict__ in0, const S* __restrict__ in1,
+                                                      S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
+                                                      int32_t nlev, int64_t ld, uint32_t nvec, Div32 dv) {
   const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;  // host guarantees < 2^31
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-    const uint32_t i = item / nvec;
+    const uint32_t i = div_by(item, dv);
     const uint32_t v = item - i * nvec;
-    stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
-                                                               static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
+    stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, IDX32>(
+        ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev, static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
   }
 }
 
@@ -199,11 +209,12 @@ template <typename S, typename A, int OP, int VEC>
 __global__ void __launch_bounds__(512) edge_flux_kernel(const int32_t* __restrict__ e2n, const A* __restrict__ coef,
                                                          const S* __restrict__ in0, const S* __restrict__ in1,
                                                          A* __restrict__ flux0, A* __restrict__ flux1,
-                                                         uint32_t nedges, int32_t nlev, int64_t ld, uint32_t nvec) {
+                                                         uint32_t nedges, int32_t nlev, int64_t ld, uint32_t nvec,
+                                                         Div32 dv) {
   const uint32_t total = nedges * nvec;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-    const uint32_t e = item / nvec;
+    const uint32_t e = div_by(item, dv);
     const int32_t lev0 = static_cast<int32_t>((item - e * nvec) * VEC);
     const int2 ab = __ldg(reinterpret_cast<const int2*>(e2n) + e);
     const A k1 = __ldg(coef + 3 * static_cast<int64_t>(e));
@@ -247,11 +258,11 @@ __global__ void __launch_bounds__(512) node_gather_kernel(const int32_t* __restr
                                                            const A* __restrict__ node, const A* __restrict__ flux0,
                                                            const A* __restrict__ flux1, const S* __restrict__ vin,
                                                            S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
-                                                           int32_t nlev, int64_t ld, uint32_t nvec) {
+                                                           int32_t nlev, int64_t ld, uint32_t nvec, Div32 dv) {
   const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-    const uint32_t i = item / nvec;
+    const uint32_t i = div_by(item, dv);
     const int32_t lev0 = static_cast<int32_t>((item - i * nvec) * VEC);
     A acc0[VEC], acc1[VEC];
 #pragma unroll
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(512) node_gather_kernel(const int32_t* __restr
 // tile_items consecutive (node, level-vector) items of that field.  All fields
 // of a batch share one VEC; operators are gradient (1 in, 2 out) and
 // divergence (2 in, 1 out, B term).
-template <typename S, typename A, int VEC>
+template <typename S, typename A, int VEC, bool IDX32>
 __global__ void __launch_bounds__(512) batch_kernel(const BatchDescDev* __restrict__ descs, int ndesc, int64_t ntiles,
                                                     int tile_items) {
   extern __shared__ int64_t s_tile0[];
@@ -336,19 +347,20 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchDescDev* __restri
     const int64_t ld = D->ld;
     const int32_t nlev = D->nlev;
     const uint32_t nvec = static_cast<uint32_t>(D->nvec);
+    const Div32 dv{D->div_m, D->div_s1, D->div_s2};
     const int op = D->op;
     const int64_t it0 = (t - D->tile0) * tile_items;
     const int64_t it1 = (it0 + tile_items < D->items) ? it0 + tile_items : D->items;
     for (int64_t it = it0 + threadIdx.x; it < it1; it += blockDim.x) {
       const uint32_t u = static_cast<uint32_t>(it);
-      const uint32_t i = u / nvec;
+      const uint32_t i = div_by(u, dv);
       const int32_t lev0 = static_cast<int32_t>((u - i * nvec) * VEC);
       if (op == 0)
-        stencil_item<S, A, 1, 2, VEC, false, false, 3>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
-                                                       static_cast<int32_t>(i), lev0);
+        stencil_item<S, A, 1, 2, VEC, false, false, 6, IDX32>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+                                                              static_cast<int32_t>(i), lev0);
       else
-        stencil_item<S, A, 2, 1, VEC, true, false, 3>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
-                                                      static_cast<int32_t>(i), lev0);
+        stencil_item<S, A, 2, 1, VEC, true, false, 3, IDX32>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+                                                             static_cast<int32_t>(i), lev0);
     }
   }
 }
@@ -357,15 +369,24 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchDescDev* __restri
 template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
   const uint32_t nvec = static_cast<uint32_t>((l.nlev + VEC - 1) / VEC);
-  stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH><<<l.blocks, l.threads, 0, stream>>>(
-      s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
-      static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec);
+  const Div32 dv = make_div32(nvec);
+  const bool idx32 = static_cast<int64_t>(s.nnodes) * l.ld < (int64_t(1) << 31);
+  if (idx32)
+    stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
+        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
+        static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec,
+        dv);
+  else
+    stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
+        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
+        static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec,
+        dv);
   return cudaGetLastError();
 }
 
 template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 const void* stencil_fn() {
-  return reinterpret_cast<const void*>(&stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH>);
+  return reinterpret_cast<const void*>(&stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, true>);
 }
 
 // Visit the kernel instantiation of (storage, shape, vec); F is called with a
@@ -419,6 +440,19 @@ struct StencilFn {
 
 }  // namespace
 
+// Host: multiplier and shifts of the branch-free division by d (d >= 1).
+Div32 make_div32(uint32_t d) {
+  Div32 r{0, 0, 0};
+  if (d <= 1) return r;
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < d) ++l;  // ceil(log2 d)
+  const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+  r.m = static_cast<uint32_t>(m);
+  r.s1 = 1;
+  r.s2 = l - 1;
+  return r;
+}
+
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
   return with_storage(st, s, l.vec, l.batch, RunStencil{s, l, stream});
 }
@@ -435,30 +469,32 @@ template <typename S, typename A, int VEC>
 cudaError_t run_edges(int op, const DevEdges& e, const void* in0, const void* in1, void* flux0, void* flux1,
                       int32_t nlev, int64_t ld, int threads, int blocks, cudaStream_t stream) {
   const uint32_t nvec = static_cast<uint32_t>((nlev + VEC - 1) / VEC);
+  const Div32 dv = make_div32(nvec);
   const A* coef = static_cast<const A*>(e.coef);
   if (op == 0)
     edge_flux_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
         e.e2n, coef, static_cast<const S*>(in0), nullptr, static_cast<A*>(flux0), static_cast<A*>(flux1),
-        static_cast<uint32_t>(e.nedges), nlev, ld, nvec);
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
   else
     edge_flux_kernel<S, A, 1, VEC><<<blocks, threads, 0, stream>>>(
         e.e2n, coef, static_cast<const S*>(in0), static_cast<const S*>(in1), static_cast<A*>(flux0), nullptr,
-        static_cast<uint32_t>(e.nedges), nlev, ld, nvec);
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
   return cudaGetLastError();
 }
 template <typename S, typename A, int VEC>
 cudaError_t run_gather(int op, const DevEdges& e, const void* flux0, const void* flux1, const void* vin, void* out0,
                        void* out1, int32_t nlev, int64_t ld, int threads, int blocks, cudaStream_t stream) {
   const uint32_t nvec = static_cast<uint32_t>((nlev + VEC - 1) / VEC);
+  const Div32 dv = make_div32(nvec);
   const A* node = static_cast<const A*>(e.node);
   if (op == 0)
     node_gather_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
         e.ptr, e.ent, node, static_cast<const A*>(flux0), static_cast<const A*>(flux1), nullptr, static_cast<S*>(out0),
-        static_cast<S*>(out1), e.nnodes, nlev, ld, nvec);
+        static_cast<S*>(out1), e.nnodes, nlev, ld, nvec, dv);
   else
     node_gather_kernel<S, A, 1, VEC><<<blocks, threads, 0, stream>>>(
         e.ptr, e.ent, node, static_cast<const A*>(flux0), nullptr, static_cast<const S*>(vin), static_cast<S*>(out0),
-        nullptr, e.nnodes, nlev, ld, nvec);
+        nullptr, e.nnodes, nlev, ld, nvec, dv);
   return cudaGetLastError();
 }
 }  // namespace
@@ -494,27 +530,31 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
 }
 
 namespace {
-const void* batch_fn(StorageType st, int vec) {
+template <bool IDX32>
+const void* batch_fn_t(StorageType st, int vec) {
   if (st == ST_F64)
-    return vec >= 2 ? reinterpret_cast<const void*>(&batch_kernel<double, double, 2>)
-                    : reinterpret_cast<const void*>(&batch_kernel<double, double, 1>);
-  if (vec >= 4) return reinterpret_cast<const void*>(&batch_kernel<float, float, 4>);
-  if (vec >= 2) return reinterpret_cast<const void*>(&batch_kernel<float, float, 2>);
-  return reinterpret_cast<const void*>(&batch_kernel<float, float, 1>);
+    return vec >= 2 ? reinterpret_cast<const void*>(&batch_kernel<double, double, 2, IDX32>)
+                    : reinterpret_cast<const void*>(&batch_kernel<double, double, 1, IDX32>);
+  if (vec >= 4) return reinterpret_cast<const void*>(&batch_kernel<float, float, 4, IDX32>);
+  if (vec >= 2) return reinterpret_cast<const void*>(&batch_kernel<float, float, 2, IDX32>);
+  return reinterpret_cast<const void*>(&batch_kernel<float, float, 1, IDX32>);
+}
+const void* batch_fn(StorageType st, int vec, bool idx32) {
+  return idx32 ? batch_fn_t<true>(st, vec) : batch_fn_t<false>(st, vec);
 }
 }  // namespace
 
-cudaError_t launch_batch(StorageType st, int vec, const BatchDescDev* descs, int ndesc, int64_t ntiles,
+cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev* descs, int ndesc, int64_t ntiles,
                          int tile_items, int threads, int blocks, cudaStream_t stream) {
   if (st != ST_F64 && st != ST_F32) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int64_t) * static_cast<size_t>(ndesc);
   void* args[] = {const_cast<BatchDescDev**>(&descs), &ndesc, &ntiles, &tile_items};
-  return cudaLaunchKernel(batch_fn(st, vec), dim3(blocks), dim3(threads), args, smem, stream);
+  return cudaLaunchKernel(batch_fn(st, vec, idx32), dim3(blocks), dim3(threads), args, smem, stream);
 }
 
-int batch_occupancy(StorageType st, int vec, int threads, int ndesc) {
+int batch_occupancy(StorageType st, int vec, bool idx32, int threads, int ndesc) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_fn(st, vec), threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_fn(st, vec, idx32), threads,
                                                     sizeof(int64_t) * static_cast<size_t>(ndesc)) != cudaSuccess)
     return 1;
   return blocks > 0 ? blocks : 1;

@@ -12,6 +12,13 @@ namespace atlasgb {
 
 enum StorageType { ST_F32 = 0, ST_F64 = 1, ST_BF16 = 2 };
 
+// Branch-free division of 32-bit unsigned integers by a divisor fixed per
+// launch: q = (t + ((n - t) >> s1)) >> s2 with t = umulhi(m, n).
+struct Div32 {
+  uint32_t m;
+  uint32_t s1, s2;
+};
+
 // Device tables of one node stencil (see Stencil in geometry.h).  w holds
 // [nnz] scalars when scalar_w, else [nnz][2] pairs; b holds [V][2] or is null.
 // Weight precision: double for ST_F64 fields, float otherwise.
@@ -68,7 +75,8 @@ struct BatchDescDev {
   int32_t nvec;
   int32_t op;         // 0 gradient (1 in, 2 out), 1 divergence (2 in, 1 out, with b)
   int32_t vec;
-  int32_t pad;
+  uint32_t div_m;     // division by nvec (see Div32)
+  uint32_t div_s1, div_s2;
 };
 
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream);
@@ -82,8 +90,9 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
                                const void* vin, void* out0, void* out1, int32_t nlev, int64_t ld, int vec,
                                int threads, int blocks, cudaStream_t stream);
 
-cudaError_t launch_batch(StorageType st, int vec, const BatchDescDev* descs, int ndesc, int64_t ntiles,
+Div32 make_div32(uint32_t d);
+cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev* descs, int ndesc, int64_t ntiles,
                          int tile_items, int threads, int blocks, cudaStream_t stream);
-int batch_occupancy(StorageType st, int vec, int threads, int ndesc);
+int batch_occupancy(StorageType st, int vec, bool idx32, int threads, int ndesc);
 
 }  // namespace atlasgb
