@@ -159,15 +159,32 @@ int ensure_stencil(atlas_fvm_s* f, int op, int prec) {
   cudaError_t err = cudaSuccess;
   const int64_t V = f->mesh->grid->g.nnodes;
   t.dev.ptr = t.mem.upload(s.ptr, err);
-  if (err == cudaSuccess) t.dev.nbr = t.mem.upload(s.nbr, err);
-  std::vector<double> w = s.w;
-  if (s.scalar_w) {
-    std::vector<double> ws(s.nbr.size());
-    for (size_t q = 0; q < ws.size(); ++q) ws[q] = s.w[2 * q];
-    w.swap(ws);
+  const size_t nnz = s.nbr.size();
+  if (prec || s.nin == 2) {
+    // double weights, or two-input operators: separate neighbour and weight arrays
+    if (err == cudaSuccess) t.dev.nbr = t.mem.upload(s.nbr, err);
+    std::vector<double> w = s.w;
+    if (s.scalar_w) {
+      std::vector<double> ws(nnz);
+      for (size_t q = 0; q < nnz; ++q) ws[q] = s.w[2 * q];
+      w.swap(ws);
+    }
+    if (err == cudaSuccess)
+      t.dev.w = prec ? static_cast<const void*>(t.mem.upload(w, err))
+                     : static_cast<const void*>(t.mem.upload(convert<float>(w), err));
+  } else {
+    // one-input operators, float weights: one packed entry per CSR slot,
+    // {j, w} or {j, w0, w1, 0}
+    const size_t stride = s.scalar_w ? 2 : 4;
+    std::vector<uint32_t> ent(nnz * stride, 0u);
+    for (size_t q = 0; q < nnz; ++q) {
+      ent[stride * q] = static_cast<uint32_t>(s.nbr[q]);
+      float w0 = static_cast<float>(s.w[2 * q]), w1 = static_cast<float>(s.w[2 * q + 1]);
+      std::memcpy(&ent[stride * q + 1], &w0, 4);
+      if (!s.scalar_w) std::memcpy(&ent[stride * q + 2], &w1, 4);
+    }
+    if (err == cudaSuccess) t.dev.w = t.mem.upload(ent, err);
   }
-  if (err == cudaSuccess) t.dev.w = prec ? static_cast<const void*>(t.mem.upload(w, err))
-                                         : static_cast<const void*>(t.mem.upload(convert<float>(w), err));
   if (err == cudaSuccess && s.has_b)
     t.dev.b = prec ? static_cast<const void*>(t.mem.upload(s.b, err))
                    : static_cast<const void*>(t.mem.upload(convert<float>(s.b), err));

@@ -89,6 +89,53 @@ template <> struct Pair<double> {
   }
 };
 
+// One CSR entry of a node stencil: neighbour id and its weight(s).  Float
+// tables of one-input operators are packed so that one aligned vector load
+// returns the entry: {j, w} (8 bytes) for the scalar-weight Laplacian,
+// {j, w0, w1, 0} (16 bytes) otherwise.  Two-input float tables and all double
+// tables keep separate nbr[] and w[][2] arrays (measured faster there).
+template <typename A, bool SCALAR_W, bool PACKED> struct Entry;
+template <bool SCALAR_W> struct Entry<float, SCALAR_W, false> {
+  static __device__ __forceinline__ void load(const int32_t* __restrict__ nbr, const float* __restrict__ w, int32_t q,
+                                              int32_t& j, float& w0, float& w1) {
+    j = __ldg(nbr + q);
+    if constexpr (SCALAR_W) {
+      w0 = __ldg(w + q);
+      w1 = 0.0f;
+    } else {
+      Pair<float>::load(w, q, w0, w1);
+    }
+  }
+};
+template <bool SCALAR_W> struct Entry<float, SCALAR_W, true> {
+  static __device__ __forceinline__ void load(const int32_t* __restrict__, const float* __restrict__ w, int32_t q,
+                                              int32_t& j, float& w0, float& w1) {
+    if constexpr (SCALAR_W) {
+      const uint2 e = __ldg(reinterpret_cast<const uint2*>(w) + q);
+      j = static_cast<int32_t>(e.x);
+      w0 = __uint_as_float(e.y);
+      w1 = 0.0f;
+    } else {
+      const uint4 e = __ldg(reinterpret_cast<const uint4*>(w) + q);
+      j = static_cast<int32_t>(e.x);
+      w0 = __uint_as_float(e.y);
+      w1 = __uint_as_float(e.z);
+    }
+  }
+};
+template <bool SCALAR_W, bool PACKED> struct Entry<double, SCALAR_W, PACKED> {
+  static __device__ __forceinline__ void load(const int32_t* __restrict__ nbr, const double* __restrict__ w, int32_t q,
+                                              int32_t& j, double& w0, double& w1) {
+    j = __ldg(nbr + q);
+    if constexpr (SCALAR_W) {
+      w0 = __ldg(w + q);
+      w1 = 0.0;
+    } else {
+      Pair<double>::load(w, q, w0, w1);
+    }
+  }
+};
+
 // ------------------------------------------------------- node stencil item
 // out_c(i) = sum_q sum_m W_cm(q) (x_m(nbr q) - x_m(i)) + sum_m B_cm(i) x_m(i)
 //
@@ -127,13 +174,9 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
     for (int t = 0; t < BATCH; ++t) {
       const bool real = qb + t < q1;
       const int32_t q = real ? qb + t : qb;
-      const int32_t j = __ldg(nbr + q);
-      A x0, x1 = A(0);
-      if constexpr (SCALAR_W) {
-        x0 = __ldg(w + q);
-      } else {
-        Pair<A>::load(w, q, x0, x1);
-      }
+      int32_t j;
+      A x0, x1;
+      Entry<A, SCALAR_W, (NIN == 1)>::load(nbr, w, q, j, x0, x1);
       jj[t] = real ? j : i;
       wa[t] = real ? x0 : A(0);
       wb[t] = real ? x1 : A(0);

@@ -19,9 +19,11 @@ struct Div32 {
   uint32_t s1, s2;
 };
 
-// Device tables of one node stencil (see Stencil in geometry.h).  w holds
-// [nnz] scalars when scalar_w, else [nnz][2] pairs; b holds [V][2] or is null.
-// Weight precision: double for ST_F64 fields, float otherwise.
+// Device tables of one node stencil (see Stencil in geometry.h).  One-input
+// operators with float weights (F32 and BF16 fields): w holds packed entries
+// {j, w} (scalar_w) or {j, w0, w1, 0} as 32-bit words and nbr is unused.
+// Otherwise nbr[nnz] and w[nnz] (scalar_w) or w[nnz][2] in the weight
+// precision (double for F64 fields).  b holds [V][2], or is null.
 struct DevStencil {
   const int32_t* ptr = nullptr;
   const int32_t* nbr = nullptr;
@@ -91,6 +93,7 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
                                int threads, int blocks, cudaStream_t stream);
 
 Div32 make_div32(uint32_t d);
+
 cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev* descs, int ndesc, int64_t ntiles,
                          int tile_items, int threads, int blocks, cudaStream_t stream);
 int batch_occupancy(StorageType st, int vec, bool idx32, int threads, int ndesc);
