@@ -208,6 +208,27 @@ int atlas_nabla_divergence_edges(atlas_fvm_t fvm, const void* u, const void* v, 
 int atlas_nabla_laplacian_edges(atlas_fvm_t fvm, const void* f, void* lap, void* ws, size_t ws_bytes,
                                 int nlev, int64_t ld, atlas_dtype dtype, void* stream);
 
+/* The two-pass Laplacian without any allocation.  The paper has no        */
+/* counterpart; it is for callers that cannot call cudaMalloc when they    */
+/* apply the operator: code running inside another framework's memory     */
+/* pool or a pre-sized arena, code in a phase that must not allocate or    */
+/* synchronise, and callers with no device allocator of their own (a       */
+/* Fortran or C model holding only field pointers).  Instead of a caller   */
+/* workspace it uses a static device array owned by the library, of 64 MiB */
+/* (67108864 bytes), which every GPU that loads the library holds until    */
+/* the process exits.  Sizes whose                                         */
+/* workspace (atlas_nabla_workspace_bytes with ATLAS_OP_LAPLACIAN) exceeds */
+/* it are rejected with ATLAS_EINVAL.  The call builds no tables: prepare  */
+/* them first with atlas_fvm_prepare (gradient and divergence bits, this   */
+/* dtype), otherwise it returns ATLAS_ESTATE.  The first call on a device, */
+/* with that device current, looks up the array's device address once;    */
+/* make that first call before any stream capture.  All calls share the    */
+/* array and it keeps the last call's contents (nothing in it needs to     */
+/* start at zero: every value read is written earlier in the same call);   */
+/* calls that overlap on the GPU race on it.  F32 or F64 fields.           */
+int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t fvm, const void* f, void* lap, int nlev, int64_t ld,
+                                        atlas_dtype dtype, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Batched launch: many fields of different grids and level counts in one */
 /* persistent kernel (one launch, capturable in a CUDA graph).            */

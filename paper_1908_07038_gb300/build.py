@@ -34,7 +34,7 @@ def _cuda_home() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "capi.cpp", "kernels.cu")]
+    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "capi.cpp", "kernels.cu", "noalloc.cu")]
 
 
 def _headers():
@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     cuda = _cuda_home()
     os.makedirs(BUILD, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=3) as ex:
+    with ThreadPoolExecutor(max_workers=4) as ex:
         objs = list(ex.map(lambda s: _compile(s, cuda), _sources()))
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [os.path.join(cuda, "bin", "nvcc"), "-shared", "-o", tmp, *objs, *ARCH,

@@ -73,6 +73,7 @@ _SIGS = {
     "atlas_nabla_gradient_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),
     "atlas_nabla_divergence_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),
     "atlas_nabla_laplacian_edges": (I32, [P, P, P, P, SZ, I32, I64, I32, P], True),
+    "atlas_nabla_laplacian_edges_noalloc": (I32, [P, P, P, I32, I64, I32, P], True),
     "atlas_batch_create": (I32, [ctypes.POINTER(atlas_batch_desc), I32, I32, ctypes.POINTER(atlas_batch_tune), PP], True),
     "atlas_batch_launch": (I32, [P, P], True),
     "atlas_batch_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)], True),

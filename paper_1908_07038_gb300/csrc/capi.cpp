@@ -777,6 +777,45 @@ int atlas_nabla_laplacian_edges(atlas_fvm_t h, const void* fin, void* lap, void*
   return rc ? rc : ok();
 }
 
+// Two-pass Laplacian on the library's static scratch (see noalloc.cu): same
+// kernels as atlas_nabla_laplacian_edges, no allocation of any kind.
+int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t h, const void* fin, void* lap, int nlev, int64_t ld,
+                                        atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
+  const void* used[2] = {fin, lap};
+  int rc = check_field_args(dtype, nlev, ld, used, 2);
+  if (rc) return rc;
+  const void* ins[1] = {fin};
+  void* outs[1] = {lap};
+  rc = check_no_overlap(ins, 1, outs, 1, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
+  if (rc) return rc;
+  const WsLayout w = ws_layout(f, ATLAS_OP_LAPLACIAN, ld, dtype);
+  if (w.total > atlasgb::noalloc_scratch_bytes())
+    return fail(ATLAS_EINVAL, "this grid and ld need %zu bytes of scratch; the static scratch holds %zu bytes",
+                w.total, atlasgb::noalloc_scratch_bytes());
+  rc = check_device(f);
+  if (rc) return rc;
+  const int prec = prec_of(dtype);
+  {
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (!f->eg[0][prec].ready || !f->eg[1][prec].ready)
+      return fail(ATLAS_ESTATE, "edge tables of this dtype are not on the device: call atlas_fvm_prepare with the "
+                                "gradient and divergence bits first (this entry point allocates nothing)");
+  }
+  void* scratch = nullptr;
+  cudaError_t e = atlasgb::noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static scratch)");
+  if (nlev == 0) return ok();
+  char* base = static_cast<char*>(scratch);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = run_edges_op(f, 0, fin, nullptr, base + w.g0, base + w.g1, base, w, nlev, ld, dtype, s);
+  if (rc) return rc;
+  rc = run_edges_op(f, 1, base + w.g0, base + w.g1, lap, nullptr, base, w, nlev, ld, dtype, s);
+  return rc ? rc : ok();
+}
+
 int atlas_field_sync(void* dst, const void* src, size_t bytes, int direction, void* stream) {
   if (bytes == 0) return ok();
   if (!dst || !src) return fail(ATLAS_EINVAL, "NULL pointer");

@@ -94,6 +94,10 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
 
 Div32 make_div32(uint32_t d);
 
+// Library-owned static device scratch (noalloc.cu): its size, and its device
+// address on the current device (looked up once per device).
+size_t noalloc_scratch_bytes();
+cudaError_t noalloc_scratch(void** ptr);
 cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev* descs, int ndesc, int64_t ntiles,
                          int tile_items, int threads, int blocks, cudaStream_t stream);
 int batch_occupancy(StorageType st, int vec, bool idx32, int threads, int ndesc);
