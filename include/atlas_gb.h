@@ -254,6 +254,7 @@ typedef struct {
   int threads;
   int blocks_per_sm;
 } atlas_batch_tune;
+/* n = 1..256 descriptors (split larger sets into several batches).       */
 /* Validates the descriptors, uploads them and the tile table to device    */
 /* memory (owned by the batch) and prepares every fvm's tables.  dtype is  */
 /* ATLAS_F32 or ATLAS_F64 for all fields of the batch.  The field pointers  */

@@ -121,7 +121,7 @@ struct atlas_fvm_s {
   int device = -1;
   int num_sms = 0;
   std::mutex mu;
-  OpTables st[atlasgb::OP_COUNT][2];  // [op][weights: 0 float, 1 double]
+  OpTables st[atlasgb::OP_COUNT][3];  // [op][storage dtype: F32, F64, BF16]
   EdgeTables eg[2][2];                // [gradient, divergence][precision]
   LaunchCfg cfg[atlasgb::OP_COUNT];
   int users = 0;
@@ -146,9 +146,11 @@ int check_device(atlas_fvm_s* f) {
   return ATLAS_OK;
 }
 
-// Build and upload the stencil tables of op in the given weight precision.
-int ensure_stencil(atlas_fvm_s* f, int op, int prec) {
-  OpTables& t = f->st[op][prec];
+// Build and upload the stencil tables of op for fields of one storage dtype
+// (double weights for F64 fields, float weights otherwise).
+int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
+  OpTables& t = f->st[op][dtype];
+  const int prec = (dtype == ATLAS_F64) ? 1 : 0;
   if (t.ready) return ATLAS_OK;
   atlasgb::Stencil s;
   try {
@@ -158,6 +160,45 @@ int ensure_stencil(atlas_fvm_s* f, int op, int prec) {
   }
   cudaError_t err = cudaSuccess;
   const int64_t V = f->mesh->grid->g.nnodes;
+  atlasgb::PairStencil ps;
+  if (op == atlasgb::OP_LAP && dtype == ATLAS_F32 && V % 2 == 0) {
+    // the FP32 Laplacian runs on node pairs (merged rows, each shared neighbour
+    // read once); FP64 (ALU-bound) and BF16 measured faster per node
+    try {
+      if (!atlasgb::build_pair_stencil(s, ps)) return fail(ATLAS_EINVAL, "pair table build failed");
+    } catch (const std::bad_alloc&) {
+      return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+    }
+    t.dev.ptr = t.mem.upload(ps.ptr, err);
+    const size_t np = ps.nbr.size();
+    if (prec) {
+      if (err == cudaSuccess) t.dev.nbr = t.mem.upload(ps.nbr, err);
+      if (err == cudaSuccess) t.dev.w = t.mem.upload(ps.w, err);
+    } else {
+      std::vector<uint32_t> ent(4 * np, 0u);
+      for (size_t q = 0; q < np; ++q) {
+        ent[4 * q] = static_cast<uint32_t>(ps.nbr[q]);
+        const float wa = static_cast<float>(ps.w[2 * q]), wb = static_cast<float>(ps.w[2 * q + 1]);
+        std::memcpy(&ent[4 * q + 1], &wa, 4);
+        std::memcpy(&ent[4 * q + 2], &wb, 4);
+      }
+      if (err == cudaSuccess) t.dev.w = t.mem.upload(ent, err);
+    }
+    if (err != cudaSuccess) {
+      t.mem.release();
+      return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for operator tables")
+                                              : cuda_fail(err, "upload of operator tables");
+    }
+    t.dev.nnodes = static_cast<int32_t>(V);
+    t.dev.nnz = static_cast<int64_t>(np);
+    t.dev.nin = 1;
+    t.dev.nout = 1;
+    t.dev.has_b = false;
+    t.dev.scalar_w = true;
+    t.dev.pair = true;
+    t.ready = true;
+    return ATLAS_OK;
+  }
   t.dev.ptr = t.mem.upload(s.ptr, err);
   const size_t nnz = s.nbr.size();
   if (prec || s.nin == 2) {
@@ -331,10 +372,9 @@ int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void
   rc = check_device(f);
   if (rc) return rc;
   if (nlev == 0 || V == 0) return ok();
-  const int prec = prec_of(dtype);
   {
     std::lock_guard<std::mutex> lk(f->mu);
-    rc = ensure_stencil(f, op, prec);
+    rc = ensure_stencil(f, op, dtype);
     if (rc) return rc;
   }
   const LaunchCfg& c = f->cfg[op];
@@ -352,8 +392,8 @@ int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void
   l.threads = c.threads;
   l.batch = c.batch;
   const StorageType st = storage_of(dtype);
-  l.blocks = grid_blocks(f, st, f->st[op][prec].dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
-  cudaError_t e = atlasgb::launch_stencil(st, f->st[op][prec].dev, l, static_cast<cudaStream_t>(stream));
+  l.blocks = grid_blocks(f, st, f->st[op][dtype].dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
+  cudaError_t e = atlasgb::launch_stencil(st, f->st[op][dtype].dev, l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
   return ok();
 }
@@ -606,7 +646,7 @@ int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
     if (!(op_mask & (1u << op))) continue;
     for (int dt = 0; dt < 3; ++dt) {
       if (!(dtype_mask & (1u << dt))) continue;
-      rc = ensure_stencil(f, op, prec_of(static_cast<atlas_dtype>(dt)));
+      rc = ensure_stencil(f, op, dt);
       if (rc) return rc;
       if (op <= atlasgb::OP_DIV && dt != ATLAS_BF16) {
         rc = ensure_edges(f, op, prec_of(static_cast<atlas_dtype>(dt)));
@@ -850,7 +890,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
                        atlas_batch_t* out) {
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!descs || n < 1 || n > 4096) return fail(ATLAS_EINVAL, "need 1..4096 descriptors");
+  if (!descs || n < 1 || n > 256) return fail(ATLAS_EINVAL, "need 1..256 descriptors");
   if (dtype != ATLAS_F32 && dtype != ATLAS_F64) return fail(ATLAS_EDTYPE, "batches take F32 or F64 fields");
   atlas_batch_tune t{0, 0, 0, 0};
   if (tune) t = *tune;
@@ -859,7 +899,6 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   const int tile_items = t.tile_items > 0 ? t.tile_items : 4096;
   const int threads = t.threads > 0 ? t.threads : 256;
   if (threads < 64 || threads > 1024 || threads % 32) return fail(ATLAS_EINVAL, "bad thread count %d", threads);
-  const int prec = prec_of(dtype);
   std::vector<atlasgb::BatchDescDev> hd(static_cast<size_t>(n));
   int64_t tiles = 0, nl = 0;
   int device = -1;
@@ -889,10 +928,10 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     if (rc) return fail(rc, "descriptor %d: %s", k, g_err.c_str());
     {
       std::lock_guard<std::mutex> lk(f->mu);
-      rc = ensure_stencil(f, grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV, prec);
+      rc = ensure_stencil(f, grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV, dtype);
       if (rc) return rc;
     }
-    const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][prec].dev;
+    const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][dtype].dev;
     atlasgb::BatchDescDev& o = hd[k];
     o.ptr = s.ptr;
     o.nbr = s.nbr;

@@ -628,6 +628,48 @@ bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
   return true;
 }
 
+bool build_pair_stencil(const Stencil& s, PairStencil& p) {
+  const int64_t V = static_cast<int64_t>(s.ptr.size()) - 1;
+  if (V % 2 != 0 || !s.scalar_w) return false;
+  const int64_t G = V / 2;
+  p.ptr.assign(static_cast<size_t>(G) + 1, 0);
+  // rows are sorted by neighbour id: merge the two rows of every pair
+  for (int64_t g = 0; g < G; ++g) {
+    int32_t qa = s.ptr[2 * g], ea = s.ptr[2 * g + 1], qb = s.ptr[2 * g + 1], eb = s.ptr[2 * g + 2];
+    for (int32_t q = qa + 1; q < ea; ++q)
+      if (s.nbr[q] <= s.nbr[q - 1]) return false;
+    for (int32_t q = qb + 1; q < eb; ++q)
+      if (s.nbr[q] <= s.nbr[q - 1]) return false;
+    int32_t c = 0;
+    while (qa < ea || qb < eb) {
+      if (qb == eb || (qa < ea && s.nbr[qa] < s.nbr[qb])) ++qa;
+      else if (qa == ea || s.nbr[qb] < s.nbr[qa]) ++qb;
+      else { ++qa; ++qb; }
+      ++c;
+    }
+    if (static_cast<int64_t>(p.ptr[g]) + c > INT32_MAX) return false;
+    p.ptr[g + 1] = p.ptr[g] + c;
+  }
+  p.nbr.resize(static_cast<size_t>(p.ptr[G]));
+  p.w.assign(static_cast<size_t>(2 * p.ptr[G]), 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t g = 0; g < G; ++g) {
+    int32_t qa = s.ptr[2 * g], ea = s.ptr[2 * g + 1], qb = s.ptr[2 * g + 1], eb = s.ptr[2 * g + 2];
+    int32_t o = p.ptr[g];
+    while (qa < ea || qb < eb) {
+      if (qb == eb || (qa < ea && s.nbr[qa] < s.nbr[qb])) {
+        p.nbr[o] = s.nbr[qa]; p.w[2 * o] = s.w[2 * qa]; ++qa;
+      } else if (qa == ea || s.nbr[qb] < s.nbr[qa]) {
+        p.nbr[o] = s.nbr[qb]; p.w[2 * o + 1] = s.w[2 * qb]; ++qb;
+      } else {
+        p.nbr[o] = s.nbr[qa]; p.w[2 * o] = s.w[2 * qa]; p.w[2 * o + 1] = s.w[2 * qb]; ++qa; ++qb;
+      }
+      ++o;
+    }
+  }
+  return true;
+}
+
 bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg) {
   const int64_t V = m.grid->nnodes, E = m.nedges;
   const bool div = (op == OP_DIV);

@@ -82,4 +82,17 @@ enum StencilOp { OP_GRAD = 0, OP_DIV = 1, OP_GRAD_ADJ = 2, OP_DIV_ADJ = 3, OP_LA
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
 bool build_edge_gather(const Mesh& m, const Dual& d, int op /*OP_GRAD or OP_DIV*/, EdgeGather& eg);
 
+// Merged table of a one-input, one-output, scalar-weight stencil over node
+// pairs (2g, 2g+1): the union of the two nodes' rows, sorted by neighbour id,
+// with the weight of each node (0 where the neighbour is not in its row).
+// Each node's own entries keep their ascending-neighbour order, so applying
+// the merged table gives the same sums as the per-node table (zero-weight
+// terms add exact zeros).  Requires an even node count.
+struct PairStencil {
+  std::vector<int32_t> ptr;   // [V/2 + 1]
+  std::vector<int32_t> nbr;   // [nnz]
+  std::vector<double> w;      // [nnz][2] (weight of node 2g, of node 2g+1)
+};
+bool build_pair_stencil(const Stencil& s, PairStencil& p);
+
 }  // namespace atlasgb

@@ -245,6 +245,86 @@ __global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict_
   }
 }
 
+// ----------------------------------------------------- node-pair stencil
+// One-input, one-output, scalar-weight stencil (the fused Laplacian) applied
+// to node pairs (2g, 2g+1) from a merged table: every entry carries the
+// neighbour and the weight of each node of the pair, so a neighbour shared by
+// both nodes is read once.  Entries are sorted by neighbour id, as is each
+// node's own row, so every node accumulates its terms in the same order as
+// the per-node kernel; zero-weight terms add exact zeros.
+template <typename A> struct PairEntry;
+template <> struct PairEntry<float> {
+  static __device__ __forceinline__ void load(const int32_t* __restrict__, const float* __restrict__ w, int32_t q,
+                                              int32_t& j, float& wa, float& wb) {
+    const uint4 e = __ldg(reinterpret_cast<const uint4*>(w) + q);
+    j = static_cast<int32_t>(e.x);
+    wa = __uint_as_float(e.y);
+    wb = __uint_as_float(e.z);
+  }
+};
+template <> struct PairEntry<double> {
+  static __device__ __forceinline__ void load(const int32_t* __restrict__ nbr, const double* __restrict__ w,
+                                              int32_t q, int32_t& j, double& wa, double& wb) {
+    j = __ldg(nbr + q);
+    Pair<double>::load(w, q, wa, wb);
+  }
+};
+
+template <typename S, typename A, int VEC, int BATCH, bool IDX32>
+__global__ void __launch_bounds__(512) pair_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
+                                                   const A* __restrict__ w, const S* __restrict__ in0,
+                                                   S* __restrict__ out0, int32_t npairs, int32_t nlev, int64_t ld,
+                                                   uint32_t nvec, Div32 dv) {
+  using Idx = typename IdxT<IDX32>::T;
+  const Idx ldx = static_cast<Idx>(ld);
+  const uint32_t total = static_cast<uint32_t>(npairs) * nvec;  // host guarantees < 2^31
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+    const uint32_t g = div_by(item, dv);
+    const int32_t lev0 = static_cast<int32_t>((item - g * nvec) * VEC);
+    const int32_t ia = static_cast<int32_t>(2 * g);
+    const Idx oa = static_cast<Idx>(ia) * ldx + static_cast<Idx>(lev0);
+    const Idx ob = oa + ldx;
+    A xa[VEC], xb[VEC], ca[VEC], cb[VEC];
+    vload<S, A, VEC>(in0 + oa, xa);
+    vload<S, A, VEC>(in0 + ob, xb);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      ca[k] = A(0);
+      cb[k] = A(0);
+    }
+    const int32_t q0 = __ldg(ptr + g), q1 = __ldg(ptr + g + 1);
+    for (int32_t qb = q0; qb < q1; qb += BATCH) {
+      int32_t jj[BATCH];
+      A wa[BATCH], wb[BATCH];
+#pragma unroll
+      for (int t = 0; t < BATCH; ++t) {
+        const bool real = qb + t < q1;
+        int32_t j;
+        A x0, x1;
+        PairEntry<A>::load(nbr, w, real ? qb + t : qb, j, x0, x1);
+        jj[t] = real ? j : ia;
+        wa[t] = real ? x0 : A(0);
+        wb[t] = real ? x1 : A(0);
+      }
+      A xj[BATCH][VEC];
+#pragma unroll
+      for (int t = 0; t < BATCH; ++t) vload<S, A, VEC>(in0 + static_cast<Idx>(jj[t]) * ldx + static_cast<Idx>(lev0), xj[t]);
+#pragma unroll
+      for (int t = 0; t < BATCH; ++t) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+          ca[k] = fma(wa[t], xj[t][k] - xa[k], ca[k]);
+          cb[k] = fma(wb[t], xj[t][k] - xb[k], cb[k]);
+        }
+      }
+    }
+    const int nvalid = nlev - lev0;
+    vstore<S, A, VEC>(out0 + oa, ca, nvalid);
+    vstore<S, A, VEC>(out0 + ob, cb, nvalid);
+  }
+}
+
 // ------------------------------------------------------------- edge pass
 // OP 0 (gradient): flux0 = k1 (x_b - x_a), flux1 = k2 (x_b - x_a)
 // OP 1 (divergence): flux0 = k1 (u_b - u_a) + k2 (v_b - v_a) + k3 v_a
@@ -367,39 +447,46 @@ __global__ void __launch_bounds__(512) node_gather_kernel(const int32_t* __restr
 // of a batch share one VEC; operators are gradient (1 in, 2 out) and
 // divergence (2 in, 1 out, B term).
 template <typename S, typename A, int VEC, bool IDX32>
-__global__ void __launch_bounds__(512) batch_kernel(const BatchDescDev* __restrict__ descs, int ndesc, int64_t ntiles,
+__global__ void __launch_bounds__(512, 2) batch_kernel(const BatchDescDev* __restrict__ descs, int ndesc, int64_t ntiles,
                                                     int tile_items) {
-  extern __shared__ int64_t s_tile0[];
-  for (int d = threadIdx.x; d < ndesc; d += blockDim.x) s_tile0[d] = descs[d].tile0;
+  // the whole descriptor table is copied to shared memory once per block
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  BatchDescDev* sd = reinterpret_cast<BatchDescDev*>(s_raw);
+  {
+    const int4* src = reinterpret_cast<const int4*>(descs);
+    int4* dst = reinterpret_cast<int4*>(s_raw);
+    const int n16 = ndesc * static_cast<int>(sizeof(BatchDescDev) / 16);
+    for (int k = threadIdx.x; k < n16; k += blockDim.x) dst[k] = src[k];
+  }
   __syncthreads();
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int lo = 0, hi = ndesc - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (s_tile0[mid] <= t) lo = mid; else hi = mid - 1;
+      if (sd[mid].tile0 <= t) lo = mid; else hi = mid - 1;
     }
-    const BatchDescDev* D = descs + lo;
-    const int32_t* ptr = D->ptr;
-    const int32_t* nbr = D->nbr;
-    const A* w = static_cast<const A*>(D->w);
-    const A* b = static_cast<const A*>(D->b);
-    const S* in0 = static_cast<const S*>(D->in0);
-    const S* in1 = static_cast<const S*>(D->in1);
-    S* out0 = static_cast<S*>(D->out0);
-    S* out1 = static_cast<S*>(D->out1);
-    const int64_t ld = D->ld;
-    const int32_t nlev = D->nlev;
-    const uint32_t nvec = static_cast<uint32_t>(D->nvec);
-    const Div32 dv{D->div_m, D->div_s1, D->div_s2};
-    const int op = D->op;
-    const int64_t it0 = (t - D->tile0) * tile_items;
-    const int64_t it1 = (it0 + tile_items < D->items) ? it0 + tile_items : D->items;
+    const BatchDescDev& D = sd[lo];
+    const int32_t* ptr = D.ptr;
+    const int32_t* nbr = D.nbr;
+    const A* w = static_cast<const A*>(D.w);
+    const A* b = static_cast<const A*>(D.b);
+    const S* in0 = static_cast<const S*>(D.in0);
+    const S* in1 = static_cast<const S*>(D.in1);
+    S* out0 = static_cast<S*>(D.out0);
+    S* out1 = static_cast<S*>(D.out1);
+    const int64_t ld = D.ld;
+    const int32_t nlev = D.nlev;
+    const uint32_t nvec = static_cast<uint32_t>(D.nvec);
+    const Div32 dv{D.div_m, D.div_s1, D.div_s2};
+    const int op = D.op;
+    const int64_t it0 = (t - D.tile0) * tile_items;
+    const int64_t it1 = (it0 + tile_items < D.items) ? it0 + tile_items : D.items;
     for (int64_t it = it0 + threadIdx.x; it < it1; it += blockDim.x) {
       const uint32_t u = static_cast<uint32_t>(it);
       const uint32_t i = div_by(u, dv);
       const int32_t lev0 = static_cast<int32_t>((u - i * nvec) * VEC);
       if (op == 0)
-        stencil_item<S, A, 1, 2, VEC, false, false, 6, IDX32>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
+        stencil_item<S, A, 1, 2, VEC, false, false, 3, IDX32>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
                                                               static_cast<int32_t>(i), lev0);
       else
         stencil_item<S, A, 2, 1, VEC, true, false, 3, IDX32>(ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev,
@@ -496,12 +583,62 @@ Div32 make_div32(uint32_t d) {
   return r;
 }
 
+namespace {
+template <typename S, typename A, int VEC, int BATCH>
+cudaError_t run_pair(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
+  const uint32_t nvec = static_cast<uint32_t>((l.nlev + VEC - 1) / VEC);
+  const Div32 dv = make_div32(nvec);
+  const int32_t npairs = s.nnodes / 2;
+  const bool idx32 = static_cast<int64_t>(s.nnodes) * l.ld < (int64_t(1) << 31);
+  if (idx32)
+    pair_kernel<S, A, VEC, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
+        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), npairs,
+        l.nlev, l.ld, nvec, dv);
+  else
+    pair_kernel<S, A, VEC, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
+        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), npairs,
+        l.nlev, l.ld, nvec, dv);
+  return cudaGetLastError();
+}
+
+// (storage, vec, batch) of the pair kernel: batch <= 3 selects 2, else 4
+template <typename S, typename A, typename F>
+auto pair_with_vec(int vec, int batch, F&& f) {
+  constexpr int maxvec = 16 / static_cast<int>(sizeof(S));
+  const bool small = batch <= 3;
+  if (vec >= 8 && maxvec >= 8)
+    return small ? f.template operator()<S, A, (maxvec >= 8 ? 8 : 1), 2>() : f.template operator()<S, A, (maxvec >= 8 ? 8 : 1), 4>();
+  if (vec >= 4 && maxvec >= 4)
+    return small ? f.template operator()<S, A, (maxvec >= 4 ? 4 : 1), 2>() : f.template operator()<S, A, (maxvec >= 4 ? 4 : 1), 4>();
+  if (vec >= 2) return small ? f.template operator()<S, A, 2, 2>() : f.template operator()<S, A, 2, 4>();
+  return small ? f.template operator()<S, A, 1, 2>() : f.template operator()<S, A, 1, 4>();
+}
+template <typename F>
+auto pair_with_storage(StorageType st, int vec, int batch, F&& f) {
+  if (st == ST_F64) return pair_with_vec<double, double>(vec, batch, f);
+  if (st == ST_BF16) return pair_with_vec<uint16_t, float>(vec, batch, f);
+  return pair_with_vec<float, float>(vec, batch, f);
+}
+struct RunPair {
+  const DevStencil& s;
+  const StencilLaunch& l;
+  cudaStream_t stream;
+  template <typename S, typename A, int VEC, int BATCH>
+  cudaError_t operator()() const { return run_pair<S, A, VEC, BATCH>(s, l, stream); }
+};
+struct PairFn {
+  template <typename S, typename A, int VEC, int BATCH>
+  const void* operator()() const { return reinterpret_cast<const void*>(&pair_kernel<S, A, VEC, BATCH, true>); }
+};
+}  // namespace
+
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
+  if (s.pair) return pair_with_storage(st, l.vec, l.batch, RunPair{s, l, stream});
   return with_storage(st, s, l.vec, l.batch, RunStencil{s, l, stream});
 }
 
 int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int batch, int threads) {
-  const void* fn = with_storage(st, s, vec, batch, StencilFn{});
+  const void* fn = s.pair ? pair_with_storage(st, vec, batch, PairFn{}) : with_storage(st, s, vec, batch, StencilFn{});
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess) return 1;
   return blocks > 0 ? blocks : 1;
@@ -590,7 +727,7 @@ const void* batch_fn(StorageType st, int vec, bool idx32) {
 cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev* descs, int ndesc, int64_t ntiles,
                          int tile_items, int threads, int blocks, cudaStream_t stream) {
   if (st != ST_F64 && st != ST_F32) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(int64_t) * static_cast<size_t>(ndesc);
+  const size_t smem = sizeof(BatchDescDev) * static_cast<size_t>(ndesc);
   void* args[] = {const_cast<BatchDescDev**>(&descs), &ndesc, &ntiles, &tile_items};
   return cudaLaunchKernel(batch_fn(st, vec, idx32), dim3(blocks), dim3(threads), args, smem, stream);
 }
@@ -598,7 +735,7 @@ cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev
 int batch_occupancy(StorageType st, int vec, bool idx32, int threads, int ndesc) {
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_fn(st, vec, idx32), threads,
-                                                    sizeof(int64_t) * static_cast<size_t>(ndesc)) != cudaSuccess)
+                                                    sizeof(BatchDescDev) * static_cast<size_t>(ndesc)) != cudaSuccess)
     return 1;
   return blocks > 0 ? blocks : 1;
 }

@@ -33,6 +33,10 @@ struct DevStencil {
   int64_t nnz = 0;
   int nin = 1, nout = 1;
   bool has_b = false, scalar_w = false;
+  // pair == true: merged node-pair table (one input, one output, scalar
+  // weights): ptr[nnodes/2 + 1]; float weights packed {j, wa, wb, 0}; double
+  // weights nbr[nnz] and w[nnz][2]
+  bool pair = false;
 };
 
 struct StencilLaunch {
@@ -60,7 +64,7 @@ struct DevEdges {
 };
 
 // Persistent batched launch: one descriptor per field.
-struct BatchDescDev {
+struct alignas(16) BatchDescDev {
   const int32_t* ptr;
   const int32_t* nbr;
   const void* w;
@@ -79,7 +83,9 @@ struct BatchDescDev {
   int32_t vec;
   uint32_t div_m;     // division by nvec (see Div32)
   uint32_t div_s1, div_s2;
+  uint32_t pad[2];
 };
+static_assert(sizeof(BatchDescDev) % 16 == 0, "descriptors are copied to shared memory in 16-byte words");
 
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream);
 // Maximum resident blocks per SM of the stencil kernel for this configuration.
