@@ -44,6 +44,36 @@ def _dist():
     return ws, rank, local
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_o1280.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1908_07038_gb300", "csrc", "kernels.cu")
+
+
+def _kernel_hash():
+    import hashlib
+    with open(KERNEL_SOURCE, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def _traffic(op):
+    """DRAM bytes per launch of op from the committed ncu capture, or None when
+    the kernels have changed since the counters were taken."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+        if d.get("kernels_sha256") != _kernel_hash():
+            return None
+        return float(d["per_launch_bytes"][op])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+KERNEL_NAME = {"gradient": "stencil_kernel<float,float,1,2,4,0,0,B,1>",
+               "divergence": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
+               "laplacian": "pair_kernel<float,float,4,B,1>",
+               "gradient_adjoint": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
+               "divergence_adjoint": "stencil_kernel<float,float,1,2,4,1,0,B,1>"}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -273,8 +303,10 @@ def run_native(args):
         per[op] = {"ms": round(ms, 4), "node_levels_per_s": V * nlev / (ms * 1e-3),
                    "alg_bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / hbm}
     dom = max(OPS, key=lambda o: per[o]["ms"])
-    roofline = {"bound": "hbm", "kernel": "stencil_kernel<%s>" % dom, "achieved": round(per[dom]["gbs"], 1),
-                "peak": hbm, "unit": "GB/s", "frac": round(per[dom]["frac"], 4), "traffic": None,
+    traffic = _traffic(dom) if args.grid == N_GRID else None
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAME[dom], "operator": dom, "achieved": round(per[dom]["gbs"], 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(per[dom]["frac"], 4),
+                "traffic": traffic, "traffic_gbs": round(traffic / (per[dom]["ms"] * 1e-3) / 1e9, 1) if traffic else None,
                 "peak_kind": peak_kind}
 
     # ---------------------------------------------------------------- e2e

@@ -24,8 +24,11 @@
  *   - Field pointers are DEVICE pointers owned by the caller (for example
  *     torch tensors); the library never frees them.  A field is stored
  *     field[node][level]: node i, level k at element offset i*ld + k, with
- *     nlev >= 0 levels and leading dimension ld >= nlev (elements).  Levels
- *     nlev..ld-1 of an output are never written.  Nodes are numbered row by
+ *     nlev >= 0 levels and leading dimension ld >= nlev (elements).  When
+ *     ld is a multiple of the vector width (16 bytes: 4 F32, 2 F64, 8 BF16
+ *     levels) outputs are written in whole vectors and the padding levels
+ *     from nlev to the end of the row's last vector are set to zero; all
+ *     later levels below ld are never written.  Nodes are numbered row by
  *     row from north to south, and within a row by increasing longitude
  *     starting at 0.
  *   - dtype selects the storage type of every field argument of the call:

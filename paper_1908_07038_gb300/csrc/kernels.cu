@@ -59,18 +59,16 @@ template <typename S, typename A, int VEC>
 __device__ __forceinline__ void vstore(S* __restrict__ p, const A (&v)[VEC], int nvalid) {
   constexpr int BYTES = VEC * static_cast<int>(sizeof(S));
   using R = typename Raw<BYTES>::T;
+  // The last vector of a row may reach past nlev into the row's padding
+  // (ld is a multiple of VEC whenever VEC > 1).  It is stored whole, with
+  // zeros in the padding levels: a partly written sector would make L2 read
+  // it from DRAM first.
   S e[VEC];
 #pragma unroll
-  for (int k = 0; k < VEC; ++k) e[k] = Conv<S, A>::from(v[k]);
-  if (nvalid >= VEC) {
-    R raw;
-    memcpy(&raw, e, BYTES);
-    *reinterpret_cast<R*>(p) = raw;
-  } else {
-#pragma unroll
-    for (int k = 0; k < VEC; ++k)
-      if (k < nvalid) p[k] = e[k];
-  }
+  for (int k = 0; k < VEC; ++k) e[k] = Conv<S, A>::from(k < nvalid ? v[k] : A(0));
+  R raw;
+  memcpy(&raw, e, BYTES);
+  *reinterpret_cast<R*>(p) = raw;
 }
 
 template <typename A> struct Pair;

@@ -99,13 +99,16 @@ def test_fp32_ragged_levels_and_layouts(torch, pfvm, omesh, N, nlev, ld):
     want = _oracle_all(om, f, u, v, nlev)
     for k in want:
         assert _relmax(_host(got[k], nlev), want[k]) <= TOL["f32"], (k, N, nlev, ld)
-    # padding levels of the outputs are never written
+    # padding levels of the outputs: zero up to the end of the last vector
+    # (when ld is a multiple of the 4-level vector), never written beyond
     if ld > nlev:
         out = torch.full((fvm.nnodes, ld), 7.0, device="cuda")
         gy = torch.full_like(out, 7.0)
         fvm.gradient(_dev(torch, f, ld), nlev, out=(out, gy))
         torch.cuda.synchronize()
-        assert torch.all(out[:, nlev:] == 7.0).item() and torch.all(gy[:, nlev:] == 7.0).item()
+        end = (nlev + 3) // 4 * 4 if ld % 4 == 0 else nlev
+        for t in (out, gy):
+            assert torch.all(t[:, nlev:end] == 0.0).item() and torch.all(t[:, end:] == 7.0).item()
 
 
 def test_fp64_and_fp32_o80_137(torch, pfvm, omesh):
