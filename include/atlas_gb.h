@@ -247,10 +247,11 @@ typedef struct {
   int64_t ld;
 } atlas_batch_desc;
 /* Work split: each descriptor is cut into tiles of tile_items (node,      */
-/* level-vector) items; vec levels per thread (1, 2 or 4; the batch uses  */
-/* the widest vec that every field's ld and pointers allow, capped by     */
-/* this value), threads per block (64..512), blocks per SM of the          */
-/* persistent grid.  Zero fields take the defaults.                        */
+/* level-vector) items (default 1024), each computed by one block; vec    */
+/* levels per thread (1, 2 or 4; the batch uses the widest vec that every */
+/* field's ld and pointers allow, capped by this value), threads per       */
+/* block (64..256, default 256), blocks per SM of the persistent grid      */
+/* (0 = as many as fit).  Zero fields take the defaults.                   */
 typedef struct {
   int vec;
   int tile_items;
@@ -258,13 +259,19 @@ typedef struct {
   int blocks_per_sm;
 } atlas_batch_tune;
 /* n = 1..256 descriptors (split larger sets into several batches).       */
-/* Validates the descriptors, uploads them and the tile table to device    */
-/* memory (owned by the batch) and prepares every fvm's tables.  dtype is  */
-/* ATLAS_F32 or ATLAS_F64 for all fields of the batch.  The field pointers  */
-/* are fixed at creation; re-create the batch for other fields.            */
+/* Validates the descriptors and prepares every fvm's tables.  The         */
+/* descriptor table is kept by the batch and passed whole to every launch  */
+/* as a kernel parameter (no device allocation).  dtype is ATLAS_F32 or    */
+/* ATLAS_F64 for all fields of the batch.  The field pointers are fixed at */
+/* creation; re-create the batch for other fields.                         */
 int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, const atlas_batch_tune* tune,
                        atlas_batch_t* out);
-/* One persistent launch over every tile of every descriptor.              */
+/* One persistent launch over every tile of every descriptor: block b     */
+/* computes tiles b, b + grid, ... (divergence tiles, and fields with more */
+/* levels, first).  Results do not depend on the tile order or the launch  */
+/* shape (each item is computed once, in CSR order).  A launch reads only  */
+/* its kernel parameters and the fields, so launches of one batch may be   */
+/* captured in CUDA graphs and replayed on any stream.                     */
 int atlas_batch_launch(atlas_batch_t b, void* stream);
 /* Total tiles and total (node, level) pairs of the batch.                  */
 int atlas_batch_info(atlas_batch_t b, int64_t* tiles, int64_t* node_levels);

@@ -2,8 +2,9 @@
 launch (``atlas_batch_*``), optionally captured once in a CUDA graph and
 replayed.
 
-A ``Batch`` holds its descriptor table on the device; the field pointers are
-fixed when it is created, which is also what a CUDA graph needs.  ``plain``
+A ``Batch`` holds its descriptor table (passed whole to each launch as a
+kernel parameter); the field pointers are fixed when it is created, which is
+also what a CUDA graph needs.  ``plain``
 runs the same work as one launch per field, for comparison.
 """
 from __future__ import annotations

@@ -876,7 +876,7 @@ int atlas_field_sync(void* dst, const void* src, size_t bytes, int direction, vo
 // ================================================================= batches
 struct atlas_batch_s {
   std::vector<atlas_fvm_s*> fvms;
-  atlasgb::BatchDescDev* d_desc = nullptr;
+  atlasgb::BatchParams params;  // descriptor table, passed by value to every launch
   int ndesc = 0;
   int64_t ntiles = 0, node_levels = 0;
   int tile_items = 0, threads = 0, blocks = 0, device = -1, vec = 1;
@@ -890,17 +890,28 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
                        atlas_batch_t* out) {
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!descs || n < 1 || n > 256) return fail(ATLAS_EINVAL, "need 1..256 descriptors");
+  if (!descs || n < 1 || n > atlasgb::kBatchMaxDesc)
+    return fail(ATLAS_EINVAL, "need 1..%d descriptors", atlasgb::kBatchMaxDesc);
   if (dtype != ATLAS_F32 && dtype != ATLAS_F64) return fail(ATLAS_EDTYPE, "batches take F32 or F64 fields");
   atlas_batch_tune t{0, 0, 0, 0};
   if (tune) t = *tune;
   const int want_vec = t.vec > 0 ? t.vec : 16 / elem_size(dtype);
   if (want_vec != 1 && want_vec != 2 && want_vec != 4) return fail(ATLAS_EINVAL, "batch vec must be 1, 2 or 4");
-  const int tile_items = t.tile_items > 0 ? t.tile_items : 4096;
+  const int tile_items = t.tile_items > 0 ? t.tile_items : 1024;
   const int threads = t.threads > 0 ? t.threads : 256;
   if (threads < 64 || threads > 1024 || threads % 32) return fail(ATLAS_EINVAL, "bad thread count %d", threads);
   std::vector<atlasgb::BatchDescDev> hd(static_cast<size_t>(n));
   int64_t tiles = 0, nl = 0;
+  // Tiles are drawn in table order: the costlier tiles (divergence, then more
+  // levels) go first so that the cheap ones fill the end of the launch.  The
+  // order changes no result: every item is computed once, by one thread.
+  std::vector<int> order(static_cast<size_t>(n));
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    const int oa = descs[a].op == ATLAS_OP_DIVERGENCE, oc = descs[c].op == ATLAS_OP_DIVERGENCE;
+    if (oa != oc) return oa > oc;
+    return descs[a].nlev > descs[c].nlev;
+  });
   int device = -1;
   std::vector<atlas_fvm_s*> fv;
   // one levels-per-thread width for the whole batch: the widest every field allows
@@ -912,8 +923,10 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     const void* used[3] = {d.in0, grad ? d.out0 : d.in1, grad ? d.out1 : d.out0};
     vec = std::min(vec, pick_vec(dtype, d.ld, used, 3, want_vec));
   }
-  if (threads > 512) return fail(ATLAS_EINVAL, "batch threads must be <= 512");
-  for (int k = 0; k < n; ++k) {
+  if (threads > atlasgb::kBatchMaxThreads)
+    return fail(ATLAS_EINVAL, "batch threads must be <= %d", atlasgb::kBatchMaxThreads);
+  for (int slot = 0; slot < n; ++slot) {
+    const int k = order[slot];
     const atlas_batch_desc& d = descs[k];
     atlas_fvm_s* f = get_fvm(d.fvm);
     if (!f) return fail(ATLAS_ESTATE, "descriptor %d: invalid fvm handle", k);
@@ -932,7 +945,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
       if (rc) return rc;
     }
     const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][dtype].dev;
-    atlasgb::BatchDescDev& o = hd[k];
+    atlasgb::BatchDescDev& o = hd[slot];
     o.ptr = s.ptr;
     o.nbr = s.nbr;
     o.w = s.w;
@@ -942,36 +955,30 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     o.out0 = d.out0;
     o.out1 = grad ? d.out1 : nullptr;
     o.ld = d.ld;
-    o.nnodes = s.nnodes;
     o.nlev = d.nlev;
-    o.vec = vec;
     o.nvec = (d.nlev + vec - 1) / vec;
-    o.items = static_cast<int64_t>(s.nnodes) * o.nvec;
-    if (o.items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "descriptor %d too large", k);
+    const int64_t items = static_cast<int64_t>(s.nnodes) * o.nvec;
+    if (items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "descriptor %d too large", k);
+    o.items = static_cast<int32_t>(items);
     o.op = grad ? 0 : 1;
     const atlasgb::Div32 dv = atlasgb::make_div32(static_cast<uint32_t>(o.nvec));
     o.div_m = dv.m;
     o.div_s1 = dv.s1;
     o.div_s2 = dv.s2;
     if (static_cast<int64_t>(s.nnodes) * d.ld >= (int64_t(1) << 31)) idx32 = false;
-    o.tile0 = tiles;
-    tiles += (o.items + tile_items - 1) / tile_items;
+    o.tile0 = static_cast<int32_t>(tiles);
+    tiles += (items + tile_items - 1) / tile_items;
+    if (tiles >= (int64_t(1) << 30)) return fail(ATLAS_EINVAL, "too many tiles: raise tile_items");
     nl += static_cast<int64_t>(s.nnodes) * d.nlev;
     fv.push_back(f);
   }
   atlas_batch_s* b = new (std::nothrow) atlas_batch_s();
   if (!b) return fail(ATLAS_ENOMEM, "out of host memory");
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_desc), sizeof(atlasgb::BatchDescDev) * n);
-  if (e != cudaSuccess) {
-    delete b;
-    return cuda_fail(e, "cudaMalloc (batch descriptors)");
-  }
-  e = cudaMemcpy(b->d_desc, hd.data(), sizeof(atlasgb::BatchDescDev) * n, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(b->d_desc);
-    delete b;
-    return cuda_fail(e, "cudaMemcpy (batch descriptors)");
-  }
+  std::memset(&b->params, 0, sizeof(b->params));
+  b->params.ndesc = n;
+  b->params.ntiles = static_cast<int32_t>(tiles);
+  b->params.tile_items = tile_items;
+  for (int k = 0; k < n; ++k) b->params.d[k] = hd[k];
   b->fvms = fv;
   for (atlas_fvm_s* f : fv) f->users++;
   b->ndesc = n;
@@ -983,7 +990,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   b->device = device;
   b->vec = vec;
   b->idx32 = idx32;
-  int bps = atlasgb::batch_occupancy(b->st, vec, idx32, threads, n);
+  int bps = atlasgb::batch_occupancy(b->st, vec, idx32, threads);
   if (t.blocks_per_sm > 0) bps = std::min(bps, t.blocks_per_sm);
   const int64_t blocks = std::min<int64_t>(static_cast<int64_t>(fv[0]->num_sms) * bps, std::max<int64_t>(tiles, 1));
   b->blocks = static_cast<int>(blocks);
@@ -999,8 +1006,8 @@ int atlas_batch_launch(atlas_batch_t h, void* stream) {
   if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device)
     return fail(ATLAS_ESTATE, "batch lives on device %d, current device is %d", b->device, cur);
   if (b->ntiles == 0) return ok();
-  cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->idx32, b->d_desc, b->ndesc, b->ntiles, b->tile_items, b->threads,
-                                        b->blocks, static_cast<cudaStream_t>(stream));
+  cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->idx32, b->params, b->threads, b->blocks,
+                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return ok();
 }
@@ -1018,7 +1025,6 @@ void atlas_batch_destroy(atlas_batch_t h) {
   atlas_batch_s* b = reinterpret_cast<atlas_batch_s*>(h);
   unreg(b);
   for (atlas_fvm_s* f : b->fvms) f->users--;
-  cudaFree(b->d_desc);
   delete b;
 }
 

@@ -64,7 +64,7 @@ struct DevEdges {
 };
 
 // Persistent batched launch: one descriptor per field.
-struct alignas(16) BatchDescDev {
+struct BatchDescDev {
   const int32_t* ptr;
   const int32_t* nbr;
   const void* w;
@@ -74,18 +74,25 @@ struct alignas(16) BatchDescDev {
   void* out0;
   void* out1;
   int64_t ld;
-  int64_t items;      // nnodes * nvec
-  int64_t tile0;      // first tile of this descriptor
-  int32_t nnodes;
+  int32_t tile0;      // first tile of this descriptor
+  int32_t items;      // nnodes * nvec (< 2^31)
   int32_t nlev;
   int32_t nvec;
   int32_t op;         // 0 gradient (1 in, 2 out), 1 divergence (2 in, 1 out, with b)
-  int32_t vec;
   uint32_t div_m;     // division by nvec (see Div32)
   uint32_t div_s1, div_s2;
-  uint32_t pad[2];
 };
-static_assert(sizeof(BatchDescDev) % 16 == 0, "descriptors are copied to shared memory in 16-byte words");
+// The whole table travels as one kernel parameter (at most 32 KB).
+constexpr int kBatchMaxDesc = 256;
+constexpr int kBatchMaxThreads = 256;  // the batch kernel's launch bound
+struct BatchParams {
+  int32_t ndesc;
+  int32_t ntiles;
+  int32_t tile_items;
+  int32_t pad;
+  BatchDescDev d[kBatchMaxDesc];
+};
+static_assert(sizeof(BatchParams) <= 32764, "kernel parameters are limited to 32764 bytes");
 
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream);
 // Maximum resident blocks per SM of the stencil kernel for this configuration.
@@ -104,8 +111,8 @@ Div32 make_div32(uint32_t d);
 // address on the current device (looked up once per device).
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(void** ptr);
-cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchDescDev* descs, int ndesc, int64_t ntiles,
-                         int tile_items, int threads, int blocks, cudaStream_t stream);
-int batch_occupancy(StorageType st, int vec, bool idx32, int threads, int ndesc);
+cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchParams& params, int threads, int blocks,
+                         cudaStream_t stream);
+int batch_occupancy(StorageType st, int vec, bool idx32, int threads);
 
 }  // namespace atlasgb

@@ -129,7 +129,7 @@ def tune_batch(make, candidates=None, reps=5, verbose=False):
     """make(tune_dict) -> Batch; returns (best Batch, best tune, sweep)."""
     if candidates is None:
         candidates = [dict(vec=v, tile_items=t, threads=th, blocks_per_sm=0)
-                      for v in (4, 2) for t in (1024, 4096, 16384) for th in (128, 256, 512)]
+                      for v in (4, 2) for t in (256, 1024, 4096) for th in (128, 256)]
     sweep = []
     best = None
     for c in candidates:
