@@ -228,6 +228,25 @@ def _table_bytes(fvm, op, wbytes):
     return 4 * (V + 1) + nnz * (4 + nw * wbytes) + (2 * wbytes * V if has_b else 0)
 
 
+# Nominal FP64 rate of a GB300 at its maximum SM clock (2070 MHz): the FP64
+# kernels are bound by the FP64 pipe, not by HBM.
+FP64_PEAK_TFLOPS, SM_MAX_MHZ = 1.25, 2070.0
+
+
+def _fp64_flops(fvm, op, nlev):
+    """Algorithmic FP64 flops of one launch (an FMA counts 2): every CSR entry
+    costs one subtraction per input and one FMA per (input, output) weight;
+    the B term costs one FMA per (input, output) pair and node."""
+    if op not in _NNZ:
+        _NNZ[op] = fvm.stencil_table(op)["nbr"].shape[0]
+    nnz, V = _NNZ[op], fvm.nnodes
+    per_entry = {"gradient": 1 + 2 * 2, "divergence_adjoint": 1 + 2 * 2, "laplacian": 1 + 2,
+                 "divergence": 2 + 2 * 2, "gradient_adjoint": 2 + 2 * 2}[op]
+    per_node = {"gradient": 0, "laplacian": 0, "divergence_adjoint": 2 * 2, "divergence": 2 * 2,
+                "gradient_adjoint": 2 * 2}[op]
+    return (nnz * per_entry + V * per_node) * nlev
+
+
 def _cpu_baseline(grid, fvm_nodes, f_host, u_host, v_host, nlev, budget_s=12.0):
     """The oracle as it stands, single-threaded, on a contiguous node sample
     of the same workload (all five operators)."""
@@ -382,6 +401,16 @@ def run_native(args):
                 bytes_ = _alg_bytes(op, V, nlev, es, _table_bytes(fvm, op, wb) if name == "fp64" else tables[op])
                 entry["per_op"][op] = {"ms": round(ms, 4), "node_levels_per_s": V * nlev / (ms * 1e-3),
                                        "frac_hbm": round(bytes_ / (ms * 1e-3) / 1e9 / hbm, 4)}
+                if name == "fp64":
+                    tf = _fp64_flops(fvm, op, nlev) / (ms * 1e-3) / 1e12
+                    entry["per_op"][op]["fp64_tflops"] = round(tf, 4)
+                    entry["per_op"][op]["frac_fp64"] = round(tf / FP64_PEAK_TFLOPS, 4)
+            if name == "fp64":
+                dom = max(OPS, key=lambda o: entry["per_op"][o]["ms"])
+                entry["roofline"] = {"bound": "alu", "operator": dom,
+                                     "achieved": entry["per_op"][dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                                     "unit": "TFLOP/s", "frac": entry["per_op"][dom]["frac_fp64"],
+                                     "peak_kind": "nominal FP64 rate at %d MHz" % SM_MAX_MHZ}
             side[name] = entry
             del fx, ux, vx, ox
             torch.cuda.empty_cache()

@@ -152,9 +152,12 @@ int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 /* Launch shape of the node-stencil kernels for one operator: levels per   */
 /* thread (vec: 1, 2, 4 or 8; 0 = default for the dtype), CSR entries per */
 /* load batch (batch: 3 or 6), threads per block (64..512, multiple of    */
-/* 32) and blocks per SM (1..32).  Any zero field keeps the current value; */
-/* results are bitwise identical for every shape.                          */
-int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int batch, int threads, int blocks_per_sm);
+/* 32), blocks per SM (1..32) and tile_passes (1..4096): each block walks */
+/* tiles of tile_passes * threads consecutive (node, level-vector) items, */
+/* 1 being a plain grid-stride loop (default).  Any zero field keeps the  */
+/* current value; results are bitwise identical for every shape.          */
+int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int batch, int threads, int blocks_per_sm,
+                         int tile_passes);
 /* Inspection: copy out the FP64 host table of one operator's node stencil */
 /*   out_c(i) = sum_{q in [ptr[i], ptr[i+1])} sum_m W_cm(q) (x_m(nbr[q]) - x_m(i))  */
 /*              + sum_m B_cm(i) x_m(i)                                     */

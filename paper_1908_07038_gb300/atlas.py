@@ -164,9 +164,9 @@ class Fvm:
                                      w.ctypes.data, b.ctypes.data)
         return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
 
-    def set_launch(self, op, vec=0, batch=0, threads=0, blocks_per_sm=0):
+    def set_launch(self, op, vec=0, batch=0, threads=0, blocks_per_sm=0, tile_passes=0):
         capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(vec), int(batch), int(threads),
-                                  int(blocks_per_sm))
+                                  int(blocks_per_sm), int(tile_passes))
 
     # ---------------------------------------------------------- operators
     def _check(self, *ts):

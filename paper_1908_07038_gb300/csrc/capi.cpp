@@ -112,6 +112,7 @@ struct LaunchCfg {
   int batch = 6;
   int threads = 128;
   int blocks_per_sm = 0;  // 0 = occupancy limit
+  int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
 };
 }  // namespace
 
@@ -393,6 +394,13 @@ int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void
   l.batch = c.batch;
   const StorageType st = storage_of(dtype);
   l.blocks = grid_blocks(f, st, f->st[op][dtype].dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
+  {
+    // items the kernel walks (node pairs for a pair table); a tile is at most
+    // one block's even share, so blocks * tile stays below 2^31 + blocks * threads
+    const int64_t walked = f->st[op][dtype].dev.pair ? items / 2 : items;
+    const int64_t share = ((walked + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
+    l.tile = static_cast<uint32_t>(std::max<int64_t>(l.threads, std::min<int64_t>(int64_t(c.tile_passes) * l.threads, share)));
+  }
   cudaError_t e = atlasgb::launch_stencil(st, f->st[op][dtype].dev, l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
   return ok();
@@ -657,7 +665,7 @@ int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
   return ok();
 }
 
-int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int batch, int threads, int blocks_per_sm) {
+int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int batch, int threads, int blocks_per_sm, int tile_passes) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
@@ -666,11 +674,13 @@ int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int batch, int threads,
   if (threads != 0 && (threads < 64 || threads > 512 || threads % 32 != 0))
     return fail(ATLAS_EINVAL, "threads must be a multiple of 32 in [64, 512]");
   if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(ATLAS_EINVAL, "blocks_per_sm must be in [0, 32]");
+  if (tile_passes < 0 || tile_passes > 4096) return fail(ATLAS_EINVAL, "tile_passes must be in [0, 4096]");
   std::lock_guard<std::mutex> lk(f->mu);
   if (vec) f->cfg[op].vec = vec;
   if (batch) f->cfg[op].batch = batch;
   if (threads) f->cfg[op].threads = threads;
   if (blocks_per_sm) f->cfg[op].blocks_per_sm = blocks_per_sm;
+  if (tile_passes) f->cfg[op].tile_passes = tile_passes;
   return ok();
 }
 

@@ -220,6 +220,24 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
   if constexpr (NOUT == 2) vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
 }
 
+// The items of a launch are cut into tiles of `tile` consecutive items
+// (a multiple of blockDim.x); block b takes tiles b, b + gridDim.x, ...  and
+// its threads walk each tile in passes of blockDim.x items.  With tile =
+// blockDim.x this is the plain grid-stride loop: all resident blocks work on
+// one contiguous window of the fields, which keeps the DRAM pages and TLB
+// entries in use few.  Longer tiles let a block walk consecutive nodes, so
+// the neighbour rows that one pass loads are largely those the next pass
+// needs and are still in the SM's L1; that helps the two-ring Laplacian and
+// hurts the one-ring operators, whose reads are mostly from DRAM (measured).
+// The host keeps gridDim.x * tile below 2^31, so no sum here overflows.
+template <typename F>
+__device__ __forceinline__ void for_each_item(uint32_t total, uint32_t tile, F&& f) {
+  for (uint32_t t0 = blockIdx.x * tile; t0 < total; t0 += gridDim.x * tile) {
+    const uint32_t t1 = t0 + tile < total ? t0 + tile : total;
+    for (uint32_t item = t0 + threadIdx.x; item < t1; item += blockDim.x) f(item);
+  }
+}
+
 // n / d for a divisor fixed per launch: t = umulhi(m, n), q = (t + ((n - t) >> s1)) >> s2
 // (branch-free unsigned division by an invariant integer; exact for all 32-bit n).
 __device__ __forceinline__ uint32_t div_by(uint32_t n, Div32 d) {
@@ -232,15 +250,15 @@ __global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict_
                                                       const A* __restrict__ w, const A* __restrict__ b,
                                                       const S* __restrict__ in0, const S* __restrict__ in1,
                                                       S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
-                                                      int32_t nlev, int64_t ld, uint32_t nvec, Div32 dv) {
+                                                      int32_t nlev, int64_t ld, uint32_t nvec, Div32 dv,
+                                                      uint32_t tile) {
   const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;  // host guarantees < 2^31
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+  for_each_item(total, tile, [&](uint32_t item) {
     const uint32_t i = div_by(item, dv);
     const uint32_t v = item - i * nvec;
     stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, IDX32>(
         ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev, static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
-  }
+  });
 }
 
 // ----------------------------------------------------- node-pair stencil
@@ -272,12 +290,11 @@ template <typename S, typename A, int VEC, int BATCH, bool IDX32>
 __global__ void __launch_bounds__(512) pair_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                                                    const A* __restrict__ w, const S* __restrict__ in0,
                                                    S* __restrict__ out0, int32_t npairs, int32_t nlev, int64_t ld,
-                                                   uint32_t nvec, Div32 dv) {
+                                                   uint32_t nvec, Div32 dv, uint32_t tile) {
   using Idx = typename IdxT<IDX32>::T;
   const Idx ldx = static_cast<Idx>(ld);
   const uint32_t total = static_cast<uint32_t>(npairs) * nvec;  // host guarantees < 2^31
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+  for_each_item(total, tile, [&](uint32_t item) {
     const uint32_t g = div_by(item, dv);
     const int32_t lev0 = static_cast<int32_t>((item - g * nvec) * VEC);
     const int32_t ia = static_cast<int32_t>(2 * g);
@@ -320,7 +337,7 @@ __global__ void __launch_bounds__(512) pair_kernel(const int32_t* __restrict__ p
     const int nvalid = nlev - lev0;
     vstore<S, A, VEC>(out0 + oa, ca, nvalid);
     vstore<S, A, VEC>(out0 + ob, cb, nvalid);
-  }
+  });
 }
 
 // ------------------------------------------------------------- edge pass
@@ -493,12 +510,12 @@ cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_
     stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
         static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec,
-        dv);
+        dv, l.tile);
   else
     stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
         static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec,
-        dv);
+        dv, l.tile);
   return cudaGetLastError();
 }
 
@@ -581,11 +598,11 @@ cudaError_t run_pair(const DevStencil& s, const StencilLaunch& l, cudaStream_t s
   if (idx32)
     pair_kernel<S, A, VEC, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), npairs,
-        l.nlev, l.ld, nvec, dv);
+        l.nlev, l.ld, nvec, dv, l.tile);
   else
     pair_kernel<S, A, VEC, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), npairs,
-        l.nlev, l.ld, nvec, dv);
+        l.nlev, l.ld, nvec, dv, l.tile);
   return cudaGetLastError();
 }
 

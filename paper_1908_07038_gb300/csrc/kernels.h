@@ -49,7 +49,8 @@ struct StencilLaunch {
   int vec = 1;
   int batch = 6;   // CSR entries whose neighbour values are requested together (3 or 6)
   int threads = 256;
-  int blocks = 0;  // grid size (grid-stride loop over all items)
+  int blocks = 0;  // grid size
+  uint32_t tile = 0;  // items per block tile: a multiple of threads, blocks * tile < 2^31
 };
 
 // Edge-based two-pass data on the device.

@@ -1,8 +1,9 @@
 """Autotuner of the launch shapes of the nabla kernels.
 
-For every operator the node-stencil kernel has four free parameters that do
+For every operator the node-stencil kernel has five free parameters that do
 not change its result (bitwise): levels per thread (``vec``), CSR entries per
-load batch (``batch``), threads per block and blocks per SM.  ``tune_fvm``
+load batch (``batch``), threads per block, blocks per SM and the length of
+the item tile each block walks (``tile``, in passes of the block).  ``tune_fvm``
 times each candidate with CUDA events on the real field sizes and installs
 the fastest with ``atlas_fvm_set_launch``; ``tune_batch`` does the same for
 the tile size and block shape of a persistent batched launch.  Results are
@@ -19,9 +20,9 @@ from . import atlas
 from .capi import ATLAS_BF16, ATLAS_F32, ATLAS_F64
 
 CANDIDATES = {
-    ATLAS_F32: dict(vec=(4, 2), batch=(6, 3), threads=(128, 256, 512), bps=(0,)),
-    ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,)),
-    ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,)),
+    ATLAS_F32: dict(vec=(4, 2), batch=(6, 3), threads=(128, 256, 512), bps=(0,), tile=(1, 8, 64)),
+    ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8)),
+    ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8, 64)),
 }
 _TORCH_DT = None
 
@@ -104,23 +105,26 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         key = key_base + "|" + op
         if key in cache:
             c = cache[key]
-            fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"])
+            fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1))
             best[op] = c
             continue
         ins = (fields[1], fields[2]) if op in ("divergence", "gradient_adjoint") else (fields[0],)
         cand = CANDIDATES[dtype]
         results = []
-        for vec, batch, threads, bps in itertools.product(cand["vec"], cand["batch"], cand["threads"], cand["bps"]):
-            fvm.set_launch(op, vec, batch, threads, bps)
+        for vec, batch, threads, bps, tile in itertools.product(cand["vec"], cand["batch"], cand["threads"],
+                                                                cand["bps"], cand["tile"]):
+            fvm.set_launch(op, vec, batch, threads, bps, tile)
             ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
-            results.append((ms, vec, batch, threads, bps))
+            results.append((ms, vec, batch, threads, bps, tile))
             if verbose:
-                print("tune %-18s vec=%d batch=%d threads=%d bps=%d: %.4f ms" % (op, vec, batch, threads, bps, ms))
-        ms, vec, batch, threads, bps = min(results)
-        fvm.set_launch(op, vec, batch, threads, bps)
-        best[op] = dict(vec=vec, batch=batch, threads=threads, bps=bps, ms=ms,
-                        sweep=[dict(ms=r[0], vec=r[1], batch=r[2], threads=r[3], bps=r[4]) for r in results])
-        cache[key] = {k: best[op][k] for k in ("vec", "batch", "threads", "bps", "ms")}
+                print("tune %-18s vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
+                      (op, vec, batch, threads, bps, tile, ms))
+        ms, vec, batch, threads, bps, tile = min(results)
+        fvm.set_launch(op, vec, batch, threads, bps, tile)
+        best[op] = dict(vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, ms=ms,
+                        sweep=[dict(ms=r[0], vec=r[1], batch=r[2], threads=r[3], bps=r[4], tile=r[5])
+                               for r in results])
+        cache[key] = {k: best[op][k] for k in ("vec", "batch", "threads", "bps", "tile", "ms")}
     _store_cache(cache)
     return best
 

@@ -186,17 +186,18 @@ def test_gradient_of_constant_is_exactly_zero_on_gpu(torch, pfvm):
 
 
 def test_deterministic_and_launch_shape_independent(torch, product):
-    """No atomics: repeated runs and every levels-per-thread / block shape give
-    bitwise identical results."""
+    """No atomics: repeated runs and every levels-per-thread / block / tile
+    shape give bitwise identical results."""
     atlas, _ = product
     fvm = atlas.build_fvm(32)
     rng = np.random.default_rng(11)
     f = _dev(torch, rng.standard_normal((fvm.nnodes, 40)).astype(np.float32))
     ref = [t.clone() for t in fvm.gradient(f)]
     lref = fvm.laplacian(f).clone()
-    for vec, batch, threads, bps in ((1, 3, 128, 2), (2, 6, 512, 1), (4, 3, 256, 0), (4, 6, 64, 3)):
-        fvm.set_launch("gradient", vec, batch, threads, bps)
-        fvm.set_launch("laplacian", vec, batch, threads, bps)
+    for vec, batch, threads, bps, tile in ((1, 3, 128, 2, 1), (2, 6, 512, 1, 4), (4, 3, 256, 0, 64),
+                                           (4, 6, 64, 3, 4096), (4, 3, 96, 0, 7)):
+        fvm.set_launch("gradient", vec, batch, threads, bps, tile)
+        fvm.set_launch("laplacian", vec, batch, threads, bps, tile)
         gx, gy = fvm.gradient(f)
         lap = fvm.laplacian(f)
         torch.cuda.synchronize()
