@@ -154,8 +154,10 @@ int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 /* load batch (batch: 3 or 6), threads per block (64..512, multiple of    */
 /* 32), blocks per SM (1..32) and tile_passes (1..4096): each block walks */
 /* tiles of tile_passes * threads consecutive (node, level-vector) items, */
-/* 1 being a plain grid-stride loop (default).  Any zero field keeps the  */
-/* current value; results are bitwise identical for every shape.          */
+/* 1 being a plain grid-stride loop (default).  Tiles apply to BF16       */
+/* fields and to the F32 Laplacian; the other F32 and F64 kernels always  */
+/* run a grid-stride loop.  Any zero field keeps the current value;       */
+/* results are bitwise identical for every shape.                          */
 int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int batch, int threads, int blocks_per_sm,
                          int tile_passes);
 /* Inspection: copy out the FP64 host table of one operator's node stencil */

@@ -19,9 +19,11 @@ import os
 from . import atlas
 from .capi import ATLAS_BF16, ATLAS_F32, ATLAS_F64
 
+# The tile length applies to bfloat16 fields and to the FP32 Laplacian (node
+# pairs); the other FP32 and FP64 kernels walk a grid-stride loop.
 CANDIDATES = {
-    ATLAS_F32: dict(vec=(4, 2), batch=(6, 3), threads=(128, 256, 512), bps=(0,), tile=(1, 8, 64)),
-    ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8)),
+    ATLAS_F32: dict(vec=(4, 2), batch=(6, 3), threads=(128, 256, 512), bps=(0,), tile=(1, 8)),
+    ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1,)),
     ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8, 64)),
 }
 _TORCH_DT = None

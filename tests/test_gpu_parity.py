@@ -192,16 +192,20 @@ def test_deterministic_and_launch_shape_independent(torch, product):
     fvm = atlas.build_fvm(32)
     rng = np.random.default_rng(11)
     f = _dev(torch, rng.standard_normal((fvm.nnodes, 40)).astype(np.float32))
+    fb = f.to(torch.bfloat16)
     ref = [t.clone() for t in fvm.gradient(f)]
     lref = fvm.laplacian(f).clone()
+    bref = [t.clone() for t in fvm.gradient(fb)]
     for vec, batch, threads, bps, tile in ((1, 3, 128, 2, 1), (2, 6, 512, 1, 4), (4, 3, 256, 0, 64),
-                                           (4, 6, 64, 3, 4096), (4, 3, 96, 0, 7)):
+                                           (4, 6, 64, 3, 4096), (4, 3, 96, 0, 7), (8, 3, 128, 0, 8)):
         fvm.set_launch("gradient", vec, batch, threads, bps, tile)
         fvm.set_launch("laplacian", vec, batch, threads, bps, tile)
         gx, gy = fvm.gradient(f)
         lap = fvm.laplacian(f)
+        bx, by = fvm.gradient(fb)
         torch.cuda.synchronize()
         assert torch.equal(gx, ref[0]) and torch.equal(gy, ref[1]) and torch.equal(lap, lref)
+        assert torch.equal(bx, bref[0]) and torch.equal(by, bref[1])
 
 
 def test_empty_and_offset_views(torch, pfvm, omesh):
