@@ -457,7 +457,7 @@ def run_native(args):
         "config": {"workload": "O%d octahedral grid (%d nodes, %d edges) x %d levels, field[node][ld=%d] FP32, "
                                "FP64-built geometry; step = gradient + divergence + Laplacian + gradient adjoint "
                                "+ divergence adjoint" % (args.grid, V, fvm.mesh.nedges, nlev, ld),
-                   "l2": "inputs larger than L2 (3.7 GB per field), no flush", "parallelism": "replicas" if ws > 1 else "single"},
+                   "l2": "inputs larger than L2 (%.2f GB per field, L2 129 MB), no flush" % (V * ld * 4 / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline, "per_op": {k: {"ms": v_["ms"], "node_levels_per_s": v_["node_levels_per_s"],
                                              "frac_hbm": round(v_["frac"], 4)} for k, v_ in per.items()},
         "side_by_side": side, "batched": batched, "tuned": {k: {kk: t[kk] for kk in ("vec", "batch", "threads")}
