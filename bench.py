@@ -44,6 +44,24 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(value, ws, device):
+    """The largest of one float per rank (a job takes as long as its slowest
+    rank); every rank gets it.  ws == 1 needs no process group."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, ws, ms):
+    """Whole-job throughput: the units all ranks processed over the time of the
+    slowest rank (milliseconds)."""
+    return ws * units_per_rank / (ms * 1e-3)
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_o1280.json")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1908_07038_gb300", "csrc", "kernels.cu")
 
@@ -306,13 +324,10 @@ def run_native(args):
     sampler.start()
     total_ms, per_op = _time_ops(torch, fvm, f, u, v, outs, nlev, args.steps, args.warmup, barrier)
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(total_ms, ws, "cuda")
     ms_step = total_ms / args.steps
     node_levels_step = 5 * V * nlev
-    value = ws * node_levels_step / (ms_step * 1e-3)
+    value = _job_rate(node_levels_step, ws, ms_step)
 
     # per-op roofline (algorithmic bytes / average kernel time)
     tables = {op: _table_bytes(fvm, op, 4) for op in OPS}
@@ -353,7 +368,7 @@ def run_native(args):
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e_ms = a.elapsed_time(b) / ksteps
+        e_ms = _max_over_ranks(a.elapsed_time(b) / ksteps, ws, "cuda")
         # the serial form on one stream
         nbytes = hs.nbytes
         sout = [hout[n] for n in ("gx", "gy", "div", "lap", "ga", "du", "dv")]
@@ -373,7 +388,7 @@ def run_native(args):
         b.record(stream)
         torch.cuda.synchronize()
         s_ms = a.elapsed_time(b) / 2
-        e2e = {"value": ws * node_levels_step / (e_ms * 1e-3), "unit": "node-levels/s",
+        e2e = {"value": _job_rate(node_levels_step, ws, e_ms), "unit": "node-levels/s",
                "h2d_bytes_per_step": hs.h2d_bytes, "d2h_bytes_per_step": hs.d2h_bytes, "ms_per_step": round(e_ms, 3),
                "steps": ksteps, "link_gbs": round((hs.h2d_bytes + hs.d2h_bytes) / (e_ms * 1e-3) / 1e9, 1),
                "pipelined": True, "serial_ms_per_step": round(s_ms, 3)}

@@ -1,0 +1,64 @@
+"""Host-side logic of the multi-rank benchmark, on CPU with the gloo backend.
+
+The operators need no exchange, so under torchrun every rank runs an
+independent replica; what the ranks share is the timing rule (the job takes
+as long as its slowest rank) and the throughput rule (all ranks' units over
+that time), and only rank 0 prints.  Two ranks run here as processes on CPU."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        # rank r "took" 10 + 5 r ms; every rank must see the slowest
+        slowest = bench._max_over_ranks(10.0 + 5.0 * rank, world, "cpu")
+        rate = bench._job_rate(1000, world, slowest)
+        with open(os.path.join(out_dir, "rank%d.txt" % rank), "w") as fh:
+            fh.write("%r %r\n" % (slowest, rate))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_rate_two_gloo_ranks(tmp_path):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    world, port = 2, _free_port()
+    mp.spawn(_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    for r in range(world):
+        slowest, rate = (float(x) for x in (tmp_path / ("rank%d.txt" % r)).read_text().split())
+        assert slowest == 15.0
+        assert rate == pytest.approx(world * 1000 / 15e-3, rel=1e-15)
+    del torch
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench._max_over_ranks(3.5, 1, "cpu") == 3.5
+    assert bench._job_rate(10, 1, 2.0) == pytest.approx(5000.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun the oracle arm runs on rank 0; other ranks return at once
+    without work or output."""
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.run_reference(None) is None
+    assert capsys.readouterr().out == ""
