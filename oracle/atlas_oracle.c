@@ -695,6 +695,101 @@ int orc_laplacian(const orc_mesh *m, const void *f, int f32, int64_t ld, int nle
 }
 
 /* ------------------------------------------------------------------------ */
+/* Curl and vector gradient (the paper lists nabla operators on fields as   */
+/* provided by the library, Sec. 2.3; these two extend the scalar ones to    */
+/* tangent vector fields in physical components).                            */
+/* ------------------------------------------------------------------------ */
+
+/* vertical vorticity of the tangent vector (u, v) at node i:
+ *   zeta = (1/(R cos)) [d_lambda v - d_phi (u cos)].
+ * Stokes' theorem on the dual cell: V_i zeta_i is the circulation of (u, v)
+ * around the cell boundary, the integral of u R cos dlambda + v R dphi.  On
+ * a face whose outward normal is n = R (dphi, -dlambda), that line element
+ * is v n_lambda - (u cos) n_phi, so the circulation is the flux of
+ * G = (v, -u cos) through the faces, with the face mean of G; the pole
+ * segments carry none (dphi = 0 and cos = 0 there).  Closure-exact form, as
+ * for the divergence: sum_{regular e} n . (G_j - G_i)/2 - G_i . n_pole,i. */
+static void curl_node(const orc_mesh *m, const void *u, const void *v, int f32, int64_t ld, int nlev,
+                      int64_t i, double *out) {
+  double ci = m->coslat[i];
+  for (int k = 0; k < nlev; ++k) {
+    acc_t a = {0, 0};
+    double ui = fld(u, f32, ld, i, k), vi = fld(v, f32, ld, i, k);
+    for (int32_t p = m->n2e_ptr[i]; p < m->n2e_ptr[i + 1]; ++p) {
+      int64_t e = m->n2e[p];
+      if (m->is_pole[e]) continue;
+      double nl, np;
+      face_normal(m, p, &nl, &np);
+      int32_t j = far_end(m, e, i);
+      double dv = 0.5 * (fld(v, f32, ld, j, k) - vi);
+      double duc = 0.5 * diff_of_products(fld(u, f32, ld, j, k), m->coslat[j], ui, ci);
+      acc_add_prod(&a, nl, dv);
+      acc_add_prod(&a, -np, duc);
+    }
+    if (m->pole_nphi[i] != 0.0) {
+      /* - G_i . n_pole = + (u cos)_i n_pole,phi */
+      double pu, eu;
+      two_prod(ui, ci, &pu, &eu);
+      acc_add_prod(&a, m->pole_nphi[i], pu);
+      acc_add_prod(&a, m->pole_nphi[i], eu);
+    }
+    out[k] = acc_val(&a) / m->V[i];
+  }
+}
+
+/* gradient of one physical component f of a tangent vector field at node i.
+ * As the scalar gradient, except on the pole segment: a polar node and its
+ * pole-edge neighbour (the node half a turn away on the same row) have
+ * opposite local east and north directions, so the neighbour's component
+ * enters the pole-face mean with its sign reversed, face value (f_i - f_j)/2.
+ * In closure-exact form that face contributes n_pole ((f_i - f_j)/2 - f_i)
+ * = -n_pole (f_i + f_j)/2. */
+static void vgrad_comp_node(const orc_mesh *m, const void *f, int f32, int64_t ld, int nlev, int64_t i,
+                            double *gx, double *gy) {
+  for (int k = 0; k < nlev; ++k) {
+    acc_t al = {0, 0}, ap = {0, 0};
+    double fi = fld(f, f32, ld, i, k);
+    for (int32_t p = m->n2e_ptr[i]; p < m->n2e_ptr[i + 1]; ++p) {
+      double nl, np;
+      face_normal(m, p, &nl, &np);
+      int64_t e = m->n2e[p];
+      int32_t j = far_end(m, e, i);
+      double fj = fld(f, f32, ld, j, k);
+      double d = m->is_pole[e] ? -0.5 * (fj + fi) : 0.5 * (fj - fi);
+      acc_add_prod(&al, nl, d);
+      acc_add_prod(&ap, np, d);
+    }
+    gx[k] = acc_val(&al) / m->V[i];
+    gy[k] = m->coslat[i] * acc_val(&ap) / m->V[i];
+  }
+}
+
+int orc_curl(const orc_mesh *m, const void *u, const void *v, int f32, int64_t ld, int nlev,
+             const int64_t *nodes, int64_t count, double *out) {
+  if (!m || !u || !v || nlev < 0 || ld < nlev || check_nodes(m, nodes, count)) return -1;
+  int64_t n = nsel(m, nodes, count);
+  for (int64_t q = 0; q < n; ++q) {
+    int64_t i = nodes ? nodes[q] : q;
+    curl_node(m, u, v, f32, ld, nlev, i, out + q * nlev);
+  }
+  return 0;
+}
+
+/* (ux, uy) = gradient of u, (vx, vy) = gradient of v, components of one
+ * tangent vector field; outputs packed [count][nlev]. */
+int orc_vector_gradient(const orc_mesh *m, const void *u, const void *v, int f32, int64_t ld, int nlev,
+                        const int64_t *nodes, int64_t count, double *ux, double *uy, double *vx, double *vy) {
+  if (!m || !u || !v || nlev < 0 || ld < nlev || check_nodes(m, nodes, count)) return -1;
+  int64_t n = nsel(m, nodes, count);
+  for (int64_t q = 0; q < n; ++q) {
+    int64_t i = nodes ? nodes[q] : q;
+    vgrad_comp_node(m, u, f32, ld, nlev, i, ux + q * nlev, uy + q * nlev);
+    vgrad_comp_node(m, v, f32, ld, nlev, i, vx + q * nlev, vy + q * nlev);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoints: the exact transposes of the linear maps above, written as the  */
 /* explicit matrix rows of the forward operator and applied transposed.     */
 /* Row i of the gradient (component c) has the off-diagonal entries          */

@@ -6,8 +6,9 @@ product package and the product never imports it.
 
 The oracle computes, in plain FP64 C, the octahedral reduced Gaussian grid,
 its zipper triangulation with pole edges, the median-dual geometry and the
-nabla operators (gradient, divergence, Laplacian and the adjoints of gradient
-and divergence) that Atlas supplies (paper Sec. 2.3).  The formulas and the
+nabla operators (gradient, divergence, Laplacian, the adjoints of gradient
+and divergence, curl and the gradient of a tangent vector field) that Atlas
+supplies (paper Sec. 2.3).  The formulas and the
 readings they follow are stated beside each function in ``atlas_oracle.c``.
 Every function here is pinned by ``tests/test_oracle_*.py``.
 """
@@ -63,6 +64,8 @@ def _load():
         lib.orc_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
         lib.orc_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
         lib.orc_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+        lib.orc_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_vector_gradient.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P, P, P]
         lib.orc_gradient_triplets.restype = i64
         lib.orc_gradient_triplets.argtypes = [P, P, P, P]
         lib.orc_divergence_triplets.restype = i64
@@ -70,7 +73,8 @@ def _load():
         lib.orc_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
         lib.orc_closure.argtypes = [P, P, P]
         for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
-                     "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes"):
+                     "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
+                     "orc_vector_gradient"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -182,6 +186,36 @@ class Mesh:
         if rc:
             raise ValueError("orc_divergence rc=%d" % rc)
         return out
+
+    def curl(self, u, v, nlev=None, nodes=None):
+        """Vertical vorticity of the tangent vector (u, v) (Stokes on the dual cell)."""
+        u, f32, ld = _field(u)
+        v, f32v, ldv = _field(v)
+        if (f32, ld) != (f32v, ldv):
+            raise ValueError("u and v need the same dtype and leading dimension")
+        nlev = u.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        rc = self._lib.orc_curl(self._h, _ptr(u), _ptr(v), f32, ld, nlev, _ptr(nodes), n, _ptr(out))
+        if rc:
+            raise ValueError("orc_curl rc=%d" % rc)
+        return out
+
+    def vector_gradient(self, u, v, nlev=None, nodes=None):
+        """Gradients of both components of a tangent vector field, with the
+        antipode's component reversed on the pole faces: (ux, uy, vx, vy)."""
+        u, f32, ld = _field(u)
+        v, f32v, ldv = _field(v)
+        if (f32, ld) != (f32v, ldv):
+            raise ValueError("u and v need the same dtype and leading dimension")
+        nlev = u.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        o = [np.empty((n, nlev)) for _ in range(4)]
+        rc = self._lib.orc_vector_gradient(self._h, _ptr(u), _ptr(v), f32, ld, nlev, _ptr(nodes), n,
+                                           *(_ptr(x) for x in o))
+        if rc:
+            raise ValueError("orc_vector_gradient rc=%d" % rc)
+        return tuple(o)
 
     def laplacian(self, f, nlev=None, nodes=None):
         f, f32, ld = _field(f)
