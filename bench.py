@@ -34,7 +34,9 @@ N_GRID, NLEV = 1280, 137
 OPS = ("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint")
 # (inputs, outputs) per operator
 IO = {"gradient": (1, 2), "divergence": (2, 1), "laplacian": (1, 1), "gradient_adjoint": (2, 1),
-      "divergence_adjoint": (1, 2)}
+      "divergence_adjoint": (1, 2), "curl": (2, 1), "vector_gradient": (2, 4)}
+# operators beyond the five of the step, timed on the same fields
+MORE_OPS = ("curl", "vector_gradient")
 
 
 def _dist():
@@ -241,7 +243,7 @@ def _table_bytes(fvm, op, wbytes):
         _NNZ[op] = fvm.stencil_table(op)["nbr"].shape[0]
     nnz = _NNZ[op]
     V = fvm.nnodes
-    has_b = op in ("divergence", "gradient_adjoint", "divergence_adjoint")
+    has_b = op in ("divergence", "gradient_adjoint", "divergence_adjoint", "curl", "vector_gradient")
     nw = 1 if op == "laplacian" else 2
     return 4 * (V + 1) + nnz * (4 + nw * wbytes) + (2 * wbytes * V if has_b else 0)
 
@@ -309,6 +311,8 @@ def run_native(args):
     V = fvm.nnodes
     g = fvm.grid.arrays()
     fvm.prepare(OPS, dtypes=(atlas.ATLAS_F32, atlas.ATLAS_F64, atlas.ATLAS_BF16))
+    if not args.no_more:
+        fvm.prepare(MORE_OPS, dtypes=(atlas.ATLAS_F32,))
     hbm, peak_kind = _peaks()
 
     # ------------------------------------------------------------ FP32 main
@@ -342,6 +346,22 @@ def run_native(args):
                 "peak": hbm, "unit": "GB/s", "frac": round(per[dom]["frac"], 4),
                 "traffic": traffic, "traffic_gbs": round(traffic / (per[dom]["ms"] * 1e-3) / 1e9, 1) if traffic else None,
                 "peak_kind": peak_kind}
+
+    # ------------------------------------------- curl and vector gradient
+    more = {}
+    if not args.no_more:
+        mt = {} if args.no_tune else tune.tune_fvm(fvm, atlas.ATLAS_F32, nlev, ld, MORE_OPS, fields=(f, u, v), reps=3)
+        calls = {"curl": lambda: fvm.curl(u, v, nlev, out=outs[0]),
+                 "vector_gradient": lambda: fvm.vector_gradient(u, v, nlev, out=tuple(outs[:4]))}
+        for op in MORE_OPS:
+            ms = _max_over_ranks(tune.time_call(calls[op], reps=max(5, args.steps), warmup=args.warmup), ws, "cuda")
+            # the vector gradient reads its table once per component
+            tb = _table_bytes(fvm, op, 4) * (2 if op == "vector_gradient" else 1)
+            b = _alg_bytes(op, V, nlev, 4, tb)
+            more[op] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(V * nlev, ws, ms),
+                        "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
+                        "launches": 2 if op == "vector_gradient" else 1,
+                        "tuned": {k: mt[op][k] for k in ("vec", "batch", "threads", "tile")} if op in mt else None}
 
     # ---------------------------------------------------------------- e2e
     # Host-resident fields through the public API: every step copies f, u, v
@@ -475,6 +495,7 @@ def run_native(args):
                    "l2": "inputs larger than L2 (%.2f GB per field, L2 129 MB), no flush" % (V * ld * 4 / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline, "per_op": {k: {"ms": v_["ms"], "node_levels_per_s": v_["node_levels_per_s"],
                                              "frac_hbm": round(v_["frac"], 4)} for k, v_ in per.items()},
+        "more_ops": more,
         "side_by_side": side, "batched": batched, "tuned": {k: {kk: t[kk] for kk in ("vec", "batch", "threads")}
                                                             for k, t in tuned.items()},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
@@ -554,6 +575,7 @@ def main():
     ap.add_argument("--no-side", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-more", action="store_true", help="skip the curl and vector-gradient timings")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (profiling runs)")
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="octahedral number of a smaller case (profiling only; the metric is O1280)")

@@ -1,8 +1,9 @@
 /*
  * atlas_gb.h -- C ABI of libatlasgb.so: median-dual finite-volume nabla
- * operators (gradient, divergence, Laplacian and the adjoints of gradient and
- * divergence) on multi-level fields over the octahedral reduced Gaussian grid,
- * computed by CUDA kernels on one GB300 (sm_103a).
+ * operators (gradient, divergence, Laplacian, the adjoints of gradient and
+ * divergence, curl and the gradient of a tangent vector field) on multi-level
+ * fields over the octahedral reduced Gaussian grid, computed by CUDA kernels
+ * on one GB300 (sm_103a).
  *
  * The paper (ESCAPE D2.3, the Atlas release) describes the workflow
  * Grid -> Mesh -> FunctionSpace -> Field (Sec. 2.3, Fig. 1 and Fig. 2), says
@@ -81,7 +82,9 @@ enum {
   ATLAS_OP_DIVERGENCE = 1,
   ATLAS_OP_GRADIENT_ADJOINT = 2,
   ATLAS_OP_DIVERGENCE_ADJOINT = 3,
-  ATLAS_OP_LAPLACIAN = 4
+  ATLAS_OP_LAPLACIAN = 4,
+  ATLAS_OP_CURL = 5,
+  ATLAS_OP_VECTOR_GRADIENT = 6
 };
 
 /* ---------------------------------------------------------------------- */
@@ -199,6 +202,26 @@ int atlas_nabla_gradient_adjoint(atlas_fvm_t fvm, const void* gx, const void* gy
                                  int64_t ld, atlas_dtype dtype, void* stream);
 int atlas_nabla_divergence_adjoint(atlas_fvm_t fvm, const void* div, void* u, void* v, int nlev,
                                    int64_t ld, atlas_dtype dtype, void* stream);
+/* Curl (vertical vorticity) of the tangent vector (u, v) in physical      */
+/* components, zeta = (1/(R cos lat)) [d_lon v - d_lat (u cos lat)], by    */
+/* Stokes' theorem on the dual cell (paper Sec. 2.3 lists curl among the  */
+/* operators): V_i zeta_i is the circulation around cell i, the flux of    */
+/* G = (v, -u cos(lat)) through its faces with face means, in the         */
+/* closure-exact form sum_{regular e} n_ie . (G_j - G_i)/2 - G_i . n_pole */
+/* (no circulation on the pole segment).  curl(u, v) = div(v, -u).         */
+/* Units: 1/s for u, v in m/s.  in: u, v; out: zeta.                       */
+int atlas_nabla_curl(atlas_fvm_t fvm, const void* u, const void* v, void* zeta, int nlev, int64_t ld,
+                     atlas_dtype dtype, void* stream);
+/* Gradient of both physical components of a tangent vector field:         */
+/* (ux, uy) = grad u, (vx, vy) = grad v, as atlas_nabla_gradient except on */
+/* the pole edge: a polar node and its antipode (its pole-edge neighbour)  */
+/* have opposite local east and north directions, so the antipode's        */
+/* component enters the pole-face mean with its sign reversed (face value  */
+/* (f_i - f_j)/2, closure-exact term -n_pole (f_i + f_j)/2).  Two launches */
+/* of the same kernel, one per component.  Outputs must not overlap the   */
+/* inputs or each other.                                                   */
+int atlas_nabla_vector_gradient(atlas_fvm_t fvm, const void* u, const void* v, void* ux, void* uy, void* vx,
+                                void* vy, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Edge-based two-kernel forms: an edge-flux kernel writes one flux per    */

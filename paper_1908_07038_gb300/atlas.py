@@ -20,7 +20,8 @@ R_EARTH = 6371220.0
 
 OPS = {"gradient": capi.ATLAS_OP_GRADIENT, "divergence": capi.ATLAS_OP_DIVERGENCE,
        "gradient_adjoint": capi.ATLAS_OP_GRADIENT_ADJOINT,
-       "divergence_adjoint": capi.ATLAS_OP_DIVERGENCE_ADJOINT, "laplacian": capi.ATLAS_OP_LAPLACIAN}
+       "divergence_adjoint": capi.ATLAS_OP_DIVERGENCE_ADJOINT, "laplacian": capi.ATLAS_OP_LAPLACIAN,
+       "curl": capi.ATLAS_OP_CURL, "vector_gradient": capi.ATLAS_OP_VECTOR_GRADIENT}
 
 
 def _view(ptr, ctype, n, shape=None, dtype=None):
@@ -215,6 +216,21 @@ class Fvm:
         capi.atlas_nabla_divergence_adjoint(self.handle, d.data_ptr(), u.data_ptr(), v.data_ptr(),
                                             d.shape[1] if nlev is None else nlev, ld, dt, _stream())
         return u, v
+
+    def curl(self, u, v, nlev=None, out=None):
+        z = self._out(u, out)
+        dt, ld = self._check(u, v, z)
+        capi.atlas_nabla_curl(self.handle, u.data_ptr(), v.data_ptr(), z.data_ptr(),
+                              u.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return z
+
+    def vector_gradient(self, u, v, nlev=None, out=None):
+        """(ux, uy, vx, vy): gradients of both components of a tangent vector."""
+        outs = out if out is not None else tuple(self._out(u, None) for _ in range(4))
+        dt, ld = self._check(u, v, *outs)
+        capi.atlas_nabla_vector_gradient(self.handle, u.data_ptr(), v.data_ptr(), *(o.data_ptr() for o in outs),
+                                         u.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return tuple(outs)
 
     # edge-based two-kernel forms
     def workspace(self, op, ld, dtype_code):

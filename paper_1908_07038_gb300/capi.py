@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libatlasgb.so")
 ATLAS_F32, ATLAS_F64, ATLAS_BF16 = 0, 1, 2
 ATLAS_OP_GRADIENT, ATLAS_OP_DIVERGENCE, ATLAS_OP_GRADIENT_ADJOINT = 0, 1, 2
 ATLAS_OP_DIVERGENCE_ADJOINT, ATLAS_OP_LAPLACIAN = 3, 4
+ATLAS_OP_CURL, ATLAS_OP_VECTOR_GRADIENT = 5, 6
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EALIGN", -5: "EDTYPE", -6: "ESTATE"}
 
 
@@ -69,6 +70,8 @@ _SIGS = {
     "atlas_nabla_laplacian": (I32, [P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_gradient_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_divergence_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
+    "atlas_nabla_curl": (I32, [P, P, P, P, I32, I64, I32, P], True),
+    "atlas_nabla_vector_gradient": (I32, [P, P, P, P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_workspace_bytes": (SZ, [P, I32, I32, I64, I32], False),
     "atlas_nabla_gradient_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),
     "atlas_nabla_divergence_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),

@@ -357,8 +357,8 @@ int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   const void* ins[2] = {in0, in1};
   void* outs[2] = {out0, out1};
-  const int nin = (op == atlasgb::OP_DIV || op == atlasgb::OP_GRAD_ADJ) ? 2 : 1;
-  const int nout = (op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ) ? 2 : 1;
+  const int nin = (op == atlasgb::OP_DIV || op == atlasgb::OP_GRAD_ADJ || op == atlasgb::OP_CURL) ? 2 : 1;
+  const int nout = (op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) ? 2 : 1;
   const void* all[4] = {in0, in1, out0, out1};
   const void* used[4];
   int nu = 0;
@@ -744,6 +744,28 @@ int atlas_nabla_gradient_adjoint(atlas_fvm_t fvm, const void* gx, const void* gy
 int atlas_nabla_divergence_adjoint(atlas_fvm_t fvm, const void* div, void* u, void* v, int nlev, int64_t ld,
                                    atlas_dtype dtype, void* stream) {
   return run_stencil_op(fvm, atlasgb::OP_DIV_ADJ, div, nullptr, u, v, nlev, ld, dtype, stream);
+}
+int atlas_nabla_curl(atlas_fvm_t fvm, const void* u, const void* v, void* zeta, int nlev, int64_t ld,
+                     atlas_dtype dtype, void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_CURL, u, v, zeta, nullptr, nlev, ld, dtype, stream);
+}
+int atlas_nabla_vector_gradient(atlas_fvm_t h, const void* u, const void* v, void* ux, void* uy, void* vx, void* vy,
+                                int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  // the two launches must not see each other's outputs as inputs
+  const void* ins[2] = {u, v};
+  void* outs[4] = {ux, uy, vx, vy};
+  for (int k = 0; k < 4; ++k)
+    if (!outs[k]) return fail(ATLAS_EINVAL, "NULL output field");
+  if (!u || !v) return fail(ATLAS_EINVAL, "NULL input field");
+  if (valid_dtype(dtype) && ld >= 1) {
+    const int rc = check_no_overlap(ins, 2, outs, 4, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
+    if (rc) return rc;
+  }
+  const int rc = run_stencil_op(h, atlasgb::OP_VGRAD, u, nullptr, ux, uy, nlev, ld, dtype, stream);
+  if (rc) return rc;
+  return run_stencil_op(h, atlasgb::OP_VGRAD, v, nullptr, vx, vy, nlev, ld, dtype, stream);
 }
 
 size_t atlas_nabla_workspace_bytes(atlas_fvm_t h, int op, int nlev, int64_t ld, atlas_dtype dtype) {

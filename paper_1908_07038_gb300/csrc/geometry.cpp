@@ -479,7 +479,7 @@ double div_vdiag(const Mesh& m, const Dual& d, int64_t i) {
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
   const int64_t V = m.grid->nnodes;
   s.ptr.assign(static_cast<size_t>(V) + 1, 0);
-  const bool regular_only = (op == OP_DIV || op == OP_DIV_ADJ);
+  const bool regular_only = (op == OP_DIV || op == OP_DIV_ADJ || op == OP_CURL);
   if (op == OP_LAP) {
     s.nin = 1; s.nout = 1; s.has_b = false; s.scalar_w = true;
     // L = D G as sparse matrices; the row sums of L vanish (G applied to a
@@ -564,11 +564,11 @@ bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
   s.w.resize(static_cast<size_t>(2 * nnz));
   s.has_b = (op != OP_GRAD);
   s.scalar_w = false;
-  s.nin = (op == OP_GRAD || op == OP_DIV_ADJ) ? 1 : 2;
+  s.nin = (op == OP_GRAD || op == OP_DIV_ADJ || op == OP_VGRAD) ? 1 : 2;
   s.nout = 3 - s.nin;
   if (s.has_b) s.b.assign(static_cast<size_t>(2 * V), 0.0);
   std::vector<double> vdiag;
-  if (op == OP_DIV || op == OP_DIV_ADJ) {
+  if (op == OP_DIV || op == OP_DIV_ADJ || op == OP_CURL) {
     vdiag.resize(static_cast<size_t>(V));
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < V; ++i) vdiag[i] = div_vdiag(m, d, i);
@@ -588,6 +588,24 @@ bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
         double nl, np;
         normal_of(m, d, q, nl, np);
         div_w(d, i, j, nl, np, w0, w1);
+      } else if (op == OP_CURL) {
+        // circulation = flux of G = (v, -u cos): the divergence weights with
+        // the inputs exchanged and the u weight negated (inputs are (u, v))
+        double nl, np, dl, dp;
+        normal_of(m, d, q, nl, np);
+        div_w(d, i, j, nl, np, dl, dp);
+        w0 = -dp;
+        w1 = dl;
+      } else if (op == OP_VGRAD) {
+        // gradient weights; on the pole edge the antipode's component enters
+        // reversed: -w (x_j + x_i) = -w (x_j - x_i) - 2 w x_i
+        grad_w(m, d, i, q, w0, w1);
+        if (m.is_pole[e]) {
+          w0 = -w0;
+          w1 = -w1;
+          b0.add(2.0 * w0);
+          b1.add(2.0 * w1);
+        }
       } else if (op == OP_GRAD_ADJ) {
         // column i of row j of the gradient: weights of row j towards node i
         double nl, np;
@@ -616,6 +634,12 @@ bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
     if (op == OP_DIV) {
       s.b[2 * i] = 0.0;
       s.b[2 * i + 1] = vdiag[i];
+    } else if (op == OP_CURL) {
+      s.b[2 * i] = -vdiag[i];
+      s.b[2 * i + 1] = 0.0;
+    } else if (op == OP_VGRAD) {
+      s.b[2 * i] = b0.value();
+      s.b[2 * i + 1] = b1.value();
     } else if (op == OP_GRAD_ADJ) {
       s.b[2 * i] = b0.value();
       s.b[2 * i + 1] = b1.value();

@@ -78,7 +78,16 @@ bool build_grid(int N, Grid& g);
 bool build_mesh(const Grid& g, Mesh& m);
 bool build_dual(const Mesh& m, double R, Dual& d);
 
-enum StencilOp { OP_GRAD = 0, OP_DIV = 1, OP_GRAD_ADJ = 2, OP_DIV_ADJ = 3, OP_LAP = 4, OP_COUNT = 5 };
+enum StencilOp {
+  OP_GRAD = 0,
+  OP_DIV = 1,
+  OP_GRAD_ADJ = 2,
+  OP_DIV_ADJ = 3,
+  OP_LAP = 4,
+  OP_CURL = 5,   // vertical vorticity of (u, v): two inputs, one output
+  OP_VGRAD = 6,  // gradient of one component of a tangent vector field
+  OP_COUNT = 7
+};
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
 bool build_edge_gather(const Mesh& m, const Dual& d, int op /*OP_GRAD or OP_DIV*/, EdgeGather& eg);
 

@@ -68,6 +68,10 @@ def _call(fvm, op, ins, outs, nlev):
         fvm.laplacian(ins[0], nlev, out=outs[0])
     elif op == "gradient_adjoint":
         fvm.gradient_adjoint(ins[0], ins[1], nlev, out=outs[0])
+    elif op == "curl":
+        fvm.curl(ins[0], ins[1], nlev, out=outs[0])
+    elif op == "vector_gradient":
+        fvm.vector_gradient(ins[0], ins[1], nlev, out=tuple(outs[:4]))
     else:
         fvm.divergence_adjoint(ins[0], nlev, out=(outs[0], outs[1]))
 
@@ -101,7 +105,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
     if fields is None:
         t = _torch_dtype(dtype)
         fields = [torch.randn((fvm.nnodes, ld), device="cuda").to(t) for _ in range(3)]
-    outs = [torch.empty_like(fields[0]) for _ in range(2)]
+    outs = [torch.empty_like(fields[0]) for _ in range(4)]
     best = {}
     for op in ops:
         key = key_base + "|" + op
@@ -110,7 +114,8 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
             fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1))
             best[op] = c
             continue
-        ins = (fields[1], fields[2]) if op in ("divergence", "gradient_adjoint") else (fields[0],)
+        ins = (fields[1], fields[2]) if op in ("divergence", "gradient_adjoint", "curl", "vector_gradient") \
+            else (fields[0],)
         cand = CANDIDATES[dtype]
         results = []
         for vec, batch, threads, bps, tile in itertools.product(cand["vec"], cand["batch"], cand["threads"],

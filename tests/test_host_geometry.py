@@ -75,6 +75,32 @@ def test_stencil_tables_reproduce_oracle(pfvm, omesh, N):
         du, dv = _apply(f.stencil_table("divergence_adjoint"), [inp])
         ou, ov = om.divergence_adjoint(inp)
         assert _relmax(du, ou) <= 1e-13 and _relmax(dv, ov) <= 1e-13
+        (z,) = _apply(f.stencil_table("curl"), [inp, y])
+        assert _relmax(z, om.curl(inp, y)) <= 1e-13
+        vg = _apply(f.stencil_table("vector_gradient"), [inp]) + _apply(f.stencil_table("vector_gradient"), [y])
+        for a, b in zip(vg, om.vector_gradient(inp, y)):
+            assert _relmax(a, b) <= 1e-13
+
+
+def test_vector_table_shapes(pfvm):
+    """Curl: two inputs, one output, B term, no pole entries; vector
+    gradient: one input (a component), two outputs, B term only on the
+    polar rows, the same neighbours as the gradient."""
+    f = pfvm(8)
+    c, d = f.stencil_table("curl"), f.stencil_table("divergence")
+    assert (c["nin"], c["nout"]) == (2, 1)
+    assert np.array_equal(c["ptr"], d["ptr"]) and np.array_equal(c["nbr"], d["nbr"])
+    assert np.array_equal(c["w"][:, 0], -d["w"][:, 1]) and np.array_equal(c["w"][:, 1], d["w"][:, 0])
+    vg, g = f.stencil_table("vector_gradient"), f.stencil_table("gradient")
+    assert (vg["nin"], vg["nout"]) == (1, 2)
+    assert np.array_equal(vg["ptr"], g["ptr"]) and np.array_equal(vg["nbr"], g["nbr"])
+    flipped = np.any(vg["w"] != g["w"], axis=1)
+    pl0 = int(f.grid.arrays()["pl"][0])
+    rows = np.repeat(np.arange(f.nnodes), np.diff(g["ptr"]))
+    assert np.all(np.isin(rows[flipped], np.r_[0:pl0, f.nnodes - pl0:f.nnodes]))
+    assert np.count_nonzero(flipped) == 2 * pl0  # one pole entry per polar node
+    assert np.array_equal(vg["w"][flipped], -g["w"][flipped])
+    assert np.count_nonzero(np.any(vg["b"] != 0, axis=1)) == 2 * pl0
 
 
 def test_laplacian_table_rows_sum_to_zero_structure(pfvm):
