@@ -306,6 +306,39 @@ int atlas_batch_info(atlas_batch_t b, int64_t* tiles, int64_t* node_levels);
 void atlas_batch_destroy(atlas_batch_t b);
 
 /* ---------------------------------------------------------------------- */
+/* Band partitions (paper Sec. 2.3: a mesh may be split into partitions,  */
+/* one per MPI task, with overlap regions filled by halo exchange).        */
+/* nparts parts split the rows north to south into                         */
+/* consecutive bands of about equal node counts; part p owns the node      */
+/* range [own0, own1) (whole rows) and reads the halo range               */
+/* [halo0, halo1) = its rows plus halo_rings (1 or 2) rows on each side,   */
+/* which is every value its nodes' stencils touch (two rings: the fused    */
+/* Laplacian).  Each part has at least halo_rings rows, so a halo row      */
+/* belongs to the adjacent part: one exchange per side refreshes it.       */
+/* Host only (works without a GPU).                                        */
+/* ---------------------------------------------------------------------- */
+typedef struct atlas_part_s* atlas_part_t;
+int atlas_part_create(atlas_fvm_t f, int nparts, int part, int halo_rings, atlas_part_t* out);
+int atlas_part_info(atlas_part_t p, int64_t* own0, int64_t* own1, int64_t* halo0, int64_t* halo1);
+/* Exchange with the part before (side 0, north) or after (side 1, south): */
+/* peer = that part's index or -1; this part sends its own nodes           */
+/* [send0, send1) and receives [recv0, recv1) into its halo.  The peer's   */
+/* recv range is this part's send range and the other way round.           */
+int atlas_part_neighbour(atlas_part_t p, int side, int* peer, int64_t* send0, int64_t* send1, int64_t* recv0,
+                         int64_t* recv1);
+/* Apply operator op (ATLAS_OP_*) to this part's own nodes.  Inputs are    */
+/* local fields of halo1 - halo0 rows (row k = node halo0 + k, halo rows   */
+/* filled by the exchange), outputs local fields of own1 - own0 rows (row */
+/* k = node own0 + k); ld, dtype and stream as for the whole-grid calls.   */
+/* Results equal the whole-grid operator's on these nodes, bitwise (same   */
+/* kernels and summation order).  For ATLAS_OP_VECTOR_GRADIENT the call    */
+/* takes one component (in0) and writes its two gradient components.      */
+/* The Laplacian needs halo_rings = 2.                                     */
+int atlas_part_apply(atlas_part_t p, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
+                     int64_t ld, atlas_dtype dtype, void* stream);
+void atlas_part_destroy(atlas_part_t p);
+
+/* ---------------------------------------------------------------------- */
 /* Field synchronisation (paper Sec. 4.2: update_host after device work).  */
 /* One cudaMemcpyAsync of bytes from src to dst on stream; direction 0 =   */
 /* host to device, 1 = device to host, 2 = device to device.  Host memory  */

@@ -71,6 +71,11 @@ _SIGS = {
     "atlas_nabla_gradient_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_divergence_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_curl": (I32, [P, P, P, P, I32, I64, I32, P], True),
+    "atlas_part_create": (I32, [P, I32, I32, I32, P], True),
+    "atlas_part_info": (I32, [P, P, P, P, P], True),
+    "atlas_part_neighbour": (I32, [P, I32, P, P, P, P, P], True),
+    "atlas_part_apply": (I32, [P, I32, P, P, P, P, I32, I64, I32, P], True),
+    "atlas_part_destroy": (None, [P], False),
     "atlas_nabla_vector_gradient": (I32, [P, P, P, P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_workspace_bytes": (SZ, [P, I32, I32, I64, I32], False),
     "atlas_nabla_gradient_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),

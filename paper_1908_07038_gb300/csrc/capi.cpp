@@ -338,6 +338,24 @@ int check_no_overlap(const void* const* ins, int nin, void* const* outs, int nou
   return ATLAS_OK;
 }
 
+// As check_no_overlap, for inputs and outputs of different sizes.
+int check_no_overlap2(const void* const* ins, int nin, int64_t in_bytes, void* const* outs, int nout,
+                      int64_t out_bytes) {
+  auto overlaps = [](const void* a, int64_t na, const void* b, int64_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + static_cast<uintptr_t>(nb) && y < x + static_cast<uintptr_t>(na);
+  };
+  for (int o = 0; o < nout; ++o) {
+    for (int i = 0; i < nin; ++i)
+      if (overlaps(outs[o], out_bytes, ins[i], in_bytes))
+        return fail(ATLAS_EINVAL, "output field %d overlaps input field %d", o, i);
+    for (int p = o + 1; p < nout; ++p)
+      if (overlaps(outs[o], out_bytes, outs[p], out_bytes))
+        return fail(ATLAS_EINVAL, "output fields %d and %d overlap", o, p);
+  }
+  return ATLAS_OK;
+}
+
 int grid_blocks(atlas_fvm_s* f, StorageType st, const atlasgb::DevStencil& s, int vec, int batch, int threads,
                 int bps_req, int64_t items) {
   int bps = atlasgb::stencil_occupancy(st, s, vec, batch, threads);
@@ -350,60 +368,82 @@ int grid_blocks(atlas_fvm_s* f, StorageType st, const atlasgb::DevStencil& s, in
 
 atlas_fvm_s* get_fvm(atlas_fvm_t h) { return live(h) ? reinterpret_cast<atlas_fvm_s*>(h) : nullptr; }
 
-// Fused node-stencil operator call.
-int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
-                   int64_t ld, atlas_dtype dtype, void* stream) {
-  atlas_fvm_s* f = get_fvm(h);
-  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+// One fused node-stencil operator over nodes [node0, node0 + count).  The
+// input fields hold the nodes from in_first on (their row 0 is node
+// in_first, in_nodes rows), the outputs the nodes from node0 on (count
+// rows).  The kernels index fields by global node id: each pointer is
+// shifted back by its first node (integer arithmetic on the address; the
+// kernel only touches rows inside the buffer).
+int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
+                      int64_t ld, atlas_dtype dtype, void* stream, int64_t node0, int64_t count, int64_t in_first,
+                      int64_t in_nodes) {
   const void* ins[2] = {in0, in1};
   void* outs[2] = {out0, out1};
   const int nin = (op == atlasgb::OP_DIV || op == atlasgb::OP_GRAD_ADJ || op == atlasgb::OP_CURL) ? 2 : 1;
   const int nout = (op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) ? 2 : 1;
-  const void* all[4] = {in0, in1, out0, out1};
   const void* used[4];
   int nu = 0;
   for (int k = 0; k < nin; ++k) used[nu++] = ins[k];
   for (int k = 0; k < nout; ++k) used[nu++] = outs[k];
-  (void)all;
   int rc = check_field_args(dtype, nlev, ld, used, nu);
   if (rc) return rc;
-  const int64_t V = f->mesh->grid->g.nnodes;
-  rc = check_no_overlap(ins, nin, outs, nout, V * ld * elem_size(dtype));
+  const int64_t es = elem_size(dtype);
+  rc = check_no_overlap2(ins, nin, in_nodes * ld * es, outs, nout, count * ld * es);
   if (rc) return rc;
   rc = check_device(f);
   if (rc) return rc;
-  if (nlev == 0 || V == 0) return ok();
+  if (nlev == 0 || count == 0) return ok();
   {
     std::lock_guard<std::mutex> lk(f->mu);
     rc = ensure_stencil(f, op, dtype);
     if (rc) return rc;
   }
+  const atlasgb::DevStencil& dev = f->st[op][dtype].dev;
+  if (dev.pair && ((node0 | count) & 1))
+    return fail(ATLAS_EINVAL, "the node-pair tables need an even first node and node count");
+  auto shift = [&](const void* p, int64_t first) -> const void* {
+    return p ? reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(p) -
+                                             static_cast<uintptr_t>(first * ld * es))
+             : nullptr;
+  };
   const LaunchCfg& c = f->cfg[op];
   atlasgb::StencilLaunch l;
-  l.in0 = in0;
-  l.in1 = nin == 2 ? in1 : nullptr;
-  l.out0 = out0;
-  l.out1 = nout == 2 ? out1 : nullptr;
+  l.in0 = shift(in0, in_first);
+  l.in1 = nin == 2 ? shift(in1, in_first) : nullptr;
+  l.out0 = const_cast<void*>(shift(out0, node0));
+  l.out1 = nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr;
   l.nlev = nlev;
   l.ld = ld;
+  l.node0 = static_cast<int32_t>(node0);
+  l.count = static_cast<int32_t>(count);
   l.vec = pick_vec(dtype, ld, used, nu, c.vec);
   const int64_t nvec = (nlev + l.vec - 1) / l.vec;
-  const int64_t items = V * nvec;
-  if (items >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
+  const int64_t items = count * nvec;
+  if (f->mesh->grid->g.nnodes * nvec >= (int64_t(1) << 31))
+    return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
   l.threads = c.threads;
   l.batch = c.batch;
   const StorageType st = storage_of(dtype);
-  l.blocks = grid_blocks(f, st, f->st[op][dtype].dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
+  l.blocks = grid_blocks(f, st, dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
   {
     // items the kernel walks (node pairs for a pair table); a tile is at most
     // one block's even share, so blocks * tile stays below 2^31 + blocks * threads
-    const int64_t walked = f->st[op][dtype].dev.pair ? items / 2 : items;
+    const int64_t walked = dev.pair ? items / 2 : items;
     const int64_t share = ((walked + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
     l.tile = static_cast<uint32_t>(std::max<int64_t>(l.threads, std::min<int64_t>(int64_t(c.tile_passes) * l.threads, share)));
   }
-  cudaError_t e = atlasgb::launch_stencil(st, f->st[op][dtype].dev, l, static_cast<cudaStream_t>(stream));
+  cudaError_t e = atlasgb::launch_stencil(st, dev, l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
   return ok();
+}
+
+// The operator over every node, on whole fields.
+int run_stencil_op(atlas_fvm_t h, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
+                   int64_t ld, atlas_dtype dtype, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  const int64_t V = f->mesh->grid->g.nnodes;
+  return run_stencil_range(f, op, in0, in1, out0, out1, nlev, ld, dtype, stream, 0, V, 0, V);
 }
 
 size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
@@ -713,7 +753,7 @@ void atlas_fvm_destroy(atlas_fvm_t h) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return;
   if (f->users > 0) {
-    fail(ATLAS_ESTATE, "fvm still used by %d batch(es); not destroyed", f->users);
+    fail(ATLAS_ESTATE, "fvm still used by %d batch(es) or partition(s); not destroyed", f->users);
     return;
   }
   unreg(f);
@@ -901,6 +941,125 @@ int atlas_field_sync(void* dst, const void* src, size_t bytes, int direction, vo
   cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
   return ok();
+}
+
+}  // extern "C"
+
+// ============================================================= partitions
+// A band partition: part p of nparts owns the consecutive rows [r0, r1) (a
+// contiguous range of node ids, rows are numbered north to south) and reads
+// a halo of `halo` rows on each side.  Neighbours of a node lie in its own
+// row (ring and pole edges) or the adjacent rows, and the two-ring Laplacian
+// reaches two rows away, so a halo of 1 (2 for the Laplacian) rows holds
+// every value the own nodes need; those rows belong to the two adjacent
+// parts (each part has at least `halo` rows), so one exchange with each of
+// them refreshes the halo.
+struct atlas_part_s {
+  atlas_fvm_s* fvm = nullptr;
+  int nparts = 1, part = 0, halo = 1;
+  int r0 = 0, r1 = 0;
+  int64_t own0 = 0, own1 = 0, halo0 = 0, halo1 = 0;
+  int peer[2] = {-1, -1};
+  int64_t send0[2] = {0, 0}, send1[2] = {0, 0}, recv0[2] = {0, 0}, recv1[2] = {0, 0};
+};
+
+extern "C" {
+
+int atlas_part_create(atlas_fvm_t h, int nparts, int part, int halo_rings, atlas_part_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (halo_rings != 1 && halo_rings != 2) return fail(ATLAS_EINVAL, "halo_rings must be 1 or 2");
+  const atlasgb::Grid& g = f->mesh->grid->g;
+  const int nrows = g.nlat;
+  if (nparts < 1 || part < 0 || part >= nparts) return fail(ATLAS_EINVAL, "need 0 <= part < nparts");
+  if (static_cast<int64_t>(nparts) * halo_rings > nrows)
+    return fail(ATLAS_EINVAL, "%d parts of at least %d rows do not fit %d rows", nparts, halo_rings, nrows);
+  // boundaries: the row start nearest to an equal share of the nodes, kept
+  // at least halo_rings rows apart and from both ends
+  std::vector<int> b(static_cast<size_t>(nparts) + 1, 0);
+  b[nparts] = nrows;
+  for (int k = 1; k < nparts; ++k) {
+    const double target = static_cast<double>(g.nnodes) * k / nparts;
+    int r = static_cast<int>(std::lower_bound(g.off.begin(), g.off.end(), static_cast<int64_t>(target)) - g.off.begin());
+    if (r > 0 && r <= nrows && target - g.off[r - 1] < g.off[r] - target) --r;
+    r = std::max(r, b[k - 1] + halo_rings);
+    r = std::min(r, nrows - (nparts - k) * halo_rings);
+    b[k] = r;
+  }
+  atlas_part_s* p = new (std::nothrow) atlas_part_s();
+  if (!p) return fail(ATLAS_ENOMEM, "out of host memory");
+  p->fvm = f;
+  p->nparts = nparts;
+  p->part = part;
+  p->halo = halo_rings;
+  p->r0 = b[part];
+  p->r1 = b[part + 1];
+  p->own0 = g.off[p->r0];
+  p->own1 = g.off[p->r1];
+  p->halo0 = g.off[std::max(0, p->r0 - halo_rings)];
+  p->halo1 = g.off[std::min(nrows, p->r1 + halo_rings)];
+  if (part > 0) {  // rows above: the end of part - 1
+    p->peer[0] = part - 1;
+    p->send0[0] = p->own0;
+    p->send1[0] = g.off[p->r0 + halo_rings];
+    p->recv0[0] = p->halo0;
+    p->recv1[0] = p->own0;
+  }
+  if (part + 1 < nparts) {  // rows below: the start of part + 1
+    p->peer[1] = part + 1;
+    p->send0[1] = g.off[p->r1 - halo_rings];
+    p->send1[1] = p->own1;
+    p->recv0[1] = p->own1;
+    p->recv1[1] = p->halo1;
+  }
+  f->users++;
+  reg(p);
+  *out = reinterpret_cast<atlas_part_t>(p);
+  return ok();
+}
+
+int atlas_part_info(atlas_part_t h, int64_t* own0, int64_t* own1, int64_t* halo0, int64_t* halo1) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed partition handle");
+  const atlas_part_s* p = reinterpret_cast<const atlas_part_s*>(h);
+  if (own0) *own0 = p->own0;
+  if (own1) *own1 = p->own1;
+  if (halo0) *halo0 = p->halo0;
+  if (halo1) *halo1 = p->halo1;
+  return ok();
+}
+
+int atlas_part_neighbour(atlas_part_t h, int side, int* peer, int64_t* send0, int64_t* send1, int64_t* recv0,
+                         int64_t* recv1) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed partition handle");
+  if (side != 0 && side != 1) return fail(ATLAS_EINVAL, "side must be 0 (the part before) or 1 (after)");
+  const atlas_part_s* p = reinterpret_cast<const atlas_part_s*>(h);
+  if (peer) *peer = p->peer[side];
+  if (send0) *send0 = p->send0[side];
+  if (send1) *send1 = p->send1[side];
+  if (recv0) *recv0 = p->recv0[side];
+  if (recv1) *recv1 = p->recv1[side];
+  return ok();
+}
+
+int atlas_part_apply(atlas_part_t h, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
+                     int64_t ld, atlas_dtype dtype, void* stream) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed partition handle");
+  atlas_part_s* p = reinterpret_cast<atlas_part_s*>(h);
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (op == atlasgb::OP_LAP && p->halo < 2) return fail(ATLAS_EINVAL, "the Laplacian needs a halo of 2 rows");
+  if (!live(p->fvm)) return fail(ATLAS_ESTATE, "the partition's fvm was destroyed");
+  return run_stencil_range(p->fvm, op, in0, in1, out0, out1, nlev, ld, dtype, stream, p->own0, p->own1 - p->own0,
+                           p->halo0, p->halo1 - p->halo0);
+}
+
+void atlas_part_destroy(atlas_part_t h) {
+  if (!live(h)) return;
+  atlas_part_s* p = reinterpret_cast<atlas_part_s*>(h);
+  unreg(p);
+  p->fvm->users--;
+  delete p;
 }
 
 }  // extern "C"

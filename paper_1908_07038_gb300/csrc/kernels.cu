@@ -282,15 +282,16 @@ template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool S
 __global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                                                       const A* __restrict__ w, const A* __restrict__ b,
                                                       const S* __restrict__ in0, const S* __restrict__ in1,
-                                                      S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
-                                                      int32_t nlev, int64_t ld, uint32_t nvec, Div32 dv,
-                                                      uint32_t tile) {
-  const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;  // host guarantees < 2^31
+                                                      S* __restrict__ out0, S* __restrict__ out1, int32_t node0,
+                                                      int32_t count, int32_t nlev, int64_t ld, uint32_t nvec,
+                                                      Div32 dv, uint32_t tile) {
+  // nodes node0 .. node0 + count - 1 (all nodes, or one partition's own)
+  const uint32_t total = static_cast<uint32_t>(count) * nvec;  // host guarantees < 2^31
   auto body = [&](uint32_t item) {
-    const uint32_t i = div_by(item, dv);
-    const uint32_t v = item - i * nvec;
+    const uint32_t k = div_by(item, dv);
+    const uint32_t v = item - k * nvec;
     stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, IDX32>(
-        ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev, static_cast<int32_t>(i), static_cast<int32_t>(v * VEC));
+        ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev, node0 + static_cast<int32_t>(k), static_cast<int32_t>(v * VEC));
   };
   // FP32 and FP64 fields: a plain grid-stride loop, which measured 7-8%
   // faster than the tile walk for the one-ring operators (the tile length
@@ -332,14 +333,15 @@ template <> struct PairEntry<double> {
 template <typename S, typename A, int VEC, int BATCH, bool IDX32>
 __global__ void __launch_bounds__(512) pair_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
                                                    const A* __restrict__ w, const S* __restrict__ in0,
-                                                   S* __restrict__ out0, int32_t npairs, int32_t nlev, int64_t ld,
-                                                   uint32_t nvec, Div32 dv, uint32_t tile) {
+                                                   S* __restrict__ out0, int32_t pair0, int32_t npairs, int32_t nlev,
+                                                   int64_t ld, uint32_t nvec, Div32 dv, uint32_t tile) {
   using Idx = typename IdxT<IDX32>::T;
   const Idx ldx = static_cast<Idx>(ld);
   const uint32_t total = static_cast<uint32_t>(npairs) * nvec;  // host guarantees < 2^31
   for_each_item(total, tile, [&](uint32_t item) {
-    const uint32_t g = div_by(item, dv);
-    const int32_t lev0 = static_cast<int32_t>((item - g * nvec) * VEC);
+    const uint32_t k = div_by(item, dv);
+    const int32_t lev0 = static_cast<int32_t>((item - k * nvec) * VEC);
+    const uint32_t g = static_cast<uint32_t>(pair0) + k;  // pairs pair0 .. pair0 + npairs - 1
     const int32_t ia = static_cast<int32_t>(2 * g);
     const Idx oa = static_cast<Idx>(ia) * ldx + static_cast<Idx>(lev0);
     const Idx ob = oa + ldx;
@@ -552,13 +554,13 @@ cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_
   if (idx32)
     stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
-        static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec,
-        dv, l.tile);
+        static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), l.node0, l.count, l.nlev, l.ld,
+        nvec, dv, l.tile);
   else
     stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
-        static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), s.nnodes, l.nlev, l.ld, nvec,
-        dv, l.tile);
+        static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), l.node0, l.count, l.nlev, l.ld,
+        nvec, dv, l.tile);
   return cudaGetLastError();
 }
 
@@ -636,16 +638,16 @@ template <typename S, typename A, int VEC, int BATCH>
 cudaError_t run_pair(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
   const uint32_t nvec = static_cast<uint32_t>((l.nlev + VEC - 1) / VEC);
   const Div32 dv = make_div32(nvec);
-  const int32_t npairs = s.nnodes / 2;
+  const int32_t pair0 = l.node0 / 2, npairs = l.count / 2;  // node0 and count are even for pair tables
   const bool idx32 = static_cast<int64_t>(s.nnodes) * l.ld < (int64_t(1) << 31);
   if (idx32)
     pair_kernel<S, A, VEC, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
-        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), npairs,
-        l.nlev, l.ld, nvec, dv, l.tile);
+        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), pair0,
+        npairs, l.nlev, l.ld, nvec, dv, l.tile);
   else
     pair_kernel<S, A, VEC, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
-        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), npairs,
-        l.nlev, l.ld, nvec, dv, l.tile);
+        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), pair0,
+        npairs, l.nlev, l.ld, nvec, dv, l.tile);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,11 @@ struct StencilLaunch {
   int threads = 256;
   int blocks = 0;  // grid size
   uint32_t tile = 0;  // items per block tile: a multiple of threads, blocks * tile < 2^31
+  // nodes computed: node0 .. node0 + count - 1 (even for pair tables).  The
+  // field pointers are indexed with global node ids within that range and
+  // its neighbours.
+  int32_t node0 = 0;
+  int32_t count = 0;
 };
 
 // Edge-based two-pass data on the device.

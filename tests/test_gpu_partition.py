@@ -1,0 +1,106 @@
+"""GPU: band partitions and level shards give the whole-grid results bitwise.
+
+The parts are emulated on one GPU, one after the other: each part's local
+input is the whole field's halo range (what the halo exchange delivers),
+``atlas_part_apply`` computes its own nodes, and the assembled outputs must
+equal the whole-grid operator's, bit for bit (same kernels, same summation
+order, only the node range and the buffers differ).  Level shards are column
+views of the whole fields passed to the whole-grid calls."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+OPS = [("gradient", 1, 2), ("divergence", 2, 1), ("laplacian", 1, 1), ("gradient_adjoint", 2, 1),
+       ("divergence_adjoint", 1, 2), ("curl", 2, 1), ("vector_gradient", 1, 2)]
+
+
+def _whole(fvm, op, ins, nlev):
+    if op == "gradient":
+        return list(fvm.gradient(ins[0], nlev))
+    if op == "divergence":
+        return [fvm.divergence(ins[0], ins[1], nlev)]
+    if op == "laplacian":
+        return [fvm.laplacian(ins[0], nlev)]
+    if op == "gradient_adjoint":
+        return [fvm.gradient_adjoint(ins[0], ins[1], nlev)]
+    if op == "divergence_adjoint":
+        return list(fvm.divergence_adjoint(ins[0], nlev))
+    if op == "curl":
+        return [fvm.curl(ins[0], ins[1], nlev)]
+    # one component through the vector-gradient table: compare with the
+    # whole-grid call's first component
+    return list(fvm.vector_gradient(ins[0], ins[0].clone(), nlev)[:2])
+
+
+@pytest.mark.parametrize("dtype,ld", [("float32", 140), ("float64", 138), ("bfloat16", 144)])
+def test_partitions_equal_whole_grid(torch, pfvm, dtype, ld):
+    from paper_1908_07038_gb300.partition import Partition
+    dt = getattr(torch, dtype)
+    fvm = pfvm(80)
+    nlev = 137
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    fields = [torch.randn((fvm.nnodes, ld), generator=gen, device="cuda").to(dt) for _ in range(2)]
+    for op, nin, nout in OPS:
+        ins = fields[:nin]
+        want = _whole(fvm, op, ins, nlev)
+        halo = 2 if op == "laplacian" else 1
+        for nparts in (2, 3, 5):
+            got = [torch.full_like(want[0], float("nan")) for _ in range(nout)]
+            for k in range(nparts):
+                p = Partition(fvm, nparts, k, halo)
+                local = [p.local_view(x).clone() for x in ins]
+                outs = [torch.empty((p.own_rows, ld), dtype=dt, device="cuda") for _ in range(nout)]
+                p.apply(op, local, outs, nlev)
+                for g_, o in zip(got, outs):
+                    g_[p.own0:p.own1] = o
+                p.close()
+            torch.cuda.synchronize()
+            for g_, w in zip(got, want):
+                assert torch.equal(g_[:, :nlev], w[:, :nlev]), (op, nparts, dtype)
+
+
+def test_partition_rejects_wrong_shapes(torch, pfvm):
+    from paper_1908_07038_gb300.partition import Partition
+    from paper_1908_07038_gb300.capi import AtlasError
+    fvm = pfvm(16)
+    p = Partition(fvm, 2, 0, 1)
+    f = torch.zeros((p.local_rows, 8), device="cuda")
+    with pytest.raises(ValueError):
+        p.apply("gradient", [f[:-1]], [torch.zeros((p.own_rows, 8), device="cuda")] * 2)
+    with pytest.raises(AtlasError):  # the Laplacian needs a two-row halo
+        p.apply("laplacian", [f], [torch.zeros((p.own_rows, 8), device="cuda")])
+    p.close()
+
+
+@pytest.mark.parametrize("nparts", [2, 3, 8])
+def test_level_shards_equal_whole_levels(torch, pfvm, nparts):
+    from paper_1908_07038_gb300.partition import level_shards
+    fvm = pfvm(80)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    f, u, v = (torch.randn((fvm.nnodes, 140), generator=gen, device="cuda") for _ in range(3))
+    gx, gy = fvm.gradient(f, 137)
+    d = fvm.divergence(u, v, 137)
+    lap = fvm.laplacian(f, 137)
+    for a, b in level_shards(137, nparts):
+        if a == b:
+            continue
+        sx = torch.zeros_like(f)
+        sy = torch.zeros_like(f)
+        sd = torch.zeros_like(f)
+        sl = torch.zeros_like(f)
+        fvm.gradient(f[:, a:], b - a, out=(sx[:, a:], sy[:, a:]))
+        fvm.divergence(u[:, a:], v[:, a:], b - a, out=sd[:, a:])
+        fvm.laplacian(f[:, a:], b - a, out=sl[:, a:])
+        torch.cuda.synchronize()
+        for s_, w in ((sx, gx), (sy, gy), (sd, d), (sl, lap)):
+            assert torch.equal(s_[:, a:b], w[:, a:b]), (a, b)

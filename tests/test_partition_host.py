@@ -1,0 +1,138 @@
+"""Band partitions (host side) and the halo exchange, on CPU.
+
+The partition geometry comes from the C ABI without a GPU; the exchange runs
+as gloo ranks on CPU tensors.  What is checked: the parts tile the nodes
+with whole rows, every stencil neighbour of an own node lies in the part's
+halo range (one ring, or two for the fused Laplacian), the send and receive
+ranges of adjacent parts match, and after one exchange every part's local
+field equals the whole field on its halo range."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+@pytest.fixture(scope="module")
+def part_mod(product):
+    from paper_1908_07038_gb300 import partition
+    return partition
+
+
+@pytest.mark.parametrize("halo", [1, 2])
+@pytest.mark.parametrize("nparts", [1, 2, 3, 5, 8])
+def test_parts_tile_the_nodes_in_whole_rows(pfvm, part_mod, nparts, halo):
+    fvm = pfvm(16)
+    off = np.concatenate([[0], np.cumsum(fvm.grid.arrays()["pl"])])
+    parts = [part_mod.Partition(fvm, nparts, p, halo) for p in range(nparts)]
+    assert parts[0].own0 == 0 and parts[-1].own1 == fvm.nnodes
+    for a, b in zip(parts, parts[1:]):
+        assert a.own1 == b.own0
+    sizes = []
+    for p in parts:
+        r0, r1 = np.searchsorted(off, p.own0), np.searchsorted(off, p.own1)
+        assert off[r0] == p.own0 and off[r1] == p.own1 and r1 - r0 >= halo
+        assert p.halo0 == off[max(0, r0 - halo)] and p.halo1 == off[min(len(off) - 1, r1 + halo)]
+        sizes.append(p.own1 - p.own0)
+    # about equal shares: no part more than one row's worth off the mean
+    assert max(sizes) - min(sizes) <= 2 * max(np.diff(off)) + 1
+    for p in parts:
+        p.close()
+
+
+@pytest.mark.parametrize("op,halo", [("gradient", 1), ("divergence", 1), ("curl", 1), ("gradient_adjoint", 1),
+                                     ("divergence_adjoint", 1), ("vector_gradient", 1), ("laplacian", 2)])
+def test_halo_holds_every_stencil_neighbour(pfvm, part_mod, op, halo):
+    fvm = pfvm(16)
+    t = fvm.stencil_table(op)
+    ptr, nbr = t["ptr"], t["nbr"]
+    for nparts in (2, 4, 7):
+        for k in range(nparts):
+            p = part_mod.Partition(fvm, nparts, k, halo)
+            cols = nbr[ptr[p.own0]:ptr[p.own1]]
+            assert cols.min() >= p.halo0 and cols.max() < p.halo1
+            p.close()
+
+
+def test_neighbour_ranges_match(pfvm, part_mod):
+    fvm = pfvm(16)
+    for halo in (1, 2):
+        parts = [part_mod.Partition(fvm, 4, k, halo) for k in range(4)]
+        for k, p in enumerate(parts):
+            for n in p.neighbours:
+                q = parts[n["peer"]]
+                back = [m for m in q.neighbours if m["peer"] == k][0]
+                assert back["recv"] == n["send"] and back["send"] == n["recv"]
+                assert p.own0 <= n["send"][0] < n["send"][1] <= p.own1
+                assert p.halo0 <= n["recv"][0] < n["recv"][1] <= p.halo1
+                assert not (p.own0 <= n["recv"][0] < p.own1)
+        for p in parts:
+            p.close()
+
+
+def test_partition_errors(pfvm, part_mod, product):
+    atlas, capi = product
+    fvm = pfvm(8)  # 16 rows
+    with pytest.raises(capi.AtlasError):
+        part_mod.Partition(fvm, 9, 0, 2)  # 9 parts of >= 2 rows do not fit 16 rows
+    with pytest.raises(capi.AtlasError):
+        part_mod.Partition(fvm, 2, 2, 1)
+    with pytest.raises(capi.AtlasError):
+        part_mod.Partition(fvm, 2, 0, 3)
+    f2 = atlas.build_fvm(4)
+    p = part_mod.Partition(f2, 2, 0, 1)
+    f2.close()  # refused while the partition holds it: the handle stays valid
+    assert p.own1 > 0
+    p.close()
+
+
+def test_level_shards(part_mod):
+    for nlev, n in ((137, 2), (137, 3), (137, 8), (5, 4), (1, 1)):
+        sh = part_mod.level_shards(nlev, n)
+        assert sh[0][0] == 0 and sh[-1][1] == nlev and len(sh) == n
+        for (a, b), (c, d) in zip(sh, sh[1:]):
+            assert b == c
+        for a, b in sh:
+            assert a % 4 == 0 and a <= b
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _exchange_rank(rank, world, port, halo, out_dir):
+    import torch
+    import torch.distributed as dist
+    from paper_1908_07038_gb300 import atlas
+    from paper_1908_07038_gb300.partition import Partition
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        fvm = atlas.build_fvm(16)
+        whole = torch.from_numpy(np.random.default_rng(9).standard_normal((fvm.nnodes, 6)))
+        p = Partition(fvm, world, rank, halo)
+        local = torch.full((p.local_rows, 6), float("nan"), dtype=torch.float64)
+        p.own_of_local(local).copy_(whole[p.own0:p.own1])
+        p.exchange(local)
+        ok = torch.equal(local, whole[p.halo0:p.halo1])
+        with open(os.path.join(out_dir, "rank%d.txt" % rank), "w") as fh:
+            fh.write("ok" if ok else "mismatch")
+        p.close()
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,halo", [(2, 1), (3, 2)])
+def test_halo_exchange_gloo(tmp_path, product, world, halo):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    mp.spawn(_exchange_rank, args=(world, _free_port(), halo, str(tmp_path)), nprocs=world, join=True)
+    for r in range(world):
+        assert (tmp_path / ("rank%d.txt" % r)).read_text() == "ok"
