@@ -976,3 +976,100 @@ void orc_closure(const orc_mesh *m, double *res /* [V][2] */, double *absum /* [
     absum[i] = s;
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Remapping (paper Sec. 4.3, Fig. 6: a field on an O32 grid is remapped to */
+/* an F8 grid with a linear element-based interpolation in 3D on the       */
+/* sphere).  Reading: a target point with unit vector p lies in the source  */
+/* triangle whose plane the ray from the centre along p crosses inside the  */
+/* triangle; its value is the linear (barycentric) interpolation of the     */
+/* three vertex values at that crossing point.  The crossing is solved with */
+/* Cramer's rule for t p = a + u (b - a) + v (c - a) (the Moller-Trumbore   */
+/* form); weights (1 - u - v, u, v).  Brute force over every triangle; when */
+/* several contain the crossing (on a shared edge or vertex, up to 1e-12)   */
+/* the one whose smallest weight is largest is taken, the lowest triangle   */
+/* id on equality.  A target in a polar cap (north of the first row or      */
+/* south of the last, where the mesh has no triangle) is not located.      */
+/* ------------------------------------------------------------------------ */
+static void unit_vector(double lon, double lat, double v[3]) {
+  v[0] = cos(lat) * cos(lon);
+  v[1] = cos(lat) * sin(lon);
+  v[2] = sin(lat);
+}
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void node_vector(const orc_mesh *m, int64_t i, double v[3]) {
+  int r = m->node_row[i];
+  double lon = TWO_PI * ((double)m->node_j[i] / (double)m->pl[r]);
+  unit_vector(lon, m->lat[r], v);
+}
+
+/* nodes[t][3], w[t][3] for every target (lon, lat) in radians.  Returns 0,
+ * or -4 when a target lies in no triangle (its nodes are set to -1). */
+int orc_remap(const orc_mesh *m, const double *lonlat, int64_t ntgt, int32_t *nodes, double *w) {
+  if (!m || !lonlat || !nodes || !w || ntgt < 0) return -1;
+  double *vx = (double *)malloc(sizeof(double) * 3 * m->nnodes);
+  if (!vx) return -2;
+  for (int64_t i = 0; i < m->nnodes; ++i) node_vector(m, i, vx + 3 * i);
+  int rc = 0;
+  for (int64_t t = 0; t < ntgt; ++t) {
+    double p[3];
+    unit_vector(lonlat[2 * t], lonlat[2 * t + 1], p);
+    double best = -1e300;
+    int64_t bq = -1;
+    double bw[3] = {0, 0, 0};
+    for (int64_t q = 0; q < m->ntri; ++q) {
+      const double *a = vx + 3 * m->tri[3 * q], *b = vx + 3 * m->tri[3 * q + 1], *c = vx + 3 * m->tri[3 * q + 2];
+      double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      double P[3], Q[3], T[3] = {-a[0], -a[1], -a[2]};
+      cross3(p, e2, P);
+      double det = dot3(e1, P);
+      if (fabs(det) < 1e-300) continue;
+      double inv = 1.0 / det;
+      double u = dot3(T, P) * inv;
+      cross3(T, e1, Q);
+      double v = dot3(p, Q) * inv;
+      double tt = dot3(e2, Q) * inv;
+      if (tt <= 0) continue; /* the far side of the sphere */
+      double w0 = 1.0 - u - v;
+      double mn = fmin(w0, fmin(u, v));
+      if (mn < -1e-12) continue;
+      if (mn > best) {
+        best = mn;
+        bq = q;
+        bw[0] = w0; bw[1] = u; bw[2] = v;
+      }
+    }
+    if (bq < 0) {
+      nodes[3 * t] = nodes[3 * t + 1] = nodes[3 * t + 2] = -1;
+      w[3 * t] = w[3 * t + 1] = w[3 * t + 2] = 0;
+      rc = -4;
+      continue;
+    }
+    for (int k = 0; k < 3; ++k) {
+      nodes[3 * t + k] = m->tri[3 * bq + k];
+      w[3 * t + k] = bw[k];
+    }
+  }
+  free(vx);
+  return rc;
+}
+
+/* out[t][k] = sum_q w[t][q] f[nodes[t][q]][k], accumulated with Dot2. */
+int orc_remap_apply(const int32_t *nodes, const double *w, int64_t ntgt, const void *f, int f32, int64_t ld, int nlev,
+                    double *out) {
+  if (!nodes || !w || !f || ntgt < 0 || nlev < 0 || ld < nlev) return -1;
+  for (int64_t t = 0; t < ntgt; ++t)
+    for (int k = 0; k < nlev; ++k) {
+      acc_t a = {0, 0};
+      for (int q = 0; q < 3; ++q) acc_add_prod(&a, w[3 * t + q], fld(f, f32, ld, nodes[3 * t + q], k));
+      out[t * nlev + k] = acc_val(&a);
+    }
+  return 0;
+}

@@ -65,6 +65,8 @@ def _load():
         lib.orc_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
         lib.orc_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
         lib.orc_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_remap.argtypes = [P, P, i64, P, P]
+        lib.orc_remap_apply.argtypes = [P, P, i64, P, ctypes.c_int, i64, ctypes.c_int, P]
         lib.orc_vector_gradient.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P, P, P]
         lib.orc_gradient_triplets.restype = i64
         lib.orc_gradient_triplets.argtypes = [P, P, P, P]
@@ -74,7 +76,7 @@ def _load():
         lib.orc_closure.argtypes = [P, P, P]
         for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
                      "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
-                     "orc_vector_gradient"):
+                     "orc_vector_gradient", "orc_remap", "orc_remap_apply"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -216,6 +218,30 @@ class Mesh:
         if rc:
             raise ValueError("orc_vector_gradient rc=%d" % rc)
         return tuple(o)
+
+    def remap_weights(self, lonlat):
+        """(nodes [T][3], weights [T][3]) locating each target (lon, lat) in
+        radians in this mesh (linear interpolation in 3D on the sphere);
+        raises if a target lies in no triangle."""
+        lonlat = np.ascontiguousarray(lonlat, dtype=np.float64)
+        T = lonlat.shape[0]
+        nodes = np.empty((T, 3), np.int32)
+        w = np.empty((T, 3))
+        rc = self._lib.orc_remap(self._h, _ptr(lonlat), T, _ptr(nodes), _ptr(w))
+        if rc:
+            raise ValueError("orc_remap rc=%d" % rc)
+        return nodes, w
+
+    def remap(self, lonlat, f, nlev=None):
+        """Field f on this mesh's nodes remapped to the target points."""
+        nodes, w = self.remap_weights(lonlat)
+        f, f32, ld = _field(f)
+        nlev = f.shape[1] if nlev is None else nlev
+        out = np.empty((nodes.shape[0], nlev))
+        rc = self._lib.orc_remap_apply(_ptr(nodes), _ptr(w), nodes.shape[0], _ptr(f), f32, ld, nlev, _ptr(out))
+        if rc:
+            raise ValueError("orc_remap_apply rc=%d" % rc)
+        return out
 
     def laplacian(self, f, nlev=None, nodes=None):
         f, f32, ld = _field(f)
