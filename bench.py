@@ -362,6 +362,19 @@ def run_native(args):
                         "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
                         "launches": 2 if op == "vector_gradient" else 1,
                         "tuned": {k: mt[op][k] for k in ("vec", "batch", "threads", "tile")} if op in mt else None}
+        # remapping to the regular Gaussian grid of half the resolution
+        M = args.grid // 2
+        rm = atlas.Remap(fvm.mesh, atlas.Grid(M, regular=True))
+        rn, _ = rm.tables()
+        dst = torch.empty((rm.ntgt, ld), device="cuda")
+        ms = _max_over_ranks(tune.time_call(lambda: rm.apply(f, nlev, out=dst), reps=max(5, args.steps),
+                                            warmup=args.warmup), ws, "cuda")
+        used = int(np.unique(rn).size)  # source rows the targets read
+        b = (used + rm.ntgt) * nlev * 4 + rm.ntgt * 32
+        more["remap_to_F%d" % M] = {"ms": round(ms, 4), "target_levels_per_s": _job_rate(rm.ntgt * nlev, ws, ms),
+                                    "targets": rm.ntgt, "source_rows_read": used, "alg_bytes": b,
+                                    "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4), "launches": 1}
+        del dst, rm
 
     # ---------------------------------------------------------------- e2e
     # Host-resident fields through the public API: every step copies f, u, v

@@ -63,6 +63,7 @@ typedef struct atlas_grid_s* atlas_grid_t;
 typedef struct atlas_mesh_s* atlas_mesh_t;
 typedef struct atlas_fvm_s* atlas_fvm_t;
 typedef struct atlas_batch_s* atlas_batch_t;
+typedef struct atlas_remap_s* atlas_remap_t;
 
 typedef enum { ATLAS_F32 = 0, ATLAS_F64 = 1, ATLAS_BF16 = 2 } atlas_dtype;
 
@@ -114,6 +115,11 @@ int atlas_grid_octahedral(int N, atlas_grid_t* out);
 /* Any output pointer may be NULL.                                         */
 int atlas_grid_info(atlas_grid_t g, int64_t* nnodes, int* nlat, const int32_t** pl,
                     const double** lonlat, const double** lat);
+/* Regular (full) Gaussian grid F<N>, 1 <= N <= 8000 (paper Sec. 4.3,     */
+/* Fig. 4 and 6: the coarse "F8" grid): the 2N Gaussian latitudes of O<N>, */
+/* each with 4N equally spaced longitudes from 0; 8N^2 points, same node   */
+/* order.  A point set: usable as a remapping target, not for meshes.      */
+int atlas_grid_regular_gaussian(int N, atlas_grid_t* out);
 void atlas_grid_destroy(atlas_grid_t g);
 
 /* ---------------------------------------------------------------------- */
@@ -304,6 +310,32 @@ int atlas_batch_launch(atlas_batch_t b, void* stream);
 /* Total tiles and total (node, level) pairs of the batch.                  */
 int atlas_batch_info(atlas_batch_t b, int64_t* tiles, int64_t* node_levels);
 void atlas_batch_destroy(atlas_batch_t b);
+
+/* ---------------------------------------------------------------------- */
+/* Remapping between grids (paper Sec. 4.3, Fig. 6: a field on an O32 grid */
+/* remapped to an F8 grid by a linear element-based interpolation in 3D on */
+/* the sphere).  Every target point (unit vector p) is located in the      */
+/* source mesh triangle whose plane the ray from the centre along p        */
+/* crosses inside the triangle; its three weights are the barycentric      */
+/* coordinates of that crossing (of several containing triangles: the one  */
+/* whose smallest weight is largest, then the lowest triangle id).  Built  */
+/* on the host; fails with ATLAS_EINVAL if a target lies in a polar cap    */
+/* (north of the source's first row or south of its last), which no        */
+/* triangle covers.  The remap keeps its mesh and grid alive.              */
+/* ---------------------------------------------------------------------- */
+int atlas_remap_create(atlas_mesh_t src, atlas_grid_t dst, atlas_remap_t* out);
+/* Views valid until atlas_remap_destroy: ntgt (the target grid's points), */
+/* nodes[ntgt][3] source node ids and weights[ntgt][3].                    */
+int atlas_remap_info(atlas_remap_t r, int64_t* ntgt, const int32_t** nodes, const double** weights);
+/* dst[t][k] = sum_q weights[t][q] src[nodes[t][q]][k] for the targets t    */
+/* and levels k < nlev: src is a field[source node][ld_src], dst a          */
+/* field[target][ld_dst] (device pointers, one dtype).  Padding levels of  */
+/* dst up to the end of the last 16-byte vector are set to zero when       */
+/* ld_dst allows whole vectors.  Tables are uploaded on the first call of   */
+/* a precision.                                                            */
+int atlas_remap_apply(atlas_remap_t r, const void* src, void* dst, int nlev, int64_t ld_src, int64_t ld_dst,
+                      atlas_dtype dtype, void* stream);
+void atlas_remap_destroy(atlas_remap_t r);
 
 /* ---------------------------------------------------------------------- */
 /* Band partitions (paper Sec. 2.3: a mesh may be split into partitions,  */

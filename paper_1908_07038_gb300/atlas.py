@@ -33,13 +33,19 @@ def _view(ptr, ctype, n, shape=None, dtype=None):
 
 
 class Grid:
-    """Octahedral reduced Gaussian grid O<N> (library-owned handle)."""
+    """Octahedral reduced Gaussian grid O<N>, or with ``regular=True`` the
+    regular (full) Gaussian grid F<N> (a point set for remapping targets);
+    library-owned handle."""
 
-    def __init__(self, N: int):
+    def __init__(self, N: int, regular: bool = False):
         h = ctypes.c_void_p()
-        capi.atlas_grid_octahedral(int(N), ctypes.byref(h))
+        if regular:
+            capi.atlas_grid_regular_gaussian(int(N), ctypes.byref(h))
+        else:
+            capi.atlas_grid_octahedral(int(N), ctypes.byref(h))
         self.handle = h
         self.N = int(N)
+        self.regular = bool(regular)
         nn = ctypes.c_int64()
         nl = ctypes.c_int()
         capi.atlas_grid_info(h, ctypes.byref(nn), ctypes.byref(nl), None, None, None)
@@ -268,6 +274,53 @@ class Fvm:
     def close(self):
         if self.handle is not None and self.handle.value:
             capi.atlas_fvm_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Remap:
+    """Linear interpolation in 3D on the sphere from the nodes of ``mesh`` to
+    the points of ``grid`` (located and weighted on the host, applied by a
+    CUDA kernel)."""
+
+    def __init__(self, mesh: Mesh, grid: Grid):
+        h = ctypes.c_void_p()
+        capi.atlas_remap_create(mesh.handle, grid.handle, ctypes.byref(h))
+        self.handle, self.mesh, self.grid = h, mesh, grid
+        n = ctypes.c_int64()
+        capi.atlas_remap_info(h, ctypes.byref(n), None, None)
+        self.ntgt = n.value
+
+    def tables(self):
+        """(nodes [T][3] int32, weights [T][3] float64), copies."""
+        pn, pw = ctypes.c_void_p(), ctypes.c_void_p()
+        capi.atlas_remap_info(self.handle, None, ctypes.byref(pn), ctypes.byref(pw))
+        return (_view(pn, ctypes.c_int32, 3 * self.ntgt, (self.ntgt, 3)),
+                _view(pw, ctypes.c_double, 3 * self.ntgt, (self.ntgt, 3)))
+
+    def apply(self, src, nlev=None, out=None, ld_dst=None):
+        """src: CUDA tensor [source nodes, ld]; returns [targets, ld_dst]."""
+        torch = _torch()
+        if not src.is_cuda or src.dim() != 2 or src.stride(1) != 1:
+            raise ValueError("src must be a CUDA tensor [nodes, ld] with unit level stride")
+        nlev = src.shape[1] if nlev is None else int(nlev)
+        if out is None:
+            out = torch.empty((self.ntgt, src.stride(0) if ld_dst is None else int(ld_dst)), dtype=src.dtype,
+                              device=src.device)
+        if out.dtype != src.dtype or out.shape[0] != self.ntgt or out.stride(1) != 1:
+            raise ValueError("out must be [%d targets, ld] of the source dtype" % self.ntgt)
+        capi.atlas_remap_apply(self.handle, src.data_ptr(), out.data_ptr(), nlev, src.stride(0), out.stride(0),
+                               _dtype_code(src), _stream())
+        return out
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            capi.atlas_remap_destroy(self.handle)
         self.handle = None
 
     def __del__(self):

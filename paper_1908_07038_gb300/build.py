@@ -1,6 +1,6 @@
 """Build libatlasgb.so in-tree (nvcc for sm_103a + g++ for the host geometry).
 
-The three translation units compile in parallel into ``_build/`` and link
+The translation units compile in parallel into ``_build/`` and link
 into ``paper_1908_07038_gb300/libatlasgb.so``.  Host geometry is compiled
 with ``-ffp-contract=off`` so that its FP64 arithmetic is evaluated exactly
 as written on every host (x86-64 and aarch64 alike).
@@ -34,7 +34,7 @@ def _cuda_home() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "capi.cpp", "kernels.cu", "noalloc.cu")]
+    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "remap.cpp", "capi.cpp", "kernels.cu", "noalloc.cu")]
 
 
 def _headers():

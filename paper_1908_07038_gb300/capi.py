@@ -71,6 +71,11 @@ _SIGS = {
     "atlas_nabla_gradient_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_divergence_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_curl": (I32, [P, P, P, P, I32, I64, I32, P], True),
+    "atlas_grid_regular_gaussian": (I32, [I32, P], True),
+    "atlas_remap_create": (I32, [P, P, P], True),
+    "atlas_remap_info": (I32, [P, P, P, P], True),
+    "atlas_remap_apply": (I32, [P, P, P, I32, I64, I64, I32, P], True),
+    "atlas_remap_destroy": (None, [P], False),
     "atlas_part_create": (I32, [P, I32, I32, I32, P], True),
     "atlas_part_info": (I32, [P, P, P, P, P], True),
     "atlas_part_neighbour": (I32, [P, I32, P, P, P, P, P], True),

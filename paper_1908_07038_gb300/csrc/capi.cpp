@@ -567,6 +567,26 @@ int atlas_grid_octahedral(int N, atlas_grid_t* out) {
   return ok();
 }
 
+int atlas_grid_regular_gaussian(int N, atlas_grid_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (N < 1 || N > 8000) return fail(ATLAS_EINVAL, "Gaussian number N=%d out of range [1, 8000]", N);
+  atlas_grid_s* g = new (std::nothrow) atlas_grid_s();
+  if (!g) return fail(ATLAS_ENOMEM, "out of host memory");
+  try {
+    if (!atlasgb::build_regular_gaussian_grid(N, g->g)) {
+      delete g;
+      return fail(ATLAS_EINVAL, "grid build failed");
+    }
+  } catch (const std::bad_alloc&) {
+    delete g;
+    return fail(ATLAS_ENOMEM, "out of host memory building F%d", N);
+  }
+  reg(g);
+  *out = reinterpret_cast<atlas_grid_t>(g);
+  return ok();
+}
+
 int atlas_grid_info(atlas_grid_t h, int64_t* nnodes, int* nlat, const int32_t** pl, const double** lonlat,
                     const double** lat) {
   if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
@@ -583,7 +603,7 @@ void atlas_grid_destroy(atlas_grid_t h) {
   if (!live(h)) return;
   atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(h);
   if (g->users > 0) {
-    fail(ATLAS_ESTATE, "grid still used by %d mesh(es); not destroyed", g->users);
+    fail(ATLAS_ESTATE, "grid still used by %d mesh(es) or remap(s); not destroyed", g->users);
     return;
   }
   unreg(g);
@@ -595,6 +615,7 @@ int atlas_mesh_build(atlas_grid_t gh, atlas_mesh_t* out) {
   *out = nullptr;
   if (!live(gh)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
   atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(gh);
+  if (!g->g.octahedral) return fail(ATLAS_EINVAL, "meshes are built on octahedral grids only");
   atlas_mesh_s* m = new (std::nothrow) atlas_mesh_s();
   if (!m) return fail(ATLAS_ENOMEM, "out of host memory");
   try {
@@ -632,7 +653,7 @@ void atlas_mesh_destroy(atlas_mesh_t h) {
   if (!live(h)) return;
   atlas_mesh_s* m = reinterpret_cast<atlas_mesh_s*>(h);
   if (m->users > 0) {
-    fail(ATLAS_ESTATE, "mesh still used by %d fvm(s); not destroyed", m->users);
+    fail(ATLAS_ESTATE, "mesh still used by %d fvm(s) or remap(s); not destroyed", m->users);
     return;
   }
   unreg(m);
@@ -1060,6 +1081,153 @@ void atlas_part_destroy(atlas_part_t h) {
   unreg(p);
   p->fvm->users--;
   delete p;
+}
+
+}  // extern "C"
+
+// ============================================================== remapping
+struct atlas_remap_s {
+  atlas_mesh_s* src = nullptr;
+  atlas_grid_s* dst = nullptr;
+  int64_t ntgt = 0;
+  std::vector<int32_t> nodes;   // [T][3]
+  std::vector<double> weights;  // [T][3]
+  int device = -1, num_sms = 0;
+  std::mutex mu;
+  bool ready[2] = {false, false};  // device tables: float weights, double weights
+  const void* d_nodes[2] = {nullptr, nullptr};
+  const void* d_w[2] = {nullptr, nullptr};
+  DevAlloc mem[2];
+};
+
+extern "C" {
+
+int atlas_remap_create(atlas_mesh_t sh, atlas_grid_t th, atlas_remap_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!live(sh)) return fail(ATLAS_ESTATE, "invalid or destroyed mesh handle");
+  if (!live(th)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
+  atlas_mesh_s* m = reinterpret_cast<atlas_mesh_s*>(sh);
+  atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(th);
+  atlas_remap_s* r = new (std::nothrow) atlas_remap_s();
+  if (!r) return fail(ATLAS_ENOMEM, "out of host memory");
+  int64_t missed = 0;
+  try {
+    if (!atlasgb::build_remap(m->m, g->g.lonlat.data(), g->g.nnodes, r->nodes, r->weights, missed)) {
+      delete r;
+      return fail(ATLAS_EINVAL, "inconsistent source mesh");
+    }
+  } catch (const std::bad_alloc&) {
+    delete r;
+    return fail(ATLAS_ENOMEM, "out of host memory building the remap");
+  }
+  if (missed) {
+    delete r;
+    return fail(ATLAS_EINVAL, "%lld target points lie in the polar caps (no source triangle)",
+                static_cast<long long>(missed));
+  }
+  if (g->g.nnodes >= (int64_t(1) << 31)) {
+    delete r;
+    return fail(ATLAS_EINVAL, "too many target points");
+  }
+  r->src = m;
+  r->dst = g;
+  r->ntgt = g->g.nnodes;
+  int dev = -1;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    r->device = dev;
+    cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  } else {
+    cudaGetLastError();
+  }
+  m->users++;
+  g->users++;
+  reg(r);
+  *out = reinterpret_cast<atlas_remap_t>(r);
+  return ok();
+}
+
+int atlas_remap_info(atlas_remap_t h, int64_t* ntgt, const int32_t** nodes, const double** weights) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed remap handle");
+  const atlas_remap_s* r = reinterpret_cast<const atlas_remap_s*>(h);
+  if (ntgt) *ntgt = r->ntgt;
+  if (nodes) *nodes = r->nodes.data();
+  if (weights) *weights = r->weights.data();
+  return ok();
+}
+
+int atlas_remap_apply(atlas_remap_t h, const void* src, void* dst, int nlev, int64_t ld_src, int64_t ld_dst,
+                      atlas_dtype dtype, void* stream) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed remap handle");
+  atlas_remap_s* r = reinterpret_cast<atlas_remap_s*>(h);
+  const void* used[2] = {src, dst};
+  int rc = check_field_args(dtype, nlev, ld_src, used, 2);
+  if (rc) return rc;
+  if (ld_dst < nlev || ld_dst < 1) return fail(ATLAS_EINVAL, "ld_dst=%lld < nlev=%d", static_cast<long long>(ld_dst), nlev);
+  const int64_t es = elem_size(dtype);
+  const void* ins[1] = {src};
+  void* outs[1] = {dst};
+  rc = check_no_overlap2(ins, 1, r->src->grid->g.nnodes * ld_src * es, outs, 1, r->ntgt * ld_dst * es);
+  if (rc) return rc;
+  if (r->device < 0) return fail(ATLAS_ECUDA, "no CUDA device was available when this remap was built");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != r->device)
+    return fail(ATLAS_ESTATE, "remap lives on device %d, current device is %d", r->device, cur);
+  if (nlev == 0 || r->ntgt == 0) return ok();
+  const int prec = dtype == ATLAS_F64 ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (!r->ready[prec]) {
+      cudaError_t err = cudaSuccess;
+      std::vector<int32_t> n4(static_cast<size_t>(4 * r->ntgt), 0);
+      for (int64_t t = 0; t < r->ntgt; ++t)
+        for (int k = 0; k < 3; ++k) n4[4 * t + k] = r->nodes[3 * t + k];
+      r->d_nodes[prec] = r->mem[prec].upload(n4, err);
+      std::vector<double> w4(static_cast<size_t>(4 * r->ntgt), 0.0);
+      for (int64_t t = 0; t < r->ntgt; ++t)
+        for (int k = 0; k < 3; ++k) w4[4 * t + k] = r->weights[3 * t + k];
+      if (err == cudaSuccess)
+        r->d_w[prec] = prec ? static_cast<const void*>(r->mem[prec].upload(w4, err))
+                            : static_cast<const void*>(r->mem[prec].upload(convert<float>(w4), err));
+      if (err != cudaSuccess) {
+        r->mem[prec].release();
+        return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for remap tables")
+                                                : cuda_fail(err, "upload of remap tables");
+      }
+      r->ready[prec] = true;
+    }
+  }
+  atlasgb::RemapLaunch l;
+  l.nodes = r->d_nodes[prec];
+  l.weights = r->d_w[prec];
+  l.src = src;
+  l.dst = dst;
+  l.ntgt = static_cast<int32_t>(r->ntgt);
+  l.nlev = nlev;
+  l.ld_src = ld_src;
+  l.ld_dst = ld_dst;
+  // one levels-per-thread width for both fields: the widest both allow
+  l.vec = std::min(pick_vec(dtype, ld_src, used, 2, 0), pick_vec(dtype, ld_dst, used, 2, 0));
+  const int64_t nvec = (nlev + l.vec - 1) / l.vec;
+  if (r->ntgt * nvec >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "targets * level-vectors must stay below 2^31");
+  l.idx32 = r->src->grid->g.nnodes * ld_src < (int64_t(1) << 31) && r->ntgt * ld_dst < (int64_t(1) << 31);
+  l.threads = 256;
+  const int64_t need = (r->ntgt * nvec + l.threads - 1) / l.threads;
+  l.blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(r->num_sms) * 8)));
+  cudaError_t e = atlasgb::launch_remap(storage_of(dtype), l, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "remap kernel launch");
+  return ok();
+}
+
+void atlas_remap_destroy(atlas_remap_t h) {
+  if (!live(h)) return;
+  atlas_remap_s* r = reinterpret_cast<atlas_remap_s*>(h);
+  unreg(r);
+  r->mem[0].release();
+  r->mem[1].release();
+  r->src->users--;
+  r->dst->users--;
+  delete r;
 }
 
 }  // extern "C"

@@ -17,6 +17,7 @@ namespace atlasgb {
 struct Grid {
   int N = 0;
   int nlat = 0;
+  bool octahedral = true;      // false: regular (full) Gaussian grid F<N>, points only
   int64_t nnodes = 0;
   std::vector<int32_t> pl;     // points per row, north -> south
   std::vector<int64_t> off;    // first node of each row, size nlat+1
@@ -103,5 +104,18 @@ struct PairStencil {
   std::vector<double> w;      // [nnz][2] (weight of node 2g, of node 2g+1)
 };
 bool build_pair_stencil(const Stencil& s, PairStencil& p);
+
+// Regular (full) Gaussian grid F<N>: the 2N Gaussian latitudes of O<N>, each
+// with 4N longitudes j/(4N) turns.  A point set (a remapping target); meshes
+// are built on octahedral grids only.
+bool build_regular_gaussian_grid(int N, Grid& g);
+
+// Remapping weights (remap.cpp): for every target (lon, lat) in radians, the
+// three source nodes nodes[3t..3t+2] and weights of the linear interpolation
+// in 3D on the sphere in the source mesh's triangle that contains it.
+// not_located counts targets in no triangle (the polar caps); their nodes
+// are -1 and weights 0.  Returns false on an inconsistent mesh.
+bool build_remap(const Mesh& m, const double* tgt_lonlat, int64_t ntgt, std::vector<int32_t>& nodes,
+                 std::vector<double>& weights, int64_t& not_located);
 
 }  // namespace atlasgb

@@ -545,6 +545,36 @@ __global__ void __launch_bounds__(256, 5) batch_kernel(const __grid_constant__ B
   }
 }
 
+// ------------------------------------------------------------- remapping
+// Linear interpolation in 3D on the sphere from a source mesh to target
+// points: dst[t][k] = w0 src[n0][k] + w1 src[n1][k] + w2 src[n2][k], one
+// (target, level-vector) item per thread.  The target's three nodes and
+// weights (tn[t] = {n0, n1, n2, 0}, tw[t] = {w0, w1, w2, 0}) are the same
+// for the items of a warp; the three source rows are requested together.
+template <typename S, typename A, int VEC, bool IDX32>
+__global__ void __launch_bounds__(512) remap_kernel(const int4* __restrict__ tn, const A* __restrict__ tw,
+                                                    const S* __restrict__ src, S* __restrict__ dst, int32_t ntgt,
+                                                    int32_t nlev, int64_t ld_src, int64_t ld_dst, uint32_t nvec,
+                                                    Div32 dv) {
+  using Idx = typename IdxT<IDX32>::T;
+  const uint32_t total = static_cast<uint32_t>(ntgt) * nvec;  // host guarantees < 2^31
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
+    const uint32_t t = div_by(item, dv);
+    const int32_t lev0 = static_cast<int32_t>((item - t * nvec) * VEC);
+    const int4 n = __ldg(tn + t);
+    const A w0 = __ldg(tw + 4 * static_cast<Idx>(t)), w1 = __ldg(tw + 4 * static_cast<Idx>(t) + 1),
+            w2 = __ldg(tw + 4 * static_cast<Idx>(t) + 2);
+    A x0[VEC], x1[VEC], x2[VEC], y[VEC];
+    vload<S, A, VEC>(src + static_cast<Idx>(n.x) * static_cast<Idx>(ld_src) + static_cast<Idx>(lev0), x0);
+    vload<S, A, VEC>(src + static_cast<Idx>(n.y) * static_cast<Idx>(ld_src) + static_cast<Idx>(lev0), x1);
+    vload<S, A, VEC>(src + static_cast<Idx>(n.z) * static_cast<Idx>(ld_src) + static_cast<Idx>(lev0), x2);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) y[k] = fma(w2, x2[k], fma(w1, x1[k], w0 * x0[k]));
+    vstore<S, A, VEC>(dst + static_cast<Idx>(t) * static_cast<Idx>(ld_dst) + static_cast<Idx>(lev0), y, nlev - lev0);
+  }
+}
+
 // ---------------------------------------------------------------- dispatch
 template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
@@ -773,6 +803,34 @@ const void* batch_fn(StorageType st, int vec, bool idx32) {
   return idx32 ? batch_fn_t<true>(st, vec) : batch_fn_t<false>(st, vec);
 }
 }  // namespace
+
+namespace {
+template <typename S, typename A, int VEC, bool IDX32>
+cudaError_t run_remap(const RemapLaunch& r, cudaStream_t stream) {
+  const uint32_t nvec = static_cast<uint32_t>((r.nlev + VEC - 1) / VEC);
+  remap_kernel<S, A, VEC, IDX32><<<r.blocks, r.threads, 0, stream>>>(
+      static_cast<const int4*>(r.nodes), static_cast<const A*>(r.weights), static_cast<const S*>(r.src),
+      static_cast<S*>(r.dst), r.ntgt, r.nlev, r.ld_src, r.ld_dst, nvec, make_div32(nvec));
+  return cudaGetLastError();
+}
+template <typename S, typename A, int MAXVEC, bool IDX32>
+cudaError_t remap_vec(const RemapLaunch& r, cudaStream_t stream) {
+  if (r.vec >= 8 && MAXVEC >= 8) return run_remap<S, A, (MAXVEC >= 8 ? 8 : 1), IDX32>(r, stream);
+  if (r.vec >= 4 && MAXVEC >= 4) return run_remap<S, A, (MAXVEC >= 4 ? 4 : 1), IDX32>(r, stream);
+  if (r.vec >= 2 && MAXVEC >= 2) return run_remap<S, A, (MAXVEC >= 2 ? 2 : 1), IDX32>(r, stream);
+  return run_remap<S, A, 1, IDX32>(r, stream);
+}
+template <bool IDX32>
+cudaError_t remap_st(StorageType st, const RemapLaunch& r, cudaStream_t stream) {
+  if (st == ST_F64) return remap_vec<double, double, 2, IDX32>(r, stream);
+  if (st == ST_BF16) return remap_vec<uint16_t, float, 8, IDX32>(r, stream);
+  return remap_vec<float, float, 4, IDX32>(r, stream);
+}
+}  // namespace
+
+cudaError_t launch_remap(StorageType st, const RemapLaunch& r, cudaStream_t stream) {
+  return r.idx32 ? remap_st<true>(st, r, stream) : remap_st<false>(st, r, stream);
+}
 
 cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchParams& params, int threads, int blocks,
                          cudaStream_t stream) {

@@ -121,4 +121,19 @@ cudaError_t launch_batch(StorageType st, int vec, bool idx32, const BatchParams&
                          cudaStream_t stream);
 int batch_occupancy(StorageType st, int vec, bool idx32, int threads);
 
+// Remapping by linear interpolation: nodes int4[ntgt] {n0, n1, n2, 0},
+// weights A[ntgt][4] (float for F32/BF16 fields, double for F64).
+struct RemapLaunch {
+  const void* nodes = nullptr;
+  const void* weights = nullptr;
+  const void* src = nullptr;
+  void* dst = nullptr;
+  int32_t ntgt = 0, nlev = 0;
+  int64_t ld_src = 0, ld_dst = 0;
+  int vec = 1;
+  bool idx32 = true;
+  int threads = 256, blocks = 1;
+};
+cudaError_t launch_remap(StorageType st, const RemapLaunch& r, cudaStream_t stream);
+
 }  // namespace atlasgb
