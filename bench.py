@@ -241,7 +241,15 @@ _NNZ = {}
 def _table_bytes(fvm, op, wbytes):
     if op not in _NNZ:
         _NNZ[op] = fvm.stencil_table(op)["nbr"].shape[0]
-    nnz = _NNZ[op]
+    return _table_bytes_nnz(fvm, op, wbytes, _NNZ[op])
+
+
+def _table_bytes_of(fvm, op, wbytes):
+    """_table_bytes for an fvm other than the benchmark's (no caching)."""
+    return _table_bytes_nnz(fvm, op, wbytes, fvm.stencil_table(op)["nbr"].shape[0])
+
+
+def _table_bytes_nnz(fvm, op, wbytes, nnz):
     V = fvm.nnodes
     has_b = op in ("divergence", "gradient_adjoint", "divergence_adjoint", "curl", "vector_gradient")
     nw = 1 if op == "laplacian" else 2
@@ -375,6 +383,21 @@ def run_native(args):
                                     "targets": rm.ntgt, "source_rows_read": used, "alg_bytes": b,
                                     "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4), "launches": 1}
         del dst, rm
+        # the regular Gaussian grid of the same latitudes (F<N/2>, 8 (N/2)^2 nodes)
+        ff = atlas.build_fvm(M, regular=True)
+        ff.prepare(("gradient", "laplacian"), dtypes=(atlas.ATLAS_F32,))
+        Vf = ff.nnodes
+        xf = torch.randn((Vf, ld), device="cuda")
+        of = [torch.empty_like(xf) for _ in range(2)]
+        if not args.no_tune:
+            tune.tune_fvm(ff, atlas.ATLAS_F32, nlev, ld, ("gradient", "laplacian"), fields=(xf, xf, xf), reps=3)
+        for op, call in (("gradient", lambda: ff.gradient(xf, nlev, out=(of[0], of[1]))),
+                         ("laplacian", lambda: ff.laplacian(xf, nlev, out=of[0]))):
+            ms = _max_over_ranks(tune.time_call(call, reps=max(5, args.steps), warmup=args.warmup), ws, "cuda")
+            b = _alg_bytes(op, Vf, nlev, 4, _table_bytes_of(ff, op, 4))
+            more["%s_F%d" % (op, M)] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(Vf * nlev, ws, ms),
+                                        "nodes": Vf, "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4)}
+        del xf, of, ff
 
     # ---------------------------------------------------------------- e2e
     # Host-resident fields through the public API: every step copies f, u, v

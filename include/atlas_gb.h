@@ -118,7 +118,9 @@ int atlas_grid_info(atlas_grid_t g, int64_t* nnodes, int* nlat, const int32_t** 
 /* Regular (full) Gaussian grid F<N>, 1 <= N <= 8000 (paper Sec. 4.3,     */
 /* Fig. 4 and 6: the coarse "F8" grid): the 2N Gaussian latitudes of O<N>, */
 /* each with 4N equally spaced longitudes from 0; 8N^2 points, same node   */
-/* order.  A point set: usable as a remapping target, not for meshes.      */
+/* order.  A remapping target, and a grid for meshes and operators like    */
+/* O<N> (the zipper then meets equal rows on every band; pole edges join  */
+/* node j to j + 2N on the first and last row).                            */
 int atlas_grid_regular_gaussian(int N, atlas_grid_t* out);
 void atlas_grid_destroy(atlas_grid_t g);
 
@@ -129,7 +131,8 @@ void atlas_grid_destroy(atlas_grid_t g);
 /* whose next longitude is smaller; on a tie the row with fewer points,    */
 /* between equal rows the northern one), plus pole edges joining node j to */
 /* j + n/2 on the first and last row.  Edges are (a, b) with a < b, sorted */
-/* by (a, b); 4N^2+36N nodes give 2V-40 triangles and 3V-20 edges.          */
+/* by (a, b); 4N^2+36N nodes give 2V-40 triangles and 3V-20 edges (F<N>: */
+/* 8N^2 nodes, 2V-8N triangles, 3V-4N edges).                               */
 int atlas_mesh_build(atlas_grid_t g, atlas_mesh_t* out);
 /* Views valid until atlas_mesh_destroy: e2n[E][2], is_pole[E],            */
 /* n2e_ptr[V+1], n2e[2E] (ascending edge ids per node), n2e_sign[2E]       */

@@ -214,8 +214,11 @@ static int cmp_u64(const void *x, const void *y) {
 void orc_free(orc_mesh *m);
 
 /* a2 + a3 + a4: grid, zipper triangulation with pole edges, CSR, median dual.
+ * regular = 0: the octahedral grid O<N> (rows of 4i+16 points); regular = 1:
+ * the regular Gaussian grid F<N> (4N points on every row, paper Sec. 4.3,
+ * Fig. 4), meshed by the same zipper (every band is then an equal-row band).
  * Returns NULL on invalid N or allocation failure. */
-orc_mesh *orc_build(int N, double R) {
+orc_mesh *orc_build_grid(int N, double R, int regular) {
   if (N < 1 || N > 8000 || !(R > 0)) return NULL;
   orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
   if (!m) return NULL;
@@ -234,10 +237,10 @@ orc_mesh *orc_build(int N, double R) {
   for (int r = 0; r < nlat; ++r) m->lat[r] = HALF_PI - m->colat[r];
   for (int r = 0; r < N; ++r) m->lat[nlat - 1 - r] = -m->lat[r];
 
-  /* a2: octahedral rows */
+  /* a2: octahedral (or regular) rows */
   m->off[0] = 0;
   for (int r = 0; r < nlat; ++r) {
-    m->pl[r] = row_size(N, r);
+    m->pl[r] = regular ? 4 * N : row_size(N, r);
     m->off[r + 1] = m->off[r] + m->pl[r];
   }
   int64_t V = m->off[nlat];
@@ -460,6 +463,8 @@ orc_mesh *orc_build(int N, double R) {
   free(vacc);
   return m;
 }
+
+orc_mesh *orc_build(int N, double R) { return orc_build_grid(N, R, 0); }
 
 void orc_free(orc_mesh *m) {
   if (!m) return;

@@ -53,6 +53,8 @@ def _load():
         i64 = ctypes.c_int64
         lib.orc_build.restype = P
         lib.orc_build.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_build_grid.restype = P
+        lib.orc_build_grid.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
         lib.orc_free.argtypes = [P]
         lib.orc_counts.argtypes = [P, P]
         lib.orc_gauss_colatitudes.argtypes = [ctypes.c_int, P]
@@ -110,9 +112,11 @@ def _field(x):
 class Mesh:
     """Oracle grid + mesh + median dual for the octahedral grid O<N>."""
 
-    def __init__(self, N: int, R: float = R_EARTH):
+    def __init__(self, N: int, R: float = R_EARTH, regular: bool = False):
+        """Octahedral grid O<N>, or with regular=True the regular Gaussian
+        grid F<N> (4N points per row), meshed and dualised the same way."""
         lib = _load()
-        h = lib.orc_build(int(N), float(R))
+        h = lib.orc_build_grid(int(N), float(R), int(bool(regular)))
         if not h:
             raise ValueError("oracle mesh build failed for N=%r" % (N,))
         self._h = ctypes.c_void_p(h)

@@ -330,9 +330,9 @@ class Remap:
             pass
 
 
-def build_fvm(N: int, radius: float = R_EARTH) -> Fvm:
-    """Grid O<N> -> Mesh -> median-dual Fvm in one call."""
-    g = Grid(N)
+def build_fvm(N: int, radius: float = R_EARTH, regular: bool = False) -> Fvm:
+    """Grid O<N> (or F<N> with regular=True) -> Mesh -> median-dual Fvm in one call."""
+    g = Grid(N, regular=regular)
     m = Mesh(g)
     return Fvm(m, radius)
 

@@ -615,7 +615,6 @@ int atlas_mesh_build(atlas_grid_t gh, atlas_mesh_t* out) {
   *out = nullptr;
   if (!live(gh)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
   atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(gh);
-  if (!g->g.octahedral) return fail(ATLAS_EINVAL, "meshes are built on octahedral grids only");
   atlas_mesh_s* m = new (std::nothrow) atlas_mesh_s();
   if (!m) return fail(ATLAS_ENOMEM, "out of host memory");
   try {

@@ -217,7 +217,8 @@ bool build_mesh(const Grid& g, Mesh& m) {
   fe.first.assign(static_cast<size_t>(V) + 1, 0);
   for (int64_t i = 0; i < V; ++i) fe.first[i + 1] = fe.first[i] + cnt[i];
   const int64_t E = fe.first[V];
-  if (E != 3 * V - 20) return false;
+  // ring edges V, cross edges 2V - n_first - n_last, pole edges (n_first + n_last)/2
+  if (E != 3 * V - (g.pl[0] + g.pl[nlat - 1]) / 2) return false;
   m.nedges = E;
   fe.b.assign(static_cast<size_t>(E), -1);
   std::vector<int32_t> fill(fe.first.begin(), fe.first.end() - 1);

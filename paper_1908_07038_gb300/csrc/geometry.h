@@ -17,7 +17,7 @@ namespace atlasgb {
 struct Grid {
   int N = 0;
   int nlat = 0;
-  bool octahedral = true;      // false: regular (full) Gaussian grid F<N>, points only
+  bool octahedral = true;      // false: regular (full) Gaussian grid F<N>
   int64_t nnodes = 0;
   std::vector<int32_t> pl;     // points per row, north -> south
   std::vector<int64_t> off;    // first node of each row, size nlat+1
@@ -106,8 +106,8 @@ struct PairStencil {
 bool build_pair_stencil(const Stencil& s, PairStencil& p);
 
 // Regular (full) Gaussian grid F<N>: the 2N Gaussian latitudes of O<N>, each
-// with 4N longitudes j/(4N) turns.  A point set (a remapping target); meshes
-// are built on octahedral grids only.
+// with 4N longitudes j/(4N) turns.  A remapping target, and meshed by the
+// same zipper as O<N>.
 bool build_regular_gaussian_grid(int N, Grid& g);
 
 // Remapping weights (remap.cpp): for every target (lon, lat) in radians, the

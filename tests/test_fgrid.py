@@ -1,0 +1,115 @@
+"""The regular Gaussian grid F<N> as a second grid family for the operators
+(no GPU): the oracle's F-grid mesh and dual pinned by the same invariants
+and closed forms as O<N>, and the product's F-grid geometry and operator
+tables against the oracle.
+
+F<N>: 2N Gaussian latitudes with 4N points each, V = 8N^2; the zipper meets
+equal rows on every band (T = 2V - 8N triangles), pole edges j <-> j + 2N
+on the first and last row (E = 3V - 4N).  Its cells are symmetric about
+their node, so the gradient converges at second order on the whole sphere
+except the polar rows."""
+import numpy as np
+import pytest
+
+from test_host_geometry import _apply, _relmax
+
+R = 6371220.0
+
+
+@pytest.fixture(scope="module")
+def fmesh():
+    from oracle.oracle import Mesh
+    cache = {}
+
+    def get(N):
+        if N not in cache:
+            cache[N] = Mesh(N, R, regular=True)
+        return cache[N]
+    return get
+
+
+@pytest.mark.parametrize("N", [1, 2, 8, 24])
+def test_counts_volume_and_closure(fmesh, N):
+    m = fmesh(N)
+    V = 8 * N * N
+    assert (m.nnodes, m.ntri, m.nedges) == (V, 2 * V - 8 * N, 3 * V - 4 * N)
+    d = m.dual()
+    assert abs(np.sum(np.sort(d["V"])) / (4 * np.pi * R * R) - 1) <= 1e-12
+    res, ab = m.closure()
+    assert np.max(np.abs(res).sum(1) / ab) <= 1e-15
+    g = m.grid()
+    assert np.all(g["pl"] == 4 * N)
+
+
+def _l2(V, e, mask):
+    return np.sqrt(np.sum(V[mask] * e[mask] ** 2) / np.sum(V[mask]))
+
+
+def test_gradient_converges_at_second_order(fmesh):
+    errs = []
+    for N in (8, 16, 32):
+        m = fmesh(N)
+        g, V = m.grid(), m.dual()["V"]
+        lam, phi = g["lon"], g["lat_node"]
+        gx, gy = m.gradient(np.cos(phi) * np.cos(lam))
+        e = np.hypot(gx[:, 0] + np.sin(lam) / R, gy[:, 0] + np.sin(phi) * np.cos(lam) / R) * R
+        polar = np.zeros(m.nnodes, bool)
+        polar[:4 * N] = polar[-4 * N:] = True
+        errs.append(_l2(V, e, ~polar))
+    s = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(s) >= 1.85, (errs, s)  # measured 1.89, 1.91
+
+
+def test_divergence_conservation_and_solid_body(fmesh):
+    m = fmesh(16)
+    rng = np.random.default_rng(2)
+    u, v = rng.standard_normal((2, m.nnodes, 2))
+    V = m.dual()["V"]
+    d = m.divergence(u, v)
+    for k in range(2):
+        t = V * d[:, k]
+        assert abs(np.sum(t)) <= 1e-12 * np.sum(np.abs(t))
+    g = m.grid()
+    dz = m.divergence(np.cos(g["lat_node"])[:, None], np.zeros((m.nnodes, 1)))
+    assert np.max(np.abs(dz)) * R <= 1e-12  # zonal flow: exact
+
+
+def test_gradient_of_constant_is_zero(fmesh):
+    m = fmesh(8)
+    gx, gy = m.gradient(np.full((m.nnodes, 2), 4.5))
+    assert np.all(gx == 0) and np.all(gy == 0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 8, 24])
+def test_product_geometry_bitwise_equal_to_oracle(product, fmesh, N):
+    atlas = product[0]
+    f = atlas.build_fvm(N, regular=True)
+    om = fmesh(N)
+    g, og = f.grid.arrays(), om.grid()
+    assert np.array_equal(g["pl"], og["pl"]) and np.array_equal(g["lat"], og["lat"])
+    assert np.array_equal(g["lon"], og["lon"]) and np.array_equal(g["lat_node"], og["lat_node"])
+    m, omm = f.mesh.arrays(), om.mesh()
+    for k in ("e2n", "is_pole", "n2e_ptr", "n2e", "n2e_sign", "tri"):
+        assert np.array_equal(m[k], omm[k]), k
+    d, od = f.arrays(), om.dual()
+    for k in ("S", "V", "coslat", "pole_nphi"):
+        assert np.array_equal(d[k], od[k]), k
+
+
+def test_product_tables_reproduce_the_oracle(product, fmesh):
+    atlas = product[0]
+    f = atlas.build_fvm(8, regular=True)
+    om = fmesh(8)
+    rng = np.random.default_rng(8)
+    x, y = rng.standard_normal((2, f.nnodes, 3))
+    gx, gy = _apply(f.stencil_table("gradient"), [x])
+    ox, oy = om.gradient(x)
+    assert _relmax(gx, ox) <= 1e-13 and _relmax(gy, oy) <= 1e-13
+    (d,) = _apply(f.stencil_table("divergence"), [x, y])
+    assert _relmax(d, om.divergence(x, y)) <= 1e-13
+    (lap,) = _apply(f.stencil_table("laplacian"), [x])
+    assert _relmax(lap, om.laplacian(x)) <= 1e-12
+    (z,) = _apply(f.stencil_table("curl"), [x, y])
+    assert _relmax(z, om.curl(x, y)) <= 1e-13
+    (ga,) = _apply(f.stencil_table("gradient_adjoint"), [x, y])
+    assert _relmax(ga, om.gradient_adjoint(x, y)) <= 1e-13

@@ -26,9 +26,10 @@ def test_regular_gaussian_grid(atlas):
         assert np.max(np.abs(a["lon"] - 2 * np.pi * j / (4 * N))) <= 1e-15
 
 
-def test_meshes_are_octahedral_only(atlas, product):
-    with pytest.raises(product[1].AtlasError):
-        atlas.Mesh(atlas.Grid(8, regular=True))
+def test_f_grid_meshes(atlas):
+    """F<N> grids are meshed like O<N> (counts: T = 2V - 8N, E = 3V - 4N)."""
+    m = atlas.Mesh(atlas.Grid(8, regular=True))
+    assert (m.ntri, m.nedges) == (2 * 512 - 64, 3 * 512 - 32)
 
 
 @pytest.mark.parametrize("N,M", [(16, 8), (32, 8), (64, 16), (48, 24)])
