@@ -161,7 +161,9 @@ int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const doub
 /* Build and upload the tables of the operators in op_mask (bits 1<<op)    */
 /* for the dtypes in dtype_mask (bits 1<<dtype).  Synchronous.             */
 int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
-/* Launch shape of the node-stencil kernels for one operator: levels per   */
+/* Launch shape of the node-stencil kernels for one operator and storage  */
+/* dtype (atlas_dtype, or -1 for all three; each starts from a measured    */
+/* default): levels per                                                    */
 /* thread (vec: 1, 2, 4 or 8; 0 = default for the dtype), CSR entries per */
 /* load batch (batch: 3 or 6), threads per block (64..512, multiple of    */
 /* 32), blocks per SM (1..32) and tile_passes (1..4096): each block walks */
@@ -170,7 +172,7 @@ int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 /* fields and to the F32 Laplacian; the other F32 and F64 kernels always  */
 /* run a grid-stride loop.  Any zero field keeps the current value;       */
 /* results are bitwise identical for every shape.                          */
-int atlas_fvm_set_launch(atlas_fvm_t f, int op, int vec, int batch, int threads, int blocks_per_sm,
+int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, int threads, int blocks_per_sm,
                          int tile_passes);
 /* Inspection: copy out the FP64 host table of one operator's node stencil */
 /*   out_c(i) = sum_{q in [ptr[i], ptr[i+1])} sum_m W_cm(q) (x_m(nbr[q]) - x_m(i))  */

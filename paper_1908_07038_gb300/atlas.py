@@ -171,8 +171,10 @@ class Fvm:
                                      w.ctypes.data, b.ctypes.data)
         return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
 
-    def set_launch(self, op, vec=0, batch=0, threads=0, blocks_per_sm=0, tile_passes=0):
-        capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(vec), int(batch), int(threads),
+    def set_launch(self, op, vec=0, batch=0, threads=0, blocks_per_sm=0, tile_passes=0, dtype=-1):
+        """Launch shape of one operator for one storage dtype (ATLAS_F32 /
+        ATLAS_F64 / ATLAS_BF16) or, with dtype=-1, for all of them."""
+        capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
                                   int(blocks_per_sm), int(tile_passes))
 
     # ---------------------------------------------------------- operators

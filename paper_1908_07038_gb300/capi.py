@@ -61,7 +61,7 @@ _SIGS = {
     "atlas_fvm_build_dual": (I32, [P, ctypes.c_double, PP], True),
     "atlas_fvm_info": (I32, [P, PP, PP, PP, PP], True),
     "atlas_fvm_prepare": (I32, [P, ctypes.c_uint, ctypes.c_uint], True),
-    "atlas_fvm_set_launch": (I32, [P, I32, I32, I32, I32, I32, I32], True),
+    "atlas_fvm_set_launch": (I32, [P, I32, I32, I32, I32, I32, I32, I32], True),
     "atlas_fvm_stencil_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                                       P, P, P, P], True),
     "atlas_fvm_destroy": (None, [P], False),

@@ -114,6 +114,27 @@ struct LaunchCfg {
   int blocks_per_sm = 0;  // 0 = occupancy limit
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
 };
+
+// Launch shape an fvm starts with, per operator and storage dtype: the
+// autotuner's choice on O1280 x 137 on a GB300 (the tuner re-measures it on
+// the caller's fields).  Two-ring Laplacian: 2 blocks of 512 threads per SM
+// keep fewer neighbourhoods in L1; one-ring FP32: 256 threads, 3 entries per
+// batch; bfloat16: tiles of 64 passes for the Laplacian.
+LaunchCfg default_launch(int op, int dt) {
+  LaunchCfg c;
+  c.batch = 3;
+  c.threads = 256;
+  if (dt == ATLAS_F32) {
+    if (op == atlasgb::OP_LAP) { c.batch = 6; c.threads = 512; }
+    if (op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) c.threads = 128;
+  } else if (dt == ATLAS_BF16) {
+    c.threads = 128;
+    if (op == atlasgb::OP_LAP) c.tile_passes = 64;
+  } else {  // F64: bound by the FP64 pipe
+    c.threads = 128;
+  }
+  return c;
+}
 }  // namespace
 
 struct atlas_fvm_s {
@@ -124,7 +145,7 @@ struct atlas_fvm_s {
   std::mutex mu;
   OpTables st[atlasgb::OP_COUNT][3];  // [op][storage dtype: F32, F64, BF16]
   EdgeTables eg[2][2];                // [gradient, divergence][precision]
-  LaunchCfg cfg[atlasgb::OP_COUNT];
+  LaunchCfg cfg[atlasgb::OP_COUNT][3];  // [op][storage dtype], defaults from default_launch
   int users = 0;
 };
 
@@ -406,7 +427,7 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
                                              static_cast<uintptr_t>(first * ld * es))
              : nullptr;
   };
-  const LaunchCfg& c = f->cfg[op];
+  const LaunchCfg& c = f->cfg[op][dtype];
   atlasgb::StencilLaunch l;
   l.in0 = shift(in0, in_first);
   l.in1 = nin == 2 ? shift(in1, in_first) : nullptr;
@@ -491,7 +512,7 @@ int run_edges_op(atlas_fvm_s* f, int which, const void* in0, const void* in1, vo
   }
   const atlasgb::DevEdges& E = f->eg[which][prec].dev;
   const void* ptrs[5] = {in0, in1, out0, out1, ws};
-  const int vec = pick_vec(dtype, ld, ptrs, 5, f->cfg[which].vec);
+  const int vec = pick_vec(dtype, ld, ptrs, 5, f->cfg[which][dtype].vec);
   const int64_t nvec = (nlev + vec - 1) / vec;
   if (E.nedges * nvec >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nedges * level-vectors must stay below 2^31");
   const int threads = 256;
@@ -668,6 +689,8 @@ int atlas_fvm_build_dual(atlas_mesh_t mh, double radius, atlas_fvm_t* out) {
   atlas_mesh_s* m = reinterpret_cast<atlas_mesh_s*>(mh);
   atlas_fvm_s* f = new (std::nothrow) atlas_fvm_s();
   if (!f) return fail(ATLAS_ENOMEM, "out of host memory");
+  for (int op = 0; op < atlasgb::OP_COUNT; ++op)
+    for (int dt = 0; dt < 3; ++dt) f->cfg[op][dt] = default_launch(op, dt);
   try {
     if (!atlasgb::build_dual(m->m, radius, f->d)) {
       delete f;
@@ -725,10 +748,12 @@ int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
   return ok();
 }
 
-int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int batch, int threads, int blocks_per_sm, int tile_passes) {
+int atlas_fvm_set_launch(atlas_fvm_t h, int op, int dtype, int vec, int batch, int threads, int blocks_per_sm,
+                         int tile_passes) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (dtype != -1 && !valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "dtype must be -1 (all) or an atlas_dtype");
   if (vec != 0 && vec != 1 && vec != 2 && vec != 4 && vec != 8) return fail(ATLAS_EINVAL, "vec must be 1, 2, 4 or 8");
   if (batch != 0 && batch != 3 && batch != 6) return fail(ATLAS_EINVAL, "batch must be 3 or 6");
   if (threads != 0 && (threads < 64 || threads > 512 || threads % 32 != 0))
@@ -736,11 +761,15 @@ int atlas_fvm_set_launch(atlas_fvm_t h, int op, int vec, int batch, int threads,
   if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(ATLAS_EINVAL, "blocks_per_sm must be in [0, 32]");
   if (tile_passes < 0 || tile_passes > 4096) return fail(ATLAS_EINVAL, "tile_passes must be in [0, 4096]");
   std::lock_guard<std::mutex> lk(f->mu);
-  if (vec) f->cfg[op].vec = vec;
-  if (batch) f->cfg[op].batch = batch;
-  if (threads) f->cfg[op].threads = threads;
-  if (blocks_per_sm) f->cfg[op].blocks_per_sm = blocks_per_sm;
-  if (tile_passes) f->cfg[op].tile_passes = tile_passes;
+  for (int d = 0; d < 3; ++d) {
+    if (dtype != -1 && d != dtype) continue;
+    LaunchCfg& c = f->cfg[op][d];
+    if (vec) c.vec = vec;
+    if (batch) c.batch = batch;
+    if (threads) c.threads = threads;
+    if (blocks_per_sm) c.blocks_per_sm = blocks_per_sm;
+    if (tile_passes) c.tile_passes = tile_passes;
+  }
   return ok();
 }
 

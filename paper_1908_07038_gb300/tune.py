@@ -111,7 +111,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         key = key_base + "|" + op
         if key in cache:
             c = cache[key]
-            fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1))
+            fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1), dtype=dtype)
             best[op] = c
             continue
         ins = (fields[1], fields[2]) if op in ("divergence", "gradient_adjoint", "curl", "vector_gradient") \
@@ -120,14 +120,14 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         results = []
         for vec, batch, threads, bps, tile in itertools.product(cand["vec"], cand["batch"], cand["threads"],
                                                                 cand["bps"], cand["tile"]):
-            fvm.set_launch(op, vec, batch, threads, bps, tile)
+            fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
             ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
             results.append((ms, vec, batch, threads, bps, tile))
             if verbose:
                 print("tune %-18s vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
                       (op, vec, batch, threads, bps, tile, ms))
         ms, vec, batch, threads, bps, tile = min(results)
-        fvm.set_launch(op, vec, batch, threads, bps, tile)
+        fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
         best[op] = dict(vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, ms=ms,
                         sweep=[dict(ms=r[0], vec=r[1], batch=r[2], threads=r[3], bps=r[4], tile=r[5])
                                for r in results])

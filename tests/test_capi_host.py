@@ -58,12 +58,16 @@ def test_error_codes_on_bad_arguments(product):
         capi.atlas_nabla_gradient_edges(h, fake, fake + 4096, fake + 8192, fake + 1 << 24, 16, 3, 4, 0, None)
     assert ei.value.code in (-1, -4)
     with pytest.raises(E) as ei:
-        capi.atlas_fvm_set_launch(h, 0, 3, 0, 0, 0, 0)
+        capi.atlas_fvm_set_launch(h, 0, -1, 3, 0, 0, 0, 0)
     assert ei.value.code == -1
     with pytest.raises(E) as ei:
-        capi.atlas_fvm_set_launch(h, 0, 0, 0, 0, 0, -1)
+        capi.atlas_fvm_set_launch(h, 0, -1, 0, 0, 0, 0, -1)
     assert ei.value.code == -1
-    capi.atlas_fvm_set_launch(h, 0, 0, 0, 0, 0, 16)
+    with pytest.raises(E) as ei:
+        capi.atlas_fvm_set_launch(h, 0, 7, 0, 0, 0, 0, 1)
+    assert ei.value.code == -5
+    capi.atlas_fvm_set_launch(h, 0, -1, 0, 0, 0, 0, 16)
+    capi.atlas_fvm_set_launch(h, 4, 1, 0, 3, 128, 0, 1)
     # a destroyed handle is rejected, not dereferenced
     fvm.close()
     with pytest.raises(E) as ei:
