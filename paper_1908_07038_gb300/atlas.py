@@ -5,7 +5,10 @@ FunctionSpace workflow (Sec. 2.3, Fig. 2).  The operator methods of ``Fvm``
 take torch CUDA tensors shaped [nnodes, ld] (field[node][level], levels
 innermost) and call the C ABI on torch's current stream; torch only provides
 the device memory and the stream.  ``GradientFn`` / ``DivergenceFn`` wrap the
-forward kernels and their hand-written adjoint kernels as autograd functions.
+forward kernels and their hand-written adjoint kernels as autograd functions;
+``CurlFn`` and ``LaplacianFn`` take their backward passes from the same
+adjoint kernels (curl(u, v) = D(v, -u), L = D G).  ``Remap`` interpolates
+between grids.
 """
 from __future__ import annotations
 
@@ -381,7 +384,39 @@ def _make_autograd():
             u_bar, v_bar = ctx.fvm.divergence_adjoint(d_bar, out=out)
             return u_bar, v_bar, None
 
-    return GradientFn, DivergenceFn
+    class CurlFn(torch.autograd.Function):
+        """z = curl (u, v) = D (v, -u); backward (u_bar, v_bar) = (-b, a) with
+        (a, b) = D^T z_bar, by the divergence adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, u, v, fvm):
+            ctx.fvm = fvm
+            u = u.contiguous()
+            return fvm.curl(u, v.contiguous(), out=torch.zeros_like(u))
+
+        @staticmethod
+        def backward(ctx, z_bar):
+            z_bar = z_bar.contiguous()
+            a, b = ctx.fvm.divergence_adjoint(z_bar, out=(torch.zeros_like(z_bar), torch.zeros_like(z_bar)))
+            return -b, a, None
+
+    class LaplacianFn(torch.autograd.Function):
+        """l = L f with the fused two-ring table L = D G; backward
+        f_bar = G^T (D^T l_bar) by the two adjoint kernels."""
+
+        @staticmethod
+        def forward(ctx, f, fvm):
+            ctx.fvm = fvm
+            f = f.contiguous()
+            return fvm.laplacian(f, out=torch.zeros_like(f))
+
+        @staticmethod
+        def backward(ctx, l_bar):
+            l_bar = l_bar.contiguous()
+            u, v = ctx.fvm.divergence_adjoint(l_bar, out=(torch.zeros_like(l_bar), torch.zeros_like(l_bar)))
+            return ctx.fvm.gradient_adjoint(u, v, out=torch.zeros_like(l_bar)), None
+
+    return GradientFn, DivergenceFn, CurlFn, LaplacianFn
 
 
 _AUTOGRAD = None
@@ -399,3 +434,17 @@ def divergence_fn(u, v, fvm: Fvm):
     if _AUTOGRAD is None:
         _AUTOGRAD = _make_autograd()
     return _AUTOGRAD[1].apply(u, v, fvm)
+
+
+def curl_fn(u, v, fvm: Fvm):
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD[2].apply(u, v, fvm)
+
+
+def laplacian_fn(f, fvm: Fvm):
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD[3].apply(f, fvm)
