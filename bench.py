@@ -119,7 +119,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -532,7 +532,7 @@ def run_native(args):
         "roofline": roofline, "per_op": {k: {"ms": v_["ms"], "node_levels_per_s": v_["node_levels_per_s"],
                                              "frac_hbm": round(v_["frac"], 4)} for k, v_ in per.items()},
         "more_ops": more,
-        "side_by_side": side, "batched": batched, "tuned": {k: {kk: t[kk] for kk in ("vec", "batch", "threads")}
+        "side_by_side": side, "batched": batched, "tuned": {k: {kk: t.get(kk, 1) for kk in ("vec", "batch", "threads", "tile")}
                                                             for k, t in tuned.items()},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": 5 * args.steps,
