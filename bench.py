@@ -398,6 +398,29 @@ def run_native(args):
             more["%s_F%d" % (op, M)] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(Vf * nlev, ws, ms),
                                         "nodes": Vf, "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4)}
         del xf, of, ff
+        # a limited-area configuration: 1536 x 1440 points at 2.5 km on a
+        # Lambert conformal cone, 90 levels, same kernels with the regional tables
+        from synthetic.regional import LAM, LAM_NLEV, LAM_NX, LAM_NY
+        rf = atlas.build_fvm_regional(LAM[0], LAM_NX, LAM_NY, **LAM[1])
+        rops = ("gradient", "divergence", "laplacian", "curl")
+        rf.prepare(rops, dtypes=(atlas.ATLAS_F32,))
+        Vr, lr, ldr = rf.nnodes, LAM_NLEV, 92
+        xr, yr = (torch.randn((Vr, ldr), device="cuda") for _ in range(2))
+        orr = [torch.empty_like(xr) for _ in range(2)]
+        if not args.no_tune:
+            tune.tune_fvm(rf, atlas.ATLAS_F32, lr, ldr, rops, fields=(xr, xr, yr), reps=3)
+        rcalls = {"gradient": lambda: rf.gradient(xr, lr, out=(orr[0], orr[1])),
+                  "divergence": lambda: rf.divergence(xr, yr, lr, out=orr[0]),
+                  "laplacian": lambda: rf.laplacian(xr, lr, out=orr[0]),
+                  "curl": lambda: rf.curl(xr, yr, lr, out=orr[0])}
+        reg = {"grid": "Lambert conformal %dx%d, %d levels" % (LAM_NX, LAM_NY, lr), "nodes": Vr}
+        for op in rops:
+            ms = _max_over_ranks(tune.time_call(rcalls[op], reps=max(5, args.steps), warmup=args.warmup), ws, "cuda")
+            b = _alg_bytes(op, Vr, lr, 4, _table_bytes_of(rf, op, 4))
+            reg[op] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(Vr * lr, ws, ms), "alg_bytes": b,
+                       "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4)}
+        more["regional_lambert"] = reg
+        del xr, yr, orr, rf
 
     # ---------------------------------------------------------------- e2e
     # Host-resident fields through the public API: every step copies f, u, v

@@ -88,6 +88,13 @@ enum {
   ATLAS_OP_VECTOR_GRADIENT = 6
 };
 
+/* Map projections of regional grids (atlas_grid_regional). */
+enum {
+  ATLAS_PROJ_ROTATED_LONLAT = 0,
+  ATLAS_PROJ_MERCATOR = 1,
+  ATLAS_PROJ_LAMBERT_CONFORMAL = 2
+};
+
 /* ---------------------------------------------------------------------- */
 /* Library lifecycle (paper Sec. 3.5, Listings 1-2: initialise/finalise). */
 /* Both are idempotent and optional; finalize releases nothing the caller  */
@@ -122,11 +129,47 @@ int atlas_grid_info(atlas_grid_t g, int64_t* nnodes, int* nlat, const int32_t** 
 /* O<N> (the zipper then meets equal rows on every band; pole edges join  */
 /* node j to j + 2N on the first and last row).                            */
 int atlas_grid_regular_gaussian(int N, atlas_grid_t* out);
+
+/* Regional (limited-area) grids (paper Sec. 2.2.3 and Sec. 5: Atlas meshes */
+/* the regional grids of limited-area models; operators that account for   */
+/* the projection are the follow-up work named there).  A rectangle of a   */
+/* map projection's plane with nx >= 2 points per row and ny >= 2 rows,    */
+/* nx * ny <= 2^28:                                                        */
+/*   x_j = xmin + j (xmax - xmin)/(nx - 1),  y_r = ymax - r (ymax - ymin)/(ny - 1), */
+/* node id r nx + j (the first row has the largest y).  params[8] =        */
+/* {xmin, xmax, ymin, ymax, p4, p5, p6, p7}:                               */
+/*   ATLAS_PROJ_ROTATED_LONLAT: x, y are rotated longitude and latitude in */
+/*     degrees, |y| < 90, xmax - xmin < 360; (p4, p5) = longitude and      */
+/*     latitude of the rotated south pole in degrees (GRIB convention; (0, */
+/*     -90) is the plain lon-lat grid); p6, p7 unused.                     */
+/*   ATLAS_PROJ_MERCATOR: x, y in metres; p4 = radius of the projection    */
+/*     sphere (metres), p5 = central longitude (degrees); |y|/p4 <= 7.     */
+/*   ATLAS_PROJ_LAMBERT_CONFORMAL: tangent cone; x, y in metres; p4 =      */
+/*     radius, p5 = central longitude, p6 = tangent latitude (degrees,     */
+/*     0 < |p6| < 90); the domain must not hold the pole or cross the cut  */
+/*     opposite the central longitude.                                     */
+/* Every point must stay more than about 0.06 degrees from a pole of the  */
+/* projection.  EINVAL (with the reason in atlas_last_error) otherwise.    */
+/* atlas_grid_info then reports nlat = ny rows of nx points and lat[r] =   */
+/* the latitude of row r's first point.                                   */
+int atlas_grid_regional(int projection, int nx, int ny, const double* params, atlas_grid_t* out);
+/* Regional grids only (EINVAL otherwise): projection, nx, ny, the plane   */
+/* coordinates xy[nnodes][2] on the unit sphere (radians, or metres over   */
+/* the projection radius) and the scale factors scale[nnodes][2] = (h_x,   */
+/* h_y): a plane step dx is a true distance R h_x dx on a sphere of radius */
+/* R (rotated lon-lat: (cos y, 1); Mercator, Lambert: 1/m, the inverse map */
+/* factor, in both directions).                                            */
+int atlas_grid_regional_info(atlas_grid_t g, int* projection, int* nx, int* ny, const double** xy,
+                             const double** scale);
 void atlas_grid_destroy(atlas_grid_t g);
 
 /* ---------------------------------------------------------------------- */
 /* Mesh (paper Sec. 2.3: connectivity of elements, edges and nodes).       */
 /* ---------------------------------------------------------------------- */
+/* A regional grid is meshed two triangles per quad: quad (r, j) with a =  */
+/* r nx + j is split along (a, a+nx+1) into {a, a+nx+1, a+1} and {a, a+nx, */
+/* a+nx+1} (counter-clockwise in the plane); 2 (nx-1)(ny-1) triangles,     */
+/* 3 nx ny - 2 nx - 2 ny + 1 edges, none of them pole edges.               */
 /* Zipper triangulation of every pair of adjacent rows (advance on the row */
 /* whose next longitude is smaller; on a tie the row with fewer points,    */
 /* between equal rows the northern one), plus pole edges joining node j to */
@@ -158,6 +201,23 @@ int atlas_fvm_build_dual(atlas_mesh_t m, double radius, atlas_fvm_t* out);
 /* coslat[nnodes], pole_nphi[nnodes] (phi-normal of the pole segment).     */
 int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const double** coslat,
                    const double** pole_nphi);
+/* The dual of a regional grid lies in the projection plane: S_e = R times */
+/* the integrated plane normal of the face of edge e (a to b), area[i] =   */
+/* R^2 times the plane area of cell i (a third of each adjacent triangle), */
+/* Sb[E][2] = R times the outward plane normal of a boundary edge (0 for  */
+/* interior edges), V_i = h_x,i h_y,i area_i, pole_nphi = 0 and coslat the */
+/* cosine of the node latitude.  Operators on it use face values          */
+/* (f_i + f_j)/2 on interior faces and (5 f_i + f_j)/6 on boundary half    */
+/* edges (exact for fields linear in the plane), the scale factors at the */
+/* nodes, and give vector components along the grid's x and y directions: */
+/*   gradient  (h_x^-1 d/dx, h_y^-1 d/dy) f                               */
+/*   divergence (h_x h_y)^-1 [d(h_y u)/dx + d(h_x v)/dy]                  */
+/*   curl       (h_x h_y)^-1 [d(h_y v)/dx - d(h_x u)/dy]                  */
+/* with the Laplacian = divergence(gradient), the adjoints the transposes */
+/* and the vector gradient the gradient of each component.  The           */
+/* edge-based two-pass calls refuse a regional fvm (EINVAL).               */
+/* Regional fvm only (EINVAL otherwise): area[nnodes] and Sb[E][2].         */
+int atlas_fvm_regional_info(atlas_fvm_t f, const double** area, const double** Sb);
 /* Build and upload the tables of the operators in op_mask (bits 1<<op)    */
 /* for the dtypes in dtype_mask (bits 1<<dtype).  Synchronous.             */
 int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
@@ -326,7 +386,9 @@ void atlas_batch_destroy(atlas_batch_t b);
 /* whose smallest weight is largest, then the lowest triangle id).  Built  */
 /* on the host; fails with ATLAS_EINVAL if a target lies in a polar cap    */
 /* (north of the source's first row or south of its last), which no        */
-/* triangle covers.  The remap keeps its mesh and grid alive.              */
+/* triangle covers.  The source must be a global mesh (O<N> or F<N>); any */
+/* grid, a regional one included, can be the target.  The remap keeps its */
+/* mesh and grid alive.                                                    */
 /* ---------------------------------------------------------------------- */
 int atlas_remap_create(atlas_mesh_t src, atlas_grid_t dst, atlas_remap_t* out);
 /* Views valid until atlas_remap_destroy: ntgt (the target grid's points), */

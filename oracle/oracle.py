@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "atlas_oracle.c")
+_SRC_REGIONAL = os.path.join(_HERE, "regional_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -36,9 +37,10 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, no GPU)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC_REGIONAL]
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(x) for x in srcs):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *srcs, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -76,6 +78,21 @@ def _load():
         lib.orc_divergence_triplets.argtypes = [P, P, P, P]
         lib.orc_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
         lib.orc_closure.argtypes = [P, P, P]
+        lib.orc_reg_build.restype = P
+        lib.orc_reg_build.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_double]
+        lib.orc_reg_free.argtypes = [P]
+        lib.orc_reg_counts.argtypes = [P, P]
+        lib.orc_reg_get.argtypes = [P] * 6
+        lib.orc_reg_closure.argtypes = [P, P, P]
+        lib.orc_reg_gradient.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+        lib.orc_reg_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_reg_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_reg_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_reg_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+        lib.orc_reg_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+        for name in ("orc_reg_gradient", "orc_reg_divergence", "orc_reg_curl", "orc_reg_laplacian",
+                     "orc_reg_gradient_adjoint", "orc_reg_divergence_adjoint"):
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
                      "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
                      "orc_vector_gradient", "orc_remap", "orc_remap_apply"):
@@ -293,3 +310,125 @@ class Mesh:
         rows = np.empty(n, np.int64); cols = np.empty(n, np.int64); vals = np.empty(n)
         fn(self._h, _ptr(rows), _ptr(cols), _ptr(vals))
         return rows, cols, vals
+
+
+PROJECTIONS = {"rotated_lonlat": 0, "mercator": 1, "lambert_conformal": 2}
+
+
+class RegionalMesh:
+    """Oracle regional grid (a rectangle of a projection's plane, two
+    triangles per quad), its plane median dual and the operators with the
+    projection's scale factors (``regional_oracle.c``)."""
+
+    def __init__(self, projection: str, nx: int, ny: int, xmin: float, xmax: float, ymin: float, ymax: float, *,
+                 radius: float = R_EARTH, lon0: float = 0.0, lat0: float = 45.0, south_pole=(0.0, -90.0)):
+        lib = _load()
+        code = PROJECTIONS[projection]
+        if code == 0:
+            tail = [float(south_pole[0]), float(south_pole[1]), 0.0, 0.0]
+        else:
+            tail = [float(radius), float(lon0), float(lat0), 0.0]
+        prm = np.array([xmin, xmax, ymin, ymax, *tail], dtype=np.float64)
+        h = lib.orc_reg_build(code, int(nx), int(ny), _ptr(prm), float(radius))
+        if not h:
+            raise ValueError("oracle regional grid build failed")
+        self._h = ctypes.c_void_p(h)
+        self._lib = lib
+        self.R = float(radius)
+        self.nx, self.ny = int(nx), int(ny)
+        c = np.zeros(2, dtype=np.int64)
+        lib.orc_reg_counts(self._h, _ptr(c))
+        self.nnodes, self.ntri = int(c[0]), int(c[1])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.orc_reg_free(h)
+            self._h = None
+
+    def geometry(self):
+        """lon, lat (radians), x, y (unit-sphere plane), hx, hy, area (R^2 x plane), tri [T][3]."""
+        V, T = self.nnodes, self.ntri
+        ll = np.empty((V, 2)); xy = np.empty((V, 2)); h = np.empty((V, 2)); A = np.empty(V)
+        tri = np.empty((T, 3), np.int32)
+        self._lib.orc_reg_get(self._h, _ptr(ll), _ptr(xy), _ptr(h), _ptr(A), _ptr(tri))
+        return dict(lon=ll[:, 0].copy(), lat=ll[:, 1].copy(), x=xy[:, 0].copy(), y=xy[:, 1].copy(),
+                    hx=h[:, 0].copy(), hy=h[:, 1].copy(), area=A, tri=tri)
+
+    def closure(self):
+        res = np.empty((self.nnodes, 2))
+        ab = np.empty(self.nnodes)
+        self._lib.orc_reg_closure(self._h, _ptr(res), _ptr(ab))
+        return res, ab
+
+    def _nodes(self, nodes):
+        if nodes is None:
+            return None, self.nnodes
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        return nodes, int(nodes.shape[0])
+
+    def _pair(self, a, b):
+        a, f32, ld = _field(a)
+        b, f32b, ldb = _field(b)
+        if (f32, ld) != (f32b, ldb):
+            raise ValueError("both inputs need the same dtype and leading dimension")
+        return a, b, f32, ld
+
+    def gradient(self, f, nlev=None, nodes=None):
+        f, f32, ld = _field(f)
+        nlev = f.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        gx = np.empty((n, nlev)); gy = np.empty((n, nlev))
+        if self._lib.orc_reg_gradient(self._h, _ptr(f), f32, ld, nlev, _ptr(nodes), n, _ptr(gx), _ptr(gy)):
+            raise ValueError("orc_reg_gradient failed")
+        return gx, gy
+
+    def vector_gradient(self, u, v, nlev=None, nodes=None):
+        ux, uy = self.gradient(u, nlev, nodes)
+        vx, vy = self.gradient(v, nlev, nodes)
+        return ux, uy, vx, vy
+
+    def divergence(self, u, v, nlev=None, nodes=None):
+        u, v, f32, ld = self._pair(u, v)
+        nlev = u.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        if self._lib.orc_reg_divergence(self._h, _ptr(u), _ptr(v), f32, ld, nlev, _ptr(nodes), n, _ptr(out)):
+            raise ValueError("orc_reg_divergence failed")
+        return out
+
+    def curl(self, u, v, nlev=None, nodes=None):
+        u, v, f32, ld = self._pair(u, v)
+        nlev = u.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        if self._lib.orc_reg_curl(self._h, _ptr(u), _ptr(v), f32, ld, nlev, _ptr(nodes), n, _ptr(out)):
+            raise ValueError("orc_reg_curl failed")
+        return out
+
+    def laplacian(self, f, nlev=None, nodes=None):
+        f, f32, ld = _field(f)
+        nlev = f.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        if self._lib.orc_reg_laplacian(self._h, _ptr(f), f32, ld, nlev, _ptr(nodes), n, _ptr(out)):
+            raise ValueError("orc_reg_laplacian failed")
+        return out
+
+    def gradient_adjoint(self, y0, y1, nlev=None, nodes=None):
+        y0, y1, f32, ld = self._pair(y0, y1)
+        nlev = y0.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        out = np.empty((n, nlev))
+        if self._lib.orc_reg_gradient_adjoint(self._h, _ptr(y0), _ptr(y1), f32, ld, nlev, _ptr(nodes), n, _ptr(out)):
+            raise ValueError("orc_reg_gradient_adjoint failed")
+        return out
+
+    def divergence_adjoint(self, d, nlev=None, nodes=None):
+        d, f32, ld = _field(d)
+        nlev = d.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        xu = np.empty((n, nlev)); xv = np.empty((n, nlev))
+        if self._lib.orc_reg_divergence_adjoint(self._h, _ptr(d), f32, ld, nlev, _ptr(nodes), n, _ptr(xu), _ptr(xv)):
+            raise ValueError("orc_reg_divergence_adjoint failed")
+        return xu, xv

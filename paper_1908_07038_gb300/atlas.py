@@ -21,6 +21,9 @@ from .capi import ATLAS_BF16, ATLAS_F32, ATLAS_F64
 
 R_EARTH = 6371220.0
 
+PROJECTIONS = {"rotated_lonlat": capi.ATLAS_PROJ_ROTATED_LONLAT, "mercator": capi.ATLAS_PROJ_MERCATOR,
+               "lambert_conformal": capi.ATLAS_PROJ_LAMBERT_CONFORMAL}
+
 OPS = {"gradient": capi.ATLAS_OP_GRADIENT, "divergence": capi.ATLAS_OP_DIVERGENCE,
        "gradient_adjoint": capi.ATLAS_OP_GRADIENT_ADJOINT,
        "divergence_adjoint": capi.ATLAS_OP_DIVERGENCE_ADJOINT, "laplacian": capi.ATLAS_OP_LAPLACIAN,
@@ -53,13 +56,50 @@ class Grid:
         nl = ctypes.c_int()
         capi.atlas_grid_info(h, ctypes.byref(nn), ctypes.byref(nl), None, None, None)
         self.nnodes, self.nlat = nn.value, nl.value
+        self.projection = None
+
+    @classmethod
+    def regional(cls, projection: str, nx: int, ny: int, xmin: float, xmax: float, ymin: float, ymax: float, *,
+                 radius: float = R_EARTH, lon0: float = 0.0, lat0: float = 45.0,
+                 south_pole=(0.0, -90.0)) -> "Grid":
+        """Regional (limited-area) grid: a rectangle of a projection's plane
+        with nx points per row and ny rows.  ``projection`` is
+        "rotated_lonlat" (x, y in rotated degrees; ``south_pole`` = the
+        rotated south pole's (lon, lat) in degrees), "mercator" (x, y in
+        metres on a sphere of ``radius``, central longitude ``lon0``) or
+        "lambert_conformal" (the same plus the tangent latitude ``lat0``)."""
+        code = PROJECTIONS[projection]
+        if code == capi.ATLAS_PROJ_ROTATED_LONLAT:
+            tail = (float(south_pole[0]), float(south_pole[1]), 0.0, 0.0)
+        else:
+            tail = (float(radius), float(lon0), float(lat0), 0.0)
+        prm = (ctypes.c_double * 8)(float(xmin), float(xmax), float(ymin), float(ymax), *tail)
+        h = ctypes.c_void_p()
+        capi.atlas_grid_regional(code, int(nx), int(ny), ctypes.cast(prm, ctypes.c_void_p), ctypes.byref(h))
+        self = cls.__new__(cls)
+        self.handle = h
+        self.N = 0
+        self.regular = False
+        self.projection = projection
+        self.nx, self.ny = int(nx), int(ny)
+        nn = ctypes.c_int64()
+        nl = ctypes.c_int()
+        capi.atlas_grid_info(h, ctypes.byref(nn), ctypes.byref(nl), None, None, None)
+        self.nnodes, self.nlat = nn.value, nl.value
+        return self
 
     def arrays(self):
         pl, ll, lat = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         capi.atlas_grid_info(self.handle, None, None, ctypes.byref(pl), ctypes.byref(ll), ctypes.byref(lat))
         lonlat = _view(ll, ctypes.c_double, 2 * self.nnodes, (self.nnodes, 2))
-        return dict(pl=_view(pl, ctypes.c_int32, self.nlat), lat=_view(lat, ctypes.c_double, self.nlat),
-                    lon=lonlat[:, 0].copy(), lat_node=lonlat[:, 1].copy())
+        out = dict(pl=_view(pl, ctypes.c_int32, self.nlat), lat=_view(lat, ctypes.c_double, self.nlat),
+                   lon=lonlat[:, 0].copy(), lat_node=lonlat[:, 1].copy())
+        if self.projection is not None:
+            xy, sc = ctypes.c_void_p(), ctypes.c_void_p()
+            capi.atlas_grid_regional_info(self.handle, None, None, None, ctypes.byref(xy), ctypes.byref(sc))
+            out["xy"] = _view(xy, ctypes.c_double, 2 * self.nnodes, (self.nnodes, 2))
+            out["scale"] = _view(sc, ctypes.c_double, 2 * self.nnodes, (self.nnodes, 2))
+        return out
 
     def close(self):
         if self.handle is not None and self.handle.value:
@@ -146,8 +186,14 @@ class Fvm:
         ptrs = [ctypes.c_void_p() for _ in range(4)]
         capi.atlas_fvm_info(self.handle, *(ctypes.byref(p) for p in ptrs))
         V, E = self.nnodes, self.mesh.nedges
-        return dict(V=_view(ptrs[0], ctypes.c_double, V), S=_view(ptrs[1], ctypes.c_double, 2 * E, (E, 2)),
-                    coslat=_view(ptrs[2], ctypes.c_double, V), pole_nphi=_view(ptrs[3], ctypes.c_double, V))
+        out = dict(V=_view(ptrs[0], ctypes.c_double, V), S=_view(ptrs[1], ctypes.c_double, 2 * E, (E, 2)),
+                   coslat=_view(ptrs[2], ctypes.c_double, V), pole_nphi=_view(ptrs[3], ctypes.c_double, V))
+        if self.grid.projection is not None:
+            a, sb = ctypes.c_void_p(), ctypes.c_void_p()
+            capi.atlas_fvm_regional_info(self.handle, ctypes.byref(a), ctypes.byref(sb))
+            out["area"] = _view(a, ctypes.c_double, V)
+            out["Sb"] = _view(sb, ctypes.c_double, 2 * E, (E, 2))
+        return out
 
     def prepare(self, ops=("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint"),
                 dtypes=(ATLAS_F32,)):
@@ -340,6 +386,14 @@ def build_fvm(N: int, radius: float = R_EARTH, regular: bool = False) -> Fvm:
     g = Grid(N, regular=regular)
     m = Mesh(g)
     return Fvm(m, radius)
+
+
+def build_fvm_regional(projection: str, nx: int, ny: int, xmin: float, xmax: float, ymin: float, ymax: float,
+                       radius: float = R_EARTH, **proj) -> Fvm:
+    """Regional Grid (see ``Grid.regional``) -> Mesh -> Fvm in one call; the
+    dual's radius is the projection's."""
+    g = Grid.regional(projection, nx, ny, xmin, xmax, ymin, ymax, radius=radius, **proj)
+    return Fvm(Mesh(g), radius)
 
 
 def field_sync(dst, src, nbytes, direction, stream=None):

@@ -19,6 +19,7 @@ ATLAS_F32, ATLAS_F64, ATLAS_BF16 = 0, 1, 2
 ATLAS_OP_GRADIENT, ATLAS_OP_DIVERGENCE, ATLAS_OP_GRADIENT_ADJOINT = 0, 1, 2
 ATLAS_OP_DIVERGENCE_ADJOINT, ATLAS_OP_LAPLACIAN = 3, 4
 ATLAS_OP_CURL, ATLAS_OP_VECTOR_GRADIENT = 5, 6
+ATLAS_PROJ_ROTATED_LONLAT, ATLAS_PROJ_MERCATOR, ATLAS_PROJ_LAMBERT_CONFORMAL = 0, 1, 2
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EALIGN", -5: "EDTYPE", -6: "ESTATE"}
 
 
@@ -72,6 +73,10 @@ _SIGS = {
     "atlas_nabla_divergence_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_curl": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_grid_regular_gaussian": (I32, [I32, P], True),
+    "atlas_grid_regional": (I32, [I32, I32, I32, P, PP], True),
+    "atlas_grid_regional_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32), PP, PP],
+                                 True),
+    "atlas_fvm_regional_info": (I32, [P, PP, PP], True),
     "atlas_remap_create": (I32, [P, P, P], True),
     "atlas_remap_info": (I32, [P, P, P, P], True),
     "atlas_remap_apply": (I32, [P, P, P, I32, I64, I64, I32, P], True),

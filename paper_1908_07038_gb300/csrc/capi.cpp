@@ -270,6 +270,8 @@ int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div*/, int prec) {
   EdgeTables& t = f->eg[which][prec];
   if (t.ready) return ATLAS_OK;
   const atlasgb::Mesh& m = f->mesh->m;
+  if (f->mesh->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
   atlasgb::EdgeGather g;
   try {
     if (!atlasgb::build_edge_gather(m, f->d, which == 0 ? atlasgb::OP_GRAD : atlasgb::OP_DIV, g))
@@ -608,6 +610,41 @@ int atlas_grid_regular_gaussian(int N, atlas_grid_t* out) {
   return ok();
 }
 
+int atlas_grid_regional(int projection, int nx, int ny, const double* params, atlas_grid_t* out) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (projection < ATLAS_PROJ_ROTATED_LONLAT || projection > ATLAS_PROJ_LAMBERT_CONFORMAL)
+    return fail(ATLAS_EINVAL, "unknown projection %d", projection);
+  atlas_grid_s* g = new (std::nothrow) atlas_grid_s();
+  if (!g) return fail(ATLAS_ENOMEM, "out of host memory");
+  const char* why = "invalid regional grid";
+  try {
+    if (!atlasgb::build_regional_grid(projection, nx, ny, params, g->g, &why)) {
+      delete g;
+      return fail(ATLAS_EINVAL, "%s", why);
+    }
+  } catch (const std::bad_alloc&) {
+    delete g;
+    return fail(ATLAS_ENOMEM, "out of host memory building a %d x %d regional grid", nx, ny);
+  }
+  reg(g);
+  *out = reinterpret_cast<atlas_grid_t>(g);
+  return ok();
+}
+
+int atlas_grid_regional_info(atlas_grid_t h, int* projection, int* nx, int* ny, const double** xy,
+                             const double** scale) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
+  const atlasgb::Grid& g = reinterpret_cast<atlas_grid_s*>(h)->g;
+  if (!g.regional()) return fail(ATLAS_EINVAL, "not a regional grid");
+  if (projection) *projection = g.projection;
+  if (nx) *nx = g.nx;
+  if (ny) *ny = g.nlat;
+  if (xy) *xy = g.xy.data();
+  if (scale) *scale = g.h.data();
+  return ok();
+}
+
 int atlas_grid_info(atlas_grid_t h, int64_t* nnodes, int* nlat, const int32_t** pl, const double** lonlat,
                     const double** lat) {
   if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
@@ -724,6 +761,15 @@ int atlas_fvm_info(atlas_fvm_t h, const double** V, const double** S, const doub
   if (S) *S = f->d.S.data();
   if (coslat) *coslat = f->d.coslat.data();
   if (pole_nphi) *pole_nphi = f->d.pole_nphi.data();
+  return ok();
+}
+
+int atlas_fvm_regional_info(atlas_fvm_t h, const double** area, const double** Sb) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (!f->mesh->grid->g.regional()) return fail(ATLAS_EINVAL, "not the dual of a regional grid");
+  if (area) *area = f->d.A.data();
+  if (Sb) *Sb = f->d.Sb.data();
   return ok();
 }
 
@@ -868,6 +914,8 @@ int atlas_nabla_gradient_edges(atlas_fvm_t h, const void* fin, void* gx, void* g
                                int64_t ld, atlas_dtype dtype, void* stream) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (f->mesh->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
   if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
   const void* used[3] = {fin, gx, gy};
   int rc = check_field_args(dtype, nlev, ld, used, 3);
@@ -891,6 +939,8 @@ int atlas_nabla_divergence_edges(atlas_fvm_t h, const void* u, const void* v, vo
                                  int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (f->mesh->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
   if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
   const void* used[3] = {u, v, div};
   int rc = check_field_args(dtype, nlev, ld, used, 3);
@@ -914,6 +964,8 @@ int atlas_nabla_laplacian_edges(atlas_fvm_t h, const void* fin, void* lap, void*
                                 int64_t ld, atlas_dtype dtype, void* stream) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (f->mesh->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
   if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
   const void* used[2] = {fin, lap};
   int rc = check_field_args(dtype, nlev, ld, used, 2);
@@ -944,6 +996,8 @@ int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t h, const void* fin, void* la
                                         atlas_dtype dtype, void* stream) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (f->mesh->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
   if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
   const void* used[2] = {fin, lap};
   int rc = check_field_args(dtype, nlev, ld, used, 2);
@@ -1137,6 +1191,8 @@ int atlas_remap_create(atlas_mesh_t sh, atlas_grid_t th, atlas_remap_t* out) {
   if (!live(th)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
   atlas_mesh_s* m = reinterpret_cast<atlas_mesh_s*>(sh);
   atlas_grid_s* g = reinterpret_cast<atlas_grid_s*>(th);
+  if (m->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the source of a remap must be a global mesh (a regional grid can be a target)");
   atlas_remap_s* r = new (std::nothrow) atlas_remap_s();
   if (!r) return fail(ATLAS_ENOMEM, "out of host memory");
   int64_t missed = 0;

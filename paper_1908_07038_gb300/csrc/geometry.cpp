@@ -18,6 +18,7 @@
 //   segment p -> q  : -((2 pi dturns) * sin(0.5 (lat_p + lat_q))) * sinc(0.5 (lat_q - lat_p))
 //   V_i             : R^2 * compensated sum of the signed segment integrals
 #include "geometry.h"
+#include "compsum.h"
 
 #include <algorithm>
 #include <cmath>
@@ -33,33 +34,6 @@ namespace {
 const double kPi = 3.14159265358979323846;
 const double kTwoPi = 2.0 * kPi;
 const double kHalfPi = 0.5 * kPi;
-
-// error-free transformations (Ogita, Rump, Oishi 2005)
-inline void tsum(double a, double b, double& s, double& e) {
-  s = a + b;
-  double z = s - a;
-  e = (a - (s - z)) + (b - z);
-}
-inline void tprod(double a, double b, double& p, double& e) {
-  p = a * b;
-  e = std::fma(a, b, -p);
-}
-struct Comp {
-  double s = 0, c = 0;
-  void add(double x) {
-    double t, e;
-    tsum(s, x, t, e);
-    s = t;
-    c += e;
-  }
-  void add_prod(double x, double y) {
-    double p, e;
-    tprod(x, y, p, e);
-    add(p);
-    c += e;
-  }
-  double value() const { return s + c; }
-};
 
 inline int64_t gcd_i64(int64_t a, int64_t b) {
   a = a < 0 ? -a : a;
@@ -189,6 +163,7 @@ struct ForwardEdges {
 }  // namespace
 
 bool build_mesh(const Grid& g, Mesh& m) {
+  if (g.regional()) return build_regional_mesh(g, m);
   m.grid = &g;
   const int nlat = g.nlat;
   const int64_t V = g.nnodes;
@@ -367,6 +342,7 @@ bool build_mesh(const Grid& g, Mesh& m) {
 }
 
 bool build_dual(const Mesh& m, double R, Dual& d) {
+  if (m.grid->regional()) return build_regional_dual(m, R, d);
   const Grid& g = *m.grid;
   const int64_t V = g.nnodes, E = m.nedges;
   if (!(R > 0)) return false;
@@ -478,6 +454,7 @@ double div_vdiag(const Mesh& m, const Dual& d, int64_t i) {
 }  // namespace
 
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
+  if (m.grid->regional()) return build_regional_stencil(m, d, op, s);
   const int64_t V = m.grid->nnodes;
   s.ptr.assign(static_cast<size_t>(V) + 1, 0);
   const bool regular_only = (op == OP_DIV || op == OP_DIV_ADJ || op == OP_CURL);
@@ -696,6 +673,7 @@ bool build_pair_stencil(const Stencil& s, PairStencil& p) {
 }
 
 bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg) {
+  if (m.grid->regional()) return false;  // the two-pass variant covers global grids only
   const int64_t V = m.grid->nnodes, E = m.nedges;
   const bool div = (op == OP_DIV);
   eg.ptr.assign(static_cast<size_t>(V) + 1, 0);

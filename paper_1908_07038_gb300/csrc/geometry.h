@@ -24,6 +24,13 @@ struct Grid {
   std::vector<double> colat;   // colatitude of each row (radians)
   std::vector<double> lat;     // latitude of each row (radians)
   std::vector<double> lonlat;  // [nnodes][2] longitude, latitude (radians)
+  // regional (limited-area) grids: projection >= 0, nlat rows of nx points
+  int projection = -1;         // -1: global; else a RegionalProjection
+  int nx = 0;
+  double proj_params[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<double> xy;      // [nnodes][2] plane coordinates on the unit sphere
+  std::vector<double> h;       // [nnodes][2] scale factors h_x, h_y on the unit sphere
+  bool regional() const { return projection >= 0; }
 };
 
 struct Mesh {
@@ -47,6 +54,9 @@ struct Dual {
   std::vector<double> V;          // [V]
   std::vector<double> coslat;     // [V]
   std::vector<double> pole_nphi;  // [V] phi-normal of the pole segment (0 off the polar rows)
+  // regional grids only: S holds R times the plane normals of the dual faces
+  std::vector<double> A;          // [V] R^2 times the plane area of the dual cell
+  std::vector<double> Sb;         // [E][2] R times the outward plane normal of a boundary edge, else 0
 };
 
 // A node-centred stencil: out_c(i) = sum_{q in row i} sum_m W_{c,m}(q) (x_m(nbr[q]) - x_m(i))
@@ -117,5 +127,30 @@ bool build_regular_gaussian_grid(int N, Grid& g);
 // are -1 and weights 0.  Returns false on an inconsistent mesh.
 bool build_remap(const Mesh& m, const double* tgt_lonlat, int64_t ntgt, std::vector<int32_t>& nodes,
                  std::vector<double>& weights, int64_t& not_located);
+
+// Regional (limited-area) grids (regional.cpp): a rectangle of a map
+// projection, nx points per row and ny rows, triangulated two triangles per
+// quad, with the median dual built in the projection plane.  The operators
+// follow the orthogonal-coordinate forms with the projection's scale factors
+// h_x, h_y taken at the nodes, and give vector components along the grid's
+// x and y directions.
+enum RegionalProjection {
+  PROJ_ROTATED_LONLAT = 0,  // x, y = rotated longitude, latitude (degrees)
+  PROJ_MERCATOR = 1,        // x, y in metres on a sphere of radius p[4]
+  PROJ_LAMBERT_CONFORMAL = 2  // tangent cone, x, y in metres
+};
+// params: {xmin, xmax, ymin, ymax, p4, p5, p6, p7} as documented in atlas_gb.h.
+// Returns false with a reason in why on an invalid domain.
+bool build_regional_grid(int projection, int nx, int ny, const double* params, Grid& g, const char** why);
+bool build_regional_mesh(const Grid& g, Mesh& m);
+bool build_regional_dual(const Mesh& m, double R, Dual& d);
+bool build_regional_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
+// Generic table algebra for difference-form stencils with symmetric 1-ring
+// sparsity: the transpose (an adjoint) and the product L = D G of a
+// two-input divergence-like table with a one-input, two-output
+// gradient-like table (the Laplacian; stored without its diagonal, which
+// requires G applied to a constant to vanish).
+bool transpose_stencil(const Stencil& a, Stencil& t);
+bool compose_stencil(const Stencil& d, const Stencil& g, Stencil& l);
 
 }  // namespace atlasgb
