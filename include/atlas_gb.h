@@ -219,7 +219,8 @@ int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const doub
 /* Regional fvm only (EINVAL otherwise): area[nnodes] and Sb[E][2].         */
 int atlas_fvm_regional_info(atlas_fvm_t f, const double** area, const double** Sb);
 /* Build and upload the tables of the operators in op_mask (bits 1<<op)    */
-/* for the dtypes in dtype_mask (bits 1<<dtype).  Synchronous.             */
+/* for the dtypes in dtype_mask (bits 1<<dtype), with the edge-based       */
+/* tables of the gradient and divergence on global grids.  Synchronous.    */
 int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 /* Launch shape of the node-stencil kernels for one operator and storage  */
 /* dtype (atlas_dtype, or -1 for all three; each starts from a measured    */

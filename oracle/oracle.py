@@ -90,8 +90,9 @@ def _load():
         lib.orc_reg_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
         lib.orc_reg_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
         lib.orc_reg_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+        lib.orc_reg_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
         for name in ("orc_reg_gradient", "orc_reg_divergence", "orc_reg_curl", "orc_reg_laplacian",
-                     "orc_reg_gradient_adjoint", "orc_reg_divergence_adjoint"):
+                     "orc_reg_gradient_adjoint", "orc_reg_divergence_adjoint", "orc_reg_gradient_averaged"):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
                      "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
@@ -423,6 +424,15 @@ class RegionalMesh:
         if self._lib.orc_reg_gradient_adjoint(self._h, _ptr(y0), _ptr(y1), f32, ld, nlev, _ptr(nodes), n, _ptr(out)):
             raise ValueError("orc_reg_gradient_adjoint failed")
         return out
+
+    def gradient_averaged(self, f):
+        """The averaged form sum n (wa f_i + wb f_j) / (A h), every node."""
+        f, f32, ld = _field(f)
+        nlev = f.shape[1]
+        gx = np.empty((self.nnodes, nlev)); gy = np.empty((self.nnodes, nlev))
+        if self._lib.orc_reg_gradient_averaged(self._h, _ptr(f), f32, ld, nlev, _ptr(gx), _ptr(gy)):
+            raise ValueError("orc_reg_gradient_averaged failed")
+        return gx, gy
 
     def divergence_adjoint(self, d, nlev=None, nodes=None):
         d, f32, ld = _field(d)

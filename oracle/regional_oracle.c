@@ -36,6 +36,13 @@
  *   segment P -> Q has the outward normal R (Q_y - P_y, -(Q_x - P_x)).
  *  Face values.  (f_i + f_j)/2 on the segments of edge ij's face, (5 f_i + f_j)/6
  *   on a boundary half edge.
+ *  Closure.  The outward normals of a closed cell sum to zero, so with
+ *   face value f_i + w (f_j - f_i) (w = 1/2 or 1/6) the segment sum
+ *   sum n fv equals sum n w (f_j - f_i) exactly in exact arithmetic; the
+ *   oracle evaluates this closure-exact form, free of the cancellation
+ *   between terms of size |f| sum|n| of the averaged form, which is kept as
+ *   orc_reg_gradient_averaged for the check that both agree within the
+ *   closure residual.
  *  Operators (h_x, h_y scale factors at node i, A_i = R^2 times the cell's
  *   plane area, sums over the segments of cell i, Dot2 summation):
  *    gradient    g_x = sum n_x fv / (A_i h_x,i),  g_y = sum n_y fv / (A_i h_y,i)
@@ -254,26 +261,57 @@ static void reg_grad_node(const orc_reg *g, const void *f, int f32, int64_t ld, 
   int ns = cell_segments(g, i, seg);
   for (int l = 0; l < nlev; ++l) {
     racc ax = {0, 0}, ay = {0, 0};
+    double fi = rfld(f, f32, ld, i, l);
     for (int s = 0; s < ns; ++s) {
-      double fa = seg[s].wa * rfld(f, f32, ld, seg[s].a, l), fb = seg[s].wb * rfld(f, f32, ld, seg[s].b, l);
-      r_add_prod(&ax, seg[s].nx, fa); r_add_prod(&ax, seg[s].nx, fb);
-      r_add_prod(&ay, seg[s].ny, fa); r_add_prod(&ay, seg[s].ny, fb);
+      double d = seg[s].wb * (rfld(f, f32, ld, seg[s].b, l) - fi);
+      r_add_prod(&ax, seg[s].nx, d);
+      r_add_prod(&ay, seg[s].ny, d);
     }
     gx[l] = r_val(&ax) / (g->A[i] * g->hx[i]);
     gy[l] = r_val(&ay) / (g->A[i] * g->hy[i]);
   }
 }
 
-/* flux form: sum n . (F1, F2) face values / (A h_x h_y), F1 = s1 * h_y * p, F2 = s2 * h_x * q */
+/* the averaged form sum n (wa f_i + wb f_j), for the closure check */
+int orc_reg_gradient_averaged(const orc_reg *g, const void *f, int f32, int64_t ld, int nlev, double *gx,
+                              double *gy) {
+  if (!g || !f || nlev < 0 || ld < nlev) return -1;
+  rseg seg[32];
+  for (int64_t i = 0; i < g->V; ++i) {
+    int ns = cell_segments(g, i, seg);
+    for (int l = 0; l < nlev; ++l) {
+      racc ax = {0, 0}, ay = {0, 0};
+      for (int s = 0; s < ns; ++s) {
+        double fa = seg[s].wa * rfld(f, f32, ld, seg[s].a, l), fb = seg[s].wb * rfld(f, f32, ld, seg[s].b, l);
+        r_add_prod(&ax, seg[s].nx, fa); r_add_prod(&ax, seg[s].nx, fb);
+        r_add_prod(&ay, seg[s].ny, fa); r_add_prod(&ay, seg[s].ny, fb);
+      }
+      gx[i * nlev + l] = r_val(&ax) / (g->A[i] * g->hx[i]);
+      gy[i * nlev + l] = r_val(&ay) / (g->A[i] * g->hy[i]);
+    }
+  }
+  return 0;
+}
+
+/* h_j x_j - h_i x_i to within a few ulps */
+static double rdiff(double hj, double xj, double hi, double xi) {
+  double pj = hj * xj, ej = fma(hj, xj, -pj), pi = hi * xi, ei = fma(hi, xi, -pi), s, t;
+  r_two_sum(pj, -pi, &s, &t);
+  return s + (t + (ej - ei));
+}
+
+/* flux form, closure-exact: sum n w . (F_j - F_i) / (A h_x h_y) with
+ * F1 = s1 h_y p, F2 = s2 h_x q */
 static double reg_flux_node(const orc_reg *g, const rseg *seg, int ns, int64_t i, const void *p, const void *q,
                             int f32, int64_t ld, int l, double s1, double s2) {
   racc a = {0, 0};
+  double pi = rfld(p, f32, ld, i, l), qi = rfld(q, f32, ld, i, l);
   for (int s = 0; s < ns; ++s) {
-    int32_t ca = seg[s].a, cb = seg[s].b;
-    double F1a = s1 * g->hy[ca] * rfld(p, f32, ld, ca, l), F1b = s1 * g->hy[cb] * rfld(p, f32, ld, cb, l);
-    double F2a = s2 * g->hx[ca] * rfld(q, f32, ld, ca, l), F2b = s2 * g->hx[cb] * rfld(q, f32, ld, cb, l);
-    r_add_prod(&a, seg[s].nx, seg[s].wa * F1a); r_add_prod(&a, seg[s].nx, seg[s].wb * F1b);
-    r_add_prod(&a, seg[s].ny, seg[s].wa * F2a); r_add_prod(&a, seg[s].ny, seg[s].wb * F2b);
+    int32_t cb = seg[s].b;
+    double d1 = s1 * rdiff(g->hy[cb], rfld(p, f32, ld, cb, l), g->hy[i], pi);
+    double d2 = s2 * rdiff(g->hx[cb], rfld(q, f32, ld, cb, l), g->hx[i], qi);
+    r_add_prod(&a, seg[s].nx, seg[s].wb * d1);
+    r_add_prod(&a, seg[s].ny, seg[s].wb * d2);
   }
   return r_val(&a) / (g->A[i] * g->hx[i] * g->hy[i]);
 }
@@ -340,10 +378,10 @@ int orc_reg_laplacian(const orc_reg *g, const void *f, int f32, int64_t ld, int 
         int ta = 0, tb = 0;
         while (cols[ta] != seg[s].a) ++ta;
         while (cols[tb] != seg[s].b) ++tb;
-        double F1a = g->hy[seg[s].a] * gx[ta * nl + l], F1b = g->hy[seg[s].b] * gx[tb * nl + l];
-        double F2a = g->hx[seg[s].a] * gy[ta * nl + l], F2b = g->hx[seg[s].b] * gy[tb * nl + l];
-        r_add_prod(&a, seg[s].nx, seg[s].wa * F1a); r_add_prod(&a, seg[s].nx, seg[s].wb * F1b);
-        r_add_prod(&a, seg[s].ny, seg[s].wa * F2a); r_add_prod(&a, seg[s].ny, seg[s].wb * F2b);
+        double d1 = rdiff(g->hy[seg[s].b], gx[tb * nl + l], g->hy[i], gx[ta * nl + l]);
+        double d2 = rdiff(g->hx[seg[s].b], gy[tb * nl + l], g->hx[i], gy[ta * nl + l]);
+        r_add_prod(&a, seg[s].nx, seg[s].wb * d1);
+        r_add_prod(&a, seg[s].ny, seg[s].wb * d2);
       }
       out[q * nlev + l] = r_val(&a) / (g->A[i] * g->hx[i] * g->hy[i]);
     }
@@ -366,7 +404,8 @@ static int ring_of(const orc_reg *g, int64_t k, int32_t *ring) {
 }
 
 /* x = G^T (y0, y1): x_k = sum_i G_x(i, k) y0_i + G_y(i, k) y1_i, the row
- * entries being the segment coefficients n w / (A_i h_i) */
+ * entries being those of the closure-exact form: n w_b / (A_i h_i) on the
+ * segment's far node and its negative on node i */
 int orc_reg_gradient_adjoint(const orc_reg *g, const void *y0, const void *y1, int f32, int64_t ld, int nlev,
                              const int64_t *nodes, int64_t count, double *x) {
   if (!g || !y0 || !y1 || nlev < 0 || ld < nlev || rcheck(g, nodes, count)) return -1;
@@ -383,7 +422,7 @@ int orc_reg_gradient_adjoint(const orc_reg *g, const void *y0, const void *y1, i
         int ns = cell_segments(g, i, seg);
         double cx = rfld(y0, f32, ld, i, l) / (g->A[i] * g->hx[i]), cy = rfld(y1, f32, ld, i, l) / (g->A[i] * g->hy[i]);
         for (int s = 0; s < ns; ++s) {
-          double w = (seg[s].a == k ? seg[s].wa : 0.0) + (seg[s].b == k ? seg[s].wb : 0.0);
+          double w = (seg[s].b == k ? seg[s].wb : 0.0) - (i == k ? seg[s].wb : 0.0);
           if (w == 0.0) continue;
           r_add_prod(&a, seg[s].nx * w, cx);
           r_add_prod(&a, seg[s].ny * w, cy);
@@ -395,8 +434,9 @@ int orc_reg_gradient_adjoint(const orc_reg *g, const void *y0, const void *y1, i
   return 0;
 }
 
-/* (xu, xv) = D^T d: row i of D has u-entries n_x w h_y,col / (A_i h_x,i h_y,i)
- * and v-entries n_y w h_x,col / (A_i h_x,i h_y,i) */
+/* (xu, xv) = D^T d: row i of D (closure-exact form) has u-entries
+ * n_x w_b h_y,col / (A_i h_x,i h_y,i) on the segment's far node and minus
+ * that with h_y,i on node i, and v-entries likewise with n_y and h_x */
 int orc_reg_divergence_adjoint(const orc_reg *g, const void *d, int f32, int64_t ld, int nlev,
                                const int64_t *nodes, int64_t count, double *xu, double *xv) {
   if (!g || !d || nlev < 0 || ld < nlev || rcheck(g, nodes, count)) return -1;
@@ -413,7 +453,7 @@ int orc_reg_divergence_adjoint(const orc_reg *g, const void *d, int f32, int64_t
         int ns = cell_segments(g, i, seg);
         double c = rfld(d, f32, ld, i, l) / (g->A[i] * g->hx[i] * g->hy[i]);
         for (int s = 0; s < ns; ++s) {
-          double w = (seg[s].a == k ? seg[s].wa : 0.0) + (seg[s].b == k ? seg[s].wb : 0.0);
+          double w = (seg[s].b == k ? seg[s].wb : 0.0) - (i == k ? seg[s].wb : 0.0);
           if (w == 0.0) continue;
           r_add_prod(&au, seg[s].nx * w * g->hy[k], c);
           r_add_prod(&av, seg[s].ny * w * g->hx[k], c);

@@ -785,7 +785,7 @@ int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
       if (!(dtype_mask & (1u << dt))) continue;
       rc = ensure_stencil(f, op, dt);
       if (rc) return rc;
-      if (op <= atlasgb::OP_DIV && dt != ATLAS_BF16) {
+      if (op <= atlasgb::OP_DIV && dt != ATLAS_BF16 && !f->mesh->grid->g.regional()) {
         rc = ensure_edges(f, op, prec_of(static_cast<atlas_dtype>(dt)));
         if (rc) return rc;
       }

@@ -69,7 +69,12 @@ def test_all_operators_against_the_oracle(torch, product, oracle_mod, name, nx, 
     fvm = atlas.build_fvm_regional(proj, nx, ny, **kw)
     om = oracle_mod.RegionalMesh(proj, nx, ny, **kw)
     g = fvm.grid.arrays()
-    f, u, v = _inputs(g, nlev, dt)
+    if nx * ny < 64:
+        # degenerate grids: the smooth recipe is almost linear across them and
+        # its Laplacian is ~1e-4 of its terms, so take N(0, 1) fields there
+        f, u, v = (synthetic.normal((nx * ny, nlev), 40 + k).astype(dt) for k in range(3))
+    else:
+        f, u, v = _inputs(g, nlev, dt)
     tf, tu, tv = (torch.from_numpy(synthetic.padded(x, ld)).cuda() for x in (f, u, v))
     got = _run_all(fvm, tf, tu, tv, nlev)
     torch.cuda.synchronize()

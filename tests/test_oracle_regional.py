@@ -242,3 +242,20 @@ def test_convergence_on_the_sphere():
     assert np.all(slopes[:, 0] >= 1.9) and np.all(slopes[:, 1] >= 1.9) and np.all(slopes[:, 2] >= 1.9), slopes
     assert np.all(slopes[:, 3] >= 0.95), slopes  # boundary nodes: first order
     assert np.all(e[:, 4] <= 1e-6)  # the rotation's divergence vanishes (to the frames' accuracy)
+
+
+def test_closure_exact_and_averaged_forms_agree():
+    """The oracle's closure-exact gradient and the averaged form differ only
+    by f_i times the rounding residual of the cell's closure (plus the
+    rounding of each sum)."""
+    m = _mesh("lambert_south", 21, 15)
+    g = m.geometry()
+    rng = np.random.default_rng(8)
+    f = (2.0 + np.cos(g["lat"]) * np.sin(2 * g["lon"]))[:, None] + 1e-3 * rng.standard_normal((m.nnodes, 1))
+    gx, gy = m.gradient(f)
+    ax, ay = m.gradient_averaged(f)
+    res, ab = m.closure()
+    eps = np.finfo(float).eps
+    for c, (d, h) in enumerate(((gx - ax, g["hx"]), (gy - ay, g["hy"]))):
+        bound = (np.abs(f[:, 0]) * (np.abs(res[:, c]) + 8 * eps * ab) + 8 * eps * ab * np.abs(f).max()) / (g["area"] * h)
+        assert np.all(np.abs(d[:, 0]) <= bound)
