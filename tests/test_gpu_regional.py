@@ -84,6 +84,26 @@ def test_all_operators_against_the_oracle(torch, product, oracle_mod, name, nx, 
     assert max(worst.values()) <= tol, worst
 
 
+@pytest.mark.parametrize("name", ["lambert", "rotated"])
+def test_bfloat16_storage(torch, product, oracle_mod, name):
+    """BF16 storage, FP32 arithmetic: against the oracle fed the same
+    BF16-rounded inputs (2e-2 relative max-norm, as on the global grids)."""
+    atlas = product[0]
+    proj, kw = DOMAINS[name]
+    nx, ny, nlev, ld = 61, 47, 9, 16
+    fvm = atlas.build_fvm_regional(proj, nx, ny, **kw)
+    om = oracle_mod.RegionalMesh(proj, nx, ny, **kw)
+    g = fvm.grid.arrays()
+    f, u, v = _inputs(g, nlev, np.float64)
+    tf, tu, tv = (torch.from_numpy(synthetic.padded(x, ld)).cuda().to(torch.bfloat16) for x in (f, u, v))
+    got = _run_all(fvm, tf, tu, tv, nlev)
+    torch.cuda.synchronize()
+    up = lambda t: t[:, :nlev].float().double().cpu().numpy()  # noqa: E731
+    want = _oracle_all(om, up(tf), up(tu), up(tv), nlev)
+    worst = {k: _relmax(up(got[k]), want[k]) for k in want}
+    assert max(worst.values()) <= 2e-2, worst
+
+
 def test_exact_results(torch, product):
     """Constants: gradient exactly 0 (difference form); fields linear in the
     plane: gradient, divergence and curl exact to FP64 rounding at every
