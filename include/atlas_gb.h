@@ -334,7 +334,8 @@ int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t fvm, const void* f, void* la
 
 /* ---------------------------------------------------------------------- */
 /* Batched launch: many fields of different grids and level counts in one */
-/* persistent kernel (one launch, capturable in a CUDA graph).            */
+/* call (small fields in one persistent kernel, large ones in plain        */
+/* launches; capturable in a CUDA graph).                                  */
 /* ---------------------------------------------------------------------- */
 typedef struct {
   int op;              /* ATLAS_OP_GRADIENT or ATLAS_OP_DIVERGENCE           */
@@ -366,10 +367,14 @@ typedef struct {
 /* creation; re-create the batch for other fields.                         */
 int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, const atlas_batch_tune* tune,
                        atlas_batch_t* out);
-/* One persistent launch over every tile of every descriptor: block b     */
-/* computes tiles b, b + grid, ... (divergence tiles, and fields with more */
-/* levels, first).  Results do not depend on the tile order or the launch  */
-/* shape (each item is computed once, in CSR order).  A launch reads only  */
+/* Fields of at least 8 x 2048 x SMs (node, level-vector) items (O160 x   */
+/* 137 levels and larger on a GB300) get a plain launch each, with the     */
+/* operator's launch shape (atlas_fvm_set_launch); the others share one    */
+/* persistent launch over their tiles: block b computes tiles b, b + grid, */
+/* ... (divergence tiles, and fields with more levels, first).  Results    */
+/* are bitwise those of plain launches and do not depend on the tile order */
+/* or the launch shape (each item is computed once, in CSR order).  A      */
+/* launch reads only                                                       */
 /* its kernel parameters and the fields, so launches of one batch may be   */
 /* captured in CUDA graphs and replayed on any stream.                     */
 int atlas_batch_launch(atlas_batch_t b, void* stream);

@@ -1,6 +1,7 @@
-"""Batched application of the operators to many fields in one persistent
-launch (``atlas_batch_*``), optionally captured once in a CUDA graph and
-replayed.
+"""Batched application of the operators to many fields in one call
+(``atlas_batch_*``: the small fields in one persistent launch, fields of
+eight or more full GPU waves in plain launches of their own), optionally
+captured once in a CUDA graph and replayed.
 
 A ``Batch`` holds its descriptor table (passed whole to each launch as a
 kernel parameter); the field pointers are fixed when it is created, which is
@@ -16,7 +17,7 @@ from .atlas import _dtype_code, _stream
 
 
 class Batch:
-    """One persistent launch over a list of (op, fvm, inputs, outputs) jobs.
+    """One batched call over a list of (op, fvm, inputs, outputs) jobs.
 
     jobs: sequence of dicts with keys op ('gradient' | 'divergence'), fvm,
     ins (tuple of tensors), outs (tuple of tensors), nlev.

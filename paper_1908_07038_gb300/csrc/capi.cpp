@@ -1319,6 +1319,20 @@ void atlas_remap_destroy(atlas_remap_t h) {
 // ================================================================= batches
 struct atlas_batch_s {
   std::vector<atlas_fvm_s*> fvms;
+  // fields large enough to fill the GPU many times over run as plain launches
+  // with their operator's launch shape; the rest share the persistent launch
+  struct Plain {
+    atlas_fvm_s* f;
+    int op;
+    const void* in0;
+    const void* in1;
+    void* out0;
+    void* out1;
+    int nlev;
+    int64_t ld;
+  };
+  std::vector<Plain> plain;
+  atlas_dtype dtype = ATLAS_F32;
   atlasgb::BatchParams params;  // descriptor table, passed by value to every launch
   int ndesc = 0;
   int64_t ntiles = 0, node_levels = 0;
@@ -1343,7 +1357,9 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   const int tile_items = t.tile_items > 0 ? t.tile_items : 1024;
   const int threads = t.threads > 0 ? t.threads : 256;
   if (threads < 64 || threads > 1024 || threads % 32) return fail(ATLAS_EINVAL, "bad thread count %d", threads);
-  std::vector<atlasgb::BatchDescDev> hd(static_cast<size_t>(n));
+  std::vector<atlasgb::BatchDescDev> hd;
+  hd.reserve(static_cast<size_t>(n));
+  std::vector<atlas_batch_s::Plain> plain;
   int64_t tiles = 0, nl = 0;
   // Tiles are drawn in table order: the costlier tiles (divergence, then more
   // levels) go first so that the cheap ones fill the end of the launch.  The
@@ -1388,7 +1404,20 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
       if (rc) return rc;
     }
     const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][dtype].dev;
-    atlasgb::BatchDescDev& o = hd[slot];
+    nl += static_cast<int64_t>(s.nnodes) * d.nlev;
+    fv.push_back(f);
+    // at least eight waves of a full GPU (2048 resident threads per SM): its
+    // own launch costs nothing next to its work and runs the plain kernel,
+    // which keeps its pointers in the parameter bank (the persistent kernel
+    // holds them in registers, 48 against 40)
+    const int64_t own_items = static_cast<int64_t>(s.nnodes) * ((d.nlev + vec - 1) / vec);
+    if (own_items >= static_cast<int64_t>(f->num_sms) * 2048 * 8) {
+      plain.push_back(atlas_batch_s::Plain{f, grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV, d.in0,
+                                           grad ? nullptr : d.in1, d.out0, grad ? d.out1 : nullptr, d.nlev, d.ld});
+      continue;
+    }
+    hd.emplace_back();
+    atlasgb::BatchDescDev& o = hd.back();
     o.ptr = s.ptr;
     o.nbr = s.nbr;
     o.w = s.w;
@@ -1412,16 +1441,16 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     o.tile0 = static_cast<int32_t>(tiles);
     tiles += (items + tile_items - 1) / tile_items;
     if (tiles >= (int64_t(1) << 30)) return fail(ATLAS_EINVAL, "too many tiles: raise tile_items");
-    nl += static_cast<int64_t>(s.nnodes) * d.nlev;
-    fv.push_back(f);
   }
   atlas_batch_s* b = new (std::nothrow) atlas_batch_s();
   if (!b) return fail(ATLAS_ENOMEM, "out of host memory");
   std::memset(&b->params, 0, sizeof(b->params));
-  b->params.ndesc = n;
+  b->params.ndesc = static_cast<int32_t>(hd.size());
   b->params.ntiles = static_cast<int32_t>(tiles);
   b->params.tile_items = tile_items;
-  for (int k = 0; k < n; ++k) b->params.d[k] = hd[k];
+  for (size_t k = 0; k < hd.size(); ++k) b->params.d[k] = hd[k];
+  b->plain = plain;
+  b->dtype = dtype;
   b->fvms = fv;
   for (atlas_fvm_s* f : fv) f->users++;
   b->ndesc = n;
@@ -1448,6 +1477,12 @@ int atlas_batch_launch(atlas_batch_t h, void* stream) {
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device)
     return fail(ATLAS_ESTATE, "batch lives on device %d, current device is %d", b->device, cur);
+  for (const atlas_batch_s::Plain& p : b->plain) {
+    const int64_t V = p.f->mesh->grid->g.nnodes;
+    const int rc = run_stencil_range(p.f, p.op, p.in0, p.in1, p.out0, p.out1, p.nlev, p.ld, b->dtype, stream, 0, V,
+                                     0, V);
+    if (rc) return rc;
+  }
   if (b->ntiles == 0) return ok();
   cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->idx32, b->params, b->threads, b->blocks,
                                         static_cast<cudaStream_t>(stream));
