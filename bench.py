@@ -525,12 +525,19 @@ def run_native(args):
         nl = bt.node_levels
         ms_graph = tune.time_call(bt.replay, reps=20, warmup=3)
         ms_plain = tune.time_call(lambda: B.plain(jobs), reps=20, warmup=3)
+        bt.close()
+        # the same batch with the fields of eight or more full GPU waves in
+        # plain launches of their own (the small ones stay persistent)
+        bh = B.Batch(jobs, tune=dict(bt_cfg, plain_waves=8))
+        bh.capture()
+        ms_hybrid = tune.time_call(bh.replay, reps=20, warmup=3)
+        bh.close()
         batched = {"fields": len(jobs), "node_levels": nl, "graph_replay_ms": round(ms_graph, 4),
                    "plain_launches_ms": round(ms_plain, 4),
                    "graph_node_levels_per_s": nl / (ms_graph * 1e-3),
                    "plain_node_levels_per_s": nl / (ms_plain * 1e-3), "tune": bt_cfg,
+                   "graph_replay_ms_large_fields_plain": round(ms_hybrid, 4),
                    "grids": sorted({j["N"] for j in jobs}), "levels": sorted({j["nlev"] for j in jobs})}
-        bt.close()
         del jobs, fvms
         torch.cuda.empty_cache()
 

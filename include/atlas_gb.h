@@ -334,8 +334,8 @@ int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t fvm, const void* f, void* la
 
 /* ---------------------------------------------------------------------- */
 /* Batched launch: many fields of different grids and level counts in one */
-/* call (small fields in one persistent kernel, large ones in plain        */
-/* launches; capturable in a CUDA graph).                                  */
+/* persistent kernel (one launch, capturable in a CUDA graph; optionally   */
+/* the largest fields in plain launches of their own).                     */
 /* ---------------------------------------------------------------------- */
 typedef struct {
   int op;              /* ATLAS_OP_GRADIENT or ATLAS_OP_DIVERGENCE           */
@@ -352,12 +352,17 @@ typedef struct {
 /* levels per thread (1, 2 or 4; the batch uses the widest vec that every */
 /* field's ld and pointers allow, capped by this value), threads per       */
 /* block (64..256, default 256), blocks per SM of the persistent grid      */
-/* (0 = as many as fit).  Zero fields take the defaults.                   */
+/* (0 = as many as fit), and plain_waves: fields of at least plain_waves  */
+/* full GPU waves (plain_waves x 2048 x SMs items) run as plain launches  */
+/* with their operator's launch shape inside atlas_batch_launch, the      */
+/* others in the persistent launch (0, the default: every field in the   */
+/* persistent launch).  Zero fields take the defaults.                     */
 typedef struct {
   int vec;
   int tile_items;
   int threads;
   int blocks_per_sm;
+  int plain_waves;
 } atlas_batch_tune;
 /* n = 1..256 descriptors (split larger sets into several batches).       */
 /* Validates the descriptors and prepares every fvm's tables.  The         */
@@ -367,11 +372,10 @@ typedef struct {
 /* creation; re-create the batch for other fields.                         */
 int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, const atlas_batch_tune* tune,
                        atlas_batch_t* out);
-/* Fields of at least 8 x 2048 x SMs (node, level-vector) items (O160 x   */
-/* 137 levels and larger on a GB300) get a plain launch each, with the     */
-/* operator's launch shape (atlas_fvm_set_launch); the others share one    */
-/* persistent launch over their tiles: block b computes tiles b, b + grid, */
-/* ... (divergence tiles, and fields with more levels, first).  Results    */
+/* One persistent launch over the tiles of every field (with plain_waves  */
+/* set, the fields that large first get plain launches of their own):     */
+/* block b computes tiles b, b + grid, ... (divergence tiles, and fields   */
+/* with more levels, first).  Results                                      */
 /* are bitwise those of plain launches and do not depend on the tile order */
 /* or the launch shape (each item is computed once, in CSR order).  A      */
 /* launch reads only                                                       */

@@ -1,7 +1,7 @@
-"""Batched application of the operators to many fields in one call
-(``atlas_batch_*``: the small fields in one persistent launch, fields of
-eight or more full GPU waves in plain launches of their own), optionally
-captured once in a CUDA graph and replayed.
+"""Batched application of the operators to many fields in one persistent
+launch (``atlas_batch_*``; with ``plain_waves`` in the tune, the fields of
+that many full GPU waves or more get plain launches of their own in the same
+call), optionally captured once in a CUDA graph and replayed.
 
 A ``Batch`` holds its descriptor table (passed whole to each launch as a
 kernel parameter); the field pointers are fixed when it is created, which is
@@ -46,7 +46,8 @@ class Batch:
         tn = None
         if tune:
             tn = capi.atlas_batch_tune(int(tune.get("vec", 0)), int(tune.get("tile_items", 0)),
-                                       int(tune.get("threads", 0)), int(tune.get("blocks_per_sm", 0)))
+                                       int(tune.get("threads", 0)), int(tune.get("blocks_per_sm", 0)),
+                                       int(tune.get("plain_waves", 0)))
         h = ctypes.c_void_p()
         capi.atlas_batch_create(arr, n, dt, ctypes.byref(tn) if tn is not None else None, ctypes.byref(h))
         self.handle = h

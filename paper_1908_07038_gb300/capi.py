@@ -37,7 +37,7 @@ class atlas_batch_desc(ctypes.Structure):
 
 class atlas_batch_tune(ctypes.Structure):
     _fields_ = [("vec", ctypes.c_int), ("tile_items", ctypes.c_int), ("threads", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("plain_waves", ctypes.c_int)]
 
 
 P = ctypes.c_void_p

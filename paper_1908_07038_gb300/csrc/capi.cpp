@@ -1350,12 +1350,13 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   if (!descs || n < 1 || n > atlasgb::kBatchMaxDesc)
     return fail(ATLAS_EINVAL, "need 1..%d descriptors", atlasgb::kBatchMaxDesc);
   if (dtype != ATLAS_F32 && dtype != ATLAS_F64) return fail(ATLAS_EDTYPE, "batches take F32 or F64 fields");
-  atlas_batch_tune t{0, 0, 0, 0};
+  atlas_batch_tune t{0, 0, 0, 0, 0};
   if (tune) t = *tune;
   const int want_vec = t.vec > 0 ? t.vec : 16 / elem_size(dtype);
   if (want_vec != 1 && want_vec != 2 && want_vec != 4) return fail(ATLAS_EINVAL, "batch vec must be 1, 2 or 4");
   const int tile_items = t.tile_items > 0 ? t.tile_items : 1024;
   const int threads = t.threads > 0 ? t.threads : 256;
+  if (t.plain_waves < 0) return fail(ATLAS_EINVAL, "plain_waves must be >= 0");
   if (threads < 64 || threads > 1024 || threads % 32) return fail(ATLAS_EINVAL, "bad thread count %d", threads);
   std::vector<atlasgb::BatchDescDev> hd;
   hd.reserve(static_cast<size_t>(n));
@@ -1406,12 +1407,12 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     const atlasgb::DevStencil& s = f->st[grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV][dtype].dev;
     nl += static_cast<int64_t>(s.nnodes) * d.nlev;
     fv.push_back(f);
-    // at least eight waves of a full GPU (2048 resident threads per SM): its
-    // own launch costs nothing next to its work and runs the plain kernel,
-    // which keeps its pointers in the parameter bank (the persistent kernel
-    // holds them in registers, 48 against 40)
+    // a field of at least plain_waves full waves of the GPU (2048 resident
+    // threads per SM): its own launch costs little next to its work and runs
+    // the plain kernel, which keeps its pointers in the parameter bank (the
+    // persistent kernel holds them in registers, 48 against 40)
     const int64_t own_items = static_cast<int64_t>(s.nnodes) * ((d.nlev + vec - 1) / vec);
-    if (own_items >= static_cast<int64_t>(f->num_sms) * 2048 * 8) {
+    if (t.plain_waves > 0 && own_items >= static_cast<int64_t>(f->num_sms) * 2048 * t.plain_waves) {
       plain.push_back(atlas_batch_s::Plain{f, grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV, d.in0,
                                            grad ? nullptr : d.in1, d.out0, grad ? d.out1 : nullptr, d.nlev, d.ld});
       continue;
