@@ -370,6 +370,19 @@ def run_native(args):
                         "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
                         "launches": 2 if op == "vector_gradient" else 1,
                         "tuned": {k: mt[op][k] for k in ("vec", "batch", "threads", "tile")} if op in mt else None}
+        # FP64 volume-weighted sums of one FP32 field (the conservation sums)
+        iw = torch.empty(max(atlas.capi.atlas_fvm_integral_workspace_bytes(fvm.handle, nlev) // 8, 1),
+                         dtype=torch.float64, device="cuda")
+        io = torch.empty(nlev, dtype=torch.float64, device="cuda")
+        ms = _max_over_ranks(tune.time_call(lambda: fvm.integral(f, nlev, out=io, ws=iw), reps=max(5, args.steps),
+                                            warmup=args.warmup), ws, "cuda")
+        b = V * nlev * 4 + V * 8
+        fl = 2.0 * V * nlev
+        more["integral_fp64"] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(V * nlev, ws, ms),
+                                 "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
+                                 "fp64_tflops": round(fl / (ms * 1e-3) / 1e12, 3),
+                                 "frac_fp64": round(fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4), "launches": 2}
+        del iw, io
         # remapping to the regular Gaussian grid of half the resolution
         M = args.grid // 2
         rm = atlas.Remap(fvm.mesh, atlas.Grid(M, regular=True))

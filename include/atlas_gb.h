@@ -218,6 +218,21 @@ int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const doub
 /* edge-based two-pass calls refuse a regional fvm (EINVAL).               */
 /* Regional fvm only (EINVAL otherwise): area[nnodes] and Sb[E][2].         */
 int atlas_fvm_regional_info(atlas_fvm_t f, const double** area, const double** Sb);
+
+/* Volume-weighted sums in FP64 (the global conservation sums): for every  */
+/* level k, out[k] = sum over nodes i = node0 .. node0+count-1 of          */
+/* V_i x[(i - node0) ld + k], where x points at the row of node node0 (a  */
+/* partition's own rows: sum its part, then add the parts across ranks).  */
+/* Of the divergence and the curl the sum over the whole sphere vanishes   */
+/* (conservation).  x is F32, F64 or BF16 with the usual layout rules; out */
+/* is a device array of nlev doubles; ws a device workspace of            */
+/* atlas_fvm_integral_workspace_bytes(f, nlev) bytes, 8-byte aligned, used */
+/* by this call only.  Deterministic: FP64 partial sums of fixed node     */
+/* blocks (four interleaved accumulators each), added in block order; no  */
+/* atomics.  Enqueued on stream.                                           */
+size_t atlas_fvm_integral_workspace_bytes(atlas_fvm_t f, int nlev);
+int atlas_fvm_integral(atlas_fvm_t f, const void* x, int64_t node0, int64_t count, int nlev, int64_t ld,
+                       atlas_dtype dtype, double* out, void* ws, size_t ws_bytes, void* stream);
 /* Build and upload the tables of the operators in op_mask (bits 1<<op)    */
 /* for the dtypes in dtype_mask (bits 1<<dtype), with the edge-based       */
 /* tables of the gradient and divergence on global grids.  Synchronous.    */

@@ -442,3 +442,32 @@ class RegionalMesh:
         if self._lib.orc_reg_divergence_adjoint(self._h, _ptr(d), f32, ld, nlev, _ptr(nodes), n, _ptr(xu), _ptr(xv)):
             raise ValueError("orc_reg_divergence_adjoint failed")
         return xu, xv
+
+
+def _split(a):
+    """Veltkamp splitting: a = hi + lo with hi, lo of at most 26 significant
+    bits, so that every product of two halves is exact in FP64."""
+    c = a * 134217729.0  # 2^27 + 1
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def integral(V, x, nlev=None):
+    """Volume-weighted sums I_k = sum_i V_i x[i, k], correctly rounded: every
+    product V_i x_ik is taken exactly as the sum of the four products of the
+    operands' 26-bit halves (Dekker 1971) and all of them are added by
+    ``math.fsum`` (exact summation, one final rounding).  V: [n] FP64 dual
+    volumes; x: [n, >= nlev] (float32 values are upcast exactly)."""
+    import math
+    V = np.asarray(V, dtype=np.float64)
+    x = np.asarray(x)
+    if x.ndim == 1:
+        x = x[:, None]
+    nlev = x.shape[1] if nlev is None else int(nlev)
+    vh, vl = _split(V)
+    out = np.empty(nlev)
+    for k in range(nlev):
+        xk = x[:, k].astype(np.float64)
+        xh, xl = _split(xk)
+        out[k] = math.fsum(np.concatenate([vh * xh, vh * xl, vl * xh, vl * xl]).tolist())
+    return out

@@ -281,6 +281,25 @@ class Fvm:
                               u.shape[1] if nlev is None else nlev, ld, dt, _stream())
         return z
 
+    def integral(self, x, nlev=None, node0=0, count=None, out=None, ws=None):
+        """FP64 volume-weighted sums over nodes node0 .. node0+count-1 of the
+        rows of x (x's first row is node node0's): a float64 CUDA tensor
+        [nlev], out[k] = sum_i V_i x[i, k]."""
+        torch = _torch()
+        if not x.is_cuda or x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("x must be a CUDA tensor [rows, ld] with unit level stride")
+        count = x.shape[0] if count is None else int(count)
+        nlev = x.shape[1] if nlev is None else int(nlev)
+        if count > x.shape[0]:
+            raise ValueError("count exceeds the rows of x")
+        out = torch.empty(nlev, dtype=torch.float64, device=x.device) if out is None else out
+        need = capi.atlas_fvm_integral_workspace_bytes(self.handle, nlev)
+        if ws is None:
+            ws = torch.empty(max(need // 8, 1), dtype=torch.float64, device=x.device)
+        capi.atlas_fvm_integral(self.handle, x.data_ptr(), int(node0), count, nlev, x.stride(0), _dtype_code(x),
+                                out.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(), _stream())
+        return out
+
     def vector_gradient(self, u, v, nlev=None, out=None):
         """(ux, uy, vx, vy): gradients of both components of a tangent vector."""
         outs = out if out is not None else tuple(self._out(u, None) for _ in range(4))

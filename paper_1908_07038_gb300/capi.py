@@ -77,6 +77,8 @@ _SIGS = {
     "atlas_grid_regional_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32), PP, PP],
                                  True),
     "atlas_fvm_regional_info": (I32, [P, PP, PP], True),
+    "atlas_fvm_integral_workspace_bytes": (SZ, [P, I32], False),
+    "atlas_fvm_integral": (I32, [P, P, I64, I64, I32, I64, I32, P, P, SZ, P], True),
     "atlas_remap_create": (I32, [P, P, P], True),
     "atlas_remap_info": (I32, [P, P, P, P], True),
     "atlas_remap_apply": (I32, [P, P, P, I32, I64, I64, I32, P], True),

@@ -146,6 +146,8 @@ struct atlas_fvm_s {
   OpTables st[atlasgb::OP_COUNT][3];  // [op][storage dtype: F32, F64, BF16]
   EdgeTables eg[2][2];                // [gradient, divergence][precision]
   LaunchCfg cfg[atlasgb::OP_COUNT][3];  // [op][storage dtype], defaults from default_launch
+  DevAlloc vmem;                       // FP64 dual volumes on the device (integrals)
+  const double* d_V = nullptr;
   int users = 0;
 };
 
@@ -844,6 +846,69 @@ int atlas_fvm_stencil_table(atlas_fvm_t h, int op, int64_t* nnz, int* nin, int* 
   return ok();
 }
 
+size_t atlas_fvm_integral_workspace_bytes(atlas_fvm_t h, int nlev) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f || nlev < 0) return 0;
+  return static_cast<size_t>(std::max(f->num_sms, 1)) * 8 * static_cast<size_t>(nlev) * sizeof(double);
+}
+
+int atlas_fvm_integral(atlas_fvm_t h, const void* x, int64_t node0, int64_t count, int nlev, int64_t ld,
+                       atlas_dtype dtype, double* out, void* ws, size_t ws_bytes, void* stream) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unknown dtype %d", static_cast<int>(dtype));
+  const int64_t V = f->mesh->grid->g.nnodes;
+  if (node0 < 0 || count < 0 || node0 + count > V)
+    return fail(ATLAS_EINVAL, "node range [%lld, %lld) outside [0, %lld)", static_cast<long long>(node0),
+                static_cast<long long>(node0 + count), static_cast<long long>(V));
+  const void* used[1] = {x};
+  int rc = check_field_args(dtype, nlev, ld, used, 1);
+  if (rc) return rc;
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  if (reinterpret_cast<uintptr_t>(out) % 8 || reinterpret_cast<uintptr_t>(ws) % 8)
+    return fail(ATLAS_EALIGN, "out and ws must be 8-byte aligned");
+  const size_t need = atlas_fvm_integral_workspace_bytes(h, nlev);
+  if (!ws && need > 0) return fail(ATLAS_EINVAL, "workspace pointer is NULL");
+  if (ws_bytes < need) return fail(ATLAS_EINVAL, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+  rc = check_device(f);
+  if (rc) return rc;
+  if (nlev == 0) return ok();
+  {
+    std::lock_guard<std::mutex> lk(f->mu);
+    if (!f->d_V) {
+      cudaError_t err = cudaSuccess;
+      f->d_V = f->vmem.upload(f->d.V, err);
+      if (err != cudaSuccess) {
+        f->vmem.release();
+        f->d_V = nullptr;
+        return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for the volumes")
+                                                : cuda_fail(err, "upload of the volumes");
+      }
+    }
+  }
+  atlasgb::IntegralLaunch l;
+  l.V = f->d_V + node0;
+  l.x = x;
+  l.count = static_cast<int32_t>(count);
+  l.nlev = nlev;
+  l.ld = ld;
+  l.part = static_cast<double*>(ws);
+  l.out = out;
+  const int64_t maxb = static_cast<int64_t>(std::max(f->num_sms, 1)) * 8;
+  if (count == 0) {
+    l.nblocks = 1;  // the sums are 0: one block with no nodes writes them
+    l.chunk = 0;
+    l.count = 0;
+  } else {
+    const int64_t chunk = (count + maxb - 1) / maxb;
+    l.chunk = static_cast<int32_t>(chunk);
+    l.nblocks = static_cast<int32_t>((count + chunk - 1) / chunk);
+  }
+  cudaError_t e = atlasgb::launch_integral(storage_of(dtype), l, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "integral kernel launch");
+  return ok();
+}
+
 void atlas_fvm_destroy(atlas_fvm_t h) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return;
@@ -856,6 +921,7 @@ void atlas_fvm_destroy(atlas_fvm_t h) {
     for (auto& t : row) t.mem.release();
   for (auto& row : f->eg)
     for (auto& t : row) t.mem.release();
+  f->vmem.release();
   f->mesh->users--;
   delete f;
 }

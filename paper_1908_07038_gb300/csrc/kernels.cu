@@ -545,6 +545,63 @@ __global__ void __launch_bounds__(256, 5) batch_kernel(const __grid_constant__ B
   }
 }
 
+// ------------------------------------------------- volume-weighted integral
+// I_k = sum over nodes i of V_i x_{i,k}, in FP64, for every level k (the
+// global conservation sums: I of the divergence vanishes on the sphere).
+// Pass 1: block b sums nodes [b chunk, (b + 1) chunk) of the range; thread t
+// owns levels t, t + blockDim.x, ... and reads its level of each node row
+// (consecutive threads, consecutive levels), accumulating with four
+// interleaved FP64 accumulators (accumulator m takes the nodes congruent to
+// m mod 4 in order, the tail goes to the first; combined as
+// (a0 + a1) + (a2 + a3)) into part[b][k].  Pass 2: out[k] = the
+// sum of part[b][k] in block order.  No atomics: the result is the same on
+// every run and for every stream.
+template <typename S>
+__device__ __forceinline__ double as_f64(const S* __restrict__ x, int64_t q) {
+  if constexpr (sizeof(S) == 8)
+    return __ldg(reinterpret_cast<const double*>(x) + q);
+  else
+    return static_cast<double>(Conv<S, float>::to(x[q]));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) integral_partial_kernel(const double* __restrict__ V, const S* __restrict__ x,
+                                                               int32_t count, int32_t chunk, int32_t nlev, int64_t ld,
+                                                               double* __restrict__ part) {
+  const int32_t n0 = blockIdx.x * chunk;
+  const int32_t n1 = min(n0 + chunk, count);
+  for (int32_t k = threadIdx.x; k < nlev; k += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int32_t i = n0;
+    // eight rows in flight per thread; accumulator m takes nodes i + m and
+    // i + 4 + m, in that order
+    for (; i + 7 < n1; i += 8) {
+      double xv[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) xv[m] = as_f64(x, static_cast<int64_t>(i + m) * ld + k);
+      a0 = fma(__ldg(V + i), xv[0], a0);
+      a1 = fma(__ldg(V + i + 1), xv[1], a1);
+      a2 = fma(__ldg(V + i + 2), xv[2], a2);
+      a3 = fma(__ldg(V + i + 3), xv[3], a3);
+      a0 = fma(__ldg(V + i + 4), xv[4], a0);
+      a1 = fma(__ldg(V + i + 5), xv[5], a1);
+      a2 = fma(__ldg(V + i + 6), xv[6], a2);
+      a3 = fma(__ldg(V + i + 7), xv[7], a3);
+    }
+    for (; i < n1; ++i) a0 = fma(__ldg(V + i), as_f64(x, static_cast<int64_t>(i) * ld + k), a0);
+    part[static_cast<int64_t>(blockIdx.x) * nlev + k] = (a0 + a1) + (a2 + a3);
+  }
+}
+
+__global__ void __launch_bounds__(256) integral_final_kernel(const double* __restrict__ part, int32_t nblocks,
+                                                             int32_t nlev, double* __restrict__ out) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nlev; k += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int32_t b = 0; b < nblocks; ++b) s += part[static_cast<int64_t>(b) * nlev + k];
+    out[k] = s;
+  }
+}
+
 // ------------------------------------------------------------- remapping
 // Linear interpolation in 3D on the sphere from a source mesh to target
 // points: dst[t][k] = w0 src[n0][k] + w1 src[n1][k] + w2 src[n2][k], one
@@ -827,6 +884,24 @@ cudaError_t remap_st(StorageType st, const RemapLaunch& r, cudaStream_t stream) 
   return remap_vec<float, float, 4, IDX32>(r, stream);
 }
 }  // namespace
+
+cudaError_t launch_integral(StorageType st, const IntegralLaunch& l, cudaStream_t stream) {
+  if (l.count < 0 || l.nlev <= 0 || l.nblocks <= 0) return cudaSuccess;
+  const int threads = l.nlev >= 256 ? 256 : ((l.nlev + 31) / 32) * 32;
+  if (st == ST_F64)
+    integral_partial_kernel<double><<<l.nblocks, threads, 0, stream>>>(
+        l.V, static_cast<const double*>(l.x), l.count, l.chunk, l.nlev, l.ld, l.part);
+  else if (st == ST_BF16)
+    integral_partial_kernel<uint16_t><<<l.nblocks, threads, 0, stream>>>(
+        l.V, static_cast<const uint16_t*>(l.x), l.count, l.chunk, l.nlev, l.ld, l.part);
+  else
+    integral_partial_kernel<float><<<l.nblocks, threads, 0, stream>>>(
+        l.V, static_cast<const float*>(l.x), l.count, l.chunk, l.nlev, l.ld, l.part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  integral_final_kernel<<<(l.nlev + 255) / 256, 256, 0, stream>>>(l.part, l.nblocks, l.nlev, l.out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_remap(StorageType st, const RemapLaunch& r, cudaStream_t stream) {
   return r.idx32 ? remap_st<true>(st, r, stream) : remap_st<false>(st, r, stream);

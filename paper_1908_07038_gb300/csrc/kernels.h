@@ -136,4 +136,17 @@ struct RemapLaunch {
 };
 cudaError_t launch_remap(StorageType st, const RemapLaunch& r, cudaStream_t stream);
 
+// Volume-weighted sums I_k = sum_i V_i x_{i,k} (FP64) over count nodes whose
+// rows start at x (V already offset to the first node): nblocks blocks of
+// chunk nodes write part[nblocks][nlev], then out[nlev].
+struct IntegralLaunch {
+  const double* V = nullptr;
+  const void* x = nullptr;
+  int32_t count = 0, chunk = 0, nlev = 0, nblocks = 0;
+  int64_t ld = 0;
+  double* part = nullptr;
+  double* out = nullptr;
+};
+cudaError_t launch_integral(StorageType st, const IntegralLaunch& l, cudaStream_t stream);
+
 }  // namespace atlasgb

@@ -92,6 +92,21 @@ class Partition:
         capi.atlas_part_apply(self.handle, OPS.get(op, op), p[0], p[1], q[0], q[1],
                               t0.shape[1] if nlev is None else int(nlev), t0.stride(0), _dtype_code(t0), _stream())
 
+    def integral(self, own, nlev=None, group=None, reduce=True):
+        """FP64 volume-weighted sums over the own nodes of ``own`` (an
+        own-row field, e.g. an output of ``apply``), added over all parts by
+        ``torch.distributed.all_reduce`` when ``reduce``: the global
+        conservation sums (0 for the divergence on the sphere).  The sum over
+        parts adds one FP64 partial per part, so it can differ from the
+        whole-grid integral by rounding."""
+        if own.shape[0] != self.own_rows:
+            raise ValueError("the field needs %d rows (the own range)" % self.own_rows)
+        out = self.fvm.integral(own, nlev, node0=self.own0, count=self.own_rows)
+        if reduce:
+            import torch.distributed as dist
+            dist.all_reduce(out, group=group)
+        return out
+
     def close(self):
         if self.handle is not None and self.handle.value:
             capi.atlas_part_destroy(self.handle)

@@ -105,3 +105,25 @@ def test_info_strings(product):
     assert b"atlasgb" in capi.atlas_info()
     capi.atlas_init()
     capi.atlas_finalize()
+
+
+def test_integral_argument_errors_without_a_gpu(product):
+    """atlas_fvm_integral validates its arguments before touching the device."""
+    atlas, capi = product
+    fvm = atlas.build_fvm(4)
+    need = capi.atlas_fvm_integral_workspace_bytes(fvm.handle, 7)
+    assert need > 0 and need % 8 == 0
+    fake = 0x100000
+    bad = [
+        (fake, -1, 10, 7, 8, capi.ATLAS_F32, fake, fake, need),          # negative node0
+        (fake, 0, fvm.nnodes + 1, 7, 8, capi.ATLAS_F32, fake, fake, need),  # past the last node
+        (fake, 0, 10, 7, 8, capi.ATLAS_F32, None, fake, need),           # out NULL
+        (fake, 0, 10, 7, 8, capi.ATLAS_F32, fake + 4, fake, need),       # out misaligned
+        (fake, 0, 10, 7, 8, capi.ATLAS_F32, fake, fake, need - 8),       # workspace too small
+        (fake, 0, 10, 7, 6, capi.ATLAS_F32, fake, fake, need),           # ld < nlev
+        (fake, 0, 10, 7, 8, 9, fake, fake, need),                        # unknown dtype
+    ]
+    for args in bad:
+        with pytest.raises(capi.AtlasError) as ei:
+            capi.atlas_fvm_integral(fvm.handle, *args, None)
+        assert ei.value.code in (-1, -4, -5), args
