@@ -2,8 +2,10 @@
  * atlas_gb.h -- C ABI of libatlasgb.so: median-dual finite-volume nabla
  * operators (gradient, divergence, Laplacian, the adjoints of gradient and
  * divergence, curl and the gradient of a tangent vector field) on multi-level
- * fields over the octahedral reduced Gaussian grid, computed by CUDA kernels
- * on one GB300 (sm_103a).
+ * fields over the octahedral reduced Gaussian grid (also the regular Gaussian
+ * grid and regional grids of map projections), with FP64 conservation sums,
+ * band partitions and grid-to-grid remapping, computed by CUDA kernels on
+ * one GB300 (sm_103a).
  *
  * The paper (ESCAPE D2.3, the Atlas release) describes the workflow
  * Grid -> Mesh -> FunctionSpace -> Field (Sec. 2.3, Fig. 1 and Fig. 2), says
@@ -18,10 +20,13 @@
  *   - Return 0 on success or a negative ATLAS_E* code; atlas_last_error()
  *     then returns a message (thread-local, valid until the next call on the
  *     same thread).  No C++ exception crosses this interface.
- *   - Handles (atlas_grid_t, atlas_mesh_t, atlas_fvm_t, atlas_batch_t) are
- *     owned by the library and released by the matching *_destroy call.  A
- *     mesh keeps a reference to its grid and an fvm to its mesh: destroy in
- *     reverse order of creation.
+ *   - Handles (atlas_grid_t, atlas_mesh_t, atlas_fvm_t, atlas_batch_t,
+ *     atlas_part_t, atlas_remap_t) are owned by the library and released by
+ *     the matching *_destroy call.  A mesh keeps a reference to its grid, an
+ *     fvm to its mesh, a batch or partition to its fvms, a remap to its mesh
+ *     and target grid: destroy in reverse order of creation (a destroy that
+ *     would break a reference does nothing and leaves an ATLAS_ESTATE
+ *     message in atlas_last_error).
  *   - Field pointers are DEVICE pointers owned by the caller (for example
  *     torch tensors); the library never frees them.  A field is stored
  *     field[node][level]: node i, level k at element offset i*ld + k, with
@@ -31,7 +36,7 @@
  *     from nlev to the end of the row's last vector are set to zero; all
  *     later levels below ld are never written.  Nodes are numbered row by
  *     row from north to south, and within a row by increasing longitude
- *     starting at 0.
+ *     starting at 0 (regional grids: by rows of decreasing y, then x).
  *   - dtype selects the storage type of every field argument of the call:
  *     ATLAS_F32 (float, FP32 arithmetic), ATLAS_F64 (double, FP64
  *     arithmetic) or ATLAS_BF16 (bfloat16 storage, FP32 arithmetic).
