@@ -383,6 +383,21 @@ def run_native(args):
                                  "fp64_tflops": round(fl / (ms * 1e-3) / 1e12, 3),
                                  "frac_fp64": round(fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4), "launches": 2}
         del iw, io
+        # the edge-based two-pass forms: edge fluxes through a workspace
+        # (E x ld per flux component), then the signed node gather
+        wsz = max(atlas.capi.atlas_nabla_workspace_bytes(fvm.handle, atlas.OPS[o], 0, ld, atlas.ATLAS_F32)
+                  for o in ("gradient", "divergence", "laplacian"))
+        ew = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+        ecalls = (("gradient", lambda: fvm.gradient_edges(f, nlev, ws=ew, out=(outs[0], outs[1]))),
+                  ("divergence", lambda: fvm.divergence_edges(u, v, nlev, ws=ew, out=outs[0])),
+                  ("laplacian", lambda: fvm.laplacian_edges(f, nlev, ws=ew, out=outs[0])))
+        for op, call in ecalls:
+            ms = _max_over_ranks(tune.time_call(call, reps=max(5, args.steps), warmup=args.warmup), ws, "cuda")
+            b = _alg_bytes(op, V, nlev, 4, 0)
+            more[op + "_edges"] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(V * nlev, ws, ms),
+                                   "alg_field_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
+                                   "launches": 4 if op == "laplacian" else 2}
+        del ew
         # remapping to the regular Gaussian grid of half the resolution
         M = args.grid // 2
         rm = atlas.Remap(fvm.mesh, atlas.Grid(M, regular=True))

@@ -388,114 +388,175 @@ __global__ void __launch_bounds__(512) pair_kernel(const int32_t* __restrict__ p
 // ------------------------------------------------------------- edge pass
 // OP 0 (gradient): flux0 = k1 (x_b - x_a), flux1 = k2 (x_b - x_a)
 // OP 1 (divergence): flux0 = k1 (u_b - u_a) + k2 (v_b - v_a) + k3 v_a
+//
+// Both passes walk their items (edge or node, level-vector) one block-wide
+// pass at a time.  The items of a pass belong to at most blockDim.x
+// consecutive edges (nodes); their connectivity and coefficients are staged
+// in shared memory by one cooperative, coalesced load between two barriers,
+// and every thread then reads its own from there (the threads of one edge or
+// node read the same words: broadcasts).  The loop bound depends only on the
+// block, so all threads reach every barrier.  Launched with at most
+// kEdgeThreads threads per block.
+constexpr int kEdgeThreads = 256;
+constexpr int kGatherStage = 2048;  // CSR entries staged per pass (else read from global memory)
+
 template <typename S, typename A, int OP, int VEC>
-__global__ void __launch_bounds__(512) edge_flux_kernel(const int32_t* __restrict__ e2n, const A* __restrict__ coef,
-                                                         const S* __restrict__ in0, const S* __restrict__ in1,
-                                                         A* __restrict__ flux0, A* __restrict__ flux1,
-                                                         uint32_t nedges, int32_t nlev, int64_t ld, uint32_t nvec,
-                                                         Div32 dv) {
+__global__ void __launch_bounds__(kEdgeThreads) edge_flux_kernel(const int32_t* __restrict__ e2n,
+                                                                 const A* __restrict__ coef,
+                                                                 const S* __restrict__ in0, const S* __restrict__ in1,
+                                                                 A* __restrict__ flux0, A* __restrict__ flux1,
+                                                                 uint32_t nedges, int32_t nlev, int64_t ld,
+                                                                 uint32_t nvec, Div32 dv) {
+  __shared__ int2 s_ab[kEdgeThreads];
+  __shared__ A s_k[3][kEdgeThreads];
   const uint32_t total = nedges * nvec;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-    const uint32_t e = div_by(item, dv);
-    const int32_t lev0 = static_cast<int32_t>((item - e * nvec) * VEC);
-    const int2 ab = __ldg(reinterpret_cast<const int2*>(e2n) + e);
-    const A k1 = __ldg(coef + 3 * static_cast<int64_t>(e));
-    const A k2 = __ldg(coef + 3 * static_cast<int64_t>(e) + 1);
-    const int64_t oa = static_cast<int64_t>(ab.x) * ld + lev0, ob = static_cast<int64_t>(ab.y) * ld + lev0;
-    const int64_t oe = static_cast<int64_t>(e) * ld + lev0;
-    A xa[VEC], xb[VEC], f0[VEC];
-    vload<S, A, VEC>(in0 + oa, xa);
-    vload<S, A, VEC>(in0 + ob, xb);
-    const int nvalid = nlev - lev0;
-    if constexpr (OP == 0) {
-      A f1[VEC];
+  for (uint32_t base = blockIdx.x * blockDim.x; base < total; base += stride) {
+    const uint32_t last = min(base + blockDim.x, total) - 1;
+    const uint32_t e0 = div_by(base, dv);
+    const uint32_t ne = div_by(last, dv) - e0 + 1;  // <= blockDim.x
+    __syncthreads();  // the previous pass has read its stage
+    for (uint32_t t = threadIdx.x; t < ne; t += blockDim.x) {
+      const int64_t e = static_cast<int64_t>(e0) + t;
+      s_ab[t] = __ldg(reinterpret_cast<const int2*>(e2n) + e);
+      s_k[0][t] = __ldg(coef + 3 * e);
+      s_k[1][t] = __ldg(coef + 3 * e + 1);
+      if constexpr (OP == 1) s_k[2][t] = __ldg(coef + 3 * e + 2);
+    }
+    __syncthreads();
+    const uint32_t item = base + threadIdx.x;
+    if (item < total) {
+      const uint32_t e = div_by(item, dv);
+      const uint32_t le = e - e0;
+      const int32_t lev0 = static_cast<int32_t>((item - e * nvec) * VEC);
+      const int2 ab = s_ab[le];
+      const A k1 = s_k[0][le], k2 = s_k[1][le];
+      const int64_t oa = static_cast<int64_t>(ab.x) * ld + lev0, ob = static_cast<int64_t>(ab.y) * ld + lev0;
+      const int64_t oe = static_cast<int64_t>(e) * ld + lev0;
+      A xa[VEC], xb[VEC], f0[VEC];
+      vload<S, A, VEC>(in0 + oa, xa);
+      vload<S, A, VEC>(in0 + ob, xb);
+      const int nvalid = nlev - lev0;
+      if constexpr (OP == 0) {
+        A f1[VEC];
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        const A d = xb[k] - xa[k];
-        f0[k] = k1 * d;
-        f1[k] = k2 * d;
-      }
-      vstore<A, A, VEC>(flux0 + oe, f0, nvalid);
-      vstore<A, A, VEC>(flux1 + oe, f1, nvalid);
-    } else {
-      const A k3 = __ldg(coef + 3 * static_cast<int64_t>(e) + 2);
-      A ya[VEC], yb[VEC];
-      vload<S, A, VEC>(in1 + oa, ya);
-      vload<S, A, VEC>(in1 + ob, yb);
+        for (int k = 0; k < VEC; ++k) {
+          const A d = xb[k] - xa[k];
+          f0[k] = k1 * d;
+          f1[k] = k2 * d;
+        }
+        vstore<A, A, VEC>(flux0 + oe, f0, nvalid);
+        vstore<A, A, VEC>(flux1 + oe, f1, nvalid);
+      } else {
+        const A k3 = s_k[2][le];
+        A ya[VEC], yb[VEC];
+        vload<S, A, VEC>(in1 + oa, ya);
+        vload<S, A, VEC>(in1 + ob, yb);
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        A t = k1 * (xb[k] - xa[k]);
-        t = fma(k2, yb[k] - ya[k], t);
-        f0[k] = fma(k3, ya[k], t);
+        for (int k = 0; k < VEC; ++k) {
+          A t = k1 * (xb[k] - xa[k]);
+          t = fma(k2, yb[k] - ya[k], t);
+          f0[k] = fma(k3, ya[k], t);
+        }
+        vstore<A, A, VEC>(flux0 + oe, f0, nvalid);
       }
-      vstore<A, A, VEC>(flux0 + oe, f0, nvalid);
     }
   }
 }
 
 // OP 0: out0 = (1/V) sum +-flux0, out1 = (cos/V) sum +-flux1
 // OP 1: out0 = (1/V) sum flux0 + pole_coef * v_i
+// The pass's nodes, CSR offsets, node coefficients and (when they fit in
+// kGatherStage) CSR entries are staged in shared memory.
 template <typename S, typename A, int OP, int VEC>
-__global__ void __launch_bounds__(512) node_gather_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
-                                                           const A* __restrict__ node, const A* __restrict__ flux0,
-                                                           const A* __restrict__ flux1, const S* __restrict__ vin,
-                                                           S* __restrict__ out0, S* __restrict__ out1, int32_t nnodes,
-                                                           int32_t nlev, int64_t ld, uint32_t nvec, Div32 dv) {
+__global__ void __launch_bounds__(kEdgeThreads) node_gather_kernel(const int32_t* __restrict__ ptr,
+                                                                   const int32_t* __restrict__ ent,
+                                                                   const A* __restrict__ node,
+                                                                   const A* __restrict__ flux0,
+                                                                   const A* __restrict__ flux1,
+                                                                   const S* __restrict__ vin, S* __restrict__ out0,
+                                                                   S* __restrict__ out1, int32_t nnodes, int32_t nlev,
+                                                                   int64_t ld, uint32_t nvec, Div32 dv) {
+  __shared__ int32_t s_ptr[kEdgeThreads + 1];
+  __shared__ int32_t s_ent[kGatherStage];
+  __shared__ A s_node[3][kEdgeThreads];
   const uint32_t total = static_cast<uint32_t>(nnodes) * nvec;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-    const uint32_t i = div_by(item, dv);
-    const int32_t lev0 = static_cast<int32_t>((item - i * nvec) * VEC);
-    A acc0[VEC], acc1[VEC];
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      acc0[k] = A(0);
-      acc1[k] = A(0);
+  for (uint32_t base = blockIdx.x * blockDim.x; base < total; base += stride) {
+    const uint32_t last = min(base + blockDim.x, total) - 1;
+    const uint32_t i0 = div_by(base, dv);
+    const uint32_t nn = div_by(last, dv) - i0 + 1;  // <= blockDim.x
+    __syncthreads();  // the previous pass has read its stage
+    for (uint32_t t = threadIdx.x; t <= nn; t += blockDim.x) s_ptr[t] = __ldg(ptr + i0 + t);  // i0 + nn <= nnodes
+    for (uint32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+      const int64_t i = static_cast<int64_t>(i0) + t;
+      s_node[0][t] = __ldg(node + 3 * i);
+      s_node[1][t] = __ldg(node + 3 * i + 1);
+      s_node[2][t] = __ldg(node + 3 * i + 2);
     }
-    const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
-    for (int32_t q = q0; q < q1; ++q) {
-      const int32_t t = __ldg(ent + q);
-      const int64_t oe = static_cast<int64_t>(t >> 1) * ld + lev0;
-      A f[VEC];
-      vload<A, A, VEC>(flux0 + oe, f);
-      if (t & 1) {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) acc0[k] -= f[k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) acc0[k] += f[k];
-      }
-      if constexpr (OP == 0) {
-        vload<A, A, VEC>(flux1 + oe, f);
-        if (t & 1) {
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) acc1[k] -= f[k];
-        } else {
-#pragma unroll
-          for (int k = 0; k < VEC; ++k) acc1[k] += f[k];
-        }
-      }
-    }
-    const A inv_v = __ldg(node + 3 * static_cast<int64_t>(i));
-    const int64_t oi = static_cast<int64_t>(i) * ld + lev0;
-    const int nvalid = nlev - lev0;
-    if constexpr (OP == 0) {
-      const A cos_v = __ldg(node + 3 * static_cast<int64_t>(i) + 1);
+    __syncthreads();
+    const int32_t qfirst = s_ptr[0];
+    const int32_t nq = s_ptr[nn] - qfirst;
+    const bool staged = nq <= kGatherStage;  // the same for the whole block
+    if (staged)
+      for (int32_t t = static_cast<int32_t>(threadIdx.x); t < nq; t += static_cast<int32_t>(blockDim.x))
+        s_ent[t] = __ldg(ent + qfirst + t);
+    __syncthreads();
+    const uint32_t item = base + threadIdx.x;
+    if (item < total) {
+      const uint32_t i = div_by(item, dv);
+      const uint32_t li = i - i0;
+      const int32_t lev0 = static_cast<int32_t>((item - i * nvec) * VEC);
+      A acc0[VEC], acc1[VEC];
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
-        acc0[k] *= inv_v;
-        acc1[k] *= cos_v;
+        acc0[k] = A(0);
+        acc1[k] = A(0);
       }
-      vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
-      vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
-    } else {
-      const A pc = __ldg(node + 3 * static_cast<int64_t>(i) + 2);
-      A vi[VEC];
-      vload<S, A, VEC>(vin + oi, vi);
+      const int32_t q0 = s_ptr[li], q1 = s_ptr[li + 1];
+      for (int32_t q = q0; q < q1; ++q) {
+        const int32_t t = staged ? s_ent[q - qfirst] : __ldg(ent + q);
+        const int64_t oe = static_cast<int64_t>(t >> 1) * ld + lev0;
+        A f[VEC];
+        vload<A, A, VEC>(flux0 + oe, f);
+        if (t & 1) {
 #pragma unroll
-      for (int k = 0; k < VEC; ++k) acc0[k] = fma(pc, vi[k], acc0[k] * inv_v);
-      vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
+          for (int k = 0; k < VEC; ++k) acc0[k] -= f[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) acc0[k] += f[k];
+        }
+        if constexpr (OP == 0) {
+          vload<A, A, VEC>(flux1 + oe, f);
+          if (t & 1) {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) acc1[k] -= f[k];
+          } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) acc1[k] += f[k];
+          }
+        }
+      }
+      const A inv_v = s_node[0][li];
+      const int64_t oi = static_cast<int64_t>(i) * ld + lev0;
+      const int nvalid = nlev - lev0;
+      if constexpr (OP == 0) {
+        const A cos_v = s_node[1][li];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+          acc0[k] *= inv_v;
+          acc1[k] *= cos_v;
+        }
+        vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
+        vstore<S, A, VEC>(out1 + oi, acc1, nvalid);
+      } else {
+        const A pc = s_node[2][li];
+        A vi[VEC];
+        vload<S, A, VEC>(vin + oi, vi);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc0[k] = fma(pc, vi[k], acc0[k] * inv_v);
+        vstore<S, A, VEC>(out0 + oi, acc0, nvalid);
+      }
     }
   }
 }
