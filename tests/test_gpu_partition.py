@@ -6,7 +6,6 @@ input is the whole field's halo range (what the halo exchange delivers),
 equal the whole-grid operator's, bit for bit (same kernels, same summation
 order, only the node range and the buffers differ).  Level shards are column
 views of the whole fields passed to the whole-grid calls."""
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

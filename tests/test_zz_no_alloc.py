@@ -8,7 +8,6 @@ atlas_nabla_laplacian_edges on a 64 MiB static scratch owned by the
 library instead of a caller workspace.  This file is collected last so that
 a run stopping at the first failure has run every other test already.
 """
-import ctypes
 
 import numpy as np
 import pytest
