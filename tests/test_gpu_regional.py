@@ -229,3 +229,24 @@ def test_edge_variant_refuses_regional(torch, product):
     with pytest.raises(capi.AtlasError) as ei:
         fvm.gradient_edges(f, 4, ws=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
     assert "global" in str(ei.value)
+
+
+@pytest.mark.parametrize("dt,tol", [(np.float64, 1e-13), (np.float32, 1e-5)])
+def test_remap_global_field_to_regional_grid(torch, product, omesh, dt, tol):
+    """Boundary data for a limited-area grid: an O64 field interpolated to a
+    97 x 73 Lambert grid on the GPU, against the oracle's located triangles
+    and weights."""
+    atlas = product[0]
+    proj, kw = DOMAINS["lambert"]
+    rg = atlas.Grid.regional(proj, 97, 73, **kw)
+    r = atlas.Remap(atlas.Mesh(atlas.Grid(64)), rg)
+    om = omesh(64)
+    g = om.grid()
+    nlev = 9
+    f = synthetic.level_scalar(g["lon"], g["lat_node"], nlev, dt)
+    out = r.apply(torch.from_numpy(synthetic.padded(f, 12)).cuda(), nlev)
+    torch.cuda.synchronize()
+    a = rg.arrays()
+    want = om.remap(np.stack([a["lon"], a["lat_node"]], 1), f, nlev)
+    assert _relmax(out[:, :nlev].double().cpu().numpy(), want) <= tol
+    r.close()

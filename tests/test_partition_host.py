@@ -136,3 +136,44 @@ def test_halo_exchange_gloo(tmp_path, product, world, halo):
     mp.spawn(_exchange_rank, args=(world, _free_port(), halo, str(tmp_path)), nprocs=world, join=True)
     for r in range(world):
         assert (tmp_path / ("rank%d.txt" % r)).read_text() == "ok"
+
+
+def _integral_rank(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    from paper_1908_07038_gb300 import atlas
+    from paper_1908_07038_gb300.partition import Partition
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        fvm = atlas.build_fvm(16)
+        V = torch.from_numpy(fvm.arrays()["V"])
+
+        # host stand-in for the device sum (the kernel needs a GPU): the same
+        # contract, FP64 sums over the given node range
+        def host_integral(x, nlev=None, node0=0, count=None, out=None, ws=None):
+            count = x.shape[0] if count is None else count
+            nlev = x.shape[1] if nlev is None else nlev
+            return (V[node0:node0 + count, None] * x[:count, :nlev].double()).sum(0)
+
+        fvm.integral = host_integral
+        whole = torch.from_numpy(np.random.default_rng(10).standard_normal((fvm.nnodes, 5)))
+        p = Partition(fvm, world, rank, 1)
+        got = p.integral(whole[p.own0:p.own1])
+        want = host_integral(whole)
+        ok = bool(torch.allclose(got, want, rtol=1e-13, atol=1e-13 * float((V[:, None] * whole.abs()).sum())))
+        with open(os.path.join(out_dir, "int%d.txt" % rank), "w") as fh:
+            fh.write("ok" if ok else "mismatch %r %r" % (got.tolist(), want.tolist()))
+        p.close()
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partition_integral_all_reduce_gloo(tmp_path, product):
+    """The parts' own-node sums added by all_reduce over gloo ranks equal the
+    whole-grid sum on every rank."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    mp.spawn(_integral_rank, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        assert (tmp_path / ("int%d.txt" % r)).read_text() == "ok"
