@@ -617,12 +617,30 @@ __global__ void __launch_bounds__(256, 5) batch_kernel(const __grid_constant__ B
 // (a0 + a1) + (a2 + a3)) into part[b][k].  Pass 2: out[k] = the
 // sum of part[b][k] in block order.  No atomics: the result is the same on
 // every run and for every stream.
+// binary32 -> binary64 from the IEEE-754 layouts, on the integer pipe: sign
+// kept; a normal exponent is rebiased by 1023 - 127; a subnormal is
+// normalised (shifted left by its leading zeros, exponent 897 - shift);
+// zeros stay zeros, infinities and NaNs take exponent 2047 with the
+// significand (payload) kept.  Exact for every input, branch-free; the
+// conversion instruction would occupy GB300's narrow FP64 pipe, which the
+// FMA of the sum needs.
+__device__ __forceinline__ double widen(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const uint32_t lz = static_cast<uint32_t>(__clz(static_cast<int>(m | 1u))) - 8u;
+  const bool sub = e == 0u;
+  const uint32_t E = sub ? (m != 0u ? 897u - lz : 0u) : (e == 0xffu ? 2047u : e + (1023u - 127u));
+  const uint32_t M = sub ? ((m << lz) & 0x7fffffu) : m;
+  const uint32_t hi = (u & 0x80000000u) | (E << 20) | (M >> 3);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(M << 29));
+}
+
 template <typename S>
 __device__ __forceinline__ double as_f64(const S* __restrict__ x, int64_t q) {
   if constexpr (sizeof(S) == 8)
     return __ldg(reinterpret_cast<const double*>(x) + q);
   else
-    return static_cast<double>(Conv<S, float>::to(x[q]));
+    return widen(Conv<S, float>::to(x[q]));
 }
 
 template <typename S>
