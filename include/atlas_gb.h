@@ -200,7 +200,8 @@ void atlas_mesh_destroy(atlas_mesh_t m);
 /* face of edge e from cell a into cell b; pole edges carry the pole       */
 /* segment normal (0, +-2 pi R / n).  Everything is FP64 on the host; the  */
 /* call also records the current CUDA device, on which every operator of  */
-/* this fvm must then run.                                                 */
+/* this fvm must then run, and ends with the checks of atlas_fvm_check     */
+/* (EINVAL if the geometry came out inconsistent).                         */
 int atlas_fvm_build_dual(atlas_mesh_t m, double radius, atlas_fvm_t* out);
 /* Host FP64 views valid until atlas_fvm_destroy: V[nnodes], S[E][2],      */
 /* coslat[nnodes], pole_nphi[nnodes] (phi-normal of the pole segment).     */
@@ -238,6 +239,21 @@ int atlas_fvm_regional_info(atlas_fvm_t f, const double** area, const double** S
 size_t atlas_fvm_integral_workspace_bytes(atlas_fvm_t f, int nlev);
 int atlas_fvm_integral(atlas_fvm_t f, const void* x, int64_t node0, int64_t count, int nlev, int64_t ld,
                        atlas_dtype dtype, double* out, void* ws, size_t ws_bytes, void* stream);
+/* Consistency check of an fvm's host geometry (host only, O(E)): the      */
+/* node->edge CSR holds every edge exactly twice, at its first node with  */
+/* sign +1 and at its second with -1; edge ends are ordered and in range;  */
+/* volumes are positive; and every dual cell closes: the sum of its        */
+/* outward face normals (pole faces at both ends; half of each boundary   */
+/* edge's outward normal on regional grids) is at most 1e-12 of the sum of */
+/* their absolute values.  worst_closure (may be NULL) receives the        */
+/* largest such ratio.  EINVAL naming the first bad node otherwise.        */
+int atlas_fvm_check(atlas_fvm_t f, double* worst_closure);
+/* Testing hook: let the next `after` device allocations of the library    */
+/* succeed and fail every one after them (as out of memory) until called   */
+/* again with -1 (the default: never fail).  Calls that need an            */
+/* allocation then return ATLAS_ENOMEM and leave no partial tables behind. */
+/* Process-wide.                                                           */
+int atlas_debug_fail_allocations(int after);
 /* Build and upload the tables of the operators in op_mask (bits 1<<op)    */
 /* for the dtypes in dtype_mask (bits 1<<dtype), with the edge-based       */
 /* tables of the gradient and divergence on global grids.  Synchronous.    */

@@ -195,6 +195,14 @@ class Fvm:
             out["Sb"] = _view(sb, ctypes.c_double, 2 * E, (E, 2))
         return out
 
+    def check(self):
+        """Consistency check of the host geometry (CSR and closure of every
+        dual cell); returns the largest relative closure residual, raises
+        AtlasError naming the first bad node."""
+        worst = ctypes.c_double()
+        capi.atlas_fvm_check(self.handle, ctypes.byref(worst))
+        return worst.value
+
     def prepare(self, ops=("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint"),
                 dtypes=(ATLAS_F32,)):
         om = 0

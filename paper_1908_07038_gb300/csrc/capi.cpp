@@ -4,8 +4,10 @@
 #include "atlas_gb.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -24,6 +26,16 @@ using atlasgb::StorageType;
 // ------------------------------------------------------------------ errors
 namespace {
 thread_local std::string g_err;
+
+// NVTX range over one library call: visible to profilers (ncu --nvtx, Nsight
+// Systems), a no-op otherwise (NVTX is header-only and does nothing unless a
+// tool is attached).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -72,12 +84,24 @@ struct atlas_mesh_s {
 };
 
 namespace {
+// Testing hook (atlas_debug_fail_allocations): the number of device
+// allocations still allowed before the next ones fail, or -1 (never fail).
+std::atomic<int64_t> g_alloc_budget{-1};
+
 struct DevAlloc {
   std::vector<void*> ptrs;
   template <typename T>
   T* upload(const std::vector<T>& h, cudaError_t& err) {
     void* p = nullptr;
     const size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
+    int64_t left = g_alloc_budget.load();
+    while (left >= 0) {  // consume one allowed allocation, or fail
+      if (left == 0) {
+        err = cudaErrorMemoryAllocation;
+        return nullptr;
+      }
+      if (g_alloc_budget.compare_exchange_weak(left, left - 1)) break;
+    }
     err = cudaMalloc(&p, bytes);
     if (err != cudaSuccess) return nullptr;
     ptrs.push_back(p);
@@ -573,6 +597,7 @@ const char* atlas_info(void) {
 const char* atlas_last_error(void) { return g_err.c_str(); }
 
 int atlas_grid_octahedral(int N, atlas_grid_t* out) {
+  CallRange range_("atlas_grid_octahedral");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (N < 1 || N > 8000) return fail(ATLAS_EINVAL, "octahedral number N=%d out of range [1, 8000]", N);
@@ -593,6 +618,7 @@ int atlas_grid_octahedral(int N, atlas_grid_t* out) {
 }
 
 int atlas_grid_regular_gaussian(int N, atlas_grid_t* out) {
+  CallRange range_("atlas_grid_regular_gaussian");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (N < 1 || N > 8000) return fail(ATLAS_EINVAL, "Gaussian number N=%d out of range [1, 8000]", N);
@@ -613,6 +639,7 @@ int atlas_grid_regular_gaussian(int N, atlas_grid_t* out) {
 }
 
 int atlas_grid_regional(int projection, int nx, int ny, const double* params, atlas_grid_t* out) {
+  CallRange range_("atlas_grid_regional");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (projection < ATLAS_PROJ_ROTATED_LONLAT || projection > ATLAS_PROJ_LAMBERT_CONFORMAL)
@@ -671,6 +698,7 @@ void atlas_grid_destroy(atlas_grid_t h) {
 }
 
 int atlas_mesh_build(atlas_grid_t gh, atlas_mesh_t* out) {
+  CallRange range_("atlas_mesh_build");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!live(gh)) return fail(ATLAS_ESTATE, "invalid or destroyed grid handle");
@@ -721,6 +749,7 @@ void atlas_mesh_destroy(atlas_mesh_t h) {
 }
 
 int atlas_fvm_build_dual(atlas_mesh_t mh, double radius, atlas_fvm_t* out) {
+  CallRange range_("atlas_fvm_build_dual");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!live(mh)) return fail(ATLAS_ESTATE, "invalid or destroyed mesh handle");
@@ -734,6 +763,14 @@ int atlas_fvm_build_dual(atlas_mesh_t mh, double radius, atlas_fvm_t* out) {
     if (!atlasgb::build_dual(m->m, radius, f->d)) {
       delete f;
       return fail(ATLAS_EINVAL, "dual build failed");
+    }
+    double worst = 0.0;
+    int64_t node = -1;
+    const char* why = "";
+    if (!atlasgb::check_geometry(m->m, f->d, 1e-12, worst, node, &why)) {
+      delete f;
+      return fail(ATLAS_EINVAL, "dual build gave an inconsistent geometry: %s (node %lld)", why,
+                  static_cast<long long>(node));
     }
   } catch (const std::bad_alloc&) {
     delete f;
@@ -775,7 +812,29 @@ int atlas_fvm_regional_info(atlas_fvm_t h, const double** area, const double** S
   return ok();
 }
 
+int atlas_fvm_check(atlas_fvm_t h, double* worst_closure) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  double worst = 0.0;
+  int64_t node = -1;
+  const char* why = "inconsistent geometry";
+  const bool good = atlasgb::check_geometry(f->mesh->m, f->d, 1e-12, worst, node, &why);
+  if (worst_closure) *worst_closure = worst;
+  if (!good) {
+    if (node >= 0) return fail(ATLAS_EINVAL, "%s (node %lld)", why, static_cast<long long>(node));
+    return fail(ATLAS_EINVAL, "%s", why);
+  }
+  return ok();
+}
+
+int atlas_debug_fail_allocations(int after) {
+  if (after < -1) return fail(ATLAS_EINVAL, "after must be >= -1");
+  g_alloc_budget.store(after);
+  return ok();
+}
+
 int atlas_fvm_prepare(atlas_fvm_t h, unsigned op_mask, unsigned dtype_mask) {
+  CallRange range_("atlas_fvm_prepare");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   int rc = check_device(f);
@@ -854,6 +913,7 @@ size_t atlas_fvm_integral_workspace_bytes(atlas_fvm_t h, int nlev) {
 
 int atlas_fvm_integral(atlas_fvm_t h, const void* x, int64_t node0, int64_t count, int nlev, int64_t ld,
                        atlas_dtype dtype, double* out, void* ws, size_t ws_bytes, void* stream) {
+  CallRange range_("atlas_fvm_integral");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unknown dtype %d", static_cast<int>(dtype));
@@ -928,30 +988,37 @@ void atlas_fvm_destroy(atlas_fvm_t h) {
 
 int atlas_nabla_gradient(atlas_fvm_t fvm, const void* f, void* gx, void* gy, int nlev, int64_t ld, atlas_dtype dtype,
                          void* stream) {
+  CallRange range_("atlas_nabla_gradient");
   return run_stencil_op(fvm, atlasgb::OP_GRAD, f, nullptr, gx, gy, nlev, ld, dtype, stream);
 }
 int atlas_nabla_divergence(atlas_fvm_t fvm, const void* u, const void* v, void* div, int nlev, int64_t ld,
                            atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_divergence");
   return run_stencil_op(fvm, atlasgb::OP_DIV, u, v, div, nullptr, nlev, ld, dtype, stream);
 }
 int atlas_nabla_laplacian(atlas_fvm_t fvm, const void* f, void* lap, int nlev, int64_t ld, atlas_dtype dtype,
                           void* stream) {
+  CallRange range_("atlas_nabla_laplacian");
   return run_stencil_op(fvm, atlasgb::OP_LAP, f, nullptr, lap, nullptr, nlev, ld, dtype, stream);
 }
 int atlas_nabla_gradient_adjoint(atlas_fvm_t fvm, const void* gx, const void* gy, void* f, int nlev, int64_t ld,
                                  atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_gradient_adjoint");
   return run_stencil_op(fvm, atlasgb::OP_GRAD_ADJ, gx, gy, f, nullptr, nlev, ld, dtype, stream);
 }
 int atlas_nabla_divergence_adjoint(atlas_fvm_t fvm, const void* div, void* u, void* v, int nlev, int64_t ld,
                                    atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_divergence_adjoint");
   return run_stencil_op(fvm, atlasgb::OP_DIV_ADJ, div, nullptr, u, v, nlev, ld, dtype, stream);
 }
 int atlas_nabla_curl(atlas_fvm_t fvm, const void* u, const void* v, void* zeta, int nlev, int64_t ld,
                      atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_curl");
   return run_stencil_op(fvm, atlasgb::OP_CURL, u, v, zeta, nullptr, nlev, ld, dtype, stream);
 }
 int atlas_nabla_vector_gradient(atlas_fvm_t h, const void* u, const void* v, void* ux, void* uy, void* vx, void* vy,
                                 int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_vector_gradient");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   // the two launches must not see each other's outputs as inputs
@@ -978,6 +1045,7 @@ size_t atlas_nabla_workspace_bytes(atlas_fvm_t h, int op, int nlev, int64_t ld, 
 
 int atlas_nabla_gradient_edges(atlas_fvm_t h, const void* fin, void* gx, void* gy, void* ws, size_t ws_bytes, int nlev,
                                int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_gradient_edges");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (f->mesh->grid->g.regional())
@@ -1003,6 +1071,7 @@ int atlas_nabla_gradient_edges(atlas_fvm_t h, const void* fin, void* gx, void* g
 
 int atlas_nabla_divergence_edges(atlas_fvm_t h, const void* u, const void* v, void* div, void* ws, size_t ws_bytes,
                                  int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_divergence_edges");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (f->mesh->grid->g.regional())
@@ -1028,6 +1097,7 @@ int atlas_nabla_divergence_edges(atlas_fvm_t h, const void* u, const void* v, vo
 
 int atlas_nabla_laplacian_edges(atlas_fvm_t h, const void* fin, void* lap, void* ws, size_t ws_bytes, int nlev,
                                 int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_laplacian_edges");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (f->mesh->grid->g.regional())
@@ -1060,6 +1130,7 @@ int atlas_nabla_laplacian_edges(atlas_fvm_t h, const void* fin, void* lap, void*
 // kernels as atlas_nabla_laplacian_edges, no allocation of any kind.
 int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t h, const void* fin, void* lap, int nlev, int64_t ld,
                                         atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_laplacian_edges_noalloc");
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (f->mesh->grid->g.regional())
@@ -1098,6 +1169,7 @@ int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t h, const void* fin, void* la
 }
 
 int atlas_field_sync(void* dst, const void* src, size_t bytes, int direction, void* stream) {
+  CallRange range_("atlas_field_sync");
   if (bytes == 0) return ok();
   if (!dst || !src) return fail(ATLAS_EINVAL, "NULL pointer");
   cudaMemcpyKind kind;
@@ -1214,6 +1286,7 @@ int atlas_part_neighbour(atlas_part_t h, int side, int* peer, int64_t* send0, in
 
 int atlas_part_apply(atlas_part_t h, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
                      int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_part_apply");
   if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed partition handle");
   atlas_part_s* p = reinterpret_cast<atlas_part_s*>(h);
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
@@ -1251,6 +1324,7 @@ struct atlas_remap_s {
 extern "C" {
 
 int atlas_remap_create(atlas_mesh_t sh, atlas_grid_t th, atlas_remap_t* out) {
+  CallRange range_("atlas_remap_create");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!live(sh)) return fail(ATLAS_ESTATE, "invalid or destroyed mesh handle");
@@ -1308,6 +1382,7 @@ int atlas_remap_info(atlas_remap_t h, int64_t* ntgt, const int32_t** nodes, cons
 
 int atlas_remap_apply(atlas_remap_t h, const void* src, void* dst, int nlev, int64_t ld_src, int64_t ld_dst,
                       atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_remap_apply");
   if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed remap handle");
   atlas_remap_s* r = reinterpret_cast<atlas_remap_s*>(h);
   const void* used[2] = {src, dst};
@@ -1411,6 +1486,7 @@ extern "C" {
 
 int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, const atlas_batch_tune* tune,
                        atlas_batch_t* out) {
+  CallRange range_("atlas_batch_create");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!descs || n < 1 || n > atlasgb::kBatchMaxDesc)
@@ -1539,6 +1615,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
 }
 
 int atlas_batch_launch(atlas_batch_t h, void* stream) {
+  CallRange range_("atlas_batch_launch");
   if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed batch handle");
   atlas_batch_s* b = reinterpret_cast<atlas_batch_s*>(h);
   int cur = -1;

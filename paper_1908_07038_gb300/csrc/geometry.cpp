@@ -707,4 +707,56 @@ bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg) {
   return true;
 }
 
+bool check_geometry(const Mesh& m, const Dual& d, double tol, double& worst, int64_t& bad_node, const char** why) {
+  const Grid& g = *m.grid;
+  const int64_t V = g.nnodes, E = m.nedges;
+  const bool regional = g.regional();
+  worst = 0.0;
+  bad_node = -1;
+  auto bad = [&](int64_t i, const char* w) {
+    bad_node = i;
+    if (why) *why = w;
+    return false;
+  };
+  if (static_cast<int64_t>(m.n2e_ptr.size()) != V + 1 || m.n2e_ptr[0] != 0 || m.n2e_ptr[V] != 2 * E)
+    return bad(-1, "node->edge offsets do not cover 2E entries");
+  if (static_cast<int64_t>(d.S.size()) != 2 * E || static_cast<int64_t>(d.V.size()) != V ||
+      (regional && static_cast<int64_t>(d.Sb.size()) != 2 * E))
+    return bad(-1, "dual arrays have the wrong sizes");
+  std::vector<uint8_t> seen(static_cast<size_t>(E), 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t a = m.e2n[2 * e], b = m.e2n[2 * e + 1];
+    if (a < 0 || b >= V || !(a < b)) return bad(-1, "edge ends out of range or not ordered");
+  }
+  for (int64_t i = 0; i < V; ++i) {
+    if (m.n2e_ptr[i + 1] < m.n2e_ptr[i]) return bad(i, "node->edge offsets decrease");
+    Comp c0, c1;
+    double absum = 0.0;
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+      const int32_t e = m.n2e[q];
+      if (e < 0 || e >= E) return bad(i, "edge id out of range");
+      const int32_t a = m.e2n[2 * e], b = m.e2n[2 * e + 1];
+      const int s = m.n2e_sign[q];
+      if (!((a == i && s == 1) || (b == i && s == -1))) return bad(i, "edge not incident to its node, or wrong sign");
+      seen[e] = static_cast<uint8_t>(seen[e] + 1);
+      const double sg = m.is_pole[e] ? 1.0 : static_cast<double>(s);
+      double nx = sg * d.S[2 * e], ny = sg * d.S[2 * e + 1];
+      if (regional) {
+        nx += 0.5 * d.Sb[2 * e];
+        ny += 0.5 * d.Sb[2 * e + 1];
+      }
+      c0.add(nx);
+      c1.add(ny);
+      absum += std::fabs(nx) + std::fabs(ny);
+    }
+    const double res = (std::fabs(c0.value()) + std::fabs(c1.value())) / (absum > 0 ? absum : 1.0);
+    if (!(res <= worst)) worst = std::isnan(res) ? res : std::max(worst, res);
+    if (!(res <= tol)) return bad(i, "dual cell does not close");
+    if (!(d.V[i] > 0)) return bad(i, "dual volume is not positive");
+  }
+  for (int64_t e = 0; e < E; ++e)
+    if (seen[e] != 2) return bad(-1, "an edge does not appear exactly twice in the node->edge rows");
+  return true;
+}
+
 }  // namespace atlasgb

@@ -145,6 +145,15 @@ bool build_regional_grid(int projection, int nx, int ny, const double* params, G
 bool build_regional_mesh(const Grid& g, Mesh& m);
 bool build_regional_dual(const Mesh& m, double R, Dual& d);
 bool build_regional_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
+// Consistency of a mesh and its dual (any grid): the node->edge CSR covers
+// every edge exactly twice, at its first node with sign +1 and at its second
+// with -1; edge ends are in range with a < b; and every dual cell closes: the
+// sum of its outward face normals (pole faces counted at both ends; half of
+// each boundary edge's normal on regional grids) is at most tol times the sum
+// of their absolute values.  On failure returns false with the first bad
+// node (or -1) and a reason; worst is the largest relative closure residual.
+bool check_geometry(const Mesh& m, const Dual& d, double tol, double& worst, int64_t& bad_node, const char** why);
+
 // Generic table algebra for difference-form stencils with symmetric 1-ring
 // sparsity: the transpose (an adjoint) and the product L = D G of a
 // two-input divergence-like table with a one-input, two-output
