@@ -481,6 +481,20 @@ int atlas_part_neighbour(atlas_part_t p, int side, int* peer, int64_t* send0, in
 /* The Laplacian needs halo_rings = 2.                                     */
 int atlas_part_apply(atlas_part_t p, int op, const void* in0, const void* in1, void* out0, void* out1, int nlev,
                      int64_t ld, atlas_dtype dtype, void* stream);
+/* Overlap of the halo exchange with computation (the asynchronous        */
+/* communication the paper aims for, Sec. 2.2.3): the interior range       */
+/* [inner0, inner1) holds the own nodes whose stencils read no halo row    */
+/* (own rows at least halo_rings rows from each side that has a            */
+/* neighbour), computable while the exchange is in flight; the own nodes   */
+/* outside it need the exchanged halo.  inner0 == inner1 when a part has   */
+/* no interior.                                                            */
+int atlas_part_interior(atlas_part_t p, int64_t* inner0, int64_t* inner1);
+/* atlas_part_apply restricted to own nodes [node0, node0 + count) within  */
+/* [own0, own1): inputs as for atlas_part_apply (halo-range fields), the   */
+/* outputs still own-range fields (row k = node own0 + k; only rows of the */
+/* range are written).  Same results, bitwise, as the whole own range.     */
+int atlas_part_apply_nodes(atlas_part_t p, int op, const void* in0, const void* in1, void* out0, void* out1,
+                           int64_t node0, int64_t count, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
 void atlas_part_destroy(atlas_part_t p);
 
 /* ---------------------------------------------------------------------- */

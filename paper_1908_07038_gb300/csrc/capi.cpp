@@ -1296,6 +1296,41 @@ int atlas_part_apply(atlas_part_t h, int op, const void* in0, const void* in1, v
                            p->halo0, p->halo1 - p->halo0);
 }
 
+int atlas_part_interior(atlas_part_t h, int64_t* inner0, int64_t* inner1) {
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed partition handle");
+  const atlas_part_s* p = reinterpret_cast<const atlas_part_s*>(h);
+  if (!live(p->fvm)) return fail(ATLAS_ESTATE, "the partition's fvm was destroyed");
+  const atlasgb::Grid& g = p->fvm->mesh->grid->g;
+  // a side with a neighbour gives up halo rows to the exchange
+  const int r0 = p->peer[0] >= 0 ? p->r0 + p->halo : p->r0;
+  const int r1 = p->peer[1] >= 0 ? p->r1 - p->halo : p->r1;
+  const int64_t a = g.off[std::min(std::max(r0, p->r0), p->r1)];
+  const int64_t b = g.off[std::min(std::max(r1, p->r0), p->r1)];
+  if (inner0) *inner0 = a;
+  if (inner1) *inner1 = std::max(a, b);  // empty when the part is thinner than its halos
+  return ok();
+}
+
+int atlas_part_apply_nodes(atlas_part_t h, int op, const void* in0, const void* in1, void* out0, void* out1,
+                           int64_t node0, int64_t count, int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_part_apply_nodes");
+  if (!live(h)) return fail(ATLAS_ESTATE, "invalid or destroyed partition handle");
+  atlas_part_s* p = reinterpret_cast<atlas_part_s*>(h);
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (op == atlasgb::OP_LAP && p->halo < 2) return fail(ATLAS_EINVAL, "the Laplacian needs a halo of 2 rows");
+  if (!live(p->fvm)) return fail(ATLAS_ESTATE, "the partition's fvm was destroyed");
+  if (count < 0 || node0 < p->own0 || node0 + count > p->own1)
+    return fail(ATLAS_EINVAL, "node range [%lld, %lld) outside the own range [%lld, %lld)",
+                static_cast<long long>(node0), static_cast<long long>(node0 + count),
+                static_cast<long long>(p->own0), static_cast<long long>(p->own1));
+  if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unknown dtype %d", static_cast<int>(dtype));
+  // the output pointers address row node0 - own0 of the own-range fields
+  const int64_t skip = (node0 - p->own0) * ld * elem_size(dtype);
+  auto at = [&](void* q) -> void* { return q ? static_cast<void*>(static_cast<char*>(q) + skip) : nullptr; };
+  return run_stencil_range(p->fvm, op, in0, in1, at(out0), at(out1), nlev, ld, dtype, stream, node0, count, p->halo0,
+                           p->halo1 - p->halo0);
+}
+
 void atlas_part_destroy(atlas_part_t h) {
   if (!live(h)) return;
   atlas_part_s* p = reinterpret_cast<atlas_part_s*>(h);

@@ -10,6 +10,10 @@ halo0 + k); ``exchange`` refreshes its halo rows from the two adjacent parts
 with point-to-point messages of ``torch.distributed`` (rank = part index:
 gloo for CPU tensors, NCCL for CUDA tensors), and the operator calls compute
 the own nodes, bitwise equal to the whole-grid operators there.
+``apply_overlapped`` hides the exchange behind computation (the asynchronous
+communication the paper aims for, Sec. 2.2.3): the messages are started,
+the interior nodes (whose stencils read no halo row) are computed, and the
+rows next to the halo follow once the messages are done.
 
 Levels are independent, so a field can instead be cut by levels with no
 exchange at all: ``level_shards`` gives the level ranges (starting on 16-byte
@@ -57,10 +61,11 @@ class Partition:
         """The own rows inside a local field."""
         return local[self.own0 - self.halo0:self.own1 - self.halo0]
 
-    def exchange(self, local, group=None):
-        """Send this part's boundary rows to the adjacent parts and receive
-        their rows into the halo of ``local`` ([halo1 - halo0, ld], contiguous
-        rows).  Blocks until the messages are done."""
+    def exchange_start(self, local, group=None):
+        """Start sending this part's boundary rows to the adjacent parts and
+        receiving their rows into the halo of ``local`` ([halo1 - halo0, ld],
+        contiguous rows); returns the pending requests for ``exchange_wait``.
+        Until then the halo rows must not be read, nor the sent rows written."""
         import torch.distributed as dist
         if local.shape[0] != self.local_rows or not local.is_contiguous():
             raise ValueError("local field must be contiguous with %d rows" % self.local_rows)
@@ -70,12 +75,45 @@ class Partition:
             r0, r1 = (x - self.halo0 for x in n["recv"])
             reqs.append(dist.isend(local[s0:s1], n["peer"], group=group))
             reqs.append(dist.irecv(local[r0:r1], n["peer"], group=group))
+        return reqs
+
+    @staticmethod
+    def exchange_wait(reqs):
         for r in reqs:
             r.wait()
+
+    def exchange(self, local, group=None):
+        """The exchange, blocking until its messages are done."""
+        self.exchange_wait(self.exchange_start(local, group))
+
+    @property
+    def interior(self):
+        """Own nodes [inner0, inner1) whose stencils read no halo row."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        capi.atlas_part_interior(self.handle, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+    def apply_overlapped(self, op, ins, outs, nlev=None, group=None):
+        """Exchange the halos of ``ins`` while the interior nodes are
+        computed, then compute the nodes next to the halo: the results of
+        ``exchange`` followed by ``apply``, bitwise."""
+        reqs = []
+        for t in ins:
+            reqs += self.exchange_start(t, group)
+        i0, i1 = self.interior
+        self.apply_nodes(op, ins, outs, i0, i1 - i0, nlev)
+        self.exchange_wait(reqs)
+        self.apply_nodes(op, ins, outs, self.own0, i0 - self.own0, nlev)
+        self.apply_nodes(op, ins, outs, i1, self.own1 - i1, nlev)
 
     def apply(self, op, ins, outs, nlev=None):
         """Operator ``op`` on the own nodes: ins are local fields (halo rows
         filled), outs own-row fields; same dtype and leading dimension."""
+        self.apply_nodes(op, ins, outs, self.own0, self.own_rows, nlev)
+
+    def apply_nodes(self, op, ins, outs, node0, count, nlev=None):
+        """``apply`` on the own nodes [node0, node0 + count) only (outs are
+        still own-row fields; only those rows are written)."""
         ins, outs = list(ins), list(outs)
         t0 = ins[0]
         for t in ins:
@@ -89,8 +127,9 @@ class Partition:
                 raise ValueError("fields must be CUDA tensors [rows, ld] of one dtype and leading dimension")
         p = [x.data_ptr() for x in ins] + [None] * (2 - len(ins))
         q = [x.data_ptr() for x in outs] + [None] * (2 - len(outs))
-        capi.atlas_part_apply(self.handle, OPS.get(op, op), p[0], p[1], q[0], q[1],
-                              t0.shape[1] if nlev is None else int(nlev), t0.stride(0), _dtype_code(t0), _stream())
+        capi.atlas_part_apply_nodes(self.handle, OPS.get(op, op), p[0], p[1], q[0], q[1], int(node0), int(count),
+                                    t0.shape[1] if nlev is None else int(nlev), t0.stride(0), _dtype_code(t0),
+                                    _stream())
 
     def integral(self, own, nlev=None, group=None, reduce=True):
         """FP64 volume-weighted sums over the own nodes of ``own`` (an

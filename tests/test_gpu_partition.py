@@ -103,3 +103,37 @@ def test_level_shards_equal_whole_levels(torch, pfvm, nparts):
         torch.cuda.synchronize()
         for s_, w in ((sx, gx), (sy, gy), (sd, d), (sl, lap)):
             assert torch.equal(s_[:, a:b], w[:, a:b]), (a, b)
+
+
+@pytest.mark.parametrize("dtype,ld", [("float32", 140), ("float64", 138)])
+def test_interior_then_boundary_equals_whole_grid(torch, pfvm, dtype, ld):
+    """The overlapped schedule on one GPU: each part computes its interior
+    nodes (no halo needed) and then the rows next to its halo, with
+    ``apply_nodes``; the assembled outputs equal the whole-grid operators
+    bitwise."""
+    from paper_1908_07038_gb300.partition import Partition
+    dt = getattr(torch, dtype)
+    fvm = pfvm(80)
+    nlev = 137
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    fields = [torch.randn((fvm.nnodes, ld), generator=gen, device="cuda").to(dt) for _ in range(2)]
+    for op, nin, nout in OPS[:6]:
+        ins = fields[:nin]
+        want = _whole(fvm, op, ins, nlev)
+        halo = 2 if op == "laplacian" else 1
+        got = [torch.full_like(want[0], float("nan")) for _ in range(nout)]
+        for k in range(3):
+            p = Partition(fvm, 3, k, halo)
+            local = [p.local_view(x).clone() for x in ins]
+            outs = [torch.full((p.own_rows, ld), float("nan"), dtype=dt, device="cuda") for _ in range(nout)]
+            i0, i1 = p.interior
+            assert p.own0 <= i0 < i1 <= p.own1
+            p.apply_nodes(op, local, outs, i0, i1 - i0, nlev)
+            p.apply_nodes(op, local, outs, p.own0, i0 - p.own0, nlev)
+            p.apply_nodes(op, local, outs, i1, p.own1 - i1, nlev)
+            for g_, o in zip(got, outs):
+                g_[p.own0:p.own1] = o
+            p.close()
+        torch.cuda.synchronize()
+        for g_, w in zip(got, want):
+            assert torch.equal(g_[:, :nlev], w[:, :nlev]), (op, dtype)

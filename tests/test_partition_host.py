@@ -177,3 +177,82 @@ def test_partition_integral_all_reduce_gloo(tmp_path, product):
     mp.spawn(_integral_rank, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     for r in range(2):
         assert (tmp_path / ("int%d.txt" % r)).read_text() == "ok"
+
+
+@pytest.mark.parametrize("nparts,halo", [(2, 1), (3, 2), (5, 1), (7, 2)])
+def test_interior_reads_no_halo(pfvm, part_mod, nparts, halo):
+    """Every node of a part's interior has all its stencil neighbours among
+    the part's own nodes, and the interior spans the own rows less the halo
+    rows on each side that has a neighbour."""
+    fvm = pfvm(32)
+    ops = ["gradient", "divergence", "curl"] + (["laplacian"] if halo == 2 else [])
+    tabs = {op: fvm.stencil_table(op) for op in ops}
+    pl = fvm.grid.arrays()["pl"]
+    off = np.concatenate([[0], np.cumsum(pl)])
+    for k in range(nparts):
+        p = part_mod.Partition(fvm, nparts, k, halo)
+        i0, i1 = p.interior
+        assert p.own0 <= i0 <= i1 <= p.own1
+        r0 = int(np.searchsorted(off, p.own0))
+        r1 = int(np.searchsorted(off, p.own1))
+        want0 = off[r0 + halo] if k > 0 else p.own0
+        want1 = off[r1 - halo] if k < nparts - 1 else p.own1
+        assert (i0, i1) == (want0, max(want0, want1))
+        for op, t in tabs.items():
+            lo, hi = t["ptr"][i0], t["ptr"][i1]
+            nb = t["nbr"][lo:hi]
+            assert nb.size == 0 or (nb.min() >= p.own0 and nb.max() < p.own1), (op, k)
+        p.close()
+
+
+def _overlap_rank(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    from paper_1908_07038_gb300 import atlas
+    from paper_1908_07038_gb300.partition import Partition
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        fvm = atlas.build_fvm(16)
+        t = fvm.stencil_table("gradient")
+        ptr, nbr, w = t["ptr"], t["nbr"], t["w"]
+
+        # host stand-in for the device kernels (they need a GPU): the FP64
+        # gradient table applied to the rows [node0, node0 + count)
+        def host_apply_nodes(p, op, ins, outs, node0, count, nlev=None):
+            x = ins[0].numpy()
+            for i in range(node0, node0 + count):
+                q = slice(ptr[i], ptr[i + 1])
+                d = x[nbr[q] - p.halo0] - x[i - p.halo0]
+                for c in range(2):
+                    outs[c][i - p.own0] = torch.from_numpy(w[q, c] @ d)
+
+        whole = torch.from_numpy(np.random.default_rng(13).standard_normal((fvm.nnodes, 3)))
+        p = Partition(fvm, world, rank, 1)
+        p.apply_nodes = lambda op, ins, outs, node0, count, nlev=None: host_apply_nodes(p, op, ins, outs, node0,
+                                                                                        count, nlev)
+        local = torch.full((p.local_rows, 3), float("nan"), dtype=torch.float64)
+        p.own_of_local(local).copy_(whole[p.own0:p.own1])
+        outs = [torch.full((p.own_rows, 3), float("nan"), dtype=torch.float64) for _ in range(2)]
+        p.apply_overlapped("gradient", [local], outs)
+        full = Partition(fvm, 1, 0, 1)
+        ref = [torch.zeros((fvm.nnodes, 3), dtype=torch.float64) for _ in range(2)]
+        host_apply_nodes(full, "gradient", [whole], ref, 0, fvm.nnodes)
+        ok = all(torch.equal(o, r[p.own0:p.own1]) for o, r in zip(outs, ref))
+        with open(os.path.join(out_dir, "ov%d.txt" % rank), "w") as fh:
+            fh.write("ok" if ok else "mismatch")
+        p.close()
+        full.close()
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_overlapped_exchange_and_apply_gloo(tmp_path, product):
+    """apply_overlapped over 2 gloo ranks (the device apply replaced by a host
+    stand-in): interior first, halo in flight, then the boundary rows; equal
+    to the whole-grid result, with no NaN from an unreceived halo."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    mp.spawn(_overlap_rank, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        assert (tmp_path / ("ov%d.txt" % r)).read_text() == "ok"
