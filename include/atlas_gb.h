@@ -248,6 +248,17 @@ int atlas_fvm_integral(atlas_fvm_t f, const void* x, int64_t node0, int64_t coun
 /* their absolute values.  worst_closure (may be NULL) receives the        */
 /* largest such ratio.  EINVAL naming the first bad node otherwise.        */
 int atlas_fvm_check(atlas_fvm_t f, double* worst_closure);
+/* Geometry cache.  atlas_fvm_save writes the fvm's host grid, mesh and   */
+/* dual (FP64, bit for bit, with a checksum) to the file path;             */
+/* atlas_fvm_load reads one back as three new handles (grid, mesh, fvm,   */
+/* linked as if built by atlas_grid_* / atlas_mesh_build /                 */
+/* atlas_fvm_build_dual, and destroyed the same way), after the checks of  */
+/* atlas_fvm_check.  EINVAL with the reason for an unreadable, truncated,  */
+/* corrupted or inconsistent file.  Host only.                             */
+int atlas_fvm_save(atlas_fvm_t f, const char* path);
+/* The sphere radius the fvm's dual was built with (metres).               */
+int atlas_fvm_radius(atlas_fvm_t f, double* radius);
+int atlas_fvm_load(const char* path, atlas_grid_t* grid, atlas_mesh_t* mesh, atlas_fvm_t* fvm);
 /* Testing hook: let the next `after` device allocations of the library    */
 /* succeed and fail every one after them (as out of memory) until called   */
 /* again with -1 (the default: never fail).  Calls that need an            */

@@ -195,6 +195,10 @@ class Fvm:
             out["Sb"] = _view(sb, ctypes.c_double, 2 * E, (E, 2))
         return out
 
+    def save(self, path):
+        """Write the host grid, mesh and dual to ``path`` (``load_fvm`` reads it)."""
+        capi.atlas_fvm_save(self.handle, str(path).encode())
+
     def check(self):
         """Consistency check of the host geometry (CSR and closure of every
         dual cell); returns the largest relative closure residual, raises
@@ -413,6 +417,37 @@ def build_fvm(N: int, radius: float = R_EARTH, regular: bool = False) -> Fvm:
     g = Grid(N, regular=regular)
     m = Mesh(g)
     return Fvm(m, radius)
+
+
+def load_fvm(path) -> Fvm:
+    """An Fvm (with its Grid and Mesh) read from a file written by ``Fvm.save``."""
+    hg, hm, hf = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    capi.atlas_fvm_load(str(path).encode(), ctypes.byref(hg), ctypes.byref(hm), ctypes.byref(hf))
+    g = Grid.__new__(Grid)
+    g.handle = hg
+    nn, nl = ctypes.c_int64(), ctypes.c_int()
+    capi.atlas_grid_info(hg, ctypes.byref(nn), ctypes.byref(nl), None, None, None)
+    g.nnodes, g.nlat = nn.value, nl.value
+    proj, nx, ny = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    try:
+        capi.atlas_grid_regional_info(hg, ctypes.byref(proj), ctypes.byref(nx), ctypes.byref(ny), None, None)
+        g.projection = {v: k for k, v in PROJECTIONS.items()}[proj.value]
+        g.nx, g.ny, g.N, g.regular = nx.value, ny.value, 0, False
+    except capi.AtlasError:  # a global grid: O<N> or F<N>
+        g.projection = None
+        g.N = g.nlat // 2
+        g.regular = g.nnodes == 8 * g.N * g.N
+    m = Mesh.__new__(Mesh)
+    m.handle, m.grid = hm, g
+    ne, nt = ctypes.c_int64(), ctypes.c_int64()
+    capi.atlas_mesh_info(hm, ctypes.byref(ne), ctypes.byref(nt), None, None, None, None, None, None)
+    m.nedges, m.ntri = ne.value, nt.value
+    f = Fvm.__new__(Fvm)
+    f.handle, f.mesh, f.grid, f.nnodes = hf, m, g, g.nnodes
+    r = ctypes.c_double()
+    capi.atlas_fvm_radius(hf, ctypes.byref(r))
+    f.R = r.value
+    return f
 
 
 def build_fvm_regional(projection: str, nx: int, ny: int, xmin: float, xmax: float, ymin: float, ymax: float,

@@ -82,6 +82,9 @@ _SIGS = {
     "atlas_part_interior": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)], True),
     "atlas_part_apply_nodes": (I32, [P, I32, P, P, P, P, I64, I64, I32, I64, I32, P], True),
     "atlas_debug_fail_allocations": (I32, [I32], True),
+    "atlas_fvm_save": (I32, [P, ctypes.c_char_p], True),
+    "atlas_fvm_radius": (I32, [P, ctypes.POINTER(ctypes.c_double)], True),
+    "atlas_fvm_load": (I32, [ctypes.c_char_p, PP, PP, PP], True),
     "atlas_fvm_integral": (I32, [P, P, I64, I64, I32, I64, I32, P, P, SZ, P], True),
     "atlas_remap_create": (I32, [P, P, P], True),
     "atlas_remap_info": (I32, [P, P, P, P], True),

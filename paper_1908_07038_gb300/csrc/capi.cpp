@@ -827,6 +827,87 @@ int atlas_fvm_check(atlas_fvm_t h, double* worst_closure) {
   return ok();
 }
 
+int atlas_fvm_radius(atlas_fvm_t h, double* radius) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (!radius) return fail(ATLAS_EINVAL, "radius is NULL");
+  *radius = f->d.R;
+  return ok();
+}
+
+int atlas_fvm_save(atlas_fvm_t h, const char* path) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (!path) return fail(ATLAS_EINVAL, "path is NULL");
+  const char* why = "";
+  try {
+    if (!atlasgb::save_geometry(f->mesh->grid->g, f->mesh->m, f->d, path, &why))
+      return fail(ATLAS_EINVAL, "saving the geometry to %s: %s", path, why);
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "out of host memory saving the geometry");
+  }
+  return ok();
+}
+
+int atlas_fvm_load(const char* path, atlas_grid_t* grid, atlas_mesh_t* mesh, atlas_fvm_t* out) {
+  if (!path || !grid || !mesh || !out) return fail(ATLAS_EINVAL, "NULL argument");
+  *grid = nullptr;
+  *mesh = nullptr;
+  *out = nullptr;
+  atlas_grid_s* g = new (std::nothrow) atlas_grid_s();
+  atlas_mesh_s* m = new (std::nothrow) atlas_mesh_s();
+  atlas_fvm_s* f = new (std::nothrow) atlas_fvm_s();
+  auto drop = [&]() {
+    delete f;
+    delete m;
+    delete g;
+  };
+  if (!g || !m || !f) {
+    drop();
+    return fail(ATLAS_ENOMEM, "out of host memory");
+  }
+  const char* why = "";
+  try {
+    if (!atlasgb::load_geometry(path, g->g, m->m, f->d, &why)) {
+      drop();
+      return fail(ATLAS_EINVAL, "loading the geometry from %s: %s", path, why);
+    }
+    double worst = 0.0;
+    int64_t node = -1;
+    if (!atlasgb::check_geometry(m->m, f->d, 1e-12, worst, node, &why)) {
+      drop();
+      return fail(ATLAS_EINVAL, "the geometry in %s is inconsistent: %s (node %lld)", path, why,
+                  static_cast<long long>(node));
+    }
+  } catch (const std::bad_alloc&) {
+    drop();
+    return fail(ATLAS_ENOMEM, "out of host memory loading the geometry");
+  }
+  for (int op = 0; op < atlasgb::OP_COUNT; ++op)
+    for (int dt = 0; dt < 3; ++dt) f->cfg[op][dt] = default_launch(op, dt);
+  m->grid = g;
+  g->users++;
+  f->mesh = m;
+  m->users++;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) == cudaSuccess && n > 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    f->device = dev;
+    cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  } else {
+    cudaGetLastError();
+    f->device = -1;
+  }
+  reg(g);
+  reg(m);
+  reg(f);
+  *grid = reinterpret_cast<atlas_grid_t>(g);
+  *mesh = reinterpret_cast<atlas_mesh_t>(m);
+  *out = reinterpret_cast<atlas_fvm_t>(f);
+  return ok();
+}
+
 int atlas_debug_fail_allocations(int after) {
   if (after < -1) return fail(ATLAS_EINVAL, "after must be >= -1");
   g_alloc_budget.store(after);

@@ -723,22 +723,33 @@ bool check_geometry(const Mesh& m, const Dual& d, double tol, double& worst, int
   if (static_cast<int64_t>(d.S.size()) != 2 * E || static_cast<int64_t>(d.V.size()) != V ||
       (regional && static_cast<int64_t>(d.Sb.size()) != 2 * E))
     return bad(-1, "dual arrays have the wrong sizes");
-  std::vector<uint8_t> seen(static_cast<size_t>(E), 0);
   for (int64_t e = 0; e < E; ++e) {
     const int32_t a = m.e2n[2 * e], b = m.e2n[2 * e + 1];
     if (a < 0 || b >= V || !(a < b)) return bad(-1, "edge ends out of range or not ordered");
   }
-  for (int64_t i = 0; i < V; ++i) {
+  for (int64_t i = 0; i < V; ++i)
     if (m.n2e_ptr[i + 1] < m.n2e_ptr[i]) return bad(i, "node->edge offsets decrease");
+  // every node's row, in parallel: incidence, signs, closure, volume; the
+  // first failing node (lowest id) is reported
+  std::vector<uint8_t> code(static_cast<size_t>(V), 0);
+  std::vector<double> res(static_cast<size_t>(V), 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < V; ++i) {
     Comp c0, c1;
     double absum = 0.0;
-    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1]; ++q) {
+    uint8_t c = 0;
+    for (int32_t q = m.n2e_ptr[i]; q < m.n2e_ptr[i + 1] && c == 0; ++q) {
       const int32_t e = m.n2e[q];
-      if (e < 0 || e >= E) return bad(i, "edge id out of range");
+      if (e < 0 || e >= E) {
+        c = 1;
+        break;
+      }
       const int32_t a = m.e2n[2 * e], b = m.e2n[2 * e + 1];
       const int s = m.n2e_sign[q];
-      if (!((a == i && s == 1) || (b == i && s == -1))) return bad(i, "edge not incident to its node, or wrong sign");
-      seen[e] = static_cast<uint8_t>(seen[e] + 1);
+      if (!((a == i && s == 1) || (b == i && s == -1))) {
+        c = 2;
+        break;
+      }
       const double sg = m.is_pole[e] ? 1.0 : static_cast<double>(s);
       double nx = sg * d.S[2 * e], ny = sg * d.S[2 * e + 1];
       if (regional) {
@@ -749,10 +760,24 @@ bool check_geometry(const Mesh& m, const Dual& d, double tol, double& worst, int
       c1.add(ny);
       absum += std::fabs(nx) + std::fabs(ny);
     }
-    const double res = (std::fabs(c0.value()) + std::fabs(c1.value())) / (absum > 0 ? absum : 1.0);
-    if (!(res <= worst)) worst = std::isnan(res) ? res : std::max(worst, res);
-    if (!(res <= tol)) return bad(i, "dual cell does not close");
-    if (!(d.V[i] > 0)) return bad(i, "dual volume is not positive");
+    if (c == 0) {
+      const double r = (std::fabs(c0.value()) + std::fabs(c1.value())) / (absum > 0 ? absum : 1.0);
+      res[i] = r;
+      if (!(r <= tol)) c = 3;
+      else if (!(d.V[i] > 0)) c = 4;
+    }
+    code[i] = c;
+  }
+  static const char* const kWhy[5] = {"", "edge id out of range", "edge not incident to its node, or wrong sign",
+                                      "dual cell does not close", "dual volume is not positive"};
+  for (int64_t i = 0; i < V; ++i) {
+    if (!(res[i] <= worst)) worst = std::isnan(res[i]) ? res[i] : std::max(worst, res[i]);
+    if (code[i]) return bad(i, kWhy[code[i]]);
+  }
+  std::vector<uint8_t> seen(static_cast<size_t>(E), 0);
+  for (int64_t q = 0; q < 2 * E; ++q) {
+    const int32_t e = m.n2e[q];
+    seen[e] = static_cast<uint8_t>(seen[e] < 3 ? seen[e] + 1 : 3);
   }
   for (int64_t e = 0; e < E; ++e)
     if (seen[e] != 2) return bad(-1, "an edge does not appear exactly twice in the node->edge rows");

@@ -154,6 +154,12 @@ bool build_regional_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
 // node (or -1) and a reason; worst is the largest relative closure residual.
 bool check_geometry(const Mesh& m, const Dual& d, double tol, double& worst, int64_t& bad_node, const char** why);
 
+// Geometry cache (geomio.cpp): the grid, mesh and dual written to a file and
+// read back bit for bit (with a checksum).  load_geometry points m.grid at g;
+// its caller then runs check_geometry.
+bool save_geometry(const Grid& g, const Mesh& m, const Dual& d, const char* path, const char** why);
+bool load_geometry(const char* path, Grid& g, Mesh& m, Dual& d, const char** why);
+
 // Generic table algebra for difference-form stencils with symmetric 1-ring
 // sparsity: the transpose (an adjoint) and the product L = D G of a
 // two-input divergence-like table with a one-input, two-output
