@@ -10,6 +10,8 @@
  *   - the divergence of the zonal flow (u, v) = (cos lat, 0) is exactly 0
  *     (its flux through every face cancels; see the oracle's pins);
  *   - sum_i V_i curl_i of random-like (u, v) vanishes to rounding.
+ * Before the device part it exercises host-only calls: a regional grid with
+ * its geometry check, and the geometry cache (argv[2] names the file).
  * Exit code 0 when every check passes, 2 when no device is present and the
  * library says so (ATLAS_ECUDA), 1 otherwise.
  */
@@ -45,6 +47,39 @@ int main(int argc, char** argv) {
   const double *lonlat, *vol;
   CHECK(atlas_grid_info(g, &V, NULL, NULL, &lonlat, NULL));
   CHECK(atlas_fvm_info(f, &vol, NULL, NULL, NULL));
+
+  /* host-only calls (no device needed): a Lambert regional grid and its
+   * geometry check, and the geometry cache round trip */
+  {
+    const double prm[8] = {-1.0e6, 1.0e6, -8.0e5, 9.0e5, 6371220.0, 5.0, 50.0, 0.0};
+    atlas_grid_t rg;
+    atlas_mesh_t rm;
+    atlas_fvm_t rf, lf;
+    atlas_grid_t lg;
+    atlas_mesh_t lm;
+    double worst = -1.0, R = 0.0;
+    int64_t rV = 0, lV = 0;
+    CHECK(atlas_grid_regional(ATLAS_PROJ_LAMBERT_CONFORMAL, 13, 9, prm, &rg));
+    CHECK(atlas_mesh_build(rg, &rm));
+    CHECK(atlas_fvm_build_dual(rm, 6371220.0, &rf));
+    CHECK(atlas_fvm_check(rf, &worst));
+    CHECK(atlas_grid_info(rg, &rV, NULL, NULL, NULL, NULL));
+    const char* path = argc > 2 ? argv[2] : "c_api_example.geom";
+    CHECK(atlas_fvm_save(rf, path));
+    CHECK(atlas_fvm_load(path, &lg, &lm, &lf));
+    CHECK(atlas_grid_info(lg, &lV, NULL, NULL, NULL, NULL));
+    CHECK(atlas_fvm_radius(lf, &R));
+    printf("regional 13 x 9: %lld nodes, closure %.1e; reloaded %lld nodes, R %.0f\n", (long long)rV, worst,
+           (long long)lV, R);
+    if (lV != rV || R != 6371220.0 || !(worst <= 1e-14)) return 1;
+    atlas_fvm_destroy(lf);
+    atlas_mesh_destroy(lm);
+    atlas_grid_destroy(lg);
+    atlas_fvm_destroy(rf);
+    atlas_mesh_destroy(rm);
+    atlas_grid_destroy(rg);
+    remove(path);
+  }
 
   const size_t bytes = (size_t)V * ld * sizeof(float);
   float* h = (float*)malloc(3 * bytes);

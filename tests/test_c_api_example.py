@@ -50,9 +50,10 @@ def _has_gpu():
 def test_c_program_without_a_gpu_gets_ecuda(example):
     if _has_gpu():
         pytest.skip("a GPU is present (the GPU test runs the program)")
-    p = subprocess.run([example, "8"], capture_output=True, text=True, timeout=120)
+    p = subprocess.run([example, "8", example + ".geom"], capture_output=True, text=True, timeout=120)
     assert p.returncode == 2, p.stdout + p.stderr
     assert "returned -3" in p.stdout
+    assert "regional 13 x 9: 117 nodes" in p.stdout and "reloaded 117 nodes" in p.stdout
 
 
 @pytest.mark.gpu
@@ -60,6 +61,6 @@ def test_c_program_on_the_gpu(example):
     if not _has_gpu():
         pytest.skip("no CUDA device")
     for N in ("16", "80"):
-        p = subprocess.run([example, N], capture_output=True, text=True, timeout=300)
+        p = subprocess.run([example, N, example + ".geom"], capture_output=True, text=True, timeout=300)
         assert p.returncode == 0, p.stdout + p.stderr
         assert "exactly 0" in p.stdout and p.stdout.rstrip().endswith("ok")
