@@ -139,3 +139,23 @@ def test_edge_variant_refuses_regional_before_any_pointer_use(atlas, product):
         with pytest.raises(capi.AtlasError) as ei:
             fn(fvm.handle, *args, fake[3], 1 << 20, 4, 4, capi.ATLAS_F32, None)
         assert ei.value.code == -1 and "global" in str(ei.value)
+
+
+@pytest.mark.parametrize("name", ["mercator", "lambert", "lambert_south"])
+def test_laplacian_table_is_zero_on_plane_linear_fields(atlas, name):
+    """The library's composed two-ring Laplacian table (FP64, applied in
+    numpy) annihilates fields linear in a conformal projection's plane at
+    every node, boundary included (they are harmonic there)."""
+    proj, kw = DOMAINS[name]
+    fvm = atlas.build_fvm_regional(proj, 19, 14, **kw)
+    g = fvm.grid.arrays()
+    x, y = g["xy"][:, 0], g["xy"][:, 1]
+    f = 0.8 * x - 1.7 * y + 2.0
+    t = fvm.stencil_table("laplacian")
+    V = fvm.nnodes
+    rows = np.repeat(np.arange(V), np.diff(t["ptr"]))
+    lap = np.zeros(V)
+    np.add.at(lap, rows, t["w"][:, 0] * (f[t["nbr"]] - f[rows]))
+    gx = _apply(fvm.stencil_table("gradient"), [f[:, None]])[0][:, 0]
+    scale = np.max(np.abs(gx)) / np.min(np.sqrt(fvm.arrays()["area"]))
+    assert np.max(np.abs(lap)) <= 1e-12 * scale
