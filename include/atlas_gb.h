@@ -97,7 +97,8 @@ enum {
 enum {
   ATLAS_PROJ_ROTATED_LONLAT = 0,
   ATLAS_PROJ_MERCATOR = 1,
-  ATLAS_PROJ_LAMBERT_CONFORMAL = 2
+  ATLAS_PROJ_LAMBERT_CONFORMAL = 2,
+  ATLAS_PROJ_POLAR_STEREOGRAPHIC = 3
 };
 
 /* ---------------------------------------------------------------------- */
@@ -153,6 +154,10 @@ int atlas_grid_regular_gaussian(int N, atlas_grid_t* out);
 /*     radius, p5 = central longitude, p6 = tangent latitude (degrees,     */
 /*     0 < |p6| < 90); the domain must not hold the pole or cross the cut  */
 /*     opposite the central longitude.                                     */
+/*   ATLAS_PROJ_POLAR_STEREOGRAPHIC: plane tangent at the pole p6 = 90 or   */
+/*     -90, projected from the opposite pole; x, y in metres; p4 = radius, */
+/*     p5 = the longitude along -y from the north pole (+y from the south  */
+/*     pole); the domain may hold its pole.                                */
 /* Every point must stay more than about 0.06 degrees from a pole of the  */
 /* projection.  EINVAL (with the reason in atlas_last_error) otherwise.    */
 /* atlas_grid_info then reports nlat = ny rows of nx points and lat[r] =   */
@@ -162,7 +167,7 @@ int atlas_grid_regional(int projection, int nx, int ny, const double* params, at
 /* coordinates xy[nnodes][2] on the unit sphere (radians, or metres over   */
 /* the projection radius) and the scale factors scale[nnodes][2] = (h_x,   */
 /* h_y): a plane step dx is a true distance R h_x dx on a sphere of radius */
-/* R (rotated lon-lat: (cos y, 1); Mercator, Lambert: 1/m, the inverse map */
+/* R (rotated lon-lat: (cos y, 1); conformal projections: 1/m, the inverse map */
 /* factor, in both directions).                                            */
 int atlas_grid_regional_info(atlas_grid_t g, int* projection, int* nx, int* ny, const double** xy,
                              const double** scale);

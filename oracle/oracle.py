@@ -313,7 +313,7 @@ class Mesh:
         return rows, cols, vals
 
 
-PROJECTIONS = {"rotated_lonlat": 0, "mercator": 1, "lambert_conformal": 2}
+PROJECTIONS = {"rotated_lonlat": 0, "mercator": 1, "lambert_conformal": 2, "polar_stereographic": 3}
 
 
 class RegionalMesh:

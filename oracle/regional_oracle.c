@@ -24,7 +24,9 @@
  *      rho = sgn(n) sqrt(x^2 + (rho0 - y)^2), theta = atan2(sgn(n) x, sgn(n)(rho0 - y)),
  *      lat = 2 atan((F/rho)^(1/n)) - pi/2, lon = lon0 + theta/n; the scale
  *      factor k = cos lat1 tan^n(pi/4+lat1/2) / (cos lat tan^n(pi/4+lat/2)),
- *      h = 1/k.
+ *      h = 1/k;
+ *    - polar stereographic (Snyder 1987, ch. 21, spherical form, tangent at
+ *      the pole): see reg_inverse.
  *  Mesh.  Each quad (r, j) is cut along its diagonal (r, j)-(r+1, j+1).  An
  *   edge lies on the domain boundary when both its ends lie on the same side
  *   of the rectangle.
@@ -118,6 +120,19 @@ static int reg_inverse(int proj, const double *p, double x, double y, double *lo
     *hx = *hy = cos(*lat);
     return 0;
   }
+  if (proj == 3) {
+    /* polar stereographic from the opposite pole onto the plane tangent at
+     * the pole p[6] = +-90: rho = sqrt(x^2 + y^2), sin|lat| =
+     * (4 - rho^2)/(4 + rho^2), cos lat = 4 rho/(4 + rho^2), the meridian lon0
+     * along -y from the north pole (+y from the south pole), scale factor
+     * h = 4/(4 + rho^2) */
+    double north = p[6] > 0 ? 1.0 : -1.0;
+    double r2 = x * x + y * y;
+    *lat = north * atan2(4.0 - r2, 4.0 * sqrt(r2));
+    *lon = p[5] * RPI / 180.0 + atan2(x, -north * y);
+    *hx = *hy = 4.0 / (4.0 + r2);
+    return 0;
+  }
   if (proj == 2) {
     double lat1 = p[6] * RPI / 180.0, n = sin(lat1);
     double t1 = tan(0.25 * RPI + 0.5 * lat1);
@@ -143,7 +158,7 @@ static int on_boundary_edge(const orc_reg *g, int32_t a, int32_t b) {
 }
 
 orc_reg *orc_reg_build(int proj, int nx, int ny, const double *prm, double R) {
-  if (nx < 2 || ny < 2 || proj < 0 || proj > 2 || !(R > 0)) return NULL;
+  if (nx < 2 || ny < 2 || proj < 0 || proj > 3 || !(R > 0)) return NULL;
   orc_reg *g = (orc_reg *)calloc(1, sizeof(orc_reg));
   if (!g) return NULL;
   g->proj = proj; g->nx = nx; g->ny = ny; g->R = R;

@@ -22,7 +22,8 @@ from .capi import ATLAS_BF16, ATLAS_F32, ATLAS_F64
 R_EARTH = 6371220.0
 
 PROJECTIONS = {"rotated_lonlat": capi.ATLAS_PROJ_ROTATED_LONLAT, "mercator": capi.ATLAS_PROJ_MERCATOR,
-               "lambert_conformal": capi.ATLAS_PROJ_LAMBERT_CONFORMAL}
+               "lambert_conformal": capi.ATLAS_PROJ_LAMBERT_CONFORMAL,
+               "polar_stereographic": capi.ATLAS_PROJ_POLAR_STEREOGRAPHIC}
 
 OPS = {"gradient": capi.ATLAS_OP_GRADIENT, "divergence": capi.ATLAS_OP_DIVERGENCE,
        "gradient_adjoint": capi.ATLAS_OP_GRADIENT_ADJOINT,
@@ -66,8 +67,10 @@ class Grid:
         with nx points per row and ny rows.  ``projection`` is
         "rotated_lonlat" (x, y in rotated degrees; ``south_pole`` = the
         rotated south pole's (lon, lat) in degrees), "mercator" (x, y in
-        metres on a sphere of ``radius``, central longitude ``lon0``) or
-        "lambert_conformal" (the same plus the tangent latitude ``lat0``)."""
+        metres on a sphere of ``radius``, central longitude ``lon0``),
+        "lambert_conformal" (the same plus the tangent latitude ``lat0``) or
+        "polar_stereographic" (the same, tangent at the pole ``lat0`` = 90
+        or -90)."""
         code = PROJECTIONS[projection]
         if code == capi.ATLAS_PROJ_ROTATED_LONLAT:
             tail = (float(south_pole[0]), float(south_pole[1]), 0.0, 0.0)

@@ -20,6 +20,7 @@ ATLAS_OP_GRADIENT, ATLAS_OP_DIVERGENCE, ATLAS_OP_GRADIENT_ADJOINT = 0, 1, 2
 ATLAS_OP_DIVERGENCE_ADJOINT, ATLAS_OP_LAPLACIAN = 3, 4
 ATLAS_OP_CURL, ATLAS_OP_VECTOR_GRADIENT = 5, 6
 ATLAS_PROJ_ROTATED_LONLAT, ATLAS_PROJ_MERCATOR, ATLAS_PROJ_LAMBERT_CONFORMAL = 0, 1, 2
+ATLAS_PROJ_POLAR_STEREOGRAPHIC = 3
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EALIGN", -5: "EDTYPE", -6: "ESTATE"}
 
 

@@ -642,7 +642,7 @@ int atlas_grid_regional(int projection, int nx, int ny, const double* params, at
   CallRange range_("atlas_grid_regional");
   if (!out) return fail(ATLAS_EINVAL, "out is NULL");
   *out = nullptr;
-  if (projection < ATLAS_PROJ_ROTATED_LONLAT || projection > ATLAS_PROJ_LAMBERT_CONFORMAL)
+  if (projection < ATLAS_PROJ_ROTATED_LONLAT || projection > ATLAS_PROJ_POLAR_STEREOGRAPHIC)
     return fail(ATLAS_EINVAL, "unknown projection %d", projection);
   atlas_grid_s* g = new (std::nothrow) atlas_grid_s();
   if (!g) return fail(ATLAS_ENOMEM, "out of host memory");

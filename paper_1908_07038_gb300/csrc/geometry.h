@@ -137,7 +137,8 @@ bool build_remap(const Mesh& m, const double* tgt_lonlat, int64_t ntgt, std::vec
 enum RegionalProjection {
   PROJ_ROTATED_LONLAT = 0,  // x, y = rotated longitude, latitude (degrees)
   PROJ_MERCATOR = 1,        // x, y in metres on a sphere of radius p[4]
-  PROJ_LAMBERT_CONFORMAL = 2  // tangent cone, x, y in metres
+  PROJ_LAMBERT_CONFORMAL = 2,  // tangent cone, x, y in metres
+  PROJ_POLAR_STEREOGRAPHIC = 3  // tangent at a pole, x, y in metres
 };
 // params: {xmin, xmax, ymin, ymax, p4, p5, p6, p7} as documented in atlas_gb.h.
 // Returns false with a reason in why on an invalid domain.

@@ -82,6 +82,17 @@ bool inverse(const Proj& p, double x, double y, double& lon, double& lat, double
     hx = hy = 1.0 / std::cosh(y);
     return std::fabs(y) <= 7.0;
   }
+  if (p.kind == PROJ_POLAR_STEREOGRAPHIC) {
+    // tangent plane at the pole (p.n = +1 north, -1 south), projected from
+    // the opposite pole: rho = 2 tan(pi/4 - |lat|/2), the central meridian
+    // lon0 pointing to -y from the north pole (+y from the south pole)
+    const double rho = std::hypot(x, y);
+    const double c = 2.0 * std::atan(0.5 * rho);  // angular distance from the pole
+    lat = p.n * (0.5 * kPi - c);
+    lon = p.lon0 + std::atan2(x, -p.n * y);
+    hx = hy = std::cos(0.5 * c) * std::cos(0.5 * c);  // 1/k, k = 2/(1 + sin|lat|)
+    return std::cos(c) > -1.0 + 1e-6;
+  }
   // Lambert conformal conic, tangent at lat0: rho = F / tan(pi/4 + lat/2)^n,
   // x = rho sin(theta), y = rho0 - rho cos(theta), theta = n (lon - lon0)
   const double s = p.n > 0 ? 1.0 : -1.0;
@@ -122,6 +133,13 @@ bool build_regional_grid(int projection, int nx, int ny, const double* prm, Grid
     p.e2[1] = p.e3[2] * p.e1[0] - p.e3[0] * p.e1[2];
     p.e2[2] = p.e3[0] * p.e1[1] - p.e3[1] * p.e1[0];
     scale = 1.0 / kDeg;
+  } else if (projection == PROJ_POLAR_STEREOGRAPHIC) {
+    const double radius = prm[4];
+    if (!(radius > 0) || !std::isfinite(radius)) return bad("the projection radius must be positive");
+    if (prm[6] != 90.0 && prm[6] != -90.0) return bad("the polar stereographic pole latitude must be 90 or -90");
+    scale = radius;
+    p.lon0 = prm[5] * kDeg;
+    p.n = prm[6] > 0 ? 1.0 : -1.0;
   } else if (projection == PROJ_MERCATOR || projection == PROJ_LAMBERT_CONFORMAL) {
     const double radius = prm[4];
     if (!(radius > 0) || !std::isfinite(radius)) return bad("the projection radius must be positive");

@@ -10,6 +10,7 @@ DOMAINS = {
     "lambert": ("lambert_conformal", dict(xmin=-1.0e6, xmax=1.0e6, ymin=-8.0e5, ymax=9.0e5, lat0=50.0, lon0=5.0)),
     "lambert_south": ("lambert_conformal",
                       dict(xmin=-1.2e6, xmax=9.0e5, ymin=-7.0e5, ymax=1.1e6, lat0=-35.0, lon0=140.0)),
+    "polar": ("polar_stereographic", dict(xmin=-1.6e6, xmax=1.4e6, ymin=-1.5e6, ymax=1.5e6, lat0=90.0, lon0=-45.0)),
 }
 
 # a convection-permitting limited-area configuration: 1536 x 1440 points at

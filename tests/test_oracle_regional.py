@@ -73,7 +73,7 @@ def test_rotated_lonlat_against_great_circle_distances():
     assert np.max(np.abs(plain["hx"] - np.cos(plain["y"]))) == 0.0
 
 
-@pytest.mark.parametrize("name", ["rotated", "mercator", "lambert", "lambert_south"])
+@pytest.mark.parametrize("name", ["rotated", "mercator", "lambert", "lambert_south", "polar"])
 def test_scale_factors_and_orthogonality_from_chords(name):
     """Tiny steps: the true distance of a plane step dx is h dx (unit
     sphere), equal in both directions for a conformal projection, and the
@@ -111,6 +111,16 @@ def test_known_points():
     c = 12  # the plane origin is (lon0, lat0), where the cone touches: scale 1
     assert abs(g["lon"][c] - np.radians(5.0)) <= 1e-15 and abs(g["lat"][c] - np.radians(50.0)) <= 1e-15
     assert abs(g["hx"][c] - 1.0) <= 1e-15
+    for pole in (90.0, -90.0):
+        g = _mesh("polar", 5, 5, xmin=-1e5, xmax=1e5, ymin=-1e5, ymax=1e5, lat0=pole).geometry()
+        c = 12  # the plane origin is the pole, where the plane touches: scale 1
+        assert abs(g["lat"][c] - np.radians(pole)) <= 1e-15 and abs(g["hx"][c] - 1.0) <= 1e-15
+        # the central meridian leaves the north pole along -y (the south pole along +y)
+        below = 22 if pole > 0 else 2
+        assert abs(g["lon"][below] - np.radians(-45.0)) <= 1e-15
+        # a point of the plane at distance rho lies at colatitude 2 atan(rho / 2R)
+        rho = np.hypot(g["x"], g["y"])
+        assert np.max(np.abs((np.pi / 2 - np.abs(g["lat"])) - 2 * np.arctan(rho / 2))) <= 1e-15
 
 
 @pytest.mark.parametrize("name", ["rotated", "lambert"])
@@ -261,7 +271,7 @@ def test_closure_exact_and_averaged_forms_agree():
         assert np.all(np.abs(d[:, 0]) <= bound)
 
 
-@pytest.mark.parametrize("name", ["mercator", "lambert", "lambert_south"])
+@pytest.mark.parametrize("name", ["mercator", "lambert", "lambert_south", "polar"])
 def test_plane_linear_fields_are_harmonic_on_conformal_grids(name):
     """On a conformal projection (h_x = h_y = h) a field linear in the plane
     is harmonic: the exact gradient (a, b)/(R h) makes h_y g_x and h_x g_y
