@@ -256,3 +256,21 @@ def test_overlapped_exchange_and_apply_gloo(tmp_path, product):
     mp.spawn(_overlap_rank, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     for r in range(2):
         assert (tmp_path / ("ov%d.txt" % r)).read_text() == "ok"
+
+
+def test_apply_nodes_range_errors(pfvm, part_mod, product):
+    """apply_nodes refuses ranges outside the part's own nodes before it
+    touches any pointer (host-side check, no GPU needed)."""
+    capi = product[1]
+    fvm = pfvm(16)
+    p = part_mod.Partition(fvm, 3, 1, 1)
+    fake = 0x100000
+    for node0, count in [(p.own0 - 1, 5), (p.own1 - 2, 5), (p.own0, -1)]:
+        with pytest.raises(capi.AtlasError) as ei:
+            capi.atlas_part_apply_nodes(p.handle, capi.ATLAS_OP_GRADIENT, fake, None, fake, fake, node0, count,
+                                        4, 4, capi.ATLAS_F32, None)
+        assert ei.value.code == -1
+    with pytest.raises(capi.AtlasError):  # the Laplacian needs two halo rows
+        capi.atlas_part_apply_nodes(p.handle, capi.ATLAS_OP_LAPLACIAN, fake, None, fake, None, p.own0, 1,
+                                    4, 4, capi.ATLAS_F32, None)
+    p.close()

@@ -99,6 +99,7 @@ def test_refusals(atlas, product):
         ("lambert_conformal", 5, 5, dict(xmin=-1e6, xmax=1e6, ymin=0.0, ymax=8e6, lat0=50.0)),  # holds the pole
         ("mercator", 5, 5, dict(xmin=-1e5, xmax=1e5, ymin=0.0, ymax=6e7)),
         ("mercator", 5, 5, dict(xmin=-1e5, xmax=1e5, ymin=-1e5, ymax=1e5, radius=-1.0)),
+        ("polar_stereographic", 5, 5, dict(xmin=-1e5, xmax=1e5, ymin=-1e5, ymax=1e5, lat0=60.0)),  # not a pole
     ]
     for proj, nx, ny, kw in bad:
         with pytest.raises(capi.AtlasError) as ei:
