@@ -45,61 +45,65 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    lib.orc_build.restype = P
+    lib.orc_build.argtypes = [ctypes.c_int, ctypes.c_double]
+    lib.orc_build_grid.restype = P
+    lib.orc_build_grid.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.orc_free.argtypes = [P]
+    lib.orc_counts.argtypes = [P, P]
+    lib.orc_gauss_colatitudes.argtypes = [ctypes.c_int, P]
+    lib.orc_get_grid.argtypes = [P, P, P, P, P]
+    lib.orc_get_mesh.argtypes = [P] * 9
+    lib.orc_get_dual.argtypes = [P] * 5
+    lib.orc_gradient.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+    lib.orc_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+    lib.orc_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_remap.argtypes = [P, P, i64, P, P]
+    lib.orc_remap_apply.argtypes = [P, P, i64, P, ctypes.c_int, i64, ctypes.c_int, P]
+    lib.orc_vector_gradient.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P, P, P]
+    lib.orc_gradient_triplets.restype = i64
+    lib.orc_gradient_triplets.argtypes = [P, P, P, P]
+    lib.orc_divergence_triplets.restype = i64
+    lib.orc_divergence_triplets.argtypes = [P, P, P, P]
+    lib.orc_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
+    lib.orc_closure.argtypes = [P, P, P]
+    lib.orc_reg_build.restype = P
+    lib.orc_reg_build.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_double]
+    lib.orc_reg_free.argtypes = [P]
+    lib.orc_reg_counts.argtypes = [P, P]
+    lib.orc_reg_get.argtypes = [P] * 6
+    lib.orc_reg_closure.argtypes = [P, P, P]
+    lib.orc_reg_gradient.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+    lib.orc_reg_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_reg_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_reg_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_reg_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_reg_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
+    lib.orc_reg_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
+    for name in ("orc_reg_gradient", "orc_reg_divergence", "orc_reg_curl", "orc_reg_laplacian",
+                 "orc_reg_gradient_adjoint", "orc_reg_divergence_adjoint", "orc_reg_gradient_averaged"):
+        getattr(lib, name).restype = ctypes.c_int
+    for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
+                 "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
+                 "orc_vector_gradient", "orc_remap", "orc_remap_apply"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
-        P = ctypes.c_void_p
-        i64 = ctypes.c_int64
-        lib.orc_build.restype = P
-        lib.orc_build.argtypes = [ctypes.c_int, ctypes.c_double]
-        lib.orc_build_grid.restype = P
-        lib.orc_build_grid.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int]
-        lib.orc_free.argtypes = [P]
-        lib.orc_counts.argtypes = [P, P]
-        lib.orc_gauss_colatitudes.argtypes = [ctypes.c_int, P]
-        lib.orc_get_grid.argtypes = [P, P, P, P, P]
-        lib.orc_get_mesh.argtypes = [P] * 9
-        lib.orc_get_dual.argtypes = [P] * 5
-        lib.orc_gradient.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
-        lib.orc_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
-        lib.orc_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_remap.argtypes = [P, P, i64, P, P]
-        lib.orc_remap_apply.argtypes = [P, P, i64, P, ctypes.c_int, i64, ctypes.c_int, P]
-        lib.orc_vector_gradient.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P, P, P]
-        lib.orc_gradient_triplets.restype = i64
-        lib.orc_gradient_triplets.argtypes = [P, P, P, P]
-        lib.orc_divergence_triplets.restype = i64
-        lib.orc_divergence_triplets.argtypes = [P, P, P, P]
-        lib.orc_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
-        lib.orc_closure.argtypes = [P, P, P]
-        lib.orc_reg_build.restype = P
-        lib.orc_reg_build.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_double]
-        lib.orc_reg_free.argtypes = [P]
-        lib.orc_reg_counts.argtypes = [P, P]
-        lib.orc_reg_get.argtypes = [P] * 6
-        lib.orc_reg_closure.argtypes = [P, P, P]
-        lib.orc_reg_gradient.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
-        lib.orc_reg_divergence.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_reg_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_reg_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_reg_gradient_adjoint.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
-        lib.orc_reg_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
-        lib.orc_reg_gradient_averaged.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, P]
-        for name in ("orc_reg_gradient", "orc_reg_divergence", "orc_reg_curl", "orc_reg_laplacian",
-                     "orc_reg_gradient_adjoint", "orc_reg_divergence_adjoint", "orc_reg_gradient_averaged"):
-            getattr(lib, name).restype = ctypes.c_int
-        for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
-                     "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
-                     "orc_vector_gradient", "orc_remap", "orc_remap_apply"):
-            getattr(lib, name).restype = ctypes.c_int
-        _lib = lib
-        return lib
+        _lib = _configure(ctypes.CDLL(build()))
+        return _lib
 
 
 def _ptr(a):
