@@ -9,8 +9,6 @@ repository root; it imports nothing but ``oracle``.
 import os
 import sys
 
-import numpy as np
-
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle.oracle import Mesh  # noqa: E402

@@ -102,7 +102,7 @@ def test_curl_of_gradient_field_converges_to_zero(omesh):
     errs = []
     for N in (16, 32, 64):
         m = omesh(N)
-        lam, phi, V, _ = _geo(m)
+        lam, phi, _, _ = _geo(m)
         z = m.curl(-np.sin(lam)[:, None], (-np.sin(phi) * np.cos(lam))[:, None])[:, 0] * R
         errs.append(np.max(np.abs(z[np.abs(phi) < np.radians(60)])))
     assert errs[0] > errs[1] > errs[2] and errs[2] < 0.01, errs
@@ -152,7 +152,7 @@ def test_vector_gradient_reverses_the_antipode_on_pole_faces(omesh):
     are the same arithmetic, bitwise."""
     for N in (16, 32):
         m = omesh(N)
-        lam, phi, V, pl = _geo(m)
+        lam, phi, _, pl = _geo(m)
         u = (-np.sin(lam))[:, None]
         v = (-np.sin(phi) * np.cos(lam))[:, None]
         ux, uy, vx, vy = m.vector_gradient(u, v)

@@ -95,7 +95,7 @@ def test_level_shards(part_mod):
     for nlev, n in ((137, 2), (137, 3), (137, 8), (5, 4), (1, 1)):
         sh = part_mod.level_shards(nlev, n)
         assert sh[0][0] == 0 and sh[-1][1] == nlev and len(sh) == n
-        for (a, b), (c, d) in zip(sh, sh[1:]):
+        for (_, b), (c, _) in zip(sh, sh[1:]):
             assert b == c
         for a, b in sh:
             assert a % 4 == 0 and a <= b
