@@ -20,6 +20,7 @@ namespace {
 
 constexpr char kMagic[8] = {'A', 'T', 'L', 'G', 'E', 'O', 'M', '1'};
 constexpr uint32_t kVersion = 1;
+constexpr uint64_t kFnvOffset = 1469598103934665603ull;
 
 // FNV-1a over the 64-bit little-endian words of each written piece, then
 // its remaining bytes (the pieces are the same when reading back)
@@ -37,7 +38,7 @@ uint64_t mix(uint64_t h, const void* p, size_t n) {
 
 struct Writer {
   FILE* f;
-  uint64_t h = 1469598103934665603ull;
+  uint64_t h = kFnvOffset;
   bool ok = true;
   void raw(const void* p, size_t n) {
     if (!ok || n == 0) return;
@@ -55,7 +56,7 @@ struct Writer {
 
 struct Reader {
   FILE* f;
-  uint64_t h = 1469598103934665603ull;
+  uint64_t h = kFnvOffset;
   uint64_t left;  // bytes of the file not read yet
   bool ok = true;
   void raw(void* p, size_t n) {
@@ -151,8 +152,8 @@ bool load_geometry(const char* path, Grid& g, Mesh& m, Dual& d, const char** why
     std::fclose(f);
     return bad("not a geometry file (too short)");
   }
-  Reader r{f};
-  r.left = static_cast<uint64_t>(size) - sizeof(uint64_t);  // the trailing hash is read apart
+  // the trailing hash is read apart
+  Reader r{f, kFnvOffset, static_cast<uint64_t>(size) - sizeof(uint64_t)};
   char magic[8];
   r.raw(magic, sizeof(magic));
   const uint32_t version = r.scalar<uint32_t>();
