@@ -51,6 +51,11 @@
  *     additionally need 16-byte aligned rows (ld a multiple of 16/sizeof),
  *     and fall back to element-wise loads otherwise.
  *   - Input and output fields of one call must not overlap.
+ *   - Calls may come from several host threads at once.  Builds of distinct
+ *     objects run concurrently; the tables that one fvm (or remap) builds on
+ *     first use are built once, under that object's lock, whichever thread
+ *     asks first.  A handle must not be destroyed while another thread is
+ *     still inside a call that uses it.
  *   - No call ever computes on the CPU: without a CUDA device every operator
  *     call fails with ATLAS_ECUDA.
  */
