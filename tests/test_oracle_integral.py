@@ -39,3 +39,25 @@ def test_sphere_area_and_odd_field(omesh):
     assert abs(I[0] - area) <= 1e-12 * area
     # sin(lat) is odd under the north-south mirror, which maps the grid onto itself
     assert abs(I[1]) <= 1e-13 * area
+
+
+def test_residual_after_cancelling_the_rounded_sum():
+    """Each level holds random products plus one term that cancels their
+    correctly rounded sum, so the exact result is the few-ulp residual that
+    rounding left: it survives only if every product is exact and the whole
+    sum is rounded once.  A naive sum, a product rounded to FP64, or a
+    dropped partial product of the splitting each give a different value."""
+    rng = np.random.default_rng(7)
+    n, nlev = 300, 6
+    V = np.concatenate([rng.uniform(0.5, 2.0, n) * 2.0 ** rng.integers(-20, 20, n), [1.0]])
+    x = np.empty((n + 1, nlev))
+    want = []
+    for k in range(nlev):
+        x[:n, k] = rng.standard_normal(n) * 2.0 ** rng.integers(-20, 20, n)
+        terms = [Fraction(float(a)) * Fraction(float(b)) for a, b in zip(V[:n], x[:n, k])]
+        s = float(sum(terms))
+        x[n, k] = -s
+        rest = sum(terms) - Fraction(s)
+        assert rest != 0  # the rounded sum is inexact, so a residual is left
+        want.append(float(rest))
+    assert list(oracle.integral(V, x)) == want

@@ -1,10 +1,13 @@
 """The oracle's pins catch plausible mistakes: each case plants one bug in a
 copy of the oracle's C source (a wrong tie rule, a dropped metric factor, a
-sign, a formula), builds it, and checks that a named pin passes on the real
-oracle and fails on the mutant.  Mutants are built in a temporary directory
-and used only inside their test; the oracle itself is never changed."""
+sign, a formula) or in one function of its Python module, builds it, and
+checks that a named pin passes on the real oracle and fails on the mutant.
+Mutants are built in a temporary directory (C) or a private namespace
+(Python) and used only inside their test; the oracle itself is never
+changed.  Several pins are the oracle's own tests, called directly."""
 import contextlib
 import ctypes
+import inspect
 import os
 import subprocess
 
@@ -14,6 +17,12 @@ import pytest
 from oracle import oracle
 from test_oracle_dual import _dual_by_quadrature
 from test_oracle_grid import _zipper_bruteforce
+from test_oracle_grid import test_latitudes_match_legendre_roots as _latitudes_test
+from test_oracle_integral import test_exact_against_fractions as _fractions_test
+from test_oracle_integral import test_residual_after_cancelling_the_rounded_sum as _residual_test
+from test_oracle_remap import test_weights_are_barycentric_coordinates_of_the_ray_crossing as _barycentric_test
+from test_oracle_vector_ops import test_curl_of_solid_body_rotation as _curl_test
+from test_oracle_vector_ops import test_vector_gradient_reverses_the_antipode_on_pole_faces as _antipode_test
 from synthetic.regional import DOMAINS
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -126,6 +135,39 @@ def pin_rotated_pole_distance():
     return np.max(np.abs(ang - (np.pi / 2 - g["y"]))) <= 1e-12
 
 
+def _meshes(N):
+    return oracle.Mesh(N, R)
+
+
+def _passes(test, *args):
+    """A test of the oracle used as a pin: True when its assertions hold."""
+    try:
+        test(*args)
+    except AssertionError:
+        return False
+    return True
+
+
+def pin_latitudes():
+    return _passes(_latitudes_test, oracle, 64)
+
+
+def pin_barycentric():
+    return _passes(_barycentric_test, _meshes, 16, 8)
+
+
+def pin_curl_solid_body():
+    return _passes(_curl_test, _meshes, 0.0)
+
+
+def pin_antipode():
+    return _passes(_antipode_test, _meshes)
+
+
+def pin_exact_sums():
+    return _passes(_fractions_test) and _passes(_residual_test)
+
+
 MUTANTS = [
     ("tie rule reversed", "global", "else north = (n1 <= n2);", "else north = (n1 > n2);", pin_zipper),
     ("pole faces signed like regular faces", "global",
@@ -162,6 +204,26 @@ MUTANTS = [
      pin_lambert_scale_from_chords),
     ("rotated frame turned the wrong way", "regional", "double b = -(0.5 * RPI + pp);",
      "double b = (0.5 * RPI + pp);", pin_rotated_pole_distance),
+    ("Legendre series coefficients g_k g_k instead of g_k g_(n-k)", "global", "c[k] = g[k] * g[n - k];",
+     "c[k] = g[k] * g[k];", pin_latitudes),
+    ("remap weights given to the wrong vertices", "global", "bw[0] = w0; bw[1] = u; bw[2] = v;",
+     "bw[0] = u; bw[1] = w0; bw[2] = v;", pin_barycentric),
+    ("remap accepts the triangle on the far side of the sphere", "global",
+     "if (tt <= 0) continue; /* the far side of the sphere */", "(void)tt;", pin_barycentric),
+    ("curl with the sign of the (u cos) term flipped", "global", "acc_add_prod(&a, -np, duc);",
+     "acc_add_prod(&a, np, duc);", pin_curl_solid_body),
+    ("vector gradient treats pole faces like scalar ones", "global",
+     "double d = m->is_pole[e] ? -0.5 * (fj + fi) : 0.5 * (fj - fi);", "double d = 0.5 * (fj - fi);",
+     pin_antipode),
+]
+
+# mistakes planted in the Python part of the oracle (the exact sums)
+PY_MUTANTS = [
+    ("low x low product dropped", "integral", "vh * xh, vh * xl, vl * xh, vl * xl", "vh * xh, vh * xl, vl * xh",
+     pin_exact_sums),
+    ("Veltkamp constant 2^26 + 1 (halves too wide for exact products)", "_split", "134217729.0", "67108865.0",
+     pin_exact_sums),
+    ("sum rounded term by term instead of exactly", "integral", "math.fsum(", "sum(", pin_exact_sums),
 ]
 
 
@@ -173,4 +235,17 @@ def test_pin_catches_planted_mistake(tmp_path, what, which, old, new, pin):
     lib = _build(str(tmp_path), which, old, new)
     with _oracle_lib(lib):
         caught = not pin()
+    assert caught, "the planted mistake (%s) passed the pin %s" % (what, pin.__name__)
+
+
+@pytest.mark.parametrize("what,name,old,new,pin", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pin_catches_planted_python_mistake(monkeypatch, what, name, old, new, pin):
+    assert pin(), "the pin fails on the real oracle"
+    src = inspect.getsource(getattr(oracle, name))
+    assert src.count(old) == 1, "mutation site not found once: %r" % old
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutant of oracle.%s>" % name, "exec"), ns)
+    monkeypatch.setattr(oracle, name, ns[name])
+    caught = not pin()
+    monkeypatch.undo()
     assert caught, "the planted mistake (%s) passed the pin %s" % (what, pin.__name__)
