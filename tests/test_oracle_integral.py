@@ -15,7 +15,7 @@ def test_exact_against_fractions():
     n = 400
     V = rng.uniform(0.5, 2.0, n) * 2.0 ** rng.integers(-30, 30, n)
     x = rng.standard_normal((n, 3)) * 2.0 ** rng.integers(-40, 40, (n, 3))
-    x[:, 2] = -x[:, 1] * (1 + 2.0 ** -40)  # heavy cancellation in level 2 against level 1's terms
+    x[:, 2] = -x[:, 1] * (1 + 2.0 ** -40)  # level 2 mirrors level 1, every value 2^-40 larger in size
     got = oracle.integral(V, x)
     for k in range(3):
         exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(V, x[:, k]))
