@@ -19,8 +19,12 @@ from test_oracle_dual import _dual_by_quadrature
 from test_oracle_grid import _zipper_bruteforce
 from test_oracle_grid import test_latitudes_match_legendre_roots as _latitudes_test
 from test_oracle_integral import test_exact_against_fractions as _fractions_test
+from test_oracle_operators import test_adjoints_are_bruteforce_transposes as _transposes_test
+from test_oracle_operators import test_node_subsets_match_full_evaluation as _subsets_test
+from test_oracle_regional import test_scale_factors_and_orthogonality_from_chords as _chords_test
 from test_oracle_integral import test_residual_after_cancelling_the_rounded_sum as _residual_test
 from test_oracle_remap import test_weights_are_barycentric_coordinates_of_the_ray_crossing as _barycentric_test
+from test_oracle_remap import test_targets_on_source_nodes_take_the_node_values as _on_nodes_test
 from test_oracle_vector_ops import test_curl_of_solid_body_rotation as _curl_test
 from test_oracle_vector_ops import test_vector_gradient_reverses_the_antipode_on_pole_faces as _antipode_test
 from synthetic.regional import DOMAINS
@@ -164,6 +168,22 @@ def pin_antipode():
     return _passes(_antipode_test, _meshes)
 
 
+def pin_transposes():
+    return _passes(_transposes_test, _meshes)
+
+
+def pin_subsets():
+    return _passes(_subsets_test, _meshes)
+
+
+def pin_remap_on_nodes():
+    return _passes(_on_nodes_test, _meshes)
+
+
+def pin_chords(name):
+    return lambda: _passes(_chords_test, name)
+
+
 def pin_exact_sums():
     return _passes(_fractions_test) and _passes(_residual_test)
 
@@ -215,6 +235,24 @@ MUTANTS = [
     ("vector gradient treats pole faces like scalar ones", "global",
      "double d = m->is_pole[e] ? -0.5 * (fj + fi) : 0.5 * (fj - fi);", "double d = 0.5 * (fj - fi);",
      pin_antipode),
+    ("divergence adjoint with the node's cos in place of the neighbour's", "global",
+     "ent[nent].c1 = np * m->coslat[j] / (2.0 * m->V[i]);", "ent[nent].c1 = np * ci / (2.0 * m->V[i]);",
+     pin_transposes),
+    ("gradient adjoint reads y_lambda for both components", "global",
+     "acc_add_prod(&acc[l], ent[t].c1, fld(y1, f32, ld, i, l));",
+     "acc_add_prod(&acc[l], ent[t].c1, fld(y0, f32, ld, i, l));", pin_transposes),
+    ("node-subset Laplacian takes the node's gradient for its neighbours'", "global",
+     "double uj = gx[(1 + p - p0) * nlev + k], vj = gy[(1 + p - p0) * nlev + k];",
+     "double uj = gx[k], vj = gy[k];", pin_subsets),
+    ("remap applies the first weight to all three vertices", "global",
+     "acc_add_prod(&a, w[3 * t + q], fld(f, f32, ld, nodes[3 * t + q], k));",
+     "acc_add_prod(&a, w[3 * t], fld(f, f32, ld, nodes[3 * t + q], k));", pin_remap_on_nodes),
+    ("Mercator scale factor 1/cos instead of cos", "regional", "*hx = *hy = cos(*lat);",
+     "*hx = *hy = 1.0 / cos(*lat);", pin_chords("mercator")),
+    ("polar stereographic scale factor inverted", "regional", "*hx = *hy = 4.0 / (4.0 + r2);",
+     "*hx = *hy = (4.0 + r2) / 4.0;", pin_chords("polar")),
+    ("polar stereographic plane mirrored", "regional", "atan2(x, -north * y);", "atan2(x, north * y);",
+     pin_chords("polar")),
 ]
 
 # mistakes planted in the Python part of the oracle (the exact sums)
