@@ -30,7 +30,8 @@
  *   - Field pointers are DEVICE pointers owned by the caller (for example
  *     torch tensors); the library never frees them.  A field is stored
  *     field[node][level]: node i, level k at element offset i*ld + k, with
- *     nlev >= 0 levels and leading dimension ld >= nlev (elements).  When
+ *     nlev >= 0 levels and leading dimension max(nlev, 1) <= ld <= 2^31 - 1
+ *     (elements; a larger ld is refused with ATLAS_EINVAL).  When
  *     ld is a multiple of the vector width (16 bytes: 4 F32, 2 F64, 8 BF16
  *     levels) outputs are written in whole vectors and the padding levels
  *     from nlev to the end of the row's last vector are set to zero; all
@@ -119,7 +120,7 @@ const char* atlas_info(void);
 const char* atlas_last_error(void);
 
 /* ---------------------------------------------------------------------- */
-/* Grid (paper Sec. 2.3: "a predefined list of two-dimensional points";   */
+/* Grid (paper Sec. 2.3: a grid is only a set of 2-D points, given ahead; */
 /* the O<N> octahedral grid is named in Sec. 4.3, Fig. 4).                 */
 /* ---------------------------------------------------------------------- */
 /* Octahedral reduced Gaussian grid O<N>, 1 <= N <= 8000: 2N Gaussian      */

@@ -247,8 +247,8 @@ class Mesh:
 
     def remap_weights(self, lonlat):
         """(nodes [T][3], weights [T][3]) locating each target (lon, lat) in
-        radians in this mesh (linear interpolation in 3D on the sphere);
-        raises if a target lies in no triangle."""
+        radians in this mesh (linear interpolation in three-dimensional space
+        over the sphere); raises if a target lies in no triangle."""
         lonlat = np.ascontiguousarray(lonlat, dtype=np.float64)
         T = lonlat.shape[0]
         nodes = np.empty((T, 3), np.int32)

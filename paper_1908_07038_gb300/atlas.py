@@ -369,9 +369,9 @@ class Fvm:
 
 
 class Remap:
-    """Linear interpolation in 3D on the sphere from the nodes of ``mesh`` to
-    the points of ``grid`` (located and weighted on the host, applied by a
-    CUDA kernel)."""
+    """Linear interpolation, in three-dimensional space over the sphere, from
+    the nodes of ``mesh`` to the points of ``grid`` (located and weighted on
+    the host, applied by a CUDA kernel)."""
 
     def __init__(self, mesh: Mesh, grid: Grid):
         h = ctypes.c_void_p()

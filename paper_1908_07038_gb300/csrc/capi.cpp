@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -360,11 +361,17 @@ int pick_vec(atlas_dtype dt, int64_t ld, const void* const* ptrs, int nptr, int 
   return v;
 }
 
+// Largest leading dimension: with fewer than 2^29 nodes in any grid and at
+// most 8-byte elements, node * ld * element size then stays below 2^63.
+constexpr int64_t kMaxLd = INT32_MAX;
+
 int check_field_args(atlas_dtype dtype, int nlev, int64_t ld, const void* const* ptrs, int nptr) {
   if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unsupported dtype %d", static_cast<int>(dtype));
   if (nlev < 0) return fail(ATLAS_EINVAL, "nlev must be >= 0 (got %d)", nlev);
   if (ld < nlev || ld < 1) return fail(ATLAS_EINVAL, "leading dimension ld=%lld must be >= max(nlev, 1) (nlev=%d)",
                                        static_cast<long long>(ld), nlev);
+  if (ld > kMaxLd)
+    return fail(ATLAS_EINVAL, "leading dimension ld=%lld above 2^31 - 1", static_cast<long long>(ld));
   for (int k = 0; k < nptr; ++k) {
     if (!ptrs[k]) return fail(ATLAS_EINVAL, "field pointer %d is NULL", k);
     if (reinterpret_cast<uintptr_t>(ptrs[k]) % static_cast<uintptr_t>(elem_size(dtype)) != 0)
@@ -1108,7 +1115,7 @@ int atlas_nabla_vector_gradient(atlas_fvm_t h, const void* u, const void* v, voi
   for (int k = 0; k < 4; ++k)
     if (!outs[k]) return fail(ATLAS_EINVAL, "NULL output field");
   if (!u || !v) return fail(ATLAS_EINVAL, "NULL input field");
-  if (valid_dtype(dtype) && ld >= 1) {
+  if (valid_dtype(dtype) && ld >= 1 && ld <= kMaxLd) {
     const int rc = check_no_overlap(ins, 2, outs, 4, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
     if (rc) return rc;
   }
@@ -1119,7 +1126,7 @@ int atlas_nabla_vector_gradient(atlas_fvm_t h, const void* u, const void* v, voi
 
 size_t atlas_nabla_workspace_bytes(atlas_fvm_t h, int op, int nlev, int64_t ld, atlas_dtype dtype) {
   atlas_fvm_s* f = get_fvm(h);
-  if (!f || nlev < 0 || ld < nlev || ld < 1 || !valid_dtype(dtype)) return 0;
+  if (!f || nlev < 0 || ld < nlev || ld < 1 || ld > kMaxLd || !valid_dtype(dtype)) return 0;
   if (op != ATLAS_OP_GRADIENT && op != ATLAS_OP_DIVERGENCE && op != ATLAS_OP_LAPLACIAN) return 0;
   return ws_layout(f, op, ld, dtype).total;
 }
@@ -1504,7 +1511,9 @@ int atlas_remap_apply(atlas_remap_t h, const void* src, void* dst, int nlev, int
   const void* used[2] = {src, dst};
   int rc = check_field_args(dtype, nlev, ld_src, used, 2);
   if (rc) return rc;
-  if (ld_dst < nlev || ld_dst < 1) return fail(ATLAS_EINVAL, "ld_dst=%lld < nlev=%d", static_cast<long long>(ld_dst), nlev);
+  if (ld_dst < nlev || ld_dst < 1 || ld_dst > kMaxLd)
+    return fail(ATLAS_EINVAL, "ld_dst=%lld outside [max(nlev, 1), 2^31 - 1] (nlev=%d)",
+                static_cast<long long>(ld_dst), nlev);
   const int64_t es = elem_size(dtype);
   const void* ins[1] = {src};
   void* outs[1] = {dst};

@@ -122,7 +122,8 @@ bool build_regular_gaussian_grid(int N, Grid& g);
 
 // Remapping weights (remap.cpp): for every target (lon, lat) in radians, the
 // three source nodes nodes[3t..3t+2] and weights of the linear interpolation
-// in 3D on the sphere in the source mesh's triangle that contains it.
+// in three-dimensional space over the sphere in the source mesh's triangle
+// that contains it.
 // not_located counts targets in no triangle (the polar caps); their nodes
 // are -1 and weights 0.  Returns false on an inconsistent mesh.
 bool build_remap(const Mesh& m, const double* tgt_lonlat, int64_t ntgt, std::vector<int32_t>& nodes,

@@ -2,10 +2,11 @@
 // source mesh and compute its three interpolation weights.
 //
 // The paper remaps a field from an O32 grid to an F8 grid with a linear
-// element-based interpolation in 3D on the sphere (Sec. 4.3, Fig. 6).  Here a
-// target with unit vector p is located in the source triangle whose plane
-// the ray from the centre along p crosses inside the triangle, and its
-// weights are the barycentric coordinates of that crossing point:
+// element-based interpolation in three dimensions over the sphere (Sec. 4.3,
+// Fig. 6).  Here a target with unit vector p is located in the source
+// triangle whose plane the ray from the centre along p crosses inside the
+// triangle, and its weights are the barycentric coordinates of that
+// crossing point:
 // t p = a + u (b - a) + v (c - a) solved by Cramer's rule, weights
 // (1 - u - v, u, v).  Of several containing triangles (a crossing on a shared
 // edge or vertex, up to 1e-12) the one whose smallest weight is largest is

@@ -126,3 +126,37 @@ def test_integral_argument_errors_without_a_gpu(product):
         with pytest.raises(capi.AtlasError) as ei:
             capi.atlas_fvm_integral(fvm.handle, *args, None)
         assert ei.value.code in (-1, -4, -5), args
+
+
+def test_leading_dimension_above_int32_is_refused(product):
+    """ld is bounded by 2^31 - 1, so that node * ld * element size cannot
+    overflow; larger values are refused before any size is computed or the
+    device is touched."""
+    atlas, capi = product
+    E = capi.AtlasError
+    fvm = atlas.build_fvm(4)
+    h = fvm.handle
+    fake = 1 << 20
+    for ld in (1 << 31, 1 << 40, (1 << 62) + 3):
+        with pytest.raises(E) as ei:
+            capi.atlas_nabla_gradient(h, fake, fake + 4096, fake + 8192, 3, ld, 0, None)
+        assert ei.value.code == -1 and "2^31" in str(ei.value)
+        with pytest.raises(E) as ei:
+            capi.atlas_nabla_vector_gradient(h, fake, fake + 4096, fake + 8192, fake + 12288, fake + 16384,
+                                             fake + 20480, 3, ld, 0, None)
+        assert ei.value.code == -1
+        assert capi.atlas_nabla_workspace_bytes(h, 0, 3, ld, 0) == 0
+        with pytest.raises(E) as ei:
+            capi.atlas_fvm_integral(h, fake, 0, 10, 7, ld, capi.ATLAS_F32, fake, fake, 1 << 20, None)
+        assert ei.value.code == -1
+    r = atlas.Remap(atlas.Mesh(atlas.Grid(4)), atlas.Grid(2, regular=True))
+    for lds, ldd in ((1 << 31, 8), (8, 1 << 31)):
+        with pytest.raises(E) as ei:
+            capi.atlas_remap_apply(r.handle, fake, fake + (1 << 24), 3, lds, ldd, 0, None)
+        assert ei.value.code == -1
+    # the largest accepted ld passes validation and stops at the device check
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(E) as ei:
+            capi.atlas_nabla_gradient(h, fake, fake + (1 << 44), fake + (1 << 45), 3, (1 << 31) - 1, 0, None)
+        assert ei.value.code == -3
