@@ -275,7 +275,7 @@ def _fp64_flops(fvm, op, nlev):
     return (nnz * per_entry + V * per_node) * nlev
 
 
-def _cpu_baseline(grid, fvm_nodes, f_host, u_host, v_host, nlev, budget_s=12.0):
+def _cpu_baseline(grid, fvm_nodes, f_host, u_host, v_host, nlev, budget_s=30.0):
     """The oracle as it stands, single-threaded, on a contiguous node sample
     of the same workload (all five operators)."""
     from oracle.oracle import Mesh
