@@ -59,6 +59,14 @@ def _store_cache(c):
     os.replace(tmp, p)
 
 
+def _grid_key(grid):
+    """Cache key of a grid: its family and size (O<N>, F<N>, or a regional
+    projection with its points per row and rows)."""
+    if grid.projection is not None:
+        return "%s%dx%d" % (grid.projection, grid.nx, grid.ny)
+    return ("F%d" if grid.regular else "O%d") % grid.N
+
+
 def _call(fvm, op, ins, outs, nlev):
     if op == "gradient":
         fvm.gradient(ins[0], nlev, out=(outs[0], outs[1]))
@@ -100,7 +108,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
     if ld is None:
         q = 16 // es
         ld = (nlev + q - 1) // q * q
-    key_base = "%s|O%d|dt%d|L%d|ld%d" % (dev_name, fvm.grid.N, dtype, nlev, ld)
+    key_base = "%s|%s|dt%d|L%d|ld%d" % (dev_name, _grid_key(fvm.grid), dtype, nlev, ld)
     cache = _load_cache()
     if fields is None:
         t = _torch_dtype(dtype)
