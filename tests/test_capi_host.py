@@ -160,3 +160,23 @@ def test_leading_dimension_above_int32_is_refused(product):
         with pytest.raises(E) as ei:
             capi.atlas_nabla_gradient(h, fake, fake + (1 << 44), fake + (1 << 45), 3, (1 << 31) - 1, 0, None)
         assert ei.value.code == -3
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """A copy of the package without its built library cannot be imported:
+    there is no other implementation to fall back on."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_1908_07038_gb300")
+    dst = tmp_path / "paper_1908_07038_gb300"
+    dst.mkdir()
+    for name in os.listdir(src):
+        if name.endswith(".py"):
+            shutil.copy(os.path.join(src, name), dst / name)
+    for mod in ("capi", "atlas", "batch", "partition", "hoststep", "tune"):
+        r = subprocess.run([sys.executable, "-c", "import paper_1908_07038_gb300.%s" % mod], cwd=str(tmp_path),
+                           capture_output=True, text=True, timeout=300,
+                           env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+        assert r.returncode != 0, mod
+        assert "ImportError" in r.stderr and "libatlasgb.so is not built" in r.stderr, (mod, r.stderr[-500:])
