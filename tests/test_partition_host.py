@@ -59,6 +59,37 @@ def test_halo_holds_every_stencil_neighbour(pfvm, part_mod, op, halo):
             p.close()
 
 
+@pytest.mark.parametrize("family", ["F16", "lambert", "polar", "rotated"])
+def test_bands_and_halos_on_other_grid_families(product, part_mod, family):
+    """The regular Gaussian grid and regional grids (rows of a projection's
+    plane) partition the same way: whole rows, and every stencil neighbour
+    of every operator within the one-row halo (two rows for the Laplacian)."""
+    atlas, _ = product
+    from synthetic.regional import DOMAINS
+    if family == "F16":
+        fvm = atlas.build_fvm(16, regular=True)
+        rows = np.full(32, 64)
+    else:
+        proj, kw = DOMAINS[family]
+        fvm = atlas.build_fvm_regional(proj, 23, 19, **kw)
+        rows = np.full(19, 23)
+    off = np.concatenate([[0], np.cumsum(rows)])
+    for op in ("gradient", "divergence", "curl", "gradient_adjoint", "divergence_adjoint", "vector_gradient",
+               "laplacian"):
+        halo = 2 if op == "laplacian" else 1
+        t = fvm.stencil_table(op)
+        for nparts in (2, 3, 6):
+            parts = [part_mod.Partition(fvm, nparts, k, halo) for k in range(nparts)]
+            assert parts[0].own0 == 0 and parts[-1].own1 == fvm.nnodes
+            for a, b in zip(parts, parts[1:]):
+                assert a.own1 == b.own0
+            for p in parts:
+                assert p.own0 in off and p.own1 in off and p.halo0 in off and p.halo1 in off
+                cols = t["nbr"][t["ptr"][p.own0]:t["ptr"][p.own1]]
+                assert cols.min() >= p.halo0 and cols.max() < p.halo1, (family, op, nparts)
+                p.close()
+
+
 def test_neighbour_ranges_match(pfvm, part_mod):
     fvm = pfvm(16)
     for halo in (1, 2):
