@@ -25,6 +25,8 @@ class Batch:
 
     def __init__(self, jobs, tune=None):
         n = len(jobs)
+        if n == 0:
+            raise ValueError("a batch needs at least one job")
         arr = (capi.atlas_batch_desc * n)()
         dt = None
         for k, j in enumerate(jobs):
