@@ -88,3 +88,37 @@ def test_reference_arm_prints_one_contract_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert "workload" in line["config"] and line["cpu_baseline"]["sample"]
+
+
+def test_algorithmic_table_bytes_follow_the_mesh_counts(pfvm):
+    """The roofline's table bytes: offsets, then 12 bytes per entry (index +
+    two FP32 weights) or 8 (the Laplacian's one weight), plus 8 bytes per
+    node for a B term.  The entry counts come from the mesh: 2E for the
+    gradient and its adjoint (every edge seen from both ends), 2E - 2P for
+    the divergence and its adjoint (P pole edges carry no flux), and for the
+    Laplacian L = D G the nodes that G reaches from the node itself or from
+    a neighbour across a face that carries divergence flux (so not across a
+    pole edge), the node itself excluded."""
+    fvm = pfvm(16)
+    V, E = fvm.nnodes, fvm.mesh.nedges
+    m = fvm.mesh.arrays()
+    P = int(m["is_pole"].sum())
+    assert E == 3 * V - 20 and P == 20
+    offsets = 4 * (V + 1)
+    want = {"gradient": offsets + 2 * E * 12,
+            "gradient_adjoint": offsets + 2 * E * 12 + 8 * V,
+            "divergence": offsets + (2 * E - 2 * P) * 12 + 8 * V,
+            "divergence_adjoint": offsets + (2 * E - 2 * P) * 12 + 8 * V}
+    for op, b in want.items():
+        assert bench._table_bytes_of(fvm, op, 4) == b, op
+    # the Laplacian's neighbourhoods by brute force over the edge list
+    nb = [set() for _ in range(V)]  # gradient neighbours (every edge)
+    nd = [set() for _ in range(V)]  # divergence neighbours (no pole edges)
+    for (a, c), pole in zip(m["e2n"], m["is_pole"]):
+        nb[a].add(c)
+        nb[c].add(a)
+        if not pole:
+            nd[a].add(c)
+            nd[c].add(a)
+    ring2 = sum(len(set().union(nb[i], *(nb[j] for j in nd[i])) - {i}) for i in range(V))
+    assert bench._table_bytes_of(fvm, "laplacian", 4) == offsets + ring2 * 8
