@@ -180,3 +180,20 @@ def test_missing_library_fails_loudly(tmp_path):
                            env=dict(os.environ, PYTHONPATH=str(tmp_path)))
         assert r.returncode != 0, mod
         assert "ImportError" in r.stderr and "libatlasgb.so is not built" in r.stderr, (mod, r.stderr[-500:])
+
+
+@pytest.mark.parametrize("compiler,std,src", [("gcc", "c89", "int main(void) { return 0; }\n"),
+                                              ("gcc", "c99", "int main(void) { return 0; }\n"),
+                                              ("g++", "c++11", "int main() { return 0; }\n"),
+                                              ("g++", "c++17", "int main() { return 0; }\n")])
+def test_header_compiles_alone(tmp_path, compiler, std, src):
+    """include/atlas_gb.h is self-contained C: it compiles on its own, warning
+    free under -pedantic, as C89, C99 and C++."""
+    import shutil
+    import subprocess
+    if not shutil.which(compiler):
+        pytest.skip(compiler + " missing")
+    f = tmp_path / ("h.c" if compiler == "gcc" else "h.cpp")
+    f.write_text('#include "atlas_gb.h"\n' + src)
+    subprocess.check_call([compiler, "-std=" + std, "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), "-c", str(f), "-o", str(tmp_path / "h.o")])
