@@ -122,3 +122,36 @@ def test_algorithmic_table_bytes_follow_the_mesh_counts(pfvm):
             nd[c].add(a)
     ring2 = sum(len(set().union(nb[i], *(nb[j] for j in nd[i])) - {i}) for i in range(V))
     assert bench._table_bytes_of(fvm, "laplacian", 4) == offsets + ring2 * 8
+
+
+def test_traffic_only_for_the_kernels_it_was_measured_on(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu capture only while the
+    kernel source hashes to the value stored with it; otherwise it is null."""
+    import hashlib
+    import json
+    src = tmp_path / "kernels.cu"
+    src.write_text("// kernels, version 1\n")
+    cap = tmp_path / "traffic.json"
+    good = hashlib.sha256(src.read_bytes()).hexdigest()
+    cap.write_text(json.dumps({"kernels_sha256": good, "per_launch_bytes": {"gradient": 123.0}}))
+    monkeypatch.setattr(bench, "KERNEL_SOURCE", str(src))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(cap))
+    assert bench._traffic("gradient") == 123.0
+    assert bench._traffic("laplacian") is None  # not captured
+    src.write_text("// kernels, version 2\n")
+    assert bench._traffic("gradient") is None  # the kernels changed since
+    cap.unlink()
+    assert bench._traffic("gradient") is None
+    # the committed capture matches the committed kernels (after a kernel
+    # change, take the capture again: profiles/dram_traffic_o1280.json)
+    monkeypatch.undo()
+    for op in ("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint"):
+        assert bench._traffic(op) is not None, "no DRAM traffic for %s: kernels.cu changed since the capture" % op
+
+
+def test_peak_is_the_measured_copy_rate_else_the_fallback(tmp_path, monkeypatch):
+    import json
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6768.8, "bf16_tflops": 1900}))
+    assert bench._peaks() == (6768.8, "measured")
