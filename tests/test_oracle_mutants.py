@@ -22,6 +22,8 @@ from test_oracle_integral import test_exact_against_fractions as _fractions_test
 from test_oracle_operators import test_adjoints_are_bruteforce_transposes as _transposes_test
 from test_oracle_operators import test_node_subsets_match_full_evaluation as _subsets_test
 from test_oracle_regional import test_scale_factors_and_orthogonality_from_chords as _chords_test
+from test_oracle_regional import test_cell_areas_and_closure as _areas_test
+from test_oracle_regional import test_linear_fields_are_exact_everywhere as _linear_test
 from test_oracle_integral import test_residual_after_cancelling_the_rounded_sum as _residual_test
 from test_oracle_remap import test_weights_are_barycentric_coordinates_of_the_ray_crossing as _barycentric_test
 from test_oracle_remap import test_targets_on_source_nodes_take_the_node_values as _on_nodes_test
@@ -184,6 +186,14 @@ def pin_chords(name):
     return lambda: _passes(_chords_test, name)
 
 
+def pin_areas(name):
+    return lambda: _passes(_areas_test, name)
+
+
+def pin_linear(name):
+    return lambda: _passes(_linear_test, name)
+
+
 def pin_exact_sums():
     return _passes(_fractions_test) and _passes(_residual_test)
 
@@ -253,6 +263,16 @@ MUTANTS = [
      "*hx = *hy = (4.0 + r2) / 4.0;", pin_chords("polar")),
     ("polar stereographic plane mirrored", "regional", "atan2(x, -north * y);", "atan2(x, north * y);",
      pin_chords("polar")),
+    ("right side of the rectangle not seen as boundary", "regional",
+     "if (ca == cb && (ca == 0 || ca == g->nx - 1)) return 1;", "if (ca == cb && ca == 0) return 1;",
+     pin_areas("rotated")),
+    ("triangle area shared in halves instead of thirds", "regional",
+     "g->A[v[k]] += R * R * (0.5 * ar) / 3.0;", "g->A[v[k]] += R * R * (0.5 * ar) / 2.0;", pin_areas("lambert")),
+    ("Lambert longitude without the cone constant", "regional", "*lon = p[5] * RPI / 180.0 + th / n;",
+     "*lon = p[5] * RPI / 180.0 + th;", pin_chords("lambert")),
+    ("flux form without the h_y factor on its first component", "regional",
+     "double d1 = s1 * rdiff(g->hy[cb], rfld(p, f32, ld, cb, l), g->hy[i], pi);",
+     "double d1 = s1 * (rfld(p, f32, ld, cb, l) - pi);", pin_linear("mercator")),
 ]
 
 # mistakes planted in the Python part of the oracle (the exact sums)
