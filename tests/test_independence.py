@@ -18,9 +18,21 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = "paper_1908_07038_gb300"
 
 
+SKIP_DIRS = {".git", "_work", "_build", "__pycache__", "gpurun_out", "baseline", ".pytest_cache"}
+
+
 def _files(prefix, exts):
-    out = subprocess.check_output(["git", "ls-files", prefix], cwd=ROOT, text=True).split()
-    return [f for f in out if f.endswith(exts)]
+    """Committed files under prefix (git), or, in a copy without its git
+    history, the source files found there."""
+    try:
+        out = subprocess.check_output(["git", "ls-files", prefix], cwd=ROOT, text=True,
+                                      stderr=subprocess.DEVNULL).split()
+    except (OSError, subprocess.CalledProcessError):
+        out = []
+        for d, dirs, names in os.walk(os.path.join(ROOT, prefix)):
+            dirs[:] = [x for x in dirs if x not in SKIP_DIRS]
+            out += [os.path.relpath(os.path.join(d, n), ROOT) for n in names]
+    return sorted(f for f in out if f.endswith(exts))
 
 
 def _text(path):
