@@ -41,6 +41,17 @@ def test_counts_volume_and_closure(fmesh, N):
     assert np.all(g["pl"] == 4 * N)
 
 
+@pytest.mark.parametrize("N", [1, 2, 4, 8])
+def test_volumes_match_quadrature(fmesh, N):
+    """Each F<N> cell volume against an independent quadrature of cos(lat)
+    over the median sub-quadrilaterals of its triangles (plus the polar
+    rectangles), the same check as for O<N>."""
+    from test_oracle_dual import _dual_by_quadrature
+    m = fmesh(N)
+    Vq, _ = _dual_by_quadrature(m)
+    assert np.max(np.abs(m.dual()["V"] - Vq) / Vq) <= 1e-13
+
+
 def _l2(V, e, mask):
     return np.sqrt(np.sum(V[mask] * e[mask] ** 2) / np.sum(V[mask]))
 
