@@ -3,7 +3,8 @@
  * finite-volume nabla operators on the octahedral reduced Gaussian grid.
  *
  * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU
- * baseline leg of the benchmark load this library. The product library
+ * legs of the benchmark (its CPU baseline and its oracle arm) load this
+ * library. The product library
  * (paper_1908_07038_gb300) never links, loads or calls it, and this file
  * includes nothing from the product.
  *

@@ -1,8 +1,9 @@
 """ctypes front end of the FP64 CPU oracle (``atlas_oracle.c``).
 
-TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
-baseline leg of ``bench.py`` import this module. It imports nothing from the
-product package and the product never imports it.
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__`` (``build()``
+compiles it, ``smoke()`` checks against it) and the CPU legs of ``bench.py``
+(its CPU baseline and its ``--impl reference`` arm) import this module. It
+imports nothing from the product package and the product never imports it.
 
 The oracle computes, in plain FP64 C, the octahedral reduced Gaussian grid,
 its zipper triangulation with pole edges, the median-dual geometry and the

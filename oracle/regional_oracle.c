@@ -1,8 +1,7 @@
 /*
  * TEST INFRASTRUCTURE: FP64 CPU oracle of the nabla operators on regional
- * (limited-area) grids with map projections.  Only tests/, the smoke check
- * and the CPU baseline of the benchmark use it; it shares no code with the
- * product library.
+ * (limited-area) grids with map projections.  Only tests/ and the smoke
+ * check use it; it shares no code with the product library.
  *
  * The paper says Atlas meshes the regional grids of limited-area models and
  * names operators that account for the projection as follow-up work (Sec.
