@@ -286,3 +286,15 @@ def test_plane_linear_fields_are_harmonic_on_conformal_grids(name):
     gx, _ = m.gradient(f)
     scale = np.max(np.abs(gx)) / np.min(np.sqrt(g["area"]))  # |grad| / cell size
     assert np.max(np.abs(lap)) <= 1e-12 * scale  # about 1e-14 measured; a non-conformal grid gives 3e-3
+
+
+def test_lambert_golden_fixture_unchanged():
+    """The regional oracle still writes the frozen 4 x 3 Lambert fixture
+    (tests/golden/lambert_4x3.txt, written by tests/golden/make_golden.py)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lambert_4x3.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    want = np.array([[float.fromhex(v) for v in r] for r in rows])
+    g = _mesh("lambert", 4, 3).geometry()
+    got = np.stack([g[k] for k in ("lon", "lat", "hx", "hy", "area")], 1)
+    assert want.shape == (12, 5) and np.array_equal(got, want)
