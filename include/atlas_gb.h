@@ -354,7 +354,8 @@ int atlas_nabla_vector_gradient(atlas_fvm_t fvm, const void* u, const void* v, v
                                 void* vy, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
 
 /* ---------------------------------------------------------------------- */
-/* Edge-based two-kernel forms: an edge-flux kernel writes one flux per    */
+/* Edge-based two-kernel forms of the operators of paper Sec. 2.3 (the    */
+/* paper gives no kernel design): an edge-flux kernel writes one flux per  */
 /* edge and level into a caller-owned device workspace, then a node-gather */
 /* kernel sums each node's CSR row of fluxes.  Same results as the fused   */
 /* calls up to rounding.  ws must hold atlas_nabla_workspace_bytes(...)    */
@@ -391,9 +392,10 @@ int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t fvm, const void* f, void* la
                                         atlas_dtype dtype, void* stream);
 
 /* ---------------------------------------------------------------------- */
-/* Batched launch: many fields of different grids and level counts in one */
-/* persistent kernel (one launch, capturable in a CUDA graph; optionally   */
-/* the largest fields in plain launches of their own).                     */
+/* Batched launch: the gradient and divergence of paper Sec. 2.3 on many  */
+/* fields of different grids and level counts in one persistent kernel    */
+/* (one launch, capturable in a CUDA graph; optionally the largest fields  */
+/* in plain launches of their own).  The paper has no counterpart.         */
 /* ---------------------------------------------------------------------- */
 typedef struct {
   int op;              /* ATLAS_OP_GRADIENT or ATLAS_OP_DIVERGENCE           */
