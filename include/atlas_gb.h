@@ -236,7 +236,8 @@ int atlas_fvm_info(atlas_fvm_t f, const double** V, const double** S, const doub
 /* Regional fvm only (EINVAL otherwise): area[nnodes] and Sb[E][2].         */
 int atlas_fvm_regional_info(atlas_fvm_t f, const double** area, const double** Sb);
 
-/* Volume-weighted sums in FP64 (the global conservation sums): for every  */
+/* Volume-weighted sums in FP64 (the global conservation sums; the paper */
+/* gives no counterpart, they check the operators of Sec. 2.3): for every  */
 /* level k, out[k] = sum over nodes i = node0 .. node0+count-1 of          */
 /* V_i x[(i - node0) ld + k], where x points at the row of node node0 (a  */
 /* partition's own rows: sum its part, then add the parts across ranks).  */
