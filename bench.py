@@ -65,13 +65,19 @@ def _job_rate(units_per_rank, ws, ms):
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_o1280.json")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1908_07038_gb300", "csrc", "kernels.cu")
+KERNEL_SOURCES = tuple(os.path.join(ROOT, "paper_1908_07038_gb300", "csrc", f)
+                       for f in ("kernels.cu", "group.cuh", "group.cu"))
 
 
 def _kernel_hash():
+    """SHA-256 of the kernel sources, in order (the traffic capture is keyed
+    to it)."""
     import hashlib
-    with open(KERNEL_SOURCE, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def _traffic(op):
@@ -87,11 +93,13 @@ def _traffic(op):
         return None
 
 
-KERNEL_NAME = {"gradient": "stencil_kernel<float,float,1,2,4,0,0,B,1>",
-               "divergence": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
-               "laplacian": "pair_kernel<float,float,4,B,1>",
-               "gradient_adjoint": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
-               "divergence_adjoint": "stencil_kernel<float,float,1,2,4,1,0,B,1>"}
+# node-group kernels: <storage, inputs, outputs, B term, weights per entry,
+# part A and part B levels per lane, entries per batch>
+KERNEL_NAME = {"gradient": "group_kernel<float,1,2,0,2,4,1,2>",
+               "divergence": "group_kernel<float,2,1,1,2,4,1,2>",
+               "laplacian": "group_kernel<float,1,1,0,1,4,1,4>",
+               "gradient_adjoint": "group_kernel<float,2,1,1,2,4,1,2>",
+               "divergence_adjoint": "group_kernel<float,1,2,1,2,4,1,2>"}
 
 
 def _peaks():

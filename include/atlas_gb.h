@@ -96,7 +96,8 @@ enum {
   ATLAS_OP_DIVERGENCE_ADJOINT = 3,
   ATLAS_OP_LAPLACIAN = 4,
   ATLAS_OP_CURL = 5,
-  ATLAS_OP_VECTOR_GRADIENT = 6
+  ATLAS_OP_VECTOR_GRADIENT = 6,
+  ATLAS_OP_CURL_ADJOINT = 7
 };
 
 /* Map projections of regional grids (atlas_grid_regional). */
@@ -294,16 +295,57 @@ int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 /* results are bitwise identical for every shape.                          */
 int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, int threads, int blocks_per_sm,
                          int tile_passes);
-/* Inspection: copy out the FP64 host table of one operator's node stencil */
-/*   out_c(i) = sum_{q in [ptr[i], ptr[i+1])} sum_m W_cm(q) (x_m(nbr[q]) - x_m(i))  */
-/*              + sum_m B_cm(i) x_m(i)                                     */
-/* (w[q][2] = (W_00, W_10) for one input, (W_00, W_01) for two; the        */
-/* Laplacian uses w[q][0] only; b[i][2] is zero when the operator has no  */
-/* B term).  Call once with NULL arrays to get nnz, nin and nout, then     */
-/* with ptr[V+1], nbr[nnz], w[nnz][2], b[V][2].  Host only: works without */
-/* a GPU; the device tables are rounded copies of these.                   */
-int atlas_fvm_stencil_table(atlas_fvm_t f, int op, int64_t* nnz, int* nin, int* nout, int32_t* ptr,
-                            int32_t* nbr, double* w, double* b);
+/* Shared-memory node-group kernels (FP32 and BF16 fields; F64 always runs */
+/* per node).  Every grid row is cut into tiles of up to 28 consecutive    */
+/* nodes; a producer warp copies the node rows a tile reads (its own and   */
+/* their neighbours, a few runs of consecutive ids) into shared memory     */
+/* with TMA bulk copies, and each of seven consumer warps computes a group */
+/* of up to four nodes from the union of their stencil rows.  The          */
+/* operators use them by default wherever they apply: field pointers       */
+/* 16-byte aligned, ld * element size a multiple of 16, the tile's rows    */
+/* fitting in shared memory (at O1280, ld up to about 190 FP32 values for */
+/* the Laplacian), and a launch made of whole tiles (whole grids,          */
+/* partitions of whole rows); the per-node kernels run elsewhere, with     */
+/* bitwise identical results.  enable: 1 use them with the default table  */
+/* layout (merged entries for the Laplacian, per-node rows otherwise), 2   */
+/* with merged entries (each distinct neighbour of a group once, weights   */
+/* of all four nodes), 3 with per-node rows (each node's own stencil row), */
+/* 0 per-node kernels only, -1 keep.  blocks_per_sm: 1 or 2 blocks of 256 */
+/* threads per SM at most (fewer when shared memory is short; 0 keeps;     */
+/* default 2).  dtype -1 sets all three dtypes.  Host only; takes effect  */
+/* at the next operator call (a layout change rebuilds the operator's tile */
+/* tables then).                                                           */
+int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm);
+/* The node-group kernels bound every wait on their pipeline barriers      */
+/* (about a second); a kernel that gives up records a code in a device     */
+/* error word and returns, its outputs then incomplete.  This call copies  */
+/* that word (synchronously: it waits for the device) into *code, 0 when   */
+/* no kernel gave up, and with clear != 0 resets it.  Codes (bits): 1 a    */
+/* consumer warp gave up waiting for a tile, 2 the producer gave up        */
+/* waiting for a free stage, 4 copies were still in flight when the        */
+/* producer left.                                                          */
+int atlas_kernel_status(unsigned* code, int clear);
+/* Testing hook: with on != 0 the following node-group launches make their */
+/* consumer warps wait on a barrier that nothing completes, with a limit of */
+/* a few milliseconds, so that the time-out path runs (code 1); 0 restores  */
+/* normal launches.  No GPU fault and no hang is involved.                  */
+int atlas_debug_tile_hang(int on);
+/* Inspection: copy out the FP64 node-group table of one operator (the     */
+/* groups the node-group kernels compute, before the tables are cut into   */
+/* tiles and rounded to float; in the kernels' tables neighbours are       */
+/* referred to by their place among the tile's staged rows).  Groups       */
+/* are runs of up to four consecutive nodes of a grid row.  head[g][4] =   */
+/* {first node, first entry, end entry, nb | count << 16 | imask << 20}:   */
+/* entries [first entry, end entry) are the distinct neighbours of the     */
+/* group's nodes in ascending id order; nb of them come before the run of  */
+/* the group's own nodes, whose offsets from the first node imask marks.   */
+/* hdr[e] = j | mask << 28: neighbour j and the group's nodes (bit t: node */
+/* first + t) whose stencil row holds j.  w[e][t][2] = that node's weights */
+/* towards j as in atlas_fvm_stencil_table (0 where the bit is clear).     */
+/* Call once with NULL arrays for the counts.  Host only; ATLAS_EINVAL     */
+/* when the stencil has no group table (then the per-node kernels run).    */
+int atlas_fvm_group_table(atlas_fvm_t f, int op, int64_t* ngroups, int64_t* nent, int32_t* head, uint32_t* hdr,
+                          double* w);
 void atlas_fvm_destroy(atlas_fvm_t f);
 
 /* ---------------------------------------------------------------------- */
@@ -343,6 +385,13 @@ int atlas_nabla_divergence_adjoint(atlas_fvm_t fvm, const void* div, void* u, vo
 /* Units: 1/s for u, v in m/s.  in: u, v; out: zeta.                       */
 int atlas_nabla_curl(atlas_fvm_t fvm, const void* u, const void* v, void* zeta, int nlev, int64_t ld,
                      atlas_dtype dtype, void* stream);
+/* Curl adjoint (u_bar, v_bar) = C^T zeta_bar: the exact transpose of the  */
+/* curl as a linear map (column i of C gathered at node i from the rows of */
+/* its regular-edge neighbours, as the other adjoints), for variational    */
+/* (reverse-mode) use of the curl.  in: zeta; out: u, v (must not overlap  */
+/* the input or each other).                                               */
+int atlas_nabla_curl_adjoint(atlas_fvm_t fvm, const void* zeta, void* u, void* v, int nlev, int64_t ld,
+                             atlas_dtype dtype, void* stream);
 /* Gradient of both physical components of a tangent vector field:         */
 /* (ux, uy) = grad u, (vx, vy) = grad v, as atlas_nabla_gradient except on */
 /* the pole edge: a polar node and its antipode (its pole-edge neighbour)  */
@@ -365,6 +414,16 @@ int atlas_nabla_vector_gradient(atlas_fvm_t fvm, const void* u, const void* v, v
 size_t atlas_nabla_workspace_bytes(atlas_fvm_t fvm, int op, int nlev, int64_t ld, atlas_dtype dtype);
 int atlas_nabla_gradient_edges(atlas_fvm_t fvm, const void* f, void* gx, void* gy, void* ws,
                                size_t ws_bytes, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
+/* The gradient of atlas_nabla_gradient_edges with the edge flux in the    */
+/* averaged (Green-Gauss) form S_e (f_a + f_b)/2, entering the two ends of  */
+/* a regular edge with opposite signs and both ends of a pole edge with +1 */
+/* (the same operator up to the cells' closure residual, sum_e n_ie).  A   */
+/* selectable variant of the edge-flux kernel for comparison: in FP32 its  */
+/* node sums cancel terms of size |f| |S_e| / V_i, about R/h times the     */
+/* result (~800 at O1280), so its error is that much larger than the       */
+/* difference form's.  Same workspace as atlas_nabla_gradient_edges.       */
+int atlas_nabla_gradient_edges_averaged(atlas_fvm_t fvm, const void* f, void* gx, void* gy, void* workspace,
+                                        size_t ws_bytes, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
 int atlas_nabla_divergence_edges(atlas_fvm_t fvm, const void* u, const void* v, void* div, void* ws,
                                  size_t ws_bytes, int nlev, int64_t ld, atlas_dtype dtype, void* stream);
 /* grad into ws, then div of it: the two-pass Laplacian.                   */

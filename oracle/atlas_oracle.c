@@ -842,6 +842,31 @@ static int div_row(const orc_mesh *m, int64_t i, row_entry *ent) {
   return nent;
 }
 
+/* Row i of the curl, written out from the circulation form of curl_node:
+ * V_i zeta_i = sum_regular [ n_lambda (v_j - v_i)/2 - n_phi (u_j cos_j - u_i cos_i)/2 ]
+ *              + n_pole,phi u_i cos_i,
+ * c0 the u coefficient, c1 the v coefficient; the diagonal is split into
+ * one entry per face and one for the pole segment. */
+static int curl_row(const orc_mesh *m, int64_t i, row_entry *ent) {
+  int nent = 0;
+  double ci = m->coslat[i];
+  for (int32_t p = m->n2e_ptr[i]; p < m->n2e_ptr[i + 1]; ++p) {
+    int64_t e = m->n2e[p];
+    if (m->is_pole[e]) continue;
+    double nl, np;
+    face_normal(m, p, &nl, &np);
+    int32_t j = far_end(m, e, i);
+    ent[nent].col = j; ent[nent].c0 = -(np * m->coslat[j]) / (2.0 * m->V[i]); ent[nent].c1 = nl / (2.0 * m->V[i]);
+    ++nent;
+    ent[nent].col = (int32_t)i; ent[nent].c0 = (np * ci) / (2.0 * m->V[i]); ent[nent].c1 = -nl / (2.0 * m->V[i]);
+    ++nent;
+  }
+  if (m->pole_nphi[i] != 0.0) {
+    ent[nent].col = (int32_t)i; ent[nent].c0 = m->pole_nphi[i] * ci / m->V[i]; ent[nent].c1 = 0.0; ++nent;
+  }
+  return nent;
+}
+
 /* Gradient adjoint x = G^T y with y = (y_lambda, y_phi):
  *   x_k = sum_i [ G_lambda(i,k) y_lambda_i + G_phi(i,k) y_phi_i ].
  * Column k of G is non-zero only on rows i in {k} U neighbours(k). */
@@ -894,6 +919,37 @@ int orc_divergence_adjoint(const orc_mesh *m, const void *d, int f32, int64_t ld
           double di = fld(d, f32, ld, i, l);
           acc_add_prod(&au[l], ent[t].c0, di);
           acc_add_prod(&av[l], ent[t].c1, di);
+        }
+      }
+    }
+    for (int l = 0; l < nlev; ++l) { xu[q * nlev + l] = acc_val(&au[l]); xv[q * nlev + l] = acc_val(&av[l]); }
+  }
+  free(au); free(av);
+  return 0;
+}
+
+/* Curl adjoint (x_u, x_v) = C^T z: column k of C is non-zero only on rows
+ * i in {k} U neighbours(k). */
+int orc_curl_adjoint(const orc_mesh *m, const void *z, int f32, int64_t ld, int nlev, const int64_t *nodes,
+                     int64_t count, double *xu, double *xv) {
+  if (!m || !z || nlev < 0 || ld < nlev || check_nodes(m, nodes, count)) return -1;
+  int64_t n = nsel(m, nodes, count);
+  row_entry ent[160];
+  acc_t *au = (acc_t *)malloc(sizeof(acc_t) * (size_t)(nlev > 0 ? nlev : 1));
+  acc_t *av = (acc_t *)malloc(sizeof(acc_t) * (size_t)(nlev > 0 ? nlev : 1));
+  if (!au || !av) { free(au); free(av); return -2; }
+  for (int64_t q = 0; q < n; ++q) {
+    int64_t k = nodes ? nodes[q] : q;
+    for (int l = 0; l < nlev; ++l) au[l].s = au[l].c = av[l].s = av[l].c = 0.0;
+    for (int32_t p = m->n2e_ptr[k] - 1; p < m->n2e_ptr[k + 1]; ++p) {
+      int64_t i = (p < m->n2e_ptr[k]) ? k : far_end(m, m->n2e[p], k);
+      int ne = curl_row(m, i, ent);
+      for (int t = 0; t < ne; ++t) {
+        if (ent[t].col != k) continue;
+        for (int l = 0; l < nlev; ++l) {
+          double zi = fld(z, f32, ld, i, l);
+          acc_add_prod(&au[l], ent[t].c0, zi);
+          acc_add_prod(&av[l], ent[t].c1, zi);
         }
       }
     }

@@ -66,6 +66,7 @@ def _configure(lib):
     lib.orc_laplacian.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
     lib.orc_divergence_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
     lib.orc_curl.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P]
+    lib.orc_curl_adjoint.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P]
     lib.orc_remap.argtypes = [P, P, i64, P, P]
     lib.orc_remap_apply.argtypes = [P, P, i64, P, ctypes.c_int, i64, ctypes.c_int, P]
     lib.orc_vector_gradient.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_int, P, i64, P, P, P, P]
@@ -93,6 +94,7 @@ def _configure(lib):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("orc_gradient", "orc_divergence", "orc_laplacian", "orc_gradient_adjoint",
                  "orc_divergence_adjoint", "orc_gradient_averaged", "orc_gauss_colatitudes", "orc_curl",
+                 "orc_curl_adjoint",
                  "orc_vector_gradient", "orc_remap", "orc_remap_apply"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -301,6 +303,17 @@ class Mesh:
         rc = self._lib.orc_divergence_adjoint(self._h, _ptr(d), f32, ld, nlev, _ptr(nodes), n, _ptr(xu), _ptr(xv))
         if rc:
             raise ValueError("orc_divergence_adjoint rc=%d" % rc)
+        return xu, xv
+
+    def curl_adjoint(self, z, nlev=None, nodes=None):
+        """(u_bar, v_bar) = C^T z: the transpose of the curl's matrix rows."""
+        z, f32, ld = _field(z)
+        nlev = z.shape[1] if nlev is None else nlev
+        nodes, n = self._nodes(nodes)
+        xu = np.empty((n, nlev)); xv = np.empty((n, nlev))
+        rc = self._lib.orc_curl_adjoint(self._h, _ptr(z), f32, ld, nlev, _ptr(nodes), n, _ptr(xu), _ptr(xv))
+        if rc:
+            raise ValueError("orc_curl_adjoint rc=%d" % rc)
         return xu, xv
 
     def gradient_averaged(self, f):

@@ -28,7 +28,8 @@ PROJECTIONS = {"rotated_lonlat": capi.ATLAS_PROJ_ROTATED_LONLAT, "mercator": cap
 OPS = {"gradient": capi.ATLAS_OP_GRADIENT, "divergence": capi.ATLAS_OP_DIVERGENCE,
        "gradient_adjoint": capi.ATLAS_OP_GRADIENT_ADJOINT,
        "divergence_adjoint": capi.ATLAS_OP_DIVERGENCE_ADJOINT, "laplacian": capi.ATLAS_OP_LAPLACIAN,
-       "curl": capi.ATLAS_OP_CURL, "vector_gradient": capi.ATLAS_OP_VECTOR_GRADIENT}
+       "curl": capi.ATLAS_OP_CURL, "vector_gradient": capi.ATLAS_OP_VECTOR_GRADIENT,
+       "curl_adjoint": capi.ATLAS_OP_CURL_ADJOINT}
 
 
 def _view(ptr, ctype, n, shape=None, dtype=None):
@@ -235,11 +236,56 @@ class Fvm:
                                      w.ctypes.data, b.ctypes.data)
         return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
 
+    def group_table(self, op):
+        """The FP64 node-group table of one operator (host only): head
+        [ngroups][4], hdr [nent], w [nent][4][2] (see atlas_fvm_group_table)."""
+        code = OPS.get(op, op)
+        ng, ne = ctypes.c_int64(), ctypes.c_int64()
+        capi.atlas_fvm_group_table(self.handle, code, ctypes.byref(ng), ctypes.byref(ne), None, None, None)
+        head = np.empty((max(ng.value, 1), 4), np.int32)
+        hdr = np.empty(max(ne.value, 1), np.uint32)
+        w = np.empty((max(ne.value, 1), 4, 2))
+        capi.atlas_fvm_group_table(self.handle, code, None, None, head.ctypes.data, hdr.ctypes.data, w.ctypes.data)
+        return dict(head=head[:ng.value], hdr=hdr[:ne.value], w=w[:ne.value])
+
     def set_launch(self, op, vec=0, batch=0, threads=0, blocks_per_sm=0, tile_passes=0, dtype=-1):
         """Launch shape of one operator for one storage dtype (ATLAS_F32 /
         ATLAS_F64 / ATLAS_BF16) or, with dtype=-1, for all of them."""
         capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
                                   int(blocks_per_sm), int(tile_passes))
+
+    def set_group(self, op, enable=-1, blocks_per_sm=0, dtype=-1):
+        """Use the shared-memory node-group kernels for one operator (enable
+        1 default table layout, 2 merged entries, 3 per-node rows) or the
+        per-node kernels only (0; -1 keeps), with at most blocks_per_sm
+        blocks per SM (1 or 2, 0 keeps), for one storage dtype or, with
+        dtype=-1, all of them."""
+        capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(blocks_per_sm))
+
+    def group_table(self, op):
+        """The FP64 node-group table of one operator (host only): head
+        [ngroups][4], hdr [nent], w [nent][4][2] (see atlas_fvm_group_table)."""
+        code = OPS.get(op, op)
+        ng, ne = ctypes.c_int64(), ctypes.c_int64()
+        capi.atlas_fvm_group_table(self.handle, code, ctypes.byref(ng), ctypes.byref(ne), None, None, None)
+        head = np.empty((max(ng.value, 1), 4), np.int32)
+        hdr = np.empty(max(ne.value, 1), np.uint32)
+        w = np.empty((max(ne.value, 1), 4, 2))
+        capi.atlas_fvm_group_table(self.handle, code, None, None, head.ctypes.data, hdr.ctypes.data, w.ctypes.data)
+        return dict(head=head[:ng.value], hdr=hdr[:ne.value], w=w[:ne.value])
+
+    def set_launch(self, op, vec=0, batch=0, threads=0, blocks_per_sm=0, tile_passes=0, dtype=-1):
+        """Launch shape of one operator for one storage dtype (ATLAS_F32 /
+        ATLAS_F64 / ATLAS_BF16) or, with dtype=-1, for all of them."""
+        capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
+                                  int(blocks_per_sm), int(tile_passes))
+
+    def set_group(self, op, enable=-1, threads=0, blocks_per_sm=0, prefetch_nodes=-2, dtype=-1):
+        """Node-group kernel settings of one operator (FP32 and BF16 fields):
+        enable 1/0 (-1 keeps), threads per block, blocks per SM cap, L2
+        prefetch distance in nodes (-1 automatic, 0 off, -2 keeps)."""
+        capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(threads),
+                                 int(blocks_per_sm), int(prefetch_nodes))
 
     # ---------------------------------------------------------- operators
     def _check(self, *ts):
@@ -296,6 +342,13 @@ class Fvm:
                               u.shape[1] if nlev is None else nlev, ld, dt, _stream())
         return z
 
+    def curl_adjoint(self, z, nlev=None, out=None):
+        u, v = out if out is not None else (self._out(z, None), self._out(z, None))
+        dt, ld = self._check(z, u, v)
+        capi.atlas_nabla_curl_adjoint(self.handle, z.data_ptr(), u.data_ptr(), v.data_ptr(),
+                                      z.shape[1] if nlev is None else nlev, ld, dt, _stream())
+        return u, v
+
     def integral(self, x, nlev=None, node0=0, count=None, out=None, ws=None):
         """FP64 volume-weighted sums over nodes node0 .. node0+count-1 of the
         rows of x (x's first row is node node0's): a float64 CUDA tensor
@@ -329,13 +382,15 @@ class Fvm:
         n = capi.atlas_nabla_workspace_bytes(self.handle, OPS.get(op, op), 0, int(ld), int(dtype_code))
         return torch.empty(max(int(n), 256), dtype=torch.uint8, device="cuda")
 
-    def gradient_edges(self, f, nlev=None, ws=None, out=None):
+    def gradient_edges(self, f, nlev=None, ws=None, out=None, averaged=False):
+        """Edge-flux + node-gather gradient; averaged=True takes the edge flux
+        in the averaged form S_e (f_a + f_b)/2 instead of the difference form."""
         gx, gy = out if out is not None else (self._out(f, None), self._out(f, None))
         dt, ld = self._check(f, gx, gy)
         ws = self.workspace("gradient", ld, dt) if ws is None else ws
-        capi.atlas_nabla_gradient_edges(self.handle, f.data_ptr(), gx.data_ptr(), gy.data_ptr(), ws.data_ptr(),
-                                        ws.numel() * ws.element_size(), f.shape[1] if nlev is None else nlev,
-                                        ld, dt, _stream())
+        call = capi.atlas_nabla_gradient_edges_averaged if averaged else capi.atlas_nabla_gradient_edges
+        call(self.handle, f.data_ptr(), gx.data_ptr(), gy.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(),
+             f.shape[1] if nlev is None else nlev, ld, dt, _stream())
         return gx, gy
 
     def divergence_edges(self, u, v, nlev=None, ws=None, out=None):
@@ -461,6 +516,14 @@ def build_fvm_regional(projection: str, nx: int, ny: int, xmin: float, xmax: flo
     return Fvm(Mesh(g), radius)
 
 
+def kernel_status(clear=True):
+    """The device error word of the node-group kernels (0: no kernel gave up
+    a wait); waits for the device.  clear resets it."""
+    code = ctypes.c_uint(0)
+    capi.atlas_kernel_status(ctypes.byref(code), 1 if clear else 0)
+    return code.value
+
+
 def field_sync(dst, src, nbytes, direction, stream=None):
     """One cudaMemcpyAsync (0 = H2D, 1 = D2H, 2 = D2D) on torch's current stream."""
     capi.atlas_field_sync(dst, src, int(nbytes), int(direction), _stream() if stream is None else stream)
@@ -504,8 +567,8 @@ def _make_autograd():
             return u_bar, v_bar, None
 
     class CurlFn(torch.autograd.Function):
-        """z = curl (u, v) = D (v, -u); backward (u_bar, v_bar) = (-b, a) with
-        (a, b) = D^T z_bar, by the divergence adjoint kernel."""
+        """z = curl (u, v); backward (u_bar, v_bar) = C^T z_bar by the curl
+        adjoint kernel."""
 
         @staticmethod
         def forward(ctx, u, v, fvm):
@@ -516,8 +579,8 @@ def _make_autograd():
         @staticmethod
         def backward(ctx, z_bar):
             z_bar = z_bar.contiguous()
-            a, b = ctx.fvm.divergence_adjoint(z_bar, out=(torch.zeros_like(z_bar), torch.zeros_like(z_bar)))
-            return -b, a, None
+            u_bar, v_bar = ctx.fvm.curl_adjoint(z_bar, out=(torch.zeros_like(z_bar), torch.zeros_like(z_bar)))
+            return u_bar, v_bar, None
 
     class LaplacianFn(torch.autograd.Function):
         """l = L f with the fused two-ring table L = D G; backward

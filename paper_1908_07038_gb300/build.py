@@ -34,7 +34,7 @@ def _cuda_home() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "remap.cpp", "regional.cpp", "geomio.cpp", "capi.cpp", "kernels.cu", "noalloc.cu")]
+    return [os.path.join(CSRC, f) for f in ("geometry.cpp", "remap.cpp", "regional.cpp", "geomio.cpp", "capi.cpp", "kernels.cu", "group.cu", "noalloc.cu")]
 
 
 def _headers():

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libatlasgb.so")
 ATLAS_F32, ATLAS_F64, ATLAS_BF16 = 0, 1, 2
 ATLAS_OP_GRADIENT, ATLAS_OP_DIVERGENCE, ATLAS_OP_GRADIENT_ADJOINT = 0, 1, 2
 ATLAS_OP_DIVERGENCE_ADJOINT, ATLAS_OP_LAPLACIAN = 3, 4
-ATLAS_OP_CURL, ATLAS_OP_VECTOR_GRADIENT = 5, 6
+ATLAS_OP_CURL, ATLAS_OP_VECTOR_GRADIENT, ATLAS_OP_CURL_ADJOINT = 5, 6, 7
 ATLAS_PROJ_ROTATED_LONLAT, ATLAS_PROJ_MERCATOR, ATLAS_PROJ_LAMBERT_CONFORMAL = 0, 1, 2
 ATLAS_PROJ_POLAR_STEREOGRAPHIC = 3
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EALIGN", -5: "EDTYPE", -6: "ESTATE"}
@@ -64,6 +64,10 @@ _SIGS = {
     "atlas_fvm_info": (I32, [P, PP, PP, PP, PP], True),
     "atlas_fvm_prepare": (I32, [P, ctypes.c_uint, ctypes.c_uint], True),
     "atlas_fvm_set_launch": (I32, [P, I32, I32, I32, I32, I32, I32, I32], True),
+    "atlas_fvm_set_group": (I32, [P, I32, I32, I32, I32], True),
+    "atlas_kernel_status": (I32, [ctypes.POINTER(ctypes.c_uint), I32], True),
+    "atlas_debug_tile_hang": (I32, [I32], True),
+    "atlas_fvm_group_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P, P], True),
     "atlas_fvm_stencil_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                                       P, P, P, P], True),
     "atlas_fvm_destroy": (None, [P], False),
@@ -73,6 +77,7 @@ _SIGS = {
     "atlas_nabla_gradient_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_divergence_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_curl": (I32, [P, P, P, P, I32, I64, I32, P], True),
+    "atlas_nabla_curl_adjoint": (I32, [P, P, P, P, I32, I64, I32, P], True),
     "atlas_grid_regular_gaussian": (I32, [I32, P], True),
     "atlas_grid_regional": (I32, [I32, I32, I32, P, PP], True),
     "atlas_grid_regional_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32), PP, PP],
@@ -99,6 +104,7 @@ _SIGS = {
     "atlas_nabla_vector_gradient": (I32, [P, P, P, P, P, P, P, I32, I64, I32, P], True),
     "atlas_nabla_workspace_bytes": (SZ, [P, I32, I32, I64, I32], False),
     "atlas_nabla_gradient_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),
+    "atlas_nabla_gradient_edges_averaged": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),
     "atlas_nabla_divergence_edges": (I32, [P, P, P, P, P, SZ, I32, I64, I32, P], True),
     "atlas_nabla_laplacian_edges": (I32, [P, P, P, P, SZ, I32, I64, I32, P], True),
     "atlas_nabla_laplacian_edges_noalloc": (I32, [P, P, P, I32, I64, I32, P], True),

@@ -122,10 +122,21 @@ std::vector<A> convert(const std::vector<double>& v) {
   return out;
 }
 
+// Tile tables of one operator for the shared-memory node-group kernels
+// (FP32 and BF16 fields): built with the per-node tables when the stencil
+// allows (ascending rows, node ids below 2^28, few row runs per tile), else
+// absent and the per-node kernels run.
+struct GroupTables {
+  bool ok = false;
+  atlasgb::DevTiles dev;
+  DevAlloc mem;
+  std::vector<int64_t> first;  // first node of every tile, then nnodes
+};
 struct OpTables {
   bool ready = false;
   atlasgb::DevStencil dev;
   DevAlloc mem;
+  GroupTables grp;
 };
 struct EdgeTables {
   bool ready = false;
@@ -138,6 +149,9 @@ struct LaunchCfg {
   int threads = 128;
   int blocks_per_sm = 0;  // 0 = occupancy limit
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
+  int group = 1;          // shared-memory node-group kernel where it applies: 1 default layout, 2 merged,
+                          // 3 per-node rows; 0 per-node kernel only
+  int tile_bps = 2;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
 };
 
 // Launch shape an fvm starts with, per operator and storage dtype: the
@@ -169,7 +183,7 @@ struct atlas_fvm_s {
   int num_sms = 0;
   std::mutex mu;
   OpTables st[atlasgb::OP_COUNT][3];  // [op][storage dtype: F32, F64, BF16]
-  EdgeTables eg[2][2];                // [gradient, divergence][precision]
+  EdgeTables eg[3][2];                // [gradient, divergence, averaged-form gradient][precision]
   LaunchCfg cfg[atlasgb::OP_COUNT][3];  // [op][storage dtype], defaults from default_launch
   DevAlloc vmem;                       // FP64 dual volumes on the device (integrals)
   const double* d_V = nullptr;
@@ -195,6 +209,60 @@ int check_device(atlas_fvm_s* f) {
   return ATLAS_OK;
 }
 
+// Groups of a tile: seven, with one consumer warp each and a producer warp
+// (256 threads).
+constexpr int kGroupsPerTile = 7;
+
+// Testing hook (atlas_debug_tile_hang): the next tile-kernel launches make
+// their consumers wait on a barrier that nothing completes, with a short
+// limit, so that the time-out path runs (no GPU fault, no hang).
+std::atomic<int> g_tile_hang{0};
+
+// Default table layout of the tile kernels: the two-ring Laplacian shares
+// most of its neighbours between the nodes of a group (8.5 merged entries
+// per node against 18), the one-ring operators little (4 against 6), where
+// the per-node rows save the merged form's zero-weight arithmetic.
+int default_tile_mode(const atlasgb::Stencil& s) { return s.scalar_w ? atlasgb::kTileMerged : atlasgb::kTileRows; }
+
+// Build and upload the tile tables of a stencil for float weights.  A
+// stencil the tile layout cannot take leaves them absent (not an error);
+// allocation failures are errors.
+int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int mode) {
+  GroupTables& g = t.grp;
+  atlasgb::GroupStencil gs;
+  atlasgb::TileStencil ts;
+  try {
+    if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs)) return ATLAS_OK;
+    if (!atlasgb::build_tile_stencil(gs, s, kGroupsPerTile, mode < 0 ? default_tile_mode(s) : mode, ts))
+      return ATLAS_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+  }
+  const int64_t nt = static_cast<int64_t>(ts.first.size()) - 1;
+  if (nt >= INT32_MAX) return ATLAS_OK;
+  cudaError_t err = cudaSuccess;
+  g.dev.head = g.mem.upload(ts.head, err);
+  if (err == cudaSuccess) g.dev.blob = g.mem.upload(ts.blob, err);
+  if (err != cudaSuccess) {
+    g.mem.release();
+    g.dev = atlasgb::DevTiles{};
+    return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for operator tables")
+                                            : cuda_fail(err, "upload of operator tables");
+  }
+  g.dev.ntiles = static_cast<int32_t>(nt);
+  g.dev.max_slots = ts.max_slots;
+  g.dev.max_blob = ts.max_blob;
+  g.dev.groups_per_tile = kGroupsPerTile;
+  g.dev.nin = s.nin;
+  g.dev.nout = s.nout;
+  g.dev.nw = ts.nw;
+  g.dev.has_b = s.has_b;
+  g.dev.mode = ts.mode;
+  g.first.swap(ts.first);
+  g.ok = true;
+  return ATLAS_OK;
+}
+
 // Build and upload the stencil tables of op for fields of one storage dtype
 // (double weights for F64 fields, float weights otherwise).
 int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
@@ -209,45 +277,6 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   }
   cudaError_t err = cudaSuccess;
   const int64_t V = f->mesh->grid->g.nnodes;
-  atlasgb::PairStencil ps;
-  if (op == atlasgb::OP_LAP && dtype == ATLAS_F32 && V % 2 == 0) {
-    // the FP32 Laplacian runs on node pairs (merged rows, each shared neighbour
-    // read once); FP64 (ALU-bound) and BF16 measured faster per node
-    try {
-      if (!atlasgb::build_pair_stencil(s, ps)) return fail(ATLAS_EINVAL, "pair table build failed");
-    } catch (const std::bad_alloc&) {
-      return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
-    }
-    t.dev.ptr = t.mem.upload(ps.ptr, err);
-    const size_t np = ps.nbr.size();
-    if (prec) {
-      if (err == cudaSuccess) t.dev.nbr = t.mem.upload(ps.nbr, err);
-      if (err == cudaSuccess) t.dev.w = t.mem.upload(ps.w, err);
-    } else {
-      std::vector<uint32_t> ent(4 * np, 0u);
-      for (size_t q = 0; q < np; ++q) {
-        ent[4 * q] = static_cast<uint32_t>(ps.nbr[q]);
-        const float wa = static_cast<float>(ps.w[2 * q]), wb = static_cast<float>(ps.w[2 * q + 1]);
-        std::memcpy(&ent[4 * q + 1], &wa, 4);
-        std::memcpy(&ent[4 * q + 2], &wb, 4);
-      }
-      if (err == cudaSuccess) t.dev.w = t.mem.upload(ent, err);
-    }
-    if (err != cudaSuccess) {
-      t.mem.release();
-      return err == cudaErrorMemoryAllocation ? fail(ATLAS_ENOMEM, "device allocation failed for operator tables")
-                                              : cuda_fail(err, "upload of operator tables");
-    }
-    t.dev.nnodes = static_cast<int32_t>(V);
-    t.dev.nnz = static_cast<int64_t>(np);
-    t.dev.nin = 1;
-    t.dev.nout = 1;
-    t.dev.has_b = false;
-    t.dev.scalar_w = true;
-    t.dev.pair = true;
-    t.ready = true;
-    return ATLAS_OK;
-  }
   t.dev.ptr = t.mem.upload(s.ptr, err);
   const size_t nnz = s.nbr.size();
   if (prec || s.nin == 2) {
@@ -289,11 +318,40 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   t.dev.nout = s.nout;
   t.dev.has_b = s.has_b;
   t.dev.scalar_w = s.scalar_w;
+  if (!prec) {
+    const int rc = build_group_tables(f, s, t, -1);
+    if (rc) {
+      t.mem.release();
+      t.dev = atlasgb::DevStencil{};
+      return rc;
+    }
+  }
   t.ready = true;
   return ATLAS_OK;
 }
 
-int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div*/, int prec) {
+// Rebuild the tile tables when the layout asked for with atlas_fvm_set_group
+// (2 merged, 3 per-node rows) differs from the one built (caller holds the
+// fvm lock; the stencil tables exist).
+int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
+  OpTables& t = f->st[op][dtype];
+  const int want = f->cfg[op][dtype].group;
+  if (dtype == ATLAS_F64 || want < 2 || !t.grp.ok) return ATLAS_OK;
+  const int mode = want == 2 ? atlasgb::kTileMerged : atlasgb::kTileRows;
+  if (t.grp.dev.mode == mode) return ATLAS_OK;
+  atlasgb::Stencil s;
+  try {
+    if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+  }
+  // the per-node FP32 B term the tile tables point at stays in t.mem
+  t.grp.mem.release();
+  t.grp = GroupTables{};
+  return build_group_tables(f, s, t, mode);
+}
+
+int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div, 2 averaged-form grad*/, int prec) {
   EdgeTables& t = f->eg[which][prec];
   if (t.ready) return ATLAS_OK;
   const atlasgb::Mesh& m = f->mesh->m;
@@ -301,7 +359,7 @@ int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div*/, int prec) {
     return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
   atlasgb::EdgeGather g;
   try {
-    if (!atlasgb::build_edge_gather(m, f->d, which == 0 ? atlasgb::OP_GRAD : atlasgb::OP_DIV, g))
+    if (!atlasgb::build_edge_gather(m, f->d, which == 1 ? atlasgb::OP_DIV : atlasgb::OP_GRAD, g, which == 2))
       return fail(ATLAS_EINVAL, "edge table build failed");
   } catch (const std::bad_alloc&) {
     return fail(ATLAS_ENOMEM, "host allocation failed while building edge tables");
@@ -310,7 +368,7 @@ int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div*/, int prec) {
   std::vector<double> coef(static_cast<size_t>(3 * E), 0.0), node(static_cast<size_t>(3 * V), 0.0);
   for (int64_t e = 0; e < E; ++e) {
     const double s0 = f->d.S[2 * e], s1 = f->d.S[2 * e + 1];
-    if (which == 0) {
+    if (which != 1) {
       coef[3 * e] = 0.5 * s0;
       coef[3 * e + 1] = 0.5 * s1;
     } else if (!m.is_pole[e]) {
@@ -321,8 +379,8 @@ int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div*/, int prec) {
   }
   for (int64_t i = 0; i < V; ++i) {
     node[3 * i] = g.inv_v[i];
-    node[3 * i + 1] = which == 0 ? g.cos_v[i] : 0.0;
-    node[3 * i + 2] = which == 0 ? 0.0 : g.pole_coef[i];
+    node[3 * i + 1] = which != 1 ? g.cos_v[i] : 0.0;
+    node[3 * i + 2] = which != 1 ? 0.0 : g.pole_coef[i];
   }
   cudaError_t err = cudaSuccess;
   t.dev.e2n = t.mem.upload(m.e2n, err);
@@ -424,6 +482,58 @@ int grid_blocks(atlas_fvm_s* f, StorageType st, const atlasgb::DevStencil& s, in
 
 atlas_fvm_s* get_fvm(atlas_fvm_t h) { return live(h) ? reinterpret_cast<atlas_fvm_s*>(h) : nullptr; }
 
+// Level layout of the node-group kernels: part A holds va levels per lane
+// (32 va per level block), part B vb; the narrowest pair whose block covers
+// nlev levels, within the vector width the rows' alignment allows (vmax).
+void group_layout(int nlev, int vmax, int& va, int& vb) {
+  if (vmax >= 4) {
+    if (nlev <= 32) { va = 1; vb = 0; }
+    else if (nlev <= 64) { va = 2; vb = 0; }
+    else if (nlev <= 96) { va = 2; vb = 1; }
+    else if (nlev <= 128) { va = 4; vb = 0; }
+    else if (nlev <= 160) { va = 4; vb = 1; }
+    else { va = 4; vb = 2; }
+  } else if (vmax >= 2) {
+    if (nlev <= 32) { va = 1; vb = 0; }
+    else if (nlev <= 64) { va = 2; vb = 0; }
+    else { va = 2; vb = 1; }
+  } else {
+    va = 1;
+    vb = 0;
+  }
+}
+
+// Launch of the shared-memory node-group kernel over tiles [t0, t0 + nt)
+// with pointers already shifted to global node ids (see run_stencil_range).
+int run_tiles(atlas_fvm_s* f, const GroupTables& gt, const LaunchCfg& c, StorageType st, const void* in0,
+              const void* in1, void* out0, void* out1, int nlev, int64_t ld, atlas_dtype dtype,
+              const void* const* used, int nu, int32_t t0, int32_t nt, void* stream) {
+  if (nt == 0) return ok();
+  atlasgb::TileLaunch l;
+  l.in0 = in0;
+  l.in1 = in1;
+  l.out0 = out0;
+  l.out1 = out1;
+  l.nlev = nlev;
+  l.ld = ld;
+  group_layout(nlev, pick_vec(dtype, ld, used, nu, 4), l.va, l.vb);
+  // padding levels written as zeros: up to the end of the widest vector
+  // the rows allow (the per-node kernels' rule)
+  const int vpad = pick_vec(dtype, ld, used, nu, 0);
+  l.nstore = static_cast<int32_t>(std::min<int64_t>(ld, (nlev + vpad - 1) / vpad * vpad));
+  l.t0 = t0;
+  l.ntiles = nt;
+  l.sms = f->num_sms;
+  l.max_bps = c.tile_bps;
+  if (g_tile_hang.load()) {
+    l.hang_test = 1;
+    l.wait_limit = 1ll << 22;  // a few milliseconds
+  }
+  cudaError_t e = atlasgb::launch_tiles(st, gt.dev, l, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "node-group kernel launch");
+  return ok();
+}
+
 // One fused node-stencil operator over nodes [node0, node0 + count).  The
 // input fields hold the nodes from in_first on (their row 0 is node
 // in_first, in_nodes rows), the outputs the nodes from node0 on (count
@@ -436,7 +546,9 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   const void* ins[2] = {in0, in1};
   void* outs[2] = {out0, out1};
   const int nin = (op == atlasgb::OP_DIV || op == atlasgb::OP_GRAD_ADJ || op == atlasgb::OP_CURL) ? 2 : 1;
-  const int nout = (op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) ? 2 : 1;
+  const int nout =
+      (op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD || op == atlasgb::OP_CURL_ADJ) ? 2
+                                                                                                                  : 1;
   const void* used[4];
   int nu = 0;
   for (int k = 0; k < nin; ++k) used[nu++] = ins[k];
@@ -453,16 +565,32 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
     std::lock_guard<std::mutex> lk(f->mu);
     rc = ensure_stencil(f, op, dtype);
     if (rc) return rc;
+    rc = ensure_tile_layout(f, op, dtype);
+    if (rc) return rc;
   }
   const atlasgb::DevStencil& dev = f->st[op][dtype].dev;
-  if (dev.pair && ((node0 | count) & 1))
-    return fail(ATLAS_EINVAL, "the node-pair tables need an even first node and node count");
+  const GroupTables& gt = f->st[op][dtype].grp;
   auto shift = [&](const void* p, int64_t first) -> const void* {
     return p ? reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(p) -
                                              static_cast<uintptr_t>(first * ld * es))
              : nullptr;
   };
   const LaunchCfg& c = f->cfg[op][dtype];
+  const StorageType st = storage_of(dtype);
+  if (gt.ok && c.group && (ld * es) % 16 == 0 && atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
+    // the shared-memory node-group kernel: TMA copies need 16-byte aligned
+    // rows, and the range must be made of whole tiles
+    bool aligned = true;
+    for (int k = 0; k < nu; ++k)
+      if (reinterpret_cast<uintptr_t>(used[k]) % 16 != 0) aligned = false;
+    const auto a = std::lower_bound(gt.first.begin(), gt.first.end(), node0);
+    const auto b = std::lower_bound(gt.first.begin(), gt.first.end(), node0 + count);
+    if (aligned && a != gt.first.end() && *a == node0 && b != gt.first.end() && *b == node0 + count)
+      return run_tiles(f, gt, c, st, shift(in0, in_first), nin == 2 ? shift(in1, in_first) : nullptr,
+                       const_cast<void*>(shift(out0, node0)), nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr,
+                       nlev, ld, dtype, used, nu, static_cast<int32_t>(a - gt.first.begin()),
+                       static_cast<int32_t>(b - a), stream);
+  }
   atlasgb::StencilLaunch l;
   l.in0 = shift(in0, in_first);
   l.in1 = nin == 2 ? shift(in1, in_first) : nullptr;
@@ -479,13 +607,11 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
     return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
   l.threads = c.threads;
   l.batch = c.batch;
-  const StorageType st = storage_of(dtype);
   l.blocks = grid_blocks(f, st, dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
   {
-    // items the kernel walks (node pairs for a pair table); a tile is at most
-    // one block's even share, so blocks * tile stays below 2^31 + blocks * threads
-    const int64_t walked = dev.pair ? items / 2 : items;
-    const int64_t share = ((walked + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
+    // a tile is at most one block's even share, so blocks * tile stays
+    // below 2^31 + blocks * threads
+    const int64_t share = ((items + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
     l.tile = static_cast<uint32_t>(std::max<int64_t>(l.threads, std::min<int64_t>(int64_t(c.tile_passes) * l.threads, share)));
   }
   cudaError_t e = atlasgb::launch_stencil(st, dev, l, static_cast<cudaStream_t>(stream));
@@ -552,11 +678,12 @@ int run_edges_op(atlas_fvm_s* f, int which, const void* in0, const void* in1, vo
   if (E.nedges * nvec >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nedges * level-vectors must stay below 2^31");
   const int threads = 256;
   const StorageType st = storage_of(dtype);
-  cudaError_t e = atlasgb::launch_edge_flux(st, which, E, in0, in1, ws + w.flux0, which == 0 ? ws + w.flux1 : nullptr,
+  const bool grad = which != 1;
+  cudaError_t e = atlasgb::launch_edge_flux(st, which, E, in0, in1, ws + w.flux0, grad ? ws + w.flux1 : nullptr,
                                             nlev, ld, vec, threads, edge_blocks(f, E.nedges * nvec, threads), stream);
   if (e != cudaSuccess) return cuda_fail(e, "edge-flux kernel launch");
-  e = atlasgb::launch_node_gather(st, which, E, ws + w.flux0, which == 0 ? ws + w.flux1 : nullptr,
-                                  which == 1 ? in1 : nullptr, out0, which == 0 ? out1 : nullptr, nlev, ld, vec, threads,
+  e = atlasgb::launch_node_gather(st, grad ? 0 : 1, E, ws + w.flux0, grad ? ws + w.flux1 : nullptr,
+                                  which == 1 ? in1 : nullptr, out0, grad ? out1 : nullptr, nlev, ld, vec, threads,
                                   edge_blocks(f, static_cast<int64_t>(E.nnodes) * nvec, threads), stream);
   if (e != cudaSuccess) return cuda_fail(e, "node-gather kernel launch");
   return ATLAS_OK;
@@ -968,6 +1095,63 @@ int atlas_fvm_set_launch(atlas_fvm_t h, int op, int dtype, int vec, int batch, i
   return ok();
 }
 
+int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks_per_sm) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (dtype != -1 && !valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "dtype must be -1 (all) or an atlas_dtype");
+  if (enable < -1 || enable > 3) return fail(ATLAS_EINVAL, "enable must be -1, 0, 1, 2 or 3");
+  if (blocks_per_sm < 0 || blocks_per_sm > 2) return fail(ATLAS_EINVAL, "blocks_per_sm must be 0, 1 or 2");
+  std::lock_guard<std::mutex> lk(f->mu);
+  for (int d = 0; d < 3; ++d) {
+    if (dtype != -1 && d != dtype) continue;
+    if (enable >= 0) f->cfg[op][d].group = enable;
+    if (blocks_per_sm) f->cfg[op][d].tile_bps = blocks_per_sm;
+  }
+  return ok();
+}
+
+int atlas_kernel_status(unsigned* code, int clear) {
+  if (!code) return fail(ATLAS_EINVAL, "code is NULL");
+  *code = 0;
+  cudaError_t e = atlasgb::tile_error(code, clear != 0);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the kernels' error word");
+  return ok();
+}
+
+int atlas_debug_tile_hang(int on) {
+  g_tile_hang.store(on ? 1 : 0);
+  return ok();
+}
+
+int atlas_fvm_group_table(atlas_fvm_t h, int op, int64_t* ngroups, int64_t* nent, int32_t* head, uint32_t* hdr,
+                          double* w) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  atlasgb::Stencil s;
+  atlasgb::GroupStencil gs;
+  try {
+    if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
+    if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs))
+      return fail(ATLAS_EINVAL, "this stencil has no node-group table");
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+  }
+  const int64_t ng = static_cast<int64_t>(gs.first.size()) - 1, ne = static_cast<int64_t>(gs.hdr.size());
+  if (ngroups) *ngroups = ng;
+  if (nent) *nent = ne;
+  if (head && ng) std::memcpy(head, gs.head.data(), sizeof(int32_t) * 4 * ng);
+  if (hdr && ne) std::memcpy(hdr, gs.hdr.data(), sizeof(uint32_t) * ne);
+  if (w && ne) {
+    for (int64_t k = 0; k < ne * atlasgb::kGroup; ++k) {
+      w[2 * k] = gs.w[gs.nw * k];
+      w[2 * k + 1] = gs.nw == 2 ? gs.w[2 * k + 1] : 0.0;
+    }
+  }
+  return ok();
+}
+
 int atlas_fvm_stencil_table(atlas_fvm_t h, int op, int64_t* nnz, int* nin, int* nout, int32_t* ptr, int32_t* nbr,
                             double* w, double* b) {
   atlas_fvm_s* f = get_fvm(h);
@@ -1104,6 +1288,11 @@ int atlas_nabla_curl(atlas_fvm_t fvm, const void* u, const void* v, void* zeta, 
   CallRange range_("atlas_nabla_curl");
   return run_stencil_op(fvm, atlasgb::OP_CURL, u, v, zeta, nullptr, nlev, ld, dtype, stream);
 }
+
+int atlas_nabla_curl_adjoint(atlas_fvm_t fvm, const void* zeta, void* u, void* v, int nlev, int64_t ld,
+                             atlas_dtype dtype, void* stream) {
+  return run_stencil_op(fvm, atlasgb::OP_CURL_ADJ, zeta, nullptr, u, v, nlev, ld, dtype, stream);
+}
 int atlas_nabla_vector_gradient(atlas_fvm_t h, const void* u, const void* v, void* ux, void* uy, void* vx, void* vy,
                                 int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
   CallRange range_("atlas_nabla_vector_gradient");
@@ -1153,6 +1342,32 @@ int atlas_nabla_gradient_edges(atlas_fvm_t h, const void* fin, void* gx, void* g
   if (rc) return rc;
   if (nlev == 0) return ok();
   rc = run_edges_op(f, 0, fin, nullptr, gx, gy, static_cast<char*>(ws), w, nlev, ld, dtype,
+                    static_cast<cudaStream_t>(stream));
+  return rc ? rc : ok();
+}
+
+int atlas_nabla_gradient_edges_averaged(atlas_fvm_t h, const void* fin, void* gx, void* gy, void* ws, size_t ws_bytes,
+                                        int nlev, int64_t ld, atlas_dtype dtype, void* stream) {
+  CallRange range_("atlas_nabla_gradient_edges_averaged");
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (f->mesh->grid->g.regional())
+    return fail(ATLAS_EINVAL, "the edge-based two-pass variant covers global grids only");
+  if (dtype == ATLAS_BF16) return fail(ATLAS_EDTYPE, "the edge-based forms take F32 or F64 fields");
+  const void* used[3] = {fin, gx, gy};
+  int rc = check_field_args(dtype, nlev, ld, used, 3);
+  if (rc) return rc;
+  const void* ins[1] = {fin};
+  void* outs[2] = {gx, gy};
+  rc = check_no_overlap(ins, 1, outs, 2, f->mesh->grid->g.nnodes * ld * elem_size(dtype));
+  if (rc) return rc;
+  WsLayout w;
+  rc = check_ws(f, ATLAS_OP_GRADIENT, ws, ws_bytes, ld, dtype, w);
+  if (rc) return rc;
+  rc = check_device(f);
+  if (rc) return rc;
+  if (nlev == 0) return ok();
+  rc = run_edges_op(f, 2, fin, nullptr, gx, gy, static_cast<char*>(ws), w, nlev, ld, dtype,
                     static_cast<cudaStream_t>(stream));
   return rc ? rc : ok();
 }

@@ -455,6 +455,13 @@ double div_vdiag(const Mesh& m, const Dual& d, int64_t i) {
 
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
   if (m.grid->regional()) return build_regional_stencil(m, d, op, s);
+  if (op == OP_CURL_ADJ) {
+    // the exact transpose of the curl's table (its faces are the regular
+    // edges, a symmetric pattern)
+    Stencil c;
+    if (!build_stencil(m, d, OP_CURL, c)) return false;
+    return transpose_stencil(c, s);
+  }
   const int64_t V = m.grid->nnodes;
   s.ptr.assign(static_cast<size_t>(V) + 1, 0);
   const bool regular_only = (op == OP_DIV || op == OP_DIV_ADJ || op == OP_CURL);
@@ -630,49 +637,252 @@ bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
   return true;
 }
 
-bool build_pair_stencil(const Stencil& s, PairStencil& p) {
+bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs) {
   const int64_t V = static_cast<int64_t>(s.ptr.size()) - 1;
-  if (V % 2 != 0 || !s.scalar_w) return false;
-  const int64_t G = V / 2;
-  p.ptr.assign(static_cast<size_t>(G) + 1, 0);
-  // rows are sorted by neighbour id: merge the two rows of every pair
-  for (int64_t g = 0; g < G; ++g) {
-    int32_t qa = s.ptr[2 * g], ea = s.ptr[2 * g + 1], qb = s.ptr[2 * g + 1], eb = s.ptr[2 * g + 2];
-    for (int32_t q = qa + 1; q < ea; ++q)
+  if (V != g.nnodes || static_cast<int64_t>(g.off.size()) != g.nlat + 1 || V >= (int64_t(1) << 28)) return false;
+  for (int64_t i = 0; i < V; ++i)
+    for (int32_t q = s.ptr[i] + 1; q < s.ptr[i + 1]; ++q)
       if (s.nbr[q] <= s.nbr[q - 1]) return false;
-    for (int32_t q = qb + 1; q < eb; ++q)
-      if (s.nbr[q] <= s.nbr[q - 1]) return false;
-    int32_t c = 0;
-    while (qa < ea || qb < eb) {
-      if (qb == eb || (qa < ea && s.nbr[qa] < s.nbr[qb])) ++qa;
-      else if (qa == ea || s.nbr[qb] < s.nbr[qa]) ++qb;
-      else { ++qa; ++qb; }
-      ++c;
+  const int nw = s.scalar_w ? 1 : 2;
+  gs.nw = nw;
+  // groups: every row cut into runs of kGroup nodes (the last one shorter)
+  gs.first.clear();
+  gs.row_start.clear();
+  for (int r = 0; r < g.nlat; ++r)
+    for (int64_t i = g.off[r]; i < g.off[r + 1]; i += kGroup) {
+      gs.row_start.push_back(i == g.off[r] ? 1 : 0);
+      gs.first.push_back(i);
     }
-    if (static_cast<int64_t>(p.ptr[g]) + c > INT32_MAX) return false;
-    p.ptr[g + 1] = p.ptr[g] + c;
+  const int64_t ng = static_cast<int64_t>(gs.first.size());
+  gs.first.push_back(V);
+  // merged rows: sizes first, then contents
+  std::vector<int32_t> len(static_cast<size_t>(ng));
+  auto merged = [&](int64_t gi, std::vector<int32_t>& cols) {
+    cols.clear();
+    for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i)
+      for (int32_t q = s.ptr[i]; q < s.ptr[i + 1]; ++q) cols.push_back(s.nbr[q]);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+  };
+#pragma omp parallel
+  {
+    std::vector<int32_t> cols;
+#pragma omp for schedule(static)
+    for (int64_t gi = 0; gi < ng; ++gi) {
+      merged(gi, cols);
+      len[gi] = static_cast<int32_t>(cols.size());
+    }
   }
-  p.nbr.resize(static_cast<size_t>(p.ptr[G]));
-  p.w.assign(static_cast<size_t>(2 * p.ptr[G]), 0.0);
-#pragma omp parallel for schedule(static)
-  for (int64_t g = 0; g < G; ++g) {
-    int32_t qa = s.ptr[2 * g], ea = s.ptr[2 * g + 1], qb = s.ptr[2 * g + 1], eb = s.ptr[2 * g + 2];
-    int32_t o = p.ptr[g];
-    while (qa < ea || qb < eb) {
-      if (qb == eb || (qa < ea && s.nbr[qa] < s.nbr[qb])) {
-        p.nbr[o] = s.nbr[qa]; p.w[2 * o] = s.w[2 * qa]; ++qa;
-      } else if (qa == ea || s.nbr[qb] < s.nbr[qa]) {
-        p.nbr[o] = s.nbr[qb]; p.w[2 * o + 1] = s.w[2 * qb]; ++qb;
-      } else {
-        p.nbr[o] = s.nbr[qa]; p.w[2 * o] = s.w[2 * qa]; p.w[2 * o + 1] = s.w[2 * qb]; ++qa; ++qb;
+  gs.head.assign(static_cast<size_t>(4 * ng), 0);
+  int64_t nent = 0;
+  for (int64_t gi = 0; gi < ng; ++gi) {
+    gs.head[4 * gi + 1] = static_cast<int32_t>(nent);
+    nent += len[gi];
+    if (nent > INT32_MAX) return false;
+    gs.head[4 * gi + 2] = static_cast<int32_t>(nent);
+  }
+  gs.hdr.assign(static_cast<size_t>(nent), 0u);
+  gs.w.assign(static_cast<size_t>(nent) * kGroup * nw, 0.0);
+#pragma omp parallel
+  {
+    std::vector<int32_t> cols;
+#pragma omp for schedule(static)
+    for (int64_t gi = 0; gi < ng; ++gi) {
+      merged(gi, cols);
+      const int64_t f = gs.first[gi];
+      const int count = static_cast<int>(gs.first[gi + 1] - f);
+      const int32_t q0 = gs.head[4 * gi + 1];
+      int nb = 0, imask = 0;
+      for (size_t k = 0; k < cols.size(); ++k) {
+        if (cols[k] < f) ++nb;
+        else if (cols[k] < f + count) imask |= 1 << (cols[k] - f);
       }
-      ++o;
+      for (int t = 0; t < count; ++t) {
+        const int64_t i = f + t;
+        // both lists are ascending: walk them together
+        size_t k = 0;
+        for (int32_t q = s.ptr[i]; q < s.ptr[i + 1]; ++q) {
+          while (cols[k] != s.nbr[q]) ++k;
+          const size_t e = static_cast<size_t>(q0) + k;
+          gs.hdr[e] |= 1u << (28 + t);
+          for (int c = 0; c < nw; ++c) gs.w[(e * kGroup + t) * nw + c] = s.w[2 * static_cast<int64_t>(q) + c];
+        }
+      }
+      for (size_t k = 0; k < cols.size(); ++k) gs.hdr[static_cast<size_t>(q0) + k] |= static_cast<uint32_t>(cols[k]);
+      gs.head[4 * gi] = static_cast<int32_t>(f);
+      gs.head[4 * gi + 3] = nb | (count << 16) | (imask << 20);
     }
   }
   return true;
 }
 
-bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg) {
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, int mode, TileStencil& ts) {
+  const int64_t ng = static_cast<int64_t>(gs.first.size()) - 1;
+  const int nw = gs.nw;
+  ts.nw = nw;
+  ts.groups_per_tile = groups_per_tile;
+  ts.mode = mode;
+  // tiles: up to groups_per_tile consecutive groups of one grid row
+  std::vector<int64_t> tg;  // first group of every tile
+  for (int64_t gi = 0; gi < ng;) {
+    tg.push_back(gi);
+    int64_t k = gi + 1;
+    while (k < ng && k - gi < groups_per_tile && !gs.row_start[k]) ++k;
+    gi = k;
+  }
+  const int64_t nt = static_cast<int64_t>(tg.size());
+  tg.push_back(ng);
+  ts.head.assign(static_cast<size_t>(nt * kTileHead), 0);
+  ts.first.resize(static_cast<size_t>(nt + 1));
+  std::vector<std::vector<uint32_t>> blobs(static_cast<size_t>(nt));
+  bool fits = true;
+  int32_t max_slots = 0, max_blob = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : max_slots, max_blob)
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t ga = tg[t], gb = tg[t + 1];
+    const int ngt = static_cast<int>(gb - ga);
+    // the node ids the tile reads: own nodes and every neighbour, ascending
+    std::vector<int32_t> ids;
+    for (int64_t gi = ga; gi < gb; ++gi) {
+      for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i) ids.push_back(static_cast<int32_t>(i));
+      for (int32_t q = gs.head[4 * gi + 1]; q < gs.head[4 * gi + 2]; ++q)
+        ids.push_back(static_cast<int32_t>(gs.hdr[q] & 0x0fffffffu));
+    }
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    int32_t* h = &ts.head[static_cast<size_t>(t * kTileHead)];
+    int nr = 0;
+    for (size_t k = 0; k < ids.size();) {
+      size_t e = k + 1;
+      while (e < ids.size() && ids[e] == ids[e - 1] + 1) ++e;
+      if (nr == kTileRanges) {
+        nr = kTileRanges + 1;
+        break;
+      }
+      h[8 + 4 * nr] = ids[k];
+      h[8 + 4 * nr + 1] = static_cast<int32_t>(e - k);
+      h[8 + 4 * nr + 2] = static_cast<int32_t>(k);
+      ++nr;
+      k = e;
+    }
+    if (nr > kTileRanges) {
+#pragma omp critical
+      fits = false;
+      continue;
+    }
+    auto slot = [&](int32_t j) {
+      return static_cast<uint32_t>(std::lower_bound(ids.begin(), ids.end(), j) - ids.begin());
+    };
+    const int32_t q_base = gs.head[4 * ga + 1];
+    const int32_t nent = gs.head[4 * (gb - 1) + 2] - q_base;
+    const int32_t nent_pad = (nent + 3) & ~3;
+    const bool has_b = s.has_b;
+    std::vector<uint32_t>& b = blobs[t];
+    auto put_f = [&](size_t at, double v) {
+      const float x = static_cast<float>(v);
+      std::memcpy(&b[at], &x, 4);
+    };
+    // head part: tile info, group heads, B term
+    const size_t o_b = 4 + 4 * static_cast<size_t>(ngt);
+    const size_t o_data = o_b + (has_b ? 8 * static_cast<size_t>(ngt) : 0);
+    b.assign(o_data, 0u);
+    b[0] = static_cast<uint32_t>(ngt);
+    b[2] = static_cast<uint32_t>(gs.first[ga]);
+    b[3] = static_cast<uint32_t>(mode);
+    for (int k = 0; k < ngt; ++k) {
+      const int64_t gi = ga + k;
+      if (has_b)
+        for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i)
+          for (int c = 0; c < 2; ++c) put_f(o_b + 8 * static_cast<size_t>(k) + 2 * static_cast<size_t>(i - gs.first[gi]) + c, s.b[2 * i + c]);
+    }
+    if (mode == kTileMerged) {
+      // merged entries: headers [nent_pad], weights as f32x2 pairs
+      // [nent_pad][4][nw][2]
+      b[1] = static_cast<uint32_t>(nent_pad);
+      const size_t o_h = o_data, o_w = o_h + static_cast<size_t>(nent_pad);
+      b.resize(o_w + static_cast<size_t>(nent_pad) * 8 * nw, 0u);
+      for (int k = 0; k < ngt; ++k) {
+        const int64_t gi = ga + k;
+        b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
+        b[4 + 4 * k + 1] = static_cast<uint32_t>(gs.head[4 * gi + 1] - q_base);
+        b[4 + 4 * k + 2] = static_cast<uint32_t>(gs.head[4 * gi + 2] - q_base);
+        b[4 + 4 * k + 3] = static_cast<uint32_t>(gs.head[4 * gi + 3]);
+      }
+      for (int32_t q = 0; q < nent; ++q) {
+        const uint32_t hv = gs.hdr[q_base + q];
+        b[o_h + q] = slot(static_cast<int32_t>(hv & 0x0fffffffu)) | (hv & 0xf0000000u);
+        for (int k = 0; k < 4 * nw; ++k) {
+          const double v = gs.w[(static_cast<size_t>(q_base + q)) * 4 * nw + k];
+          put_f(o_w + (static_cast<size_t>(q) * 4 * nw + k) * 2, v);
+          put_f(o_w + (static_cast<size_t>(q) * 4 * nw + k) * 2 + 1, v);
+        }
+      }
+    } else {
+      // per-node rows: for group k with D = its nodes' largest row, slots
+      // [D][4] then weights as f32x2 pairs [D][4][nw][2]; entry e of node t
+      // is its row's e-th term, or (own slot, weight 0) past its row's end
+      for (int k = 0; k < ngt; ++k) {
+        const int64_t gi = ga + k;
+        const int cnt = static_cast<int>(gs.first[gi + 1] - gs.first[gi]);
+        int D = 0;
+        for (int u = 0; u < cnt; ++u) {
+          const int64_t i = gs.first[gi] + u;
+          D = std::max(D, static_cast<int>(s.ptr[i + 1] - s.ptr[i]));
+        }
+        const size_t off = b.size();
+        b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
+        b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
+        b[4 + 4 * k + 2] = static_cast<uint32_t>(D);
+        b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt);
+        b.resize(off + static_cast<size_t>(D) * 4 * (1 + 2 * nw), 0u);
+        const size_t o_w = off + static_cast<size_t>(D) * 4;
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = gs.first[gi] + std::min(u, cnt - 1);
+          const uint32_t own = slot(static_cast<int32_t>(i));
+          const int32_t deg = u < cnt ? s.ptr[i + 1] - s.ptr[i] : 0;
+          for (int e = 0; e < D; ++e) {
+            b[off + 4 * static_cast<size_t>(e) + u] = e < deg ? slot(s.nbr[s.ptr[i] + e]) : own;
+            for (int c = 0; c < nw; ++c) {
+              const double v = e < deg ? s.w[2 * static_cast<int64_t>(s.ptr[i] + e) + c] : 0.0;
+              const size_t at = o_w + ((static_cast<size_t>(e) * 4 + u) * nw + c) * 2;
+              put_f(at, v);
+              put_f(at + 1, v);
+            }
+          }
+        }
+      }
+    }
+    b.resize((b.size() + 3) & ~size_t(3), 0u);
+    const size_t words = b.size();
+    h[0] = static_cast<int32_t>(gs.first[ga]);
+    h[1] = ngt;
+    h[2] = nr;
+    h[3] = static_cast<int32_t>(ids.size());
+    h[5] = static_cast<int32_t>(4 * words);
+    ts.first[t] = gs.first[ga];
+    max_slots = std::max(max_slots, static_cast<int32_t>(ids.size()));
+    max_blob = std::max(max_blob, static_cast<int32_t>(4 * words));
+  }
+  if (!fits) return false;
+  ts.first[nt] = gs.first[ng];
+  size_t total = 0;
+  for (int64_t t = 0; t < nt; ++t) {
+    ts.head[static_cast<size_t>(t * kTileHead) + 4] = static_cast<int32_t>(total / 4);
+    total += blobs[t].size();
+    if (total / 4 > static_cast<size_t>(INT32_MAX)) return false;
+  }
+  ts.blob.resize(total);
+  size_t pos = 0;
+  for (int64_t t = 0; t < nt; ++t) {
+    std::copy(blobs[t].begin(), blobs[t].end(), ts.blob.begin() + static_cast<std::ptrdiff_t>(pos));
+    pos += blobs[t].size();
+  }
+  ts.max_slots = max_slots;
+  ts.max_blob = max_blob;
+  return true;
+}
+
+bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg, bool averaged) {
   if (m.grid->regional()) return false;  // the two-pass variant covers global grids only
   const int64_t V = m.grid->nnodes, E = m.nedges;
   const bool div = (op == OP_DIV);
@@ -694,8 +904,12 @@ bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg) {
       const int32_t e = m.n2e[q];
       if (div && m.is_pole[e]) continue;
       // difference-form edge flux S_e (x_b - x_a)/2 enters both ends with +1;
-      // a pole edge enters its second end with -1 (its normal is the same at both ends)
-      const bool neg = m.is_pole[e] && m.n2e_sign[q] < 0;
+      // a pole edge enters its second end with -1 (its normal is the same at
+      // both ends).  The averaged flux S_e (x_a + x_b)/2 enters the ends of a
+      // regular edge with the sign of the outward normal, +1 at a and -1 at
+      // b, and both ends of a pole edge with +1.
+      const bool second = m.n2e_sign[q] < 0;
+      const bool neg = averaged ? (second && !m.is_pole[e]) : (m.is_pole[e] && second);
       eg.ent[o++] = (e << 1) | (neg ? 1 : 0);
     }
     eg.inv_v[i] = 1.0 / d.V[i];

@@ -97,23 +97,82 @@ enum StencilOp {
   OP_LAP = 4,
   OP_CURL = 5,   // vertical vorticity of (u, v): two inputs, one output
   OP_VGRAD = 6,  // gradient of one component of a tangent vector field
-  OP_COUNT = 7
+  OP_CURL_ADJ = 7,  // adjoint of the curl: one input, two outputs
+  OP_COUNT = 8
 };
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s);
-bool build_edge_gather(const Mesh& m, const Dual& d, int op /*OP_GRAD or OP_DIV*/, EdgeGather& eg);
+// averaged: the gradient's edge flux in the averaged form S_e (x_a + x_b)/2
+// (enters a with +1, b with -1 on regular edges, both ends with +1 on pole
+// edges) instead of the difference form S_e (x_b - x_a)/2.
+bool build_edge_gather(const Mesh& m, const Dual& d, int op /*OP_GRAD or OP_DIV*/, EdgeGather& eg,
+                       bool averaged = false);
 
-// Merged table of a one-input, one-output, scalar-weight stencil over node
-// pairs (2g, 2g+1): the union of the two nodes' rows, sorted by neighbour id,
-// with the weight of each node (0 where the neighbour is not in its row).
-// Each node's own entries keep their ascending-neighbour order, so applying
-// the merged table gives the same sums as the per-node table (zero-weight
-// terms add exact zeros).  Requires an even node count.
-struct PairStencil {
-  std::vector<int32_t> ptr;   // [V/2 + 1]
-  std::vector<int32_t> nbr;   // [nnz]
-  std::vector<double> w;      // [nnz][2] (weight of node 2g, of node 2g+1)
+// Node-group table of a stencil (the warp-per-group kernels).  Each row of
+// the grid is cut into groups of up to kGroup consecutive nodes; a group's
+// table is the union of its nodes' stencil rows, sorted by neighbour id, one
+// entry per distinct neighbour j with a mask of the group's nodes whose row
+// holds j and, for each node of the group, its weight(s) towards j (0 where
+// the mask bit is clear).  Every node therefore meets its own terms in the
+// order of its per-node row, so applying the group table gives the same sums
+// as the per-node table, operation for operation.  The group's own nodes
+// that appear as neighbours form one contiguous run of the sorted entries
+// (ids first .. first + count - 1); the kernels take their values from the
+// registers that already hold them.
+constexpr int kGroup = 4;
+struct GroupStencil {
+  int nw = 1;                   // weights per (entry, node): 1 (scalar weights) or 2
+  // [ng][4]: first node, first entry q0, end entry q1,
+  //          nb | count << 16 | imask << 20, where nb entries precede the
+  //          internal run and imask marks the group's nodes that occur in it
+  std::vector<int32_t> head;
+  std::vector<uint32_t> hdr;    // [nent]: j | mask << 28 (j < 2^28)
+  std::vector<double> w;        // [nent][kGroup][nw]
+  std::vector<int64_t> first;   // [ng + 1]: first node of every group, then nnodes
+  std::vector<uint8_t> row_start;  // [ng]: 1 where the group begins a grid row
 };
-bool build_pair_stencil(const Stencil& s, PairStencil& p);
+// Fails (false) when a per-node row is not strictly ascending, a node id
+// does not fit in 28 bits or the entry count overflows 32 bits; the caller
+// then keeps the per-node kernels.
+bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
+
+// Tile table of the shared-memory node-group kernels, built from a group
+// table.  Every grid row is cut into tiles of up to groups_per_tile
+// consecutive groups.  A tile lists the node rows its groups read (their own
+// nodes and all their neighbours) as at most kTileRanges runs of
+// consecutive node ids; the kernel copies those runs into shared memory in
+// order, so the node with the s-th smallest id of the list sits in slot s.
+// The tile's group table refers to slots instead of node ids.
+//   head[t][kTileHead]: first node, groups, ranges, slots (rows staged),
+//     blob offset (16-byte units), blob bytes, 0, 0, then per range
+//     (first node, count, first slot, 0).
+//   blob: per tile, 16-byte aligned: {groups, entries, first node, mode};
+//     a 16-byte head per group; B term [groups * 4][2] (floats; operators
+//     with one); then, by mode, either
+//     kTileMerged: group heads {slot of its first node, first entry, end
+//       entry, nb | count << 16 | imask << 20} (entries counted from the
+//       tile's first); headers [entries] slot | mask << 28; weights
+//       [entries][4][nw] as f32x2 pairs (each weight twice);
+//     kTileRows: group heads {slot of its first node, word offset of its
+//       data in the blob, D, count}; data: slots [D][4] (entry e of node t:
+//       its row's e-th neighbour, or its own slot past its row's end), then
+//       weights [D][4][nw] as f32x2 pairs (0 past the row's end).
+constexpr int kTileMerged = 0;
+constexpr int kTileRows = 1;
+constexpr int kTileRanges = 16;
+constexpr int kTileHead = 8 + 4 * kTileRanges;
+struct TileStencil {
+  int nw = 1;
+  int mode = kTileRows;
+  int groups_per_tile = 8;
+  std::vector<int32_t> head;      // [ntiles][kTileHead]
+  std::vector<uint32_t> blob;     // 32-bit words
+  std::vector<int64_t> first;     // [ntiles + 1]: first node of every tile, then nnodes
+  int32_t max_slots = 0;          // most rows any tile stages
+  int32_t max_blob = 0;           // largest tile blob (bytes)
+};
+// Fails (false) when a tile needs more than kTileRanges runs (the caller
+// keeps the per-node kernels).
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, int mode, TileStencil& ts);
 
 // Regular (full) Gaussian grid F<N>: the 2N Gaussian latitudes of O<N>, each
 // with 4N longitudes j/(4N) turns.  A remapping target, and meshed by the

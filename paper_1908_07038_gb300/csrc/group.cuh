@@ -1,0 +1,630 @@
+// Shared-memory node-group stencil kernels (sm_103a) for FP32 and bfloat16
+// fields: a TMA producer warp and consumer warps.
+//
+// The node-stencil operators read, for every output value, the values of the
+// node and of its 6-18 stencil neighbours at the same level.  With levels
+// innermost one neighbour row is a contiguous run of nlev values, so the
+// work is a sequence of row gathers.  Every input row leaves HBM about once
+// (the rows of nearby latitudes stay in L2); what limits the per-node
+// kernels is the L1 data pipe, one 128-byte line per cycle and SM, which
+// their gathers use about twice per line of data: a warp spans two nodes and
+// two rows that do not start on line boundaries, and each lane reads the CSR
+// entry of its own node.  These kernels instead
+//   * cut every grid row into tiles of up to 32 (28 for two-input
+//     operators) consecutive nodes and let the host list, per tile, the node
+//     rows the tile reads -- its own and all their neighbours -- as a few
+//     runs of consecutive node ids (the rows above and below, the wrap of
+//     the row, the antipodes of the polar rows);
+//   * have one producer warp copy those runs, and the tile's table, from
+//     global memory into shared memory with TMA bulk copies
+//     (cp.async.bulk, completion counted in bytes on an mbarrier), two tiles
+//     ahead of the consumers, so each row crosses the L1 data pipe once and
+//     the consumers never wait for L2 or DRAM;
+//   * give each consumer warp one group of up to four consecutive nodes of
+//     the tile and all levels: lane l holds levels 4l .. 4l+3 of every row it
+//     reads (part A, one 16-byte shared load) and level 128 + l (part B); the
+//     group's table is the union of its four nodes' stencil rows, so a
+//     neighbour of two or three of them is read once;
+//   * take the values of the group's own nodes, which are also neighbours of
+//     each other, from the registers that hold them;
+//   * do the arithmetic on pairs of levels with the packed FP32 instructions
+//     (sub.rn.f32x2, fma.rn.f32x2): each half rounds as the scalar
+//     instruction does.
+// Every node accumulates its terms in ascending neighbour order with the same
+// subtraction and fused multiply-add as the per-node kernels, so the results
+// are bitwise those of the per-node kernels (the merged entries a node does
+// not use are skipped, not added as zeros).  No atomics: deterministic.
+// Every wait on an mbarrier is bounded: past the limit the kernel records an
+// error code in a device word that the host reads, waits (bounded again) for
+// the copies it issued, and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "geometry.h"
+#include "kernels.h"
+
+namespace atlasgb {
+namespace grp {
+
+// ---------------------------------------------------------------- values
+// N levels of one node row as float: N/2 pairs (the operands of the
+// packed f32x2 instructions) for even N, else one scalar.
+template <int N, bool PAIRS = (N % 2 == 0)> struct Vals {
+  float2 p[N / 2];
+};
+template <int N> struct Vals<N, false> {
+  float s[N];
+};
+template <> struct Vals<0, true> {};
+
+__device__ __forceinline__ float2 pk(float x, float y) { return make_float2(x, y); }
+
+template <int N>
+__device__ __forceinline__ void v_zero(Vals<N>& x) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) x.p[k] = make_float2(0.0f, 0.0f);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) x.s[k] = 0.0f;
+  }
+}
+// d = x - y, as x + (-y) (the same IEEE operation) on pairs
+template <int N>
+__device__ __forceinline__ void v_sub(const Vals<N>& x, const Vals<N>& y, Vals<N>& d) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) d.p[k] = __fadd2_rn(x.p[k], make_float2(-y.p[k].x, -y.p[k].y));
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) d.s[k] = x.s[k] - y.s[k];
+  }
+}
+// acc = fma(w, d, acc), w the same for every level, given as a pair {w, w}
+// (a scalar part uses its first half)
+template <int N>
+__device__ __forceinline__ void v_fma(float2 ww, const Vals<N>& d, Vals<N>& acc) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) acc.p[k] = __ffma2_rn(ww, d.p[k], acc.p[k]);
+  } else {
+    const float w = ww.x;
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc.s[k] = fmaf(w, d.s[k], acc.s[k]);
+  }
+}
+
+// A lane's share of one node row: VA levels of part A and VB of part B.
+template <int VA, int VB> struct Lv {
+  Vals<VA> a;
+  Vals<VB> b;
+};
+template <int VA, int VB>
+__device__ __forceinline__ void lv_zero(Lv<VA, VB>& x) {
+  v_zero<VA>(x.a);
+  if constexpr (VB > 0) v_zero<VB>(x.b);
+}
+template <int VA, int VB>
+__device__ __forceinline__ void lv_sub(const Lv<VA, VB>& x, const Lv<VA, VB>& y, Lv<VA, VB>& d) {
+  v_sub<VA>(x.a, y.a, d.a);
+  if constexpr (VB > 0) v_sub<VB>(x.b, y.b, d.b);
+}
+template <int VA, int VB>
+__device__ __forceinline__ void lv_fma(float2 ww, const Lv<VA, VB>& d, Lv<VA, VB>& acc) {
+  v_fma<VA>(ww, d.a, acc.a);
+  if constexpr (VB > 0) v_fma<VB>(ww, d.b, acc.b);
+}
+
+// N consecutive values of storage type S, as float, from shared memory
+// (32-bit shared-window address)
+template <typename S, int N> struct Ld;
+template <int N> struct Ld<float, N> {
+  static __device__ __forceinline__ void run(uint32_t a, Vals<N>& v) {
+    if constexpr (N == 4) {
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(v.p[0].x), "=f"(v.p[0].y), "=f"(v.p[1].x), "=f"(v.p[1].y)
+                   : "r"(a));
+    } else if constexpr (N == 2) {
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.p[0].x), "=f"(v.p[0].y) : "r"(a));
+    } else {
+      asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v.s[0]) : "r"(a));
+    }
+  }
+};
+template <int N> struct Ld<uint16_t, N> {
+  // bfloat16 -> float is the 16-bit pattern shifted into the high half
+  static __device__ __forceinline__ float2 two(uint32_t t) {
+    return make_float2(__uint_as_float(t << 16), __uint_as_float(t & 0xffff0000u));
+  }
+  static __device__ __forceinline__ void run(uint32_t a, Vals<N>& v) {
+    if constexpr (N == 4) {
+      uint32_t x, y;
+      asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(a));
+      v.p[0] = two(x);
+      v.p[1] = two(y);
+    } else if constexpr (N == 2) {
+      uint32_t x;
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(x) : "r"(a));
+      v.p[0] = two(x);
+    } else {
+      unsigned short x;
+      asm volatile("ld.shared.u16 %0, [%1];" : "=h"(x) : "r"(a));
+      v.s[0] = __uint_as_float(static_cast<uint32_t>(x) << 16);
+    }
+  }
+};
+
+// N values stored whole: levels at or past nlev (the row's padding up to
+// the end of the vector) are written as zeros.
+template <int N>
+__device__ __forceinline__ void v_unpack(const Vals<N>& v, float* e, int nvalid) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      e[2 * k] = 2 * k < nvalid ? v.p[k].x : 0.0f;
+      e[2 * k + 1] = 2 * k + 1 < nvalid ? v.p[k].y : 0.0f;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) e[k] = k < nvalid ? v.s[k] : 0.0f;
+  }
+}
+template <typename S, int N> struct St;
+template <int N> struct St<float, N> {
+  static __device__ __forceinline__ void run(float* __restrict__ p, const Vals<N>& v, int nvalid) {
+    float e[N];
+    v_unpack<N>(v, e, nvalid);
+    if constexpr (N == 4) *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
+    else if constexpr (N == 2) *reinterpret_cast<float2*>(p) = make_float2(e[0], e[1]);
+    else *p = e[0];
+  }
+};
+template <int N> struct St<uint16_t, N> {
+  static __device__ __forceinline__ void run(uint16_t* __restrict__ p, const Vals<N>& v, int nvalid) {
+    float f[N];
+    v_unpack<N>(v, f, nvalid);
+    uint16_t e[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) e[k] = __bfloat16_as_ushort(__float2bfloat16_rn(f[k]));
+    if constexpr (N == 4) {
+      uint2 r;
+      memcpy(&r, e, 8);
+      *reinterpret_cast<uint2*>(p) = r;
+    } else if constexpr (N == 2) {
+      uint32_t r;
+      memcpy(&r, e, 4);
+      *reinterpret_cast<uint32_t*>(p) = r;
+    } else {
+      *p = e[0];
+    }
+  }
+};
+
+// Lane layout of one level block starting at level lev0: part A levels
+// lev0 + VA*lane .. + VA-1, part B levels lev0 + 32*VA + VB*lane .. + VB-1.
+template <int VA, int VB> struct Layout {
+  int offA, offB;  // first level of the lane's part A and part B
+  __device__ __forceinline__ Layout(int lev0, int lane) : offA(lev0 + VA * lane), offB(lev0 + 32 * VA + VB * lane) {}
+};
+
+// One node row's share of this lane from a staged row (rowa: shared address
+// of the row's level 0).  Unconditional: lanes past nlev read the padding
+// of the row, the next row or the stage's slack (in bounds of the block's
+// shared memory) and those values are never stored.
+template <typename S, int VA, int VB>
+__device__ __forceinline__ void lv_load(uint32_t rowa, const Layout<VA, VB>& L, Lv<VA, VB>& x) {
+  constexpr uint32_t ES = sizeof(S);
+  Ld<S, VA>::run(rowa + ES * static_cast<uint32_t>(L.offA), x.a);
+  if constexpr (VB > 0) Ld<S, VB>::run(rowa + ES * static_cast<uint32_t>(L.offB), x.b);
+}
+// Stores cover the levels below nstore: nlev rounded up to the widest
+// vector the row layout allows, so the padding up to the end of the last
+// 16-byte vector is zeroed whatever VA and VB the launch uses.
+template <typename S, int VA, int VB>
+__device__ __forceinline__ void lv_store(S* __restrict__ row, const Layout<VA, VB>& L, int nlev, int nstore,
+                                         const Lv<VA, VB>& x) {
+  if (L.offA < nstore) St<S, VA>::run(row + L.offA, x.a, nlev - L.offA);
+  if constexpr (VB > 0)
+    if (L.offB < nstore) St<S, VB>::run(row + L.offB, x.b, nlev - L.offB);
+}
+
+// N weight pairs {w, w} (8 N bytes, 16-byte aligned for N >= 2) from the
+// staged table: warp-uniform shared loads (broadcasts).
+template <int N> struct Wts { float2 w[N]; };
+template <int N>
+__device__ __forceinline__ void load_wts(uint32_t a, Wts<N>& r) {
+  if constexpr (N == 1) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.w[0].x), "=f"(r.w[0].y) : "r"(a));
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; k += 2)
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(r.w[k].x), "=f"(r.w[k].y), "=f"(r.w[k + 1].x), "=f"(r.w[k + 1].y)
+                   : "r"(a + 8u * k));
+  }
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int4 lds_i4(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds_u4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+
+// One merged entry applied to the group, for every node g of the group with
+// its weights (zero where node g's row does not hold the entry: a fused
+// multiply-add of an exact zero product leaves the sum as it is, so the
+// straight-line form adds exactly the per-node kernel's terms):
+//   NIN 1, NOUT 1 (scalar weight):  acc0 += w (x - xo)
+//   NIN 1, NOUT 2:                  d = x - xo; acc0 += w0 d; acc1 += w1 d
+//   NIN 2, NOUT 1:                  acc0 += w0 (x0 - xo0); acc0 += w1 (x1 - xo1)
+template <int NIN, int NOUT, int NW, int VA, int VB>
+__device__ __forceinline__ void apply(const Wts<4 * NW>& W, const Lv<VA, VB> (&x)[NIN], const Lv<VA, VB> (&xo)[NIN][4],
+                                      Lv<VA, VB> (&acc)[NOUT][4]) {
+  Lv<VA, VB> d[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) lv_sub(x[0], xo[0][g], d[g]);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    if constexpr (NIN == 1 && NOUT == 1) {
+      lv_fma(W.w[g], d[g], acc[0][g]);
+    } else if constexpr (NIN == 1) {
+      lv_fma(W.w[2 * g], d[g], acc[0][g]);
+      lv_fma(W.w[2 * g + 1], d[g], acc[1][g]);
+    } else {
+      lv_fma(W.w[2 * g], d[g], acc[0][g]);
+    }
+  }
+  if constexpr (NIN == 2) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) lv_sub(x[1], xo[1][g], d[g]);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) lv_fma(W.w[2 * g + 1], d[g], acc[0][g]);
+  }
+}
+
+// ------------------------------------------------------------- mbarriers
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Wait until the phase with the given parity has completed, for at most
+// `limit` SM clock cycles; false on time-out.  Each try suspends the thread
+// until the phase completes or about 20 microseconds pass, so a wait costs
+// one or two instructions rather than a spin.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(20000u)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+// Bulk copy of bytes (a multiple of 16) from global src to shared dst (both
+// 16-byte aligned), its completion counted on bar.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// The device error word: bits of the codes below, set by any tile kernel
+// that gave up a wait; read and cleared by the host (tile_error).
+__device__ unsigned g_tile_error = 0u;
+// Error codes recorded in the device error word (bits).
+constexpr unsigned kErrConsumerWait = 1u;  // a consumer gave up waiting for a tile
+constexpr unsigned kErrProducerWait = 2u;  // the producer gave up waiting for a free buffer
+constexpr unsigned kErrDrainWait = 4u;     // copies still in flight when the kernel gave up
+
+struct TileArgs {
+  const int32_t* head;    // [ntiles][kTileHead]
+  const uint32_t* blob;   // per-tile tables
+  const void* in0;
+  const void* in1;
+  void* out0;
+  void* out1;
+  int32_t t0, ntiles;     // tiles t0 .. t0 + ntiles - 1
+  int32_t nlev, nstore, nlb;
+  int64_t ld;
+  uint32_t rows_bytes;    // bytes of one field's staged rows in a stage (slots cap * row bytes)
+  uint32_t stage_bytes;   // bytes of one stage (NIN fields' rows, then the tile blob)
+  int32_t nstages;        // 2 .. kMaxStages tiles in flight per block
+  long long wait_limit;   // clock cycles any wait may take
+  int32_t hang_test;      // 1: the consumers also wait on a barrier nothing completes (test of the time-out)
+};
+
+constexpr int kMaxStages = 4;
+
+// Block: NC consumer warps (warp 0 .. NC-1), then one producer warp.  Tiles
+// t0 + blockIdx.x, + gridDim.x, ...; the block's k-th tile goes to stage
+// k % nstages, the (k / nstages)-th use of that stage.
+template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int BATCH, int MODE>
+__global__ void __launch_bounds__(256, 2) tile_kernel(const TileArgs a) {
+  constexpr int LB = 32 * (VA + VB);  // levels per level block
+  constexpr uint32_t ES = sizeof(S);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  const int ns = a.nstages;
+  const uint32_t full0 = base + static_cast<uint32_t>(ns) * a.stage_bytes;  // full[4], empty[4], hang
+  const uint32_t empty0 = full0 + 8 * kMaxStages;
+  const uint32_t hang = empty0 + 8 * kMaxStages;
+  const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31u);
+  const int nc = static_cast<int>(blockDim.x >> 5) - 1;  // consumer warps
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ns; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, static_cast<uint32_t>(nc));
+    }
+    mbar_init(hang, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t row_bytes = a.ld * static_cast<int64_t>(ES);
+
+  if (warp == nc) {
+    // ------------------------------------------------------------ producer
+    // The tile header: words 0..7 (two uniform 16-byte loads) and range
+    // r = (first node, count, first slot, 0) in lane r.  The next tile's
+    // header is requested before this tile's copies are issued, so its
+    // latency hides behind the wait for a free stage.
+    const int32_t t_end = a.t0 + a.ntiles;
+    struct Head {
+      int4 i0, i1, r;
+    };
+    auto load_head = [&](int32_t t) {
+      const int4* h = reinterpret_cast<const int4*>(a.head + static_cast<int64_t>(t) * kTileHead);
+      Head x;
+      x.i0 = __ldg(h);
+      x.i1 = __ldg(h + 1);
+      x.r = lane < kTileRanges ? __ldg(h + 2 + lane) : make_int4(0, 0, 0, 0);
+      return x;
+    };
+    int k = 0;
+    bool ok = true;
+    int32_t t = a.t0 + static_cast<int32_t>(blockIdx.x);
+    Head cur{};
+    if (t < t_end) cur = load_head(t);
+    for (; t < t_end; t += static_cast<int32_t>(gridDim.x), ++k) {
+      const int32_t tn = t + static_cast<int32_t>(gridDim.x);
+      Head nxt{};
+      if (tn < t_end) nxt = load_head(tn);
+      const int st = k % ns;
+      const uint32_t use = static_cast<uint32_t>(k / ns);
+      const uint32_t full = full0 + 8 * st, empty = empty0 + 8 * st;
+      const int32_t nranges = cur.i0.z, slots = cur.i0.w, boff = cur.i1.x, bbytes = cur.i1.y;
+      if (k >= ns && ok) {
+        // the consumers released this stage's previous tile
+        bool got = true;
+        if (lane == 0) got = mbar_wait(empty, (use - 1) & 1u, a.wait_limit);
+        got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+        if (!got) {
+          if (lane == 0) atomicOr(&g_tile_error, kErrProducerWait);
+          ok = false;
+        }
+      }
+      if (!ok) break;
+      const uint32_t sbase = base + static_cast<uint32_t>(st) * a.stage_bytes;
+      if (lane == 0)
+        mbar_expect_tx(full, static_cast<uint32_t>(NIN) * static_cast<uint32_t>(slots) * static_cast<uint32_t>(row_bytes) +
+                                 static_cast<uint32_t>(bbytes));
+      __syncwarp();
+      if (lane < nranges) {
+        const uint32_t bytes = static_cast<uint32_t>(cur.r.y) * static_cast<uint32_t>(row_bytes);
+        const uint32_t dst = sbase + static_cast<uint32_t>(cur.r.z) * static_cast<uint32_t>(row_bytes);
+        bulk_copy(dst, static_cast<const char*>(a.in0) + static_cast<int64_t>(cur.r.x) * row_bytes, bytes, full);
+        if constexpr (NIN == 2)
+          bulk_copy(dst + a.rows_bytes, static_cast<const char*>(a.in1) + static_cast<int64_t>(cur.r.x) * row_bytes,
+                    bytes, full);
+      }
+      if (lane == 31)
+        bulk_copy(sbase + static_cast<uint32_t>(NIN) * a.rows_bytes, a.blob + 4 * static_cast<int64_t>(boff),
+                  static_cast<uint32_t>(bbytes), full);
+      cur = nxt;
+    }
+    // before leaving, the copies of the last tiles must have landed (a
+    // consumer may have given up early; the shared memory must not go away
+    // under them)
+    if (lane == 0) {
+      for (int kk = (k >= ns ? k - ns : 0); kk < k; ++kk)
+        if (!mbar_wait(full0 + 8 * (kk % ns), static_cast<uint32_t>(kk / ns) & 1u, a.wait_limit))
+          atomicOr(&g_tile_error, kErrDrainWait);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  if (a.hang_test && !mbar_wait(hang, 0u, a.wait_limit)) {
+    if (lane == 0) atomicOr(&g_tile_error, kErrConsumerWait);
+    return;
+  }
+  int k = 0;
+  for (int32_t t = a.t0 + static_cast<int32_t>(blockIdx.x); t < a.t0 + a.ntiles; t += static_cast<int32_t>(gridDim.x), ++k) {
+    const int st = k % ns;
+    if (!mbar_wait(full0 + 8 * st, static_cast<uint32_t>(k / ns) & 1u, a.wait_limit)) {
+      if (lane == 0) atomicOr(&g_tile_error, kErrConsumerWait);
+      return;
+    }
+    const uint32_t sbase = base + static_cast<uint32_t>(st) * a.stage_bytes;
+    const uint32_t blob = sbase + static_cast<uint32_t>(NIN) * a.rows_bytes;
+    const int4 ti = lds_i4(blob);
+    const int ngt = ti.x, nent = ti.y;
+    const int32_t tfirst = ti.z;
+    const uint32_t o_b = blob + 16u + 16u * static_cast<uint32_t>(ngt);
+    const uint32_t o_h = o_b + (HAS_B ? 32u * static_cast<uint32_t>(ngt) : 0u);
+    const uint32_t o_w = o_h + 4u * static_cast<uint32_t>(nent);
+    uint32_t rows[2] = {sbase, sbase + a.rows_bytes};
+    const uint32_t rb = static_cast<uint32_t>(row_bytes);
+    for (int g = warp; g < ngt; g += nc) {
+      const int4 gh = lds_i4(blob + 16u + 16u * static_cast<uint32_t>(g));
+      const uint32_t slot0 = static_cast<uint32_t>(gh.x);
+      const int count = MODE == kTileMerged ? (gh.w >> 16) & 0xf : gh.w;
+      const int32_t node0 = tfirst + 4 * g;
+      for (int lb = 0; lb < a.nlb; ++lb) {
+        const Layout<VA, VB> L(lb * LB, lane);
+        Lv<VA, VB> xo[NIN][4], acc[NOUT][4];
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg) {
+#pragma unroll
+          for (int m = 0; m < NIN; ++m) {
+            if (gg < count)  // warp-uniform
+              lv_load<S, VA, VB>(rows[m] + (slot0 + gg) * rb, L, xo[m][gg]);
+            else lv_zero(xo[m][gg]);
+          }
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) lv_zero(acc[c][gg]);
+        }
+        if constexpr (MODE == kTileRows) {
+          // every node of the group walks its own stencil row, the four in
+          // step (four independent sums); D entries each, BATCH at a time
+          const uint32_t o_s = blob + 4u * static_cast<uint32_t>(gh.y);
+          const int D = gh.z;
+          const uint32_t o_ws = o_s + 16u * static_cast<uint32_t>(D);
+          auto step = [&](int e, Lv<VA, VB> (&x)[4][NIN], Wts<4 * NW>& W) {
+            const uint4 sl = lds_u4(o_s + 16u * static_cast<uint32_t>(e));
+            load_wts<4 * NW>(o_ws + 32u * NW * static_cast<uint32_t>(e), W);
+            const uint32_t sls[4] = {sl.x, sl.y, sl.z, sl.w};
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+              for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
+          };
+          auto use = [&](const Lv<VA, VB> (&x)[4][NIN], const Wts<4 * NW>& W) {
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg) {
+              Lv<VA, VB> d;
+              lv_sub(x[gg][0], xo[0][gg], d);
+              if constexpr (NIN == 1 && NOUT == 1) {
+                lv_fma(W.w[gg], d, acc[0][gg]);
+              } else if constexpr (NIN == 1) {
+                lv_fma(W.w[2 * gg], d, acc[0][gg]);
+                lv_fma(W.w[2 * gg + 1], d, acc[1][gg]);
+              } else {
+                lv_fma(W.w[2 * gg], d, acc[0][gg]);
+                lv_sub(x[gg][1], xo[1][gg], d);
+                lv_fma(W.w[2 * gg + 1], d, acc[0][gg]);
+              }
+            }
+          };
+          int e = 0;
+          for (; e + BATCH <= D; e += BATCH) {
+            Lv<VA, VB> x[BATCH][4][NIN];
+            Wts<4 * NW> W[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) step(e + u, x[u], W[u]);
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) use(x[u], W[u]);
+          }
+          for (; e < D; ++e) {
+            Lv<VA, VB> x[4][NIN];
+            Wts<4 * NW> W;
+            step(e, x, W);
+            use(x, W);
+          }
+        } else {
+          const int32_t q0 = gh.y, q1 = gh.z;
+          const int nb = gh.w & 0xffff, imask = (gh.w >> 20) & 0xf;
+          // merged entries [qs, qe): whole batches of BATCH, then one at a
+          // time; headers, weights and rows of a batch are requested before use
+          auto one = [&](int32_t q) {
+            const uint32_t hd = lds_u32(o_h + 4u * static_cast<uint32_t>(q));
+            Wts<4 * NW> W;
+            load_wts<4 * NW>(o_w + 32u * NW * static_cast<uint32_t>(q), W);
+            Lv<VA, VB> x[NIN];
+            const uint32_t off = (hd & 0x0fffffffu) * rb;
+#pragma unroll
+            for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + off, L, x[m]);
+            apply<NIN, NOUT, NW>(W, x, xo, acc);
+          };
+          auto run = [&](int32_t qs, int32_t qe) {
+            int32_t q = qs;
+            for (; q + BATCH <= qe; q += BATCH) {
+              uint32_t hd[BATCH];
+              Wts<4 * NW> W[BATCH];
+              Lv<VA, VB> x[BATCH][NIN];
+#pragma unroll
+              for (int u = 0; u < BATCH; ++u) hd[u] = lds_u32(o_h + 4u * static_cast<uint32_t>(q + u));
+#pragma unroll
+              for (int u = 0; u < BATCH; ++u) load_wts<4 * NW>(o_w + 32u * NW * static_cast<uint32_t>(q + u), W[u]);
+#pragma unroll
+              for (int u = 0; u < BATCH; ++u) {
+                const uint32_t off = (hd[u] & 0x0fffffffu) * rb;
+#pragma unroll
+                for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + off, L, x[u][m]);
+              }
+#pragma unroll
+              for (int u = 0; u < BATCH; ++u) apply<NIN, NOUT, NW>(W[u], x[u], xo, acc);
+            }
+            for (; q < qe; ++q) one(q);
+          };
+          run(q0, q0 + nb);
+          // the internal run: own nodes that are neighbours of others of the
+          // group, in ascending order; values already in registers
+          int32_t q = q0 + nb;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (imask & (1 << u)) {
+              Wts<4 * NW> W;
+              load_wts<4 * NW>(o_w + 32u * NW * static_cast<uint32_t>(q), W);
+              Lv<VA, VB> x[NIN];
+#pragma unroll
+              for (int m = 0; m < NIN; ++m) x[m] = xo[m][u];
+              apply<NIN, NOUT, NW>(W, x, xo, acc);
+              ++q;
+            }
+          }
+          run(q, q1);
+        }
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg) {
+          if (gg < count) {
+            if constexpr (HAS_B) {
+              const float2 b = lds_f2(o_b + 32u * static_cast<uint32_t>(g) + 8u * static_cast<uint32_t>(gg));
+              if constexpr (NIN == 2) {
+                lv_fma(pk(b.x, b.x), xo[0][gg], acc[0][gg]);
+                lv_fma(pk(b.y, b.y), xo[1][gg], acc[0][gg]);
+              } else {
+                lv_fma(pk(b.x, b.x), xo[0][gg], acc[0][gg]);
+                lv_fma(pk(b.y, b.y), xo[0][gg], acc[1][gg]);
+              }
+            }
+            const int64_t o = static_cast<int64_t>(node0 + gg) * a.ld;
+            lv_store<S, VA, VB>(static_cast<S*>(a.out0) + o, L, a.nlev, a.nstore, acc[0][gg]);
+            if constexpr (NOUT == 2) lv_store<S, VA, VB>(static_cast<S*>(a.out1) + o, L, a.nlev, a.nstore, acc[1][gg]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty0 + 8 * st);
+  }
+}
+
+}  // namespace grp
+}  // namespace atlasgb

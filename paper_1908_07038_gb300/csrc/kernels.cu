@@ -250,8 +250,8 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
 // entries in use few.  Longer tiles let a block walk consecutive nodes, so
 // the neighbour rows that one pass loads are largely those the next pass
 // needs and are still in the SM's L1.  Measured on O1280 x 137: tiles of 8
-// to 64 passes help the bfloat16 operators and the Laplacian; the other FP32
-// and FP64 kernels run faster with their own grid-stride loop.
+// to 64 passes help the bfloat16 operators; the FP32 and FP64 kernels run
+// faster with their own grid-stride loop.
 // The host keeps gridDim.x * tile below 2^31 + gridDim.x * blockDim.x, so no
 // sum here overflows 32 bits.
 template <typename F>
@@ -305,89 +305,12 @@ __global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict_
   }
 }
 
-// ----------------------------------------------------- node-pair stencil
-// One-input, one-output, scalar-weight stencil (the fused Laplacian) applied
-// to node pairs (2g, 2g+1) from a merged table: every entry carries the
-// neighbour and the weight of each node of the pair, so a neighbour shared by
-// both nodes is read once.  Entries are sorted by neighbour id, as is each
-// node's own row, so every node accumulates its terms in the same order as
-// the per-node kernel; zero-weight terms add exact zeros.
-template <typename A> struct PairEntry;
-template <> struct PairEntry<float> {
-  static __device__ __forceinline__ void load(const int32_t* __restrict__, const float* __restrict__ w, int32_t q,
-                                              int32_t& j, float& wa, float& wb) {
-    const uint4 e = __ldg(reinterpret_cast<const uint4*>(w) + q);
-    j = static_cast<int32_t>(e.x);
-    wa = __uint_as_float(e.y);
-    wb = __uint_as_float(e.z);
-  }
-};
-template <> struct PairEntry<double> {
-  static __device__ __forceinline__ void load(const int32_t* __restrict__ nbr, const double* __restrict__ w,
-                                              int32_t q, int32_t& j, double& wa, double& wb) {
-    j = __ldg(nbr + q);
-    Pair<double>::load(w, q, wa, wb);
-  }
-};
-
-template <typename S, typename A, int VEC, int BATCH, bool IDX32>
-__global__ void __launch_bounds__(512) pair_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ nbr,
-                                                   const A* __restrict__ w, const S* __restrict__ in0,
-                                                   S* __restrict__ out0, int32_t pair0, int32_t npairs, int32_t nlev,
-                                                   int64_t ld, uint32_t nvec, Div32 dv, uint32_t tile) {
-  using Idx = typename IdxT<IDX32>::T;
-  const Idx ldx = static_cast<Idx>(ld);
-  const uint32_t total = static_cast<uint32_t>(npairs) * nvec;  // host guarantees < 2^31
-  for_each_item(total, tile, [&](uint32_t item) {
-    const uint32_t k = div_by(item, dv);
-    const int32_t lev0 = static_cast<int32_t>((item - k * nvec) * VEC);
-    const uint32_t g = static_cast<uint32_t>(pair0) + k;  // pairs pair0 .. pair0 + npairs - 1
-    const int32_t ia = static_cast<int32_t>(2 * g);
-    const Idx oa = static_cast<Idx>(ia) * ldx + static_cast<Idx>(lev0);
-    const Idx ob = oa + ldx;
-    A xa[VEC], xb[VEC], ca[VEC], cb[VEC];
-    vload<S, A, VEC>(in0 + oa, xa);
-    vload<S, A, VEC>(in0 + ob, xb);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      ca[k] = A(0);
-      cb[k] = A(0);
-    }
-    const int32_t q0 = __ldg(ptr + g), q1 = __ldg(ptr + g + 1);
-    for (int32_t qb = q0; qb < q1; qb += BATCH) {
-      int32_t jj[BATCH];
-      A wa[BATCH], wb[BATCH];
-#pragma unroll
-      for (int t = 0; t < BATCH; ++t) {
-        const bool real = qb + t < q1;
-        int32_t j;
-        A x0, x1;
-        PairEntry<A>::load(nbr, w, real ? qb + t : qb, j, x0, x1);
-        jj[t] = real ? j : ia;
-        wa[t] = real ? x0 : A(0);
-        wb[t] = real ? x1 : A(0);
-      }
-      A xj[BATCH][VEC];
-#pragma unroll
-      for (int t = 0; t < BATCH; ++t) vload<S, A, VEC>(in0 + static_cast<Idx>(jj[t]) * ldx + static_cast<Idx>(lev0), xj[t]);
-#pragma unroll
-      for (int t = 0; t < BATCH; ++t) {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-          ca[k] = fma(wa[t], xj[t][k] - xa[k], ca[k]);
-          cb[k] = fma(wb[t], xj[t][k] - xb[k], cb[k]);
-        }
-      }
-    }
-    const int nvalid = nlev - lev0;
-    vstore<S, A, VEC>(out0 + oa, ca, nvalid);
-    vstore<S, A, VEC>(out0 + ob, cb, nvalid);
-  });
-}
-
 // ------------------------------------------------------------- edge pass
 // OP 0 (gradient): flux0 = k1 (x_b - x_a), flux1 = k2 (x_b - x_a)
 // OP 1 (divergence): flux0 = k1 (u_b - u_a) + k2 (v_b - v_a) + k3 v_a
+// OP 2 (gradient, averaged form): flux0 = k1 (x_a + x_b), flux1 = k2 (x_a + x_b)
+//   (the face value of the Green-Gauss sum; in FP32 its node sums cancel
+//   terms of size |x| S / V to leave a gradient of size |x| / R)
 //
 // Both passes walk their items (edge or node, level-vector) one block-wide
 // pass at a time.  The items of a pass belong to at most blockDim.x
@@ -437,11 +360,11 @@ __global__ void __launch_bounds__(kEdgeThreads) edge_flux_kernel(const int32_t* 
       vload<S, A, VEC>(in0 + oa, xa);
       vload<S, A, VEC>(in0 + ob, xb);
       const int nvalid = nlev - lev0;
-      if constexpr (OP == 0) {
+      if constexpr (OP == 0 || OP == 2) {
         A f1[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
-          const A d = xb[k] - xa[k];
+          const A d = OP == 0 ? xb[k] - xa[k] : xa[k] + xb[k];
           f0[k] = k1 * d;
           f1[k] = k2 * d;
         }
@@ -799,62 +722,12 @@ Div32 make_div32(uint32_t d) {
   return r;
 }
 
-namespace {
-template <typename S, typename A, int VEC, int BATCH>
-cudaError_t run_pair(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
-  const uint32_t nvec = static_cast<uint32_t>((l.nlev + VEC - 1) / VEC);
-  const Div32 dv = make_div32(nvec);
-  const int32_t pair0 = l.node0 / 2, npairs = l.count / 2;  // node0 and count are even for pair tables
-  const bool idx32 = static_cast<int64_t>(s.nnodes) * l.ld < (int64_t(1) << 31);
-  if (idx32)
-    pair_kernel<S, A, VEC, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
-        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), pair0,
-        npairs, l.nlev, l.ld, nvec, dv, l.tile);
-  else
-    pair_kernel<S, A, VEC, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
-        s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const S*>(l.in0), static_cast<S*>(l.out0), pair0,
-        npairs, l.nlev, l.ld, nvec, dv, l.tile);
-  return cudaGetLastError();
-}
-
-// (storage, vec, batch) of the pair kernel: batch <= 3 selects 2, else 4
-template <typename S, typename A, typename F>
-auto pair_with_vec(int vec, int batch, F&& f) {
-  constexpr int maxvec = 16 / static_cast<int>(sizeof(S));
-  const bool small = batch <= 3;
-  if (vec >= 8 && maxvec >= 8)
-    return small ? f.template operator()<S, A, (maxvec >= 8 ? 8 : 1), 2>() : f.template operator()<S, A, (maxvec >= 8 ? 8 : 1), 4>();
-  if (vec >= 4 && maxvec >= 4)
-    return small ? f.template operator()<S, A, (maxvec >= 4 ? 4 : 1), 2>() : f.template operator()<S, A, (maxvec >= 4 ? 4 : 1), 4>();
-  if (vec >= 2) return small ? f.template operator()<S, A, 2, 2>() : f.template operator()<S, A, 2, 4>();
-  return small ? f.template operator()<S, A, 1, 2>() : f.template operator()<S, A, 1, 4>();
-}
-template <typename F>
-auto pair_with_storage(StorageType st, int vec, int batch, F&& f) {
-  if (st == ST_F64) return pair_with_vec<double, double>(vec, batch, f);
-  if (st == ST_BF16) return pair_with_vec<uint16_t, float>(vec, batch, f);
-  return pair_with_vec<float, float>(vec, batch, f);
-}
-struct RunPair {
-  const DevStencil& s;
-  const StencilLaunch& l;
-  cudaStream_t stream;
-  template <typename S, typename A, int VEC, int BATCH>
-  cudaError_t operator()() const { return run_pair<S, A, VEC, BATCH>(s, l, stream); }
-};
-struct PairFn {
-  template <typename S, typename A, int VEC, int BATCH>
-  const void* operator()() const { return reinterpret_cast<const void*>(&pair_kernel<S, A, VEC, BATCH, true>); }
-};
-}  // namespace
-
 cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
-  if (s.pair) return pair_with_storage(st, l.vec, l.batch, RunPair{s, l, stream});
   return with_storage(st, s, l.vec, l.batch, RunStencil{s, l, stream});
 }
 
 int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int batch, int threads) {
-  const void* fn = s.pair ? pair_with_storage(st, vec, batch, PairFn{}) : with_storage(st, s, vec, batch, StencilFn{});
+  const void* fn = with_storage(st, s, vec, batch, StencilFn{});
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, 0) != cudaSuccess) return 1;
   return blocks > 0 ? blocks : 1;
@@ -869,6 +742,10 @@ cudaError_t run_edges(int op, const DevEdges& e, const void* in0, const void* in
   const A* coef = static_cast<const A*>(e.coef);
   if (op == 0)
     edge_flux_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
+        e.e2n, coef, static_cast<const S*>(in0), nullptr, static_cast<A*>(flux0), static_cast<A*>(flux1),
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
+  else if (op == 2)
+    edge_flux_kernel<S, A, 2, VEC><<<blocks, threads, 0, stream>>>(
         e.e2n, coef, static_cast<const S*>(in0), nullptr, static_cast<A*>(flux0), static_cast<A*>(flux1),
         static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
   else

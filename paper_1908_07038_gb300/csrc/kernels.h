@@ -1,5 +1,5 @@
 // Launch interface between the C ABI (capi.cpp) and the CUDA kernels
-// (kernels.cu).  Plain structs of device pointers; no CUDA types leak into
+// (kernels.cu, group.cu).  Plain structs of device pointers; no CUDA types leak into
 // the C ABI header.
 #pragma once
 
@@ -33,10 +33,6 @@ struct DevStencil {
   int64_t nnz = 0;
   int nin = 1, nout = 1;
   bool has_b = false, scalar_w = false;
-  // pair == true: merged node-pair table (one input, one output, scalar
-  // weights): ptr[nnodes/2 + 1]; float weights packed {j, wa, wb, 0}; double
-  // weights nbr[nnz] and w[nnz][2]
-  bool pair = false;
 };
 
 struct StencilLaunch {
@@ -51,12 +47,50 @@ struct StencilLaunch {
   int threads = 256;
   int blocks = 0;  // grid size
   uint32_t tile = 0;  // items per block tile: a multiple of threads, blocks * tile < 2^31
-  // nodes computed: node0 .. node0 + count - 1 (even for pair tables).  The
+  // nodes computed: node0 .. node0 + count - 1.  The
   // field pointers are indexed with global node ids within that range and
   // its neighbours.
   int32_t node0 = 0;
   int32_t count = 0;
 };
+
+// Shared-memory node-group kernels (group.cu; tables as TileStencil in
+// geometry.h): tile heads int32 [ntiles][kTileHead] and the per-tile table
+// blob.  The kernels run on tiles t0 .. t0 + ntiles - 1 with one producer
+// warp and one consumer warp per group of a tile.
+struct DevTiles {
+  const int32_t* head = nullptr;
+  const uint32_t* blob = nullptr;
+  int32_t ntiles = 0;
+  int32_t max_slots = 0;  // most node rows a tile stages
+  int32_t max_blob = 0;   // largest tile table (bytes)
+  int groups_per_tile = 8;
+  int nin = 1, nout = 1, nw = 1;
+  bool has_b = false;
+  int mode = 1;           // table layout: 0 merged entries, 1 per-node rows (kTileMerged, kTileRows)
+};
+struct TileLaunch {
+  const void* in0 = nullptr;
+  const void* in1 = nullptr;
+  void* out0 = nullptr;
+  void* out1 = nullptr;
+  int32_t nlev = 0;
+  int32_t nstore = 0;  // stores cover levels < nstore (nlev rounded up to the row's vector width)
+  int64_t ld = 0;      // ld * element size must be a multiple of 16, the field pointers 16-byte aligned
+  int va = 4, vb = 1;  // levels per lane in part A and part B of a level block
+  int32_t t0 = 0, ntiles = 0;
+  int sms = 1;         // grid: sms * (blocks that fit per SM, at most 2), at most ntiles
+  int max_bps = 2;
+  long long wait_limit = 0;  // clock cycles a wait may take (0: the default, about one second)
+  int hang_test = 0;         // 1: the consumers wait on a barrier nothing completes (tests the time-out)
+};
+// Valid (va, vb) pairs: (1,0) (2,0) (2,1) (4,0) (4,1) (4,2).
+cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream);
+// Dynamic shared memory one block needs (two stages), or 0 above the limit.
+size_t tile_smem_bytes(const DevTiles& d, int64_t ld, int elem_size);
+// Read (and with clear, reset) the device error word of the tile kernels
+// (a synchronous copy).
+cudaError_t tile_error(unsigned* code, bool clear);
 
 // Edge-based two-pass data on the device.
 struct DevEdges {

@@ -540,9 +540,10 @@ bool build_regional_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
       one_ring(m, d, op, s);
       return true;
     case OP_GRAD_ADJ:
-    case OP_DIV_ADJ: {
+    case OP_DIV_ADJ:
+    case OP_CURL_ADJ: {
       Stencil a;
-      one_ring(m, d, op == OP_GRAD_ADJ ? OP_GRAD : OP_DIV, a);
+      one_ring(m, d, op == OP_GRAD_ADJ ? OP_GRAD : (op == OP_DIV_ADJ ? OP_DIV : OP_CURL), a);
       return transpose_stencil(a, s);
     }
     case OP_LAP: {

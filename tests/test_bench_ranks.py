@@ -134,7 +134,7 @@ def test_traffic_only_for_the_kernels_it_was_measured_on(tmp_path, monkeypatch):
     cap = tmp_path / "traffic.json"
     good = hashlib.sha256(src.read_bytes()).hexdigest()
     cap.write_text(json.dumps({"kernels_sha256": good, "per_launch_bytes": {"gradient": 123.0}}))
-    monkeypatch.setattr(bench, "KERNEL_SOURCE", str(src))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(src),))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(cap))
     assert bench._traffic("gradient") == 123.0
     assert bench._traffic("laplacian") is None  # not captured
@@ -146,7 +146,7 @@ def test_traffic_only_for_the_kernels_it_was_measured_on(tmp_path, monkeypatch):
     # change, take the capture again: profiles/dram_traffic_o1280.json)
     monkeypatch.undo()
     for op in ("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint"):
-        assert bench._traffic(op) is not None, "no DRAM traffic for %s: kernels.cu changed since the capture" % op
+        assert bench._traffic(op) is not None, "no DRAM traffic for %s: the kernel sources changed since the capture" % op
 
 
 def test_peak_is_the_measured_copy_rate_else_the_fallback(tmp_path, monkeypatch):

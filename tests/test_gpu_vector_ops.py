@@ -127,3 +127,48 @@ def test_sampled_137_levels(torch, pfvm, omesh, N, count, dt, ld):
     del tu, tv, got
     torch.cuda.empty_cache()
     assert max(worst) <= TOL[dt], worst
+
+
+# ------------------------------------------------------------ curl adjoint
+@pytest.mark.parametrize("N,nlev,ld,dt", [(16, 3, 4, np.float64), (80, 137, 138, np.float64),
+                                          (16, 5, 8, np.float32), (80, 137, 140, np.float32),
+                                          (32, 9, 9, np.float32)])
+def test_curl_adjoint_parity(torch, pfvm, omesh, N, nlev, ld, dt):
+    """atlas_nabla_curl_adjoint against the oracle's transpose of the curl's
+    matrix rows, on N(0,1) inputs."""
+    fvm, om = pfvm(N), omesh(N)
+    rng = np.random.default_rng(N + nlev)
+    z = rng.standard_normal((om.nnodes, nlev)).astype(dt)
+    gu, gv = fvm.curl_adjoint(_dev(torch, z, ld), nlev)
+    torch.cuda.synchronize()
+    wu, wv = om.curl_adjoint(z)
+    worst = [_relmax(a[:, :nlev].double().cpu().numpy(), b) for a, b in ((gu, wu), (gv, wv))]
+    assert max(worst) <= TOL[dt], worst
+
+
+def test_curl_adjoint_bf16(torch, pfvm, omesh):
+    fvm, om = pfvm(32), omesh(32)
+    rng = np.random.default_rng(5)
+    z = rng.standard_normal((om.nnodes, 8)).astype(np.float32)
+    tz = _dev(torch, z, 8, torch.bfloat16)
+    gu, gv = fvm.curl_adjoint(tz, 8)
+    torch.cuda.synchronize()
+    wu, wv = om.curl_adjoint(tz.float().cpu().numpy())
+    worst = [_relmax(a.float().cpu().numpy(), b) for a, b in ((gu, wu), (gv, wv))]
+    assert max(worst) <= 2e-2, worst
+
+
+def test_curl_backward_is_the_curl_adjoint_kernel(torch, pfvm):
+    """CurlFn.backward returns exactly what atlas_nabla_curl_adjoint gives
+    (no arithmetic of the binding's own)."""
+    from paper_1908_07038_gb300 import atlas
+    fvm = pfvm(16)
+    rng = np.random.default_rng(6)
+    u, v, zb = (torch.from_numpy(rng.standard_normal((fvm.nnodes, 4))).cuda() for _ in range(3))
+    u.requires_grad_(True)
+    v.requires_grad_(True)
+    z = atlas.curl_fn(u, v, fvm)
+    (z * zb).sum().backward()
+    au, av = fvm.curl_adjoint(zb)
+    torch.cuda.synchronize()
+    assert torch.equal(u.grad, au) and torch.equal(v.grad, av)

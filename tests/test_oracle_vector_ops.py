@@ -181,3 +181,45 @@ def test_vector_ops_node_subsets_and_float32(omesh):
     sub = m.vector_gradient(u, v, nodes=nodes)
     for a, b in zip(full, sub):
         assert np.array_equal(a[nodes], b)
+
+
+# ------------------------------------------------------------ curl adjoint
+def test_curl_adjoint_is_the_dense_transpose_on_o2(omesh):
+    """O2 brute force: the curl's matrix, column by column from orc_curl on
+    unit fields, transposed and applied, against curl_adjoint."""
+    m = omesh(2)
+    V = m.nnodes
+    C = np.zeros((V, 2 * V))
+    for k in range(V):
+        e = np.zeros((V, 1))
+        e[k] = 1.0
+        C[:, k] = m.curl(e, np.zeros((V, 1)))[:, 0]
+        C[:, V + k] = m.curl(np.zeros((V, 1)), e)[:, 0]
+    rng = np.random.default_rng(21)
+    z = rng.standard_normal((V, 3))
+    xu, xv = m.curl_adjoint(z)
+    want = C.T @ z
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(xu - want[:V])) <= 1e-13 * scale
+    assert np.max(np.abs(xv - want[V:])) <= 1e-13 * scale
+
+
+def test_curl_adjoint_dot_product_o16(omesh):
+    """<C (u, v), z> = <(u, v), C^T z> to 1e-12 with N(0,1) fields."""
+    m = omesh(16)
+    rng = np.random.default_rng(22)
+    u, v, z = (rng.standard_normal((m.nnodes, 4)) for _ in range(3))
+    lhs = np.sum(m.curl(u, v) * z)
+    xu, xv = m.curl_adjoint(z)
+    rhs = np.sum(u * xu) + np.sum(v * xv)
+    assert abs(lhs - rhs) <= 1e-12 * (np.sum(np.abs(m.curl(u, v) * z)))
+
+
+def test_curl_adjoint_node_subset(omesh):
+    m = omesh(8)
+    rng = np.random.default_rng(23)
+    z = rng.standard_normal((m.nnodes, 2))
+    nodes = np.array([0, 5, 17, m.nnodes - 1], dtype=np.int64)
+    fu, fv = m.curl_adjoint(z)
+    su, sv = m.curl_adjoint(z, nodes=nodes)
+    assert np.array_equal(su, fu[nodes]) and np.array_equal(sv, fv[nodes])
