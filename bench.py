@@ -93,13 +93,19 @@ def _traffic(op):
         return None
 
 
-# node-group kernels: <storage, inputs, outputs, B term, weights per entry,
-# part A and part B levels per lane, entries per batch>
-KERNEL_NAME = {"gradient": "group_kernel<float,1,2,0,2,4,1,2>",
-               "divergence": "group_kernel<float,2,1,1,2,4,1,2>",
-               "laplacian": "group_kernel<float,1,1,0,1,4,1,4>",
-               "gradient_adjoint": "group_kernel<float,2,1,1,2,4,1,2>",
-               "divergence_adjoint": "group_kernel<float,1,2,1,2,4,1,2>"}
+# kernels of the FP32 operators on 137 levels: the shared-memory node-group
+# kernel <storage, inputs, outputs, B term, weights per entry, part A and
+# part B levels per lane, steps per batch>, or the per-node kernel
+TILE_KERNEL_NAME = {"gradient": "tile_kernel<float,1,2,0,2,4,1,2>",
+                    "divergence": "tile_kernel<float,2,1,1,2,4,1,2>",
+                    "laplacian": "tile_kernel<float,1,1,0,1,4,1,2>",
+                    "gradient_adjoint": "tile_kernel<float,2,1,1,2,4,1,2>",
+                    "divergence_adjoint": "tile_kernel<float,1,2,1,2,4,1,2>"}
+NODE_KERNEL_NAME = {"gradient": "stencil_kernel<float,float,1,2,4,0,0,B,1>",
+                    "divergence": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
+                    "laplacian": "stencil_kernel<float,float,1,1,4,0,1,B,1>",
+                    "gradient_adjoint": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
+                    "divergence_adjoint": "stencil_kernel<float,float,1,2,4,1,0,B,1>"}
 
 
 def _peaks():
@@ -264,15 +270,18 @@ def _table_bytes_nnz(fvm, op, wbytes, nnz):
     return 4 * (V + 1) + nnz * (4 + nw * wbytes) + (2 * wbytes * V if has_b else 0)
 
 
-# Nominal FP64 rate of a GB300 at its maximum SM clock (2070 MHz): the FP64
-# kernels are bound by the FP64 pipe, not by HBM.
-FP64_PEAK_TFLOPS, SM_MAX_MHZ = 1.25, 2070.0
+# Nominal FP64 rate of a GB300 at its maximum SM clock (2070 MHz), for
+# context; the FP64 roofline is quoted against the rate the library's FP64
+# FMA kernel measures in the same run (atlas.measure_fp64_rate).
+FP64_NOMINAL_TFLOPS, SM_MAX_MHZ = 1.25, 2070.0
 
 
 def _fp64_flops(fvm, op, nlev):
-    """Algorithmic FP64 flops of one launch (an FMA counts 2): every CSR entry
-    costs one subtraction per input and one FMA per (input, output) weight;
-    the B term costs one FMA per (input, output) pair and node."""
+    """Algorithmic FP64 flops of one launch (an FMA counts 2), the arithmetic
+    of the operator's node formula as the method writes it: each stencil
+    term w (x_j - x_i) of every output costs one subtraction per input and
+    one multiply-add per (input, output) weight, and the per-node B term one
+    multiply-add per (input, output) pair."""
     if op not in _NNZ:
         _NNZ[op] = fvm.stencil_table(op)["nbr"].shape[0]
     nnz, V = _NNZ[op], fvm.nnodes
@@ -281,6 +290,66 @@ def _fp64_flops(fvm, op, nlev):
     per_node = {"gradient": 0, "laplacian": 0, "divergence_adjoint": 2 * 2, "divergence": 2 * 2,
                 "gradient_adjoint": 2 * 2}[op]
     return (nnz * per_entry + V * per_node) * nlev
+
+
+def _precision(torch, fvm, lon, lat, nlev, seed):
+    """Error of the FP32 and BF16-storage paths against the FP64 path on the
+    whole field: max |x - x64| / max |x64| per operator (worst output
+    component), over all nodes and levels.  The FP64 path (pinned to the FP64
+    oracle at 1e-13) stands in for the oracle at this size; each path's FP64
+    reference runs on the same rounded inputs, so the figure is the
+    arithmetic's error, not the inputs' rounding."""
+    ops = ("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint", "curl", "vector_gradient",
+           "curl_adjoint")
+    nin = {"divergence": 2, "gradient_adjoint": 2, "curl": 2, "vector_gradient": 2}
+
+    def run(op, a, b):
+        if op == "gradient":
+            return fvm.gradient(a, nlev)
+        if op == "laplacian":
+            return (fvm.laplacian(a, nlev),)
+        if op == "divergence_adjoint":
+            return fvm.divergence_adjoint(a, nlev)
+        if op == "curl_adjoint":
+            return fvm.curl_adjoint(a, nlev)
+        if op == "vector_gradient":
+            return fvm.vector_gradient(a, b, nlev)
+        return (getattr(fvm, op)(a, b, nlev),)
+
+    def relmax(x, ref):
+        den = ref.abs().max().item()
+        return (x[:, :nlev].double() - ref[:, :nlev]).abs().max().item() / (den if den > 0 else 1.0)
+
+    f64, u64, v64 = _fields_torch(torch, lon, lat, nlev, 138, torch.float64, "cuda", seed)
+    out = {}
+    for name, dt, ldx in (("fp32", torch.float32, 140), ("bf16", torch.bfloat16, 144)):
+        out[name] = {}
+        for op in ops:
+            a = f64 if nin.get(op, 1) == 1 else u64
+            b = v64
+            ar = torch.zeros((a.shape[0], ldx), dtype=dt, device="cuda")
+            br = torch.zeros((a.shape[0], ldx), dtype=dt, device="cuda")
+            ar[:, :nlev] = a[:, :nlev].to(dt)
+            br[:, :nlev] = b[:, :nlev].to(dt)
+            a64 = torch.zeros((a.shape[0], 138), dtype=torch.float64, device="cuda")
+            b64 = torch.zeros((a.shape[0], 138), dtype=torch.float64, device="cuda")
+            a64[:, :nlev] = ar[:, :nlev].double()
+            b64[:, :nlev] = br[:, :nlev].double()
+            ref = run(op, a64, b64)
+            got = run(op, ar, br)
+            out[name][op] = float("%.3g" % max(relmax(x, r) for x, r in zip(got, ref)))
+            del ar, br, a64, b64, ref, got
+    del f64, u64, v64
+    torch.cuda.empty_cache()
+    return out
+
+
+def _shape(t):
+    """The launch shape the tuner picked, as a short string."""
+    if t.get("kernel") == "tile":
+        return "tile kernel, %d groups per tile, %d block(s) per SM" % (t["groups"], t["tile_bps"])
+    return "per-node kernel, vec %d, batch %d, %d threads, tile %d" % (t["vec"], t["batch"], t["threads"],
+                                                                       t.get("tile", 1))
 
 
 def _cpu_baseline(grid, fvm_nodes, f_host, u_host, v_host, nlev, budget_s=30.0):
@@ -338,8 +407,7 @@ def run_native(args):
     outs = [torch.empty_like(f) for _ in range(7)]
     tuned = {} if args.no_tune else tune.tune_fvm(fvm, atlas.ATLAS_F32, nlev, ld, OPS, fields=(f, u, v), reps=3)
     for op, t in tuned.items():
-        print("tuned %s: vec=%d batch=%d threads=%d (%.3f ms)" % (op, t["vec"], t["batch"], t["threads"], t["ms"]),
-              file=sys.stderr)
+        print("tuned %s: %s (%.3f ms)" % (op, _shape(t), t["ms"]), file=sys.stderr)
     sampler = ClockSampler(local)
     sampler.start()
     total_ms, per_op = _time_ops(torch, fvm, f, u, v, outs, nlev, args.steps, args.warmup, barrier)
@@ -358,7 +426,9 @@ def run_native(args):
                    "alg_bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / hbm}
     dom = max(OPS, key=lambda o: per[o]["ms"])
     traffic = _traffic(dom) if args.grid == N_GRID else None
-    roofline = {"bound": "hbm", "kernel": KERNEL_NAME[dom], "operator": dom, "achieved": round(per[dom]["gbs"], 1),
+    dom_tile = tuned.get(dom, {}).get("kernel", "tile") == "tile"
+    roofline = {"bound": "hbm", "kernel": (TILE_KERNEL_NAME if dom_tile else NODE_KERNEL_NAME)[dom], "operator": dom,
+                "achieved": round(per[dom]["gbs"], 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(per[dom]["frac"], 4),
                 "traffic": traffic, "traffic_gbs": round(traffic / (per[dom]["ms"] * 1e-3) / 1e9, 1) if traffic else None,
                 "peak_kind": peak_kind}
@@ -377,7 +447,7 @@ def run_native(args):
             more[op] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(V * nlev, ws, ms),
                         "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
                         "launches": 2 if op == "vector_gradient" else 1,
-                        "tuned": {k: mt[op][k] for k in ("vec", "batch", "threads", "tile")} if op in mt else None}
+                        "tuned": _shape(mt[op]) if op in mt else None}
         # FP64 volume-weighted sums of one FP32 field (the conservation sums)
         iw = torch.empty(max(atlas.capi.atlas_fvm_integral_workspace_bytes(fvm.handle, nlev) // 8, 1),
                          dtype=torch.float64, device="cuda")
@@ -389,7 +459,7 @@ def run_native(args):
         more["integral_fp64"] = {"ms": round(ms, 4), "node_levels_per_s": _job_rate(V * nlev, ws, ms),
                                  "alg_bytes": b, "frac_hbm": round(b / (ms * 1e-3) / 1e9 / hbm, 4),
                                  "fp64_tflops": round(fl / (ms * 1e-3) / 1e12, 3),
-                                 "frac_fp64": round(fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4), "launches": 2}
+                                 "launches": 2}
         del iw, io
         # the edge-based two-pass forms: edge fluxes through a workspace
         # (E x ld per flux component), then the signed node gather
@@ -517,6 +587,7 @@ def run_native(args):
         v_host = v[:, :nlev].cpu().numpy() if f_host is not None else None
         del f, u, v, outs
         torch.cuda.empty_cache()
+        fp64_rate = atlas.measure_fp64_rate()  # TFLOP/s of dependent FP64 FMAs on every SM
         for name, dt, ldx, es, wb in (("fp64", torch.float64, 138, 8, 8), ("bf16", torch.bfloat16, 144, 2, 4)):
             fx, ux, vx = _fields_torch(torch, g["lon"], g["lat_node"], nlev, ldx, dt, "cuda", 99 + rank)
             ox = [torch.empty_like(fx) for _ in range(7)]
@@ -534,18 +605,25 @@ def run_native(args):
                 if name == "fp64":
                     tf = _fp64_flops(fvm, op, nlev) / (ms * 1e-3) / 1e12
                     entry["per_op"][op]["fp64_tflops"] = round(tf, 4)
-                    entry["per_op"][op]["frac_fp64"] = round(tf / FP64_PEAK_TFLOPS, 4)
+                    entry["per_op"][op]["frac_fp64"] = round(tf / fp64_rate, 4)
             if name == "fp64":
                 dom = max(OPS, key=lambda o: entry["per_op"][o]["ms"])
                 entry["roofline"] = {"bound": "alu", "operator": dom,
-                                     "achieved": entry["per_op"][dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                                     "achieved": entry["per_op"][dom]["fp64_tflops"], "peak": round(fp64_rate, 4),
                                      "unit": "TFLOP/s", "frac": entry["per_op"][dom]["frac_fp64"],
-                                     "peak_kind": "nominal FP64 rate at %d MHz" % SM_MAX_MHZ}
+                                     "peak_kind": "measured",
+                                     "peak_source": "the library's dependent FP64 FMA kernel on every SM, this run",
+                                     "nominal": FP64_NOMINAL_TFLOPS}
             side[name] = entry
             del fx, ux, vx, ox
             torch.cuda.empty_cache()
     else:
         f_host = None
+
+    # ------------------- FP32 and BF16 error against the FP64 path, whole field
+    precision = None
+    if not args.no_precision:
+        precision = _precision(torch, fvm, g["lon"], g["lat_node"], nlev, 7 + rank)
 
     # ------------------------------------- 24 mixed fields, one launch each vs batched
     batched = None
@@ -598,8 +676,8 @@ def run_native(args):
         "roofline": roofline, "per_op": {k: {"ms": v_["ms"], "node_levels_per_s": v_["node_levels_per_s"],
                                              "frac_hbm": round(v_["frac"], 4)} for k, v_ in per.items()},
         "more_ops": more,
-        "side_by_side": side, "batched": batched, "tuned": {k: {kk: t.get(kk, 1) for kk in ("vec", "batch", "threads", "tile")}
-                                                            for k, t in tuned.items()},
+        "side_by_side": side, "precision_vs_fp64": precision, "batched": batched,
+        "tuned": {k: _shape(t) for k, t in tuned.items()},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": 5 * args.steps,
     }
@@ -677,6 +755,7 @@ def main():
     ap.add_argument("--no-side", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32/BF16 error against the FP64 path")
     ap.add_argument("--no-more", action="store_true", help="skip the curl and vector-gradient timings")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (profiling runs)")
     ap.add_argument("--grid", type=int, default=N_GRID,

@@ -59,6 +59,17 @@
  *     still inside a call that uses it.
  *   - No call ever computes on the CPU: without a CUDA device every operator
  *     call fails with ATLAS_ECUDA.
+ *   - Bounds-checked build (the library compiled with -DATLASGB_BOUNDSCHECK,
+ *     a debugging aid): every kernel checks each index it takes from a table
+ *     (neighbour ids, CSR row ranges, edge ids, staged slots, copy ranges)
+ *     against the buffers of its launch, skips an access that would leave
+ *     them and records the first such index in a device word; every
+ *     operator, batch and remap call then waits for its stream and returns
+ *     ATLAS_EBOUNDS, with the kernel's check code and the index in
+ *     atlas_last_error().  Tables are validated on the host before upload
+ *     (atlas_fvm_load refuses inconsistent connectivity), so a library
+ *     table never trips a check; the checks guard the kernels' own index
+ *     arithmetic.  atlas_info() names the build.
  */
 #ifndef ATLAS_GB_H
 #define ATLAS_GB_H
@@ -85,7 +96,9 @@ enum {
   ATLAS_ECUDA = -3,   /* CUDA runtime error, or no CUDA device */
   ATLAS_EALIGN = -4,  /* pointer not aligned to its element size */
   ATLAS_EDTYPE = -5,  /* unsupported dtype */
-  ATLAS_ESTATE = -6   /* handle in the wrong state (destroyed, wrong device) */
+  ATLAS_ESTATE = -6,  /* handle in the wrong state (destroyed, wrong device) */
+  ATLAS_EBOUNDS = -7  /* bounds-checked build only: a kernel met a table index
+                         outside its buffers (the access was skipped) */
 };
 
 /* Operator identifiers (atlas_fvm_prepare masks use 1 << op). */
@@ -296,26 +309,42 @@ int atlas_fvm_prepare(atlas_fvm_t f, unsigned op_mask, unsigned dtype_mask);
 int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, int threads, int blocks_per_sm,
                          int tile_passes);
 /* Shared-memory node-group kernels (FP32 and BF16 fields; F64 always runs */
-/* per node).  Every grid row is cut into tiles of up to 28 consecutive    */
-/* nodes; a producer warp copies the node rows a tile reads (its own and   */
-/* their neighbours, a few runs of consecutive ids) into shared memory     */
-/* with TMA bulk copies, and each of seven consumer warps computes a group */
-/* of up to four nodes from the union of their stencil rows.  The          */
-/* operators use them by default wherever they apply: field pointers       */
-/* 16-byte aligned, ld * element size a multiple of 16, the tile's rows    */
-/* fitting in shared memory (at O1280, ld up to about 190 FP32 values for */
-/* the Laplacian), and a launch made of whole tiles (whole grids,          */
-/* partitions of whole rows); the per-node kernels run elsewhere, with     */
-/* bitwise identical results.  enable: 1 use them with the default table  */
-/* layout (merged entries for the Laplacian, per-node rows otherwise), 2   */
-/* with merged entries (each distinct neighbour of a group once, weights   */
-/* of all four nodes), 3 with per-node rows (each node's own stencil row), */
-/* 0 per-node kernels only, -1 keep.  blocks_per_sm: 1 or 2 blocks of 256 */
-/* threads per SM at most (fewer when shared memory is short; 0 keeps;     */
-/* default 2).  dtype -1 sets all three dtypes.  Host only; takes effect  */
-/* at the next operator call (a layout change rebuilds the operator's tile */
-/* tables then).                                                           */
-int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm);
+/* per node).  Every grid row is cut into tiles of up to groups_per_tile  */
+/* groups of four consecutive nodes; a producer warp copies the node rows */
+/* a tile reads (its own and their neighbours, a few runs of consecutive  */
+/* ids) into shared memory with TMA bulk copies, up to four tiles ahead,  */
+/* and each consumer warp computes one group, its four nodes walking their */
+/* own stencil rows from shared memory.  The operators use them by default */
+/* wherever they apply: field pointers 16-byte aligned, ld * element size  */
+/* a multiple of 16, two stages of the tile's rows fitting in shared       */
+/* memory (at O1280 x 137 FP32 with ld 140: every operator), and a launch  */
+/* made of whole tiles (whole grids, partitions of whole rows); the        */
+/* per-node kernels run elsewhere, with bitwise identical results.        */
+/* enable: 1 use them, 0 per-node kernels only, -1 keep.  blocks_per_sm: 1 */
+/* or 2 blocks of 32 (groups_per_tile + 1) threads per SM at most (fewer   */
+/* when shared memory is short; 0 keeps; default 1: one block holding up  */
+/* to four stages measured faster than two blocks of two).                 */
+/* groups_per_tile: 1..7 (0 keeps; default 7; smaller tiles take less     */
+/* shared memory, so more stages fit; a change rebuilds the operator's     */
+/* tile tables at its next call).  dtype -1 sets all three dtypes.  Host  */
+/* only; takes effect at the next operator call.                           */
+int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile);
+/* Launch shape the node-group kernel of one operator takes on fields of   */
+/* nlev levels and leading dimension ld (16-byte aligned pointers          */
+/* assumed): blocks per SM, pipeline stages per block, dynamic shared      */
+/* memory per block in bytes, and the most node rows a tile stages; all 0  */
+/* when the operator runs per node for these sizes (F64, unaligned rows,  */
+/* tiles too large for shared memory).  Builds the operator's tables.      */
+int atlas_fvm_tile_info(atlas_fvm_t f, int op, int dtype, int nlev, int64_t ld, int* blocks_per_sm, int* stages,
+                        int64_t* smem_bytes, int64_t* max_rows);
+/* FP64 rate probe (the FP64 operators are bound by GB300's FP64 pipe):    */
+/* launches blocks x threads threads (threads a multiple of 32, <= 256),   */
+/* each running 8 independent chains of iters dependent FP64 fused        */
+/* multiply-adds, 16 * iters flops per thread, and stores one double per  */
+/* thread in out (device, blocks * threads doubles).  The caller times it */
+/* (CUDA events on the stream) to measure the FP64 rate the FP64 roofline */
+/* is quoted against.                                                      */
+int atlas_fp64_fma_rate_kernel(double* out, int blocks, int threads, int64_t iters, void* stream);
 /* The node-group kernels bound every wait on their pipeline barriers      */
 /* (about a second); a kernel that gives up records a code in a device     */
 /* error word and returns, its outputs then incomplete.  This call copies  */
@@ -330,10 +359,14 @@ int atlas_kernel_status(unsigned* code, int clear);
 /* a few milliseconds, so that the time-out path runs (code 1); 0 restores  */
 /* normal launches.  No GPU fault and no hang is involved.                  */
 int atlas_debug_tile_hang(int on);
-/* Inspection: copy out the FP64 node-group table of one operator (the     */
-/* groups the node-group kernels compute, before the tables are cut into   */
-/* tiles and rounded to float; in the kernels' tables neighbours are       */
-/* referred to by their place among the tile's staged rows).  Groups       */
+/* Tuning hook: the consumer warps of the node-group kernels wait for a    */
+/* tile's copies with mbarrier try-waits that may suspend the thread for   */
+/* up to ns nanoseconds each (0, the default: the hardware's own short    */
+/* suspension).  Results do not depend on it.                              */
+int atlas_debug_tile_wait_hint(unsigned ns);
+/* Inspection: copy out the FP64 node-group table of one operator: the    */
+/* union of each group's stencil rows (the node-group kernels' tiles are   */
+/* cut from these groups, and stage exactly these neighbours).  Groups     */
 /* are runs of up to four consecutive nodes of a grid row.  head[g][4] =   */
 /* {first node, first entry, end entry, nb | count << 16 | imask << 20}:   */
 /* entries [first entry, end entry) are the distinct neighbours of the     */
@@ -444,10 +477,14 @@ int atlas_nabla_laplacian_edges(atlas_fvm_t fvm, const void* f, void* lap, void*
 /* them first with atlas_fvm_prepare (gradient and divergence bits, this   */
 /* dtype), otherwise it returns ATLAS_ESTATE.  The first call on a device, */
 /* with that device current, looks up the array's device address once;    */
-/* make that first call before any stream capture.  All calls share the    */
-/* array and it keeps the last call's contents (nothing in it needs to     */
-/* start at zero: every value read is written earlier in the same call);   */
-/* calls that overlap on the GPU race on it.  F32 or F64 fields.           */
+/* make that first call before any stream capture.  The address stays     */
+/* cached for the process: after cudaDeviceReset (which also invalidates   */
+/* every fvm's device tables) the entry point must not be called again.    */
+/* All calls share the array and it keeps the last call's contents;        */
+/* nothing in it needs to start at zero: both passes use one vector width, */
+/* so every value the second pass reads, padding lanes included, was       */
+/* written by the first pass of the same call.  Calls that overlap on the  */
+/* GPU race on it.  F32 or F64 fields.                                     */
 int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t fvm, const void* f, void* lap, int nlev, int64_t ld,
                                         atlas_dtype dtype, void* stream);
 

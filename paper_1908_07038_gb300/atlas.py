@@ -236,6 +236,16 @@ class Fvm:
                                      w.ctypes.data, b.ctypes.data)
         return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
 
+    def tile_info(self, op, nlev, ld, dtype=ATLAS_F32):
+        """Launch shape of the node-group kernel of op on [nnodes, ld] fields
+        of nlev levels: blocks per SM, stages, shared memory per block,
+        the most rows a tile stages (all 0 when it runs per node)."""
+        b, s = ctypes.c_int(), ctypes.c_int()
+        m, r = ctypes.c_int64(), ctypes.c_int64()
+        capi.atlas_fvm_tile_info(self.handle, OPS.get(op, op), int(dtype), int(nlev), int(ld), ctypes.byref(b),
+                                 ctypes.byref(s), ctypes.byref(m), ctypes.byref(r))
+        return dict(blocks_per_sm=b.value, stages=s.value, smem=m.value, max_rows=r.value)
+
     def group_table(self, op):
         """The FP64 node-group table of one operator (host only): head
         [ngroups][4], hdr [nent], w [nent][4][2] (see atlas_fvm_group_table)."""
@@ -254,13 +264,14 @@ class Fvm:
         capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
                                   int(blocks_per_sm), int(tile_passes))
 
-    def set_group(self, op, enable=-1, blocks_per_sm=0, dtype=-1):
+    def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1):
         """Use the shared-memory node-group kernels for one operator (enable
-        1 default table layout, 2 merged entries, 3 per-node rows) or the
-        per-node kernels only (0; -1 keeps), with at most blocks_per_sm
-        blocks per SM (1 or 2, 0 keeps), for one storage dtype or, with
-        dtype=-1, all of them."""
-        capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(blocks_per_sm))
+        1) or the per-node kernels only (0; -1 keeps), with at most
+        blocks_per_sm blocks per SM (1 or 2; 0 keeps) and groups_per_tile
+        groups of four nodes per tile (1..7; 0 keeps), for one storage dtype
+        or, with dtype=-1, all of them."""
+        capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(blocks_per_sm),
+                                 int(groups_per_tile))
 
     def group_table(self, op):
         """The FP64 node-group table of one operator (host only): head
@@ -279,13 +290,6 @@ class Fvm:
         ATLAS_F64 / ATLAS_BF16) or, with dtype=-1, for all of them."""
         capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
                                   int(blocks_per_sm), int(tile_passes))
-
-    def set_group(self, op, enable=-1, threads=0, blocks_per_sm=0, prefetch_nodes=-2, dtype=-1):
-        """Node-group kernel settings of one operator (FP32 and BF16 fields):
-        enable 1/0 (-1 keeps), threads per block, blocks per SM cap, L2
-        prefetch distance in nodes (-1 automatic, 0 off, -2 keeps)."""
-        capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(threads),
-                                 int(blocks_per_sm), int(prefetch_nodes))
 
     # ---------------------------------------------------------- operators
     def _check(self, *ts):
@@ -514,6 +518,26 @@ def build_fvm_regional(projection: str, nx: int, ny: int, xmin: float, xmax: flo
     dual's radius is the projection's."""
     g = Grid.regional(projection, nx, ny, xmin, xmax, ymin, ymax, radius=radius, **proj)
     return Fvm(Mesh(g), radius)
+
+
+def measure_fp64_rate(iters=1 << 14, blocks_per_sm=8, reps=3):
+    """Measured FP64 FMA rate of the current device (TFLOP/s): the library's
+    FP64 FMA kernel on every SM, timed with CUDA events after a warm-up."""
+    torch = _torch()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads = sms * blocks_per_sm, 256
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    s = _stream()
+    run = lambda: capi.atlas_fp64_fma_rate_kernel(out.data_ptr(), blocks, threads, int(iters), s)
+    run()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        run()
+    b.record()
+    b.synchronize()
+    sec = a.elapsed_time(b) * 1e-3 / reps
+    return 16.0 * iters * blocks * threads / sec / 1e12
 
 
 def kernel_status(clear=True):

@@ -5,7 +5,9 @@ Every ``atlas_*`` function here takes plain integers (handles, device
 pointers, sizes, stream) exactly like its C counterpart and raises
 ``AtlasError`` when the call returns a negative code.  The library is loaded
 from the package directory; if it has not been built the import fails
-loudly -- there is no CPU fallback.
+loudly -- there is no CPU fallback.  With the environment variable
+ATLASGB_BOUNDSCHECK=1 the bounds-checked build of the same library is loaded
+instead (kernels that check every table index; see build.py).
 """
 from __future__ import annotations
 
@@ -13,7 +15,8 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libatlasgb.so")
+BOUNDSCHECK = os.environ.get("ATLASGB_BOUNDSCHECK", "") == "1"
+LIB_PATH = os.path.join(_PKG, "libatlasgb_boundscheck.so" if BOUNDSCHECK else "libatlasgb.so")
 
 ATLAS_F32, ATLAS_F64, ATLAS_BF16 = 0, 1, 2
 ATLAS_OP_GRADIENT, ATLAS_OP_DIVERGENCE, ATLAS_OP_GRADIENT_ADJOINT = 0, 1, 2
@@ -21,7 +24,7 @@ ATLAS_OP_DIVERGENCE_ADJOINT, ATLAS_OP_LAPLACIAN = 3, 4
 ATLAS_OP_CURL, ATLAS_OP_VECTOR_GRADIENT, ATLAS_OP_CURL_ADJOINT = 5, 6, 7
 ATLAS_PROJ_ROTATED_LONLAT, ATLAS_PROJ_MERCATOR, ATLAS_PROJ_LAMBERT_CONFORMAL = 0, 1, 2
 ATLAS_PROJ_POLAR_STEREOGRAPHIC = 3
-ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EALIGN", -5: "EDTYPE", -6: "ESTATE"}
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EALIGN", -5: "EDTYPE", -6: "ESTATE", -7: "EBOUNDS"}
 
 
 class AtlasError(RuntimeError):
@@ -64,9 +67,13 @@ _SIGS = {
     "atlas_fvm_info": (I32, [P, PP, PP, PP, PP], True),
     "atlas_fvm_prepare": (I32, [P, ctypes.c_uint, ctypes.c_uint], True),
     "atlas_fvm_set_launch": (I32, [P, I32, I32, I32, I32, I32, I32, I32], True),
-    "atlas_fvm_set_group": (I32, [P, I32, I32, I32, I32], True),
+    "atlas_fvm_set_group": (I32, [P, I32, I32, I32, I32, I32], True),
     "atlas_kernel_status": (I32, [ctypes.POINTER(ctypes.c_uint), I32], True),
+    "atlas_fp64_fma_rate_kernel": (I32, [P, I32, I32, I64, P], True),
+    "atlas_fvm_tile_info": (I32, [P, I32, I32, I32, I64, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                  ctypes.POINTER(I64), ctypes.POINTER(I64)], True),
     "atlas_debug_tile_hang": (I32, [I32], True),
+    "atlas_debug_tile_wait_hint": (I32, [ctypes.c_uint], True),
     "atlas_fvm_group_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P, P], True),
     "atlas_fvm_stencil_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                                       P, P, P, P], True),

@@ -56,6 +56,26 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(ATLAS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Bounds-checked build: wait for the stream and turn an index violation a
+// kernel recorded into ATLAS_EBOUNDS (a stream being captured into a graph
+// is not waited for).  The normal build returns at once.
+int bounds_after(void* stream, const char* what) {
+  if (!atlasgb::bounds_checked()) return ATLAS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return ATLAS_OK;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  unsigned long long code = 0;
+  long long index = 0;
+  e = atlasgb::bounds_error(&code, &index, true);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the bounds-check word");
+  if (code != 0)
+    return fail(ATLAS_EBOUNDS, "%s: bounds check %llu failed at index %lld (the access was skipped)", what, code,
+                index);
+  return ATLAS_OK;
+}
+
 std::mutex g_registry_mu;
 std::set<const void*> g_live;  // live handles of every kind
 
@@ -131,6 +151,7 @@ struct GroupTables {
   atlasgb::DevTiles dev;
   DevAlloc mem;
   std::vector<int64_t> first;  // first node of every tile, then nnodes
+  int groups = 0;              // groups per tile the tables were cut with
 };
 struct OpTables {
   bool ready = false;
@@ -149,9 +170,9 @@ struct LaunchCfg {
   int threads = 128;
   int blocks_per_sm = 0;  // 0 = occupancy limit
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
-  int group = 1;          // shared-memory node-group kernel where it applies: 1 default layout, 2 merged,
-                          // 3 per-node rows; 0 per-node kernel only
-  int tile_bps = 2;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
+  int group = 1;          // 1: shared-memory node-group kernel where it applies; 0: per-node kernel only
+  int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
+  int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..7), one consumer warp each
 };
 
 // Launch shape an fvm starts with, per operator and storage dtype: the
@@ -209,32 +230,26 @@ int check_device(atlas_fvm_s* f) {
   return ATLAS_OK;
 }
 
-// Groups of a tile: seven, with one consumer warp each and a producer warp
-// (256 threads).
-constexpr int kGroupsPerTile = 7;
 
 // Testing hook (atlas_debug_tile_hang): the next tile-kernel launches make
 // their consumers wait on a barrier that nothing completes, with a short
 // limit, so that the time-out path runs (no GPU fault, no hang).
 std::atomic<int> g_tile_hang{0};
+// Tuning hook (atlas_debug_tile_wait_hint): suspension hint of the
+// consumers' barrier waits in nanoseconds, 0 for none.
+std::atomic<unsigned> g_tile_wait_hint{0};
 
-// Default table layout of the tile kernels: the two-ring Laplacian shares
-// most of its neighbours between the nodes of a group (8.5 merged entries
-// per node against 18), the one-ring operators little (4 against 6), where
-// the per-node rows save the merged form's zero-weight arithmetic.
-int default_tile_mode(const atlasgb::Stencil& s) { return s.scalar_w ? atlasgb::kTileMerged : atlasgb::kTileRows; }
 
 // Build and upload the tile tables of a stencil for float weights.  A
 // stencil the tile layout cannot take leaves them absent (not an error);
 // allocation failures are errors.
-int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int mode) {
+int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int groups) {
   GroupTables& g = t.grp;
   atlasgb::GroupStencil gs;
   atlasgb::TileStencil ts;
   try {
     if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs)) return ATLAS_OK;
-    if (!atlasgb::build_tile_stencil(gs, s, kGroupsPerTile, mode < 0 ? default_tile_mode(s) : mode, ts))
-      return ATLAS_OK;
+    if (!atlasgb::build_tile_stencil(gs, s, groups, ts)) return ATLAS_OK;
   } catch (const std::bad_alloc&) {
     return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
   }
@@ -252,13 +267,14 @@ int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, i
   g.dev.ntiles = static_cast<int32_t>(nt);
   g.dev.max_slots = ts.max_slots;
   g.dev.max_blob = ts.max_blob;
-  g.dev.groups_per_tile = kGroupsPerTile;
+  g.dev.blob_words = static_cast<int64_t>(ts.blob.size());
+  g.dev.groups_per_tile = groups;
   g.dev.nin = s.nin;
   g.dev.nout = s.nout;
   g.dev.nw = ts.nw;
   g.dev.has_b = s.has_b;
-  g.dev.mode = ts.mode;
   g.first.swap(ts.first);
+  g.groups = groups;
   g.ok = true;
   return ATLAS_OK;
 }
@@ -319,7 +335,7 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   t.dev.has_b = s.has_b;
   t.dev.scalar_w = s.scalar_w;
   if (!prec) {
-    const int rc = build_group_tables(f, s, t, -1);
+    const int rc = build_group_tables(f, s, t, f->cfg[op][dtype].tile_groups);
     if (rc) {
       t.mem.release();
       t.dev = atlasgb::DevStencil{};
@@ -330,15 +346,13 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   return ATLAS_OK;
 }
 
-// Rebuild the tile tables when the layout asked for with atlas_fvm_set_group
-// (2 merged, 3 per-node rows) differs from the one built (caller holds the
-// fvm lock; the stencil tables exist).
+// Rebuild the tile tables when the groups per tile asked for with
+// atlas_fvm_set_group differ from those built (caller holds the fvm lock;
+// the stencil tables exist).
 int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
   OpTables& t = f->st[op][dtype];
-  const int want = f->cfg[op][dtype].group;
-  if (dtype == ATLAS_F64 || want < 2 || !t.grp.ok) return ATLAS_OK;
-  const int mode = want == 2 ? atlasgb::kTileMerged : atlasgb::kTileRows;
-  if (t.grp.dev.mode == mode) return ATLAS_OK;
+  const int want = f->cfg[op][dtype].tile_groups;
+  if (dtype == ATLAS_F64 || !t.grp.ok || t.grp.groups == want) return ATLAS_OK;
   atlasgb::Stencil s;
   try {
     if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
@@ -348,7 +362,7 @@ int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
   // the per-node FP32 B term the tile tables point at stays in t.mem
   t.grp.mem.release();
   t.grp = GroupTables{};
-  return build_group_tables(f, s, t, mode);
+  return build_group_tables(f, s, t, want);
 }
 
 int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div, 2 averaged-form grad*/, int prec) {
@@ -399,6 +413,7 @@ int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div, 2 averaged-form grad
   }
   t.dev.nnodes = static_cast<int32_t>(V);
   t.dev.nedges = E;
+  t.dev.nent = static_cast<int64_t>(g.ent.size());
   t.ready = true;
   return ATLAS_OK;
 }
@@ -507,7 +522,7 @@ void group_layout(int nlev, int vmax, int& va, int& vb) {
 // with pointers already shifted to global node ids (see run_stencil_range).
 int run_tiles(atlas_fvm_s* f, const GroupTables& gt, const LaunchCfg& c, StorageType st, const void* in0,
               const void* in1, void* out0, void* out1, int nlev, int64_t ld, atlas_dtype dtype,
-              const void* const* used, int nu, int32_t t0, int32_t nt, void* stream) {
+              const void* const* used, int nu, int32_t t0, int32_t nt, atlasgb::Bounds bd, void* stream) {
   if (nt == 0) return ok();
   atlasgb::TileLaunch l;
   l.in0 = in0;
@@ -523,15 +538,18 @@ int run_tiles(atlas_fvm_s* f, const GroupTables& gt, const LaunchCfg& c, Storage
   l.nstore = static_cast<int32_t>(std::min<int64_t>(ld, (nlev + vpad - 1) / vpad * vpad));
   l.t0 = t0;
   l.ntiles = nt;
+  l.bd = bd;
   l.sms = f->num_sms;
   l.max_bps = c.tile_bps;
+  l.wait_hint_ns = g_tile_wait_hint.load();
   if (g_tile_hang.load()) {
     l.hang_test = 1;
     l.wait_limit = 1ll << 22;  // a few milliseconds
   }
   cudaError_t e = atlasgb::launch_tiles(st, gt.dev, l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "node-group kernel launch");
-  return ok();
+  const int rc = bounds_after(stream, "node-group kernel");
+  return rc ? rc : ok();
 }
 
 // One fused node-stencil operator over nodes [node0, node0 + count).  The
@@ -577,6 +595,12 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   };
   const LaunchCfg& c = f->cfg[op][dtype];
   const StorageType st = storage_of(dtype);
+  atlasgb::Bounds bd;  // checked by the bounds-checked build's kernels
+  bd.lo = static_cast<int32_t>(in_first);
+  bd.hi = static_cast<int32_t>(in_first + in_nodes);
+  bd.olo = static_cast<int32_t>(node0);
+  bd.ohi = static_cast<int32_t>(node0 + count);
+  bd.err = atlasgb::bounds_word();
   if (gt.ok && c.group && (ld * es) % 16 == 0 && atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned
     // rows, and the range must be made of whole tiles
@@ -589,7 +613,7 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
       return run_tiles(f, gt, c, st, shift(in0, in_first), nin == 2 ? shift(in1, in_first) : nullptr,
                        const_cast<void*>(shift(out0, node0)), nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr,
                        nlev, ld, dtype, used, nu, static_cast<int32_t>(a - gt.first.begin()),
-                       static_cast<int32_t>(b - a), stream);
+                       static_cast<int32_t>(b - a), bd, stream);
   }
   atlasgb::StencilLaunch l;
   l.in0 = shift(in0, in_first);
@@ -614,9 +638,12 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
     const int64_t share = ((items + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
     l.tile = static_cast<uint32_t>(std::max<int64_t>(l.threads, std::min<int64_t>(int64_t(c.tile_passes) * l.threads, share)));
   }
+  bd.nnz = dev.nnz;
+  l.bd = bd;
   cudaError_t e = atlasgb::launch_stencil(st, dev, l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
-  return ok();
+  rc = bounds_after(stream, "stencil kernel");
+  return rc ? rc : ok();
 }
 
 // The operator over every node, on whole fields.
@@ -664,7 +691,7 @@ int edge_blocks(atlas_fvm_s* f, int64_t items, int threads) {
 
 // Edge-based two-kernel gradient (which = 0) or divergence (which = 1).
 int run_edges_op(atlas_fvm_s* f, int which, const void* in0, const void* in1, void* out0, void* out1, char* ws,
-                 const WsLayout& w, int nlev, int64_t ld, atlas_dtype dtype, cudaStream_t stream) {
+                 const WsLayout& w, int nlev, int64_t ld, atlas_dtype dtype, cudaStream_t stream, int vec_cap = 0) {
   const int prec = prec_of(dtype);
   {
     std::lock_guard<std::mutex> lk(f->mu);
@@ -673,7 +700,8 @@ int run_edges_op(atlas_fvm_s* f, int which, const void* in0, const void* in1, vo
   }
   const atlasgb::DevEdges& E = f->eg[which][prec].dev;
   const void* ptrs[5] = {in0, in1, out0, out1, ws};
-  const int vec = pick_vec(dtype, ld, ptrs, 5, f->cfg[which][dtype].vec);
+  const int cap = f->cfg[which == 1 ? 1 : 0][dtype].vec;
+  const int vec = pick_vec(dtype, ld, ptrs, 5, vec_cap > 0 ? (cap > 0 ? std::min(cap, vec_cap) : vec_cap) : cap);
   const int64_t nvec = (nlev + vec - 1) / vec;
   if (E.nedges * nvec >= (int64_t(1) << 31)) return fail(ATLAS_EINVAL, "nedges * level-vectors must stay below 2^31");
   const int threads = 256;
@@ -686,7 +714,7 @@ int run_edges_op(atlas_fvm_s* f, int which, const void* in0, const void* in1, vo
                                   which == 1 ? in1 : nullptr, out0, grad ? out1 : nullptr, nlev, ld, vec, threads,
                                   edge_blocks(f, static_cast<int64_t>(E.nnodes) * nvec, threads), stream);
   if (e != cudaSuccess) return cuda_fail(e, "node-gather kernel launch");
-  return ATLAS_OK;
+  return bounds_after(stream, "edge-flux and node-gather kernels");
 }
 
 int check_ws(atlas_fvm_s* f, int op, void* ws, size_t ws_bytes, int64_t ld, atlas_dtype dt, WsLayout& w) {
@@ -715,14 +743,16 @@ const char* atlas_info(void) {
   cudaError_t e = cudaGetDeviceCount(&n);
   char buf[512];
   if (e != cudaSuccess || n == 0) {
-    std::snprintf(buf, sizeof buf, "%s; no CUDA device (%s)", kVersion, cudaGetErrorString(e));
+    std::snprintf(buf, sizeof buf, "%s%s; no CUDA device (%s)", kVersion,
+                  atlasgb::bounds_checked() ? " (bounds-checked kernels)" : "", cudaGetErrorString(e));
   } else {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp p;
     cudaGetDeviceProperties(&p, dev);
-    std::snprintf(buf, sizeof buf, "%s; device %d: %s, sm_%d%d, %d SMs, %.1f GiB", kVersion, dev, p.name, p.major,
-                  p.minor, p.multiProcessorCount, static_cast<double>(p.totalGlobalMem) / (1 << 30));
+    std::snprintf(buf, sizeof buf, "%s%s; device %d: %s, sm_%d%d, %d SMs, %.1f GiB", kVersion,
+                  atlasgb::bounds_checked() ? " (bounds-checked kernels)" : "", dev, p.name, p.major, p.minor,
+                  p.multiProcessorCount, static_cast<double>(p.totalGlobalMem) / (1 << 30));
   }
   s = buf;
   return s.c_str();
@@ -1095,19 +1125,72 @@ int atlas_fvm_set_launch(atlas_fvm_t h, int op, int dtype, int vec, int batch, i
   return ok();
 }
 
-int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks_per_sm) {
+int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
   if (dtype != -1 && !valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "dtype must be -1 (all) or an atlas_dtype");
-  if (enable < -1 || enable > 3) return fail(ATLAS_EINVAL, "enable must be -1, 0, 1, 2 or 3");
+  if (enable < -1 || enable > 1) return fail(ATLAS_EINVAL, "enable must be -1, 0 or 1");
   if (blocks_per_sm < 0 || blocks_per_sm > 2) return fail(ATLAS_EINVAL, "blocks_per_sm must be 0, 1 or 2");
+  if (groups_per_tile < 0 || groups_per_tile > 7) return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, 7]");
   std::lock_guard<std::mutex> lk(f->mu);
   for (int d = 0; d < 3; ++d) {
     if (dtype != -1 && d != dtype) continue;
     if (enable >= 0) f->cfg[op][d].group = enable;
     if (blocks_per_sm) f->cfg[op][d].tile_bps = blocks_per_sm;
+    if (groups_per_tile) f->cfg[op][d].tile_groups = groups_per_tile;
   }
+  return ok();
+}
+
+int atlas_fvm_tile_info(atlas_fvm_t h, int op, int dtype, int nlev, int64_t ld, int* blocks_per_sm, int* stages,
+                        int64_t* smem_bytes, int64_t* max_rows) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unsupported dtype %d", dtype);
+  if (nlev < 1 || ld < nlev) return fail(ATLAS_EINVAL, "need 1 <= nlev <= ld");
+  int rc = check_device(f);
+  if (rc) return rc;
+  if (blocks_per_sm) *blocks_per_sm = 0;
+  if (stages) *stages = 0;
+  if (smem_bytes) *smem_bytes = 0;
+  if (max_rows) *max_rows = 0;
+  {
+    std::lock_guard<std::mutex> lk(f->mu);
+    rc = ensure_stencil(f, op, dtype);
+    if (rc) return rc;
+    rc = ensure_tile_layout(f, op, dtype);
+    if (rc) return rc;
+  }
+  const GroupTables& gt = f->st[op][dtype].grp;
+  const int es = elem_size(static_cast<atlas_dtype>(dtype));
+  if (!gt.ok || (ld * es) % 16 != 0) return ok();
+  atlasgb::TileLaunch l;
+  l.nlev = nlev;
+  l.ld = ld;
+  const void* none[1] = {nullptr};
+  group_layout(nlev, pick_vec(static_cast<atlas_dtype>(dtype), ld, none, 0, 4), l.va, l.vb);
+  l.sms = f->num_sms;
+  l.max_bps = f->cfg[op][dtype].tile_bps;
+  int b = 0, s = 0;
+  size_t m = 0;
+  cudaError_t e = atlasgb::tile_shape(storage_of(static_cast<atlas_dtype>(dtype)), gt.dev, l, &b, &s, &m);
+  if (e != cudaSuccess) return cuda_fail(e, "tile launch shape");
+  if (blocks_per_sm) *blocks_per_sm = b;
+  if (stages) *stages = s;
+  if (smem_bytes) *smem_bytes = static_cast<int64_t>(m);
+  if (max_rows) *max_rows = gt.dev.max_slots;
+  return ok();
+}
+
+int atlas_fp64_fma_rate_kernel(double* out, int blocks, int threads, int64_t iters, void* stream) {
+  if (!out) return fail(ATLAS_EINVAL, "out is NULL");
+  if (blocks < 1 || threads < 32 || threads > 256 || threads % 32 != 0 || iters < 0)
+    return fail(ATLAS_EINVAL, "need blocks >= 1, threads a multiple of 32 in [32, 256], iters >= 0");
+  if (reinterpret_cast<uintptr_t>(out) % 8 != 0) return fail(ATLAS_EALIGN, "out must be 8-byte aligned");
+  cudaError_t e = atlasgb::launch_fp64_fma(out, blocks, threads, iters, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "FP64 rate kernel launch");
   return ok();
 }
 
@@ -1116,6 +1199,11 @@ int atlas_kernel_status(unsigned* code, int clear) {
   *code = 0;
   cudaError_t e = atlasgb::tile_error(code, clear != 0);
   if (e != cudaSuccess) return cuda_fail(e, "reading the kernels' error word");
+  return ok();
+}
+
+int atlas_debug_tile_wait_hint(unsigned ns) {
+  g_tile_wait_hint.store(ns);
   return ok();
 }
 
@@ -1465,9 +1553,13 @@ int atlas_nabla_laplacian_edges_noalloc(atlas_fvm_t h, const void* fin, void* la
   if (nlev == 0) return ok();
   char* base = static_cast<char*>(scratch);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  rc = run_edges_op(f, 0, fin, nullptr, base + w.g0, base + w.g1, base, w, nlev, ld, dtype, s);
+  // one vector width for both passes: the second reads whole vectors of the
+  // intermediate gradient exactly where the first wrote them
+  const void* all[4] = {fin, lap, base + w.g0, base + w.g1};
+  const int vec = pick_vec(dtype, ld, all, 4, 0);
+  rc = run_edges_op(f, 0, fin, nullptr, base + w.g0, base + w.g1, base, w, nlev, ld, dtype, s, vec);
   if (rc) return rc;
-  rc = run_edges_op(f, 1, base + w.g0, base + w.g1, lap, nullptr, base, w, nlev, ld, dtype, s);
+  rc = run_edges_op(f, 1, base + w.g0, base + w.g1, lap, nullptr, base, w, nlev, ld, dtype, s, vec);
   return rc ? rc : ok();
 }
 
@@ -1779,9 +1871,12 @@ int atlas_remap_apply(atlas_remap_t h, const void* src, void* dst, int nlev, int
   l.threads = 256;
   const int64_t need = (r->ntgt * nvec + l.threads - 1) / l.threads;
   l.blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(r->num_sms) * 8)));
+  l.bd.hi = static_cast<int32_t>(r->src->grid->g.nnodes);
+  l.bd.err = atlasgb::bounds_word();
   cudaError_t e = atlasgb::launch_remap(storage_of(dtype), l, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "remap kernel launch");
-  return ok();
+  const int brc = bounds_after(stream, "remap kernel");
+  return brc ? brc : ok();
 }
 
 void atlas_remap_destroy(atlas_remap_t h) {
@@ -1920,6 +2015,8 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     o.div_m = dv.m;
     o.div_s1 = dv.s1;
     o.div_s2 = dv.s2;
+    o.nnodes = s.nnodes;
+    o.nnz = s.nnz;
     if (static_cast<int64_t>(s.nnodes) * d.ld >= (int64_t(1) << 31)) idx32 = false;
     o.tile0 = static_cast<int32_t>(tiles);
     tiles += (items + tile_items - 1) / tile_items;
@@ -1931,6 +2028,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   b->params.ndesc = static_cast<int32_t>(hd.size());
   b->params.ntiles = static_cast<int32_t>(tiles);
   b->params.tile_items = tile_items;
+  b->params.err = atlasgb::bounds_word();
   for (size_t k = 0; k < hd.size(); ++k) b->params.d[k] = hd[k];
   b->plain = plain;
   b->dtype = dtype;
@@ -1971,7 +2069,8 @@ int atlas_batch_launch(atlas_batch_t h, void* stream) {
   cudaError_t e = atlasgb::launch_batch(b->st, b->vec, b->idx32, b->params, b->threads, b->blocks,
                                         static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
-  return ok();
+  const int rc = bounds_after(stream, "batch kernel");
+  return rc ? rc : ok();
 }
 
 int atlas_batch_info(atlas_batch_t h, int64_t* tiles, int64_t* node_levels) {

@@ -716,12 +716,11 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs) {
   return true;
 }
 
-bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, int mode, TileStencil& ts) {
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts) {
   const int64_t ng = static_cast<int64_t>(gs.first.size()) - 1;
   const int nw = gs.nw;
   ts.nw = nw;
   ts.groups_per_tile = groups_per_tile;
-  ts.mode = mode;
   // tiles: up to groups_per_tile consecutive groups of one grid row
   std::vector<int64_t> tg;  // first group of every tile
   for (int64_t gi = 0; gi < ng;) {
@@ -773,9 +772,6 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
     auto slot = [&](int32_t j) {
       return static_cast<uint32_t>(std::lower_bound(ids.begin(), ids.end(), j) - ids.begin());
     };
-    const int32_t q_base = gs.head[4 * ga + 1];
-    const int32_t nent = gs.head[4 * (gb - 1) + 2] - q_base;
-    const int32_t nent_pad = (nent + 3) & ~3;
     const bool has_b = s.has_b;
     std::vector<uint32_t>& b = blobs[t];
     auto put_f = [&](size_t at, double v) {
@@ -788,66 +784,41 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
     b.assign(o_data, 0u);
     b[0] = static_cast<uint32_t>(ngt);
     b[2] = static_cast<uint32_t>(gs.first[ga]);
-    b[3] = static_cast<uint32_t>(mode);
     for (int k = 0; k < ngt; ++k) {
       const int64_t gi = ga + k;
       if (has_b)
         for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i)
           for (int c = 0; c < 2; ++c) put_f(o_b + 8 * static_cast<size_t>(k) + 2 * static_cast<size_t>(i - gs.first[gi]) + c, s.b[2 * i + c]);
     }
-    if (mode == kTileMerged) {
-      // merged entries: headers [nent_pad], weights as f32x2 pairs
-      // [nent_pad][4][nw][2]
-      b[1] = static_cast<uint32_t>(nent_pad);
-      const size_t o_h = o_data, o_w = o_h + static_cast<size_t>(nent_pad);
-      b.resize(o_w + static_cast<size_t>(nent_pad) * 8 * nw, 0u);
-      for (int k = 0; k < ngt; ++k) {
-        const int64_t gi = ga + k;
-        b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
-        b[4 + 4 * k + 1] = static_cast<uint32_t>(gs.head[4 * gi + 1] - q_base);
-        b[4 + 4 * k + 2] = static_cast<uint32_t>(gs.head[4 * gi + 2] - q_base);
-        b[4 + 4 * k + 3] = static_cast<uint32_t>(gs.head[4 * gi + 3]);
+    // per-node rows: for group k with D = its nodes' largest row, slots
+    // [D][4] then weights as f32x2 pairs [D][4][nw][2]; entry e of node t
+    // is its row's e-th term, or (own slot, weight 0) past its row's end
+    for (int k = 0; k < ngt; ++k) {
+      const int64_t gi = ga + k;
+      const int cnt = static_cast<int>(gs.first[gi + 1] - gs.first[gi]);
+      int D = 0;
+      for (int u = 0; u < cnt; ++u) {
+        const int64_t i = gs.first[gi] + u;
+        D = std::max(D, static_cast<int>(s.ptr[i + 1] - s.ptr[i]));
       }
-      for (int32_t q = 0; q < nent; ++q) {
-        const uint32_t hv = gs.hdr[q_base + q];
-        b[o_h + q] = slot(static_cast<int32_t>(hv & 0x0fffffffu)) | (hv & 0xf0000000u);
-        for (int k = 0; k < 4 * nw; ++k) {
-          const double v = gs.w[(static_cast<size_t>(q_base + q)) * 4 * nw + k];
-          put_f(o_w + (static_cast<size_t>(q) * 4 * nw + k) * 2, v);
-          put_f(o_w + (static_cast<size_t>(q) * 4 * nw + k) * 2 + 1, v);
-        }
-      }
-    } else {
-      // per-node rows: for group k with D = its nodes' largest row, slots
-      // [D][4] then weights as f32x2 pairs [D][4][nw][2]; entry e of node t
-      // is its row's e-th term, or (own slot, weight 0) past its row's end
-      for (int k = 0; k < ngt; ++k) {
-        const int64_t gi = ga + k;
-        const int cnt = static_cast<int>(gs.first[gi + 1] - gs.first[gi]);
-        int D = 0;
-        for (int u = 0; u < cnt; ++u) {
-          const int64_t i = gs.first[gi] + u;
-          D = std::max(D, static_cast<int>(s.ptr[i + 1] - s.ptr[i]));
-        }
-        const size_t off = b.size();
-        b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
-        b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
-        b[4 + 4 * k + 2] = static_cast<uint32_t>(D);
-        b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt);
-        b.resize(off + static_cast<size_t>(D) * 4 * (1 + 2 * nw), 0u);
-        const size_t o_w = off + static_cast<size_t>(D) * 4;
-        for (int u = 0; u < 4; ++u) {
-          const int64_t i = gs.first[gi] + std::min(u, cnt - 1);
-          const uint32_t own = slot(static_cast<int32_t>(i));
-          const int32_t deg = u < cnt ? s.ptr[i + 1] - s.ptr[i] : 0;
-          for (int e = 0; e < D; ++e) {
-            b[off + 4 * static_cast<size_t>(e) + u] = e < deg ? slot(s.nbr[s.ptr[i] + e]) : own;
-            for (int c = 0; c < nw; ++c) {
-              const double v = e < deg ? s.w[2 * static_cast<int64_t>(s.ptr[i] + e) + c] : 0.0;
-              const size_t at = o_w + ((static_cast<size_t>(e) * 4 + u) * nw + c) * 2;
-              put_f(at, v);
-              put_f(at + 1, v);
-            }
+      const size_t off = b.size();
+      b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
+      b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
+      b[4 + 4 * k + 2] = static_cast<uint32_t>(D);
+      b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt);
+      b.resize(off + static_cast<size_t>(D) * 4 * (1 + 2 * nw), 0u);
+      const size_t o_w = off + static_cast<size_t>(D) * 4;
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = gs.first[gi] + std::min(u, cnt - 1);
+        const uint32_t own = slot(static_cast<int32_t>(i));
+        const int32_t deg = u < cnt ? s.ptr[i + 1] - s.ptr[i] : 0;
+        for (int e = 0; e < D; ++e) {
+          b[off + 4 * static_cast<size_t>(e) + u] = e < deg ? slot(s.nbr[s.ptr[i] + e]) : own;
+          for (int c = 0; c < nw; ++c) {
+            const double v = e < deg ? s.w[2 * static_cast<int64_t>(s.ptr[i] + e) + c] : 0.0;
+            const size_t at = o_w + ((static_cast<size_t>(e) * 4 + u) * nw + c) * 2;
+            put_f(at, v);
+            put_f(at + 1, v);
           }
         }
       }

@@ -141,29 +141,21 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
 // nodes and all their neighbours) as at most kTileRanges runs of
 // consecutive node ids; the kernel copies those runs into shared memory in
 // order, so the node with the s-th smallest id of the list sits in slot s.
-// The tile's group table refers to slots instead of node ids.
 //   head[t][kTileHead]: first node, groups, ranges, slots (rows staged),
 //     blob offset (16-byte units), blob bytes, 0, 0, then per range
 //     (first node, count, first slot, 0).
-//   blob: per tile, 16-byte aligned: {groups, entries, first node, mode};
-//     a 16-byte head per group; B term [groups * 4][2] (floats; operators
-//     with one); then, by mode, either
-//     kTileMerged: group heads {slot of its first node, first entry, end
-//       entry, nb | count << 16 | imask << 20} (entries counted from the
-//       tile's first); headers [entries] slot | mask << 28; weights
-//       [entries][4][nw] as f32x2 pairs (each weight twice);
-//     kTileRows: group heads {slot of its first node, word offset of its
-//       data in the blob, D, count}; data: slots [D][4] (entry e of node t:
-//       its row's e-th neighbour, or its own slot past its row's end), then
-//       weights [D][4][nw] as f32x2 pairs (0 past the row's end).
-constexpr int kTileMerged = 0;
-constexpr int kTileRows = 1;
+//   blob: per tile, 16-byte aligned: {groups, 0, first node, 0}; per group
+//     {slot of its first node, word offset of its data in the blob, D,
+//     count}; the B term [groups * 4][2] (floats; operators with one); then
+//     per group, D being its nodes' longest stencil row: slots [D][4]
+//     (entry e of node t: its row's e-th neighbour, or its own slot past its
+//     row's end) and weights [D][4][nw] as f32x2 pairs (each weight twice;
+//     0 past the row's end).
 constexpr int kTileRanges = 16;
 constexpr int kTileHead = 8 + 4 * kTileRanges;
 struct TileStencil {
   int nw = 1;
-  int mode = kTileRows;
-  int groups_per_tile = 8;
+  int groups_per_tile = 7;
   std::vector<int32_t> head;      // [ntiles][kTileHead]
   std::vector<uint32_t> blob;     // 32-bit words
   std::vector<int64_t> first;     // [ntiles + 1]: first node of every tile, then nnodes
@@ -172,7 +164,7 @@ struct TileStencil {
 };
 // Fails (false) when a tile needs more than kTileRanges runs (the caller
 // keeps the per-node kernels).
-bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, int mode, TileStencil& ts);
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts);
 
 // Regular (full) Gaussian grid F<N>: the 2N Gaussian latitudes of O<N>, each
 // with 4N longitudes j/(4N) turns.  A remapping target, and meshed by the

@@ -1,6 +1,8 @@
-// Dispatch of the shared-memory node-group kernels (group.cuh): storage type
-// (FP32, bfloat16) x operator shape x level layout (va, vb).
+// Launch of the shared-memory node-group kernels (group.cuh); the kernels
+// themselves are instantiated per storage type in group_f32.cu and
+// group_bf16.cu (compiled in parallel).
 #include <algorithm>
+#include <mutex>
 
 #include "group.cuh"
 
@@ -9,54 +11,32 @@ namespace {
 
 constexpr size_t kSmemLimit = 232448;  // 227 KiB of dynamic shared memory per block
 
-template <typename F>
-cudaError_t with_shape(const DevTiles& d, F&& f) {
-  if (d.nin == 1 && d.nout == 1) return f.template operator()<1, 1, false, 1>();
-  if (d.nin == 1 && d.nout == 2 && !d.has_b) return f.template operator()<1, 2, false, 2>();
-  if (d.nin == 1 && d.nout == 2) return f.template operator()<1, 2, true, 2>();
-  if (d.nin == 2 && d.nout == 1 && d.has_b) return f.template operator()<2, 1, true, 2>();
-  return cudaErrorInvalidValue;
-}
-
-template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int MODE>
-const void* kernel_of(int va, int vb) {
-  // entries in flight: merged, four; per-node rows, two steps of four nodes
-  constexpr int BATCH = MODE == kTileMerged ? 4 : 2;
-  using namespace grp;
-#define ATLASGB_TILE(A, B) \
-  if (va == A && vb == B) return reinterpret_cast<const void*>(&tile_kernel<S, NIN, NOUT, HAS_B, NW, A, B, BATCH, MODE>);
-  ATLASGB_TILE(4, 2)
-  ATLASGB_TILE(4, 1)
-  ATLASGB_TILE(4, 0)
-  ATLASGB_TILE(2, 1)
-  ATLASGB_TILE(2, 0)
-  ATLASGB_TILE(1, 0)
-#undef ATLASGB_TILE
-  return nullptr;
-}
-
-template <typename S>
-struct Pick {
-  int va, vb, mode;
-  const void* fn = nullptr;
-  template <int NIN, int NOUT, bool HAS_B, int NW>
-  cudaError_t operator()() {
-    fn = mode == kTileMerged ? kernel_of<S, NIN, NOUT, HAS_B, NW, kTileMerged>(va, vb)
-                             : kernel_of<S, NIN, NOUT, HAS_B, NW, kTileRows>(va, vb);
-    return fn ? cudaSuccess : cudaErrorInvalidValue;
-  }
-};
-
 const void* tile_fn(StorageType st, const DevTiles& d, int va, int vb) {
-  if (st == ST_F32) {
-    Pick<float> p{va, vb, d.mode};
-    return with_shape(d, p) == cudaSuccess ? p.fn : nullptr;
-  }
-  if (st == ST_BF16) {
-    Pick<uint16_t> p{va, vb, d.mode};
-    return with_shape(d, p) == cudaSuccess ? p.fn : nullptr;
-  }
+  if (st == ST_F32) return tile_fn_f32(d, va, vb);
+  if (st == ST_BF16) return tile_fn_bf16(d, va, vb);
   return nullptr;
+}
+
+// The device error word of the tile kernels and its address per device
+// (looked up once, with the device current).
+__device__ unsigned g_tile_error = 0u;
+constexpr int kMaxDevices = 64;
+std::mutex g_err_mu;
+unsigned* g_err_addr[kMaxDevices] = {};
+cudaError_t error_word(unsigned** p) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_addr[dev]) {
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_tile_error);
+    if (e != cudaSuccess) return e;
+    g_err_addr[dev] = static_cast<unsigned*>(q);
+  }
+  *p = g_err_addr[dev];
+  return cudaSuccess;
 }
 
 // one field's staged rows (plus slack: the consumers' unconditional loads
@@ -86,10 +66,13 @@ size_t tile_smem_bytes(const DevTiles& d, int64_t ld, int elem_size) {
   return ns ? static_cast<size_t>(ns) * stage + 128 : 0;
 }
 
-cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream) {
+cudaError_t tile_shape(StorageType st, const DevTiles& d, const TileLaunch& l, int* bps_out, int* stages_out,
+                       size_t* smem_out) {
+  *bps_out = 0;
+  *stages_out = 0;
+  *smem_out = 0;
   const void* fn = tile_fn(st, d, l.va, l.vb);
   if (!fn) return cudaErrorInvalidValue;
-  if (l.ntiles <= 0 || l.nlev <= 0) return cudaSuccess;
   const int es = st == ST_BF16 ? 2 : 4;
   size_t rows, stage;
   stage_sizes(d, l.ld, es, rows, stage);
@@ -97,10 +80,34 @@ cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l,
   int bps = std::max(1, std::min(l.max_bps, 2));
   int ns = stages_for(stage, bps);
   if (ns == 0 && bps == 2) ns = stages_for(stage, bps = 1);
-  if (ns == 0) return cudaErrorInvalidValue;
+  if (ns == 0) return cudaSuccess;
   const size_t smem = static_cast<size_t>(ns) * stage + 128;
+  const int threads = 32 * (d.groups_per_tile + 1);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
+  int fit = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  *bps_out = std::max(1, std::min(bps, fit));
+  *stages_out = ns;
+  *smem_out = smem;
+  return cudaSuccess;
+}
+
+cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream) {
+  const void* fn = tile_fn(st, d, l.va, l.vb);
+  if (!fn) return cudaErrorInvalidValue;
+  if (l.ntiles <= 0 || l.nlev <= 0) return cudaSuccess;
+  const int threads = 32 * (d.groups_per_tile + 1);  // at most 256 (the kernels' launch bound)
+  if (threads > 256) return cudaErrorInvalidValue;
+  int bps = 0, ns = 0;
+  size_t smem = 0;
+  cudaError_t e = tile_shape(st, d, l, &bps, &ns, &smem);
+  if (e != cudaSuccess) return e;
+  if (ns == 0) return cudaErrorInvalidValue;
+  const int es = st == ST_BF16 ? 2 : 4;
+  size_t rows, stage;
+  stage_sizes(d, l.ld, es, rows, stage);
   grp::TileArgs a{};
   a.head = d.head;
   a.blob = d.blob;
@@ -120,22 +127,22 @@ cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l,
   a.nstages = ns;
   a.wait_limit = l.wait_limit > 0 ? l.wait_limit : (1ll << 31);  // about a second at 2 GHz
   a.hang_test = l.hang_test;
-  void* args[] = {&a};
-  const int threads = 32 * (d.groups_per_tile + 1);  // at most 256 (the kernels' launch bound)
-  if (threads > 256) return cudaErrorInvalidValue;
-  int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, threads, smem);
+  a.wait_hint_ns = l.wait_hint_ns;
+  a.bd = l.bd;
+  a.bd.nnz = d.blob_words;
+  a.max_groups = d.groups_per_tile;
+  e = error_word(&a.err);
   if (e != cudaSuccess) return e;
-  bps = std::max(1, std::min(bps, fit));
+  void* args[] = {&a};
   const int blocks = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(l.sms) * bps, l.ntiles));
   return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, stream);
 }
 
 cudaError_t tile_error(unsigned* code, bool clear) {
-  cudaError_t e = cudaMemcpyFromSymbol(code, grp::g_tile_error, sizeof(unsigned));
+  cudaError_t e = cudaMemcpyFromSymbol(code, g_tile_error, sizeof(unsigned));
   if (e != cudaSuccess || !clear) return e;
   const unsigned zero = 0u;
-  return cudaMemcpyToSymbol(grp::g_tile_error, &zero, sizeof(unsigned));
+  return cudaMemcpyToSymbol(g_tile_error, &zero, sizeof(unsigned));
 }
 
 }  // namespace atlasgb

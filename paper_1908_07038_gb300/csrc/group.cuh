@@ -1,5 +1,5 @@
 // Shared-memory node-group stencil kernels (sm_103a) for FP32 and bfloat16
-// fields: a TMA producer warp and consumer warps.
+// fields: a TMA producer warp feeding consumer warps through shared memory.
 //
 // The node-stencil operators read, for every output value, the values of the
 // node and of its 6-18 stencil neighbours at the same level.  With levels
@@ -10,33 +10,33 @@
 // their gathers use about twice per line of data: a warp spans two nodes and
 // two rows that do not start on line boundaries, and each lane reads the CSR
 // entry of its own node.  These kernels instead
-//   * cut every grid row into tiles of up to 32 (28 for two-input
-//     operators) consecutive nodes and let the host list, per tile, the node
-//     rows the tile reads -- its own and all their neighbours -- as a few
-//     runs of consecutive node ids (the rows above and below, the wrap of
-//     the row, the antipodes of the polar rows);
+//   * cut every grid row into tiles of up to seven groups of four
+//     consecutive nodes and let the host list, per tile, the node rows the
+//     tile reads -- its own and all their neighbours -- as a few runs of
+//     consecutive node ids (the rows above and below, the wrap of the row,
+//     the antipodes of the polar rows);
 //   * have one producer warp copy those runs, and the tile's table, from
-//     global memory into shared memory with TMA bulk copies
-//     (cp.async.bulk, completion counted in bytes on an mbarrier), two tiles
-//     ahead of the consumers, so each row crosses the L1 data pipe once and
-//     the consumers never wait for L2 or DRAM;
-//   * give each consumer warp one group of up to four consecutive nodes of
-//     the tile and all levels: lane l holds levels 4l .. 4l+3 of every row it
-//     reads (part A, one 16-byte shared load) and level 128 + l (part B); the
-//     group's table is the union of its four nodes' stencil rows, so a
-//     neighbour of two or three of them is read once;
-//   * take the values of the group's own nodes, which are also neighbours of
-//     each other, from the registers that hold them;
+//     global memory into shared memory with TMA bulk copies (cp.async.bulk,
+//     completion counted in bytes on an mbarrier), up to four tiles ahead of
+//     the consumers, so that the consumers read their rows from shared
+//     memory, where a warp's 16-byte-per-lane load of a row costs exactly its
+//     four lines, and each staged row serves every node of the tile that
+//     needs it;
+//   * give each consumer warp one group and all levels: lane l holds levels
+//     4l .. 4l+3 of every row it reads (part A) and level 128 + l (part B);
+//     the group's four nodes walk their own stencil rows in step, which gives
+//     four independent chains of arithmetic per lane;
 //   * do the arithmetic on pairs of levels with the packed FP32 instructions
-//     (sub.rn.f32x2, fma.rn.f32x2): each half rounds as the scalar
-//     instruction does.
+//     (__fadd2_rn, __ffma2_rn): each half rounds as the scalar instruction
+//     does.
 // Every node accumulates its terms in ascending neighbour order with the same
-// subtraction and fused multiply-add as the per-node kernels, so the results
-// are bitwise those of the per-node kernels (the merged entries a node does
-// not use are skipped, not added as zeros).  No atomics: deterministic.
-// Every wait on an mbarrier is bounded: past the limit the kernel records an
-// error code in a device word that the host reads, waits (bounded again) for
-// the copies it issued, and returns.
+// subtraction and fused multiply-add as the per-node kernels (a row shorter
+// than its group's longest is padded with zero-weight terms of the node
+// itself, which add exact zeros), so the results are bitwise those of the
+// per-node kernels.  No atomics: deterministic.  Every wait on an mbarrier is
+// bounded: past the limit the kernel records an error code in a device word
+// that the host reads, waits (bounded again) for the copies it issued, and
+// returns.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -44,6 +44,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "bounds.cuh"
 #include "geometry.h"
 #include "kernels.h"
 
@@ -268,38 +269,6 @@ __device__ __forceinline__ uint4 lds_u4(uint32_t a) {
   return v;
 }
 
-// One merged entry applied to the group, for every node g of the group with
-// its weights (zero where node g's row does not hold the entry: a fused
-// multiply-add of an exact zero product leaves the sum as it is, so the
-// straight-line form adds exactly the per-node kernel's terms):
-//   NIN 1, NOUT 1 (scalar weight):  acc0 += w (x - xo)
-//   NIN 1, NOUT 2:                  d = x - xo; acc0 += w0 d; acc1 += w1 d
-//   NIN 2, NOUT 1:                  acc0 += w0 (x0 - xo0); acc0 += w1 (x1 - xo1)
-template <int NIN, int NOUT, int NW, int VA, int VB>
-__device__ __forceinline__ void apply(const Wts<4 * NW>& W, const Lv<VA, VB> (&x)[NIN], const Lv<VA, VB> (&xo)[NIN][4],
-                                      Lv<VA, VB> (&acc)[NOUT][4]) {
-  Lv<VA, VB> d[4];
-#pragma unroll
-  for (int g = 0; g < 4; ++g) lv_sub(x[0], xo[0][g], d[g]);
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    if constexpr (NIN == 1 && NOUT == 1) {
-      lv_fma(W.w[g], d[g], acc[0][g]);
-    } else if constexpr (NIN == 1) {
-      lv_fma(W.w[2 * g], d[g], acc[0][g]);
-      lv_fma(W.w[2 * g + 1], d[g], acc[1][g]);
-    } else {
-      lv_fma(W.w[2 * g], d[g], acc[0][g]);
-    }
-  }
-  if constexpr (NIN == 2) {
-#pragma unroll
-    for (int g = 0; g < 4; ++g) lv_sub(x[1], xo[1][g], d[g]);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) lv_fma(W.w[2 * g + 1], d[g], acc[0][g]);
-  }
-}
-
 // ------------------------------------------------------------- mbarriers
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -311,18 +280,25 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // Wait until the phase with the given parity has completed, for at most
-// `limit` SM clock cycles; false on time-out.  Each try suspends the thread
-// until the phase completes or about 20 microseconds pass, so a wait costs
-// one or two instructions rather than a spin.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+// `limit` SM clock cycles; false on time-out.  hint_ns > 0 lets each try
+// suspend the thread for up to that many nanoseconds (fewer tries, a later
+// wake-up); 0 tries with the hardware's own short suspension.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit, uint32_t hint_ns = 0) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity), "r"(20000u)
-        : "memory");
+    if (hint_ns)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity), "r"(hint_ns)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
     if (done) return true;
     if (clock64() - t0 > limit) return false;
   }
@@ -335,10 +311,8 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-// The device error word: bits of the codes below, set by any tile kernel
-// that gave up a wait; read and cleared by the host (tile_error).
-__device__ unsigned g_tile_error = 0u;
-// Error codes recorded in the device error word (bits).
+// Error codes recorded in the device error word (bits); the word lives in
+// group.cu and its device address travels in the kernel arguments.
 constexpr unsigned kErrConsumerWait = 1u;  // a consumer gave up waiting for a tile
 constexpr unsigned kErrProducerWait = 2u;  // the producer gave up waiting for a free buffer
 constexpr unsigned kErrDrainWait = 4u;     // copies still in flight when the kernel gave up
@@ -358,6 +332,10 @@ struct TileArgs {
   int32_t nstages;        // 2 .. kMaxStages tiles in flight per block
   long long wait_limit;   // clock cycles any wait may take
   int32_t hang_test;      // 1: the consumers also wait on a barrier nothing completes (test of the time-out)
+  uint32_t wait_hint_ns;  // suspension hint of the consumers' waits (0: none)
+  unsigned* err;          // the device error word
+  Bounds bd;              // bounds-checked build: input and output rows, blob words (nnz)
+  int32_t max_groups;     // groups per tile of the table
 };
 
 constexpr int kMaxStages = 4;
@@ -365,8 +343,8 @@ constexpr int kMaxStages = 4;
 // Block: NC consumer warps (warp 0 .. NC-1), then one producer warp.  Tiles
 // t0 + blockIdx.x, + gridDim.x, ...; the block's k-th tile goes to stage
 // k % nstages, the (k / nstages)-th use of that stage.
-template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int BATCH, int MODE>
-__global__ void __launch_bounds__(256, 2) tile_kernel(const TileArgs a) {
+template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int BATCH>
+__global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
   constexpr int LB = 32 * (VA + VB);  // levels per level block
   constexpr uint32_t ES = sizeof(S);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -425,12 +403,35 @@ __global__ void __launch_bounds__(256, 2) tile_kernel(const TileArgs a) {
         if (lane == 0) got = mbar_wait(empty, (use - 1) & 1u, a.wait_limit);
         got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
         if (!got) {
-          if (lane == 0) atomicOr(&g_tile_error, kErrProducerWait);
+          if (lane == 0) atomicOr(a.err, kErrProducerWait);
           ok = false;
         }
       }
       if (!ok) break;
       const uint32_t sbase = base + static_cast<uint32_t>(st) * a.stage_bytes;
+      if constexpr (kBoundsCheck) {
+        // the header's sizes and copy ranges against the stage and the
+        // field rows of the launch; a tile that fails is not copied: its
+        // stage gets an empty table (no groups) and its barrier completes
+        const bool hv = nranges >= 0 && nranges <= kTileRanges && slots >= 0 &&
+                        static_cast<int64_t>(slots) * row_bytes <= a.rows_bytes && bbytes >= 16 && bbytes % 16 == 0 &&
+                        static_cast<uint32_t>(NIN) * a.rows_bytes + static_cast<uint32_t>(bbytes) <= a.stage_bytes &&
+                        boff >= 0 && boff % 4 == 0 && static_cast<int64_t>(boff) + bbytes / 4 <= a.bd.nnz;
+        const bool rv = lane >= nranges || (cur.r.y >= 0 && cur.r.x >= a.bd.lo &&
+                                            static_cast<int64_t>(cur.r.x) + cur.r.y <= a.bd.hi && cur.r.z >= 0 &&
+                                            cur.r.z + cur.r.y <= slots);
+        if (!__all_sync(0xffffffffu, hv && rv)) {
+          if (lane == 0) {
+            in_bounds(false, a.bd.err, BC_TILE_HEAD, t);
+            const uint32_t tb = sbase + static_cast<uint32_t>(NIN) * a.rows_bytes;
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(tb), "r"(0u) : "memory");
+            mbar_expect_tx(full, 0u);
+          }
+          __syncwarp();
+          cur = nxt;
+          continue;
+        }
+      }
       if (lane == 0)
         mbar_expect_tx(full, static_cast<uint32_t>(NIN) * static_cast<uint32_t>(slots) * static_cast<uint32_t>(row_bytes) +
                                  static_cast<uint32_t>(bbytes));
@@ -454,38 +455,48 @@ __global__ void __launch_bounds__(256, 2) tile_kernel(const TileArgs a) {
     if (lane == 0) {
       for (int kk = (k >= ns ? k - ns : 0); kk < k; ++kk)
         if (!mbar_wait(full0 + 8 * (kk % ns), static_cast<uint32_t>(kk / ns) & 1u, a.wait_limit))
-          atomicOr(&g_tile_error, kErrDrainWait);
+          atomicOr(a.err, kErrDrainWait);
     }
     return;
   }
 
   // -------------------------------------------------------------- consumers
   if (a.hang_test && !mbar_wait(hang, 0u, a.wait_limit)) {
-    if (lane == 0) atomicOr(&g_tile_error, kErrConsumerWait);
+    if (lane == 0) atomicOr(a.err, kErrConsumerWait);
     return;
   }
   int k = 0;
   for (int32_t t = a.t0 + static_cast<int32_t>(blockIdx.x); t < a.t0 + a.ntiles; t += static_cast<int32_t>(gridDim.x), ++k) {
     const int st = k % ns;
-    if (!mbar_wait(full0 + 8 * st, static_cast<uint32_t>(k / ns) & 1u, a.wait_limit)) {
-      if (lane == 0) atomicOr(&g_tile_error, kErrConsumerWait);
+    if (!mbar_wait(full0 + 8 * st, static_cast<uint32_t>(k / ns) & 1u, a.wait_limit, a.wait_hint_ns)) {
+      if (lane == 0) atomicOr(a.err, kErrConsumerWait);
       return;
     }
     const uint32_t sbase = base + static_cast<uint32_t>(st) * a.stage_bytes;
     const uint32_t blob = sbase + static_cast<uint32_t>(NIN) * a.rows_bytes;
     const int4 ti = lds_i4(blob);
-    const int ngt = ti.x, nent = ti.y;
+    int ngt = ti.x;
     const int32_t tfirst = ti.z;
+    // bounds-checked build: the stage's table capacity and row slots
+    const uint32_t blob_cap = a.stage_bytes - static_cast<uint32_t>(NIN) * a.rows_bytes;
+    const uint32_t slot_cap = a.rows_bytes / static_cast<uint32_t>(row_bytes);
+    if (!in_bounds(ngt >= 0 && ngt <= a.max_groups && 16u + 48u * static_cast<uint32_t>(ngt) <= blob_cap, a.bd.err,
+                   BC_TILE_TABLE, t))
+      ngt = 0;
     const uint32_t o_b = blob + 16u + 16u * static_cast<uint32_t>(ngt);
-    const uint32_t o_h = o_b + (HAS_B ? 32u * static_cast<uint32_t>(ngt) : 0u);
-    const uint32_t o_w = o_h + 4u * static_cast<uint32_t>(nent);
     uint32_t rows[2] = {sbase, sbase + a.rows_bytes};
     const uint32_t rb = static_cast<uint32_t>(row_bytes);
     for (int g = warp; g < ngt; g += nc) {
       const int4 gh = lds_i4(blob + 16u + 16u * static_cast<uint32_t>(g));
       const uint32_t slot0 = static_cast<uint32_t>(gh.x);
-      const int count = MODE == kTileMerged ? (gh.w >> 16) & 0xf : gh.w;
+      const int count = gh.w;
       const int32_t node0 = tfirst + 4 * g;
+      if (!in_bounds(count >= 0 && count <= 4 && gh.x >= 0 && slot0 + static_cast<uint32_t>(count) <= slot_cap &&
+                         gh.y >= 0 && gh.z >= 0 &&
+                         4ll * gh.y + (16ll + 32ll * NW) * gh.z <= static_cast<long long>(blob_cap) &&
+                         node0 >= a.bd.olo && static_cast<int64_t>(node0) + count <= a.bd.ohi,
+                     a.bd.err, BC_TILE_TABLE, t))
+        continue;
       for (int lb = 0; lb < a.nlb; ++lb) {
         const Layout<VA, VB> L(lb * LB, lane);
         Lv<VA, VB> xo[NIN][4], acc[NOUT][4];
@@ -500,106 +511,56 @@ __global__ void __launch_bounds__(256, 2) tile_kernel(const TileArgs a) {
 #pragma unroll
           for (int c = 0; c < NOUT; ++c) lv_zero(acc[c][gg]);
         }
-        if constexpr (MODE == kTileRows) {
-          // every node of the group walks its own stencil row, the four in
-          // step (four independent sums); D entries each, BATCH at a time
-          const uint32_t o_s = blob + 4u * static_cast<uint32_t>(gh.y);
-          const int D = gh.z;
-          const uint32_t o_ws = o_s + 16u * static_cast<uint32_t>(D);
-          auto step = [&](int e, Lv<VA, VB> (&x)[4][NIN], Wts<4 * NW>& W) {
-            const uint4 sl = lds_u4(o_s + 16u * static_cast<uint32_t>(e));
-            load_wts<4 * NW>(o_ws + 32u * NW * static_cast<uint32_t>(e), W);
-            const uint32_t sls[4] = {sl.x, sl.y, sl.z, sl.w};
+        // every node of the group walks its own stencil row, the four in
+        // step (four independent sums); D entries each, BATCH at a time
+        const uint32_t o_s = blob + 4u * static_cast<uint32_t>(gh.y);
+        const int D = gh.z;
+        const uint32_t o_ws = o_s + 16u * static_cast<uint32_t>(D);
+        auto step = [&](int e, Lv<VA, VB> (&x)[4][NIN], Wts<4 * NW>& W) {
+          const uint4 sl = lds_u4(o_s + 16u * static_cast<uint32_t>(e));
+          load_wts<4 * NW>(o_ws + 32u * NW * static_cast<uint32_t>(e), W);
+          uint32_t sls[4] = {sl.x, sl.y, sl.z, sl.w};
+          if constexpr (kBoundsCheck) {
 #pragma unroll
             for (int gg = 0; gg < 4; ++gg)
-#pragma unroll
-              for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
-          };
-          auto use = [&](const Lv<VA, VB> (&x)[4][NIN], const Wts<4 * NW>& W) {
-#pragma unroll
-            for (int gg = 0; gg < 4; ++gg) {
-              Lv<VA, VB> d;
-              lv_sub(x[gg][0], xo[0][gg], d);
-              if constexpr (NIN == 1 && NOUT == 1) {
-                lv_fma(W.w[gg], d, acc[0][gg]);
-              } else if constexpr (NIN == 1) {
-                lv_fma(W.w[2 * gg], d, acc[0][gg]);
-                lv_fma(W.w[2 * gg + 1], d, acc[1][gg]);
-              } else {
-                lv_fma(W.w[2 * gg], d, acc[0][gg]);
-                lv_sub(x[gg][1], xo[1][gg], d);
-                lv_fma(W.w[2 * gg + 1], d, acc[0][gg]);
-              }
-            }
-          };
-          int e = 0;
-          for (; e + BATCH <= D; e += BATCH) {
-            Lv<VA, VB> x[BATCH][4][NIN];
-            Wts<4 * NW> W[BATCH];
-#pragma unroll
-            for (int u = 0; u < BATCH; ++u) step(e + u, x[u], W[u]);
-#pragma unroll
-            for (int u = 0; u < BATCH; ++u) use(x[u], W[u]);
+              if (!in_bounds(sls[gg] < slot_cap, a.bd.err, BC_TILE_TABLE, t)) sls[gg] = slot0;
           }
-          for (; e < D; ++e) {
-            Lv<VA, VB> x[4][NIN];
-            Wts<4 * NW> W;
-            step(e, x, W);
-            use(x, W);
-          }
-        } else {
-          const int32_t q0 = gh.y, q1 = gh.z;
-          const int nb = gh.w & 0xffff, imask = (gh.w >> 20) & 0xf;
-          // merged entries [qs, qe): whole batches of BATCH, then one at a
-          // time; headers, weights and rows of a batch are requested before use
-          auto one = [&](int32_t q) {
-            const uint32_t hd = lds_u32(o_h + 4u * static_cast<uint32_t>(q));
-            Wts<4 * NW> W;
-            load_wts<4 * NW>(o_w + 32u * NW * static_cast<uint32_t>(q), W);
-            Lv<VA, VB> x[NIN];
-            const uint32_t off = (hd & 0x0fffffffu) * rb;
 #pragma unroll
-            for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + off, L, x[m]);
-            apply<NIN, NOUT, NW>(W, x, xo, acc);
-          };
-          auto run = [&](int32_t qs, int32_t qe) {
-            int32_t q = qs;
-            for (; q + BATCH <= qe; q += BATCH) {
-              uint32_t hd[BATCH];
-              Wts<4 * NW> W[BATCH];
-              Lv<VA, VB> x[BATCH][NIN];
+          for (int gg = 0; gg < 4; ++gg)
 #pragma unroll
-              for (int u = 0; u < BATCH; ++u) hd[u] = lds_u32(o_h + 4u * static_cast<uint32_t>(q + u));
+            for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
+        };
+        auto use = [&](const Lv<VA, VB> (&x)[4][NIN], const Wts<4 * NW>& W) {
 #pragma unroll
-              for (int u = 0; u < BATCH; ++u) load_wts<4 * NW>(o_w + 32u * NW * static_cast<uint32_t>(q + u), W[u]);
-#pragma unroll
-              for (int u = 0; u < BATCH; ++u) {
-                const uint32_t off = (hd[u] & 0x0fffffffu) * rb;
-#pragma unroll
-                for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + off, L, x[u][m]);
-              }
-#pragma unroll
-              for (int u = 0; u < BATCH; ++u) apply<NIN, NOUT, NW>(W[u], x[u], xo, acc);
-            }
-            for (; q < qe; ++q) one(q);
-          };
-          run(q0, q0 + nb);
-          // the internal run: own nodes that are neighbours of others of the
-          // group, in ascending order; values already in registers
-          int32_t q = q0 + nb;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (imask & (1 << u)) {
-              Wts<4 * NW> W;
-              load_wts<4 * NW>(o_w + 32u * NW * static_cast<uint32_t>(q), W);
-              Lv<VA, VB> x[NIN];
-#pragma unroll
-              for (int m = 0; m < NIN; ++m) x[m] = xo[m][u];
-              apply<NIN, NOUT, NW>(W, x, xo, acc);
-              ++q;
+          for (int gg = 0; gg < 4; ++gg) {
+            Lv<VA, VB> d;
+            lv_sub(x[gg][0], xo[0][gg], d);
+            if constexpr (NIN == 1 && NOUT == 1) {
+              lv_fma(W.w[gg], d, acc[0][gg]);
+            } else if constexpr (NIN == 1) {
+              lv_fma(W.w[2 * gg], d, acc[0][gg]);
+              lv_fma(W.w[2 * gg + 1], d, acc[1][gg]);
+            } else {
+              lv_fma(W.w[2 * gg], d, acc[0][gg]);
+              lv_sub(x[gg][1], xo[1][gg], d);
+              lv_fma(W.w[2 * gg + 1], d, acc[0][gg]);
             }
           }
-          run(q, q1);
+        };
+        int e = 0;
+        for (; e + BATCH <= D; e += BATCH) {
+          Lv<VA, VB> x[BATCH][4][NIN];
+          Wts<4 * NW> W[BATCH];
+#pragma unroll
+          for (int u = 0; u < BATCH; ++u) step(e + u, x[u], W[u]);
+#pragma unroll
+          for (int u = 0; u < BATCH; ++u) use(x[u], W[u]);
+        }
+        for (; e < D; ++e) {
+          Lv<VA, VB> x[4][NIN];
+          Wts<4 * NW> W;
+          step(e, x, W);
+          use(x, W);
         }
 #pragma unroll
         for (int gg = 0; gg < 4; ++gg) {
@@ -627,4 +588,47 @@ __global__ void __launch_bounds__(256, 2) tile_kernel(const TileArgs a) {
 }
 
 }  // namespace grp
+
+// Kernel of (operator shape, level layout, table layout) for storage S; the
+// instantiations live in group_f32.cu and group_bf16.cu.
+namespace grp {
+template <typename F>
+inline cudaError_t with_shape(const DevTiles& d, F&& f) {
+  if (d.nin == 1 && d.nout == 1) return f.template operator()<1, 1, false, 1>();
+  if (d.nin == 1 && d.nout == 2 && !d.has_b) return f.template operator()<1, 2, false, 2>();
+  if (d.nin == 1 && d.nout == 2) return f.template operator()<1, 2, true, 2>();
+  if (d.nin == 2 && d.nout == 1 && d.has_b) return f.template operator()<2, 1, true, 2>();
+  return cudaErrorInvalidValue;
+}
+
+template <typename S, int NIN, int NOUT, bool HAS_B, int NW>
+inline const void* kernel_of(int va, int vb) {
+  constexpr int BATCH = 2;  // steps (four nodes' entries each) whose rows are requested together
+#define ATLASGB_TILE(A, B) \
+  if (va == A && vb == B) return reinterpret_cast<const void*>(&tile_kernel<S, NIN, NOUT, HAS_B, NW, A, B, BATCH>);
+  ATLASGB_TILE(4, 2)
+  ATLASGB_TILE(4, 1)
+  ATLASGB_TILE(4, 0)
+  ATLASGB_TILE(2, 1)
+  ATLASGB_TILE(2, 0)
+  ATLASGB_TILE(1, 0)
+#undef ATLASGB_TILE
+  return nullptr;
+}
+
+template <typename S>
+struct Pick {
+  int va, vb;
+  const void* fn = nullptr;
+  template <int NIN, int NOUT, bool HAS_B, int NW>
+  cudaError_t operator()() {
+    fn = kernel_of<S, NIN, NOUT, HAS_B, NW>(va, vb);
+    return fn ? cudaSuccess : cudaErrorInvalidValue;
+  }
+};
+}  // namespace grp
+
+const void* tile_fn_f32(const DevTiles& d, int va, int vb);
+const void* tile_fn_bf16(const DevTiles& d, int va, int vb);
+
 }  // namespace atlasgb

@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "bounds.cuh"
 #include "kernels.h"
 
 namespace atlasgb {
@@ -174,11 +175,13 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
                                              const A* __restrict__ w, const A* __restrict__ b,
                                              const S* __restrict__ in0, const S* __restrict__ in1,
                                              S* __restrict__ out0, S* __restrict__ out1, int64_t ld, int32_t nlev,
-                                             int32_t i, int32_t lev0) {
+                                             int32_t i, int32_t lev0, const Bounds& bd) {
   using Idx = typename IdxT<IDX32>::T;
   const Idx ldx = static_cast<Idx>(ld);
   const Idx oi = static_cast<Idx>(i) * ldx + static_cast<Idx>(lev0);
-  const int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
+  if (!in_bounds(i >= bd.lo && i < bd.hi && i >= bd.olo && i < bd.ohi, bd.err, BC_OUTPUT, i)) return;
+  int32_t q0 = __ldg(ptr + i), q1 = __ldg(ptr + i + 1);
+  if (!in_bounds(q0 >= 0 && q0 <= q1 && q1 <= bd.nnz, bd.err, BC_ROW, i)) q0 = q1 = 0;
   A xi0[VEC], xi1[VEC], acc0[VEC], acc1[VEC];
   vload<S, A, VEC>(in0 + oi, xi0);
   if constexpr (NIN == 2) vload<S, A, VEC>(in1 + oi, xi1);
@@ -197,6 +200,7 @@ __device__ __forceinline__ void stencil_item(const int32_t* __restrict__ ptr, co
       int32_t j;
       A x0, x1;
       Entry<A, SCALAR_W, (NIN == 1)>::load(nbr, w, q, j, x0, x1);
+      if (real && !in_bounds(j >= bd.lo && j < bd.hi, bd.err, BC_NEIGHBOUR, q)) j = i;
       jj[t] = real ? j : i;
       wa[t] = real ? x0 : A(0);
       wb[t] = real ? x1 : A(0);
@@ -284,14 +288,15 @@ __global__ void __launch_bounds__(512) stencil_kernel(const int32_t* __restrict_
                                                       const S* __restrict__ in0, const S* __restrict__ in1,
                                                       S* __restrict__ out0, S* __restrict__ out1, int32_t node0,
                                                       int32_t count, int32_t nlev, int64_t ld, uint32_t nvec,
-                                                      Div32 dv, uint32_t tile) {
+                                                      Div32 dv, uint32_t tile, Bounds bd) {
   // nodes node0 .. node0 + count - 1 (all nodes, or one partition's own)
   const uint32_t total = static_cast<uint32_t>(count) * nvec;  // host guarantees < 2^31
   auto body = [&](uint32_t item) {
     const uint32_t k = div_by(item, dv);
     const uint32_t v = item - k * nvec;
     stencil_item<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, IDX32>(
-        ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev, node0 + static_cast<int32_t>(k), static_cast<int32_t>(v * VEC));
+        ptr, nbr, w, b, in0, in1, out0, out1, ld, nlev, node0 + static_cast<int32_t>(k), static_cast<int32_t>(v * VEC),
+        bd);
   };
   // FP32 and FP64 fields: a plain grid-stride loop, which measured 7-8%
   // faster than the tile walk for the one-ring operators (the tile length
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(kEdgeThreads) edge_flux_kernel(const int32_t* 
                                                                  const S* __restrict__ in0, const S* __restrict__ in1,
                                                                  A* __restrict__ flux0, A* __restrict__ flux1,
                                                                  uint32_t nedges, int32_t nlev, int64_t ld,
-                                                                 uint32_t nvec, Div32 dv) {
+                                                                 uint32_t nvec, Div32 dv, Bounds bd) {
   __shared__ int2 s_ab[kEdgeThreads];
   __shared__ A s_k[3][kEdgeThreads];
   const uint32_t total = nedges * nvec;
@@ -341,7 +346,10 @@ __global__ void __launch_bounds__(kEdgeThreads) edge_flux_kernel(const int32_t* 
     __syncthreads();  // the previous pass has read its stage
     for (uint32_t t = threadIdx.x; t < ne; t += blockDim.x) {
       const int64_t e = static_cast<int64_t>(e0) + t;
-      s_ab[t] = __ldg(reinterpret_cast<const int2*>(e2n) + e);
+      int2 ab = __ldg(reinterpret_cast<const int2*>(e2n) + e);
+      if (!in_bounds(ab.x >= bd.lo && ab.x < bd.hi && ab.y >= bd.lo && ab.y < bd.hi, bd.err, BC_EDGE_END, e))
+        ab = make_int2(bd.lo, bd.lo);
+      s_ab[t] = ab;
       s_k[0][t] = __ldg(coef + 3 * e);
       s_k[1][t] = __ldg(coef + 3 * e + 1);
       if constexpr (OP == 1) s_k[2][t] = __ldg(coef + 3 * e + 2);
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(kEdgeThreads) node_gather_kernel(const int32_t
                                                                    const A* __restrict__ flux1,
                                                                    const S* __restrict__ vin, S* __restrict__ out0,
                                                                    S* __restrict__ out1, int32_t nnodes, int32_t nlev,
-                                                                   int64_t ld, uint32_t nvec, Div32 dv) {
+                                                                   int64_t ld, uint32_t nvec, Div32 dv, Bounds bd) {
   __shared__ int32_t s_ptr[kEdgeThreads + 1];
   __shared__ int32_t s_ent[kGatherStage];
   __shared__ A s_node[3][kEdgeThreads];
@@ -420,7 +428,9 @@ __global__ void __launch_bounds__(kEdgeThreads) node_gather_kernel(const int32_t
     __syncthreads();
     const int32_t qfirst = s_ptr[0];
     const int32_t nq = s_ptr[nn] - qfirst;
-    const bool staged = nq <= kGatherStage;  // the same for the whole block
+    // bounds-checked build: a pass whose entries leave the table is not staged
+    const bool rows_ok = !kBoundsCheck || (qfirst >= 0 && nq >= 0 && static_cast<int64_t>(qfirst) + nq <= bd.nnz);
+    const bool staged = rows_ok && nq <= kGatherStage;  // the same for the whole block
     if (staged)
       for (int32_t t = static_cast<int32_t>(threadIdx.x); t < nq; t += static_cast<int32_t>(blockDim.x))
         s_ent[t] = __ldg(ent + qfirst + t);
@@ -436,9 +446,13 @@ __global__ void __launch_bounds__(kEdgeThreads) node_gather_kernel(const int32_t
         acc0[k] = A(0);
         acc1[k] = A(0);
       }
-      const int32_t q0 = s_ptr[li], q1 = s_ptr[li + 1];
+      int32_t q0 = s_ptr[li], q1 = s_ptr[li + 1];
+      if (!in_bounds(q0 >= 0 && q0 <= q1 && q1 <= bd.nnz && (!staged || (q0 >= qfirst && q1 - qfirst <= nq)), bd.err,
+                     BC_ROW, i))
+        q1 = q0;
       for (int32_t q = q0; q < q1; ++q) {
         const int32_t t = staged ? s_ent[q - qfirst] : __ldg(ent + q);
+        if (!in_bounds((t >> 1) >= bd.lo && (t >> 1) < bd.hi, bd.err, BC_EDGE_ID, q)) continue;
         const int64_t oe = static_cast<int64_t>(t >> 1) * ld + lev0;
         A f[VEC];
         vload<A, A, VEC>(flux0 + oe, f);
@@ -510,6 +524,12 @@ __global__ void __launch_bounds__(256, 5) batch_kernel(const __grid_constant__ B
     }
     const BatchDescDev& D = P.d[lo];
     const Div32 dv{D.div_m, D.div_s1, D.div_s2};
+    Bounds bd;
+    if constexpr (kBoundsCheck) {
+      bd.hi = bd.ohi = D.nnodes;
+      bd.nnz = D.nnz;
+      bd.err = P.err;
+    }
     const uint32_t it0 = static_cast<uint32_t>(t - D.tile0) * static_cast<uint32_t>(P.tile_items);
     const uint32_t it1 = min(it0 + static_cast<uint32_t>(P.tile_items), static_cast<uint32_t>(D.items));
     for (uint32_t u = it0 + threadIdx.x; u < it1; u += blockDim.x) {
@@ -519,12 +539,12 @@ __global__ void __launch_bounds__(256, 5) batch_kernel(const __grid_constant__ B
         stencil_item<S, A, 1, 2, VEC, false, false, 6, IDX32>(
             D.ptr, D.nbr, static_cast<const A*>(D.w), static_cast<const A*>(D.b), static_cast<const S*>(D.in0),
             static_cast<const S*>(D.in1), static_cast<S*>(D.out0), static_cast<S*>(D.out1), D.ld, D.nlev,
-            static_cast<int32_t>(i), lev0);
+            static_cast<int32_t>(i), lev0, bd);
       else
         stencil_item<S, A, 2, 1, VEC, true, false, 3, IDX32>(
             D.ptr, D.nbr, static_cast<const A*>(D.w), static_cast<const A*>(D.b), static_cast<const S*>(D.in0),
             static_cast<const S*>(D.in1), static_cast<S*>(D.out0), static_cast<S*>(D.out1), D.ld, D.nlev,
-            static_cast<int32_t>(i), lev0);
+            static_cast<int32_t>(i), lev0, bd);
     }
   }
 }
@@ -614,14 +634,17 @@ template <typename S, typename A, int VEC, bool IDX32>
 __global__ void __launch_bounds__(512) remap_kernel(const int4* __restrict__ tn, const A* __restrict__ tw,
                                                     const S* __restrict__ src, S* __restrict__ dst, int32_t ntgt,
                                                     int32_t nlev, int64_t ld_src, int64_t ld_dst, uint32_t nvec,
-                                                    Div32 dv) {
+                                                    Div32 dv, Bounds bd) {
   using Idx = typename IdxT<IDX32>::T;
   const uint32_t total = static_cast<uint32_t>(ntgt) * nvec;  // host guarantees < 2^31
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
     const uint32_t t = div_by(item, dv);
     const int32_t lev0 = static_cast<int32_t>((item - t * nvec) * VEC);
-    const int4 n = __ldg(tn + t);
+    int4 n = __ldg(tn + t);
+    if (!in_bounds(n.x >= bd.lo && n.x < bd.hi && n.y >= bd.lo && n.y < bd.hi && n.z >= bd.lo && n.z < bd.hi, bd.err,
+                   BC_REMAP, t))
+      n = make_int4(bd.lo, bd.lo, bd.lo, 0);
     const A w0 = __ldg(tw + 4 * static_cast<Idx>(t)), w1 = __ldg(tw + 4 * static_cast<Idx>(t) + 1),
             w2 = __ldg(tw + 4 * static_cast<Idx>(t) + 2);
     A x0[VEC], x1[VEC], x2[VEC], y[VEC];
@@ -634,6 +657,24 @@ __global__ void __launch_bounds__(512) remap_kernel(const int4* __restrict__ tn,
   }
 }
 
+// ------------------------------------------------------- FP64 FMA rate
+// Eight independent chains of FP64 fused multiply-adds per thread,
+// x <- x b + a (b < 1: the values stay bounded), iters steps each: 16 iters
+// flops per thread, enough independent work to keep the FP64 pipe of every
+// SM busy.  The sum of the chains is stored so nothing is optimised away.
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double* __restrict__ out, int64_t iters) {
+  const int t = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  const double a = 1.0e-3 + 1.0e-12 * t, b = 0.999999;
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1.0e-3 * k + 1.0e-9 * t;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], b, a);
+  }
+  out[t] = ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+}
+
 // ---------------------------------------------------------------- dispatch
 template <typename S, typename A, int NIN, int NOUT, int VEC, bool HAS_B, bool SCALAR_W, int BATCH>
 cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_t stream) {
@@ -644,12 +685,12 @@ cudaError_t run_stencil(const DevStencil& s, const StencilLaunch& l, cudaStream_
     stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, true><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
         static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), l.node0, l.count, l.nlev, l.ld,
-        nvec, dv, l.tile);
+        nvec, dv, l.tile, l.bd);
   else
     stencil_kernel<S, A, NIN, NOUT, VEC, HAS_B, SCALAR_W, BATCH, false><<<l.blocks, l.threads, 0, stream>>>(
         s.ptr, s.nbr, static_cast<const A*>(s.w), static_cast<const A*>(s.b), static_cast<const S*>(l.in0),
         static_cast<const S*>(l.in1), static_cast<S*>(l.out0), static_cast<S*>(l.out1), l.node0, l.count, l.nlev, l.ld,
-        nvec, dv, l.tile);
+        nvec, dv, l.tile, l.bd);
   return cudaGetLastError();
 }
 
@@ -709,6 +750,33 @@ struct StencilFn {
 
 }  // namespace
 
+// The bounds checks' device word pair {code, index} (bounds.cuh).
+__device__ unsigned long long g_bounds[2];
+
+bool bounds_checked() { return kBoundsCheck; }
+
+unsigned long long* bounds_word() {
+  if (!kBoundsCheck) return nullptr;
+  static void* addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev] && cudaGetSymbolAddress(&addr[dev], g_bounds) != cudaSuccess) addr[dev] = nullptr;
+  return static_cast<unsigned long long*>(addr[dev]);
+}
+
+cudaError_t bounds_error(unsigned long long* code, long long* index, bool clear) {
+  unsigned long long w[2] = {0, 0};
+  cudaError_t e = cudaMemcpyFromSymbol(w, g_bounds, sizeof(w));
+  if (e != cudaSuccess) return e;
+  *code = w[0];
+  *index = static_cast<long long>(w[1]);
+  if (clear && w[0] != 0) {
+    const unsigned long long z[2] = {0, 0};
+    e = cudaMemcpyToSymbol(g_bounds, z, sizeof(z));
+  }
+  return e;
+}
+
 // Host: multiplier and shifts of the branch-free division by d (d >= 1).
 Div32 make_div32(uint32_t d) {
   Div32 r{0, 0, 0};
@@ -740,18 +808,21 @@ cudaError_t run_edges(int op, const DevEdges& e, const void* in0, const void* in
   const uint32_t nvec = static_cast<uint32_t>((nlev + VEC - 1) / VEC);
   const Div32 dv = make_div32(nvec);
   const A* coef = static_cast<const A*>(e.coef);
+  Bounds bd;
+  bd.hi = bd.ohi = e.nnodes;
+  bd.err = bounds_word();
   if (op == 0)
     edge_flux_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
         e.e2n, coef, static_cast<const S*>(in0), nullptr, static_cast<A*>(flux0), static_cast<A*>(flux1),
-        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv, bd);
   else if (op == 2)
     edge_flux_kernel<S, A, 2, VEC><<<blocks, threads, 0, stream>>>(
         e.e2n, coef, static_cast<const S*>(in0), nullptr, static_cast<A*>(flux0), static_cast<A*>(flux1),
-        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv, bd);
   else
     edge_flux_kernel<S, A, 1, VEC><<<blocks, threads, 0, stream>>>(
         e.e2n, coef, static_cast<const S*>(in0), static_cast<const S*>(in1), static_cast<A*>(flux0), nullptr,
-        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv);
+        static_cast<uint32_t>(e.nedges), nlev, ld, nvec, dv, bd);
   return cudaGetLastError();
 }
 template <typename S, typename A, int VEC>
@@ -760,14 +831,19 @@ cudaError_t run_gather(int op, const DevEdges& e, const void* flux0, const void*
   const uint32_t nvec = static_cast<uint32_t>((nlev + VEC - 1) / VEC);
   const Div32 dv = make_div32(nvec);
   const A* node = static_cast<const A*>(e.node);
+  Bounds bd;  // input rows: the edges' fluxes; entries: the node->edge table
+  bd.hi = static_cast<int32_t>(e.nedges);
+  bd.ohi = e.nnodes;
+  bd.nnz = e.nent;
+  bd.err = bounds_word();
   if (op == 0)
     node_gather_kernel<S, A, 0, VEC><<<blocks, threads, 0, stream>>>(
         e.ptr, e.ent, node, static_cast<const A*>(flux0), static_cast<const A*>(flux1), nullptr, static_cast<S*>(out0),
-        static_cast<S*>(out1), e.nnodes, nlev, ld, nvec, dv);
+        static_cast<S*>(out1), e.nnodes, nlev, ld, nvec, dv, bd);
   else
     node_gather_kernel<S, A, 1, VEC><<<blocks, threads, 0, stream>>>(
         e.ptr, e.ent, node, static_cast<const A*>(flux0), nullptr, static_cast<const S*>(vin), static_cast<S*>(out0),
-        nullptr, e.nnodes, nlev, ld, nvec, dv);
+        nullptr, e.nnodes, nlev, ld, nvec, dv, bd);
   return cudaGetLastError();
 }
 }  // namespace
@@ -823,7 +899,7 @@ cudaError_t run_remap(const RemapLaunch& r, cudaStream_t stream) {
   const uint32_t nvec = static_cast<uint32_t>((r.nlev + VEC - 1) / VEC);
   remap_kernel<S, A, VEC, IDX32><<<r.blocks, r.threads, 0, stream>>>(
       static_cast<const int4*>(r.nodes), static_cast<const A*>(r.weights), static_cast<const S*>(r.src),
-      static_cast<S*>(r.dst), r.ntgt, r.nlev, r.ld_src, r.ld_dst, nvec, make_div32(nvec));
+      static_cast<S*>(r.dst), r.ntgt, r.nlev, r.ld_src, r.ld_dst, nvec, make_div32(nvec), r.bd);
   return cudaGetLastError();
 }
 template <typename S, typename A, int MAXVEC, bool IDX32>
@@ -856,6 +932,11 @@ cudaError_t launch_integral(StorageType st, const IntegralLaunch& l, cudaStream_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   integral_final_kernel<<<(l.nlev + 255) / 256, 256, 0, stream>>>(l.part, l.nblocks, l.nlev, l.out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_fma(double* out, int blocks, int threads, int64_t iters, cudaStream_t stream) {
+  fp64_fma_kernel<<<blocks, threads, 0, stream>>>(out, iters);
   return cudaGetLastError();
 }
 

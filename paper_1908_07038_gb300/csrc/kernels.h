@@ -19,6 +19,23 @@ struct Div32 {
   uint32_t s1, s2;
 };
 
+// Index bounds of one launch, checked by the kernels of the bounds-checked
+// build (ATLASGB_BOUNDSCHECK; see bounds.cuh) and ignored otherwise: input
+// rows [lo, hi) and output rows [olo, ohi) in global node ids, table entries
+// [0, nnz) (CSR entries, edges or source nodes, by kernel), and the device
+// word pair {code, index} the first violation is recorded in.
+struct Bounds {
+  int32_t lo = 0, hi = 0, olo = 0, ohi = 0;
+  int64_t nnz = 0;
+  unsigned long long* err = nullptr;
+};
+// The device word pair of the bounds checks on the current device (looked
+// up once per device), and a synchronous read of it (with clear, reset).
+unsigned long long* bounds_word();
+cudaError_t bounds_error(unsigned long long* code, long long* index, bool clear);
+// Whether this library was built with the kernels' bounds checks.
+bool bounds_checked();
+
 // Device tables of one node stencil (see Stencil in geometry.h).  One-input
 // operators with float weights (F32 and BF16 fields): w holds packed entries
 // {j, w} (scalar_w) or {j, w0, w1, 0} as 32-bit words and nbr is unused.
@@ -52,6 +69,7 @@ struct StencilLaunch {
   // its neighbours.
   int32_t node0 = 0;
   int32_t count = 0;
+  Bounds bd;
 };
 
 // Shared-memory node-group kernels (group.cu; tables as TileStencil in
@@ -64,10 +82,10 @@ struct DevTiles {
   int32_t ntiles = 0;
   int32_t max_slots = 0;  // most node rows a tile stages
   int32_t max_blob = 0;   // largest tile table (bytes)
+  int64_t blob_words = 0; // 32-bit words of blob
   int groups_per_tile = 8;
   int nin = 1, nout = 1, nw = 1;
   bool has_b = false;
-  int mode = 1;           // table layout: 0 merged entries, 1 per-node rows (kTileMerged, kTileRows)
 };
 struct TileLaunch {
   const void* in0 = nullptr;
@@ -83,11 +101,16 @@ struct TileLaunch {
   int max_bps = 2;
   long long wait_limit = 0;  // clock cycles a wait may take (0: the default, about one second)
   int hang_test = 0;         // 1: the consumers wait on a barrier nothing completes (tests the time-out)
+  uint32_t wait_hint_ns = 0; // suspension hint of the consumers' barrier waits (0: none)
+  Bounds bd;                 // input rows, output rows; nnz: the blob's 32-bit words
 };
 // Valid (va, vb) pairs: (1,0) (2,0) (2,1) (4,0) (4,1) (4,2).
 cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream);
 // Dynamic shared memory one block needs (two stages), or 0 above the limit.
 size_t tile_smem_bytes(const DevTiles& d, int64_t ld, int elem_size);
+// The launch shape launch_tiles would take: blocks per SM, stages per block
+// and dynamic shared memory per block (0s when the tiles do not fit).
+cudaError_t tile_shape(StorageType st, const DevTiles& d, const TileLaunch& l, int* bps, int* stages, size_t* smem);
 // Read (and with clear, reset) the device error word of the tile kernels
 // (a synchronous copy).
 cudaError_t tile_error(unsigned* code, bool clear);
@@ -101,6 +124,7 @@ struct DevEdges {
   const void* node = nullptr;     // [V][3] (1/V, cos/V, pole coefficient)
   int32_t nnodes = 0;
   int64_t nedges = 0;
+  int64_t nent = 0;               // entries of ent
 };
 
 // Persistent batched launch: one descriptor per field.
@@ -121,6 +145,8 @@ struct BatchDescDev {
   int32_t op;         // 0 gradient (1 in, 2 out), 1 divergence (2 in, 1 out, with b)
   uint32_t div_m;     // division by nvec (see Div32)
   uint32_t div_s1, div_s2;
+  int32_t nnodes;     // nodes of the field (rows of in0/in1/out0/out1)
+  int64_t nnz;        // CSR entries of the table
 };
 // The whole table travels as one kernel parameter (at most 32 KB).
 constexpr int kBatchMaxDesc = 256;
@@ -130,6 +156,7 @@ struct BatchParams {
   int32_t ntiles;
   int32_t tile_items;
   int32_t pad;
+  unsigned long long* err;  // the bounds checks' word pair (bounds-checked build)
   BatchDescDev d[kBatchMaxDesc];
 };
 static_assert(sizeof(BatchParams) <= 32764, "kernel parameters are limited to 32764 bytes");
@@ -138,6 +165,8 @@ cudaError_t launch_stencil(StorageType st, const DevStencil& s, const StencilLau
 // Maximum resident blocks per SM of the stencil kernel for this configuration.
 int stencil_occupancy(StorageType st, const DevStencil& s, int vec, int batch, int threads);
 
+// The two passes check their tables against the mesh: node ids [0, nnodes),
+// edge ids [0, nedges).
 cudaError_t launch_edge_flux(StorageType st, int op, const DevEdges& e, const void* in0, const void* in1,
                              void* flux0, void* flux1, int32_t nlev, int64_t ld, int vec, int threads,
                              int blocks, cudaStream_t stream);
@@ -146,6 +175,9 @@ cudaError_t launch_node_gather(StorageType st, int op, const DevEdges& e, const 
                                int threads, int blocks, cudaStream_t stream);
 
 Div32 make_div32(uint32_t d);
+
+// FP64 rate probe: blocks x threads threads, 8 chains of iters FMAs each.
+cudaError_t launch_fp64_fma(double* out, int blocks, int threads, int64_t iters, cudaStream_t stream);
 
 // Library-owned static device scratch (noalloc.cu): its size, and its device
 // address on the current device (looked up once per device).
@@ -167,6 +199,7 @@ struct RemapLaunch {
   int vec = 1;
   bool idx32 = true;
   int threads = 256, blocks = 1;
+  Bounds bd;  // source rows [lo, hi)
 };
 cudaError_t launch_remap(StorageType st, const RemapLaunch& r, cudaStream_t stream);
 

@@ -13,9 +13,11 @@
 // library holds it (kScratchBytes) until the process exits.  Its device
 // address is looked up once per device (cudaGetSymbolAddress) on the first
 // call made with that device current; that first call should therefore come
-// before any stream capture.  All calls on a device share the array and it
-// keeps the last call's contents; calls that overlap on the GPU (different
-// streams without ordering) race on it.
+// before any stream capture.  The address stays cached: after a
+// cudaDeviceReset, which also invalidates every fvm's device tables, the
+// entry point must not be called again in the process.  All calls on a
+// device share the array and it keeps the last call's contents; calls that
+// overlap on the GPU (different streams without ordering) race on it.
 #include <cuda_runtime.h>
 
 #include <cstddef>

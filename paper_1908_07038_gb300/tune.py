@@ -1,14 +1,17 @@
 """Autotuner of the launch shapes of the nabla kernels.
 
-For every operator the node-stencil kernel has five free parameters that do
-not change its result (bitwise): levels per thread (``vec``), CSR entries per
-load batch (``batch``), threads per block, blocks per SM and the length of
-the item tile each block walks (``tile``, in passes of the block).  ``tune_fvm``
-times each candidate with CUDA events on the real field sizes and installs
-the fastest with ``atlas_fvm_set_launch``; ``tune_batch`` does the same for
-the tile size and block shape of a persistent batched launch.  Results are
-cached in the JSON file named by ``ATLASGB_TUNE_CACHE`` (if set), keyed by
-device name, grid, dtype, level count and leading dimension.
+Every operator has two kernels whose results are bitwise equal: the
+shared-memory node-group (tile) kernel, with the groups per tile and the
+blocks per SM free (``atlas_fvm_set_group``), and the per-node kernel, with
+five free parameters: levels per thread (``vec``), CSR entries per load
+batch (``batch``), threads per block, blocks per SM and the length of the
+item tile each block walks (``tile``, in passes of the block;
+``atlas_fvm_set_launch``).  ``tune_fvm`` times each candidate of both with
+CUDA events on the real field sizes and installs the fastest;
+``tune_batch`` does the same for the tile size and block shape of a
+persistent batched launch.  Results are cached in the JSON file named by
+``ATLASGB_TUNE_CACHE`` (if set), keyed by device name, grid, dtype, level
+count and leading dimension.
 """
 from __future__ import annotations
 
@@ -26,6 +29,8 @@ CANDIDATES = {
     ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1,)),
     ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8, 64)),
 }
+# node-group (tile) kernel candidates: (groups per tile, blocks per SM)
+TILE_CANDIDATES = ((7, 1), (5, 1), (4, 1), (3, 2))
 _TORCH_DT = None
 
 
@@ -120,26 +125,47 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         if key in cache:
             c = cache[key]
             fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1), dtype=dtype)
+            if c.get("kernel", "node") == "tile":
+                fvm.set_group(op, 1, c["tile_bps"], c["groups"], dtype=dtype)
+            else:
+                fvm.set_group(op, 0, dtype=dtype)
             best[op] = c
             continue
         ins = (fields[1], fields[2]) if op in ("divergence", "gradient_adjoint", "curl", "vector_gradient") \
             else (fields[0],)
         cand = CANDIDATES[dtype]
         results = []
+        # the per-node kernel's shapes
+        fvm.set_group(op, 0, dtype=dtype)
         for vec, batch, threads, bps, tile in itertools.product(cand["vec"], cand["batch"], cand["threads"],
                                                                 cand["bps"], cand["tile"]):
             fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
             ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
-            results.append((ms, vec, batch, threads, bps, tile))
+            results.append((ms, "node", vec, batch, threads, bps, tile, 0, 0))
             if verbose:
-                print("tune %-18s vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
+                print("tune %-18s node vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
                       (op, vec, batch, threads, bps, tile, ms))
-        ms, vec, batch, threads, bps, tile = min(results)
+        _, _, vec, batch, threads, bps, tile, _, _ = min(results)
         fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
-        best[op] = dict(vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, ms=ms,
-                        sweep=[dict(ms=r[0], vec=r[1], batch=r[2], threads=r[3], bps=r[4], tile=r[5])
-                               for r in results])
-        cache[key] = {k: best[op][k] for k in ("vec", "batch", "threads", "bps", "tile", "ms")}
+        # the tile kernel's shapes (where it applies to these fields)
+        if fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
+            for groups, tbps in TILE_CANDIDATES:
+                fvm.set_group(op, 1, tbps, groups, dtype=dtype)
+                ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
+                results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps))
+                if verbose:
+                    print("tune %-18s tile groups=%d bps=%d: %.4f ms" % (op, groups, tbps, ms))
+        ms, kernel, vec, batch, threads, bps, tile, groups, tbps = min(results)
+        if kernel == "tile":
+            fvm.set_group(op, 1, tbps, groups, dtype=dtype)
+        else:
+            fvm.set_group(op, 0, dtype=dtype)
+        best[op] = dict(kernel=kernel, vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, groups=groups,
+                        tile_bps=tbps, ms=ms,
+                        sweep=[dict(ms=r[0], kernel=r[1], vec=r[2], batch=r[3], threads=r[4], bps=r[5], tile=r[6],
+                                    groups=r[7], tile_bps=r[8]) for r in results])
+        cache[key] = {k: best[op][k] for k in ("kernel", "vec", "batch", "threads", "bps", "tile", "groups",
+                                              "tile_bps", "ms")}
     _store_cache(cache)
     return best
 

@@ -63,3 +63,82 @@ def test_damaged_files_are_refused(atlas, product, tmp_path):
         assert ei.value.code == -1 and why in str(ei.value), (name, str(ei.value))
         cases[why] = True
     assert all(cases.values())
+
+
+# ---------------------------------------------------------------- file pieces
+_FNV_OFFSET, _FNV_PRIME, _M64 = 1469598103934665603, 1099511628211, (1 << 64) - 1
+# vectors of a geometry file in write order, with their element types
+_VECS = (("pl", "<i4"), ("off", "<i8"), ("colat", "<f8"), ("lat", "<f8"), ("lonlat", "<f8"), ("xy", "<f8"),
+         ("h", "<f8"), ("e2n", "<i4"), ("is_pole", "u1"), ("n2e_ptr", "<i4"), ("n2e", "<i4"), ("n2e_sign", "<i1"),
+         ("tri", "<i4"), ("side_off", "<f8"), ("side_lat", "<f8"), ("mid_lat", "<f8"), ("S", "<f8"), ("V", "<f8"),
+         ("coslat", "<f8"), ("pole_nphi", "<f8"), ("A", "<f8"), ("Sb", "<f8"))
+
+
+def _pieces(raw):
+    """Split a geometry file into the pieces its writer hashed one by one:
+    magic, version, reserved word, eight sizes, the radius, eight projection
+    parameters, then per vector (length, element size, reserved, data);
+    returns [(offset, length)] and the offsets of each vector's data."""
+    out, data, o = [], {}, 0
+
+    def take(n):
+        nonlocal o
+        out.append((o, n))
+        o += n
+
+    for n in (8, 4, 4) + (8,) * 8 + (8,) + (8,) * 8:
+        take(n)
+    for name, dt in _VECS:
+        n = int(np.frombuffer(raw, "<u8", 1, o)[0])
+        es = int(np.frombuffer(raw, "<u4", 1, o + 8)[0])
+        assert es == np.dtype(dt).itemsize, (name, es)
+        take(8), take(4), take(4)
+        data[name] = (o, n, dt)
+        if n:
+            take(n * es)
+    assert o == len(raw) - 8
+    return out, data
+
+
+def _fnv(raw, pieces):
+    """The file's checksum: FNV-1a over each piece's 64-bit little-endian
+    words, then its remaining bytes."""
+    h = _FNV_OFFSET
+    for o, n in pieces:
+        k = 0
+        while k + 8 <= n:
+            h = ((h ^ int.from_bytes(raw[o + k:o + k + 8], "little")) * _FNV_PRIME) & _M64
+            k += 8
+        for c in raw[o + k:o + n]:
+            h = ((h ^ c) * _FNV_PRIME) & _M64
+    return h
+
+
+def test_out_of_range_connectivity_is_refused_before_any_launch(atlas, product, tmp_path):
+    """A geometry file whose checksum is right but whose edge table points
+    past the last node (a corrupted table, not a damaged file) is refused by
+    the host validation of atlas_fvm_load, with the reason; no table built
+    from it ever reaches a kernel.  The same holds for a node->edge entry
+    past the last edge."""
+    capi = product[1]
+    fvm = atlas.build_fvm(8)
+    path = tmp_path / "geom.bin"
+    fvm.save(path)
+    raw = bytearray(path.read_bytes())
+    pieces, data = _pieces(raw)
+    assert _fnv(raw, pieces) == int.from_bytes(raw[-8:], "little")  # the checksum is understood
+    V, E = fvm.nnodes, fvm.mesh.nedges
+    for name, index, value, why in (("e2n", 2 * (E // 2) + 1, V + 5, "edge ends out of range"),
+                                    ("n2e", 7, E + 3, "edge id out of range (node 1)")):
+        bad = bytearray(raw)
+        o, n, dt = data[name]
+        es = np.dtype(dt).itemsize
+        bad[o + index * es:o + (index + 1) * es] = int(value).to_bytes(es, "little", signed=True)
+        bad[-8:] = _fnv(bad, pieces).to_bytes(8, "little")
+        p = tmp_path / ("bad_%s.bin" % name)
+        p.write_bytes(bytes(bad))
+        with pytest.raises(capi.AtlasError) as ei:
+            atlas.load_fvm(p)
+        assert ei.value.code == -1 and "inconsistent" in str(ei.value) and why in str(ei.value), (name, str(ei.value))
+    # the untouched bytes still load
+    assert atlas.load_fvm(path).nnodes == V

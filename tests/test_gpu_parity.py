@@ -267,3 +267,38 @@ def test_o1280_137_fp32_sampled(torch, pfvm, omesh):
 def test_o1280_137_fp64_sampled(torch, pfvm, omesh):
     w64 = _sampled_case(torch, pfvm, omesh, 1280, 137, 3000, np.float64, TOL["f64"], 138)
     assert max(w64.values()) <= TOL["f64"], w64
+
+
+def test_o1280_64bit_element_offsets(torch, pfvm, omesh):
+    """O1280 with ld = 328: nnodes * ld = 2.16e9 elements, past 2^31, so the
+    per-node kernels take their 64-bit offset form (the tiles do not fit in
+    shared memory at this ld, so every operator runs per node); 8 levels,
+    sampled nodes against the oracle."""
+    fvm, om = pfvm(1280), omesh(1280)
+    g = om.grid()
+    V, nlev, ld = om.nnodes, 8, 328
+    assert V * ld >= 2 ** 31
+    off = np.concatenate([[0], np.cumsum(g["pl"])])
+    nodes = synthetic.sample_nodes(V, off, 4000)
+    f = synthetic.level_scalar(g["lon"], g["lat_node"], nlev, np.float32)
+    u, v = synthetic.level_vector(g["lon"], g["lat_node"], nlev, np.float32)
+    assert fvm.tile_info("gradient", nlev, ld)["stages"] == 0  # per node at this ld
+    big = []
+    for x in (f, u, v):
+        t = torch.zeros((V, ld), device="cuda")
+        t[:, :nlev] = torch.from_numpy(x).cuda()
+        big.append(t)
+    tf, tu, tv = big
+    idx = torch.from_numpy(nodes).cuda()
+    pick = lambda t: t.index_select(0, idx)[:, :nlev].double().cpu().numpy()
+    gx, gy = fvm.gradient(tf, nlev)
+    wx, wy = om.gradient(f, nlev, nodes=nodes)
+    assert _relmax(pick(gx), wx) <= TOL["f32"] and _relmax(pick(gy), wy) <= TOL["f32"]
+    del gx, gy
+    d = fvm.divergence(tu, tv, nlev)
+    assert _relmax(pick(d), om.divergence(u, v, nlev, nodes=nodes)) <= TOL["f32"]
+    del d
+    lap = fvm.laplacian(tf, nlev)
+    assert _relmax(pick(lap), om.laplacian(f, nlev, nodes=nodes)) <= TOL["f32"]
+    del lap, tf, tu, tv, big
+    torch.cuda.empty_cache()

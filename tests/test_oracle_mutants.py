@@ -21,6 +21,7 @@ from test_oracle_grid import test_latitudes_match_legendre_roots as _latitudes_t
 from test_oracle_integral import test_exact_against_fractions as _fractions_test
 from test_oracle_operators import test_adjoints_are_bruteforce_transposes as _transposes_test
 from test_oracle_operators import test_node_subsets_match_full_evaluation as _subsets_test
+from test_oracle_operators import convergence_orders, orders_meet_floors
 from test_oracle_regional import test_scale_factors_and_orthogonality_from_chords as _chords_test
 from test_oracle_regional import test_cell_areas_and_closure as _areas_test
 from test_oracle_regional import test_linear_fields_are_exact_everywhere as _linear_test
@@ -85,6 +86,10 @@ def pin_gradient_closed_form():
     gx, gy = m.gradient(np.cos(phi) * np.cos(lam))
     e = np.hypot(gx[:, 0] + np.sin(lam) / R, gy[:, 0] + np.sin(phi) * np.cos(lam) / R) * R
     return e[np.abs(phi) < np.radians(60)].max() <= 0.05  # 0.014 for the scheme
+
+
+def pin_convergence_orders():
+    return orders_meet_floors(convergence_orders(oracle.Mesh))
 
 
 def pin_sphere_area():
@@ -209,6 +214,12 @@ MUTANTS = [
      "      double d = 0.5 * (fld(f, f32, ld, j, k) - fi);\n      acc_add_prod(&al, nl, d);\n"
      "      acc_add_prod(&ap, np, d);\n    }\n    gx[k] = acc_val(&al) / m->V[i];\n"
      "    gy[k] = acc_val(&ap) / m->V[i];", pin_gradient_closed_form),
+    ("cross-row edge midpoints at a third of the row spacing (first-order volumes)", "global",
+     "double mphi = (tr[ia] == tr[ib]) ? phia : 0.5 * (m->lat[r] + m->lat[s]);",
+     "double mphi = (tr[ia] == tr[ib]) ? phia : (2.0 * m->lat[r] + m->lat[s]) / 3.0;", pin_convergence_orders),
+    ("centroid latitude as the mean of two rows (order pin)", "global",
+     "double cphi = ((m->lat[p] + m->lat[p]) + m->lat[qq]) / 3.0;",
+     "double cphi = (m->lat[p] + m->lat[qq]) / 2.0;", pin_convergence_orders),
     ("pole segment dropped from the volumes", "global",
      "acc_add(&vacc[m->off[rr] + j], ipole);", "(void)ipole;", pin_sphere_area),
     ("centroid latitude as the mean of two rows", "global",

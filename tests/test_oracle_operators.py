@@ -3,14 +3,19 @@ forms and convergence, spherical-harmonic Laplacians, and the adjoints
 against brute-force transposes and finite differences.
 
 Operators named in the paper (Sec. 2.3): gradient, divergence, Laplacian.
-Convergence reading: this median-dual scheme is consistent in the interior
-but its cells at the zipper seams and in the first and last rows are not
-symmetric, so pointwise errors there decay at first order (the polar row
-keeps an O(1) relative error); the volume-weighted L2 error over the band
-|lat| < 60 deg is asserted to decay at order >= 1.2 on each refinement and
->= 1.35 on the last (O32 -> O64), and the full-sphere gradient error at
-order >= 0.9.  The measured orders are reported in the
-design notes.
+
+Convergence reading.  The median-dual cells of the octahedral grid are
+smooth inside each octant, and there the scheme converges at second order;
+along the octant seams (the meridians at multiples of 90 deg and the
+equator, where the row triangulation turns) and in the polar rows the cells
+are not symmetric and pointwise errors decay at first order only.  Seams
+are lines, so over a band that contains them the volume-weighted L2 error
+decays at about order 1.5.  The floors asserted below sit 0.03 to 0.09 under
+the measured orders (O16 -> O32 -> O64; measured, O32 -> O64: gradient 1.78
+and divergence 1.95 in the octant interiors, 1.47 and 1.59 over the band
+|lat| < 60 deg, 0.99 for the gradient over the whole sphere), so a mistake
+that costs half an order fails them (two such mutants are planted in the
+mutant tests).
 """
 import numpy as np
 import pytest
@@ -28,9 +33,49 @@ def _slopes(errs):
     return [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
 
 
-def _bulk_order_ok(errs):
+# floors: (each refinement, the last refinement O32 -> O64)
+FLOORS = {"gradient_interior": (1.5, 1.7), "divergence_interior": (1.8, 1.9),
+          "gradient_band": (1.3, 1.4), "divergence_band": (1.5, 1.55), "rotation_band": (1.25, 1.4),
+          "gradient_sphere": (0.95, 0.95)}
+
+
+def _bulk_order_ok(errs, floor=(1.25, 1.4)):
     s = _slopes(errs)
-    return min(s) >= 1.2 and s[-1] >= 1.35
+    return min(s) >= floor[0] and s[-1] >= floor[1]
+
+
+def octant_interior(lam, phi, margin_deg=3.0):
+    """Nodes of the band |lat| < 60 deg at least margin_deg from the octant
+    seams (the meridians at multiples of 90 deg and the equator)."""
+    dl = np.degrees(np.abs((lam + np.pi / 4) % (np.pi / 2) - np.pi / 4))
+    return (np.abs(phi) < np.radians(60)) & (dl >= margin_deg) & (np.degrees(np.abs(phi)) >= margin_deg)
+
+
+def convergence_orders(mesh_of):
+    """Orders of the volume-weighted L2 errors of the closed-form gradient
+    (f = cos lat cos lon) and divergence ((u, v) = (cos lat, 0.1 sin lon cos
+    lat)) on O16, O32, O64, over the octant interiors, the band
+    |lat| < 60 deg and (gradient) the whole sphere; mesh_of(N) gives the
+    oracle mesh."""
+    errs = {k: [] for k in FLOORS if k != "rotation_band"}
+    for N in (16, 32, 64):
+        m = mesh_of(N)
+        lam, phi, V = _fields(m)
+        band, inner = np.abs(phi) < np.radians(60), octant_interior(lam, phi)
+        gx, gy = m.gradient(np.cos(phi) * np.cos(lam))
+        e = np.hypot(gx[:, 0] + np.sin(lam) / R, gy[:, 0] + np.sin(phi) * np.cos(lam) / R) * R
+        errs["gradient_interior"].append(_l2(V, e, inner))
+        errs["gradient_band"].append(_l2(V, e, band))
+        errs["gradient_sphere"].append(_l2(V, e))
+        d = m.divergence(np.cos(phi), 0.1 * np.sin(lam) * np.cos(phi))[:, 0] * R
+        e = d + 0.2 * np.sin(lam) * np.sin(phi)
+        errs["divergence_interior"].append(_l2(V, e, inner))
+        errs["divergence_band"].append(_l2(V, e, band))
+    return {k: _slopes(v) for k, v in errs.items()}
+
+
+def orders_meet_floors(orders):
+    return all(min(s) >= FLOORS[k][0] and s[-1] >= FLOORS[k][1] for k, s in orders.items())
 
 
 def test_gradient_of_constant_is_exactly_zero(omesh):
@@ -48,18 +93,12 @@ def _fields(m):
     return g["lon"], g["lat_node"], m.dual()["V"]
 
 
-def test_gradient_convergence(omesh):
-    bulk_err, full_err = [], []
-    for N in (16, 32, 64):
-        m = omesh(N)
-        lam, phi, V = _fields(m)
-        gx, gy = m.gradient(np.cos(phi) * np.cos(lam))
-        e = np.hypot(gx[:, 0] + np.sin(lam) / R, gy[:, 0] + np.sin(phi) * np.cos(lam) / R) * R
-        bulk = np.abs(phi) < np.radians(60)
-        bulk_err.append(_l2(V, e, bulk))
-        full_err.append(_l2(V, e))
-    assert _bulk_order_ok(bulk_err)
-    assert min(_slopes(full_err)) >= 0.9
+def test_gradient_and_divergence_convergence(omesh):
+    """Second order in the octant interiors, about 1.5 over the band, first
+    order over the whole sphere (the polar rows)."""
+    orders = convergence_orders(omesh)
+    for k, s in orders.items():
+        assert min(s) >= FLOORS[k][0] and s[-1] >= FLOORS[k][1], (k, s)
 
 
 @pytest.mark.parametrize("alpha", [0.0, np.pi / 4])
@@ -75,7 +114,7 @@ def test_solid_body_rotation_divergence_free(omesh, alpha):
     if alpha == 0.0:
         assert max(errs) <= 1e-13  # zonal flow: exact to rounding
     else:
-        assert _bulk_order_ok(errs)
+        assert _bulk_order_ok(errs, FLOORS["rotation_band"]), _slopes(errs)
 
 
 def test_divergence_closed_form(omesh):
@@ -86,7 +125,7 @@ def test_divergence_closed_form(omesh):
         lam, phi, V = _fields(m)
         d = m.divergence(np.cos(phi), 0.1 * np.sin(lam) * np.cos(phi))[:, 0] * R
         errs.append(_l2(V, d + 0.2 * np.sin(lam) * np.sin(phi), np.abs(phi) < np.radians(60)))
-    assert _bulk_order_ok(errs)
+    assert _bulk_order_ok(errs, FLOORS["divergence_band"]), _slopes(errs)
 
 
 def _real_sph_harm(l, m_, lam, phi):
