@@ -634,23 +634,31 @@ def run_native(args):
         for N, fv in fvms.items():
             fv.prepare(("gradient", "divergence"), dtypes=(atlas.ATLAS_F32,))
             tune.tune_fvm(fv, atlas.ATLAS_F32, 137, 140, ("gradient", "divergence"), reps=2)
+
+        def graph_ms(cfg):
+            bb = B.Batch(jobs, tune=cfg)
+            bb.capture()
+            ms = tune.time_call(bb.replay, reps=20, warmup=3)
+            n = bb.node_levels
+            bb.close()
+            return ms, n
+
+        # the library's default split (fields of four waves and more in plain
+        # launches of their own, the rest in one persistent launch), the
+        # tuned split, and every field in the persistent launch
+        ms_default, nl = graph_ms(None)
         bt, bt_cfg, _ = tune.tune_batch(lambda c: B.Batch(jobs, tune=c), reps=5)
-        bt.capture()
-        nl = bt.node_levels
-        ms_graph = tune.time_call(bt.replay, reps=20, warmup=3)
-        ms_plain = tune.time_call(lambda: B.plain(jobs), reps=20, warmup=3)
         bt.close()
-        # the same batch with the fields of eight or more full GPU waves in
-        # plain launches of their own (the small ones stay persistent)
-        bh = B.Batch(jobs, tune=dict(bt_cfg, plain_waves=8))
-        bh.capture()
-        ms_hybrid = tune.time_call(bh.replay, reps=20, warmup=3)
-        bh.close()
-        batched = {"fields": len(jobs), "node_levels": nl, "graph_replay_ms": round(ms_graph, 4),
+        ms_tuned, _ = graph_ms(bt_cfg)
+        ms_persistent, _ = graph_ms(dict(bt_cfg, plain_waves=-1))
+        ms_plain = tune.time_call(lambda: B.plain(jobs), reps=20, warmup=3)
+        batched = {"fields": len(jobs), "node_levels": nl, "graph_replay_ms": round(ms_default, 4),
+                   "config": "library default (plain_waves 4)",
                    "plain_launches_ms": round(ms_plain, 4),
-                   "graph_node_levels_per_s": nl / (ms_graph * 1e-3),
-                   "plain_node_levels_per_s": nl / (ms_plain * 1e-3), "tune": bt_cfg,
-                   "graph_replay_ms_large_fields_plain": round(ms_hybrid, 4),
+                   "graph_node_levels_per_s": nl / (ms_default * 1e-3),
+                   "plain_node_levels_per_s": nl / (ms_plain * 1e-3),
+                   "tuned_graph_replay_ms": round(ms_tuned, 4), "tune": bt_cfg,
+                   "all_persistent_graph_replay_ms": round(ms_persistent, 4),
                    "grids": sorted({j["N"] for j in jobs}), "levels": sorted({j["nlev"] for j in jobs})}
         del jobs, fvms
         torch.cuda.empty_cache()

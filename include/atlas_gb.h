@@ -314,8 +314,10 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* a tile reads (its own and their neighbours, a few runs of consecutive  */
 /* ids) into shared memory with TMA bulk copies, up to four tiles ahead,  */
 /* and each consumer warp computes one group, its four nodes walking their */
-/* own stencil rows from shared memory.  The operators use them by default */
-/* wherever they apply: field pointers 16-byte aligned, ld * element size  */
+/* own stencil rows from shared memory.  By default every FP32 operator   */
+/* and the BF16 Laplacian use them (the BF16 one-ring operators measured   */
+/* faster per node) wherever they apply: field pointers 16-byte aligned,   */
+/* ld * element size                                                       */
 /* a multiple of 16, two stages of the tile's rows fitting in shared       */
 /* memory (at O1280 x 137 FP32 with ld 140: every operator), and a launch  */
 /* made of whole tiles (whole grids, partitions of whole rows); the        */
@@ -511,9 +513,10 @@ typedef struct {
 /* block (64..256, default 256), blocks per SM of the persistent grid      */
 /* (0 = as many as fit), and plain_waves: fields of at least plain_waves  */
 /* full GPU waves (plain_waves x 2048 x SMs items) run as plain launches  */
-/* with their operator's launch shape inside atlas_batch_launch, the      */
-/* others in the persistent launch (0, the default: every field in the   */
-/* persistent launch).  Zero fields take the defaults.                     */
+/* with their operator's own kernel and launch shape inside               */
+/* atlas_batch_launch, the others in the persistent launch (0: the        */
+/* default, 4 waves; -1: every field in the persistent launch).  Zero     */
+/* fields take the defaults.                                               */
 typedef struct {
   int vec;
   int tile_items;

@@ -1,7 +1,7 @@
 """Batched application of the operators to many fields in one persistent
-launch (``atlas_batch_*``; with ``plain_waves`` in the tune, the fields of
-that many full GPU waves or more get plain launches of their own in the same
-call), optionally captured once in a CUDA graph and replayed.
+launch (``atlas_batch_*``; the fields of ``plain_waves`` full GPU waves or
+more -- four by default, none with -1 -- get plain launches of their own in
+the same call), optionally captured once in a CUDA graph and replayed.
 
 A ``Batch`` holds its descriptor table (passed whole to each launch as a
 kernel parameter); the field pointers are fixed when it is created, which is

@@ -190,6 +190,10 @@ LaunchCfg default_launch(int op, int dt) {
   } else if (dt == ATLAS_BF16) {
     c.threads = 128;
     if (op == atlasgb::OP_LAP) c.tile_passes = 64;
+    // bfloat16 one-ring operators: the per-node kernels measured faster than
+    // the node-group kernels (O1280 x 137: 2.0 against 2.7 ms for the
+    // gradient); the Laplacian keeps the node-group kernel (4.1 against 4.3)
+    if (op != atlasgb::OP_LAP) c.group = 0;
   } else {  // F64: bound by the FP64 pipe
     c.threads = 128;
   }
@@ -1933,7 +1937,12 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
   if (want_vec != 1 && want_vec != 2 && want_vec != 4) return fail(ATLAS_EINVAL, "batch vec must be 1, 2 or 4");
   const int tile_items = t.tile_items > 0 ? t.tile_items : 1024;
   const int threads = t.threads > 0 ? t.threads : 256;
-  if (t.plain_waves < 0) return fail(ATLAS_EINVAL, "plain_waves must be >= 0");
+  if (t.plain_waves < -1) return fail(ATLAS_EINVAL, "plain_waves must be >= -1");
+  // default: fields of four full waves and more run as plain launches (their
+  // operators' own kernels, the node-group ones for FP32), the smaller ones
+  // share the persistent launch, where they cost no launch and no tail of
+  // their own; -1 puts every field in the persistent launch
+  const int plain_waves = t.plain_waves == 0 ? 4 : t.plain_waves;
   if (threads < 64 || threads > 1024 || threads % 32) return fail(ATLAS_EINVAL, "bad thread count %d", threads);
   std::vector<atlasgb::BatchDescDev> hd;
   hd.reserve(static_cast<size_t>(n));
@@ -1989,7 +1998,7 @@ int atlas_batch_create(const atlas_batch_desc* descs, int n, atlas_dtype dtype, 
     // the plain kernel, which keeps its pointers in the parameter bank (the
     // persistent kernel holds them in registers, 48 against 40)
     const int64_t own_items = static_cast<int64_t>(s.nnodes) * ((d.nlev + vec - 1) / vec);
-    if (t.plain_waves > 0 && own_items >= static_cast<int64_t>(f->num_sms) * 2048 * t.plain_waves) {
+    if (plain_waves > 0 && own_items >= static_cast<int64_t>(f->num_sms) * 2048 * plain_waves) {
       plain.push_back(atlas_batch_s::Plain{f, grad ? atlasgb::OP_GRAD : atlasgb::OP_DIV, d.in0,
                                            grad ? nullptr : d.in1, d.out0, grad ? d.out1 : nullptr, d.nlev, d.ld});
       continue;

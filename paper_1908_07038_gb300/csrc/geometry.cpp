@@ -453,13 +453,81 @@ double div_vdiag(const Mesh& m, const Dual& d, int64_t i) {
 
 }  // namespace
 
+namespace {
+bool build_stencil_by_id(const Mesh& m, const Dual& d, int op, Stencil& s);
+}  // namespace
+
+// Entry order within each node's row: first the neighbours on the node's own
+// grid row at offsets -2, -1, +1, +2 along the row (a ring on global grids;
+// those present, in that order), then the others by ascending id.  Every
+// kernel accumulates a node's terms in this order, so all of them give the
+// same bits; the node-group kernels take a group's in-group row neighbours
+// from registers because their positions are known.
+namespace {
+void row_neighbours_first(const Grid& g, Stencil& s) {
+  const bool ring = !g.regional();
+#pragma omp parallel
+  {
+    std::vector<std::pair<int, int32_t>> row_e;  // (offset, entry)
+    std::vector<int32_t> rest, nbr;
+    std::vector<double> w;
+#pragma omp for schedule(static)
+    for (int r = 0; r < g.nlat; ++r) {
+      const int64_t a = g.off[r], n = g.off[r + 1] - g.off[r];
+      for (int64_t i = a; i < a + n; ++i) {
+        const int32_t q0 = s.ptr[i], q1 = s.ptr[i + 1];
+        row_e.clear();
+        rest.clear();
+        for (int32_t q = q0; q < q1; ++q) {
+          const int64_t j = s.nbr[q];
+          int64_t off = j - i;
+          if (j >= a && j < a + n && ring) {
+            off = ((j - i) % n + n) % n;  // ring offset in (-n/2, n/2]
+            if (2 * off > n) off -= n;
+          }
+          if (j >= a && j < a + n && off != 0 && off >= -2 && off <= 2)
+            row_e.emplace_back(static_cast<int>(off), q);
+          else
+            rest.push_back(q);
+        }
+        if (row_e.empty()) continue;
+        std::stable_sort(row_e.begin(), row_e.end(),
+                         [](const std::pair<int, int32_t>& x, const std::pair<int, int32_t>& y) { return x.first < y.first; });
+        nbr.clear();
+        w.clear();
+        auto take = [&](int32_t q) {
+          nbr.push_back(s.nbr[q]);
+          w.push_back(s.w[2 * static_cast<int64_t>(q)]);
+          w.push_back(s.w[2 * static_cast<int64_t>(q) + 1]);
+        };
+        for (const auto& x : row_e) take(x.second);
+        for (int32_t q : rest) take(q);
+        for (int32_t k = 0; k < q1 - q0; ++k) {
+          s.nbr[q0 + k] = nbr[k];
+          s.w[2 * static_cast<int64_t>(q0 + k)] = w[2 * k];
+          s.w[2 * static_cast<int64_t>(q0 + k) + 1] = w[2 * k + 1];
+        }
+      }
+    }
+  }
+}
+}  // namespace
+
 bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
+  if (!build_stencil_by_id(m, d, op, s)) return false;
+  row_neighbours_first(*m.grid, s);
+  return true;
+}
+
+namespace {
+// Rows in ascending neighbour id.
+bool build_stencil_by_id(const Mesh& m, const Dual& d, int op, Stencil& s) {
   if (m.grid->regional()) return build_regional_stencil(m, d, op, s);
   if (op == OP_CURL_ADJ) {
     // the exact transpose of the curl's table (its faces are the regular
     // edges, a symmetric pattern)
     Stencil c;
-    if (!build_stencil(m, d, OP_CURL, c)) return false;
+    if (!build_stencil_by_id(m, d, OP_CURL, c)) return false;
     return transpose_stencil(c, s);
   }
   const int64_t V = m.grid->nnodes;
@@ -637,12 +705,11 @@ bool build_stencil(const Mesh& m, const Dual& d, int op, Stencil& s) {
   return true;
 }
 
+}  // namespace
+
 bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs) {
   const int64_t V = static_cast<int64_t>(s.ptr.size()) - 1;
   if (V != g.nnodes || static_cast<int64_t>(g.off.size()) != g.nlat + 1 || V >= (int64_t(1) << 28)) return false;
-  for (int64_t i = 0; i < V; ++i)
-    for (int32_t q = s.ptr[i] + 1; q < s.ptr[i + 1]; ++q)
-      if (s.nbr[q] <= s.nbr[q - 1]) return false;
   const int nw = s.scalar_w ? 1 : 2;
   gs.nw = nw;
   // groups: every row cut into runs of kGroup nodes (the last one shorter)
@@ -699,10 +766,8 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs) {
       }
       for (int t = 0; t < count; ++t) {
         const int64_t i = f + t;
-        // both lists are ascending: walk them together
-        size_t k = 0;
         for (int32_t q = s.ptr[i]; q < s.ptr[i + 1]; ++q) {
-          while (cols[k] != s.nbr[q]) ++k;
+          const size_t k = static_cast<size_t>(std::lower_bound(cols.begin(), cols.end(), s.nbr[q]) - cols.begin());
           const size_t e = static_cast<size_t>(q0) + k;
           gs.hdr[e] |= 1u << (28 + t);
           for (int c = 0; c < nw; ++c) gs.w[(e * kGroup + t) * nw + c] = s.w[2 * static_cast<int64_t>(q) + c];
@@ -801,11 +866,27 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
         const int64_t i = gs.first[gi] + u;
         D = std::max(D, static_cast<int>(s.ptr[i + 1] - s.ptr[i]));
       }
+      // a regular group: four nodes whose first R entries are their
+      // neighbours at row offsets -1, +1 (one-ring tables, R = 2) or -2, -1,
+      // +1, +2 (the Laplacian, R = 4), wherever that neighbour is a node
+      // of the group; the kernels then read those values from registers
+      const int R = s.scalar_w ? 4 : 2;
+      static const int kOffLap[4] = {-2, -1, 1, 2}, kOffRing[2] = {-1, 1};
+      const int* dr = s.scalar_w ? kOffLap : kOffRing;
+      bool reg = cnt == kGroup && D >= R;
+      for (int u = 0; u < cnt && reg; ++u) {
+        const int64_t i = gs.first[gi] + u;
+        const int32_t deg = s.ptr[i + 1] - s.ptr[i];
+        for (int r = 0; r < R && reg; ++r) {
+          const int t = u + dr[r];
+          if (t >= 0 && t < kGroup) reg = deg > r && s.nbr[s.ptr[i] + r] == gs.first[gi] + t;
+        }
+      }
       const size_t off = b.size();
       b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
       b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
       b[4 + 4 * k + 2] = static_cast<uint32_t>(D);
-      b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt);
+      b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt) | (reg ? 1u << 16 : 0u);
       b.resize(off + static_cast<size_t>(D) * 4 * (1 + 2 * nw), 0u);
       const size_t o_w = off + static_cast<size_t>(D) * 4;
       for (int u = 0; u < 4; ++u) {

@@ -63,7 +63,10 @@ struct Dual {
 //                                    + sum_m B_{c,m}(i) x_m(i)
 // with one (NIN = 1) or two (NIN = 2) inputs and one or two outputs.  The
 // weight pair w[2q], w[2q+1] is (W_{0,0}, W_{1,0}) when NIN = 1 and
-// (W_{0,0}, W_{0,1}) when NIN = 2; b[2i], b[2i+1] likewise.
+// (W_{0,0}, W_{0,1}) when NIN = 2; b[2i], b[2i+1] likewise.  Entry order in
+// a row (build_stencil): the neighbours on the node's own grid row at
+// offsets -2, -1, +1, +2 along the row (those present), then the others by
+// ascending id; every kernel sums a node's terms in this order.
 struct Stencil {
   int nin = 1, nout = 1;
   bool has_b = false;
@@ -146,7 +149,11 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
 //     (first node, count, first slot, 0).
 //   blob: per tile, 16-byte aligned: {groups, 0, first node, 0}; per group
 //     {slot of its first node, word offset of its data in the blob, D,
-//     count}; the B term [groups * 4][2] (floats; operators with one); then
+//     count | regular << 16} (regular: four nodes whose first R entries, R
+//     = 2 for one-ring tables and 4 for the Laplacian, are their row
+//     neighbours at offsets -1, +1, resp. -2, -1, +1, +2 wherever that
+//     neighbour belongs to the group, and D >= R); the B term
+//     [groups * 4][2] (floats; operators with one); then
 //     per group, D being its nodes' longest stencil row: slots [D][4]
 //     (entry e of node t: its row's e-th neighbour, or its own slot past its
 //     row's end) and weights [D][4][nw] as f32x2 pairs (each weight twice;

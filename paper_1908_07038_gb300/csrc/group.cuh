@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
         const bool hv = nranges >= 0 && nranges <= kTileRanges && slots >= 0 &&
                         static_cast<int64_t>(slots) * row_bytes <= a.rows_bytes && bbytes >= 16 && bbytes % 16 == 0 &&
                         static_cast<uint32_t>(NIN) * a.rows_bytes + static_cast<uint32_t>(bbytes) <= a.stage_bytes &&
-                        boff >= 0 && boff % 4 == 0 && static_cast<int64_t>(boff) + bbytes / 4 <= a.bd.nnz;
+                        boff >= 0 && 4ll * boff + bbytes / 4 <= a.bd.nnz;  // boff: 16-byte units
         const bool rv = lane >= nranges || (cur.r.y >= 0 && cur.r.x >= a.bd.lo &&
                                             static_cast<int64_t>(cur.r.x) + cur.r.y <= a.bd.hi && cur.r.z >= 0 &&
                                             cur.r.z + cur.r.y <= slots);
@@ -489,9 +489,10 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
     for (int g = warp; g < ngt; g += nc) {
       const int4 gh = lds_i4(blob + 16u + 16u * static_cast<uint32_t>(g));
       const uint32_t slot0 = static_cast<uint32_t>(gh.x);
-      const int count = gh.w;
+      const int count = gh.w & 0xffff;
+      const bool regular = ((gh.w >> 16) & 1) != 0;  // the same for the whole warp
       const int32_t node0 = tfirst + 4 * g;
-      if (!in_bounds(count >= 0 && count <= 4 && gh.x >= 0 && slot0 + static_cast<uint32_t>(count) <= slot_cap &&
+      if (!in_bounds(count <= 4 && (!regular || count == 4) && gh.x >= 0 && slot0 + static_cast<uint32_t>(count) <= slot_cap &&
                          gh.y >= 0 && gh.z >= 0 &&
                          4ll * gh.y + (16ll + 32ll * NW) * gh.z <= static_cast<long long>(blob_cap) &&
                          node0 >= a.bd.olo && static_cast<int64_t>(node0) + count <= a.bd.ohi,
@@ -548,6 +549,37 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
           }
         };
         int e = 0;
+        if (regular) {
+          // the first R entries of every node are its row neighbours at
+          // offsets kOff: those inside the group are already in registers
+          // (its own values xo), the others are read from shared memory
+          constexpr int R = (NIN == 1 && NOUT == 1) ? 4 : 2;
+          constexpr int kOff[4] = {R == 4 ? -2 : -1, R == 4 ? -1 : 1, 1, 2};
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            Lv<VA, VB> x[4][NIN];
+            Wts<4 * NW> W;
+            const uint4 sl = lds_u4(o_s + 16u * static_cast<uint32_t>(r));
+            load_wts<4 * NW>(o_ws + 32u * NW * static_cast<uint32_t>(r), W);
+            uint32_t sls[4] = {sl.x, sl.y, sl.z, sl.w};
+            if constexpr (kBoundsCheck) {
+#pragma unroll
+              for (int gg = 0; gg < 4; ++gg)
+                if (!in_bounds(sls[gg] < slot_cap, a.bd.err, BC_TILE_TABLE, t)) sls[gg] = slot0;
+            }
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg) {
+              const int src = gg + kOff[r];
+#pragma unroll
+              for (int m = 0; m < NIN; ++m) {
+                if (src >= 0 && src < 4) x[gg][m] = xo[m][src];
+                else lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
+              }
+            }
+            use(x, W);
+          }
+          e = R;
+        }
         for (; e + BATCH <= D; e += BATCH) {
           Lv<VA, VB> x[BATCH][4][NIN];
           Wts<4 * NW> W[BATCH];

@@ -173,8 +173,8 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
 def tune_batch(make, candidates=None, reps=5, verbose=False):
     """make(tune_dict) -> Batch; returns (best Batch, best tune, sweep)."""
     if candidates is None:
-        candidates = [dict(vec=v, tile_items=t, threads=th, blocks_per_sm=0)
-                      for v in (4, 2) for t in (256, 1024, 4096) for th in (128, 256)]
+        candidates = [dict(vec=4, tile_items=t, threads=th, blocks_per_sm=0, plain_waves=pw)
+                      for t in (1024, 4096) for th in (128, 256) for pw in (-1, 1, 2, 4, 8)]
     sweep = []
     best = None
     for c in candidates:

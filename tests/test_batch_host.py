@@ -60,7 +60,7 @@ def test_batch_argument_checks(fvms, product):
     with pytest.raises(ValueError):
         batch.Batch(mixed)
     for tune, code in ((dict(vec=3), EINVAL), (dict(threads=48), EINVAL),
-                       (dict(threads=100), EINVAL), (dict(plain_waves=-1), EINVAL)):
+                       (dict(threads=100), EINVAL), (dict(plain_waves=-2), EINVAL)):
         with pytest.raises(capi.AtlasError) as ei:
             batch.Batch(jobs, tune=tune)
         assert ei.value.code == code, tune

@@ -88,17 +88,18 @@ def batch_jobs(torch, pfvm):
     return batch.make_jobs(fvms, 24, seed=3)
 
 
-@pytest.mark.parametrize("plain_waves", [0, 8, 1])
+@pytest.mark.parametrize("plain_waves", [-1, 0, 8, 1])
 def test_batched_launch_equals_plain_launches(torch, batch_jobs, plain_waves):
     """24 fields (grids O80..O640, levels {1,60,91,137}) in one persistent
-    launch give bitwise the results of 24 separate launches; the CUDA-graph
-    replay does too.  With plain_waves, the fields of that many full waves
-    run as plain launches inside the batched call (8: O160 x 137 and up; 1:
-    nearly all), with the same results."""
+    launch (plain_waves -1) give bitwise the results of 24 separate launches;
+    the CUDA-graph replay does too.  With plain_waves, the fields of that
+    many full waves run as plain launches inside the batched call (0: the
+    default, 4 waves; 8: O160 x 137 and up; 1: nearly all), with the same
+    results."""
     from paper_1908_07038_gb300 import batch
     jobs = batch_jobs
     b = batch.Batch(jobs, tune=dict(plain_waves=plain_waves))
-    if plain_waves == 0:
+    if plain_waves in (-1, 0):
         assert b.tiles > 0
     b.launch()
     torch.cuda.synchronize()

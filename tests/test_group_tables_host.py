@@ -1,12 +1,14 @@
 """Host checks of the node-group tables (no GPU).
 
-The node-group kernels compute each node's sum from its group's merged
-table.  They give the per-node kernels' results bit for bit only if every
-node meets exactly its own stencil row, entry for entry and in the same
-order, with the same weights.  These tests check that on every grid family
-and operator, against the per-node table of the same fvm, plus the group
-layout the kernels rely on (whole-row groups of at most four nodes, sorted
-entries, the run of the group's own nodes).
+The group table is the union of the stencil rows of each group of up to
+four consecutive nodes (what a tile stages).  Every node must find there
+exactly its own stencil row, with the same weights.  These tests check that
+on every grid family and operator, against the per-node table of the same
+fvm, plus the group layout the kernels rely on (whole-row groups of at most
+four nodes, sorted entries, the run of the group's own nodes), and the
+entry order of the stencil rows that every kernel sums in: the neighbours on
+the node's own grid row at offsets -2, -1, +1, +2 (those present) first,
+then the others by ascending id.
 """
 import numpy as np
 import pytest
@@ -67,9 +69,52 @@ def test_group_table_reproduces_every_node_row(fvms, name, op):
         for t in range(cnt):
             i = f0 + t
             sel = (ms >> t) & 1 == 1
-            assert np.array_equal(js[sel], nbr[ptr[i]:ptr[i + 1]]), (name, op, i)
-            assert np.array_equal(w[q0:q1][sel, t, :nw], sw[ptr[i]:ptr[i + 1], :nw]), (name, op, i)
+            order = np.argsort(nbr[ptr[i]:ptr[i + 1]], kind="stable")
+            assert np.array_equal(js[sel], nbr[ptr[i]:ptr[i + 1]][order]), (name, op, i)
+            assert np.array_equal(w[q0:q1][sel, t, :nw], sw[ptr[i]:ptr[i + 1], :nw][order]), (name, op, i)
             assert np.all(w[q0:q1][~sel, t] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["O2", "O9", "F6", "lambert13x9", "lambert7x5"])
+@pytest.mark.parametrize("op", OPS)
+def test_stencil_rows_put_row_neighbours_first(fvms, name, op):
+    """Each row starts with the node's neighbours on its own grid row at
+    offsets -2, -1, +1, +2 along the row (a ring on global grids), in that
+    order, then lists the others by ascending id; on global grids every node
+    of a row of more than four points has its -1 and +1 neighbours there
+    (and the Laplacian its -2 and +2 ones too)."""
+    fvm = fvms[name]
+    st = fvm.stencil_table(op)
+    ptr, nbr = st["ptr"], st["nbr"]
+    off = _rows(fvm)
+    ring = fvm.grid.projection is None
+    for r in range(len(off) - 1):
+        a, n = int(off[r]), int(off[r + 1] - off[r])
+        for i in range(a, a + n):
+            row = [int(j) for j in nbr[ptr[i]:ptr[i + 1]]]
+            offs = []
+            for j in row:
+                if a <= j < a + n:
+                    d = j - i
+                    if ring:
+                        d = (j - i) % n
+                        if 2 * d > n:
+                            d -= n
+                    offs.append(d if d != 0 and abs(d) <= 2 else None)
+                else:
+                    offs.append(None)
+            k = 0
+            while k < len(row) and offs[k] is not None:
+                k += 1
+            head, rest = offs[:k], row[k:]
+            assert head == sorted(head), (name, op, i, row)
+            assert all(o is None for o in offs[k:]), (name, op, i, row)
+            assert rest == sorted(rest), (name, op, i, row)
+            if ring and n > 4:
+                want = {-2, -1, 1, 2} if op == "laplacian" else {-1, 1}
+                if op in ("gradient", "laplacian", "gradient_adjoint", "divergence_adjoint", "vector_gradient",
+                          "divergence", "curl"):
+                    assert want <= set(head), (name, op, i, row)
 
 
 def test_group_tables_of_the_benchmark_grid_are_compact(product):
