@@ -324,8 +324,9 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* per-node kernels run elsewhere, with bitwise identical results.        */
 /* enable: 1 use them, 0 per-node kernels only, -1 keep.  blocks_per_sm: 1 */
 /* or 2 blocks of 32 (groups_per_tile + 1) threads per SM at most (fewer   */
-/* when shared memory is short; 0 keeps; default 1: one block holding up  */
-/* to four stages measured faster than two blocks of two).                 */
+/* when shared memory or registers are short; 0 keeps; default 1: one     */
+/* block holding up to four stages measured faster than two blocks of two, */
+/* except for the BF16 Laplacian, default 2).                              */
 /* groups_per_tile: 1..7 (0 keeps; default 7; smaller tiles take less     */
 /* shared memory, so more stages fit; a change rebuilds the operator's     */
 /* tile tables at its next call).  dtype -1 sets all three dtypes.  Host  */

@@ -192,8 +192,10 @@ LaunchCfg default_launch(int op, int dt) {
     if (op == atlasgb::OP_LAP) c.tile_passes = 64;
     // bfloat16 one-ring operators: the per-node kernels measured faster than
     // the node-group kernels (O1280 x 137: 2.0 against 2.7 ms for the
-    // gradient); the Laplacian keeps the node-group kernel (4.1 against 4.3)
+    // gradient); the Laplacian keeps the node-group kernel, two blocks per
+    // SM (its stages are half the FP32 size): 3.2 against 4.4 ms per node
     if (op != atlasgb::OP_LAP) c.group = 0;
+    else c.tile_bps = 2;
   } else {  // F64: bound by the FP64 pipe
     c.threads = 128;
   }

@@ -635,7 +635,8 @@ inline cudaError_t with_shape(const DevTiles& d, F&& f) {
 
 template <typename S, int NIN, int NOUT, bool HAS_B, int NW>
 inline const void* kernel_of(int va, int vb) {
-  constexpr int BATCH = 2;  // steps (four nodes' entries each) whose rows are requested together
+  // steps (four nodes' entries each) whose rows are requested together
+  constexpr int BATCH = (NIN == 1 && NW == 1) ? 4 : 2;
 #define ATLASGB_TILE(A, B) \
   if (va == A && vb == B) return reinterpret_cast<const void*>(&tile_kernel<S, NIN, NOUT, HAS_B, NW, A, B, BATCH>);
   ATLASGB_TILE(4, 2)

@@ -30,7 +30,7 @@ CANDIDATES = {
     ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8, 64)),
 }
 # node-group (tile) kernel candidates: (groups per tile, blocks per SM)
-TILE_CANDIDATES = ((7, 1), (5, 1), (4, 1), (3, 2))
+TILE_CANDIDATES = ((7, 1), (7, 2), (5, 1), (3, 2))
 _TORCH_DT = None
 
 
