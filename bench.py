@@ -347,7 +347,10 @@ def _precision(torch, fvm, lon, lat, nlev, seed):
 def _shape(t):
     """The launch shape the tuner picked, as a short string."""
     if t.get("kernel") == "tile":
-        return "tile kernel, %d groups per tile, %d block(s) per SM" % (t["groups"], t["tile_bps"])
+        if "tile_blocks" in t:
+            return "tile kernel, %d groups per tile, %d block(s) of %d stages per SM" % (
+                t["groups"], t["tile_blocks"], t["tile_stages"])
+        return "tile kernel, %d groups per tile, %d block(s) per SM asked" % (t["groups"], t["tile_bps"])
     return "per-node kernel, vec %d, batch %d, %d threads, tile %d" % (t["vec"], t["batch"], t["threads"],
                                                                        t.get("tile", 1))
 

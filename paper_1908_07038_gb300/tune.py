@@ -160,8 +160,11 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
             fvm.set_group(op, 1, tbps, groups, dtype=dtype)
         else:
             fvm.set_group(op, 0, dtype=dtype)
+        # the launch shape the node-group kernel takes (blocks per SM may be
+        # fewer than asked when shared memory or registers are short)
+        shape = fvm.tile_info(op, nlev, ld, dtype) if kernel == "tile" else dict(blocks_per_sm=0, stages=0)
         best[op] = dict(kernel=kernel, vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, groups=groups,
-                        tile_bps=tbps, ms=ms,
+                        tile_bps=tbps, tile_blocks=shape["blocks_per_sm"], tile_stages=shape["stages"], ms=ms,
                         sweep=[dict(ms=r[0], kernel=r[1], vec=r[2], batch=r[3], threads=r[4], bps=r[5], tile=r[6],
                                     groups=r[7], tile_bps=r[8]) for r in results])
         cache[key] = {k: best[op][k] for k in ("kernel", "vec", "batch", "threads", "bps", "tile", "groups",
