@@ -95,12 +95,21 @@ def _traffic(op):
 
 # kernels of the FP32 operators on 137 levels: the shared-memory node-group
 # kernel <storage, inputs, outputs, B term, weights per entry, part A and
-# part B levels per lane, steps per batch>, or the per-node kernel
-TILE_KERNEL_NAME = {"gradient": "tile_kernel<float,1,2,0,2,4,1,2>",
-                    "divergence": "tile_kernel<float,2,1,1,2,4,1,2>",
-                    "laplacian": "tile_kernel<float,1,1,0,1,4,1,4>",
-                    "gradient_adjoint": "tile_kernel<float,2,1,1,2,4,1,2>",
-                    "divergence_adjoint": "tile_kernel<float,1,2,1,2,4,1,2>"}
+# part B levels per lane, steps per batch, nodes per consumer warp>, or the
+# per-node kernel
+TILE_KERNEL_BASE = {"gradient": "tile_kernel<float,1,2,0,2,4,1,2",
+                    "divergence": "tile_kernel<float,2,1,1,2,4,1,2",
+                    "laplacian": "tile_kernel<float,1,1,0,1,4,1,4",
+                    "gradient_adjoint": "tile_kernel<float,2,1,1,2,4,1,2",
+                    "divergence_adjoint": "tile_kernel<float,1,2,1,2,4,1,2"}
+TILE_DEFAULT_NPW = {"laplacian": 2}
+
+
+def _tile_kernel_name(op, npw=None):
+    npw = TILE_DEFAULT_NPW.get(op, 4) if npw is None else npw
+    return "%s,%d>" % (TILE_KERNEL_BASE[op], npw)
+
+
 NODE_KERNEL_NAME = {"gradient": "stencil_kernel<float,float,1,2,4,0,0,B,1>",
                     "divergence": "stencil_kernel<float,float,2,1,4,1,0,B,1>",
                     "laplacian": "stencil_kernel<float,float,1,1,4,0,1,B,1>",
@@ -348,8 +357,8 @@ def _shape(t):
     """The launch shape the tuner picked, as a short string."""
     if t.get("kernel") == "tile":
         if "tile_blocks" in t:
-            return "tile kernel, %d groups per tile, %d block(s) of %d stages per SM" % (
-                t["groups"], t["tile_blocks"], t["tile_stages"])
+            return "tile kernel, %d groups per tile, %d node(s) per warp, %d block(s) of %d stages per SM" % (
+                t["groups"], t.get("npw", 4), t["tile_blocks"], t["tile_stages"])
         return "tile kernel, %d groups per tile, %d block(s) per SM asked" % (t["groups"], t["tile_bps"])
     return "per-node kernel, vec %d, batch %d, %d threads, tile %d" % (t["vec"], t["batch"], t["threads"],
                                                                        t.get("tile", 1))
@@ -429,8 +438,9 @@ def run_native(args):
                    "alg_bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / hbm}
     dom = max(OPS, key=lambda o: per[o]["ms"])
     traffic = _traffic(dom) if args.grid == N_GRID else None
-    dom_tile = tuned.get(dom, {}).get("kernel", "tile") == "tile"
-    roofline = {"bound": "hbm", "kernel": (TILE_KERNEL_NAME if dom_tile else NODE_KERNEL_NAME)[dom], "operator": dom,
+    dom_t = tuned.get(dom, {})
+    dom_name = _tile_kernel_name(dom, dom_t.get("npw")) if dom_t.get("kernel", "tile") == "tile" else NODE_KERNEL_NAME[dom]
+    roofline = {"bound": "hbm", "kernel": dom_name, "operator": dom,
                 "achieved": round(per[dom]["gbs"], 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(per[dom]["frac"], 4),
                 "traffic": traffic, "traffic_gbs": round(traffic / (per[dom]["ms"] * 1e-3) / 1e9, 1) if traffic else None,

@@ -331,7 +331,11 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* shared memory, so more stages fit; a change rebuilds the operator's     */
 /* tile tables at its next call).  dtype -1 sets all three dtypes.  Host  */
 /* only; takes effect at the next operator call.                           */
-int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile);
+/* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
+/* group, each walking two of its nodes: twice the warps per block); 0    */
+/* keeps; default 4.                                                       */
+int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile,
+                        int nodes_per_warp);
 /* Launch shape the node-group kernel of one operator takes on fields of   */
 /* nlev levels and leading dimension ld (16-byte aligned pointers          */
 /* assumed): blocks per SM, pipeline stages per block, dynamic shared      */

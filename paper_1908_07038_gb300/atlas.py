@@ -264,14 +264,15 @@ class Fvm:
         capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
                                   int(blocks_per_sm), int(tile_passes))
 
-    def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1):
+    def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1, nodes_per_warp=0):
         """Use the shared-memory node-group kernels for one operator (enable
         1) or the per-node kernels only (0; -1 keeps), with at most
-        blocks_per_sm blocks per SM (1 or 2; 0 keeps) and groups_per_tile
-        groups of four nodes per tile (1..7; 0 keeps), for one storage dtype
-        or, with dtype=-1, all of them."""
+        blocks_per_sm blocks per SM (1 or 2; 0 keeps), groups_per_tile
+        groups of four nodes per tile (1..7; 0 keeps) and nodes_per_warp
+        nodes per consumer warp (4 or 2; 0 keeps), for one storage dtype or,
+        with dtype=-1, all of them."""
         capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(blocks_per_sm),
-                                 int(groups_per_tile))
+                                 int(groups_per_tile), int(nodes_per_warp))
 
     def group_table(self, op):
         """The FP64 node-group table of one operator (host only): head

@@ -11,11 +11,16 @@ namespace {
 
 constexpr size_t kSmemLimit = 232448;  // 227 KiB of dynamic shared memory per block
 
-const void* tile_fn(StorageType st, const DevTiles& d, int va, int vb) {
-  if (st == ST_F32) return tile_fn_f32(d, va, vb);
-  if (st == ST_BF16) return tile_fn_bf16(d, va, vb);
+const void* tile_fn(StorageType st, const DevTiles& d, const TileLaunch& l) {
+  if (l.npw != 4 && l.npw != 2) return nullptr;
+  if (st == ST_F32) return tile_fn_f32(d, l.va, l.vb, l.npw);
+  if (st == ST_BF16) return tile_fn_bf16(d, l.va, l.vb, l.npw);
   return nullptr;
 }
+
+// threads of a block: a consumer warp per part of every group of a tile
+// (4 / npw parts of npw nodes per group), then the producer warp
+int tile_threads(const DevTiles& d, const TileLaunch& l) { return 32 * ((4 / l.npw) * d.groups_per_tile + 1); }
 
 // The device error word of the tile kernels and its address per device
 // (looked up once, with the device current).
@@ -71,7 +76,7 @@ cudaError_t tile_shape(StorageType st, const DevTiles& d, const TileLaunch& l, i
   *bps_out = 0;
   *stages_out = 0;
   *smem_out = 0;
-  const void* fn = tile_fn(st, d, l.va, l.vb);
+  const void* fn = tile_fn(st, d, l);
   if (!fn) return cudaErrorInvalidValue;
   const int es = st == ST_BF16 ? 2 : 4;
   size_t rows, stage;
@@ -82,7 +87,7 @@ cudaError_t tile_shape(StorageType st, const DevTiles& d, const TileLaunch& l, i
   if (ns == 0 && bps == 2) ns = stages_for(stage, bps = 1);
   if (ns == 0) return cudaSuccess;
   const size_t smem = static_cast<size_t>(ns) * stage + 128;
-  const int threads = 32 * (d.groups_per_tile + 1);
+  const int threads = tile_threads(d, l);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   int fit = 0;
@@ -95,11 +100,11 @@ cudaError_t tile_shape(StorageType st, const DevTiles& d, const TileLaunch& l, i
 }
 
 cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream) {
-  const void* fn = tile_fn(st, d, l.va, l.vb);
+  const void* fn = tile_fn(st, d, l);
   if (!fn) return cudaErrorInvalidValue;
   if (l.ntiles <= 0 || l.nlev <= 0) return cudaSuccess;
-  const int threads = 32 * (d.groups_per_tile + 1);  // at most 256 (the kernels' launch bound)
-  if (threads > 256) return cudaErrorInvalidValue;
+  const int threads = tile_threads(d, l);  // within the kernels' launch bound (256, or 512 with npw 2)
+  if (threads > (l.npw == 4 ? 256 : 512)) return cudaErrorInvalidValue;
   int bps = 0, ns = 0;
   size_t smem = 0;
   cudaError_t e = tile_shape(st, d, l, &bps, &ns, &smem);

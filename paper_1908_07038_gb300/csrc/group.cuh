@@ -253,6 +253,11 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
   return v;
 }
+__device__ __forceinline__ uint2 lds_u2(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ int4 lds_i4(uint32_t a) {
   int4 v;
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
@@ -343,8 +348,8 @@ constexpr int kMaxStages = 4;
 // Block: NC consumer warps (warp 0 .. NC-1), then one producer warp.  Tiles
 // t0 + blockIdx.x, + gridDim.x, ...; the block's k-th tile goes to stage
 // k % nstages, the (k / nstages)-th use of that stage.
-template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int BATCH>
-__global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
+template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int BATCH, int NPW>
+__global__ void __launch_bounds__(NPW == 4 ? 256 : 512, 1) tile_kernel(const TileArgs a) {
   constexpr int LB = 32 * (VA + VB);  // levels per level block
   constexpr uint32_t ES = sizeof(S);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -486,7 +491,11 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
     const uint32_t o_b = blob + 16u + 16u * static_cast<uint32_t>(ngt);
     uint32_t rows[2] = {sbase, sbase + a.rows_bytes};
     const uint32_t rb = static_cast<uint32_t>(row_bytes);
-    for (int g = warp; g < ngt; g += nc) {
+    // work items: (group, part); a part is NPW consecutive nodes of the
+    // group (NPW = 4: one warp per group; NPW = 2: two warps per group)
+    constexpr int PARTS = 4 / NPW;
+    for (int item = warp; item < ngt * PARTS; item += nc) {
+      const int g = item / PARTS, n0 = (item % PARTS) * NPW;
       const int4 gh = lds_i4(blob + 16u + 16u * static_cast<uint32_t>(g));
       const uint32_t slot0 = static_cast<uint32_t>(gh.x);
       const int count = gh.w & 0xffff;
@@ -498,42 +507,63 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
                          node0 >= a.bd.olo && static_cast<int64_t>(node0) + count <= a.bd.ohi,
                      a.bd.err, BC_TILE_TABLE, t))
         continue;
+      const int cnt = count - n0;  // nodes of this part (warp-uniform)
+      if (cnt <= 0) continue;
       for (int lb = 0; lb < a.nlb; ++lb) {
         const Layout<VA, VB> L(lb * LB, lane);
-        Lv<VA, VB> xo[NIN][4], acc[NOUT][4];
+        Lv<VA, VB> xo[NIN][NPW], acc[NOUT][NPW];
 #pragma unroll
-        for (int gg = 0; gg < 4; ++gg) {
+        for (int gg = 0; gg < NPW; ++gg) {
 #pragma unroll
           for (int m = 0; m < NIN; ++m) {
-            if (gg < count)  // warp-uniform
-              lv_load<S, VA, VB>(rows[m] + (slot0 + gg) * rb, L, xo[m][gg]);
+            if (gg < cnt)  // warp-uniform
+              lv_load<S, VA, VB>(rows[m] + (slot0 + n0 + gg) * rb, L, xo[m][gg]);
             else lv_zero(xo[m][gg]);
           }
 #pragma unroll
           for (int c = 0; c < NOUT; ++c) lv_zero(acc[c][gg]);
         }
-        // every node of the group walks its own stencil row, the four in
-        // step (four independent sums); D entries each, BATCH at a time
+        // every node of the part walks its own stencil row, all in step
+        // (independent sums); D entries each, BATCH at a time.  Entry e of
+        // the group: slots [4] (16 bytes), weight pairs [4][NW]; this part
+        // reads its NPW of them.
         const uint32_t o_s = blob + 4u * static_cast<uint32_t>(gh.y);
         const int D = gh.z;
         const uint32_t o_ws = o_s + 16u * static_cast<uint32_t>(D);
-        auto step = [&](int e, Lv<VA, VB> (&x)[4][NIN], Wts<4 * NW>& W) {
-          const uint4 sl = lds_u4(o_s + 16u * static_cast<uint32_t>(e));
-          load_wts<4 * NW>(o_ws + 32u * NW * static_cast<uint32_t>(e), W);
-          uint32_t sls[4] = {sl.x, sl.y, sl.z, sl.w};
+        auto slots = [&](int e, uint32_t (&sls)[NPW]) {
+          const uint32_t at = o_s + 16u * static_cast<uint32_t>(e) + 4u * static_cast<uint32_t>(n0);
+          if constexpr (NPW == 4) {
+            const uint4 sl = lds_u4(at);
+            sls[0] = sl.x;
+            sls[1] = sl.y;
+            sls[2] = sl.z;
+            sls[3] = sl.w;
+          } else {
+            const uint2 sl = lds_u2(at);
+            sls[0] = sl.x;
+            sls[1] = sl.y;
+          }
           if constexpr (kBoundsCheck) {
 #pragma unroll
-            for (int gg = 0; gg < 4; ++gg)
+            for (int gg = 0; gg < NPW; ++gg)
               if (!in_bounds(sls[gg] < slot_cap, a.bd.err, BC_TILE_TABLE, t)) sls[gg] = slot0;
           }
+        };
+        auto weights = [&](int e, Wts<NPW * NW>& W) {
+          load_wts<NPW * NW>(o_ws + 32u * NW * static_cast<uint32_t>(e) + 8u * NW * static_cast<uint32_t>(n0), W);
+        };
+        auto step = [&](int e, Lv<VA, VB> (&x)[NPW][NIN], Wts<NPW * NW>& W) {
+          uint32_t sls[NPW];
+          slots(e, sls);
+          weights(e, W);
 #pragma unroll
-          for (int gg = 0; gg < 4; ++gg)
+          for (int gg = 0; gg < NPW; ++gg)
 #pragma unroll
             for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
         };
-        auto use = [&](const Lv<VA, VB> (&x)[4][NIN], const Wts<4 * NW>& W) {
+        auto use = [&](const Lv<VA, VB> (&x)[NPW][NIN], const Wts<NPW * NW>& W) {
 #pragma unroll
-          for (int gg = 0; gg < 4; ++gg) {
+          for (int gg = 0; gg < NPW; ++gg) {
             Lv<VA, VB> d;
             lv_sub(x[gg][0], xo[0][gg], d);
             if constexpr (NIN == 1 && NOUT == 1) {
@@ -551,28 +581,23 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
         int e = 0;
         if (regular) {
           // the first R entries of every node are its row neighbours at
-          // offsets kOff: those inside the group are already in registers
+          // offsets kOff: those inside this part are already in registers
           // (its own values xo), the others are read from shared memory
           constexpr int R = (NIN == 1 && NOUT == 1) ? 4 : 2;
           constexpr int kOff[4] = {R == 4 ? -2 : -1, R == 4 ? -1 : 1, 1, 2};
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            Lv<VA, VB> x[4][NIN];
-            Wts<4 * NW> W;
-            const uint4 sl = lds_u4(o_s + 16u * static_cast<uint32_t>(r));
-            load_wts<4 * NW>(o_ws + 32u * NW * static_cast<uint32_t>(r), W);
-            uint32_t sls[4] = {sl.x, sl.y, sl.z, sl.w};
-            if constexpr (kBoundsCheck) {
+            Lv<VA, VB> x[NPW][NIN];
+            Wts<NPW * NW> W;
+            uint32_t sls[NPW];
+            slots(r, sls);
+            weights(r, W);
 #pragma unroll
-              for (int gg = 0; gg < 4; ++gg)
-                if (!in_bounds(sls[gg] < slot_cap, a.bd.err, BC_TILE_TABLE, t)) sls[gg] = slot0;
-            }
-#pragma unroll
-            for (int gg = 0; gg < 4; ++gg) {
+            for (int gg = 0; gg < NPW; ++gg) {
               const int src = gg + kOff[r];
 #pragma unroll
               for (int m = 0; m < NIN; ++m) {
-                if (src >= 0 && src < 4) x[gg][m] = xo[m][src];
+                if (src >= 0 && src < NPW) x[gg][m] = xo[m][src];
                 else lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
               }
             }
@@ -581,24 +606,25 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
           e = R;
         }
         for (; e + BATCH <= D; e += BATCH) {
-          Lv<VA, VB> x[BATCH][4][NIN];
-          Wts<4 * NW> W[BATCH];
+          Lv<VA, VB> x[BATCH][NPW][NIN];
+          Wts<NPW * NW> W[BATCH];
 #pragma unroll
           for (int u = 0; u < BATCH; ++u) step(e + u, x[u], W[u]);
 #pragma unroll
           for (int u = 0; u < BATCH; ++u) use(x[u], W[u]);
         }
         for (; e < D; ++e) {
-          Lv<VA, VB> x[4][NIN];
-          Wts<4 * NW> W;
+          Lv<VA, VB> x[NPW][NIN];
+          Wts<NPW * NW> W;
           step(e, x, W);
           use(x, W);
         }
 #pragma unroll
-        for (int gg = 0; gg < 4; ++gg) {
-          if (gg < count) {
+        for (int gg = 0; gg < NPW; ++gg) {
+          if (gg < cnt) {
             if constexpr (HAS_B) {
-              const float2 b = lds_f2(o_b + 32u * static_cast<uint32_t>(g) + 8u * static_cast<uint32_t>(gg));
+              const float2 b =
+                  lds_f2(o_b + 32u * static_cast<uint32_t>(g) + 8u * static_cast<uint32_t>(n0 + gg));
               if constexpr (NIN == 2) {
                 lv_fma(pk(b.x, b.x), xo[0][gg], acc[0][gg]);
                 lv_fma(pk(b.y, b.y), xo[1][gg], acc[0][gg]);
@@ -607,7 +633,7 @@ __global__ void __launch_bounds__(256, 1) tile_kernel(const TileArgs a) {
                 lv_fma(pk(b.y, b.y), xo[0][gg], acc[1][gg]);
               }
             }
-            const int64_t o = static_cast<int64_t>(node0 + gg) * a.ld;
+            const int64_t o = static_cast<int64_t>(node0 + n0 + gg) * a.ld;
             lv_store<S, VA, VB>(static_cast<S*>(a.out0) + o, L, a.nlev, a.nstore, acc[0][gg]);
             if constexpr (NOUT == 2) lv_store<S, VA, VB>(static_cast<S*>(a.out1) + o, L, a.nlev, a.nstore, acc[1][gg]);
           }
@@ -633,12 +659,13 @@ inline cudaError_t with_shape(const DevTiles& d, F&& f) {
   return cudaErrorInvalidValue;
 }
 
-template <typename S, int NIN, int NOUT, bool HAS_B, int NW>
+template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int NPW>
 inline const void* kernel_of(int va, int vb) {
-  // steps (four nodes' entries each) whose rows are requested together
+  // steps (entries of the warp's nodes) whose rows are requested together
   constexpr int BATCH = (NIN == 1 && NW == 1) ? 4 : 2;
-#define ATLASGB_TILE(A, B) \
-  if (va == A && vb == B) return reinterpret_cast<const void*>(&tile_kernel<S, NIN, NOUT, HAS_B, NW, A, B, BATCH>);
+#define ATLASGB_TILE(A, B)                                                                                    \
+  if (va == A && vb == B)                                                                                     \
+    return reinterpret_cast<const void*>(&tile_kernel<S, NIN, NOUT, HAS_B, NW, A, B, BATCH, NPW>);
   ATLASGB_TILE(4, 2)
   ATLASGB_TILE(4, 1)
   ATLASGB_TILE(4, 0)
@@ -651,17 +678,18 @@ inline const void* kernel_of(int va, int vb) {
 
 template <typename S>
 struct Pick {
-  int va, vb;
+  int va, vb, npw;
   const void* fn = nullptr;
   template <int NIN, int NOUT, bool HAS_B, int NW>
   cudaError_t operator()() {
-    fn = kernel_of<S, NIN, NOUT, HAS_B, NW>(va, vb);
+    fn = npw == 2 ? kernel_of<S, NIN, NOUT, HAS_B, NW, 2>(va, vb) : kernel_of<S, NIN, NOUT, HAS_B, NW, 4>(va, vb);
     return fn ? cudaSuccess : cudaErrorInvalidValue;
   }
 };
 }  // namespace grp
 
-const void* tile_fn_f32(const DevTiles& d, int va, int vb);
-const void* tile_fn_bf16(const DevTiles& d, int va, int vb);
+// npw: nodes per consumer warp, 4 (one warp per group) or 2 (two warps per group)
+const void* tile_fn_f32(const DevTiles& d, int va, int vb, int npw);
+const void* tile_fn_bf16(const DevTiles& d, int va, int vb, int npw);
 
 }  // namespace atlasgb

@@ -96,6 +96,7 @@ struct TileLaunch {
   int32_t nstore = 0;  // stores cover levels < nstore (nlev rounded up to the row's vector width)
   int64_t ld = 0;      // ld * element size must be a multiple of 16, the field pointers 16-byte aligned
   int va = 4, vb = 1;  // levels per lane in part A and part B of a level block
+  int npw = 4;         // nodes per consumer warp: 4 (a warp per group) or 2 (two warps per group)
   int32_t t0 = 0, ntiles = 0;
   int sms = 1;         // grid: sms * (blocks that fit per SM, at most 2), at most ntiles
   int max_bps = 2;

@@ -29,8 +29,8 @@ CANDIDATES = {
     ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1,)),
     ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8, 64)),
 }
-# node-group (tile) kernel candidates: (groups per tile, blocks per SM)
-TILE_CANDIDATES = ((7, 1), (7, 2), (5, 1), (3, 2))
+# node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp)
+TILE_CANDIDATES = ((7, 1, 4), (7, 2, 4), (7, 1, 2), (5, 1, 4))
 _TORCH_DT = None
 
 
@@ -126,7 +126,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
             c = cache[key]
             fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1), dtype=dtype)
             if c.get("kernel", "node") == "tile":
-                fvm.set_group(op, 1, c["tile_bps"], c["groups"], dtype=dtype)
+                fvm.set_group(op, 1, c["tile_bps"], c["groups"], dtype=dtype, nodes_per_warp=c.get("npw", 4))
             else:
                 fvm.set_group(op, 0, dtype=dtype)
             best[op] = c
@@ -141,7 +141,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
                                                                 cand["bps"], cand["tile"]):
             fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
             ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
-            results.append((ms, "node", vec, batch, threads, bps, tile, 0, 0))
+            results.append((ms, "node", vec, batch, threads, bps, tile, 0, 0, 0))
             if verbose:
                 print("tune %-18s node vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
                       (op, vec, batch, threads, bps, tile, ms))
@@ -149,26 +149,26 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
         # the tile kernel's shapes (where it applies to these fields)
         if fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
-            for groups, tbps in TILE_CANDIDATES:
-                fvm.set_group(op, 1, tbps, groups, dtype=dtype)
+            for groups, tbps, npw in TILE_CANDIDATES:
+                fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw)
                 ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
-                results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps))
+                results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps, npw))
                 if verbose:
-                    print("tune %-18s tile groups=%d bps=%d: %.4f ms" % (op, groups, tbps, ms))
-        ms, kernel, vec, batch, threads, bps, tile, groups, tbps = min(results)
+                    print("tune %-18s tile groups=%d bps=%d npw=%d: %.4f ms" % (op, groups, tbps, npw, ms))
+        ms, kernel, vec, batch, threads, bps, tile, groups, tbps, npw = min(results)
         if kernel == "tile":
-            fvm.set_group(op, 1, tbps, groups, dtype=dtype)
+            fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw)
         else:
             fvm.set_group(op, 0, dtype=dtype)
         # the launch shape the node-group kernel takes (blocks per SM may be
         # fewer than asked when shared memory or registers are short)
         shape = fvm.tile_info(op, nlev, ld, dtype) if kernel == "tile" else dict(blocks_per_sm=0, stages=0)
         best[op] = dict(kernel=kernel, vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, groups=groups,
-                        tile_bps=tbps, tile_blocks=shape["blocks_per_sm"], tile_stages=shape["stages"], ms=ms,
+                        tile_bps=tbps, npw=npw, tile_blocks=shape["blocks_per_sm"], tile_stages=shape["stages"], ms=ms,
                         sweep=[dict(ms=r[0], kernel=r[1], vec=r[2], batch=r[3], threads=r[4], bps=r[5], tile=r[6],
-                                    groups=r[7], tile_bps=r[8]) for r in results])
+                                    groups=r[7], tile_bps=r[8], npw=r[9]) for r in results])
         cache[key] = {k: best[op][k] for k in ("kernel", "vec", "batch", "threads", "bps", "tile", "groups",
-                                              "tile_bps", "ms")}
+                                              "tile_bps", "npw", "ms")}
     _store_cache(cache)
     return best
 

@@ -3,7 +3,8 @@
 Run with ATLASGB_BOUNDSCHECK=1: the package then loads the bounds-checked
 build of the library, whose kernels check every index they take from a
 table.  On O2 and O4 every kind of launch runs once -- the per-node and the
-node-group (tile) stencil kernels for every operator, FP64 and FP32, the
+node-group (tile) stencil kernels (one or two consumer warps per group) for
+every operator, FP64 and FP32, the
 edge-based two-pass forms, a batched launch, band partitions and a remap --
 and is compared with the FP64 oracle.  Any bounds violation makes the call
 raise (ATLAS_EBOUNDS).  Prints one JSON line: the library's info string, the
@@ -72,8 +73,9 @@ def main():
             for op in OPS:
                 x, y = (ud, vd) if op in TWO_IN else (fd, None)
                 want = oracle_op(om, op, u if op in TWO_IN else f, v, nlev)
-                for group in ((0, 1) if name == "f32" else (0,)):  # the tile kernels take FP32/BF16 fields
-                    fvm.set_group(op, enable=group)
+                # per-node kernel; node-group kernels (FP32/BF16 fields) with one or two warps per group
+                for group, npw in (((0, 4), (1, 4), (1, 2)) if name == "f32" else ((0, 4),)):
+                    fvm.set_group(op, enable=group, nodes_per_warp=npw)
                     got = gpu_op(fvm, op, x, y, nlev)
                     torch.cuda.synchronize()
                     for a, b in zip(got, want):
@@ -81,7 +83,7 @@ def main():
                         assert e <= tol[name], (N, name, op, group, e)
                         worst[name] = max(worst[name], e)
                         cases += 1
-                fvm.set_group(op, enable=1)
+                fvm.set_group(op, enable=1, nodes_per_warp=2 if op == "laplacian" else 4)
             # edge-based two-pass forms
             gx, gy = fvm.gradient_edges(fd, nlev)
             d = fvm.divergence_edges(ud, vd, nlev)

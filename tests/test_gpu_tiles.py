@@ -58,21 +58,23 @@ def _filled(torch, x, n):
     return [torch.full_like(x, 7.0) for _ in range(n)]
 
 
-def _compare(torch, fvm, x, y, nlev, groups=(7, 3, 1), ops=OPS):
-    """Every operator with the tile kernels (tiles of several sizes) against
-    the per-node kernels: identical outputs, padding included (outputs start
-    filled with 7: the levels past the stored vectors must keep it)."""
+def _compare(torch, fvm, x, y, nlev, groups=(7, 3, 1), ops=OPS, npws=(4, 2)):
+    """Every operator with the tile kernels (tiles of several sizes, one or
+    two consumer warps per group) against the per-node kernels: identical
+    outputs, padding included (outputs start filled with 7: the levels past
+    the stored vectors must keep it)."""
     for op in ops:
         n = NOUT.get(op, 1)
         fvm.set_group(op, enable=0)
         ref = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
         for gpt in groups:
-            fvm.set_group(op, enable=1, groups_per_tile=gpt)
-            got = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
-            torch.cuda.synchronize()
-            for a, b in zip(got, ref):
-                assert torch.equal(a, b), (op, gpt)
-        fvm.set_group(op, enable=1, groups_per_tile=7)
+            for npw in npws:
+                fvm.set_group(op, enable=1, groups_per_tile=gpt, nodes_per_warp=npw)
+                got = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
+                torch.cuda.synchronize()
+                for a, b in zip(got, ref):
+                    assert torch.equal(a, b), (op, gpt, npw)
+        fvm.set_group(op, enable=1, groups_per_tile=7, nodes_per_warp=2 if op == "laplacian" else 4)
 
 
 def _fields(torch, V, ld, dt, seed):
