@@ -222,6 +222,14 @@ __device__ __forceinline__ void lv_load(uint32_t rowa, const Layout<VA, VB>& L, 
   Ld<S, VA>::run(rowa + ES * static_cast<uint32_t>(L.offA), x.a);
   if constexpr (VB > 0) Ld<S, VB>::run(rowa + ES * static_cast<uint32_t>(L.offB), x.b);
 }
+// The same from the lane's part A and part B addresses of slot 0 (baseA,
+// baseB) and a row offset in bytes: one multiply-add per part and load.
+template <typename S, int VA, int VB>
+__device__ __forceinline__ void lv_load_at(uint32_t slot, uint32_t rb, uint32_t baseA, uint32_t baseB,
+                                           Lv<VA, VB>& x) {
+  Ld<S, VA>::run(slot * rb + baseA, x.a);
+  if constexpr (VB > 0) Ld<S, VB>::run(slot * rb + baseB, x.b);
+}
 // Stores cover the levels below nstore: nlev rounded up to the widest
 // vector the row layout allows, so the padding up to the end of the last
 // 16-byte vector is zeroed whatever VA and VB the launch uses.
@@ -511,13 +519,20 @@ __global__ void __launch_bounds__(NPW == 4 ? 256 : 512, 1) tile_kernel(const Til
       if (cnt <= 0) continue;
       for (int lb = 0; lb < a.nlb; ++lb) {
         const Layout<VA, VB> L(lb * LB, lane);
+        // this lane's part A and part B addresses in slot 0 of each field
+        uint32_t baseA[NIN], baseB[NIN];
+#pragma unroll
+        for (int m = 0; m < NIN; ++m) {
+          baseA[m] = rows[m] + static_cast<uint32_t>(sizeof(S)) * static_cast<uint32_t>(L.offA);
+          baseB[m] = rows[m] + static_cast<uint32_t>(sizeof(S)) * static_cast<uint32_t>(L.offB);
+        }
         Lv<VA, VB> xo[NIN][NPW], acc[NOUT][NPW];
 #pragma unroll
         for (int gg = 0; gg < NPW; ++gg) {
 #pragma unroll
           for (int m = 0; m < NIN; ++m) {
             if (gg < cnt)  // warp-uniform
-              lv_load<S, VA, VB>(rows[m] + (slot0 + n0 + gg) * rb, L, xo[m][gg]);
+              lv_load_at<S, VA, VB>(slot0 + n0 + gg, rb, baseA[m], baseB[m], xo[m][gg]);
             else lv_zero(xo[m][gg]);
           }
 #pragma unroll
@@ -559,7 +574,7 @@ __global__ void __launch_bounds__(NPW == 4 ? 256 : 512, 1) tile_kernel(const Til
 #pragma unroll
           for (int gg = 0; gg < NPW; ++gg)
 #pragma unroll
-            for (int m = 0; m < NIN; ++m) lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
+            for (int m = 0; m < NIN; ++m) lv_load_at<S, VA, VB>(sls[gg], rb, baseA[m], baseB[m], x[gg][m]);
         };
         auto use = [&](const Lv<VA, VB> (&x)[NPW][NIN], const Wts<NPW * NW>& W) {
 #pragma unroll
@@ -598,7 +613,7 @@ __global__ void __launch_bounds__(NPW == 4 ? 256 : 512, 1) tile_kernel(const Til
 #pragma unroll
               for (int m = 0; m < NIN; ++m) {
                 if (src >= 0 && src < NPW) x[gg][m] = xo[m][src];
-                else lv_load<S, VA, VB>(rows[m] + sls[gg] * rb, L, x[gg][m]);
+                else lv_load_at<S, VA, VB>(sls[gg], rb, baseA[m], baseB[m], x[gg][m]);
               }
             }
             use(x, W);
