@@ -22,14 +22,18 @@
 //     memory, where a warp's 16-byte-per-lane load of a row costs exactly its
 //     four lines, and each staged row serves every node of the tile that
 //     needs it;
-//   * give each consumer warp one group and all levels: lane l holds levels
-//     4l .. 4l+3 of every row it reads (part A) and level 128 + l (part B);
-//     the group's four nodes walk their own stencil rows in step, which gives
-//     four independent chains of arithmetic per lane;
+//   * give each consumer warp a group (or half a group: two of its nodes)
+//     and all levels: lane l holds levels 4l .. 4l+3 of every row it reads
+//     (part A) and level 128 + l (part B); the warp's nodes walk their own
+//     stencil rows in step, which gives independent chains of arithmetic
+//     per lane;
+//   * take the row neighbours that belong to the same group from the
+//     registers that hold the group's own values (their entries come first
+//     in every row, at known offsets);
 //   * do the arithmetic on pairs of levels with the packed FP32 instructions
 //     (__fadd2_rn, __ffma2_rn): each half rounds as the scalar instruction
 //     does.
-// Every node accumulates its terms in ascending neighbour order with the same
+// Every node accumulates its terms in its stencil row's order with the same
 // subtraction and fused multiply-add as the per-node kernels (a row shorter
 // than its group's longest is padded with zero-weight terms of the node
 // itself, which add exact zeros), so the results are bitwise those of the
@@ -212,18 +216,12 @@ template <int VA, int VB> struct Layout {
   __device__ __forceinline__ Layout(int lev0, int lane) : offA(lev0 + VA * lane), offB(lev0 + 32 * VA + VB * lane) {}
 };
 
-// One node row's share of this lane from a staged row (rowa: shared address
-// of the row's level 0).  Unconditional: lanes past nlev read the padding
-// of the row, the next row or the stage's slack (in bounds of the block's
-// shared memory) and those values are never stored.
-template <typename S, int VA, int VB>
-__device__ __forceinline__ void lv_load(uint32_t rowa, const Layout<VA, VB>& L, Lv<VA, VB>& x) {
-  constexpr uint32_t ES = sizeof(S);
-  Ld<S, VA>::run(rowa + ES * static_cast<uint32_t>(L.offA), x.a);
-  if constexpr (VB > 0) Ld<S, VB>::run(rowa + ES * static_cast<uint32_t>(L.offB), x.b);
-}
-// The same from the lane's part A and part B addresses of slot 0 (baseA,
-// baseB) and a row offset in bytes: one multiply-add per part and load.
+// One node row's share of this lane from the staged row in slot `slot`
+// (rb bytes per staged row), given the lane's part A and part B addresses in
+// slot 0 (baseA, baseB): one multiply-add per part and load.  Unconditional:
+// lanes past nlev read the padding of the row, the next row or the stage's
+// slack (in bounds of the block's shared memory) and those values are never
+// stored.
 template <typename S, int VA, int VB>
 __device__ __forceinline__ void lv_load_at(uint32_t slot, uint32_t rb, uint32_t baseA, uint32_t baseB,
                                            Lv<VA, VB>& x) {
