@@ -333,7 +333,7 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* only; takes effect at the next operator call.                           */
 /* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
 /* group, each walking two of its nodes: twice the warps per block); 0    */
-/* keeps; default 4.                                                       */
+/* keeps; default 4, 2 for the FP32 Laplacian.                             */
 int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile,
                         int nodes_per_warp);
 /* Launch shape the node-group kernel of one operator takes on fields of   */

@@ -145,7 +145,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
             if verbose:
                 print("tune %-18s node vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
                       (op, vec, batch, threads, bps, tile, ms))
-        _, _, vec, batch, threads, bps, tile, _, _ = min(results)
+        _, _, vec, batch, threads, bps, tile, _, _, _ = min(results)
         fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
         # the tile kernel's shapes (where it applies to these fields)
         if fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:

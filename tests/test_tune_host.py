@@ -57,3 +57,54 @@ def test_candidates_respect_the_kernels_limits(product, dtype):
         for vec, batch, threads, bps, tile in itertools.product(c["vec"], c["batch"], c["threads"], c["bps"],
                                                                 c["tile"]):
             fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
+
+
+def test_tune_fvm_picks_and_installs_the_fastest_candidate(product, monkeypatch, tmp_path):
+    """The tuner's bookkeeping on the host, with the timing faked: every
+    candidate (per-node shapes, then node-group shapes) is timed once, the
+    fastest is installed (set_group / set_launch), reported with the
+    node-group kernel's actual launch shape, and cached; a second run takes
+    it from the cache without timing anything."""
+    import torch
+    atlas, _ = product
+    from paper_1908_07038_gb300 import tune
+    real = atlas.build_fvm(8)
+
+    class Fvm:
+        grid, nnodes = real.grid, real.nnodes
+
+        def __init__(self):
+            self.calls = []
+
+        def set_launch(self, *a, **k):
+            self.calls.append(("launch", a, k))
+            real.set_launch(*a, **k)
+
+        def set_group(self, *a, **k):
+            self.calls.append(("group", a, k))
+            real.set_group(*a, **k)
+
+        def tile_info(self, op, nlev, ld, dtype=0):
+            return dict(blocks_per_sm=1, stages=3, smem=1 << 17, max_rows=100)
+
+    fvm = Fvm()
+    timings = iter([5.0 - 0.01 * k for k in range(1000)])  # every later candidate is faster
+    monkeypatch.setattr(tune, "time_call", lambda fn, reps=5, warmup=3: next(timings))
+    monkeypatch.setattr(tune, "_call", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "fake-gpu")
+    monkeypatch.setenv("ATLASGB_TUNE_CACHE", str(tmp_path / "tune.json"))
+    fields = tuple(torch.zeros((real.nnodes, 140)) for _ in range(3))
+    best = tune.tune_fvm(fvm, atlas.ATLAS_F32, 137, 140, ("gradient",), fields=fields, reps=1)
+    b = best["gradient"]
+    last = tune.TILE_CANDIDATES[-1]  # timed last, hence fastest
+    assert b["kernel"] == "tile" and (b["groups"], b["tile_bps"], b["npw"]) == last
+    assert (b["tile_blocks"], b["tile_stages"]) == (1, 3)
+    n_node = 1
+    for v in tune.CANDIDATES[atlas.ATLAS_F32].values():
+        n_node *= len(v)
+    assert len(b["sweep"]) == n_node + len(tune.TILE_CANDIDATES)
+    assert fvm.calls[-1][0] == "group" and fvm.calls[-1][2].get("nodes_per_warp") == last[2]
+    # cached: the second run times nothing
+    monkeypatch.setattr(tune, "time_call", lambda *a, **k: pytest.fail("timed a cached shape"))
+    again = tune.tune_fvm(fvm, atlas.ATLAS_F32, 137, 140, ("gradient",), fields=fields, reps=1)
+    assert again["gradient"]["npw"] == last[2] and again["gradient"]["kernel"] == "tile"
