@@ -170,7 +170,7 @@ struct LaunchCfg {
   int threads = 128;
   int blocks_per_sm = 0;  // 0 = occupancy limit
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
-  int group = 1;          // 1: shared-memory node-group kernel where it applies; 0: per-node kernel only
+  int group = 1;          // node-group kernel: 1 where it applies and pays (kTileMinLevels), 2 wherever it applies, 0 never
   int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
   int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..7)
   int tile_npw = 4;       // node-group kernel: nodes per consumer warp (4: a warp per group; 2: two per group)
@@ -181,6 +181,10 @@ struct LaunchCfg {
 // the caller's fields).  Two-ring Laplacian: 2 blocks of 512 threads per SM
 // keep fewer neighbourhoods in L1; one-ring FP32: 256 threads, 3 entries per
 // batch; bfloat16: tiles of 64 passes for the Laplacian.
+// Fields of this many levels or fewer run on the per-node kernels unless the
+// node-group kernels are forced (atlas_fvm_set_group enable 2).
+constexpr int kTileMinLevels = 96;
+
 LaunchCfg default_launch(int op, int dt) {
   LaunchCfg c;
   c.batch = 3;
@@ -612,7 +616,13 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   bd.olo = static_cast<int32_t>(node0);
   bd.ohi = static_cast<int32_t>(node0 + count);
   bd.err = atlasgb::bounds_word();
-  if (gt.ok && c.group && (ld * es) % 16 == 0 && atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
+  // the node-group kernel's table work per tile is the same for any level
+  // count, so it pays only on fields of many levels: on O640 a one-level
+  // gradient took 0.37 ms in it, and 60 levels 0.43 ms against 0.55 ms for
+  // 137; the per-node kernels run fields of kTileMinLevels levels or fewer
+  const bool tiles_wanted = c.group == 2 || (c.group == 1 && nlev > kTileMinLevels);
+  if (gt.ok && tiles_wanted && (ld * es) % 16 == 0 &&
+      atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned
     // rows, and the range must be made of whole tiles
     bool aligned = true;
@@ -1142,7 +1152,7 @@ int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
   if (dtype != -1 && !valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "dtype must be -1 (all) or an atlas_dtype");
-  if (enable < -1 || enable > 1) return fail(ATLAS_EINVAL, "enable must be -1, 0 or 1");
+  if (enable < -1 || enable > 2) return fail(ATLAS_EINVAL, "enable must be -1, 0, 1 or 2");
   if (blocks_per_sm < 0 || blocks_per_sm > 2) return fail(ATLAS_EINVAL, "blocks_per_sm must be 0, 1 or 2");
   if (groups_per_tile < 0 || groups_per_tile > 7) return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, 7]");
   if (nodes_per_warp != 0 && nodes_per_warp != 2 && nodes_per_warp != 4)

@@ -74,7 +74,7 @@ def main():
                 x, y = (ud, vd) if op in TWO_IN else (fd, None)
                 want = oracle_op(om, op, u if op in TWO_IN else f, v, nlev)
                 # per-node kernel; node-group kernels (FP32/BF16 fields) with one or two warps per group
-                for group, npw in (((0, 4), (1, 4), (1, 2)) if name == "f32" else ((0, 4),)):
+                for group, npw in (((0, 4), (2, 4), (2, 2)) if name == "f32" else ((0, 4),)):
                     fvm.set_group(op, enable=group, nodes_per_warp=npw)
                     got = gpu_op(fvm, op, x, y, nlev)
                     torch.cuda.synchronize()

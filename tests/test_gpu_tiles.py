@@ -69,7 +69,7 @@ def _compare(torch, fvm, x, y, nlev, groups=(7, 3, 1), ops=OPS, npws=(4, 2)):
         ref = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
         for gpt in groups:
             for npw in npws:
-                fvm.set_group(op, enable=1, groups_per_tile=gpt, nodes_per_warp=npw)
+                fvm.set_group(op, enable=2, groups_per_tile=gpt, nodes_per_warp=npw)
                 got = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
                 torch.cuda.synchronize()
                 for a, b in zip(got, ref):
