@@ -316,16 +316,18 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* and each consumer warp computes one group, its four nodes walking their */
 /* own stencil rows from shared memory.  By default every FP32 operator   */
 /* and the BF16 Laplacian use them (the BF16 one-ring operators measured   */
-/* faster per node) on fields of more than 96 levels wherever they apply:  */
+/* faster per node), the one-ring operators on fields of more than 96      */
+/* levels, wherever they apply:                                            */
 /* field pointers 16-byte aligned, ld * element size                       */
 /* a multiple of 16, two stages of the tile's rows fitting in shared       */
 /* memory (at O1280 x 137 FP32 with ld 140: every operator), and a launch  */
 /* made of whole tiles (whole grids, partitions of whole rows); the        */
 /* per-node kernels run elsewhere, with bitwise identical results.        */
-/* enable: 1 use them on fields of more than 96 levels (their table work  */
-/* per tile does not shrink with the levels: below that the per-node      */
-/* kernels measured faster), 2 use them wherever they apply, 0 per-node    */
-/* kernels only, -1 keep.  blocks_per_sm: 1                               */
+/* enable: 1 use them by default (one-ring operators on fields of more     */
+/* than 96 levels: their table work per tile does not shrink with the     */
+/* levels, and below that the per-node kernels measured faster; the        */
+/* Laplacian on any), 2 use them wherever they apply, 0 per-node kernels   */
+/* only, -1 keep.  blocks_per_sm: 1                                        */
 /* or 2 blocks of 32 (groups_per_tile + 1) threads per SM at most (fewer   */
 /* when shared memory or registers are short; 0 keeps; default 1: one     */
 /* block holding up to four stages measured faster than two blocks of two, */

@@ -265,9 +265,10 @@ class Fvm:
                                   int(blocks_per_sm), int(tile_passes))
 
     def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1, nodes_per_warp=0):
-        """Use the shared-memory node-group kernels for one operator on
-        fields of more than 96 levels (enable 1, the default), on every
-        field they apply to (2), or the per-node kernels only (0; -1 keeps),
+        """Use the shared-memory node-group kernels for one operator by
+        default (enable 1: one-ring operators on fields of more than 96
+        levels, the Laplacian on any), on every field they apply to (2), or
+        the per-node kernels only (0; -1 keeps),
         with at most
         blocks_per_sm blocks per SM (1 or 2; 0 keeps), groups_per_tile
         groups of four nodes per tile (1..7; 0 keeps) and nodes_per_warp

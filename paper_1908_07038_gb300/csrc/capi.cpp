@@ -174,6 +174,13 @@ struct LaunchCfg {
   int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
   int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..7)
   int tile_npw = 4;       // node-group kernel: nodes per consumer warp (4: a warp per group; 2: two per group)
+  // fields of this many levels or fewer run on the per-node kernel unless
+  // the node-group kernel is forced (group 2): its table work per tile does
+  // not shrink with the levels.  Measured on O640 (FP32): a one-level
+  // gradient 0.37 ms in the node-group kernel; 60 levels 0.43 ms against
+  // 0.26 per node; 91 levels 0.51 against 0.49.  The Laplacian's per-node
+  // kernel is slower at any level count, so its threshold is 0.
+  int tile_min_levels = 96;
 };
 
 // Launch shape an fvm starts with, per operator and storage dtype: the
@@ -181,12 +188,9 @@ struct LaunchCfg {
 // the caller's fields).  Two-ring Laplacian: 2 blocks of 512 threads per SM
 // keep fewer neighbourhoods in L1; one-ring FP32: 256 threads, 3 entries per
 // batch; bfloat16: tiles of 64 passes for the Laplacian.
-// Fields of this many levels or fewer run on the per-node kernels unless the
-// node-group kernels are forced (atlas_fvm_set_group enable 2).
-constexpr int kTileMinLevels = 96;
-
 LaunchCfg default_launch(int op, int dt) {
   LaunchCfg c;
+  if (op == atlasgb::OP_LAP) c.tile_min_levels = 0;
   c.batch = 3;
   c.threads = 256;
   if (dt == ATLAS_F32) {
@@ -616,11 +620,8 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   bd.olo = static_cast<int32_t>(node0);
   bd.ohi = static_cast<int32_t>(node0 + count);
   bd.err = atlasgb::bounds_word();
-  // the node-group kernel's table work per tile is the same for any level
-  // count, so it pays only on fields of many levels: on O640 a one-level
-  // gradient took 0.37 ms in it, and 60 levels 0.43 ms against 0.55 ms for
-  // 137; the per-node kernels run fields of kTileMinLevels levels or fewer
-  const bool tiles_wanted = c.group == 2 || (c.group == 1 && nlev > kTileMinLevels);
+  // the node-group kernel where it pays (LaunchCfg::tile_min_levels)
+  const bool tiles_wanted = c.group == 2 || (c.group == 1 && nlev > c.tile_min_levels);
   if (gt.ok && tiles_wanted && (ld * es) % 16 == 0 &&
       atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned

@@ -29,8 +29,9 @@ CANDIDATES = {
     ATLAS_F64: dict(vec=(2, 1), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1,)),
     ATLAS_BF16: dict(vec=(8, 4), batch=(6, 3), threads=(128, 256), bps=(0,), tile=(1, 8, 64)),
 }
-# fields of this many levels or fewer run on the per-node kernels unless the
-# node-group kernels are forced (the library's rule)
+# fields of this many levels or fewer run the one-ring operators on the
+# per-node kernels unless the node-group kernels are forced (the library's
+# rule; the Laplacian runs the node-group kernel at any level count)
 TILE_MIN_LEVELS = 96
 # node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp)
 TILE_CANDIDATES = ((7, 1, 4), (7, 2, 4), (7, 1, 2), (5, 1, 4))
@@ -152,7 +153,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
         # the tile kernel's shapes (where it applies to these fields: the
         # library runs it on fields of more than TILE_MIN_LEVELS levels)
-        if nlev > TILE_MIN_LEVELS and fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
+        if (nlev > TILE_MIN_LEVELS or op == "laplacian") and fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
             for groups, tbps, npw in TILE_CANDIDATES:
                 fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw)
                 ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
