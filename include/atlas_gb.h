@@ -313,32 +313,31 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* groups of four consecutive nodes; a producer warp copies the node rows */
 /* a tile reads (its own and their neighbours, a few runs of consecutive  */
 /* ids) into shared memory with TMA bulk copies, up to four tiles ahead,  */
-/* and each consumer warp computes one group, its four nodes walking their */
-/* own stencil rows from shared memory.  By default every FP32 operator   */
-/* and the BF16 Laplacian use them (the BF16 one-ring operators measured   */
-/* faster per node), the one-ring operators on fields of more than 96      */
-/* levels, wherever they apply:                                            */
-/* field pointers 16-byte aligned, ld * element size                       */
-/* a multiple of 16, two stages of the tile's rows fitting in shared       */
-/* memory (at O1280 x 137 FP32 with ld 140: every operator), and a launch  */
-/* made of whole tiles (whole grids, partitions of whole rows); the        */
-/* per-node kernels run elsewhere, with bitwise identical results.        */
-/* enable: 1 use them by default (one-ring operators on fields of more     */
-/* than 96 levels: their table work per tile does not shrink with the     */
-/* levels, and below that the per-node kernels measured faster; the        */
-/* Laplacian on any), 2 use them wherever they apply, 0 per-node kernels   */
-/* only, -1 keep.  blocks_per_sm: 1                                        */
-/* or 2 blocks of 32 (groups_per_tile + 1) threads per SM at most (fewer   */
-/* when shared memory or registers are short; 0 keeps; default 1: one     */
-/* block holding up to four stages measured faster than two blocks of two, */
-/* except for the BF16 Laplacian, default 2).                              */
+/* and the consumer warps (one per group, or two per group with two nodes */
+/* each) walk their nodes' stencil rows from shared memory.  They apply   */
+/* where the field pointers are 16-byte aligned, ld * element size is a   */
+/* multiple of 16, two stages of a tile's rows fit in shared memory (at   */
+/* O1280 x 137 FP32 with ld 140: every operator) and the launch is made   */
+/* of whole tiles (whole grids, partitions of whole rows); elsewhere the  */
+/* per-node kernels run, with bitwise identical results.                  */
+/* enable: 1 (default) uses them for the FP32 operators and the BF16      */
+/* Laplacian, the one-ring operators only on fields of more than 96       */
+/* levels (their table work per tile does not shrink with the levels;     */
+/* below that, and for the BF16 one-ring operators, the per-node kernels  */
+/* measured faster); 2 uses them wherever they apply; 0 per-node kernels  */
+/* only; -1 keeps.                                                        */
+/* blocks_per_sm: 1 or 2 blocks per SM at most (fewer when shared memory  */
+/* or registers are short; 0 keeps; default 1: one block holding up to    */
+/* four stages measured faster than two blocks of two, except for the     */
+/* BF16 Laplacian, default 2).                                            */
 /* groups_per_tile: 1..7 (0 keeps; default 7; smaller tiles take less     */
-/* shared memory, so more stages fit; a change rebuilds the operator's     */
-/* tile tables at its next call).  dtype -1 sets all three dtypes.  Host  */
-/* only; takes effect at the next operator call.                           */
+/* shared memory, so more stages fit, but measured slower; a change       */
+/* rebuilds the operator's tile tables at its next call).                 */
 /* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
 /* group, each walking two of its nodes: twice the warps per block); 0    */
 /* keeps; default 4, 2 for the FP32 Laplacian.                             */
+/* dtype -1 sets all three dtypes.  Host only; takes effect at the next   */
+/* operator call.                                                          */
 int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile,
                         int nodes_per_warp);
 /* Launch shape the node-group kernel of one operator takes on fields of   */
