@@ -321,18 +321,20 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* of whole tiles (whole grids, partitions of whole rows); elsewhere the  */
 /* per-node kernels run, with bitwise identical results.                  */
 /* enable: 1 (default) uses them for the FP32 operators and the BF16      */
-/* Laplacian, the one-ring operators only on fields of more than 96       */
-/* levels (their table work per tile does not shrink with the levels;     */
-/* below that, and for the BF16 one-ring operators, the per-node kernels  */
-/* measured faster); 2 uses them wherever they apply; 0 per-node kernels  */
-/* only; -1 keeps.                                                        */
+/* one-input operators and Laplacian, the one-ring operators only on      */
+/* fields of more than 96 levels (their table work per tile does not      */
+/* shrink with the levels; below that, and for the BF16 two-input         */
+/* operators, the per-node kernels measured as fast or faster); 2 uses    */
+/* them wherever they apply; 0 per-node kernels only; -1 keeps.           */
 /* blocks_per_sm: 1 or 2 blocks per SM at most (fewer when shared memory  */
 /* or registers are short; 0 keeps; default 1: one block holding up to    */
-/* four stages measured faster than two blocks of two, except for the     */
-/* BF16 Laplacian, default 2).                                            */
-/* groups_per_tile: 1..7 (0 keeps; default 7; smaller tiles take less     */
-/* shared memory, so more stages fit, but measured slower; a change       */
-/* rebuilds the operator's tile tables at its next call).                 */
+/* four stages measured faster than two blocks of two).                   */
+/* groups_per_tile: 1..11 (0 keeps; default 11 for the one-input one-    */
+/* ring operators and the BF16 Laplacian, else 7; with two warps per group */
+/* at most 7 run on the node-group kernel, more fall back per node;       */
+/* smaller tiles take less shared memory, so more stages fit, but         */
+/* measured slower; a change rebuilds the operator's tile tables at its   */
+/* next call).                                                             */
 /* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
 /* group, each walking two of its nodes: twice the warps per block); 0    */
 /* keeps; default 4, 2 for the FP32 Laplacian.                             */

@@ -271,7 +271,7 @@ class Fvm:
         the per-node kernels only (0; -1 keeps),
         with at most
         blocks_per_sm blocks per SM (1 or 2; 0 keeps), groups_per_tile
-        groups of four nodes per tile (1..7; 0 keeps) and nodes_per_warp
+        groups of four nodes per tile (1..11; 0 keeps) and nodes_per_warp
         nodes per consumer warp (4 or 2; 0 keeps), for one storage dtype or,
         with dtype=-1, all of them."""
         capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(blocks_per_sm),

@@ -172,7 +172,7 @@ struct LaunchCfg {
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
   int group = 1;          // node-group kernel: 1 where it applies and pays (kTileMinLevels), 2 wherever it applies, 0 never
   int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
-  int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..7)
+  int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..11)
   int tile_npw = 4;       // node-group kernel: nodes per consumer warp (4: a warp per group; 2: two per group)
   // fields of this many levels or fewer run on the per-node kernel unless
   // the node-group kernel is forced (group 2): its table work per tile does
@@ -193,21 +193,28 @@ LaunchCfg default_launch(int op, int dt) {
   if (op == atlasgb::OP_LAP) c.tile_min_levels = 0;
   c.batch = 3;
   c.threads = 256;
+  // one-input one-ring operators (one field staged): tiles of eleven groups,
+  // the most nodes in flight per SM that the register file allows (384
+  // threads); their stages still fit twice.  O1280 x 137 FP32 gradient:
+  // 1.97 ms against 2.26 with seven groups
+  const bool one_in = op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD ||
+                      op == atlasgb::OP_CURL_ADJ;
   if (dt == ATLAS_F32) {
     // the Laplacian's node-group kernel: two consumer warps per group
-    // measured 2% faster (3.16 against 3.23 ms at O1280 x 137); the one-ring
-    // operators are faster with one
+    // measured 2% faster (3.16 against 3.23 ms at O1280 x 137); its larger
+    // stages fit no larger tile
     if (op == atlasgb::OP_LAP) { c.batch = 6; c.threads = 512; c.tile_npw = 2; }
     if (op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) c.threads = 128;
+    if (one_in) c.tile_groups = 11;
   } else if (dt == ATLAS_BF16) {
     c.threads = 128;
     if (op == atlasgb::OP_LAP) c.tile_passes = 64;
-    // bfloat16 one-ring operators: the per-node kernels measured faster than
-    // the node-group kernels (O1280 x 137: 2.0 against 2.7 ms for the
-    // gradient); the Laplacian keeps the node-group kernel, two blocks per
-    // SM (its stages are half the FP32 size): 3.2 against 4.4 ms per node
-    if (op != atlasgb::OP_LAP) c.group = 0;
-    else c.tile_bps = 2;
+    // bfloat16: tiles of eleven groups for the one-input operators and the
+    // Laplacian (O1280 x 137: gradient 1.90 ms against 1.99 per node,
+    // Laplacian 2.94 against 4.4 per node); the two-input operators measured
+    // the same either way (2.35 ms) and keep the per-node kernel
+    if (one_in || op == atlasgb::OP_LAP) c.tile_groups = 11;
+    else c.group = 0;
   } else {  // F64: bound by the FP64 pipe
     c.threads = 128;
   }
@@ -622,7 +629,8 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   bd.err = atlasgb::bounds_word();
   // the node-group kernel where it pays (LaunchCfg::tile_min_levels)
   const bool tiles_wanted = c.group == 2 || (c.group == 1 && nlev > c.tile_min_levels);
-  if (gt.ok && tiles_wanted && (ld * es) % 16 == 0 &&
+  const bool tiles_fit = 32 * ((4 / c.tile_npw) * c.tile_groups + 1) <= atlasgb::tile_max_threads(c.tile_npw);
+  if (gt.ok && tiles_wanted && tiles_fit && (ld * es) % 16 == 0 &&
       atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned
     // rows, and the range must be made of whole tiles
@@ -1155,7 +1163,7 @@ int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks
   if (dtype != -1 && !valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "dtype must be -1 (all) or an atlas_dtype");
   if (enable < -1 || enable > 2) return fail(ATLAS_EINVAL, "enable must be -1, 0, 1 or 2");
   if (blocks_per_sm < 0 || blocks_per_sm > 2) return fail(ATLAS_EINVAL, "blocks_per_sm must be 0, 1 or 2");
-  if (groups_per_tile < 0 || groups_per_tile > 7) return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, 7]");
+  if (groups_per_tile < 0 || groups_per_tile > 11) return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, 11]");
   if (nodes_per_warp != 0 && nodes_per_warp != 2 && nodes_per_warp != 4)
     return fail(ATLAS_EINVAL, "nodes_per_warp must be 0, 2 or 4");
   std::lock_guard<std::mutex> lk(f->mu);

@@ -106,6 +106,9 @@ struct TileLaunch {
   Bounds bd;                 // input rows, output rows; nnz: the blob's 32-bit words
 };
 // Valid (va, vb) pairs: (1,0) (2,0) (2,1) (4,0) (4,1) (4,2).
+// Threads a node-group block may have (the kernels' launch bound): 384 with
+// four nodes per warp (up to 11 groups per tile), 512 with two (up to 7).
+inline int tile_max_threads(int npw) { return npw == 4 ? 384 : 512; }
 cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream);
 // Dynamic shared memory one block needs (two stages), or 0 above the limit.
 size_t tile_smem_bytes(const DevTiles& d, int64_t ld, int elem_size);
