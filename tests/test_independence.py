@@ -18,7 +18,22 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = "paper_1908_07038_gb300"
 
 
-SKIP_DIRS = {".git", "_work", "_build", "__pycache__", "gpurun_out", "baseline", ".pytest_cache"}
+def _ignored_dirs():
+    """Directory names the repository's .gitignore lists (plain names and
+    paths, not patterns), plus .git: what a copy without git history skips."""
+    names = {".git"}
+    try:
+        with open(os.path.join(ROOT, ".gitignore"), encoding="utf-8") as fh:
+            for line in fh:
+                line = line.strip()
+                if line and not line.startswith("#") and not any(c in line for c in "*?["):
+                    names.add(line.strip("/").split("/")[0])
+    except OSError:
+        pass
+    return names
+
+
+SKIP_DIRS = _ignored_dirs()
 
 
 def _files(prefix, exts):
