@@ -66,7 +66,7 @@ def _job_rate(units_per_rank, ws, ms):
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_o1280.json")
 KERNEL_SOURCES = tuple(os.path.join(ROOT, "paper_1908_07038_gb300", "csrc", f)
-                       for f in ("kernels.cu", "group.cuh", "group.cu", "group_f32.cu", "bounds.cuh"))
+                       for f in ("kernels.cu", "group.cuh", "group.cu", "group_f32.cu", "bounds.cuh", "patterns.h"))
 
 
 def _kernel_hash():
@@ -102,7 +102,7 @@ TILE_KERNEL_BASE = {"gradient": "tile_kernel<float,1,2,0,2,4,1,2",
                     "laplacian": "tile_kernel<float,1,1,0,1,4,1,4",
                     "gradient_adjoint": "tile_kernel<float,2,1,1,2,4,1,2",
                     "divergence_adjoint": "tile_kernel<float,1,2,1,2,4,1,2"}
-TILE_DEFAULT_NPW = {"laplacian": 2}
+TILE_DEFAULT_NPW = {}
 
 
 def _tile_kernel_name(op, npw=None):

@@ -320,24 +320,26 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* O1280 x 137 FP32 with ld 140: every operator) and the launch is made   */
 /* of whole tiles (whole grids, partitions of whole rows); elsewhere the  */
 /* per-node kernels run, with bitwise identical results.                  */
-/* enable: 1 (default) uses them for the FP32 operators and the BF16      */
-/* one-input operators and Laplacian, the one-ring operators only on      */
-/* fields of more than 96 levels (their table work per tile does not      */
-/* shrink with the levels; below that, and for the BF16 two-input         */
-/* operators, the per-node kernels measured as fast or faster); 2 uses    */
-/* them wherever they apply; 0 per-node kernels only; -1 keeps.           */
+/* enable: 1 (default) uses them for the FP32 and BF16 operators, the     */
+/* one-ring operators only on fields of more than 96 levels (their table  */
+/* work per tile does not shrink with the levels; below that the per-node */
+/* kernels measured as fast or faster); 2 uses them wherever they apply;  */
+/* 0 per-node kernels only; -1 keeps.                                      */
 /* blocks_per_sm: 1 or 2 blocks per SM at most (fewer when shared memory  */
-/* or registers are short; 0 keeps; default 1: one block holding up to    */
-/* four stages measured faster than two blocks of two).                   */
+/* or registers are short; 0 keeps; default 2 for the FP32 Laplacian,     */
+/* else 1: one block holding up to four stages measured faster than two   */
+/* blocks of two).                                                         */
 /* groups_per_tile: 1..11 (0 keeps; default 11 for the one-input one-    */
-/* ring operators and the BF16 Laplacian, else 7; with two warps per group */
-/* at most 7 run on the node-group kernel, more fall back per node;       */
-/* smaller tiles take less shared memory, so more stages fit, but         */
-/* measured slower; a change rebuilds the operator's tile tables at its   */
-/* next call).                                                             */
+/* ring operators and for BF16 fields, 4 for the FP32 Laplacian, else 7;  */
+/* with two warps per group at most 7 run on the node-group kernel, more  */
+/* fall back per node; a change rebuilds the operator's tile tables at    */
+/* its next call).                                                         */
 /* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
 /* group, each walking two of its nodes: twice the warps per block); 0    */
-/* keeps; default 4, 2 for the FP32 Laplacian.                             */
+/* keeps; default 4.  With one warp per group the tables store the groups */
+/* whose union of stencil rows matches the operator's pattern in union    */
+/* form (atlas_fvm_tile_union_groups): each distinct neighbour row is      */
+/* read once for the group's four nodes.  A change rebuilds the tables.   */
 /* dtype -1 sets all three dtypes.  Host only; takes effect at the next   */
 /* operator call.                                                          */
 int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile,
@@ -377,6 +379,20 @@ int atlas_debug_tile_hang(int on);
 /* up to ns nanoseconds each (0, the default: the hardware's own short    */
 /* suspension).  Results do not depend on it.                              */
 int atlas_debug_tile_wait_hint(unsigned ns);
+/* Tuning hook: with on == 0, node-group tables built afterwards keep      */
+/* every group in per-node form; 1 (the default) stores the groups whose   */
+/* union of stencil rows matches their operator's pattern in union form    */
+/* (tiles of one consumer warp per group only; see                          */
+/* atlas_fvm_tile_union_groups).  Results do not depend on it.             */
+int atlas_debug_tile_unions(int on);
+/* Inspection: in *n, how many groups of the node-group tables of op for   */
+/* fields of dtype are stored in union form: each distinct neighbour row   */
+/* of the group's four nodes read once and applied to every node whose     */
+/* stencil row holds it, in that row's order (the sums are those of the    */
+/* per-node form, operation for operation).  Builds the tables with the    */
+/* operator's current launch shape; 0 when there are none (F64, or tiles   */
+/* of two warps per group).                                                 */
+int atlas_fvm_tile_union_groups(atlas_fvm_t f, int op, int dtype, int64_t* n);
 /* Inspection: copy out the FP64 node-group table of one operator: the    */
 /* union of each group's stencil rows (the node-group kernels' tiles are   */
 /* cut from these groups, and stage exactly these neighbours).  Groups     */
@@ -392,6 +408,22 @@ int atlas_debug_tile_wait_hint(unsigned ns);
 /* when the stencil has no group table (then the per-node kernels run).    */
 int atlas_fvm_group_table(atlas_fvm_t f, int op, int64_t* ngroups, int64_t* nent, int32_t* head, uint32_t* hdr,
                           double* w);
+/* Inspection: copy out the FP32 tile table of one operator's node-group  */
+/* kernels, cut into tiles of groups_per_tile (1..11) groups, with union  */
+/* groups when unions != 0 (as for tiles of one warp per group).           */
+/* head[t][72] = {first node, groups, ranges, slots, blob offset (16-byte  */
+/* units), blob bytes, 0, 0}, then per copy range {first node, count,      */
+/* first slot, 0}; the staged row of slot s is the s-th smallest node id  */
+/* of the ranges.  blob: per tile {groups, 0, first node, 0}, per group    */
+/* {slot of its first node, word offset of its data, D, count | regular << */
+/* 16 | union << 17}, the B term [groups][4][2] (operators with one),      */
+/* then each group's data.  Per-node form: slots [D][4], weights           */
+/* [D][4][nw][2] (each weight twice).  Union form: slots [U] (padded to    */
+/* four words), then per entry and per node whose stencil row holds it,   */
+/* in node order, its nw weights.  Call once with NULL arrays for the      */
+/* counts.  Host only; ATLAS_EINVAL when the stencil has no tile table.   */
+int atlas_fvm_tile_table(atlas_fvm_t f, int op, int groups_per_tile, int unions, int64_t* ntiles, int64_t* nwords,
+                         int32_t* head, uint32_t* blob);
 void atlas_fvm_destroy(atlas_fvm_t f);
 
 /* ---------------------------------------------------------------------- */

@@ -236,6 +236,27 @@ class Fvm:
                                      w.ctypes.data, b.ctypes.data)
         return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
 
+    def tile_table(self, op, groups_per_tile=7, unions=True):
+        """The FP32 tile table of op's node-group kernels (host only): head
+        [ntiles][72] and blob (uint32 words; see atlas_fvm_tile_table)."""
+        code = OPS.get(op, op)
+        nt, nw = ctypes.c_int64(), ctypes.c_int64()
+        capi.atlas_fvm_tile_table(self.handle, code, int(groups_per_tile), int(bool(unions)), ctypes.byref(nt),
+                                  ctypes.byref(nw), None, None)
+        head = np.empty((max(nt.value, 1), 72), np.int32)
+        blob = np.empty(max(nw.value, 1), np.uint32)
+        capi.atlas_fvm_tile_table(self.handle, code, int(groups_per_tile), int(bool(unions)), None, None,
+                                  head.ctypes.data, blob.ctypes.data)
+        return dict(head=head[:nt.value], blob=blob[:nw.value])
+
+    def tile_union_groups(self, op, dtype=ATLAS_F32):
+        """How many groups of op's node-group tables are stored in union
+        form (each distinct neighbour row read once for the group's four
+        nodes); 0 when there are none."""
+        n = ctypes.c_int64()
+        capi.atlas_fvm_tile_union_groups(self.handle, OPS.get(op, op), int(dtype), ctypes.byref(n))
+        return n.value
+
     def tile_info(self, op, nlev, ld, dtype=ATLAS_F32):
         """Launch shape of the node-group kernel of op on [nnodes, ld] fields
         of nlev levels: blocks per SM, stages, shared memory per block,

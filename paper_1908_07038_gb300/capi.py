@@ -74,7 +74,10 @@ _SIGS = {
                                   ctypes.POINTER(I64), ctypes.POINTER(I64)], True),
     "atlas_debug_tile_hang": (I32, [I32], True),
     "atlas_debug_tile_wait_hint": (I32, [ctypes.c_uint], True),
+    "atlas_debug_tile_unions": (I32, [I32], True),
+    "atlas_fvm_tile_union_groups": (I32, [P, I32, I32, ctypes.POINTER(I64)], True),
     "atlas_fvm_group_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P, P], True),
+    "atlas_fvm_tile_table": (I32, [P, I32, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P], True),
     "atlas_fvm_stencil_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                                       P, P, P, P], True),
     "atlas_fvm_destroy": (None, [P], False),

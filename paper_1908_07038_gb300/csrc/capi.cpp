@@ -152,6 +152,7 @@ struct GroupTables {
   DevAlloc mem;
   std::vector<int64_t> first;  // first node of every tile, then nnodes
   int groups = 0;              // groups per tile the tables were cut with
+  bool unions = false;         // groups matching their union pattern stored in union form
 };
 struct OpTables {
   bool ready = false;
@@ -200,21 +201,25 @@ LaunchCfg default_launch(int op, int dt) {
   const bool one_in = op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD ||
                       op == atlasgb::OP_CURL_ADJ;
   if (dt == ATLAS_F32) {
-    // the Laplacian's node-group kernel: two consumer warps per group
-    // measured 2% faster (3.16 against 3.23 ms at O1280 x 137); its larger
-    // stages fit no larger tile
-    if (op == atlasgb::OP_LAP) { c.batch = 6; c.threads = 512; c.tile_npw = 2; }
+    // the Laplacian's node-group kernel: one warp per group (union groups),
+    // two blocks per SM of tiles of four groups (two stages each): 2.40 ms
+    // at O1280 x 137, against 2.52 in one block of tiles of eight, 2.74 of
+    // seven, and 3.12 with two warps per group (per-node form)
+    if (op == atlasgb::OP_LAP) {
+      c.batch = 6;
+      c.threads = 512;
+      c.tile_groups = 4;
+      c.tile_bps = 2;
+    }
     if (op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) c.threads = 128;
     if (one_in) c.tile_groups = 11;
   } else if (dt == ATLAS_BF16) {
     c.threads = 128;
     if (op == atlasgb::OP_LAP) c.tile_passes = 64;
-    // bfloat16: tiles of eleven groups for the one-input operators and the
-    // Laplacian (O1280 x 137: gradient 1.90 ms against 1.99 per node,
-    // Laplacian 2.94 against 4.4 per node); the two-input operators measured
-    // the same either way (2.35 ms) and keep the per-node kernel
-    if (one_in || op == atlasgb::OP_LAP) c.tile_groups = 11;
-    else c.group = 0;
+    // bfloat16: tiles of eleven groups (their stages fit at half the
+    // bytes), union groups; O1280 x 137: gradient 1.79 ms against 2.02 per
+    // node, divergence 2.17 against 2.38, Laplacian 2.39 against 4.46
+    c.tile_groups = 11;
   } else {  // F64: bound by the FP64 pipe
     c.threads = 128;
   }
@@ -263,18 +268,25 @@ std::atomic<int> g_tile_hang{0};
 // Tuning hook (atlas_debug_tile_wait_hint): suspension hint of the
 // consumers' barrier waits in nanoseconds, 0 for none.
 std::atomic<unsigned> g_tile_wait_hint{0};
+// Tuning hook (atlas_debug_tile_unions): 0 keeps every group in per-node
+// form (tables built afterwards).
+std::atomic<int> g_tile_unions{1};
+
+// Tables for launches with nodes_per_warp npw carry union groups when every
+// group has one warp.
+bool wants_unions(int npw) { return npw == 4 && g_tile_unions.load() != 0; }
 
 
 // Build and upload the tile tables of a stencil for float weights.  A
 // stencil the tile layout cannot take leaves them absent (not an error);
 // allocation failures are errors.
-int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int groups) {
+int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int groups, bool unions) {
   GroupTables& g = t.grp;
   atlasgb::GroupStencil gs;
   atlasgb::TileStencil ts;
   try {
     if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs)) return ATLAS_OK;
-    if (!atlasgb::build_tile_stencil(gs, s, groups, ts)) return ATLAS_OK;
+    if (!atlasgb::build_tile_stencil(gs, s, groups, ts, unions)) return ATLAS_OK;
   } catch (const std::bad_alloc&) {
     return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
   }
@@ -298,8 +310,11 @@ int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, i
   g.dev.nout = s.nout;
   g.dev.nw = ts.nw;
   g.dev.has_b = s.has_b;
+  g.dev.unions = ts.unions;
+  g.dev.union_groups = ts.union_groups;
   g.first.swap(ts.first);
   g.groups = groups;
+  g.unions = unions;
   g.ok = true;
   return ATLAS_OK;
 }
@@ -360,7 +375,8 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   t.dev.has_b = s.has_b;
   t.dev.scalar_w = s.scalar_w;
   if (!prec) {
-    const int rc = build_group_tables(f, s, t, f->cfg[op][dtype].tile_groups);
+    const LaunchCfg& c = f->cfg[op][dtype];
+    const int rc = build_group_tables(f, s, t, c.tile_groups, wants_unions(c.tile_npw));
     if (rc) {
       t.mem.release();
       t.dev = atlasgb::DevStencil{};
@@ -371,13 +387,15 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   return ATLAS_OK;
 }
 
-// Rebuild the tile tables when the groups per tile asked for with
-// atlas_fvm_set_group differ from those built (caller holds the fvm lock;
-// the stencil tables exist).
+// Rebuild the tile tables when the groups per tile or the nodes per warp
+// asked for with atlas_fvm_set_group differ from those built (caller holds
+// the fvm lock; the stencil tables exist).  Tiles of one warp per group
+// carry union groups, tiles of two warps per group do not.
 int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
   OpTables& t = f->st[op][dtype];
   const int want = f->cfg[op][dtype].tile_groups;
-  if (dtype == ATLAS_F64 || !t.grp.ok || t.grp.groups == want) return ATLAS_OK;
+  const bool unions = wants_unions(f->cfg[op][dtype].tile_npw);
+  if (dtype == ATLAS_F64 || !t.grp.ok || (t.grp.groups == want && t.grp.unions == unions)) return ATLAS_OK;
   atlasgb::Stencil s;
   try {
     if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
@@ -387,7 +405,7 @@ int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
   // the per-node FP32 B term the tile tables point at stays in t.mem
   t.grp.mem.release();
   t.grp = GroupTables{};
-  return build_group_tables(f, s, t, want);
+  return build_group_tables(f, s, t, want, unions);
 }
 
 int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div, 2 averaged-form grad*/, int prec) {
@@ -566,7 +584,7 @@ int run_tiles(atlas_fvm_s* f, const GroupTables& gt, const LaunchCfg& c, Storage
   l.bd = bd;
   l.sms = f->num_sms;
   l.max_bps = c.tile_bps;
-  l.npw = c.tile_npw;
+  l.npw = gt.dev.unions ? 4 : c.tile_npw;  // union groups need a warp per group
   l.wait_hint_ns = g_tile_wait_hint.load();
   if (g_tile_hang.load()) {
     l.hang_test = 1;
@@ -1207,7 +1225,7 @@ int atlas_fvm_tile_info(atlas_fvm_t h, int op, int dtype, int nlev, int64_t ld, 
   group_layout(nlev, pick_vec(static_cast<atlas_dtype>(dtype), ld, none, 0, 4), l.va, l.vb);
   l.sms = f->num_sms;
   l.max_bps = f->cfg[op][dtype].tile_bps;
-  l.npw = f->cfg[op][dtype].tile_npw;
+  l.npw = gt.dev.unions ? 4 : f->cfg[op][dtype].tile_npw;
   int b = 0, s = 0;
   size_t m = 0;
   cudaError_t e = atlasgb::tile_shape(storage_of(static_cast<atlas_dtype>(dtype)), gt.dev, l, &b, &s, &m);
@@ -1242,6 +1260,30 @@ int atlas_debug_tile_wait_hint(unsigned ns) {
   return ok();
 }
 
+int atlas_debug_tile_unions(int on) {
+  g_tile_unions.store(on ? 1 : 0);
+  return ok();
+}
+
+int atlas_fvm_tile_union_groups(atlas_fvm_t h, int op, int dtype, int64_t* n) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (!n) return fail(ATLAS_EINVAL, "n is NULL");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (!valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "unsupported dtype %d", dtype);
+  *n = 0;
+  int rc = check_device(f);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(f->mu);
+  rc = ensure_stencil(f, op, dtype);
+  if (rc) return rc;
+  rc = ensure_tile_layout(f, op, dtype);
+  if (rc) return rc;
+  const GroupTables& gt = f->st[op][dtype].grp;
+  if (gt.ok) *n = gt.dev.union_groups;
+  return ok();
+}
+
 int atlas_debug_tile_hang(int on) {
   g_tile_hang.store(on ? 1 : 0);
   return ok();
@@ -1272,6 +1314,31 @@ int atlas_fvm_group_table(atlas_fvm_t h, int op, int64_t* ngroups, int64_t* nent
       w[2 * k + 1] = gs.nw == 2 ? gs.w[2 * k + 1] : 0.0;
     }
   }
+  return ok();
+}
+
+int atlas_fvm_tile_table(atlas_fvm_t h, int op, int groups_per_tile, int unions, int64_t* ntiles, int64_t* nwords,
+                         int32_t* head, uint32_t* blob) {
+  atlas_fvm_s* f = get_fvm(h);
+  if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
+  if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
+  if (groups_per_tile < 1 || groups_per_tile > 11) return fail(ATLAS_EINVAL, "groups_per_tile must be in [1, 11]");
+  atlasgb::Stencil s;
+  atlasgb::GroupStencil gs;
+  atlasgb::TileStencil ts;
+  try {
+    if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
+    if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs) ||
+        !atlasgb::build_tile_stencil(gs, s, groups_per_tile, ts, unions != 0))
+      return fail(ATLAS_EINVAL, "this stencil has no node-group tile table");
+  } catch (const std::bad_alloc&) {
+    return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
+  }
+  const int64_t nt = static_cast<int64_t>(ts.first.size()) - 1, nw = static_cast<int64_t>(ts.blob.size());
+  if (ntiles) *ntiles = nt;
+  if (nwords) *nwords = nw;
+  if (head && nt) std::memcpy(head, ts.head.data(), sizeof(int32_t) * atlasgb::kTileHead * nt);
+  if (blob && nw) std::memcpy(blob, ts.blob.data(), sizeof(uint32_t) * nw);
   return ok();
 }
 

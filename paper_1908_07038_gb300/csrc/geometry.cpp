@@ -19,6 +19,7 @@
 //   V_i             : R^2 * compensated sum of the signed segment integrals
 #include "geometry.h"
 #include "compsum.h"
+#include "patterns.h"
 
 #include <algorithm>
 #include <cmath>
@@ -781,11 +782,66 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs) {
   return true;
 }
 
-bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts) {
+namespace {
+
+// The union of the stencil rows of the four nodes first .. first + 3 (one
+// grid row, nodes row0 .. row0 + rowlen - 1, periodic) in pattern P's order
+// (patterns.h): the run of own-row offsets, then the other neighbours by
+// ascending id.  True, with the union in `order`, when it matches P entry
+// by entry and every node's row is a subsequence of it.
+template <class P>
+bool union_of(const Stencil& s, int64_t first, int64_t row0, int64_t rowlen, std::vector<int32_t>& order) {
+  order.clear();
+  if (rowlen < P::NRUN) return false;
+  for (int e = 0; e < P::NRUN; ++e) {
+    int64_t o = (first - row0 + P::RUN0 + e) % rowlen;
+    if (o < 0) o += rowlen;
+    order.push_back(static_cast<int32_t>(row0 + o));
+  }
+  std::vector<int32_t> rest;
+  for (int t = 0; t < kGroup; ++t)
+    for (int32_t q = s.ptr[first + t]; q < s.ptr[first + t + 1]; ++q)
+      if (std::find(order.begin(), order.end(), s.nbr[q]) == order.end()) rest.push_back(s.nbr[q]);
+  std::sort(rest.begin(), rest.end());
+  rest.erase(std::unique(rest.begin(), rest.end()), rest.end());
+  order.insert(order.end(), rest.begin(), rest.end());
+  if (static_cast<int>(order.size()) != P::U) return false;
+  for (int e = 0; e < P::U; ++e) {
+    int m = 0;
+    for (int t = 0; t < kGroup; ++t)
+      for (int32_t q = s.ptr[first + t]; q < s.ptr[first + t + 1]; ++q)
+        if (s.nbr[q] == order[e]) m |= 1 << t;
+    if (m != P::mask(e)) return false;
+  }
+  for (int t = 0; t < kGroup; ++t) {
+    int at = -1;
+    for (int32_t q = s.ptr[first + t]; q < s.ptr[first + t + 1]; ++q) {
+      const int pos = static_cast<int>(std::find(order.begin(), order.end(), s.nbr[q]) - order.begin());
+      if (pos <= at) return false;
+      at = pos;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts, bool unions) {
   const int64_t ng = static_cast<int64_t>(gs.first.size()) - 1;
   const int nw = gs.nw;
   ts.nw = nw;
   ts.groups_per_tile = groups_per_tile;
+  ts.unions = unions;
+  // every group's grid row: its first node and the end of the row
+  std::vector<int64_t> grow0(static_cast<size_t>(ng)), grow1(static_cast<size_t>(ng));
+  for (int64_t gi = 0, r0 = 0; gi < ng; ++gi) {
+    if (gs.row_start[gi]) r0 = gs.first[gi];
+    grow0[gi] = r0;
+  }
+  for (int64_t gi = ng - 1, r1 = gs.first[ng]; gi >= 0; --gi) {
+    grow1[gi] = r1;
+    if (gs.row_start[gi]) r1 = gs.first[gi];
+  }
   // tiles: up to groups_per_tile consecutive groups of one grid row
   std::vector<int64_t> tg;  // first group of every tile
   for (int64_t gi = 0; gi < ng;) {
@@ -801,7 +857,8 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
   std::vector<std::vector<uint32_t>> blobs(static_cast<size_t>(nt));
   bool fits = true;
   int32_t max_slots = 0, max_blob = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(max : max_slots, max_blob)
+  int64_t n_union = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : max_slots, max_blob) reduction(+ : n_union)
   for (int64_t t = 0; t < nt; ++t) {
     const int64_t ga = tg[t], gb = tg[t + 1];
     const int ngt = static_cast<int>(gb - ga);
@@ -858,9 +915,41 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
     // per-node rows: for group k with D = its nodes' largest row, slots
     // [D][4] then weights as f32x2 pairs [D][4][nw][2]; entry e of node t
     // is its row's e-th term, or (own slot, weight 0) past its row's end
+    std::vector<int32_t> order;
     for (int k = 0; k < ngt; ++k) {
       const int64_t gi = ga + k;
       const int cnt = static_cast<int>(gs.first[gi + 1] - gs.first[gi]);
+      // a union group (patterns.h): slots [U] (padded to a multiple of
+      // four; entries of the group's own nodes hold their slots, unused),
+      // then the weights of every (entry, node holding it) in union order,
+      // nw floats each (padded likewise)
+      if (unions && cnt == kGroup &&
+          (s.scalar_w ? union_of<pat::Ring2>(s, gs.first[gi], grow0[gi], grow1[gi] - grow0[gi], order)
+                      : union_of<pat::Ring1>(s, gs.first[gi], grow0[gi], grow1[gi] - grow0[gi], order))) {
+        const int U = static_cast<int>(order.size());
+        const size_t off = b.size();
+        b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
+        b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
+        b[4 + 4 * k + 2] = static_cast<uint32_t>(U);
+        b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt) | 1u << 16 | 1u << 17;
+        const size_t o_w = off + ((static_cast<size_t>(U) + 3) & ~size_t(3));
+        b.resize(o_w, 0u);
+        for (int e = 0; e < U; ++e) b[off + static_cast<size_t>(e)] = slot(order[e]);
+        for (int e = 0; e < U; ++e)
+          for (int u = 0; u < kGroup; ++u) {
+            const int64_t i = gs.first[gi] + u;
+            for (int32_t q = s.ptr[i]; q < s.ptr[i + 1]; ++q) {
+              if (s.nbr[q] != order[e]) continue;
+              for (int c = 0; c < nw; ++c) {
+                b.push_back(0u);
+                put_f(b.size() - 1, s.w[2 * static_cast<int64_t>(q) + c]);
+              }
+            }
+          }
+        b.resize((b.size() + 3) & ~size_t(3), 0u);
+        ++n_union;
+        continue;
+      }
       int D = 0;
       for (int u = 0; u < cnt; ++u) {
         const int64_t i = gs.first[gi] + u;
@@ -931,6 +1020,7 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
   }
   ts.max_slots = max_slots;
   ts.max_blob = max_blob;
+  ts.union_groups = n_union;
   return true;
 }
 

@@ -158,11 +158,20 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
 //     (entry e of node t: its row's e-th neighbour, or its own slot past its
 //     row's end) and weights [D][4][nw] as f32x2 pairs (each weight twice;
 //     0 past the row's end).
+// With unions, a group of four nodes whose union of rows matches its
+// operator's pattern (patterns.h) is stored in union form instead: its
+// header's word 3 has bit 17 set and D = U, and its data are the slots of
+// the U union entries (padded to a multiple of four words), then, entry by
+// entry and for each node holding the entry in node order, its nw weights
+// as floats (padded likewise).  Only kernels that give each group one warp
+// read union groups.
 constexpr int kTileRanges = 16;
 constexpr int kTileHead = 8 + 4 * kTileRanges;
 struct TileStencil {
   int nw = 1;
   int groups_per_tile = 7;
+  bool unions = false;
+  int64_t union_groups = 0;       // groups stored in union form
   std::vector<int32_t> head;      // [ntiles][kTileHead]
   std::vector<uint32_t> blob;     // 32-bit words
   std::vector<int64_t> first;     // [ntiles + 1]: first node of every tile, then nnodes
@@ -171,7 +180,8 @@ struct TileStencil {
 };
 // Fails (false) when a tile needs more than kTileRanges runs (the caller
 // keeps the per-node kernels).
-bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts);
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts,
+                        bool unions = false);
 
 // Regular (full) Gaussian grid F<N>: the 2N Gaussian latitudes of O<N>, each
 // with 4N longitudes j/(4N) turns.  A remapping target, and meshed by the

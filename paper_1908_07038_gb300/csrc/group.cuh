@@ -10,7 +10,7 @@
 // their gathers use about twice per line of data: a warp spans two nodes and
 // two rows that do not start on line boundaries, and each lane reads the CSR
 // entry of its own node.  These kernels instead
-//   * cut every grid row into tiles of up to seven groups of four
+//   * cut every grid row into tiles of up to eleven groups of four
 //     consecutive nodes and let the host list, per tile, the node rows the
 //     tile reads -- its own and all their neighbours -- as a few runs of
 //     consecutive node ids (the rows above and below, the wrap of the row,
@@ -30,11 +30,19 @@
 //   * take the row neighbours that belong to the same group from the
 //     registers that hold the group's own values (their entries come first
 //     in every row, at known offsets);
+//   * with one warp per group, walk a group whose union of stencil rows
+//     matches its operator's pattern (patterns.h; almost every group of an
+//     octahedral grid) in union form: each distinct neighbour row is read
+//     once and applied to every node of the group whose row holds it, the
+//     pattern's masks compiled in.  A two-ring Laplacian group reads 30
+//     rows instead of 62, a one-ring group 12 instead of 18 per field;
+//     the other groups keep per-node rows;
 //   * do the arithmetic on pairs of levels with the packed FP32 instructions
 //     (__fadd2_rn, __ffma2_rn): each half rounds as the scalar instruction
 //     does.
 // Every node accumulates its terms in its stencil row's order with the same
-// subtraction and fused multiply-add as the per-node kernels (a row shorter
+// subtraction and fused multiply-add as the per-node kernels (the union
+// order meets every node's terms in its row's order; a row shorter
 // than its group's longest is padded with zero-weight terms of the node
 // itself, which add exact zeros), so the results are bitwise those of the
 // per-node kernels.  No atomics: deterministic.  Every wait on an mbarrier is
@@ -48,9 +56,12 @@
 #include <cstdint>
 #include <cstring>
 
+#include <type_traits>
+
 #include "bounds.cuh"
 #include "geometry.h"
 #include "kernels.h"
+#include "patterns.h"
 
 namespace atlasgb {
 namespace grp {
@@ -280,6 +291,112 @@ __device__ __forceinline__ uint4 lds_u4(uint32_t a) {
   return v;
 }
 
+// ------------------------------------------------------------ union groups
+// One term of one node: per input the difference x - x_node and the fused
+// multiply-adds of its weights, in the per-node kernels' order (w0, w1: the
+// node's weights towards the neighbour).
+template <int NIN, int NOUT, int VA, int VB>
+__device__ __forceinline__ void term(const Lv<VA, VB>& x0, const Lv<VA, VB>& x1, const Lv<VA, VB>& o0,
+                                     const Lv<VA, VB>& o1, float w0, float w1, Lv<VA, VB>& a0, Lv<VA, VB>& a1) {
+  Lv<VA, VB> d;
+  lv_sub(x0, o0, d);
+  lv_fma(pk(w0, w0), d, a0);
+  if constexpr (NIN == 1 && NOUT == 2) {
+    lv_fma(pk(w1, w1), d, a1);
+  } else if constexpr (NIN == 2) {
+    lv_sub(x1, o1, d);
+    lv_fma(pk(w1, w1), d, a0);
+  }
+}
+
+// Union entry E of pattern P (patterns.h): the rows x of its neighbour (or,
+// for a node of the group, its values in xo) applied to every node whose
+// mask bit is set, in node order.  wv holds the weight words WLO .. of the
+// entry's chunk.
+template <class P, int E, int WLO, int NW, int NIN, int NOUT, int VA, int VB, int NWV>
+__device__ __forceinline__ void union_entry(const Lv<VA, VB> (&x)[NIN], const float (&wv)[NWV],
+                                            const Lv<VA, VB> (&xo)[NIN][4], Lv<VA, VB> (&acc)[NOUT][4]) {
+  if constexpr (E < P::U) {
+    constexpr int msk = P::mask(E);
+    constexpr int wb = pat::wbase<P>(E) * NW - WLO;
+    int r = 0;
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg) {
+      if ((msk >> gg) & 1) {
+        const int wi = wb + r * NW;
+        if constexpr (pat::in_group<P>(E)) {
+          constexpr int src = P::RUN0 + E;
+          term<NIN, NOUT>(xo[0][src], xo[NIN - 1][src], xo[0][gg], xo[NIN - 1][gg], wv[wi], wv[wi + NW - 1],
+                          acc[0][gg], acc[NOUT - 1][gg]);
+        } else {
+          term<NIN, NOUT>(x[0], x[NIN - 1], xo[0][gg], xo[NIN - 1][gg], wv[wi], wv[wi + NW - 1], acc[0][gg],
+                          acc[NOUT - 1][gg]);
+        }
+        ++r;
+      }
+    }
+  }
+}
+// the rows of union entry E from its staged slot (entries of the group's
+// own nodes are not loaded)
+template <class P, int E, typename S, int NIN, int VA, int VB>
+__device__ __forceinline__ void union_load(uint32_t slot, uint32_t rb, const uint32_t (&baseA)[NIN],
+                                           const uint32_t (&baseB)[NIN], Lv<VA, VB> (&x)[NIN]) {
+  if constexpr (E < P::U && !pat::in_group<P>(E)) {
+#pragma unroll
+    for (int m = 0; m < NIN; ++m) lv_load_at<S, VA, VB>(slot, rb, baseA[m], baseB[m], x[m]);
+  }
+}
+// Words of a union group's table: U slots, then the weights, each part
+// padded to a multiple of four words.
+template <class P, int NW>
+__host__ __device__ constexpr int union_words() {
+  return ((P::U + 3) & ~3) + ((pat::wbase<P>(P::U) * NW + 3) & ~3);
+}
+
+// The union walk of one group over one level block, four entries (chunk C)
+// at a time: their slots (one 16-byte load), their weights, their rows,
+// then the entries in order.  o_s: the group's slots; o_w: its weights.
+template <class P, int C, typename S, int NIN, int NOUT, int NW, int VA, int VB>
+__device__ __forceinline__ void union_walk(const uint32_t o_s, const uint32_t o_w, const uint32_t rb,
+                                           const uint32_t (&baseA)[NIN], const uint32_t (&baseB)[NIN],
+                                           const Lv<VA, VB> (&xo)[NIN][4], Lv<VA, VB> (&acc)[NOUT][4],
+                                           const uint32_t slot_cap, const uint32_t own,
+                                           unsigned long long* const bd_err, const int32_t t) {
+  constexpr int E0 = 4 * C;
+  constexpr int NE = P::U - E0 < 4 ? P::U - E0 : 4;
+  constexpr int WLO = (pat::wbase<P>(E0) * NW) & ~3;
+  constexpr int WHI = (pat::wbase<P>(E0 + NE) * NW + 3) & ~3;
+  constexpr int NWV = WHI - WLO;
+  const uint4 q = lds_u4(o_s + 16u * static_cast<uint32_t>(C));
+  uint32_t sl[4] = {q.x, q.y, q.z, q.w};
+  if constexpr (kBoundsCheck) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (!in_bounds(u >= NE || sl[u] < slot_cap, bd_err, BC_TILE_TABLE, t)) sl[u] = own;
+  }
+  float wv[NWV];
+#pragma unroll
+  for (int k = 0; k < NWV / 4; ++k) {
+    const uint4 w4 = lds_u4(o_w + 4u * static_cast<uint32_t>(WLO + 4 * k));
+    wv[4 * k] = __uint_as_float(w4.x);
+    wv[4 * k + 1] = __uint_as_float(w4.y);
+    wv[4 * k + 2] = __uint_as_float(w4.z);
+    wv[4 * k + 3] = __uint_as_float(w4.w);
+  }
+  Lv<VA, VB> x[4][NIN];
+  union_load<P, E0, S, NIN>(sl[0], rb, baseA, baseB, x[0]);
+  union_load<P, E0 + 1, S, NIN>(sl[1], rb, baseA, baseB, x[1]);
+  union_load<P, E0 + 2, S, NIN>(sl[2], rb, baseA, baseB, x[2]);
+  union_load<P, E0 + 3, S, NIN>(sl[3], rb, baseA, baseB, x[3]);
+  union_entry<P, E0, WLO, NW, NIN, NOUT>(x[0], wv, xo, acc);
+  union_entry<P, E0 + 1, WLO, NW, NIN, NOUT>(x[1], wv, xo, acc);
+  union_entry<P, E0 + 2, WLO, NW, NIN, NOUT>(x[2], wv, xo, acc);
+  union_entry<P, E0 + 3, WLO, NW, NIN, NOUT>(x[3], wv, xo, acc);
+  if constexpr (E0 + 4 < P::U)
+    union_walk<P, C + 1, S, NIN, NOUT, NW, VA, VB>(o_s, o_w, rb, baseA, baseB, xo, acc, slot_cap, own, bd_err, t);
+}
+
 // ------------------------------------------------------------- mbarriers
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -358,6 +475,8 @@ template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int
 __global__ void __launch_bounds__(NPW == 4 ? 384 : 512, 1) tile_kernel(const TileArgs a) {
   constexpr int LB = 32 * (VA + VB);  // levels per level block
   constexpr uint32_t ES = sizeof(S);
+  // union pattern of the operator: the two-ring Laplacian or a one-ring table
+  using UP = std::conditional_t<NIN == 1 && NOUT == 1, pat::Ring2, pat::Ring1>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
   const int ns = a.nstages;
@@ -506,10 +625,16 @@ __global__ void __launch_bounds__(NPW == 4 ? 384 : 512, 1) tile_kernel(const Til
       const uint32_t slot0 = static_cast<uint32_t>(gh.x);
       const int count = gh.w & 0xffff;
       const bool regular = ((gh.w >> 16) & 1) != 0;  // the same for the whole warp
+      const bool uni = ((gh.w >> 17) & 1) != 0;      // a union group (one warp per group only)
       const int32_t node0 = tfirst + 4 * g;
-      if (!in_bounds(count <= 4 && (!regular || count == 4) && gh.x >= 0 && slot0 + static_cast<uint32_t>(count) <= slot_cap &&
-                         gh.y >= 0 && gh.z >= 0 &&
-                         4ll * gh.y + (16ll + 32ll * NW) * gh.z <= static_cast<long long>(blob_cap) &&
+      if (NPW != 4 && uni) {
+        in_bounds(false, a.bd.err, BC_TILE_TABLE, t);
+        continue;
+      }
+      if (!in_bounds(count <= 4 && (!regular || count == 4) && (!uni || (count == 4 && gh.z == UP::U)) && gh.x >= 0 &&
+                         slot0 + static_cast<uint32_t>(count) <= slot_cap && gh.y >= 0 && gh.z >= 0 &&
+                         4ll * gh.y + (uni ? 4ll * union_words<UP, NW>() : (16ll + 32ll * NW) * gh.z) <=
+                             static_cast<long long>(blob_cap) &&
                          node0 >= a.bd.olo && static_cast<int64_t>(node0) + count <= a.bd.ohi,
                      a.bd.err, BC_TILE_TABLE, t))
         continue;
@@ -591,8 +716,16 @@ __global__ void __launch_bounds__(NPW == 4 ? 384 : 512, 1) tile_kernel(const Til
             }
           }
         };
-        int e = 0;
-        if (regular) {
+        bool walked = false;
+        if constexpr (NPW == 4) {
+          if (uni) {
+            union_walk<UP, 0, S, NIN, NOUT, NW, VA, VB>(o_s, o_s + 4u * ((UP::U + 3) & ~3), rb, baseA, baseB, xo, acc,
+                                                        slot_cap, slot0, a.bd.err, t);
+            walked = true;
+          }
+        }
+        int e = walked ? D : 0;
+        if (regular && !walked) {
           // the first R entries of every node are its row neighbours at
           // offsets kOff: those inside this part are already in registers
           // (its own values xo), the others are read from shared memory

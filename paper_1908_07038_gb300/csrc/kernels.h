@@ -86,6 +86,8 @@ struct DevTiles {
   int groups_per_tile = 8;
   int nin = 1, nout = 1, nw = 1;
   bool has_b = false;
+  bool unions = false;       // union groups present: one warp per group only
+  int64_t union_groups = 0;  // groups stored in union form
 };
 struct TileLaunch {
   const void* in0 = nullptr;

@@ -34,7 +34,7 @@ CANDIDATES = {
 # rule; the Laplacian runs the node-group kernel at any level count)
 TILE_MIN_LEVELS = 96
 # node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp)
-TILE_CANDIDATES = ((11, 1, 4), (9, 1, 4), (7, 1, 4), (7, 2, 4), (7, 1, 2))
+TILE_CANDIDATES = ((11, 1, 4), (9, 1, 4), (8, 1, 4), (7, 1, 4), (7, 2, 4), (7, 1, 2))
 _TORCH_DT = None
 
 

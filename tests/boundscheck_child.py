@@ -83,7 +83,7 @@ def main():
                         assert e <= tol[name], (N, name, op, group, e)
                         worst[name] = max(worst[name], e)
                         cases += 1
-                fvm.set_group(op, enable=1, nodes_per_warp=2 if op == "laplacian" else 4)
+                fvm.set_group(op, enable=1, nodes_per_warp=4)
             # edge-based two-pass forms
             gx, gy = fvm.gradient_edges(fd, nlev)
             d = fvm.divergence_edges(ud, vd, nlev)

@@ -31,6 +31,9 @@ def torch():
 
 
 NOUT = {"gradient": 2, "divergence_adjoint": 2, "vector_gradient": 4, "curl_adjoint": 2}
+# the library's default groups per tile, per operator and storage (F32, F64, BF16)
+DEFAULT_GROUPS = {op: (11, 7, 11) if op in ("gradient", "divergence_adjoint", "vector_gradient", "curl_adjoint")
+                  else (4 if op == "laplacian" else 7, 7, 11) for op in OPS}
 
 
 def _call(fvm, op, x, y, nlev, out=None):
@@ -60,24 +63,30 @@ def _filled(torch, x, n):
 
 def _compare(torch, fvm, x, y, nlev, groups=(11, 7, 3, 1), ops=OPS, npws=(4, 2)):
     """Every operator with the tile kernels (tiles of several sizes, one or
-    two consumer warps per group) against the per-node kernels: identical
+    two consumer warps per group; with one warp per group, the tables with
+    union groups and without) against the per-node kernels: identical
     outputs, padding included (outputs start filled with 7: the levels past
     the stored vectors must keep it).  Shapes the kernels cannot take (two
     warps per group in tiles of eleven groups, stages too large) run per
     node and compare trivially."""
+    from paper_1908_07038_gb300 import capi
+    dt = {torch.float32: 0, torch.float64: 1, torch.bfloat16: 2}[x.dtype]
     for op in ops:
         n = NOUT.get(op, 1)
-        fvm.set_group(op, enable=0)
+        fvm.set_group(op, enable=0, dtype=dt)
         ref = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
         for gpt in groups:
-            for npw in npws:
-                fvm.set_group(op, enable=2, groups_per_tile=gpt, nodes_per_warp=npw)
-                got = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
-                torch.cuda.synchronize()
+            for npw, unions in [(w, u) for w in npws for u in ((1, 0) if w == 4 else (1,))]:
+                capi.atlas_debug_tile_unions(unions)
+                try:
+                    fvm.set_group(op, enable=2, groups_per_tile=gpt, nodes_per_warp=npw, dtype=dt)
+                    got = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
+                    torch.cuda.synchronize()
+                finally:
+                    capi.atlas_debug_tile_unions(1)
                 for a, b in zip(got, ref):
-                    assert torch.equal(a, b), (op, gpt, npw)
-        one_in = op in ("gradient", "divergence_adjoint", "vector_gradient", "curl_adjoint")
-        fvm.set_group(op, enable=1, groups_per_tile=11 if one_in else 7, nodes_per_warp=2 if op == "laplacian" else 4)
+                    assert torch.equal(a, b), (op, gpt, npw, unions)
+        fvm.set_group(op, enable=1, groups_per_tile=DEFAULT_GROUPS[op][dt], nodes_per_warp=4, dtype=dt)
 
 
 def _fields(torch, V, ld, dt, seed):
@@ -121,6 +130,10 @@ def test_tiles_o1280_benchmark_layout(torch, pfvm):
     fvm = pfvm(1280)
     x, y = _fields(torch, fvm.nnodes, 140, torch.float32, 11)
     _compare(torch, fvm, x, y, 137, groups=(7,))
+    # with one warp per group almost every group takes the union form
+    for op in OPS:
+        ng = sum(-(-p // 4) for p in fvm.grid.arrays()["pl"])
+        assert fvm.tile_union_groups(op) > 0.95 * ng, op
     del x, y
     torch.cuda.empty_cache()
 

@@ -1,0 +1,164 @@
+"""Host checks of the node-group kernels' tile tables (no GPU).
+
+A tile stages the node rows its groups read in shared memory and carries a
+table per group in one of two forms.  The kernels read it as follows.
+  * Per-node form: for entry e, one slot and one weight pair per node of
+    the group.
+  * Union form (groups of four whose union of stencil rows matches the
+    operator's pattern in patterns.h): one slot per distinct neighbour,
+    applied to the nodes of the pattern's mask for that entry, in node
+    order, each consuming its next weights.
+These tests decode both forms the way the kernels do and check that every
+node meets exactly its own stencil row, in its order, with its FP32
+weights.  The union form is also checked against the compiled pattern
+(masks, and the entries that are the group's own nodes, which the kernels
+take from registers), and its coverage on octahedral grids is checked.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+OPS = ("gradient", "divergence", "laplacian", "gradient_adjoint", "divergence_adjoint", "curl", "vector_gradient")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _patterns():
+    """The compiled union patterns: {name: (U, RUN0, NRUN, masks)}."""
+    src = open(os.path.join(ROOT, "paper_1908_07038_gb300", "csrc", "patterns.h")).read()
+    out = {}
+    for name, body in re.findall(r"struct (Ring\d) \{(.*?)\};", src, re.S):
+        u = int(re.search(r"U = (\d+)", body).group(1))
+        run0 = int(re.search(r"RUN0 = (-?\d+)", body).group(1))
+        nrun = int(re.search(r"NRUN = (\d+)", body).group(1))
+        masks = [int(c, 16) for c in re.search(r'hexval\("([0-9a-f]+)"', body).group(1)]
+        assert len(masks) == u
+        out[name] = (u, run0, nrun, masks)
+    return out
+
+
+@pytest.fixture(scope="module")
+def fvms(product):
+    atlas, _ = product
+    from synthetic.regional import DOMAINS
+    proj, kw = DOMAINS["lambert"]
+    return {"O2": atlas.build_fvm(2), "O24": atlas.build_fvm(24), "O64": atlas.build_fvm(64),
+            "F6": atlas.build_fvm(6, regular=True),
+            "lambert13x9": atlas.build_fvm_regional(proj, 13, 9, **kw)}
+
+
+def _f32(words):
+    return np.asarray(words, np.uint32).view(np.float32)
+
+
+def _decode(fvm, op, groups_per_tile, unions):
+    """Per node: the (neighbour, weights) terms the kernels apply, in order;
+    and the number of union groups."""
+    st = fvm.stencil_table(op)
+    tt = fvm.tile_table(op, groups_per_tile, unions)
+    head, blob = tt["head"], tt["blob"]
+    nw = 1 if op == "laplacian" else 2
+    ptr, nbr = st["ptr"], st["nbr"]
+    pats = _patterns()
+    pat = pats["Ring2"] if op == "laplacian" else pats["Ring1"]
+    V = fvm.nnodes
+    terms = [None] * V
+    nuni = 0
+    covered = 0
+    for t in range(head.shape[0]):
+        h = head[t]
+        first, ngt, nr, nslots, boff, bbytes = (int(x) for x in h[:6])
+        ids = np.full(nslots, -1, np.int64)
+        for r in range(nr):
+            rf, rc, rs = (int(x) for x in h[8 + 4 * r: 11 + 4 * r])
+            ids[rs:rs + rc] = np.arange(rf, rf + rc)
+        assert np.all(ids >= 0) and np.all(np.diff(ids) > 0)  # slot s: the s-th smallest id
+        b = blob[4 * boff: 4 * boff + bbytes // 4]
+        assert int(b[0]) == ngt and int(b[2]) == first
+        node0 = first
+        for k in range(ngt):
+            slot0, off, D, flags = (int(x) for x in b[4 + 4 * k: 8 + 4 * k])
+            cnt, regular, uni = flags & 0xFFFF, (flags >> 16) & 1, (flags >> 17) & 1
+            assert ids[slot0] == node0
+            nodes = [node0 + u for u in range(cnt)]
+            rows = [list(nbr[ptr[i]:ptr[i + 1]]) for i in nodes]
+            got = [[] for _ in nodes]
+            if uni:
+                U, run0, nrun, masks = pat
+                assert unions and cnt == 4 and regular and D == U
+                sl = b[off: off + U]
+                wv = _f32(b[off + ((U + 3) & ~3):])
+                p = 0
+                for e in range(U):
+                    j = int(ids[sl[e]]) if e >= nrun or not 0 <= run0 + e < 4 else node0 + run0 + e
+                    if e < nrun and 0 <= run0 + e < 4:
+                        assert int(ids[sl[e]]) == j  # the group's own node: taken from registers
+                    m = sum(1 << u for u in range(4) if j in rows[u])
+                    assert m == masks[e], (t, k, e)
+                    for u in range(4):
+                        if m >> u & 1:
+                            got[u].append((j, tuple(wv[p:p + nw])))
+                            p += nw
+                assert p == sum(bin(x).count("1") for x in masks) * nw
+                nuni += 1
+            else:
+                sl = b[off: off + 4 * D].reshape(D, 4)
+                wv = _f32(b[off + 4 * D: off + 4 * D * (1 + 2 * nw)]).reshape(D, 4, nw, 2)
+                assert np.all(wv[..., 0] == wv[..., 1])  # each weight twice
+                for u in range(4):
+                    i = node0 + min(u, cnt - 1)
+                    deg = ptr[i + 1] - ptr[i] if u < cnt else 0
+                    for e in range(D):
+                        if e < deg:
+                            got[u].append((int(ids[sl[e, u]]), tuple(wv[e, u, :, 0])))
+                        else:
+                            assert ids[sl[e, u]] == i and np.all(wv[e, u] == 0)
+                if regular:
+                    R, off_r = (4, (-2, -1, 1, 2)) if op == "laplacian" else (2, (-1, 1))
+                    assert cnt == 4 and D >= R
+                    for u in range(4):
+                        for r in range(R):
+                            if 0 <= u + off_r[r] < 4:
+                                assert ids[sl[r, u]] == node0 + u + off_r[r]
+            for u, i in enumerate(nodes):
+                terms[i] = got[u]
+            covered += cnt
+            node0 += cnt
+    assert covered == V
+    return terms, nuni, head.shape[0]
+
+
+@pytest.mark.parametrize("name", ["O2", "O24", "F6", "lambert13x9"])
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("unions", [True, False])
+def test_tile_tables_give_every_node_its_row(fvms, name, op, unions):
+    fvm = fvms[name]
+    st = fvm.stencil_table(op)
+    nw = 1 if op == "laplacian" else 2
+    terms, nuni, _ = _decode(fvm, op, 7, unions)
+    ptr, nbr, w = st["ptr"], st["nbr"], st["w"]
+    for i in range(fvm.nnodes):
+        want = [(int(nbr[q]), tuple(np.float32(w[q, c]) for c in range(nw))) for q in range(ptr[i], ptr[i + 1])]
+        assert terms[i] == want, i
+    if not unions:
+        assert nuni == 0
+
+
+@pytest.mark.parametrize("op", ["gradient", "laplacian", "divergence"])
+def test_union_groups_cover_octahedral_interiors(fvms, op):
+    # the patterns are those of an octant's interior: most groups of an
+    # octahedral grid take the union form, more of them on finer grids
+    frac = {}
+    for name in ("O24", "O64"):
+        _, n, _ = _decode(fvms[name], op, 11, True)
+        frac[name] = n / sum(-(-p // 4) for p in fvms[name].grid.arrays()["pl"])
+    assert frac["O64"] > frac["O24"] and frac["O64"] > (0.8 if op == "laplacian" else 0.85), frac
+
+
+def test_tile_table_arguments(fvms):
+    from paper_1908_07038_gb300.capi import AtlasError
+    with pytest.raises(AtlasError):
+        fvms["O2"].tile_table("gradient", 12)
+    with pytest.raises(AtlasError):
+        fvms["O2"].tile_table("gradient", 0)
