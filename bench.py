@@ -357,8 +357,8 @@ def _shape(t):
     """The launch shape the tuner picked, as a short string."""
     if t.get("kernel") == "tile":
         if "tile_blocks" in t:
-            return "tile kernel, %d groups per tile, %d node(s) per warp, %d block(s) of %d stages per SM" % (
-                t["groups"], t.get("npw", 4), t["tile_blocks"], t["tile_stages"])
+            return "tile kernel, %d groups per tile over %d grid row(s), %d node(s) per warp, %d block(s) of %d " \
+                "stages per SM" % (t["groups"], t.get("rows", 1), t.get("npw", 4), t["tile_blocks"], t["tile_stages"])
         return "tile kernel, %d groups per tile, %d block(s) per SM asked" % (t["groups"], t["tile_bps"])
     return "per-node kernel, vec %d, batch %d, %d threads, tile %d" % (t["vec"], t["batch"], t["threads"],
                                                                        t.get("tile", 1))

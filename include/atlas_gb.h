@@ -326,24 +326,32 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* kernels measured as fast or faster); 2 uses them wherever they apply;  */
 /* 0 per-node kernels only; -1 keeps.                                      */
 /* blocks_per_sm: 1 or 2 blocks per SM at most (fewer when shared memory  */
-/* or registers are short; 0 keeps; default 2 for the FP32 Laplacian,     */
-/* else 1: one block holding up to four stages measured faster than two   */
-/* blocks of two).                                                         */
-/* groups_per_tile: 1..11 (0 keeps; default 11 for the one-input one-    */
-/* ring operators and for BF16 fields, 4 for the FP32 Laplacian, else 7;  */
-/* with two warps per group at most 7 run on the node-group kernel, more  */
-/* fall back per node; a change rebuilds the operator's tile tables at    */
-/* its next call).                                                         */
+/* or registers are short; 0 keeps; default 1: one block holding up to    */
+/* four stages measured faster than two blocks of two).                   */
+/* groups_per_tile: 1..11 (0 keeps; default 10 for FP32 fields, 11 for    */
+/* BF16; with two warps per group at most 7 run on the node-group kernel, */
+/* more fall back per node; a change rebuilds the operator's tile tables  */
+/* at its next call).                                                      */
 /* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
 /* group, each walking two of its nodes: twice the warps per block); 0    */
 /* keeps; default 4.  With one warp per group the tables store the groups */
 /* whose union of stencil rows matches the operator's pattern in union    */
 /* form (atlas_fvm_tile_union_groups): each distinct neighbour row is      */
 /* read once for the group's four nodes.  A change rebuilds the tables.   */
+/* rows_per_tile: 1..3 grid rows a tile spans (0 keeps; default 2 for     */
+/* FP32 fields, 1 for BF16): tile                                          */
+/* k of a run of that many consecutive rows holds groups k * G .. k * G + */
+/* G - 1 of each row, G = groups_per_tile / rows_per_tile.  The rows above */
+/* and below are then staged once for several output rows (a two-ring     */
+/* tile of two rows stages six grid rows, not ten).  Launches must cover  */
+/* whole runs of rows: the rows of a run that a launch cuts (a partition */
+/* boundary) run on the per-node kernel, with identical results.  A run  */
+/* whose tile would need more than 16 copy runs (rows near the poles) is  */
+/* tiled row by row.  A change rebuilds the tables.                        */
 /* dtype -1 sets all three dtypes.  Host only; takes effect at the next   */
 /* operator call.                                                          */
 int atlas_fvm_set_group(atlas_fvm_t f, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile,
-                        int nodes_per_warp);
+                        int nodes_per_warp, int rows_per_tile);
 /* Launch shape the node-group kernel of one operator takes on fields of   */
 /* nlev levels and leading dimension ld (16-byte aligned pointers          */
 /* assumed): blocks per SM, pipeline stages per block, dynamic shared      */
@@ -409,21 +417,26 @@ int atlas_fvm_tile_union_groups(atlas_fvm_t f, int op, int dtype, int64_t* n);
 int atlas_fvm_group_table(atlas_fvm_t f, int op, int64_t* ngroups, int64_t* nent, int32_t* head, uint32_t* hdr,
                           double* w);
 /* Inspection: copy out the FP32 tile table of one operator's node-group  */
-/* kernels, cut into tiles of groups_per_tile (1..11) groups, with union  */
+/* kernels, cut into tiles of groups_per_tile (1..11) groups spanning      */
+/* rows_per_tile (1..3) grid rows (see atlas_fvm_set_group), with union    */
 /* groups when unions != 0 (as for tiles of one warp per group).           */
 /* head[t][72] = {first node, groups, ranges, slots, blob offset (16-byte  */
 /* units), blob bytes, 0, 0}, then per copy range {first node, count,      */
 /* first slot, 0}; the staged row of slot s is the s-th smallest node id  */
 /* of the ranges.  blob: per tile {groups, 0, first node, 0}, per group    */
-/* {slot of its first node, word offset of its data, D, count | regular << */
-/* 16 | union << 17}, the B term [groups][4][2] (operators with one),      */
-/* then each group's data.  Per-node form: slots [D][4], weights           */
-/* [D][4][nw][2] (each weight twice).  Union form: slots [U] (padded to    */
-/* four words), then per entry and per node whose stencil row holds it,   */
-/* in node order, its nw weights.  Call once with NULL arrays for the      */
-/* counts.  Host only; ATLAS_EINVAL when the stencil has no tile table.   */
-int atlas_fvm_tile_table(atlas_fvm_t f, int op, int groups_per_tile, int unions, int64_t* ntiles, int64_t* nwords,
-                         int32_t* head, uint32_t* blob);
+/* {slot of its first node, word offset of its data, its first node,       */
+/* count | regular << 16 | union << 17 | D << 20}, the B term              */
+/* [groups][4][2] (operators with one), then each group's data.  Per-node */
+/* form: slots [D][4], weights [D][4][nw][2] (each weight twice).  Union   */
+/* form (D = U): slots [U] (padded to four words), then per entry and per */
+/* node whose stencil row holds it, in node order, its nw weights.        */
+/* Units: unit u covers nodes unit_first[u] .. unit_first[u + 1] - 1 with */
+/* tiles unit_tile[u] .. unit_tile[u + 1] - 1 (nunits + 1 entries each).  */
+/* Call once with NULL arrays for the counts.  Host only; ATLAS_EINVAL     */
+/* when the stencil has no tile table.                                     */
+int atlas_fvm_tile_table(atlas_fvm_t f, int op, int groups_per_tile, int rows_per_tile, int unions, int64_t* ntiles,
+                         int64_t* nwords, int32_t* head, uint32_t* blob, int64_t* nunits, int64_t* unit_first,
+                         int32_t* unit_tile);
 void atlas_fvm_destroy(atlas_fvm_t f);
 
 /* ---------------------------------------------------------------------- */

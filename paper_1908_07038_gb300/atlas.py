@@ -236,18 +236,23 @@ class Fvm:
                                      w.ctypes.data, b.ctypes.data)
         return dict(ptr=ptr, nbr=nbr[:n], w=w[:n], b=b, nin=nin.value, nout=nout.value)
 
-    def tile_table(self, op, groups_per_tile=7, unions=True):
+    def tile_table(self, op, groups_per_tile=7, unions=True, rows_per_tile=1):
         """The FP32 tile table of op's node-group kernels (host only): head
-        [ntiles][72] and blob (uint32 words; see atlas_fvm_tile_table)."""
+        [ntiles][72], blob (uint32 words), and the units (runs of grid rows
+        whose tiles are consecutive): unit_first [nunits + 1] (first node,
+        then nnodes), unit_tile [nunits + 1] (first tile, then ntiles); see
+        atlas_fvm_tile_table."""
         code = OPS.get(op, op)
-        nt, nw = ctypes.c_int64(), ctypes.c_int64()
-        capi.atlas_fvm_tile_table(self.handle, code, int(groups_per_tile), int(bool(unions)), ctypes.byref(nt),
-                                  ctypes.byref(nw), None, None)
+        nt, nw, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        args = (self.handle, code, int(groups_per_tile), int(rows_per_tile), int(bool(unions)))
+        capi.atlas_fvm_tile_table(*args, ctypes.byref(nt), ctypes.byref(nw), None, None, ctypes.byref(nu), None, None)
         head = np.empty((max(nt.value, 1), 72), np.int32)
         blob = np.empty(max(nw.value, 1), np.uint32)
-        capi.atlas_fvm_tile_table(self.handle, code, int(groups_per_tile), int(bool(unions)), None, None,
-                                  head.ctypes.data, blob.ctypes.data)
-        return dict(head=head[:nt.value], blob=blob[:nw.value])
+        uf = np.empty(nu.value + 1, np.int64)
+        ut = np.empty(nu.value + 1, np.int32)
+        capi.atlas_fvm_tile_table(*args, None, None, head.ctypes.data, blob.ctypes.data, None, uf.ctypes.data,
+                                  ut.ctypes.data)
+        return dict(head=head[:nt.value], blob=blob[:nw.value], unit_first=uf, unit_tile=ut)
 
     def tile_union_groups(self, op, dtype=ATLAS_F32):
         """How many groups of op's node-group tables are stored in union
@@ -285,18 +290,20 @@ class Fvm:
         capi.atlas_fvm_set_launch(self.handle, OPS.get(op, op), int(dtype), int(vec), int(batch), int(threads),
                                   int(blocks_per_sm), int(tile_passes))
 
-    def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1, nodes_per_warp=0):
+    def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1, nodes_per_warp=0,
+                  rows_per_tile=0):
         """Use the shared-memory node-group kernels for one operator by
         default (enable 1: one-ring operators on fields of more than 96
         levels, the Laplacian on any), on every field they apply to (2), or
         the per-node kernels only (0; -1 keeps),
         with at most
         blocks_per_sm blocks per SM (1 or 2; 0 keeps), groups_per_tile
-        groups of four nodes per tile (1..11; 0 keeps) and nodes_per_warp
-        nodes per consumer warp (4 or 2; 0 keeps), for one storage dtype or,
-        with dtype=-1, all of them."""
+        groups of four nodes per tile (1..11; 0 keeps), nodes_per_warp
+        nodes per consumer warp (4 or 2; 0 keeps) and tiles spanning
+        rows_per_tile grid rows (1..3, groups_per_tile split between them;
+        0 keeps), for one storage dtype or, with dtype=-1, all of them."""
         capi.atlas_fvm_set_group(self.handle, OPS.get(op, op), int(dtype), int(enable), int(blocks_per_sm),
-                                 int(groups_per_tile), int(nodes_per_warp))
+                                 int(groups_per_tile), int(nodes_per_warp), int(rows_per_tile))
 
     def group_table(self, op):
         """The FP64 node-group table of one operator (host only): head

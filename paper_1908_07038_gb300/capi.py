@@ -67,7 +67,7 @@ _SIGS = {
     "atlas_fvm_info": (I32, [P, PP, PP, PP, PP], True),
     "atlas_fvm_prepare": (I32, [P, ctypes.c_uint, ctypes.c_uint], True),
     "atlas_fvm_set_launch": (I32, [P, I32, I32, I32, I32, I32, I32, I32], True),
-    "atlas_fvm_set_group": (I32, [P, I32, I32, I32, I32, I32, I32], True),
+    "atlas_fvm_set_group": (I32, [P, I32, I32, I32, I32, I32, I32, I32], True),
     "atlas_kernel_status": (I32, [ctypes.POINTER(ctypes.c_uint), I32], True),
     "atlas_fp64_fma_rate_kernel": (I32, [P, I32, I32, I64, P], True),
     "atlas_fvm_tile_info": (I32, [P, I32, I32, I32, I64, ctypes.POINTER(I32), ctypes.POINTER(I32),
@@ -77,7 +77,8 @@ _SIGS = {
     "atlas_debug_tile_unions": (I32, [I32], True),
     "atlas_fvm_tile_union_groups": (I32, [P, I32, I32, ctypes.POINTER(I64)], True),
     "atlas_fvm_group_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P, P], True),
-    "atlas_fvm_tile_table": (I32, [P, I32, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P], True),
+    "atlas_fvm_tile_table": (I32, [P, I32, I32, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), P, P,
+                                   ctypes.POINTER(I64), P, P], True),
     "atlas_fvm_stencil_table": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32),
                                       P, P, P, P], True),
     "atlas_fvm_destroy": (None, [P], False),

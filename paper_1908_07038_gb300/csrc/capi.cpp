@@ -150,9 +150,11 @@ struct GroupTables {
   bool ok = false;
   atlasgb::DevTiles dev;
   DevAlloc mem;
-  std::vector<int64_t> first;  // first node of every tile, then nnodes
-  int groups = 0;              // groups per tile the tables were cut with
-  bool unions = false;         // groups matching their union pattern stored in union form
+  std::vector<int64_t> first;      // first node of every unit (runs of whole grid rows), then nnodes
+  std::vector<int32_t> unit_tile;  // first tile of every unit, then ntiles
+  int groups = 0;                  // groups per tile the tables were cut with
+  int rows = 1;                    // grid rows per tile
+  bool unions = false;             // groups matching their union pattern stored in union form
 };
 struct OpTables {
   bool ready = false;
@@ -175,6 +177,7 @@ struct LaunchCfg {
   int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
   int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..11)
   int tile_npw = 4;       // node-group kernel: nodes per consumer warp (4: a warp per group; 2: two per group)
+  int tile_rows = 1;      // node-group kernel: grid rows a tile spans (1..3)
   // fields of this many levels or fewer run on the per-node kernel unless
   // the node-group kernel is forced (group 2): its table work per tile does
   // not shrink with the levels.  Measured on O640 (FP32): a one-level
@@ -194,25 +197,21 @@ LaunchCfg default_launch(int op, int dt) {
   if (op == atlasgb::OP_LAP) c.tile_min_levels = 0;
   c.batch = 3;
   c.threads = 256;
-  // one-input one-ring operators (one field staged): tiles of eleven groups,
-  // the most nodes in flight per SM that the register file allows (384
-  // threads); their stages still fit twice.  O1280 x 137 FP32 gradient:
-  // 1.97 ms against 2.26 with seven groups
-  const bool one_in = op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD ||
-                      op == atlasgb::OP_CURL_ADJ;
   if (dt == ATLAS_F32) {
-    // the Laplacian's node-group kernel: one warp per group (union groups),
-    // two blocks per SM of tiles of four groups (two stages each): 2.40 ms
-    // at O1280 x 137, against 2.52 in one block of tiles of eight, 2.74 of
-    // seven, and 3.12 with two warps per group (per-node form)
+    // the node-group kernels: tiles of ten groups spanning two grid rows
+    // (five groups of each), so the rows above and below are staged once
+    // for both; one block per SM, union groups.  O1280 x 137: gradient 1.87
+    // ms (1.90 with one-row tiles of eleven groups), divergence 2.19 (2.50
+    // with one-row tiles of seven), Laplacian 2.31 (2.38 with two blocks
+    // per SM of one-row tiles of four, 3.12 with per-node rows and two
+    // warps per group)
+    c.tile_groups = 10;
+    c.tile_rows = 2;
     if (op == atlasgb::OP_LAP) {
       c.batch = 6;
       c.threads = 512;
-      c.tile_groups = 4;
-      c.tile_bps = 2;
     }
     if (op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) c.threads = 128;
-    if (one_in) c.tile_groups = 11;
   } else if (dt == ATLAS_BF16) {
     c.threads = 128;
     if (op == atlasgb::OP_LAP) c.tile_passes = 64;
@@ -280,17 +279,17 @@ bool wants_unions(int npw) { return npw == 4 && g_tile_unions.load() != 0; }
 // Build and upload the tile tables of a stencil for float weights.  A
 // stencil the tile layout cannot take leaves them absent (not an error);
 // allocation failures are errors.
-int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int groups, bool unions) {
+int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, int groups, bool unions, int rows) {
   GroupTables& g = t.grp;
   atlasgb::GroupStencil gs;
   atlasgb::TileStencil ts;
   try {
     if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs)) return ATLAS_OK;
-    if (!atlasgb::build_tile_stencil(gs, s, groups, ts, unions)) return ATLAS_OK;
+    if (!atlasgb::build_tile_stencil(gs, s, groups, ts, unions, rows)) return ATLAS_OK;
   } catch (const std::bad_alloc&) {
     return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
   }
-  const int64_t nt = static_cast<int64_t>(ts.first.size()) - 1;
+  const int64_t nt = ts.ntiles;
   if (nt >= INT32_MAX) return ATLAS_OK;
   cudaError_t err = cudaSuccess;
   g.dev.head = g.mem.upload(ts.head, err);
@@ -306,6 +305,7 @@ int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, i
   g.dev.max_blob = ts.max_blob;
   g.dev.blob_words = static_cast<int64_t>(ts.blob.size());
   g.dev.groups_per_tile = groups;
+  g.dev.max_groups = ts.max_groups;
   g.dev.nin = s.nin;
   g.dev.nout = s.nout;
   g.dev.nw = ts.nw;
@@ -313,7 +313,9 @@ int build_group_tables(atlas_fvm_s* f, const atlasgb::Stencil& s, OpTables& t, i
   g.dev.unions = ts.unions;
   g.dev.union_groups = ts.union_groups;
   g.first.swap(ts.first);
+  g.unit_tile.swap(ts.unit_tile);
   g.groups = groups;
+  g.rows = rows;
   g.unions = unions;
   g.ok = true;
   return ATLAS_OK;
@@ -376,7 +378,7 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
   t.dev.scalar_w = s.scalar_w;
   if (!prec) {
     const LaunchCfg& c = f->cfg[op][dtype];
-    const int rc = build_group_tables(f, s, t, c.tile_groups, wants_unions(c.tile_npw));
+    const int rc = build_group_tables(f, s, t, c.tile_groups, wants_unions(c.tile_npw), c.tile_rows);
     if (rc) {
       t.mem.release();
       t.dev = atlasgb::DevStencil{};
@@ -393,9 +395,10 @@ int ensure_stencil(atlas_fvm_s* f, int op, int dtype) {
 // carry union groups, tiles of two warps per group do not.
 int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
   OpTables& t = f->st[op][dtype];
-  const int want = f->cfg[op][dtype].tile_groups;
+  const int want = f->cfg[op][dtype].tile_groups, rows = f->cfg[op][dtype].tile_rows;
   const bool unions = wants_unions(f->cfg[op][dtype].tile_npw);
-  if (dtype == ATLAS_F64 || !t.grp.ok || (t.grp.groups == want && t.grp.unions == unions)) return ATLAS_OK;
+  if (dtype == ATLAS_F64 || !t.grp.ok || (t.grp.groups == want && t.grp.unions == unions && t.grp.rows == rows))
+    return ATLAS_OK;
   atlasgb::Stencil s;
   try {
     if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
@@ -405,7 +408,7 @@ int ensure_tile_layout(atlas_fvm_s* f, int op, int dtype) {
   // the per-node FP32 B term the tile tables point at stays in t.mem
   t.grp.mem.release();
   t.grp = GroupTables{};
-  return build_group_tables(f, s, t, want, unions);
+  return build_group_tables(f, s, t, want, unions, rows);
 }
 
 int ensure_edges(atlas_fvm_s* f, int which /*0 grad, 1 div, 2 averaged-form grad*/, int prec) {
@@ -647,50 +650,68 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   bd.err = atlasgb::bounds_word();
   // the node-group kernel where it pays (LaunchCfg::tile_min_levels)
   const bool tiles_wanted = c.group == 2 || (c.group == 1 && nlev > c.tile_min_levels);
-  const bool tiles_fit = 32 * ((4 / c.tile_npw) * c.tile_groups + 1) <= atlasgb::tile_max_threads(c.tile_npw);
+  // the per-node kernel over nodes [n0, n0 + cnt) of the range
+  auto per_node = [&](int64_t n0, int64_t cnt) -> int {
+    if (cnt == 0) return ATLAS_OK;
+    atlasgb::StencilLaunch l;
+    l.in0 = shift(in0, in_first);
+    l.in1 = nin == 2 ? shift(in1, in_first) : nullptr;
+    l.out0 = const_cast<void*>(shift(out0, node0));
+    l.out1 = nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr;
+    l.nlev = nlev;
+    l.ld = ld;
+    l.node0 = static_cast<int32_t>(n0);
+    l.count = static_cast<int32_t>(cnt);
+    l.vec = pick_vec(dtype, ld, used, nu, c.vec);
+    const int64_t nvec = (nlev + l.vec - 1) / l.vec;
+    const int64_t items = cnt * nvec;
+    if (f->mesh->grid->g.nnodes * nvec >= (int64_t(1) << 31))
+      return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
+    l.threads = c.threads;
+    l.batch = c.batch;
+    l.blocks = grid_blocks(f, st, dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
+    {
+      // a tile is at most one block's even share, so blocks * tile stays
+      // below 2^31 + blocks * threads
+      const int64_t share = ((items + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
+      l.tile = static_cast<uint32_t>(
+          std::max<int64_t>(l.threads, std::min<int64_t>(int64_t(c.tile_passes) * l.threads, share)));
+    }
+    atlasgb::Bounds b2 = bd;
+    b2.nnz = dev.nnz;
+    l.bd = b2;
+    cudaError_t e = atlasgb::launch_stencil(st, dev, l, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
+    return bounds_after(stream, "stencil kernel");
+  };
+  const int npw = gt.dev.unions ? 4 : c.tile_npw;  // as run_tiles launches
+  const bool tiles_fit = gt.ok && 32 * ((4 / npw) * gt.dev.max_groups + 1) <= atlasgb::tile_max_threads(npw);
   if (gt.ok && tiles_wanted && tiles_fit && (ld * es) % 16 == 0 &&
       atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned
-    // rows, and the range must be made of whole tiles
+    // rows; it takes the whole units (runs of grid rows whose tiles are
+    // consecutive) inside the range, the per-node kernel the rest (the
+    // rows of units the range cuts), with identical results
     bool aligned = true;
     for (int k = 0; k < nu; ++k)
       if (reinterpret_cast<uintptr_t>(used[k]) % 16 != 0) aligned = false;
     const auto a = std::lower_bound(gt.first.begin(), gt.first.end(), node0);
-    const auto b = std::lower_bound(gt.first.begin(), gt.first.end(), node0 + count);
-    if (aligned && a != gt.first.end() && *a == node0 && b != gt.first.end() && *b == node0 + count)
-      return run_tiles(f, gt, c, st, shift(in0, in_first), nin == 2 ? shift(in1, in_first) : nullptr,
-                       const_cast<void*>(shift(out0, node0)), nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr,
-                       nlev, ld, dtype, used, nu, static_cast<int32_t>(a - gt.first.begin()),
-                       static_cast<int32_t>(b - a), bd, stream);
+    auto b = std::upper_bound(gt.first.begin(), gt.first.end(), node0 + count);
+    if (b != gt.first.begin()) --b;
+    if (aligned && a != gt.first.end() && a < b) {
+      const int32_t t0 = gt.unit_tile[static_cast<size_t>(a - gt.first.begin())];
+      const int32_t t1 = gt.unit_tile[static_cast<size_t>(b - gt.first.begin())];
+      rc = run_tiles(f, gt, c, st, shift(in0, in_first), nin == 2 ? shift(in1, in_first) : nullptr,
+                     const_cast<void*>(shift(out0, node0)), nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr,
+                     nlev, ld, dtype, used, nu, t0, t1 - t0, bd, stream);
+      if (rc) return rc;
+      rc = per_node(node0, *a - node0);
+      if (rc) return rc;
+      rc = per_node(*b, node0 + count - *b);
+      return rc ? rc : ok();
+    }
   }
-  atlasgb::StencilLaunch l;
-  l.in0 = shift(in0, in_first);
-  l.in1 = nin == 2 ? shift(in1, in_first) : nullptr;
-  l.out0 = const_cast<void*>(shift(out0, node0));
-  l.out1 = nout == 2 ? const_cast<void*>(shift(out1, node0)) : nullptr;
-  l.nlev = nlev;
-  l.ld = ld;
-  l.node0 = static_cast<int32_t>(node0);
-  l.count = static_cast<int32_t>(count);
-  l.vec = pick_vec(dtype, ld, used, nu, c.vec);
-  const int64_t nvec = (nlev + l.vec - 1) / l.vec;
-  const int64_t items = count * nvec;
-  if (f->mesh->grid->g.nnodes * nvec >= (int64_t(1) << 31))
-    return fail(ATLAS_EINVAL, "nnodes * level-vectors must stay below 2^31");
-  l.threads = c.threads;
-  l.batch = c.batch;
-  l.blocks = grid_blocks(f, st, dev, l.vec, l.batch, l.threads, c.blocks_per_sm, items);
-  {
-    // a tile is at most one block's even share, so blocks * tile stays
-    // below 2^31 + blocks * threads
-    const int64_t share = ((items + l.blocks - 1) / l.blocks + l.threads - 1) / l.threads * l.threads;
-    l.tile = static_cast<uint32_t>(std::max<int64_t>(l.threads, std::min<int64_t>(int64_t(c.tile_passes) * l.threads, share)));
-  }
-  bd.nnz = dev.nnz;
-  l.bd = bd;
-  cudaError_t e = atlasgb::launch_stencil(st, dev, l, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "stencil kernel launch");
-  rc = bounds_after(stream, "stencil kernel");
+  rc = per_node(node0, count);
   return rc ? rc : ok();
 }
 
@@ -1174,7 +1195,7 @@ int atlas_fvm_set_launch(atlas_fvm_t h, int op, int dtype, int vec, int batch, i
 }
 
 int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks_per_sm, int groups_per_tile,
-                        int nodes_per_warp) {
+                        int nodes_per_warp, int rows_per_tile) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
@@ -1184,6 +1205,8 @@ int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks
   if (groups_per_tile < 0 || groups_per_tile > 11) return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, 11]");
   if (nodes_per_warp != 0 && nodes_per_warp != 2 && nodes_per_warp != 4)
     return fail(ATLAS_EINVAL, "nodes_per_warp must be 0, 2 or 4");
+  if (rows_per_tile < 0 || rows_per_tile > atlasgb::kMaxTileRows)
+    return fail(ATLAS_EINVAL, "rows_per_tile must be in [0, %d]", atlasgb::kMaxTileRows);
   std::lock_guard<std::mutex> lk(f->mu);
   for (int d = 0; d < 3; ++d) {
     if (dtype != -1 && d != dtype) continue;
@@ -1191,6 +1214,7 @@ int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks
     if (blocks_per_sm) f->cfg[op][d].tile_bps = blocks_per_sm;
     if (groups_per_tile) f->cfg[op][d].tile_groups = groups_per_tile;
     if (nodes_per_warp) f->cfg[op][d].tile_npw = nodes_per_warp;
+    if (rows_per_tile) f->cfg[op][d].tile_rows = rows_per_tile;
   }
   return ok();
 }
@@ -1317,28 +1341,35 @@ int atlas_fvm_group_table(atlas_fvm_t h, int op, int64_t* ngroups, int64_t* nent
   return ok();
 }
 
-int atlas_fvm_tile_table(atlas_fvm_t h, int op, int groups_per_tile, int unions, int64_t* ntiles, int64_t* nwords,
-                         int32_t* head, uint32_t* blob) {
+int atlas_fvm_tile_table(atlas_fvm_t h, int op, int groups_per_tile, int rows_per_tile, int unions, int64_t* ntiles,
+                         int64_t* nwords, int32_t* head, uint32_t* blob, int64_t* nunits, int64_t* unit_first,
+                         int32_t* unit_tile) {
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
   if (groups_per_tile < 1 || groups_per_tile > 11) return fail(ATLAS_EINVAL, "groups_per_tile must be in [1, 11]");
+  if (rows_per_tile < 1 || rows_per_tile > atlasgb::kMaxTileRows)
+    return fail(ATLAS_EINVAL, "rows_per_tile must be in [1, %d]", atlasgb::kMaxTileRows);
   atlasgb::Stencil s;
   atlasgb::GroupStencil gs;
   atlasgb::TileStencil ts;
   try {
     if (!atlasgb::build_stencil(f->mesh->m, f->d, op, s)) return fail(ATLAS_EINVAL, "stencil table overflow");
     if (!atlasgb::build_group_stencil(s, f->mesh->grid->g, gs) ||
-        !atlasgb::build_tile_stencil(gs, s, groups_per_tile, ts, unions != 0))
+        !atlasgb::build_tile_stencil(gs, s, groups_per_tile, ts, unions != 0, rows_per_tile))
       return fail(ATLAS_EINVAL, "this stencil has no node-group tile table");
   } catch (const std::bad_alloc&) {
     return fail(ATLAS_ENOMEM, "host allocation failed while building operator tables");
   }
-  const int64_t nt = static_cast<int64_t>(ts.first.size()) - 1, nw = static_cast<int64_t>(ts.blob.size());
+  const int64_t nt = ts.ntiles, nw = static_cast<int64_t>(ts.blob.size());
+  const int64_t nun = static_cast<int64_t>(ts.first.size()) - 1;
   if (ntiles) *ntiles = nt;
   if (nwords) *nwords = nw;
+  if (nunits) *nunits = nun;
   if (head && nt) std::memcpy(head, ts.head.data(), sizeof(int32_t) * atlasgb::kTileHead * nt);
   if (blob && nw) std::memcpy(blob, ts.blob.data(), sizeof(uint32_t) * nw);
+  if (unit_first) std::memcpy(unit_first, ts.first.data(), sizeof(int64_t) * (nun + 1));
+  if (unit_tile) std::memcpy(unit_tile, ts.unit_tile.data(), sizeof(int32_t) * (nun + 1));
   return ok();
 }
 

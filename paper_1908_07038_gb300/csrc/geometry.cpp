@@ -826,7 +826,8 @@ bool union_of(const Stencil& s, int64_t first, int64_t row0, int64_t rowlen, std
 
 }  // namespace
 
-bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts, bool unions) {
+bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts, bool unions,
+                        int rows_per_tile) {
   const int64_t ng = static_cast<int64_t>(gs.first.size()) - 1;
   const int nw = gs.nw;
   ts.nw = nw;
@@ -842,186 +843,264 @@ bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per
     grow1[gi] = r1;
     if (gs.row_start[gi]) r1 = gs.first[gi];
   }
-  // tiles: up to groups_per_tile consecutive groups of one grid row
-  std::vector<int64_t> tg;  // first group of every tile
-  for (int64_t gi = 0; gi < ng;) {
-    tg.push_back(gi);
-    int64_t k = gi + 1;
-    while (k < ng && k - gi < groups_per_tile && !gs.row_start[k]) ++k;
-    gi = k;
-  }
-  const int64_t nt = static_cast<int64_t>(tg.size());
-  tg.push_back(ng);
-  ts.head.assign(static_cast<size_t>(nt * kTileHead), 0);
-  ts.first.resize(static_cast<size_t>(nt + 1));
-  std::vector<std::vector<uint32_t>> blobs(static_cast<size_t>(nt));
-  bool fits = true;
-  int32_t max_slots = 0, max_blob = 0;
-  int64_t n_union = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(max : max_slots, max_blob) reduction(+ : n_union)
-  for (int64_t t = 0; t < nt; ++t) {
-    const int64_t ga = tg[t], gb = tg[t + 1];
-    const int ngt = static_cast<int>(gb - ga);
-    // the node ids the tile reads: own nodes and every neighbour, ascending
-    std::vector<int32_t> ids;
-    for (int64_t gi = ga; gi < gb; ++gi) {
-      for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i) ids.push_back(static_cast<int32_t>(i));
-      for (int32_t q = gs.head[4 * gi + 1]; q < gs.head[4 * gi + 2]; ++q)
-        ids.push_back(static_cast<int32_t>(gs.hdr[q] & 0x0fffffffu));
-    }
-    std::sort(ids.begin(), ids.end());
-    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
-    int32_t* h = &ts.head[static_cast<size_t>(t * kTileHead)];
-    int nr = 0;
-    for (size_t k = 0; k < ids.size();) {
-      size_t e = k + 1;
-      while (e < ids.size() && ids[e] == ids[e - 1] + 1) ++e;
-      if (nr == kTileRanges) {
-        nr = kTileRanges + 1;
-        break;
+  // grid rows as runs of groups
+  std::vector<int64_t> rg;
+  for (int64_t gi = 0; gi < ng; ++gi)
+    if (gs.row_start[gi]) rg.push_back(gi);
+  rg.push_back(ng);
+  const int64_t nrows = static_cast<int64_t>(rg.size()) - 1;
+  const int rows = std::max(1, std::min({rows_per_tile, kMaxTileRows, groups_per_tile}));
+  const int64_t G = std::max(1, groups_per_tile / rows);  // groups per grid row of a tile
+  // Units: runs of `rows` grid rows (the last one shorter).  Tile k of a
+  // unit holds groups k G .. k G + G - 1 of each of its rows (rows of a
+  // unit differ by a group at most, so these are neighbours).  A unit with
+  // a tile that needs more than kTileRanges copy runs is cut into single
+  // rows.
+  struct Span {
+    int64_t ga[kMaxTileRows], gb[kMaxTileRows];
+    int n;
+    int64_t unit;
+  };
+  std::vector<uint8_t> single(static_cast<size_t>(nrows), 0);
+  std::vector<Span> spans;
+  std::vector<int64_t> ufirst, urow0, urows;
+  std::vector<int32_t> utile;
+  auto cut_units = [&]() {
+    spans.clear();
+    ufirst.clear();
+    urow0.clear();
+    urows.clear();
+    utile.clear();
+    for (int64_t r0 = 0; r0 < nrows;) {
+      const int64_t nr = single[r0] ? 1 : std::min<int64_t>(rows, nrows - r0);
+      const int64_t u = static_cast<int64_t>(ufirst.size());
+      ufirst.push_back(gs.first[rg[r0]]);
+      urow0.push_back(r0);
+      urows.push_back(nr);
+      utile.push_back(static_cast<int32_t>(spans.size()));
+      int64_t most = 0;
+      for (int64_t r = r0; r < r0 + nr; ++r) most = std::max(most, (rg[r + 1] - rg[r] + G - 1) / G);
+      for (int64_t k = 0; k < most; ++k) {
+        Span sp{};
+        sp.unit = u;
+        for (int64_t r = r0; r < r0 + nr; ++r) {
+          const int64_t ga = rg[r] + k * G, gb = std::min(ga + G, rg[r + 1]);
+          if (ga < gb) {
+            sp.ga[sp.n] = ga;
+            sp.gb[sp.n] = gb;
+            ++sp.n;
+          }
+        }
+        spans.push_back(sp);
       }
-      h[8 + 4 * nr] = ids[k];
-      h[8 + 4 * nr + 1] = static_cast<int32_t>(e - k);
-      h[8 + 4 * nr + 2] = static_cast<int32_t>(k);
-      ++nr;
-      k = e;
+      r0 += nr;
     }
-    if (nr > kTileRanges) {
-#pragma omp critical
-      fits = false;
-      continue;
-    }
-    auto slot = [&](int32_t j) {
-      return static_cast<uint32_t>(std::lower_bound(ids.begin(), ids.end(), j) - ids.begin());
-    };
-    const bool has_b = s.has_b;
-    std::vector<uint32_t>& b = blobs[t];
-    auto put_f = [&](size_t at, double v) {
-      const float x = static_cast<float>(v);
-      std::memcpy(&b[at], &x, 4);
-    };
-    // head part: tile info, group heads, B term
-    const size_t o_b = 4 + 4 * static_cast<size_t>(ngt);
-    const size_t o_data = o_b + (has_b ? 8 * static_cast<size_t>(ngt) : 0);
-    b.assign(o_data, 0u);
-    b[0] = static_cast<uint32_t>(ngt);
-    b[2] = static_cast<uint32_t>(gs.first[ga]);
-    for (int k = 0; k < ngt; ++k) {
-      const int64_t gi = ga + k;
-      if (has_b)
-        for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i)
-          for (int c = 0; c < 2; ++c) put_f(o_b + 8 * static_cast<size_t>(k) + 2 * static_cast<size_t>(i - gs.first[gi]) + c, s.b[2 * i + c]);
-    }
-    // per-node rows: for group k with D = its nodes' largest row, slots
-    // [D][4] then weights as f32x2 pairs [D][4][nw][2]; entry e of node t
-    // is its row's e-th term, or (own slot, weight 0) past its row's end
-    std::vector<int32_t> order;
-    for (int k = 0; k < ngt; ++k) {
-      const int64_t gi = ga + k;
-      const int cnt = static_cast<int>(gs.first[gi + 1] - gs.first[gi]);
-      // a union group (patterns.h): slots [U] (padded to a multiple of
-      // four; entries of the group's own nodes hold their slots, unused),
-      // then the weights of every (entry, node holding it) in union order,
-      // nw floats each (padded likewise)
-      if (unions && cnt == kGroup &&
-          (s.scalar_w ? union_of<pat::Ring2>(s, gs.first[gi], grow0[gi], grow1[gi] - grow0[gi], order)
-                      : union_of<pat::Ring1>(s, gs.first[gi], grow0[gi], grow1[gi] - grow0[gi], order))) {
-        const int U = static_cast<int>(order.size());
+    ufirst.push_back(gs.first[ng]);
+    utile.push_back(static_cast<int32_t>(spans.size()));
+  };
+  for (int pass = 0;; ++pass) {
+    cut_units();
+    const int64_t nt = static_cast<int64_t>(spans.size());
+    if (nt >= INT32_MAX) return false;
+    ts.head.assign(static_cast<size_t>(nt * kTileHead), 0);
+    std::vector<std::vector<uint32_t>> blobs(static_cast<size_t>(nt));
+    std::vector<uint8_t> bad(static_cast<size_t>(nt), 0);
+    bool fits = true;
+    int32_t max_slots = 0, max_blob = 0, max_groups = 0;
+    int64_t n_union = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : max_slots, max_blob, max_groups) reduction(+ : n_union)
+    for (int64_t t = 0; t < nt; ++t) {
+      // the tile's groups, row by row
+      std::vector<int64_t> gl;
+      for (int p = 0; p < spans[t].n; ++p)
+        for (int64_t gi = spans[t].ga[p]; gi < spans[t].gb[p]; ++gi) gl.push_back(gi);
+      const int ngt = static_cast<int>(gl.size());
+      // the node ids the tile reads: own nodes and every neighbour, ascending
+      std::vector<int32_t> ids;
+      for (const int64_t gi : gl) {
+        for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i) ids.push_back(static_cast<int32_t>(i));
+        for (int32_t q = gs.head[4 * gi + 1]; q < gs.head[4 * gi + 2]; ++q)
+          ids.push_back(static_cast<int32_t>(gs.hdr[q] & 0x0fffffffu));
+      }
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+      int32_t* h = &ts.head[static_cast<size_t>(t * kTileHead)];
+      int nr = 0;
+      for (size_t k = 0; k < ids.size();) {
+        size_t e = k + 1;
+        while (e < ids.size() && ids[e] == ids[e - 1] + 1) ++e;
+        if (nr == kTileRanges) {
+          nr = kTileRanges + 1;
+          break;
+        }
+        h[8 + 4 * nr] = ids[k];
+        h[8 + 4 * nr + 1] = static_cast<int32_t>(e - k);
+        h[8 + 4 * nr + 2] = static_cast<int32_t>(k);
+        ++nr;
+        k = e;
+      }
+      if (nr > kTileRanges) {
+        bad[t] = 1;
+        continue;
+      }
+      auto slot = [&](int32_t j) {
+        return static_cast<uint32_t>(std::lower_bound(ids.begin(), ids.end(), j) - ids.begin());
+      };
+      const bool has_b = s.has_b;
+      std::vector<uint32_t>& b = blobs[t];
+      auto put_f = [&](size_t at, double v) {
+        const float x = static_cast<float>(v);
+        std::memcpy(&b[at], &x, 4);
+      };
+      // head part: tile info, group heads, B term
+      const size_t o_b = 4 + 4 * static_cast<size_t>(ngt);
+      const size_t o_data = o_b + (has_b ? 8 * static_cast<size_t>(ngt) : 0);
+      b.assign(o_data, 0u);
+      b[0] = static_cast<uint32_t>(ngt);
+      b[2] = static_cast<uint32_t>(gs.first[gl[0]]);
+      for (int k = 0; k < ngt; ++k) {
+        const int64_t gi = gl[k];
+        if (has_b)
+          for (int64_t i = gs.first[gi]; i < gs.first[gi + 1]; ++i)
+            for (int c = 0; c < 2; ++c)
+              put_f(o_b + 8 * static_cast<size_t>(k) + 2 * static_cast<size_t>(i - gs.first[gi]) + c, s.b[2 * i + c]);
+      }
+      // group header k: slot of the group's first node, word offset of its
+      // data, its first node, count | regular << 16 | union << 17 | D << 20
+      std::vector<int32_t> order;
+      for (int k = 0; k < ngt; ++k) {
+        const int64_t gi = gl[k];
+        const int cnt = static_cast<int>(gs.first[gi + 1] - gs.first[gi]);
+        // a union group (patterns.h): slots [U] (padded to a multiple of
+        // four; entries of the group's own nodes hold their slots, unused),
+        // then the weights of every (entry, node holding it) in union order,
+        // nw floats each (padded likewise)
+        if (unions && cnt == kGroup &&
+            (s.scalar_w ? union_of<pat::Ring2>(s, gs.first[gi], grow0[gi], grow1[gi] - grow0[gi], order)
+                        : union_of<pat::Ring1>(s, gs.first[gi], grow0[gi], grow1[gi] - grow0[gi], order))) {
+          const int U = static_cast<int>(order.size());
+          const size_t off = b.size();
+          b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
+          b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
+          b[4 + 4 * k + 2] = static_cast<uint32_t>(gs.first[gi]);
+          b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt) | 1u << 16 | 1u << 17 | static_cast<uint32_t>(U) << 20;
+          const size_t o_w = off + ((static_cast<size_t>(U) + 3) & ~size_t(3));
+          b.resize(o_w, 0u);
+          for (int e = 0; e < U; ++e) b[off + static_cast<size_t>(e)] = slot(order[e]);
+          for (int e = 0; e < U; ++e)
+            for (int u = 0; u < kGroup; ++u) {
+              const int64_t i = gs.first[gi] + u;
+              for (int32_t q = s.ptr[i]; q < s.ptr[i + 1]; ++q) {
+                if (s.nbr[q] != order[e]) continue;
+                for (int c = 0; c < nw; ++c) {
+                  b.push_back(0u);
+                  put_f(b.size() - 1, s.w[2 * static_cast<int64_t>(q) + c]);
+                }
+              }
+            }
+          b.resize((b.size() + 3) & ~size_t(3), 0u);
+          ++n_union;
+          continue;
+        }
+        // per-node rows: D = the group's longest stencil row, slots [D][4]
+        // then weights as f32x2 pairs [D][4][nw][2]; entry e of node t is
+        // its row's e-th term, or (own slot, weight 0) past its row's end
+        int D = 0;
+        for (int u = 0; u < cnt; ++u) {
+          const int64_t i = gs.first[gi] + u;
+          D = std::max(D, static_cast<int>(s.ptr[i + 1] - s.ptr[i]));
+        }
+        if (D > kMaxTileRow) {
+          bad[t] = 2;
+          break;
+        }
+        // a regular group: four nodes whose first R entries are their
+        // neighbours at row offsets -1, +1 (one-ring tables, R = 2) or -2, -1,
+        // +1, +2 (the Laplacian, R = 4), wherever that neighbour is a node
+        // of the group; the kernels then read those values from registers
+        const int R = s.scalar_w ? 4 : 2;
+        static const int kOffLap[4] = {-2, -1, 1, 2}, kOffRing[2] = {-1, 1};
+        const int* dr = s.scalar_w ? kOffLap : kOffRing;
+        bool reg = cnt == kGroup && D >= R;
+        for (int u = 0; u < cnt && reg; ++u) {
+          const int64_t i = gs.first[gi] + u;
+          const int32_t deg = s.ptr[i + 1] - s.ptr[i];
+          for (int r = 0; r < R && reg; ++r) {
+            const int tt = u + dr[r];
+            if (tt >= 0 && tt < kGroup) reg = deg > r && s.nbr[s.ptr[i] + r] == gs.first[gi] + tt;
+          }
+        }
         const size_t off = b.size();
         b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
         b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
-        b[4 + 4 * k + 2] = static_cast<uint32_t>(U);
-        b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt) | 1u << 16 | 1u << 17;
-        const size_t o_w = off + ((static_cast<size_t>(U) + 3) & ~size_t(3));
-        b.resize(o_w, 0u);
-        for (int e = 0; e < U; ++e) b[off + static_cast<size_t>(e)] = slot(order[e]);
-        for (int e = 0; e < U; ++e)
-          for (int u = 0; u < kGroup; ++u) {
-            const int64_t i = gs.first[gi] + u;
-            for (int32_t q = s.ptr[i]; q < s.ptr[i + 1]; ++q) {
-              if (s.nbr[q] != order[e]) continue;
-              for (int c = 0; c < nw; ++c) {
-                b.push_back(0u);
-                put_f(b.size() - 1, s.w[2 * static_cast<int64_t>(q) + c]);
-              }
+        b[4 + 4 * k + 2] = static_cast<uint32_t>(gs.first[gi]);
+        b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt) | (reg ? 1u << 16 : 0u) | static_cast<uint32_t>(D) << 20;
+        b.resize(off + static_cast<size_t>(D) * 4 * (1 + 2 * nw), 0u);
+        const size_t o_w = off + static_cast<size_t>(D) * 4;
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = gs.first[gi] + std::min(u, cnt - 1);
+          const uint32_t own = slot(static_cast<int32_t>(i));
+          const int32_t deg = u < cnt ? s.ptr[i + 1] - s.ptr[i] : 0;
+          for (int e = 0; e < D; ++e) {
+            b[off + 4 * static_cast<size_t>(e) + u] = e < deg ? slot(s.nbr[s.ptr[i] + e]) : own;
+            for (int c = 0; c < nw; ++c) {
+              const double v = e < deg ? s.w[2 * static_cast<int64_t>(s.ptr[i] + e) + c] : 0.0;
+              const size_t at = o_w + ((static_cast<size_t>(e) * 4 + u) * nw + c) * 2;
+              put_f(at, v);
+              put_f(at + 1, v);
             }
           }
-        b.resize((b.size() + 3) & ~size_t(3), 0u);
-        ++n_union;
-        continue;
-      }
-      int D = 0;
-      for (int u = 0; u < cnt; ++u) {
-        const int64_t i = gs.first[gi] + u;
-        D = std::max(D, static_cast<int>(s.ptr[i + 1] - s.ptr[i]));
-      }
-      // a regular group: four nodes whose first R entries are their
-      // neighbours at row offsets -1, +1 (one-ring tables, R = 2) or -2, -1,
-      // +1, +2 (the Laplacian, R = 4), wherever that neighbour is a node
-      // of the group; the kernels then read those values from registers
-      const int R = s.scalar_w ? 4 : 2;
-      static const int kOffLap[4] = {-2, -1, 1, 2}, kOffRing[2] = {-1, 1};
-      const int* dr = s.scalar_w ? kOffLap : kOffRing;
-      bool reg = cnt == kGroup && D >= R;
-      for (int u = 0; u < cnt && reg; ++u) {
-        const int64_t i = gs.first[gi] + u;
-        const int32_t deg = s.ptr[i + 1] - s.ptr[i];
-        for (int r = 0; r < R && reg; ++r) {
-          const int t = u + dr[r];
-          if (t >= 0 && t < kGroup) reg = deg > r && s.nbr[s.ptr[i] + r] == gs.first[gi] + t;
         }
       }
-      const size_t off = b.size();
-      b[4 + 4 * k] = slot(static_cast<int32_t>(gs.first[gi]));
-      b[4 + 4 * k + 1] = static_cast<uint32_t>(off);
-      b[4 + 4 * k + 2] = static_cast<uint32_t>(D);
-      b[4 + 4 * k + 3] = static_cast<uint32_t>(cnt) | (reg ? 1u << 16 : 0u);
-      b.resize(off + static_cast<size_t>(D) * 4 * (1 + 2 * nw), 0u);
-      const size_t o_w = off + static_cast<size_t>(D) * 4;
-      for (int u = 0; u < 4; ++u) {
-        const int64_t i = gs.first[gi] + std::min(u, cnt - 1);
-        const uint32_t own = slot(static_cast<int32_t>(i));
-        const int32_t deg = u < cnt ? s.ptr[i + 1] - s.ptr[i] : 0;
-        for (int e = 0; e < D; ++e) {
-          b[off + 4 * static_cast<size_t>(e) + u] = e < deg ? slot(s.nbr[s.ptr[i] + e]) : own;
-          for (int c = 0; c < nw; ++c) {
-            const double v = e < deg ? s.w[2 * static_cast<int64_t>(s.ptr[i] + e) + c] : 0.0;
-            const size_t at = o_w + ((static_cast<size_t>(e) * 4 + u) * nw + c) * 2;
-            put_f(at, v);
-            put_f(at + 1, v);
-          }
-        }
-      }
+      if (bad[t]) continue;
+      b.resize((b.size() + 3) & ~size_t(3), 0u);
+      const size_t words = b.size();
+      h[0] = static_cast<int32_t>(gs.first[gl[0]]);
+      h[1] = ngt;
+      h[2] = nr;
+      h[3] = static_cast<int32_t>(ids.size());
+      h[5] = static_cast<int32_t>(4 * words);
+      max_slots = std::max(max_slots, static_cast<int32_t>(ids.size()));
+      max_blob = std::max(max_blob, static_cast<int32_t>(4 * words));
+      max_groups = std::max(max_groups, static_cast<int32_t>(ngt));
     }
-    b.resize((b.size() + 3) & ~size_t(3), 0u);
-    const size_t words = b.size();
-    h[0] = static_cast<int32_t>(gs.first[ga]);
-    h[1] = ngt;
-    h[2] = nr;
-    h[3] = static_cast<int32_t>(ids.size());
-    h[5] = static_cast<int32_t>(4 * words);
-    ts.first[t] = gs.first[ga];
-    max_slots = std::max(max_slots, static_cast<int32_t>(ids.size()));
-    max_blob = std::max(max_blob, static_cast<int32_t>(4 * words));
+    // a tile with too many copy runs: cut its unit into single rows and
+    // start again (once); other failures keep the per-node kernels
+    bool again = false;
+    for (int64_t t = 0; t < nt; ++t) {
+      if (!bad[t]) continue;
+      const int64_t u = spans[t].unit;
+      if (bad[t] == 2 || urows[u] == 1 || pass > 0) {
+        fits = false;
+        break;
+      }
+      for (int64_t r = urow0[u]; r < urow0[u] + urows[u]; ++r) single[r] = 1;
+      again = true;
+    }
+    if (!fits) return false;
+    if (again) continue;
+    size_t total = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+      ts.head[static_cast<size_t>(t * kTileHead) + 4] = static_cast<int32_t>(total / 4);
+      total += blobs[t].size();
+      if (total / 4 > static_cast<size_t>(INT32_MAX)) return false;
+    }
+    ts.blob.resize(total);
+    size_t pos = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+      std::copy(blobs[t].begin(), blobs[t].end(), ts.blob.begin() + static_cast<std::ptrdiff_t>(pos));
+      pos += blobs[t].size();
+    }
+    ts.first = ufirst;
+    ts.unit_tile = utile;
+    ts.ntiles = nt;
+    ts.rows_per_tile = rows;
+    ts.max_slots = max_slots;
+    ts.max_blob = max_blob;
+    ts.max_groups = max_groups;
+    ts.union_groups = n_union;
+    return true;
   }
-  if (!fits) return false;
-  ts.first[nt] = gs.first[ng];
-  size_t total = 0;
-  for (int64_t t = 0; t < nt; ++t) {
-    ts.head[static_cast<size_t>(t * kTileHead) + 4] = static_cast<int32_t>(total / 4);
-    total += blobs[t].size();
-    if (total / 4 > static_cast<size_t>(INT32_MAX)) return false;
-  }
-  ts.blob.resize(total);
-  size_t pos = 0;
-  for (int64_t t = 0; t < nt; ++t) {
-    std::copy(blobs[t].begin(), blobs[t].end(), ts.blob.begin() + static_cast<std::ptrdiff_t>(pos));
-    pos += blobs[t].size();
-  }
-  ts.max_slots = max_slots;
-  ts.max_blob = max_blob;
-  ts.union_groups = n_union;
-  return true;
 }
 
 bool build_edge_gather(const Mesh& m, const Dual& d, int op, EdgeGather& eg, bool averaged) {

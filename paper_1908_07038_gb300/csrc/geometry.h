@@ -139,8 +139,8 @@ struct GroupStencil {
 bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
 
 // Tile table of the shared-memory node-group kernels, built from a group
-// table.  Every grid row is cut into tiles of up to groups_per_tile
-// consecutive groups.  A tile lists the node rows its groups read (their own
+// table.  Tiles hold groups of one to three consecutive grid rows (see
+// build_tile_stencil).  A tile lists the node rows its groups read (their own
 // nodes and all their neighbours) as at most kTileRanges runs of
 // consecutive node ids; the kernel copies those runs into shared memory in
 // order, so the node with the s-th smallest id of the list sits in slot s.
@@ -148,8 +148,9 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
 //     blob offset (16-byte units), blob bytes, 0, 0, then per range
 //     (first node, count, first slot, 0).
 //   blob: per tile, 16-byte aligned: {groups, 0, first node, 0}; per group
-//     {slot of its first node, word offset of its data in the blob, D,
-//     count | regular << 16} (regular: four nodes whose first R entries, R
+//     {slot of its first node, word offset of its data in the blob, its
+//     first node, count | regular << 16 | union << 17 | D << 20}
+//     (regular: four nodes whose first R entries, R
 //     = 2 for one-ring tables and 4 for the Laplacian, are their row
 //     neighbours at offsets -1, +1, resp. -2, -1, +1, +2 wherever that
 //     neighbour belongs to the group, and D >= R); the B term
@@ -160,28 +161,41 @@ bool build_group_stencil(const Stencil& s, const Grid& g, GroupStencil& gs);
 //     0 past the row's end).
 // With unions, a group of four nodes whose union of rows matches its
 // operator's pattern (patterns.h) is stored in union form instead: its
-// header's word 3 has bit 17 set and D = U, and its data are the slots of
+// header's word 3 has bit 17 set and D (bits 20..27) = U, and its data are the slots of
 // the U union entries (padded to a multiple of four words), then, entry by
 // entry and for each node holding the entry in node order, its nw weights
 // as floats (padded likewise).  Only kernels that give each group one warp
 // read union groups.
 constexpr int kTileRanges = 16;
 constexpr int kTileHead = 8 + 4 * kTileRanges;
+constexpr int kMaxTileRows = 3;   // grid rows a tile may span
+constexpr int kMaxTileRow = 255;  // longest stencil row a per-node group may have (8 bits of its header)
 struct TileStencil {
   int nw = 1;
   int groups_per_tile = 7;
+  int rows_per_tile = 1;
   bool unions = false;
   int64_t union_groups = 0;       // groups stored in union form
+  int64_t ntiles = 0;
   std::vector<int32_t> head;      // [ntiles][kTileHead]
   std::vector<uint32_t> blob;     // 32-bit words
-  std::vector<int64_t> first;     // [ntiles + 1]: first node of every tile, then nnodes
+  // units: runs of whole grid rows whose tiles are consecutive; unit u
+  // holds nodes first[u] .. first[u + 1] - 1 and tiles unit_tile[u] ..
+  // unit_tile[u + 1] - 1 (a launch covers whole units)
+  std::vector<int64_t> first;     // [nunits + 1], then nnodes
+  std::vector<int32_t> unit_tile; // [nunits + 1], then ntiles
   int32_t max_slots = 0;          // most rows any tile stages
   int32_t max_blob = 0;           // largest tile blob (bytes)
+  int32_t max_groups = 0;         // most groups any tile holds
 };
-// Fails (false) when a tile needs more than kTileRanges runs (the caller
+// Tiles span rows_per_tile (1..kMaxTileRows) consecutive grid rows, with up
+// to groups_per_tile / rows_per_tile groups of each; a unit of rows one of
+// whose tiles would need more than kTileRanges copy runs is tiled row by
+// row instead.  Fails (false) when a single-row tile needs more than
+// kTileRanges runs or a stencil row is longer than kMaxTileRow (the caller
 // keeps the per-node kernels).
 bool build_tile_stencil(const GroupStencil& gs, const Stencil& s, int groups_per_tile, TileStencil& ts,
-                        bool unions = false);
+                        bool unions = false, int rows_per_tile = 1);
 
 // Regular (full) Gaussian grid F<N>: the 2N Gaussian latitudes of O<N>, each
 // with 4N longitudes j/(4N) turns.  A remapping target, and meshed by the

@@ -20,7 +20,7 @@ const void* tile_fn(StorageType st, const DevTiles& d, const TileLaunch& l) {
 
 // threads of a block: a consumer warp per part of every group of a tile
 // (4 / npw parts of npw nodes per group), then the producer warp
-int tile_threads(const DevTiles& d, const TileLaunch& l) { return 32 * ((4 / l.npw) * d.groups_per_tile + 1); }
+int tile_threads(const DevTiles& d, const TileLaunch& l) { return 32 * ((4 / l.npw) * d.max_groups + 1); }
 
 // The device error word of the tile kernels and its address per device
 // (looked up once, with the device current).
@@ -135,7 +135,7 @@ cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l,
   a.wait_hint_ns = l.wait_hint_ns;
   a.bd = l.bd;
   a.bd.nnz = d.blob_words;
-  a.max_groups = d.groups_per_tile;
+  a.max_groups = d.max_groups;
   e = error_word(&a.err);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};

@@ -606,7 +606,6 @@ __global__ void __launch_bounds__(NPW == 4 ? 384 : 512, 1) tile_kernel(const Til
     const uint32_t blob = sbase + static_cast<uint32_t>(NIN) * a.rows_bytes;
     const int4 ti = lds_i4(blob);
     int ngt = ti.x;
-    const int32_t tfirst = ti.z;
     // bounds-checked build: the stage's table capacity and row slots
     const uint32_t blob_cap = a.stage_bytes - static_cast<uint32_t>(NIN) * a.rows_bytes;
     const uint32_t slot_cap = a.rows_bytes / static_cast<uint32_t>(row_bytes);
@@ -626,14 +625,15 @@ __global__ void __launch_bounds__(NPW == 4 ? 384 : 512, 1) tile_kernel(const Til
       const int count = gh.w & 0xffff;
       const bool regular = ((gh.w >> 16) & 1) != 0;  // the same for the whole warp
       const bool uni = ((gh.w >> 17) & 1) != 0;      // a union group (one warp per group only)
-      const int32_t node0 = tfirst + 4 * g;
+      const int32_t node0 = gh.z;                    // the group's first node
+      const int D = (gh.w >> 20) & 0xff;             // entries: union length, or the longest row
       if (NPW != 4 && uni) {
         in_bounds(false, a.bd.err, BC_TILE_TABLE, t);
         continue;
       }
-      if (!in_bounds(count <= 4 && (!regular || count == 4) && (!uni || (count == 4 && gh.z == UP::U)) && gh.x >= 0 &&
-                         slot0 + static_cast<uint32_t>(count) <= slot_cap && gh.y >= 0 && gh.z >= 0 &&
-                         4ll * gh.y + (uni ? 4ll * union_words<UP, NW>() : (16ll + 32ll * NW) * gh.z) <=
+      if (!in_bounds(count <= 4 && (!regular || count == 4) && (!uni || (count == 4 && D == UP::U)) && gh.x >= 0 &&
+                         slot0 + static_cast<uint32_t>(count) <= slot_cap && gh.y >= 0 &&
+                         4ll * gh.y + (uni ? 4ll * union_words<UP, NW>() : (16ll + 32ll * NW) * D) <=
                              static_cast<long long>(blob_cap) &&
                          node0 >= a.bd.olo && static_cast<int64_t>(node0) + count <= a.bd.ohi,
                      a.bd.err, BC_TILE_TABLE, t))
@@ -666,7 +666,6 @@ __global__ void __launch_bounds__(NPW == 4 ? 384 : 512, 1) tile_kernel(const Til
         // the group: slots [4] (16 bytes), weight pairs [4][NW]; this part
         // reads its NPW of them.
         const uint32_t o_s = blob + 4u * static_cast<uint32_t>(gh.y);
-        const int D = gh.z;
         const uint32_t o_ws = o_s + 16u * static_cast<uint32_t>(D);
         auto slots = [&](int e, uint32_t (&sls)[NPW]) {
           const uint32_t at = o_s + 16u * static_cast<uint32_t>(e) + 4u * static_cast<uint32_t>(n0);

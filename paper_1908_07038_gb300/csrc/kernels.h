@@ -84,6 +84,7 @@ struct DevTiles {
   int32_t max_blob = 0;   // largest tile table (bytes)
   int64_t blob_words = 0; // 32-bit words of blob
   int groups_per_tile = 8;
+  int max_groups = 8;        // most groups any tile holds (sets the consumer warps)
   int nin = 1, nout = 1, nw = 1;
   bool has_b = false;
   bool unions = false;       // union groups present: one warp per group only

@@ -33,8 +33,10 @@ CANDIDATES = {
 # per-node kernels unless the node-group kernels are forced (the library's
 # rule; the Laplacian runs the node-group kernel at any level count)
 TILE_MIN_LEVELS = 96
-# node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp)
-TILE_CANDIDATES = ((11, 1, 4), (9, 1, 4), (8, 1, 4), (7, 1, 4), (7, 2, 4), (7, 1, 2))
+# node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp,
+# grid rows per tile)
+TILE_CANDIDATES = ((10, 1, 4, 2), (8, 1, 4, 2), (9, 1, 4, 3), (11, 1, 4, 1), (7, 1, 4, 1), (4, 2, 4, 1),
+                   (7, 1, 2, 1))
 _TORCH_DT = None
 
 
@@ -130,7 +132,8 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
             c = cache[key]
             fvm.set_launch(op, c["vec"], c["batch"], c["threads"], c["bps"], c.get("tile", 1), dtype=dtype)
             if c.get("kernel", "node") == "tile":
-                fvm.set_group(op, 1, c["tile_bps"], c["groups"], dtype=dtype, nodes_per_warp=c.get("npw", 4))
+                fvm.set_group(op, 1, c["tile_bps"], c["groups"], dtype=dtype, nodes_per_warp=c.get("npw", 4),
+                              rows_per_tile=c.get("rows", 1))
             else:
                 fvm.set_group(op, 0, dtype=dtype)
             best[op] = c
@@ -145,35 +148,37 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
                                                                 cand["bps"], cand["tile"]):
             fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
             ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
-            results.append((ms, "node", vec, batch, threads, bps, tile, 0, 0, 0))
+            results.append((ms, "node", vec, batch, threads, bps, tile, 0, 0, 0, 0))
             if verbose:
                 print("tune %-18s node vec=%d batch=%d threads=%d bps=%d tile=%d: %.4f ms" %
                       (op, vec, batch, threads, bps, tile, ms))
-        _, _, vec, batch, threads, bps, tile, _, _, _ = min(results)
+        _, _, vec, batch, threads, bps, tile, _, _, _, _ = min(results)
         fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
         # the tile kernel's shapes (where it applies to these fields: the
         # library runs it on fields of more than TILE_MIN_LEVELS levels)
         if (nlev > TILE_MIN_LEVELS or op == "laplacian") and fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
-            for groups, tbps, npw in TILE_CANDIDATES:
-                fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw)
+            for groups, tbps, npw, rows in TILE_CANDIDATES:
+                fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw, rows_per_tile=rows)
                 ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
-                results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps, npw))
+                results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps, npw, rows))
                 if verbose:
-                    print("tune %-18s tile groups=%d bps=%d npw=%d: %.4f ms" % (op, groups, tbps, npw, ms))
-        ms, kernel, vec, batch, threads, bps, tile, groups, tbps, npw = min(results)
+                    print("tune %-18s tile groups=%d bps=%d npw=%d rows=%d: %.4f ms" % (op, groups, tbps, npw, rows,
+                                                                                      ms))
+        ms, kernel, vec, batch, threads, bps, tile, groups, tbps, npw, rows = min(results)
         if kernel == "tile":
-            fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw)
+            fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw, rows_per_tile=rows)
         else:
             fvm.set_group(op, 0, dtype=dtype)
         # the launch shape the node-group kernel takes (blocks per SM may be
         # fewer than asked when shared memory or registers are short)
         shape = fvm.tile_info(op, nlev, ld, dtype) if kernel == "tile" else dict(blocks_per_sm=0, stages=0)
         best[op] = dict(kernel=kernel, vec=vec, batch=batch, threads=threads, bps=bps, tile=tile, groups=groups,
-                        tile_bps=tbps, npw=npw, tile_blocks=shape["blocks_per_sm"], tile_stages=shape["stages"], ms=ms,
+                        tile_bps=tbps, npw=npw, rows=rows, tile_blocks=shape["blocks_per_sm"],
+                        tile_stages=shape["stages"], ms=ms,
                         sweep=[dict(ms=r[0], kernel=r[1], vec=r[2], batch=r[3], threads=r[4], bps=r[5], tile=r[6],
-                                    groups=r[7], tile_bps=r[8], npw=r[9]) for r in results])
+                                    groups=r[7], tile_bps=r[8], npw=r[9], rows=r[10]) for r in results])
         cache[key] = {k: best[op][k] for k in ("kernel", "vec", "batch", "threads", "bps", "tile", "groups",
-                                              "tile_bps", "npw", "ms")}
+                                              "tile_bps", "npw", "rows", "ms")}
     _store_cache(cache)
     return best
 

@@ -32,8 +32,8 @@ def torch():
 
 NOUT = {"gradient": 2, "divergence_adjoint": 2, "vector_gradient": 4, "curl_adjoint": 2}
 # the library's default groups per tile, per operator and storage (F32, F64, BF16)
-DEFAULT_GROUPS = {op: (11, 7, 11) if op in ("gradient", "divergence_adjoint", "vector_gradient", "curl_adjoint")
-                  else (4 if op == "laplacian" else 7, 7, 11) for op in OPS}
+DEFAULT_GROUPS = {op: (10, 7, 11) for op in OPS}
+DEFAULT_ROWS = {op: (2, 1, 1) for op in OPS}
 
 
 def _call(fvm, op, x, y, nlev, out=None):
@@ -71,22 +71,26 @@ def _compare(torch, fvm, x, y, nlev, groups=(11, 7, 3, 1), ops=OPS, npws=(4, 2))
     node and compare trivially."""
     from paper_1908_07038_gb300 import capi
     dt = {torch.float32: 0, torch.float64: 1, torch.bfloat16: 2}[x.dtype]
+    shapes = [(w, u, 1) for w in npws for u in ((1, 0) if w == 4 else (1,))]
+    if 4 in npws:
+        shapes += [(4, 1, 2), (4, 0, 2), (4, 1, 3)]  # tiles spanning two and three grid rows
     for op in ops:
         n = NOUT.get(op, 1)
         fvm.set_group(op, enable=0, dtype=dt)
         ref = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
         for gpt in groups:
-            for npw, unions in [(w, u) for w in npws for u in ((1, 0) if w == 4 else (1,))]:
+            for npw, unions, rows in shapes:
                 capi.atlas_debug_tile_unions(unions)
                 try:
-                    fvm.set_group(op, enable=2, groups_per_tile=gpt, nodes_per_warp=npw, dtype=dt)
+                    fvm.set_group(op, enable=2, groups_per_tile=gpt, nodes_per_warp=npw, dtype=dt, rows_per_tile=rows)
                     got = _call(fvm, op, x, y, nlev, _filled(torch, x, n))
                     torch.cuda.synchronize()
                 finally:
                     capi.atlas_debug_tile_unions(1)
                 for a, b in zip(got, ref):
-                    assert torch.equal(a, b), (op, gpt, npw, unions)
-        fvm.set_group(op, enable=1, groups_per_tile=DEFAULT_GROUPS[op][dt], nodes_per_warp=4, dtype=dt)
+                    assert torch.equal(a, b), (op, gpt, npw, unions, rows)
+        fvm.set_group(op, enable=1, groups_per_tile=DEFAULT_GROUPS[op][dt], nodes_per_warp=4, dtype=dt,
+                      rows_per_tile=DEFAULT_ROWS[op][dt])
 
 
 def _fields(torch, V, ld, dt, seed):

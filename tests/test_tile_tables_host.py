@@ -52,12 +52,13 @@ def _f32(words):
     return np.asarray(words, np.uint32).view(np.float32)
 
 
-def _decode(fvm, op, groups_per_tile, unions):
+def _decode(fvm, op, groups_per_tile, unions, rows_per_tile=1):
     """Per node: the (neighbour, weights) terms the kernels apply, in order;
-    and the number of union groups."""
+    the number of union groups and of tiles.  Also checks the units: runs
+    of whole grid rows whose consecutive tiles hold exactly their nodes."""
     st = fvm.stencil_table(op)
-    tt = fvm.tile_table(op, groups_per_tile, unions)
-    head, blob = tt["head"], tt["blob"]
+    tt = fvm.tile_table(op, groups_per_tile, unions, rows_per_tile)
+    head, blob, uf, ut = tt["head"], tt["blob"], tt["unit_first"], tt["unit_tile"]
     nw = 1 if op == "laplacian" else 2
     ptr, nbr = st["ptr"], st["nbr"]
     pats = _patterns()
@@ -66,6 +67,12 @@ def _decode(fvm, op, groups_per_tile, unions):
     terms = [None] * V
     nuni = 0
     covered = 0
+    off = np.concatenate([[0], np.cumsum(fvm.grid.arrays()["pl"])])
+    assert uf[0] == 0 and uf[-1] == V and np.all(np.diff(uf) > 0) and np.all(np.isin(uf, off))
+    assert ut[0] == 0 and ut[-1] == head.shape[0] and np.all(np.diff(ut) > 0)
+    unit_of_tile = np.repeat(np.arange(len(ut) - 1), np.diff(ut))
+    rows_of_unit = np.diff(np.searchsorted(off, uf))
+    assert np.all(rows_of_unit <= rows_per_tile)
     for t in range(head.shape[0]):
         h = head[t]
         first, ngt, nr, nslots, boff, bbytes = (int(x) for x in h[:6])
@@ -75,12 +82,14 @@ def _decode(fvm, op, groups_per_tile, unions):
             ids[rs:rs + rc] = np.arange(rf, rf + rc)
         assert np.all(ids >= 0) and np.all(np.diff(ids) > 0)  # slot s: the s-th smallest id
         b = blob[4 * boff: 4 * boff + bbytes // 4]
-        assert int(b[0]) == ngt and int(b[2]) == first
-        node0 = first
+        assert int(b[0]) == ngt and int(b[2]) == first and 1 <= ngt <= groups_per_tile
+        u_t = unit_of_tile[t]
         for k in range(ngt):
-            slot0, off, D, flags = (int(x) for x in b[4 + 4 * k: 8 + 4 * k])
-            cnt, regular, uni = flags & 0xFFFF, (flags >> 16) & 1, (flags >> 17) & 1
-            assert ids[slot0] == node0
+            slot0, off, node0, flags = (int(x) for x in b[4 + 4 * k: 8 + 4 * k])
+            cnt, regular, uni, D = flags & 0xFFFF, (flags >> 16) & 1, (flags >> 17) & 1, (flags >> 20) & 0xFF
+            assert flags >> 28 == 0 and (flags >> 18) & 3 == 0
+            assert ids[slot0] == node0 and uf[u_t] <= node0 and node0 + cnt <= uf[u_t + 1]
+            assert terms[node0] is None  # every node in one group of one tile
             nodes = [node0 + u for u in range(cnt)]
             rows = [list(nbr[ptr[i]:ptr[i + 1]]) for i in nodes]
             got = [[] for _ in nodes]
@@ -124,19 +133,19 @@ def _decode(fvm, op, groups_per_tile, unions):
             for u, i in enumerate(nodes):
                 terms[i] = got[u]
             covered += cnt
-            node0 += cnt
     assert covered == V
     return terms, nuni, head.shape[0]
 
 
 @pytest.mark.parametrize("name", ["O2", "O24", "F6", "lambert13x9"])
 @pytest.mark.parametrize("op", OPS)
-@pytest.mark.parametrize("unions", [True, False])
-def test_tile_tables_give_every_node_its_row(fvms, name, op, unions):
+@pytest.mark.parametrize("unions,rows,groups", [(True, 1, 7), (False, 1, 7), (True, 2, 8), (False, 2, 4),
+                                                (True, 3, 6)])
+def test_tile_tables_give_every_node_its_row(fvms, name, op, unions, rows, groups):
     fvm = fvms[name]
     st = fvm.stencil_table(op)
     nw = 1 if op == "laplacian" else 2
-    terms, nuni, _ = _decode(fvm, op, 7, unions)
+    terms, nuni, _ = _decode(fvm, op, groups, unions, rows)
     ptr, nbr, w = st["ptr"], st["nbr"], st["w"]
     for i in range(fvm.nnodes):
         want = [(int(nbr[q]), tuple(np.float32(w[q, c]) for c in range(nw))) for q in range(ptr[i], ptr[i + 1])]
@@ -156,9 +165,21 @@ def test_union_groups_cover_octahedral_interiors(fvms, op):
     assert frac["O64"] > frac["O24"] and frac["O64"] > (0.8 if op == "laplacian" else 0.85), frac
 
 
+def test_multi_row_tiles_stage_fewer_rows(fvms):
+    # a tile spanning two grid rows stages the rows above and below once for
+    # both: fewer staged rows per node than tiles of one row
+    def per_node(op, groups, rows):
+        tt = fvms["O64"].tile_table(op, groups, True, rows)
+        return tt["head"][:, 3].sum() / fvms["O64"].nnodes
+    assert per_node("laplacian", 8, 2) < 0.75 * per_node("laplacian", 4, 1)
+    assert per_node("divergence", 8, 2) < 0.8 * per_node("divergence", 7, 1)
+
+
 def test_tile_table_arguments(fvms):
     from paper_1908_07038_gb300.capi import AtlasError
     with pytest.raises(AtlasError):
         fvms["O2"].tile_table("gradient", 12)
     with pytest.raises(AtlasError):
         fvms["O2"].tile_table("gradient", 0)
+    with pytest.raises(AtlasError):
+        fvms["O2"].tile_table("gradient", 4, True, 4)

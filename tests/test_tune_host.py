@@ -97,13 +97,14 @@ def test_tune_fvm_picks_and_installs_the_fastest_candidate(product, monkeypatch,
     best = tune.tune_fvm(fvm, atlas.ATLAS_F32, 137, 140, ("gradient",), fields=fields, reps=1)
     b = best["gradient"]
     last = tune.TILE_CANDIDATES[-1]  # timed last, hence fastest
-    assert b["kernel"] == "tile" and (b["groups"], b["tile_bps"], b["npw"]) == last
+    assert b["kernel"] == "tile" and (b["groups"], b["tile_bps"], b["npw"], b["rows"]) == last
     assert (b["tile_blocks"], b["tile_stages"]) == (1, 3)
     n_node = 1
     for v in tune.CANDIDATES[atlas.ATLAS_F32].values():
         n_node *= len(v)
     assert len(b["sweep"]) == n_node + len(tune.TILE_CANDIDATES)
     assert fvm.calls[-1][0] == "group" and fvm.calls[-1][2].get("nodes_per_warp") == last[2]
+    assert fvm.calls[-1][2].get("rows_per_tile") == last[3]
     # cached: the second run times nothing
     monkeypatch.setattr(tune, "time_call", lambda *a, **k: pytest.fail("timed a cached shape"))
     again = tune.tune_fvm(fvm, atlas.ATLAS_F32, 137, 140, ("gradient",), fields=fields, reps=1)
