@@ -321,10 +321,10 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* of whole tiles (whole grids, partitions of whole rows); elsewhere the  */
 /* per-node kernels run, with bitwise identical results.                  */
 /* enable: 1 (default) uses them for the FP32 and BF16 operators, the     */
-/* one-ring operators only on fields of more than 96 levels (their table  */
-/* work per tile does not shrink with the levels; below that the per-node */
-/* kernels measured as fast or faster); 2 uses them wherever they apply;  */
-/* 0 per-node kernels only; -1 keeps.                                      */
+/* one-ring operators only on fields of more than 80 levels (FP32) or 96  */
+/* (BF16): their table work per tile does not shrink with the levels, and */
+/* below that the per-node kernels measured as fast or faster; 2 uses     */
+/* them wherever they apply; 0 per-node kernels only; -1 keeps.            */
 /* blocks_per_sm: 1 or 2 blocks per SM at most (fewer when shared memory  */
 /* or registers are short; 0 keeps; default 1: one block holding up to    */
 /* four stages measured faster than two blocks of two).                   */

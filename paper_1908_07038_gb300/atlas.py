@@ -293,8 +293,9 @@ class Fvm:
     def set_group(self, op, enable=-1, blocks_per_sm=0, groups_per_tile=0, dtype=-1, nodes_per_warp=0,
                   rows_per_tile=0):
         """Use the shared-memory node-group kernels for one operator by
-        default (enable 1: one-ring operators on fields of more than 96
-        levels, the Laplacian on any), on every field they apply to (2), or
+        default (enable 1: one-ring operators on fields of more than 80
+        levels for FP32 and 96 for BF16, the Laplacian on any), on every
+        field they apply to (2), or
         the per-node kernels only (0; -1 keeps),
         with at most
         blocks_per_sm blocks per SM (1 or 2; 0 keeps), groups_per_tile

@@ -173,17 +173,19 @@ struct LaunchCfg {
   int threads = 128;
   int blocks_per_sm = 0;  // 0 = occupancy limit
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
-  int group = 1;          // node-group kernel: 1 where it applies and pays (kTileMinLevels), 2 wherever it applies, 0 never
+  int group = 1;          // node-group kernel: 1 where it applies and pays (tile_min_levels), 2 wherever it applies, 0 never
   int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
   int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..11)
   int tile_npw = 4;       // node-group kernel: nodes per consumer warp (4: a warp per group; 2: two per group)
   int tile_rows = 1;      // node-group kernel: grid rows a tile spans (1..3)
   // fields of this many levels or fewer run on the per-node kernel unless
   // the node-group kernel is forced (group 2): its table work per tile does
-  // not shrink with the levels.  Measured on O640 (FP32): a one-level
-  // gradient 0.37 ms in the node-group kernel; 60 levels 0.43 ms against
-  // 0.26 per node; 91 levels 0.51 against 0.49.  The Laplacian's per-node
-  // kernel is slower at any level count, so its threshold is 0.
+  // not shrink with the levels.  Measured on O640 with union groups (node
+  // group against per node, ms): FP32 gradient 30 levels 0.31 / 0.15, 60
+  // levels 0.34 / 0.26, 91 levels 0.38 / 0.39; FP32 divergence 91 levels
+  // 0.42 / 0.48; BF16 gradient 91 levels 0.39 / 0.34.  So 80 for FP32, 96
+  // for BF16.  The Laplacian's per-node kernel is slower at any level
+  // count, so its threshold is 0.
   int tile_min_levels = 96;
 };
 
@@ -198,6 +200,7 @@ LaunchCfg default_launch(int op, int dt) {
   c.batch = 3;
   c.threads = 256;
   if (dt == ATLAS_F32) {
+    if (op != atlasgb::OP_LAP) c.tile_min_levels = 80;
     // the node-group kernels: tiles of ten groups spanning two grid rows
     // (five groups of each), so the rows above and below are staged once
     // for both; one block per SM, union groups.  O1280 x 137: gradient 1.87

@@ -32,7 +32,7 @@ CANDIDATES = {
 # fields of this many levels or fewer run the one-ring operators on the
 # per-node kernels unless the node-group kernels are forced (the library's
 # rule; the Laplacian runs the node-group kernel at any level count)
-TILE_MIN_LEVELS = 96
+TILE_MIN_LEVELS = {ATLAS_F32: 80, ATLAS_BF16: 96}
 # node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp,
 # grid rows per tile)
 TILE_CANDIDATES = ((10, 1, 4, 2), (8, 1, 4, 2), (9, 1, 4, 3), (11, 1, 4, 1), (7, 1, 4, 1), (4, 2, 4, 1),
@@ -156,7 +156,8 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         fvm.set_launch(op, vec, batch, threads, bps, tile, dtype=dtype)
         # the tile kernel's shapes (where it applies to these fields: the
         # library runs it on fields of more than TILE_MIN_LEVELS levels)
-        if (nlev > TILE_MIN_LEVELS or op == "laplacian") and fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
+        if (nlev > TILE_MIN_LEVELS.get(dtype, 96) or op == "laplacian") and \
+                fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
             for groups, tbps, npw, rows in TILE_CANDIDATES:
                 fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw, rows_per_tile=rows)
                 ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
