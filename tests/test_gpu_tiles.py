@@ -126,6 +126,10 @@ def test_tiles_on_f_and_regional_grids(torch, product):
     for fvm in grids:
         x, y = _fields(torch, fvm.nnodes, 140, torch.float32, 3)
         _compare(torch, fvm, x, y, 137, groups=(7, 2))
+        # away from their edges these grids have the octahedral interior's
+        # neighbourhood: the default tables hold union groups for them too
+        for op in ("gradient", "divergence", "laplacian"):
+            assert fvm.tile_union_groups(op) > 0, op
 
 
 def test_tiles_o1280_benchmark_layout(torch, pfvm):
