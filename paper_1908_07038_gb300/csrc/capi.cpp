@@ -175,7 +175,7 @@ struct LaunchCfg {
   int tile_passes = 1;    // block tile = tile_passes * threads items (1 = grid-stride loop)
   int group = 1;          // node-group kernel: 1 where it applies and pays (tile_min_levels), 2 wherever it applies, 0 never
   int tile_bps = 1;       // node-group kernel: blocks per SM at most (1 or 2; fewer when shared memory is short)
-  int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..11)
+  int tile_groups = 7;    // node-group kernel: groups of four nodes per tile (1..kTileMaxGroups)
   int tile_npw = 4;       // node-group kernel: nodes per consumer warp (4: a warp per group; 2: two per group)
   int tile_rows = 1;      // node-group kernel: grid rows a tile spans (1..3)
   // fields of this many levels or fewer run on the per-node kernel unless
@@ -213,6 +213,10 @@ LaunchCfg default_launch(int op, int dt) {
     if (op == atlasgb::OP_LAP) {
       c.batch = 6;
       c.threads = 512;
+      // the Laplacian's kernel needs fewer than 128 registers, so sixteen
+      // warps fit and its tiles take twelve groups (six of each row):
+      // 2.10 ms against 2.36 with ten
+      c.tile_groups = 12;
     }
     if (op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD) c.threads = 128;
   } else if (dt == ATLAS_BF16) {
@@ -220,8 +224,10 @@ LaunchCfg default_launch(int op, int dt) {
     if (op == atlasgb::OP_LAP) c.tile_passes = 64;
     // bfloat16: tiles of eleven groups (their stages fit at half the
     // bytes), union groups; O1280 x 137: gradient 1.79 ms against 2.02 per
-    // node, divergence 2.17 against 2.38, Laplacian 2.39 against 4.46
-    c.tile_groups = 11;
+    // node, divergence 2.17 against 2.38.  The Laplacian takes fifteen
+    // groups (sixteen warps under 128 registers): 2.15 ms against 2.43
+    // with eleven and 4.38 per node
+    c.tile_groups = op == atlasgb::OP_LAP ? 15 : 11;
   } else {  // F64: bound by the FP64 pipe
     c.threads = 128;
   }
@@ -688,7 +694,8 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
     return bounds_after(stream, "stencil kernel");
   };
   const int npw = gt.dev.unions ? 4 : c.tile_npw;  // as run_tiles launches
-  const bool tiles_fit = gt.ok && 32 * ((4 / npw) * gt.dev.max_groups + 1) <= atlasgb::tile_max_threads(npw);
+  const bool tiles_fit =
+      gt.ok && 32 * ((4 / npw) * gt.dev.max_groups + 1) <= atlasgb::tile_max_threads(npw, gt.dev.nin, gt.dev.nout);
   if (gt.ok && tiles_wanted && tiles_fit && (ld * es) % 16 == 0 &&
       atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned
@@ -1205,7 +1212,8 @@ int atlas_fvm_set_group(atlas_fvm_t h, int op, int dtype, int enable, int blocks
   if (dtype != -1 && !valid_dtype(dtype)) return fail(ATLAS_EDTYPE, "dtype must be -1 (all) or an atlas_dtype");
   if (enable < -1 || enable > 2) return fail(ATLAS_EINVAL, "enable must be -1, 0, 1 or 2");
   if (blocks_per_sm < 0 || blocks_per_sm > 2) return fail(ATLAS_EINVAL, "blocks_per_sm must be 0, 1 or 2");
-  if (groups_per_tile < 0 || groups_per_tile > 11) return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, 11]");
+  if (groups_per_tile < 0 || groups_per_tile > atlasgb::kTileMaxGroups)
+    return fail(ATLAS_EINVAL, "groups_per_tile must be in [0, %d]", atlasgb::kTileMaxGroups);
   if (nodes_per_warp != 0 && nodes_per_warp != 2 && nodes_per_warp != 4)
     return fail(ATLAS_EINVAL, "nodes_per_warp must be 0, 2 or 4");
   if (rows_per_tile < 0 || rows_per_tile > atlasgb::kMaxTileRows)
@@ -1350,7 +1358,8 @@ int atlas_fvm_tile_table(atlas_fvm_t h, int op, int groups_per_tile, int rows_pe
   atlas_fvm_s* f = get_fvm(h);
   if (!f) return fail(ATLAS_ESTATE, "invalid or destroyed fvm handle");
   if (op < 0 || op >= atlasgb::OP_COUNT) return fail(ATLAS_EINVAL, "unknown operator %d", op);
-  if (groups_per_tile < 1 || groups_per_tile > 11) return fail(ATLAS_EINVAL, "groups_per_tile must be in [1, 11]");
+  if (groups_per_tile < 1 || groups_per_tile > atlasgb::kTileMaxGroups)
+    return fail(ATLAS_EINVAL, "groups_per_tile must be in [1, %d]", atlasgb::kTileMaxGroups);
   if (rows_per_tile < 1 || rows_per_tile > atlasgb::kMaxTileRows)
     return fail(ATLAS_EINVAL, "rows_per_tile must be in [1, %d]", atlasgb::kMaxTileRows);
   atlasgb::Stencil s;

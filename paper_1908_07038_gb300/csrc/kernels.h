@@ -111,7 +111,17 @@ struct TileLaunch {
 // Valid (va, vb) pairs: (1,0) (2,0) (2,1) (4,0) (4,1) (4,2).
 // Threads a node-group block may have (the kernels' launch bound): 384 with
 // four nodes per warp (up to 11 groups per tile), 512 with two (up to 7).
-inline int tile_max_threads(int npw) { return npw == 4 ? 384 : 512; }
+// Launch bound of the node-group kernels.  Each of an SM's four schedulers
+// holds a quarter of the register file, so 12 warps (three per scheduler)
+// can have up to 168 registers and 16 warps up to 128.  With one warp per
+// group: 384 threads (eleven groups and the producer) for the one-ring
+// shapes, which need about 150 registers, and 512 (fifteen groups) for the
+// one-input one-output Laplacian, which needs fewer than 128.  With two
+// warps per group, 512.
+inline int tile_max_threads(int npw, int nin, int nout) {
+  return npw == 4 ? (nin == 1 && nout == 1 ? 512 : 384) : 512;
+}
+constexpr int kTileMaxGroups = 15;  // groups per tile the tables may hold
 cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream);
 // Dynamic shared memory one block needs (two stages), or 0 above the limit.
 size_t tile_smem_bytes(const DevTiles& d, int64_t ld, int elem_size);

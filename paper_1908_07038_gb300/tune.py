@@ -35,9 +35,17 @@ CANDIDATES = {
 TILE_MIN_LEVELS = {ATLAS_F32: 80, ATLAS_BF16: 96}
 # node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp,
 # grid rows per tile)
-TILE_CANDIDATES = ((10, 1, 4, 2), (8, 1, 4, 2), (9, 1, 4, 3), (11, 1, 4, 1), (7, 1, 4, 1), (4, 2, 4, 1),
-                   (7, 1, 2, 1))
+# (more than eleven groups: the Laplacian only; other operators then run
+# per node)
+TILE_CANDIDATES = ((10, 1, 4, 2), (12, 1, 4, 2), (15, 1, 4, 1), (8, 1, 4, 2), (9, 1, 4, 3), (11, 1, 4, 1),
+                   (7, 1, 4, 1), (4, 2, 4, 1), (7, 1, 2, 1))
 _TORCH_DT = None
+
+
+def tile_candidates(op):
+    """The node-group candidates that apply to op: tiles of more than eleven
+    groups only for the Laplacian, whose kernel has the registers for them."""
+    return tuple(c for c in TILE_CANDIDATES if c[0] <= 11 or op == "laplacian")
 
 
 def _torch_dtype(code):
@@ -158,7 +166,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         # library runs it on fields of more than TILE_MIN_LEVELS levels)
         if (nlev > TILE_MIN_LEVELS.get(dtype, 96) or op == "laplacian") and \
                 fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
-            for groups, tbps, npw, rows in TILE_CANDIDATES:
+            for groups, tbps, npw, rows in tile_candidates(op):
                 fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw, rows_per_tile=rows)
                 ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
                 results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps, npw, rows))

@@ -68,9 +68,9 @@ def test_error_codes_on_bad_arguments(product):
     capi.atlas_fvm_set_launch(h, 0, -1, 0, 0, 0, 0, 16)
     capi.atlas_fvm_set_launch(h, 4, 1, 0, 3, 128, 0, 1)
     # node-group kernel settings: enable -1..2, blocks per SM 0..2, groups
-    # per tile 0..11, nodes per warp 0, 2 or 4, rows per tile 0..3; a bad
+    # per tile 0..15, nodes per warp 0, 2 or 4, rows per tile 0..3; a bad
     # one changes nothing
-    for args in ((0, -1, 3, 0, 0, 0, 0), (0, -1, -2, 0, 0, 0, 0), (0, -1, 1, 3, 0, 0, 0), (0, -1, 1, 0, 12, 0, 0),
+    for args in ((0, -1, 3, 0, 0, 0, 0), (0, -1, -2, 0, 0, 0, 0), (0, -1, 1, 3, 0, 0, 0), (0, -1, 1, 0, 16, 0, 0),
                  (0, -1, 1, 0, 0, 3, 0), (0, -1, 1, 0, 0, 1, 0), (8, -1, 1, 0, 0, 0, 0), (0, -1, 1, 0, 0, 0, 4),
                  (0, -1, 1, 0, 0, 0, -1)):
         with pytest.raises(E) as ei:

@@ -178,7 +178,7 @@ def test_multi_row_tiles_stage_fewer_rows(fvms):
 def test_tile_table_arguments(fvms):
     from paper_1908_07038_gb300.capi import AtlasError
     with pytest.raises(AtlasError):
-        fvms["O2"].tile_table("gradient", 12)
+        fvms["O2"].tile_table("gradient", 16)
     with pytest.raises(AtlasError):
         fvms["O2"].tile_table("gradient", 0)
     with pytest.raises(AtlasError):

@@ -102,7 +102,8 @@ def test_tune_fvm_picks_and_installs_the_fastest_candidate(product, monkeypatch,
     n_node = 1
     for v in tune.CANDIDATES[atlas.ATLAS_F32].values():
         n_node *= len(v)
-    assert len(b["sweep"]) == n_node + len(tune.TILE_CANDIDATES)
+    assert len(b["sweep"]) == n_node + len(tune.tile_candidates("gradient"))
+    assert len(tune.tile_candidates("gradient")) < len(tune.tile_candidates("laplacian"))
     assert fvm.calls[-1][0] == "group" and fvm.calls[-1][2].get("nodes_per_warp") == last[2]
     assert fvm.calls[-1][2].get("rows_per_tile") == last[3]
     # cached: the second run times nothing
