@@ -226,8 +226,11 @@ LaunchCfg default_launch(int op, int dt) {
     // bytes), union groups; O1280 x 137: gradient 1.79 ms against 2.02 per
     // node, divergence 2.17 against 2.38.  The Laplacian takes fifteen
     // groups (sixteen warps under 128 registers): 2.15 ms against 2.43
-    // with eleven and 4.38 per node
-    c.tile_groups = op == atlasgb::OP_LAP ? 15 : 11;
+    // with eleven and 4.38 per node.  The one-input operators' kernels fit
+    // in 128 registers in bfloat16 too and take fifteen groups as well
+    const bool one_in = op == atlasgb::OP_GRAD || op == atlasgb::OP_DIV_ADJ || op == atlasgb::OP_VGRAD ||
+                        op == atlasgb::OP_CURL_ADJ;
+    c.tile_groups = (op == atlasgb::OP_LAP || one_in) ? 15 : 11;
   } else {  // F64: bound by the FP64 pipe
     c.threads = 128;
   }
@@ -695,7 +698,8 @@ int run_stencil_range(atlas_fvm_s* f, int op, const void* in0, const void* in1, 
   };
   const int npw = gt.dev.unions ? 4 : c.tile_npw;  // as run_tiles launches
   const bool tiles_fit =
-      gt.ok && 32 * ((4 / npw) * gt.dev.max_groups + 1) <= atlasgb::tile_max_threads(npw, gt.dev.nin, gt.dev.nout);
+      gt.ok && 32 * ((4 / npw) * gt.dev.max_groups + 1) <=
+                   atlasgb::tile_max_threads(npw, gt.dev.nin, gt.dev.nout, static_cast<int>(es));
   if (gt.ok && tiles_wanted && tiles_fit && (ld * es) % 16 == 0 &&
       atlasgb::tile_smem_bytes(gt.dev, ld, static_cast<int>(es)) > 0) {
     // the shared-memory node-group kernel: TMA copies need 16-byte aligned

@@ -104,7 +104,7 @@ cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l,
   if (!fn) return cudaErrorInvalidValue;
   if (l.ntiles <= 0 || l.nlev <= 0) return cudaSuccess;
   const int threads = tile_threads(d, l);  // within the kernels' launch bound
-  if (threads > tile_max_threads(l.npw, d.nin, d.nout)) return cudaErrorInvalidValue;
+  if (threads > tile_max_threads(l.npw, d.nin, d.nout, st == ST_BF16 ? 2 : 4)) return cudaErrorInvalidValue;
   int bps = 0, ns = 0;
   size_t smem = 0;
   cudaError_t e = tile_shape(st, d, l, &bps, &ns, &smem);

@@ -472,7 +472,9 @@ constexpr int kMaxStages = 4;
 // t0 + blockIdx.x, + gridDim.x, ...; the block's k-th tile goes to stage
 // k % nstages, the (k / nstages)-th use of that stage.
 template <typename S, int NIN, int NOUT, bool HAS_B, int NW, int VA, int VB, int BATCH, int NPW>
-__global__ void __launch_bounds__(NPW == 4 ? (NIN == 1 && NOUT == 1 ? 512 : 384) : 512, 1)
+__global__ void __launch_bounds__(NPW == 4 ? ((NIN == 1 && NOUT == 1) || (NIN == 1 && sizeof(S) == 2) ? 512 : 384)
+                                            : 512,
+                                  1)
     tile_kernel(const TileArgs a) {
   constexpr int LB = 32 * (VA + VB);  // levels per level block
   constexpr uint32_t ES = sizeof(S);

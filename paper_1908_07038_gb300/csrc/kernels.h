@@ -116,10 +116,10 @@ struct TileLaunch {
 // can have up to 168 registers and 16 warps up to 128.  With one warp per
 // group: 384 threads (eleven groups and the producer) for the one-ring
 // shapes, which need about 150 registers, and 512 (fifteen groups) for the
-// one-input one-output Laplacian, which needs fewer than 128.  With two
-// warps per group, 512.
-inline int tile_max_threads(int npw, int nin, int nout) {
-  return npw == 4 ? (nin == 1 && nout == 1 ? 512 : 384) : 512;
+// one-input one-output Laplacian and the one-input bfloat16 shapes, which
+// need no more than 128.  With two warps per group, 512.
+inline int tile_max_threads(int npw, int nin, int nout, int elem_size) {
+  return npw == 4 ? ((nin == 1 && nout == 1) || (nin == 1 && elem_size == 2) ? 512 : 384) : 512;
 }
 constexpr int kTileMaxGroups = 15;  // groups per tile the tables may hold
 cudaError_t launch_tiles(StorageType st, const DevTiles& d, const TileLaunch& l, cudaStream_t stream);

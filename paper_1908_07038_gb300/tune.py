@@ -33,6 +33,7 @@ CANDIDATES = {
 # per-node kernels unless the node-group kernels are forced (the library's
 # rule; the Laplacian runs the node-group kernel at any level count)
 TILE_MIN_LEVELS = {ATLAS_F32: 80, ATLAS_BF16: 96}
+ONE_INPUT = ("gradient", "divergence_adjoint", "vector_gradient", "curl_adjoint")
 # node-group (tile) kernel candidates: (groups per tile, blocks per SM, nodes per consumer warp,
 # grid rows per tile)
 # (more than eleven groups: the Laplacian only; other operators then run
@@ -42,10 +43,12 @@ TILE_CANDIDATES = ((10, 1, 4, 2), (12, 1, 4, 2), (15, 1, 4, 1), (8, 1, 4, 2), (9
 _TORCH_DT = None
 
 
-def tile_candidates(op):
+def tile_candidates(op, dtype=ATLAS_F32):
     """The node-group candidates that apply to op: tiles of more than eleven
-    groups only for the Laplacian, whose kernel has the registers for them."""
-    return tuple(c for c in TILE_CANDIDATES if c[0] <= 11 or op == "laplacian")
+    groups only where the kernel has the registers for them (the Laplacian;
+    the one-input operators in bfloat16)."""
+    big = op == "laplacian" or (dtype == ATLAS_BF16 and op in ONE_INPUT)
+    return tuple(c for c in TILE_CANDIDATES if c[0] <= 11 or big)
 
 
 def _torch_dtype(code):
@@ -166,7 +169,7 @@ def tune_fvm(fvm, dtype=ATLAS_F32, nlev=137, ld=None, ops=tuple(atlas.OPS), fiel
         # library runs it on fields of more than TILE_MIN_LEVELS levels)
         if (nlev > TILE_MIN_LEVELS.get(dtype, 96) or op == "laplacian") and \
                 fvm.tile_info(op, nlev, ld, dtype)["stages"] > 0:
-            for groups, tbps, npw, rows in tile_candidates(op):
+            for groups, tbps, npw, rows in tile_candidates(op, dtype):
                 fvm.set_group(op, 1, tbps, groups, dtype=dtype, nodes_per_warp=npw, rows_per_tile=rows)
                 ms = time_call(lambda: _call(fvm, op, ins, outs, nlev), reps=reps)
                 results.append((ms, "tile", vec, batch, threads, bps, tile, groups, tbps, npw, rows))

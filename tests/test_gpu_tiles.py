@@ -32,7 +32,9 @@ def torch():
 
 NOUT = {"gradient": 2, "divergence_adjoint": 2, "vector_gradient": 4, "curl_adjoint": 2}
 # the library's default groups per tile, per operator and storage (F32, F64, BF16)
-DEFAULT_GROUPS = {op: (12, 7, 15) if op == "laplacian" else (10, 7, 11) for op in OPS}
+DEFAULT_GROUPS = {op: (12, 7, 15) if op == "laplacian" else
+                  (10, 7, 15) if op in ("gradient", "divergence_adjoint", "vector_gradient", "curl_adjoint") else
+                  (10, 7, 11) for op in OPS}
 DEFAULT_ROWS = {op: (2, 1, 1) for op in OPS}
 
 
