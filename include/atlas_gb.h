@@ -328,10 +328,12 @@ int atlas_fvm_set_launch(atlas_fvm_t f, int op, int dtype, int vec, int batch, i
 /* blocks_per_sm: 1 or 2 blocks per SM at most (fewer when shared memory  */
 /* or registers are short; 0 keeps; default 1: one block holding up to    */
 /* four stages measured faster than two blocks of two).                   */
-/* groups_per_tile: 1..11 (0 keeps; default 10 for FP32 fields, 11 for    */
-/* BF16; with two warps per group at most 7 run on the node-group kernel, */
-/* more fall back per node; a change rebuilds the operator's tile tables  */
-/* at its next call).                                                      */
+/* groups_per_tile: 1..15 (0 keeps).  Defaults: FP32 10, the Laplacian  */
+/* 12; BF16 11, the Laplacian and the one-input operators 15.  More than */
+/* 11 run only where the kernel fits in 128 registers (the Laplacian, the */
+/* BF16 one-input operators); with two warps per group at most 7 run.     */
+/* Elsewhere the call falls back to the per-node kernel.  A change        */
+/* rebuilds the operator's tile tables at its next call.                  */
 /* nodes_per_warp: 4 (one consumer warp per group) or 2 (two warps per    */
 /* group, each walking two of its nodes: twice the warps per block); 0    */
 /* keeps; default 4.  With one warp per group the tables store the groups */
