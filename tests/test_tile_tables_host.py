@@ -140,7 +140,7 @@ def _decode(fvm, op, groups_per_tile, unions, rows_per_tile=1):
 @pytest.mark.parametrize("name", ["O2", "O24", "F6", "lambert13x9"])
 @pytest.mark.parametrize("op", OPS)
 @pytest.mark.parametrize("unions,rows,groups", [(True, 1, 7), (False, 1, 7), (True, 2, 8), (False, 2, 4),
-                                                (True, 3, 6)])
+                                                (True, 3, 6), (True, 2, 10), (True, 2, 12), (True, 1, 15)])
 def test_tile_tables_give_every_node_its_row(fvms, name, op, unions, rows, groups):
     fvm = fvms[name]
     st = fvm.stencil_table(op)
